@@ -1,0 +1,162 @@
+"""FP64 CPU oracle for the multi-view direction fusion (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` import
+this package.  It shares no code with the CUDA library and never calls it.
+
+The arithmetic lives in ``oracle.c`` (plain C, IEEE double, one point at a time, OpenMP over
+points); this module only marshals numpy arrays.  ``mlp.py`` holds the FP64 reference of the
+learned proposal network.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+
+OK, NO_VIEWS, BAD_INPUT = 0, 1, 2
+FLAG_IDX_TIE, FLAG_REFINE_TIE, FLAG_BOUNDARY = 1, 2, 4
+
+
+class _Scene(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_longlong), ("V", ctypes.c_int), ("W", ctypes.c_int), ("H", ctypes.c_int),
+                ("k", ctypes.c_int), ("pts", ctypes.c_void_p), ("cams", ctypes.c_void_p),
+                ("angle", ctypes.c_void_p), ("conf", ctypes.c_void_p), ("conf_f16", ctypes.c_int),
+                ("nbr", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def build():
+    """Compile liboracle.so next to this file (gcc -O2, OpenMP)."""
+    import subprocess
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", _LIB_PATH,
+                           os.path.join(_HERE, "oracle.c"), "-lm"])
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, ll, i32 = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int
+        lib.or_fuse.argtypes = [vp, ll, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, i32]
+        lib.or_eval_costs.argtypes = [vp, ll, vp, i32, vp, i32, vp, i32]
+        lib.or_fibonacci_hemisphere.argtypes = [i32, vp]
+        lib.or_fibonacci_hemisphere.restype = None
+        lib.or_project.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
+        lib.or_reproject_dir.argtypes = [vp, vp, vp, vp]
+        lib.or_reproject_dir.restype = ctypes.c_double
+        lib.or_view_term.argtypes = [vp, ll, i32, vp]
+        lib.or_view_term.restype = ctypes.c_double
+        lib.or_view_set.argtypes = [vp, ll, i32, vp]
+        lib.or_max_threads.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Scene:
+    """Holds contiguous copies of the scene arrays and the C view of them."""
+
+    def __init__(self, points, cams, angle, conf, nbr):
+        # f32 inputs widen exactly; callers may also pass float64 geometry directly
+        self.points = np.ascontiguousarray(points, np.float64)
+        self.cams = np.ascontiguousarray(cams, np.float64)
+        self.angle = np.ascontiguousarray(angle, np.float32)
+        self.conf_f16 = conf.dtype == np.float16
+        self.conf = np.ascontiguousarray(conf, np.float16 if self.conf_f16 else np.float32)
+        self.k = 0 if nbr is None else int(nbr.shape[1])
+        self.nbr = np.ascontiguousarray(nbr if nbr is not None else np.zeros((len(self.points), 0)), np.int32)
+        V, H, W = self.angle.shape
+        self.V, self.H, self.W, self.N = V, H, W, len(self.points)
+        self.c = _Scene(self.N, V, W, H, self.k, self.points.ctypes.data, self.cams.ctypes.data,
+                        self.angle.ctypes.data, self.conf.ctypes.data, int(self.conf_f16), self.nbr.ctypes.data)
+
+    @classmethod
+    def from_dict(cls, sc, exact=False):
+        if exact:
+            return cls(sc["points"], sc["cams"], sc["exact_angle"], sc["exact_conf"], sc.get("nbr"))
+        return cls(sc["points"], sc["cams"], sc["angle"], sc["conf"], sc.get("nbr"))
+
+
+def fibonacci_hemisphere(H):
+    """(H, 3) float64 Fibonacci hemisphere directions (z_m = 1 - (m+1/2)/H)."""
+    out = np.empty((H, 3), np.float64)
+    _load().or_fibonacci_hemisphere(H, _p(out))
+    return out
+
+
+def fuse(scene, hyps, T, top_k=0, idx=None, threads=0):
+    """Oracle fusion of the listed points (all when idx is None).
+
+    hyps: (H,3) unit directions (f32 values widen exactly).  Returns dict of
+    dir (n,3) f64, cost (n,) f64, idx (n,) i32, status (n,) u8, flags (n,) u8."""
+    lib = _load()
+    hyps = np.ascontiguousarray(hyps, np.float64)
+    H = hyps.shape[0]
+    if idx is None:
+        n, ip = scene.N, None
+    else:
+        idx = np.ascontiguousarray(idx, np.int64)
+        n, ip = len(idx), _p(idx)
+    out = dict(dir=np.empty((n, 3)), cost=np.empty(n), idx=np.empty(n, np.int32),
+               status=np.empty(n, np.uint8), flags=np.empty(n, np.uint8))
+    lib.or_fuse(ctypes.byref(scene.c), n, ip, _p(hyps), H, T, top_k, _p(out["dir"]), _p(out["cost"]),
+                _p(out["idx"]), _p(out["status"]), _p(out["flags"]), threads)
+    return out
+
+
+def eval_costs(scene, dirs, idx=None, top_k=0, threads=0):
+    """c_i(d) for each listed point i and each of its M directions; dirs (n, M, 3)."""
+    lib = _load()
+    dirs = np.ascontiguousarray(dirs, np.float64)
+    n, M = dirs.shape[0], dirs.shape[1]
+    idx = np.arange(scene.N, dtype=np.int64) if idx is None else np.ascontiguousarray(idx, np.int64)
+    assert len(idx) == n
+    out = np.empty((n, M))
+    lib.or_eval_costs(ctypes.byref(scene.c), n, _p(idx), M, _p(dirs), top_k, _p(out), threads)
+    return out
+
+
+def project(cam, p, W, H):
+    """(visible, u, v, a, b) of point p (3,) in camera cam (16,)."""
+    lib = _load()
+    cam = np.ascontiguousarray(cam, np.float64)
+    p = np.ascontiguousarray(p, np.float64)
+    u, v, a, b = (ctypes.c_double() for _ in range(4))
+    vis = lib.or_project(_p(cam), _p(p), W, H, ctypes.byref(u), ctypes.byref(v), ctypes.byref(a), ctypes.byref(b))
+    return vis, u.value, v.value, a.value, b.value
+
+
+def reproject_dir(cam, p, d):
+    """Image-plane offset r (2,) = dPi/dp . d of direction d at point p."""
+    lib = _load()
+    cam = np.ascontiguousarray(cam, np.float64)
+    p = np.ascontiguousarray(p, np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    r = np.empty(2)
+    lib.or_reproject_dir(_p(cam), _p(p), _p(d), _p(r))
+    return r
+
+
+def view_term(scene, i, v, d):
+    """L_v(d) of point i in view v."""
+    d = np.ascontiguousarray(d, np.float64)
+    return _load().or_view_term(ctypes.byref(scene.c), i, v, _p(d))
+
+
+def view_set(scene, i, top_k=0):
+    mask = np.zeros(scene.V, np.uint8)
+    n = _load().or_view_set(ctypes.byref(scene.c), i, top_k, _p(mask))
+    return n, mask
+
+
+def max_threads():
+    return int(_load().or_max_threads())
