@@ -1,0 +1,159 @@
+/*
+ * hair_fuse.h - C ABI of the B300 multi-view hair direction-fusion library.
+ *
+ * The library assigns each 3D hair point a strand direction by fusing per-view 2D orientation
+ * evidence: EfficientMonoHair, Sec. 3.1 ("Fusion-Patch-based Multi-View Optimization"),
+ * patch-based consistency step (Eqs. proj_r, sim, patchloss, patch_min, final_dout), evaluated
+ * over an explicit set of candidate directions (hypotheses), followed by an argmin and a short
+ * rotation pattern-search refinement.  For a point p_i and unit direction d:
+ *
+ *   r_v(d)  = dPi_v/dp(p_i) . d                      image offset of d in view v   (Eq. proj_r)
+ *   L_v(d)  = max_{j in {i} U nbr(i), visible in v}  C_v(u_j) |<r_v/|r_v|, O_v(u_j)>|
+ *                                                    (Eqs. sim, patchloss, patch_min)
+ *   c_i(d)  = 1 - mean_{v in V_i} L_v(d)             (aggregation for Eq. final_dout)
+ *
+ * with O_v(u) = (cos theta, sin theta) from the angle map, nearest-pixel sampling at
+ * (floor u, floor v), V_i the views in which p_i projects inside the image (optionally only the
+ * top-K of them by confidence at p_i's pixel, Sec. 3.1.2).  The output direction is the best
+ * hypothesis refined by T rounds of +-alpha rotations about the world x, y, z axes (alpha_0 =
+ * sqrt(2 pi / H) / 2, halved every round, move only on a strictly lower cost), normalised, with
+ * the first of z, y, x whose magnitude exceeds 1e-12 made positive.
+ *
+ * Conventions (all entry points):
+ *  - Return 0 (HF_OK) or a negative HF_ERR_* code; hair_fuse_last_error() gives a message.
+ *    No entry point aborts the process.
+ *  - mem_kind HF_HOST: pointers are host memory (pageable or pinned); the call copies inputs in
+ *    and, for outputs, returns after they are written back (synchronous).
+ *    mem_kind HF_DEVICE: pointers are device memory of the current device; the work is queued on
+ *    the context's stream and the call returns without waiting.  Device inputs must stay valid
+ *    until the stream has consumed them; outputs are valid once the stream reaches that point.
+ *  - Uploads copy into buffers the context owns; the caller keeps ownership of its own buffers.
+ *  - Errors found on the device (a bad hypothesis, a timed-out wait) are latched in the context
+ *    and returned by the next synchronising call (an HF_HOST call or hair_fuse_sync()).
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef HAIR_FUSE_H
+#define HAIR_FUSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define HF_OK 0
+#define HF_ERR_INVALID_ARG (-1)   /* bad pointer, size, dtype, value (e.g. non-unit hypothesis) */
+#define HF_ERR_NOT_UPLOADED (-2)  /* views or points missing, or inconsistent with each other */
+#define HF_ERR_OOM (-3)           /* a device or pinned allocation failed */
+#define HF_ERR_CUDA (-4)          /* a CUDA runtime call failed */
+#define HF_ERR_TIMEOUT (-5)       /* a bounded device-side wait expired */
+#define HF_ERR_SHAPE (-6)         /* a size exceeds a documented limit */
+
+/* memory kinds */
+#define HF_HOST 0
+#define HF_DEVICE 1
+
+/* confidence map element types */
+#define HF_F32 0
+#define HF_F16 1
+
+/* per-point status values written to status_out */
+#define HF_STATUS_OK 0
+#define HF_STATUS_NO_VIEWS 1    /* the point projects into no view: cost 1, direction = best of ties */
+#define HF_STATUS_BAD_INPUT 2   /* non-finite coordinates: direction 0, cost NaN, index -1 */
+#define HF_STATUS_FELL_BACK 3   /* learned path only: the proposal was rejected, plain fusion used */
+
+/* limits */
+#define HF_MAX_K 16       /* neighbours per point */
+#define HF_MAX_T 24       /* refinement rounds */
+#define HF_MAX_H 1024     /* hypotheses */
+#define HF_MAX_TOPK 16    /* top-K views */
+
+typedef struct hf_ctx hf_ctx;
+
+typedef struct {
+    int H;               /* number of hypotheses, 1..HF_MAX_H */
+    int k;               /* neighbours per point in the patch, 0..HF_MAX_K */
+    int T;               /* refinement rounds, 0..HF_MAX_T */
+    int top_k_views;     /* 0: all views that see the point; K>0: the K most confident (Sec. 3.1.2) */
+    float fallback_tau;  /* learned path: proposals with cost above tau fall back to plain fusion */
+    int flags;           /* reserved, 0 */
+} hf_config;
+
+/* Create a context bound to the current CUDA device and to `cuda_stream` (a cudaStream_t; NULL =
+ * the legacy default stream).  *out receives the context, or NULL on error. */
+int hair_fuse_create(hf_ctx** out, const hf_config* cfg, void* cuda_stream);
+
+/* Rebind the context to another stream (cudaStream_t). */
+int hair_fuse_set_stream(hf_ctx* ctx, void* cuda_stream);
+
+/* Upload the V calibrated views (Sec. 3.1: cameras Pi_v, orientation maps O_v, confidence C_v).
+ *  cams:  V x 16 f32 per view: fx, fy, cx, cy, R (3x3 row-major, world -> camera), t (3);
+ *         camera frame x right, y down, z forward; u = fx X/Z + cx, v = fy Y/Z + cy.
+ *  angle: V x height x width f32, orientation angle theta in [0, pi) in pixel axes (+u right,
+ *         +v down), row-major (row = v, column = u).
+ *  conf:  V x height x width, f32 or IEEE half (conf_dtype HF_F32 / HF_F16), values in [0, 1].
+ * Errors: V < 1, width/height < 1, null pointers, bad dtype -> HF_ERR_INVALID_ARG. */
+int hair_fuse_upload_views(hf_ctx* ctx, int V, int width, int height, const float* cams, const float* angle,
+                           const void* conf, int conf_dtype, int mem_kind);
+
+/* Upload the raw outer point cloud P_raw (Sec. 3.1) and each point's fusion patch.
+ *  xyz: N x 3 f32 world coordinates.
+ *  nbr: N x k int32, the k neighbours of each point (excluding the point itself), each in [0, N).
+ * Errors: N < 1, k >= N, an index outside [0, N) -> HF_ERR_INVALID_ARG.  The indices are checked
+ * by a device kernel and read back, so this call synchronises the stream for either mem_kind. */
+int hair_fuse_upload_points(hf_ctx* ctx, int N, const float* xyz, const int32_t* nbr, int mem_kind);
+
+/* Fuse the directions of all uploaded points (Eqs. proj_r .. final_dout, argmin, refinement).
+ *  hyps:       H x 3 f32 unit directions (|h| within 1e-3 of 1), or NULL for the built-in
+ *              Fibonacci hemisphere z_m = 1 - (m + 1/2)/H, azimuth m pi (3 - sqrt 5).
+ *  dir_out:    N x 3 f32, unit direction with canonical sign.
+ *  cost_out:   N f32, c_i of the returned direction (may be NULL).
+ *  idx_out:    N int32, index of the best hypothesis (may be NULL).
+ *  status_out: N uint8, HF_STATUS_* (may be NULL).
+ * All of hyps and the outputs are of kind mem_kind.
+ * Errors: nothing uploaded -> HF_ERR_NOT_UPLOADED; non-unit hypothesis -> HF_ERR_INVALID_ARG. */
+int hair_fuse_fuse_directions(hf_ctx* ctx, const float* hyps, float* dir_out, float* cost_out, int32_t* idx_out,
+                              uint8_t* status_out, int mem_kind);
+
+/* Evaluate the cost c_i(d) of M given directions for every point (no argmin, no refinement).
+ *  dirs: N x M x 3 f32 (any non-zero length; the cost is scale- and sign-invariant),
+ *  cost_out: N x M f32.  Both of kind mem_kind. */
+int hair_fuse_eval_costs(hf_ctx* ctx, int M, const float* dirs, float* cost_out, int mem_kind);
+
+/* The built-in hypothesis set (host memory): H x 3 f32 Fibonacci hemisphere directions. */
+int hair_fuse_fibonacci_hemisphere(int H, float* out);
+
+/* Wait for the context's stream and return any error latched on the device. */
+int hair_fuse_sync(hf_ctx* ctx);
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around every launch.
+ * hair_fuse_profile(ctx, 1) clears and enables it; hair_fuse_profile_read() synchronises and
+ * fills up to max_entries records, returning how many kernels have records. */
+typedef struct {
+    char name[32];
+    int launches;
+    double total_ms;
+} hf_kernel_time;
+int hair_fuse_profile(hf_ctx* ctx, int enable);
+int hair_fuse_profile_read(hf_ctx* ctx, hf_kernel_time* out, int max_entries);
+
+/* Number of (point, view) pairs in the points' view sets V_i at the last fuse or eval call
+ * (synchronises the stream): the unit of work of the cost evaluation. */
+int hair_fuse_work(hf_ctx* ctx, long long* point_views);
+
+/* Bytes of device memory the context holds and the number of kernel launches it has issued
+ * (kernels of this library only). */
+int hair_fuse_stats(const hf_ctx* ctx, long long* device_bytes, long long* launches);
+
+void hair_fuse_destroy(hf_ctx* ctx);
+
+/* Message of the last error on this context (never NULL); ctx may be NULL for create errors. */
+const char* hair_fuse_last_error(const hf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAIR_FUSE_H */

@@ -1,0 +1,216 @@
+"""Python binding of libhairfuse (multi-view hair direction fusion on B300, sm_103a).
+
+Argument marshalling only: every step of the fusion runs in the library's CUDA kernels.  The
+functions below carry the C names of ``include/hair_fuse.h``; ``HairFuse`` wraps a context.
+Tensors may be CUDA tensors (passed as device pointers, work queued on the context's stream) or
+host tensors / numpy arrays (the library copies in and out and returns when done).
+
+There is no CPU fallback: importing this package raises if the compiled library is missing.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhairfuse.so")
+
+HF_OK, HF_ERR_INVALID_ARG, HF_ERR_NOT_UPLOADED, HF_ERR_OOM, HF_ERR_CUDA, HF_ERR_TIMEOUT, HF_ERR_SHAPE = 0, -1, -2, -3, -4, -5, -6
+HF_HOST, HF_DEVICE = 0, 1
+HF_F32, HF_F16 = 0, 1
+HF_STATUS_OK, HF_STATUS_NO_VIEWS, HF_STATUS_BAD_INPUT, HF_STATUS_FELL_BACK = 0, 1, 2, 3
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libhairfuse.so is not built ({LIB_PATH}); run __graft_entry__.build() or "
+                      "python paper_2604_05794_b300/build.py")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class hf_config(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("k", ctypes.c_int), ("T", ctypes.c_int), ("top_k_views", ctypes.c_int),
+                ("fallback_tau", ctypes.c_float), ("flags", ctypes.c_int)]
+
+
+class hf_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double)]
+
+
+_vp, _i, _ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+_SIGS = {
+    "hair_fuse_create": ([ctypes.POINTER(_vp), ctypes.POINTER(hf_config), _vp], _i),
+    "hair_fuse_set_stream": ([_vp, _vp], _i),
+    "hair_fuse_upload_views": ([_vp, _i, _i, _i, _vp, _vp, _vp, _i, _i], _i),
+    "hair_fuse_upload_points": ([_vp, _i, _vp, _vp, _i], _i),
+    "hair_fuse_fuse_directions": ([_vp, _vp, _vp, _vp, _vp, _vp, _i], _i),
+    "hair_fuse_eval_costs": ([_vp, _i, _vp, _vp, _i], _i),
+    "hair_fuse_fibonacci_hemisphere": ([_i, _vp], _i),
+    "hair_fuse_sync": ([_vp], _i),
+    "hair_fuse_profile": ([_vp, _i], _i),
+    "hair_fuse_profile_read": ([_vp, ctypes.POINTER(hf_kernel_time), _i], _i),
+    "hair_fuse_stats": ([_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll)], _i),
+    "hair_fuse_work": ([_vp, ctypes.POINTER(_ll)], _i),
+    "hair_fuse_destroy": ([_vp], None),
+    "hair_fuse_last_error": ([_vp], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+# the C entry points, under their C names
+hair_fuse_create = _lib.hair_fuse_create
+hair_fuse_set_stream = _lib.hair_fuse_set_stream
+hair_fuse_upload_views = _lib.hair_fuse_upload_views
+hair_fuse_upload_points = _lib.hair_fuse_upload_points
+hair_fuse_fuse_directions = _lib.hair_fuse_fuse_directions
+hair_fuse_eval_costs = _lib.hair_fuse_eval_costs
+hair_fuse_fibonacci_hemisphere = _lib.hair_fuse_fibonacci_hemisphere
+hair_fuse_sync = _lib.hair_fuse_sync
+hair_fuse_profile = _lib.hair_fuse_profile
+hair_fuse_profile_read = _lib.hair_fuse_profile_read
+hair_fuse_stats = _lib.hair_fuse_stats
+hair_fuse_work = _lib.hair_fuse_work
+hair_fuse_destroy = _lib.hair_fuse_destroy
+hair_fuse_last_error = _lib.hair_fuse_last_error
+
+
+class HairFuseError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hair_fuse error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc, ctx=None):
+    if rc != HF_OK:
+        msg = hair_fuse_last_error(ctx)
+        raise HairFuseError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr_kind(x):
+    """(pointer, mem_kind, keepalive) of a torch tensor or numpy array; None -> NULL."""
+    if x is None:
+        return None, None, None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays must be C-contiguous")
+        return x.ctypes.data, HF_HOST, x
+    import torch
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr(), (HF_DEVICE if x.is_cuda else HF_HOST), x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _same_kind(*kinds):
+    ks = {k for k in kinds if k is not None}
+    if len(ks) > 1:
+        raise ValueError("all buffers of one call must be either host or device memory")
+    return ks.pop() if ks else HF_HOST
+
+
+def current_stream_handle():
+    """torch's current CUDA stream (cudaStream_t as int), or 0 (default stream) without CUDA."""
+    import torch
+    if not torch.cuda.is_available():
+        return 0
+    return torch.cuda.current_stream().cuda_stream
+
+
+def fibonacci_hemisphere(H):
+    """The library's built-in hypotheses, (H, 3) float32 (computed on the GPU)."""
+    out = np.empty((H, 3), np.float32)
+    _check(hair_fuse_fibonacci_hemisphere(H, out.ctypes.data))
+    return out
+
+
+class HairFuse:
+    """One fusion context: a scene (views + points) and the configuration (H, k, T, top-K)."""
+
+    def __init__(self, H, k, T, top_k_views=0, fallback_tau=0.0, stream=None):
+        self.cfg = hf_config(H, k, T, top_k_views, fallback_tau, 0)
+        if stream is None:
+            stream = current_stream_handle()
+        h = _vp()
+        _check(hair_fuse_create(ctypes.byref(h), ctypes.byref(self.cfg), stream))
+        self.h = h
+        self.N = self.V = 0
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            hair_fuse_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _c(self, rc):
+        return _check(rc, self.h)
+
+    def set_stream(self, stream):
+        self._c(hair_fuse_set_stream(self.h, stream))
+
+    def upload_views(self, cams, angle, conf):
+        """cams (V,16) f32, angle (V,H,W) f32, conf (V,H,W) f32 or f16."""
+        V, Hh, W = angle.shape
+        cdt = HF_F16 if str(conf.dtype).endswith("float16") else HF_F32
+        pc, k1, a = _ptr_kind(cams)
+        pa, k2, b = _ptr_kind(angle)
+        pf, k3, c = _ptr_kind(conf)
+        kind = _same_kind(k1, k2, k3)
+        self._c(hair_fuse_upload_views(self.h, V, W, Hh, pc, pa, pf, cdt, kind))
+        self.V = V
+        self._keep = [a, b, c]
+
+    def upload_points(self, xyz, nbr):
+        """xyz (N,3) f32, nbr (N,k) int32."""
+        px, k1, a = _ptr_kind(xyz)
+        pn, k2, b = _ptr_kind(nbr)
+        self._c(hair_fuse_upload_points(self.h, xyz.shape[0], px, pn, _same_kind(k1, k2)))
+        self.N = xyz.shape[0]
+        self._keep += [a, b]
+
+    def fuse(self, dir_out, cost_out=None, idx_out=None, status_out=None, hyps=None):
+        """Fuse all points into caller buffers (all host or all device)."""
+        ptrs = [_ptr_kind(x) for x in (hyps, dir_out, cost_out, idx_out, status_out)]
+        kind = _same_kind(*[p[1] for p in ptrs])
+        self._c(hair_fuse_fuse_directions(self.h, *[p[0] for p in ptrs], kind))
+
+    def eval_costs(self, dirs, cost_out):
+        """Costs (N,M) of the directions dirs (N,M,3)."""
+        pd, k1, _ = _ptr_kind(dirs)
+        pc, k2, _ = _ptr_kind(cost_out)
+        self._c(hair_fuse_eval_costs(self.h, dirs.shape[1], pd, pc, _same_kind(k1, k2)))
+
+    def sync(self):
+        self._c(hair_fuse_sync(self.h))
+
+    def profile(self, enable=True):
+        self._c(hair_fuse_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel name: (launches, total_ms)} of the launches since profile(True)."""
+        buf = (hf_kernel_time * 64)()
+        n = hair_fuse_profile_read(self.h, buf, 64)
+        if n < 0:
+            self._c(n)
+        return {buf[q].name.decode(): (buf[q].launches, buf[q].total_ms) for q in range(min(n, 64))}
+
+    def work(self):
+        """(point, view) pairs in the view sets at the last fuse / eval call."""
+        w = _ll()
+        self._c(hair_fuse_work(self.h, ctypes.byref(w)))
+        return w.value
+
+    def stats(self):
+        b, l = _ll(), _ll()
+        self._c(hair_fuse_stats(self.h, ctypes.byref(b), ctypes.byref(l)))
+        return {"device_bytes": b.value, "launches": l.value}

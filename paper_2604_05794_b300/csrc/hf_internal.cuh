@@ -1,0 +1,113 @@
+// hf_internal.cuh - internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/hair_fuse.h"
+
+// Device-side error word bits (latched, read back by synchronising calls).
+enum : uint32_t {
+    HF_DEV_ERR_BAD_HYP = 1u,      // a hypothesis is not unit length within 1e-3
+    HF_DEV_ERR_BAD_NBR = 2u,      // a neighbour index outside [0, N)
+    HF_DEV_ERR_TIMEOUT = 4u,      // a bounded wait expired
+};
+
+// Grow-only device buffer owned by the context.
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+// Per-kernel timing record (profiling mode).
+struct ProfRec {
+    std::string name;
+    cudaEvent_t beg, end;
+};
+
+struct hf_ctx {
+    hf_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    // views
+    int V = 0, W = 0, Hh = 0, conf_dtype = HF_F32;
+    DevBuf cams, angle, conf;
+    // points
+    int N = 0, k = 0;
+    DevBuf pts, nbr;
+    // scratch of the fusion path
+    DevBuf samp;    // [V][N] float2: C (cos theta, sin theta) at the point's pixel, 0 when not visible
+    DevBuf ab;      // [V][N] float2: projection ratios (X/Z, Y/Z); NaN when v is not in the point's view set
+    DevBuf qtab;    // [V][Hpad] float4: (fx q_x, fx q_z, fy q_y, fy q_z), q = R_v h_m
+    DevBuf vthr;    // [V] float: degenerate-offset threshold 1e-20 (fx^2 + fy^2)
+    DevBuf hyps;    // [Hpad] x 3 float
+    DevBuf rot;     // [T] float2: (cos alpha_t, sin alpha_t)
+    DevBuf outs;    // device outputs staged for HF_HOST calls
+    DevBuf evald;   // device copy of eval directions for HF_HOST calls
+    DevBuf errw;    // uint32 device error word
+    DevBuf work;    // uint64 (point, view) pairs of the last projection
+    uint32_t* errw_host = nullptr;  // pinned read-back slot
+    long long launches = 0;
+    long long dev_bytes = 0;
+    bool prof = false;
+    std::vector<ProfRec> prof_recs;
+};
+
+// Error helpers -------------------------------------------------------------------------------
+int hf_set_err(hf_ctx* c, int code, const char* fmt, ...);
+int hf_cuda_err(hf_ctx* c, cudaError_t e, const char* what);
+int hf_ensure(hf_ctx* c, DevBuf& b, size_t bytes);
+
+// Kernel-launch helpers (defined in hf_kernels.cu); each returns the launch error -------------
+struct ProjectArgs {
+    const float* pts; int N;
+    const float* cams; int V; int W; int H;
+    const float* angle; const void* conf; int conf_f16;
+    int top_k;
+    float2* samp; float2* ab;
+    unsigned long long* work;   // += number of (point, view) pairs in the view sets
+};
+cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s);
+
+struct PrepArgs {
+    const float* cams; int V;
+    const float* hyps_in;  // device H x 3, or nullptr for the Fibonacci set
+    int H; int Hpad; int T;
+    float* hyps;           // out Hpad x 3
+    float4* qtab;          // out [V][Hpad]
+    float* vthr;           // out [V]
+    float2* rot;           // out [T]
+    uint32_t* errw;
+};
+cudaError_t hf_launch_prep(const PrepArgs& a, cudaStream_t s);
+
+struct FuseArgs {
+    const float* pts; int N;
+    const int32_t* nbr; int k;
+    const float* cams; int V;
+    const float2* samp; const float2* ab;
+    const float4* qtab; const float* vthr;
+    const float* hyps; int H; int Hpad;
+    const float2* rot; int T;
+    float* dir_out; float* cost_out; int32_t* idx_out; uint8_t* status_out;
+};
+int hf_fuse_chunk_for(int H);
+cudaError_t hf_launch_fuse(const FuseArgs& a, int hchunk, cudaStream_t s, const char** kname);
+
+struct EvalArgs {
+    const float* pts; int N;
+    const int32_t* nbr; int k;
+    const float* cams; int V;
+    const float2* samp; const float2* ab;
+    const float* vthr;
+    const float* dirs; int M;
+    float* cost_out;
+};
+cudaError_t hf_launch_eval(const EvalArgs& a, cudaStream_t s);
+
+cudaError_t hf_launch_fib(int H, float* out, cudaStream_t s);
+cudaError_t hf_launch_check_nbr(const int32_t* nbr, long long n, int N, uint32_t* errw, cudaStream_t s);

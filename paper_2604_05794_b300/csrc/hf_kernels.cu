@@ -1,0 +1,465 @@
+// hf_kernels.cu - the fusion path's device code for sm_103a.
+//
+//   k_prep          per-scene constants: hypothesis table q = R_v h_m (folded with fx, fy),
+//                   degenerate thresholds, refinement rotation steps.
+//   k_project       K1, thread per point: projection of the point into every view with the pixel
+//                   index decided in float-float arithmetic, nearest-pixel gather of the orientation
+//                   and confidence maps, view set (visible or top-K) of the point.
+//   k_fuse<HC, KP>  K2 + K3, thread per point: cost of all hypotheses (Eqs. proj_r .. patch_min and
+//                   the view mean), argmin, then T rounds of the six-rotation refinement.
+//   k_eval<KP>      cost of caller-given directions (no argmin).
+#include <math.h>
+
+#include "hf_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------ float-float arithmetic
+// Error-free transformations on FP32 (Knuth two-sum, FMA two-product).  A value is hi + lo with
+// |lo| <= ulp(hi)/2; about 44 significant bits survive the operations below, which places a
+// projected pixel coordinate within ~1e-10 px of its exact value, so floor() picks the same pixel
+// as an exact evaluation except for coordinates within that distance of a pixel edge.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return {p, e};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    ff s = two_sum(x.hi, y.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return fast_two_sum(s.hi, e);
+}
+// r0 p0 + r1 p1 + r2 p2 + t, all inputs exact FP32
+__device__ __forceinline__ ff ff_dot3_plus(float r0, float r1, float r2, float p0, float p1, float p2, float t) {
+    ff s = ff_add(two_prod(r0, p0), two_prod(r1, p1));
+    s = ff_add(s, two_prod(r2, p2));
+    return ff_add(s, ff{t, 0.0f});
+}
+// x / y
+__device__ __forceinline__ ff ff_div(ff x, ff y) {
+    float q1 = __fdiv_rn(x.hi, y.hi);
+    ff p = two_prod(q1, y.hi);
+    float r = __fsub_rn(x.hi, p.hi);  // exact (Sterbenz): p.hi is within a factor 2 of x.hi
+    r = __fsub_rn(r, p.lo);
+    r = __fadd_rn(r, x.lo);
+    r = __fmaf_rn(-q1, y.lo, r);
+    float q2 = __fdiv_rn(r, y.hi);
+    return fast_two_sum(q1, q2);
+}
+// f * a + c, f and c exact FP32
+__device__ __forceinline__ ff ff_affine(float f, ff a, float c) {
+    ff m = two_prod(f, a.hi);
+    m.lo = __fmaf_rn(f, a.lo, m.lo);
+    m = fast_two_sum(m.hi, m.lo);
+    return ff_add(m, ff{c, 0.0f});
+}
+// floor(hi + lo) for a normalised pair
+__device__ __forceinline__ float ff_floor(ff x) {
+    float f = floorf(x.hi);
+    if (f == x.hi && x.lo < 0.0f) f -= 1.0f;
+    return f;
+}
+
+__device__ __forceinline__ float load_conf(const void* conf, int f16, size_t o) {
+    if (f16) return __half2float(reinterpret_cast<const __half*>(conf)[o]);
+    return reinterpret_cast<const float*>(conf)[o];
+}
+
+// ------------------------------------------------------------------ K1: project + gather
+// One thread per point, views in order.  For view v it writes
+//   samp[v][i] = C (cos theta, sin theta) at the point's pixel (0 when outside the view),
+//   ab[v][i]   = (X/Z, Y/Z) when v is in the point's view set, NaN otherwise.
+// The view set is every view the point projects into, or with top_k > 0 the top_k of them by the
+// confidence at the point's own pixel, ties to the lower view index.
+template <bool TOPK>
+__global__ void __launch_bounds__(128) k_project(ProjectArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
+    const size_t npx = (size_t)a.W * a.H;
+    const float qnan = __int_as_float(0x7fc00000);
+    float topc[HF_MAX_TOPK];
+    int topv[HF_MAX_TOPK];
+    int ntop = 0, nset = 0;
+    for (int v = 0; v < a.V; ++v) {
+        const float* cam = a.cams + 16 * v;
+        const float fx = __ldg(cam), fy = __ldg(cam + 1), cx = __ldg(cam + 2), cy = __ldg(cam + 3);
+        ff X0 = ff_dot3_plus(__ldg(cam + 4), __ldg(cam + 5), __ldg(cam + 6), p0, p1, p2, __ldg(cam + 13));
+        ff X1 = ff_dot3_plus(__ldg(cam + 7), __ldg(cam + 8), __ldg(cam + 9), p0, p1, p2, __ldg(cam + 14));
+        ff X2 = ff_dot3_plus(__ldg(cam + 10), __ldg(cam + 11), __ldg(cam + 12), p0, p1, p2, __ldg(cam + 15));
+        bool vis = X2.hi > 1e-6f;
+        float2 s = make_float2(0.0f, 0.0f), r = make_float2(qnan, qnan);
+        if (vis) {
+            ff ra = ff_div(X0, X2), rb = ff_div(X1, X2);
+            float fu = ff_floor(ff_affine(fx, ra, cx));
+            float fv = ff_floor(ff_affine(fy, rb, cy));
+            vis = fu >= 0.0f && fu < (float)a.W && fv >= 0.0f && fv < (float)a.H;
+            if (vis) {
+                const size_t o = (size_t)v * npx + (size_t)fv * a.W + (size_t)fu;
+                const float th = __ldg(a.angle + o);
+                const float C = load_conf(a.conf, a.conf_f16, o);
+                float sn, cs;
+                sincosf(th, &sn, &cs);
+                s = make_float2(C * cs, C * sn);
+                r = make_float2(ra.hi, rb.hi);
+                ++nset;
+                if (TOPK) {
+                    // keep the top_k (conf desc, view asc); later views need a strictly larger conf
+                    if (ntop < a.top_k || C > topc[ntop - 1]) {
+                        int pos = ntop < a.top_k ? ntop++ : ntop - 1;
+                        while (pos > 0 && C > topc[pos - 1]) {
+                            topc[pos] = topc[pos - 1];
+                            topv[pos] = topv[pos - 1];
+                            --pos;
+                        }
+                        topc[pos] = C;
+                        topv[pos] = v;
+                    }
+                }
+            }
+        }
+        a.samp[(size_t)v * a.N + i] = s;
+        a.ab[(size_t)v * a.N + i] = r;
+    }
+    if (TOPK) {
+        for (int v = 0; v < a.V; ++v) {
+            bool keep = false;
+            for (int q = 0; q < ntop; ++q) keep |= (topv[q] == v);
+            if (!keep) a.ab[(size_t)v * a.N + i] = make_float2(qnan, qnan);
+        }
+        nset = ntop;
+    }
+    // warp-aggregated count of the (point, view) pairs in the view sets
+    const unsigned am = __activemask();
+    const unsigned tot = __reduce_add_sync(am, (unsigned)nset);
+    if ((threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(a.work, (unsigned long long)tot);
+}
+
+// ------------------------------------------------------------------ per-scene constants
+// Built-in hypothesis m of H: Fibonacci lattice on the upper hemisphere (the cost is
+// sign-invariant, Eq. sim), z_m = 1 - (m + 1/2)/H, azimuth m * pi * (3 - sqrt 5).
+__device__ void fib_dir(int m, int H, double* h) {
+    const double kPi = 3.14159265358979323846;
+    const double z = 1.0 - (m + 0.5) / H;
+    const double rho = sqrt(fmax(0.0, 1.0 - z * z));
+    const double ph = m * kPi * (3.0 - sqrt(5.0));
+    h[0] = rho * cos(ph);
+    h[1] = rho * sin(ph);
+    h[2] = z;
+}
+
+__global__ void k_fib(int H, float* out) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < H; m += gridDim.x * blockDim.x) {
+        double h[3];
+        fib_dir(m, H, h);
+        for (int q = 0; q < 3; ++q) out[3 * m + q] = (float)h[q];
+    }
+}
+
+__global__ void k_prep(PrepArgs a) {
+    const double kPi = 3.14159265358979323846;
+    for (int m = threadIdx.x; m < a.Hpad; m += blockDim.x) {
+        const int src = m < a.H ? m : 0;
+        double h[3];
+        if (a.hyps_in == nullptr) {
+            fib_dir(src, a.H, h);
+        } else {
+            for (int q = 0; q < 3; ++q) h[q] = a.hyps_in[3 * src + q];
+            const double n = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+            if (!(fabs(n - 1.0) <= 1e-3)) atomicOr(a.errw, HF_DEV_ERR_BAD_HYP);
+        }
+        for (int q = 0; q < 3; ++q) a.hyps[3 * m + q] = (float)h[q];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < a.V * a.Hpad; e += blockDim.x) {
+        const int v = e / a.Hpad, m = e % a.Hpad;
+        const float* cam = a.cams + 16 * v;
+        double q[3];
+        for (int r = 0; r < 3; ++r)
+            q[r] = (double)cam[4 + 3 * r] * a.hyps[3 * m] + (double)cam[5 + 3 * r] * a.hyps[3 * m + 1] +
+                   (double)cam[6 + 3 * r] * a.hyps[3 * m + 2];
+        a.qtab[e] = make_float4((float)(cam[0] * q[0]), (float)(cam[0] * q[2]), (float)(cam[1] * q[1]),
+                                (float)(cam[1] * q[2]));
+    }
+    for (int v = threadIdx.x; v < a.V; v += blockDim.x) {
+        const double fx = a.cams[16 * v], fy = a.cams[16 * v + 1];
+        a.vthr[v] = (float)(1e-20 * (fx * fx + fy * fy));
+    }
+    for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
+        const double al = 0.5 * sqrt(2.0 * kPi / a.H) / (double)(1u << t);
+        a.rot[t] = make_float2((float)cos(al), (float)sin(al));
+    }
+}
+
+// ------------------------------------------------------------------ K2 + K3
+// Patch term of one direction in one view: r = (rx, ry) is Z times the image offset (the scale
+// cancels), s[] the patch samples C (cos theta, sin theta).  Returns max_j |<r, s_j>| / |r|, or 0
+// when |r|^2 is below the degenerate threshold.
+template <int KP>
+__device__ __forceinline__ float view_term(float rx, float ry, const float2 (&s)[KP], float thr) {
+    const float r2 = fmaf(rx, rx, ry * ry);
+    float mx = 0.0f;
+#pragma unroll
+    for (int j = 0; j < KP; ++j) mx = fmaxf(mx, fabsf(fmaf(rx, s[j].x, ry * s[j].y)));
+    return r2 >= thr ? mx * rsqrtf(r2) : 0.0f;
+}
+
+template <int KP>
+__device__ __forceinline__ void load_patch(const float2* __restrict__ samp, size_t base, int i, const int (&nb)[KP],
+                                           float2 (&s)[KP]) {
+    s[0] = samp[base + i];
+#pragma unroll
+    for (int j = 1; j < KP; ++j) s[j] = nb[j] >= 0 ? samp[base + nb[j]] : make_float2(0.0f, 0.0f);
+}
+
+template <int HC, int KP>
+__global__ void __launch_bounds__(128) k_fuse(FuseArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
+    if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) {
+        a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
+        if (a.cost_out) a.cost_out[i] = __int_as_float(0x7fc00000);
+        if (a.idx_out) a.idx_out[i] = -1;
+        if (a.status_out) a.status_out[i] = HF_STATUS_BAD_INPUT;
+        return;
+    }
+    int nb[KP];
+    nb[0] = i;
+#pragma unroll
+    for (int j = 1; j < KP; ++j) nb[j] = (j - 1) < a.k ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
+
+    // ---- cost of every hypothesis, HC at a time; argmin with the lowest index on ties
+    float best = INFINITY;
+    int bestm = 0, nv = 0;
+    for (int c0 = 0; c0 < a.Hpad; c0 += HC) {
+        float acc[HC];
+#pragma unroll
+        for (int m = 0; m < HC; ++m) acc[m] = 0.0f;
+        nv = 0;
+        for (int v = 0; v < a.V; ++v) {
+            const size_t base = (size_t)v * a.N;
+            const float2 r = a.ab[base + i];
+            if (r.x != r.x) continue;
+            ++nv;
+            float2 s[KP];
+            load_patch<KP>(a.samp, base, i, nb, s);
+            const float thr = __ldg(a.vthr + v);
+            const float4* __restrict__ q = a.qtab + (size_t)v * a.Hpad + c0;
+#pragma unroll
+            for (int m = 0; m < HC; ++m) {
+                const float4 Q = __ldg(q + m);
+                acc[m] += view_term<KP>(fmaf(-r.x, Q.y, Q.x), fmaf(-r.y, Q.w, Q.z), s, thr);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < HC; ++m) {
+            const float c = nv ? 1.0f - acc[m] / (float)nv : 1.0f;
+            if (c0 + m < a.H && c < best) {
+                best = c;
+                bestm = c0 + m;
+            }
+        }
+    }
+
+    // ---- refinement: +-alpha about x, y, z; move to the first strictly lowest cost; halve alpha
+    float d0 = a.hyps[3 * bestm], d1 = a.hyps[3 * bestm + 1], d2 = a.hyps[3 * bestm + 2];
+    for (int t = 0; t < a.T; ++t) {
+        const float2 cs = a.rot[t];
+        const float c = cs.x, sn = cs.y;
+        float cd[6][3] = {{d0, c * d1 - sn * d2, sn * d1 + c * d2}, {d0, c * d1 + sn * d2, -sn * d1 + c * d2},
+                          {c * d0 + sn * d2, d1, -sn * d0 + c * d2}, {c * d0 - sn * d2, d1, sn * d0 + c * d2},
+                          {c * d0 - sn * d1, sn * d0 + c * d1, d2}, {c * d0 + sn * d1, -sn * d0 + c * d1, d2}};
+        float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (nv) {
+            for (int v = 0; v < a.V; ++v) {
+                const size_t base = (size_t)v * a.N;
+                const float2 r = a.ab[base + i];
+                if (r.x != r.x) continue;
+                float2 s[KP];
+                load_patch<KP>(a.samp, base, i, nb, s);
+                const float* cam = a.cams + 16 * v;
+                const float fx = __ldg(cam), fy = __ldg(cam + 1);
+                const float R6 = __ldg(cam + 10), R7 = __ldg(cam + 11), R8 = __ldg(cam + 12);
+                // Z times the projection Jacobian: rows fx (R_0 - a R_2), fy (R_1 - b R_2)
+                const float j0 = fx * fmaf(-r.x, R6, __ldg(cam + 4)), j1 = fx * fmaf(-r.x, R7, __ldg(cam + 5)),
+                            j2 = fx * fmaf(-r.x, R8, __ldg(cam + 6));
+                const float j3 = fy * fmaf(-r.y, R6, __ldg(cam + 7)), j4 = fy * fmaf(-r.y, R7, __ldg(cam + 8)),
+                            j5 = fy * fmaf(-r.y, R8, __ldg(cam + 9));
+                const float thr = __ldg(a.vthr + v);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const float rx = fmaf(j0, cd[q][0], fmaf(j1, cd[q][1], j2 * cd[q][2]));
+                    const float ry = fmaf(j3, cd[q][0], fmaf(j4, cd[q][1], j5 * cd[q][2]));
+                    acc[q] += view_term<KP>(rx, ry, s, thr);
+                }
+            }
+        }
+        int choice = -1;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const float cq = nv ? 1.0f - acc[q] / (float)nv : 1.0f;
+            if (cq < best) {
+                best = cq;
+                choice = q;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            if (q == choice) {
+                d0 = cd[q][0];
+                d1 = cd[q][1];
+                d2 = cd[q][2];
+            }
+    }
+    const float n = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    d0 /= n;
+    d1 /= n;
+    d2 /= n;
+    const float sg = fabsf(d2) > 1e-12f ? copysignf(1.0f, d2) : fabsf(d1) > 1e-12f ? copysignf(1.0f, d1) : copysignf(1.0f, d0);
+    a.dir_out[3 * i] = sg * d0;
+    a.dir_out[3 * i + 1] = sg * d1;
+    a.dir_out[3 * i + 2] = sg * d2;
+    if (a.cost_out) a.cost_out[i] = best;
+    if (a.idx_out) a.idx_out[i] = bestm;
+    if (a.status_out) a.status_out[i] = nv ? HF_STATUS_OK : HF_STATUS_NO_VIEWS;
+}
+
+// ------------------------------------------------------------------ cost of given directions
+template <int KP>
+__global__ void __launch_bounds__(128) k_eval(EvalArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    int nb[KP];
+    nb[0] = i;
+#pragma unroll
+    for (int j = 1; j < KP; ++j) nb[j] = (j - 1) < a.k ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
+    for (int m = 0; m < a.M; ++m) {
+        const float* d = a.dirs + ((size_t)i * a.M + m) * 3;
+        const float d0 = d[0], d1 = d[1], d2 = d[2];
+        const float dn2 = d0 * d0 + d1 * d1 + d2 * d2;
+        float acc = 0.0f;
+        int nv = 0;
+        for (int v = 0; v < a.V; ++v) {
+            const size_t base = (size_t)v * a.N;
+            const float2 r = a.ab[base + i];
+            if (r.x != r.x) continue;
+            ++nv;
+            float2 s[KP];
+            load_patch<KP>(a.samp, base, i, nb, s);
+            const float* cam = a.cams + 16 * v;
+            const float fx = cam[0], fy = cam[1];
+            float q[3];
+            for (int rr = 0; rr < 3; ++rr) q[rr] = fmaf(cam[4 + 3 * rr], d0, fmaf(cam[5 + 3 * rr], d1, cam[6 + 3 * rr] * d2));
+            const float rx = fx * fmaf(-r.x, q[2], q[0]);
+            const float ry = fy * fmaf(-r.y, q[2], q[1]);
+            acc += view_term<KP>(rx, ry, s, a.vthr[v] * dn2);
+        }
+        a.cost_out[(size_t)i * a.M + m] = nv ? 1.0f - acc / (float)nv : 1.0f;
+    }
+}
+
+__global__ void k_check_nbr(const int32_t* __restrict__ nbr, long long n, int N, uint32_t* errw) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int j = nbr[e];
+        if (j < 0 || j >= N) {
+            atomicOr(errw, HF_DEV_ERR_BAD_NBR);
+            return;
+        }
+    }
+}
+
+// patch width (k + 1) rounded up to an instantiated size
+int kp_for(int k) {
+    const int need = k + 1;
+    if (need <= 1) return 1;
+    if (need <= 4) return 4;
+    if (need <= 6) return 6;
+    if (need <= 9) return 9;
+    if (need <= 12) return 12;
+    return 17;
+}
+
+template <int HC>
+cudaError_t launch_fuse_hc(const FuseArgs& a, cudaStream_t s, const char** kname) {
+    const dim3 grid((a.N + 127) / 128), block(128);
+    switch (kp_for(a.k)) {
+        case 1: k_fuse<HC, 1><<<grid, block, 0, s>>>(a); break;
+        case 4: k_fuse<HC, 4><<<grid, block, 0, s>>>(a); break;
+        case 6: k_fuse<HC, 6><<<grid, block, 0, s>>>(a); break;
+        case 9: k_fuse<HC, 9><<<grid, block, 0, s>>>(a); break;
+        case 12: k_fuse<HC, 12><<<grid, block, 0, s>>>(a); break;
+        default: k_fuse<HC, 17><<<grid, block, 0, s>>>(a); break;
+    }
+    if (kname) *kname = "k_fuse";
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int hf_fuse_chunk_for(int H) {
+    if (H <= 8) return 8;
+    if (H <= 16) return 16;
+    return 32;
+}
+
+cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s) {
+    const dim3 grid((a.N + 127) / 128), block(128);
+    if (a.top_k > 0) k_project<true><<<grid, block, 0, s>>>(a);
+    else k_project<false><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_prep(const PrepArgs& a, cudaStream_t s) {
+    k_prep<<<1, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_fuse(const FuseArgs& a, int hchunk, cudaStream_t s, const char** kname) {
+    switch (hchunk) {
+        case 8: return launch_fuse_hc<8>(a, s, kname);
+        case 16: return launch_fuse_hc<16>(a, s, kname);
+        case 32: return launch_fuse_hc<32>(a, s, kname);
+        default: return launch_fuse_hc<64>(a, s, kname);
+    }
+}
+
+cudaError_t hf_launch_eval(const EvalArgs& a, cudaStream_t s) {
+    const dim3 grid((a.N + 127) / 128), block(128);
+    switch (kp_for(a.k)) {
+        case 1: k_eval<1><<<grid, block, 0, s>>>(a); break;
+        case 4: k_eval<4><<<grid, block, 0, s>>>(a); break;
+        case 6: k_eval<6><<<grid, block, 0, s>>>(a); break;
+        case 9: k_eval<9><<<grid, block, 0, s>>>(a); break;
+        case 12: k_eval<12><<<grid, block, 0, s>>>(a); break;
+        default: k_eval<17><<<grid, block, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_fib(int H, float* out, cudaStream_t s) {
+    k_fib<<<(H + 127) / 128, 128, 0, s>>>(H, out);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_check_nbr(const int32_t* nbr, long long n, int N, uint32_t* errw, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = (n + 255) / 256;
+    k_check_nbr<<<(unsigned)(blocks < 1184 ? blocks : 1184), 256, 0, s>>>(nbr, n, N, errw);
+    return cudaGetLastError();
+}
