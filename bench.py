@@ -114,12 +114,13 @@ def make_workload(name, seed_offset=0):
     return sc
 
 
-def cpu_baseline(sc, H, T, budget_s=12.0):
+def cpu_baseline(sc, H, T, budget_s=15.0):
     """The FP64 oracle on the host cores over a bounded sample of points (stratified, every n-th)."""
     import oracle
     osc = oracle.Scene.from_dict(sc)
     hyps = oracle.fibonacci_hemisphere(H)
-    probe = np.arange(0, sc["N"], max(1, sc["N"] // 64))
+    probe = np.arange(0, sc["N"], max(1, sc["N"] // 512))
+    oracle.fuse(osc, hyps, T, idx=probe[:64])             # thread start-up
     t0 = time.perf_counter()
     oracle.fuse(osc, hyps, T, idx=probe)
     per_pt = (time.perf_counter() - t0) / len(probe)
@@ -158,7 +159,8 @@ def run_reference(args):
     osc = oracle.Scene.from_dict(sc)
     hyps = oracle.fibonacci_hemisphere(H)
     # bounded sample per step so that warmup + steps finish within a few minutes
-    probe = np.arange(0, sc["N"], max(1, sc["N"] // 64))
+    probe = np.arange(0, sc["N"], max(1, sc["N"] // 512))
+    oracle.fuse(osc, hyps, T, idx=probe[:64])             # thread start-up
     t0 = time.perf_counter()
     oracle.fuse(osc, hyps, T, idx=probe)
     per_pt = (time.perf_counter() - t0) / len(probe)

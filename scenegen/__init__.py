@@ -183,7 +183,8 @@ def subset_scene(scene, idx):
     out["tangents"] = np.ascontiguousarray(scene["tangents"][idx])
     out["strand_id"] = np.ascontiguousarray(scene["strand_id"][idx])
     out["N"] = len(idx)
-    if scene.get("k", 0) > 0:
-        out["nbr"] = knn_of(out["points"], scene["k"])
+    k = min(scene.get("k", 0), len(idx) - 1)
+    out["k"] = k
+    out["nbr"] = knn_of(out["points"], k) if k > 0 else np.zeros((len(idx), 0), np.int32)
     out.pop("owner", None)
     return out
