@@ -122,6 +122,31 @@ int hair_fuse_fuse_directions(hf_ctx* ctx, const float* hyps, float* dir_out, fl
  *  cost_out: N x M f32.  Both of kind mem_kind. */
 int hair_fuse_eval_costs(hf_ctx* ctx, int M, const float* dirs, float* cost_out, int mem_kind);
 
+/* Direction fusion that allocates nothing, for callers that may not call cudaMalloc: plugin
+ * hosts whose enqueue hooks forbid allocation, processes whose device memory belongs to a
+ * framework's caching allocator, real-time code with a fixed memory budget.  The paper has no
+ * counterpart; it computes exactly what upload_views + upload_points + fuse_directions compute.
+ *  - All pointers are device memory of the current device: cams, angle, conf, xyz, nbr and hyps
+ *    (NULL = built-in set) as in those calls; dir_out (required), cost_out, idx_out, status_out
+ *    (each may be NULL) as in hair_fuse_fuse_directions.  cfg gives H, k, T and top_k_views.
+ *  - The scratch between the kernels is one static device array of 17.1 MB inside this library,
+ *    which every GPU that loads the library holds until the process exits.  Limits: N * V <=
+ *    1,048,576, V <= 1024, V * Hpad <= 65,536 (Hpad = H rounded up to 8, 16 or 32); larger inputs
+ *    are rejected with HF_ERR_SHAPE before any work is queued.
+ *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress, with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents behind; the call clears
+ *    what must start at zero.  Calls whose GPU work overlaps (different host threads or streams
+ *    on the same device) race on the array and corrupt each other's results.
+ *  - The call runs on cuda_stream (a cudaStream_t) and waits for it before returning: it checks
+ *    the neighbour indices (-> HF_ERR_INVALID_ARG) before the fusion reads through them, and
+ *    reports a non-unit hypothesis (-> HF_ERR_INVALID_ARG) after it.
+ *  - Messages are read with hair_fuse_last_error(NULL). */
+int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, int V, int width, int height, const float* cams,
+                                      const float* angle, const void* conf, int conf_dtype, const float* xyz,
+                                      const int32_t* nbr, const float* hyps, float* dir_out, float* cost_out,
+                                      int32_t* idx_out, uint8_t* status_out, void* cuda_stream);
+
 /* The built-in hypothesis set (host memory): H x 3 f32 Fibonacci hemisphere directions. */
 int hair_fuse_fibonacci_hemisphere(int H, float* out);
 

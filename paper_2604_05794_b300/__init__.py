@@ -42,6 +42,8 @@ _SIGS = {
     "hair_fuse_upload_views": ([_vp, _i, _i, _i, _vp, _vp, _vp, _i, _i], _i),
     "hair_fuse_upload_points": ([_vp, _i, _vp, _vp, _i], _i),
     "hair_fuse_fuse_directions": ([_vp, _vp, _vp, _vp, _vp, _vp, _i], _i),
+    "hair_fuse_fuse_directions_noalloc": ([ctypes.POINTER(hf_config), _i, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp,
+                                           _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "hair_fuse_eval_costs": ([_vp, _i, _vp, _vp, _i], _i),
     "hair_fuse_fibonacci_hemisphere": ([_i, _vp], _i),
     "hair_fuse_sync": ([_vp], _i),
@@ -63,6 +65,7 @@ hair_fuse_set_stream = _lib.hair_fuse_set_stream
 hair_fuse_upload_views = _lib.hair_fuse_upload_views
 hair_fuse_upload_points = _lib.hair_fuse_upload_points
 hair_fuse_fuse_directions = _lib.hair_fuse_fuse_directions
+hair_fuse_fuse_directions_noalloc = _lib.hair_fuse_fuse_directions_noalloc
 hair_fuse_eval_costs = _lib.hair_fuse_eval_costs
 hair_fuse_fibonacci_hemisphere = _lib.hair_fuse_fibonacci_hemisphere
 hair_fuse_sync = _lib.hair_fuse_sync
