@@ -43,7 +43,7 @@ def _load():
             build()
         lib = ctypes.CDLL(_LIB_PATH)
         vp, ll, i32 = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int
-        lib.or_fuse.argtypes = [vp, ll, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, i32]
+        lib.or_fuse.argtypes = [vp, ll, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, i32]
         lib.or_eval_costs.argtypes = [vp, ll, vp, i32, vp, i32, vp, i32]
         lib.or_fibonacci_hemisphere.argtypes = [i32, vp]
         lib.or_fibonacci_hemisphere.restype = None
@@ -97,7 +97,8 @@ def fuse(scene, hyps, T, top_k=0, idx=None, threads=0):
     """Oracle fusion of the listed points (all when idx is None).
 
     hyps: (H,3) unit directions (f32 values widen exactly).  Returns dict of
-    dir (n,3) f64, cost (n,) f64, idx (n,) i32, status (n,) u8, flags (n,) u8."""
+    dir (n,3) f64, cost (n,) f64, idx (n,) i32, status (n,) u8, flags (n,) u8 (FLAG_*),
+    tie_step (n,) i8: first refinement round whose two best costs are within 2e-6, else -1."""
     lib = _load()
     hyps = np.ascontiguousarray(hyps, np.float64)
     H = hyps.shape[0]
@@ -107,9 +108,9 @@ def fuse(scene, hyps, T, top_k=0, idx=None, threads=0):
         idx = np.ascontiguousarray(idx, np.int64)
         n, ip = len(idx), _p(idx)
     out = dict(dir=np.empty((n, 3)), cost=np.empty(n), idx=np.empty(n, np.int32),
-               status=np.empty(n, np.uint8), flags=np.empty(n, np.uint8))
+               status=np.empty(n, np.uint8), flags=np.empty(n, np.uint8), tie_step=np.empty(n, np.int8))
     lib.or_fuse(ctypes.byref(scene.c), n, ip, _p(hyps), H, T, top_k, _p(out["dir"]), _p(out["cost"]),
-                _p(out["idx"]), _p(out["status"]), _p(out["flags"]), threads)
+                _p(out["idx"]), _p(out["status"]), _p(out["flags"]), _p(out["tie_step"]), threads)
     return out
 
 

@@ -212,10 +212,16 @@ void or_fibonacci_hemisphere(int H, double* out) {
     }
 }
 
+/* Exemption thresholds for the parity tests (bookkeeping, not part of the method).
+ * Hypothesis index: the two best costs within 1e-5 relative (plus a 1e-6 floor for costs near 0).
+ * Refinement: two best of the seven costs of a round within 2e-6, about twice the worst-case
+ * error of an FP32 evaluation of the cost, below which the order of two candidates is not fixed
+ * by FP32 arithmetic. */
 static int near_tie(double c1, double c2) {
     double m = fmax(fabs(c1), fabs(c2));
     return fabs(c1 - c2) <= 1e-5 * m + 1e-6;
 }
+static int near_tie_refine(double c1, double c2) { return fabs(c1 - c2) <= 2e-6; }
 
 /* rotation of d about world axis ax (0 x, 1 y, 2 z) by angle th (right-handed) */
 static void rotate_axis(int ax, double th, const double* d, double* o) {
@@ -254,9 +260,10 @@ static int boundary_ambiguous(const or_scene* s, long long i) {
  * then halves alpha.  The result is normalised and its sign made canonical: the first of
  * z, y, x with magnitude above 1e-12 is positive. */
 void or_fuse_point(const or_scene* s, long long i, const double* hyps, int H, int T, int top_k,
-                   double* dir, double* cost, int32_t* idx, uint8_t* status, uint8_t* flags) {
+                   double* dir, double* cost, int32_t* idx, uint8_t* status, uint8_t* flags, int8_t* tie_step) {
     const double* p = s->pts + 3 * i;
     *flags = 0;
+    *tie_step = -1;
     if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) {
         dir[0] = dir[1] = dir[2] = 0.0;
         *cost = NAN;
@@ -295,7 +302,10 @@ void or_fuse_point(const or_scene* s, long long i, const double* hyps, int H, in
             if (cs[c] < l1) { l2 = l1; l1 = cs[c]; }
             else if (cs[c] < l2) l2 = cs[c];
         }
-        if (near_tie(l1, l2)) *flags |= OR_FLAG_REFINE_TIE;
+        if (near_tie_refine(l1, l2)) {
+            *flags |= OR_FLAG_REFINE_TIE;
+            if (*tie_step < 0) *tie_step = (int8_t)t;
+        }
         if (choice >= 0) { d[0] = cand[choice][0]; d[1] = cand[choice][1]; d[2] = cand[choice][2]; bc = best; }
         alpha *= 0.5;
     }
@@ -313,14 +323,15 @@ void or_fuse_point(const or_scene* s, long long i, const double* hyps, int H, in
 /* Fusion of the listed points (idx = NULL: all N); hyps H x 3. */
 int or_fuse(const or_scene* s, long long n_idx, const long long* idx, const double* hyps, int H, int T,
             int top_k, double* dir, double* cost, int32_t* out_idx, uint8_t* status, uint8_t* flags,
-            int n_threads) {
+            int8_t* tie_step, int n_threads) {
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #endif
 #pragma omp parallel for schedule(dynamic, 16)
     for (long long q = 0; q < n_idx; q++) {
         long long i = idx ? idx[q] : q;
-        or_fuse_point(s, i, hyps, H, T, top_k, dir + 3 * q, cost + q, out_idx + q, status + q, flags + q);
+        or_fuse_point(s, i, hyps, H, T, top_k, dir + 3 * q, cost + q, out_idx + q, status + q, flags + q,
+                      tie_step + q);
     }
     return 0;
 }
