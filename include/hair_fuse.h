@@ -129,10 +129,10 @@ int hair_fuse_eval_costs(hf_ctx* ctx, int M, const float* dirs, float* cost_out,
  *  - All pointers are device memory of the current device: cams, angle, conf, xyz, nbr and hyps
  *    (NULL = built-in set) as in those calls; dir_out (required), cost_out, idx_out, status_out
  *    (each may be NULL) as in hair_fuse_fuse_directions.  cfg gives H, k, T and top_k_views.
- *  - The scratch between the kernels is one static device array of 17.1 MB inside this library,
+ *  - The scratch between the kernels is one static device array of 20.2 MB inside this library,
  *    which every GPU that loads the library holds until the process exits.  Limits: N * V <=
- *    1,048,576, V <= 1024, V * Hpad <= 65,536 (Hpad = H rounded up to 8, 16 or 32); larger inputs
- *    are rejected with HF_ERR_SHAPE before any work is queued.
+ *    1,048,576, N <= 262,144, V <= 1024, V * Hpad <= 65,536 (Hpad = H rounded up to 8, 16 or 32);
+ *    larger inputs are rejected with HF_ERR_SHAPE before any work is queued.
  *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress, with
  *    that device current); make that first call before any stream capture.
  *  - Every call on a device shares the one array and leaves its contents behind; the call clears

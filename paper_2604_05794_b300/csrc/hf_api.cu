@@ -251,10 +251,14 @@ int hair_fuse_fuse_directions(hf_ctx* c, const float* hyps, float* dir_out, floa
         d_idx = idx_out ? (int32_t*)(base + (size_t)N * 16) : nullptr;
         d_status = status_out ? (uint8_t*)(base + (size_t)N * 20) : nullptr;
     }
+    if ((rc = hf_ensure(c, c->best, (size_t)N * 12))) return rc;
+    int32_t* bi = (int32_t*)c->best.p;
     FuseArgs fa{(const float*)c->pts.p, N, (const int32_t*)c->nbr.p, c->k, (const float*)c->cams.p, V,
                 (const float2*)c->samp.p, (const float2*)c->ab.p, (const float4*)c->qtab.p, (const float*)c->vthr.p,
-                (const float*)c->hyps.p, H, Hpad, (const float2*)c->rot.p, T, d_dir, d_cost, d_idx, d_status};
-    if ((rc = run_launch(c, "k_fuse", [&] { return hf_launch_fuse(fa, hc, c->stream, nullptr); }))) return rc;
+                (const float*)c->hyps.p, H, Hpad, (const float2*)c->rot.p, T, d_dir, d_cost, d_idx, d_status,
+                bi, (float*)(bi + N), bi + 2 * (size_t)N, hf_fuse_vblock_q(V, hc), hf_fuse_vblock_c(V)};
+    if ((rc = run_launch(c, "k_argmin", [&] { return hf_launch_argmin(fa, hc, c->stream); }))) return rc;
+    if ((rc = run_launch(c, "k_refine", [&] { return hf_launch_refine(fa, c->stream); }))) return rc;
     if (mem_kind == HF_HOST) {
         cudaError_t e = cudaMemcpyAsync(dir_out, d_dir, (size_t)N * 12, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess && cost_out) e = cudaMemcpyAsync(cost_out, d_cost, (size_t)N * 4, cudaMemcpyDeviceToHost, c->stream);
@@ -387,7 +391,7 @@ void hair_fuse_destroy(hf_ctx* c) {
         cudaEventDestroy(r.end);
     }
     DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->pts, &c->nbr, &c->samp, &c->ab, &c->qtab,
-                      &c->vthr, &c->hyps, &c->rot, &c->outs, &c->evald, &c->errw, &c->work};
+                      &c->vthr, &c->hyps, &c->rot, &c->outs, &c->evald, &c->errw, &c->work, &c->best};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->errw_host) cudaFreeHost(c->errw_host);

@@ -42,11 +42,12 @@ struct hf_ctx {
     // scratch of the fusion path
     DevBuf samp;    // [V][N] float2: C (cos theta, sin theta) at the point's pixel, 0 when not visible
     DevBuf ab;      // [V][N] float2: projection ratios (X/Z, Y/Z); NaN when v is not in the point's view set
-    DevBuf qtab;    // [V][Hpad] float4: (fx q_x, fx q_z, fy q_y, fy q_z), q = R_v h_m
+    DevBuf qtab;    // [V][Hpad] float4: hypothesis pairs of (fx q_x, fx q_z) and (fy q_y, fy q_z), q = R_v h_m
     DevBuf vthr;    // [V] float: degenerate-offset threshold 1e-20 (fx^2 + fy^2)
     DevBuf hyps;    // [Hpad] x 3 float
     DevBuf rot;     // [T] float2: (cos alpha_t, sin alpha_t)
     DevBuf outs;    // device outputs staged for HF_HOST calls
+    DevBuf best;    // [N] x (int32 index, f32 cost, int32 view count) from argmin to refinement
     DevBuf evald;   // device copy of eval directions for HF_HOST calls
     DevBuf errw;    // uint32 device error word
     DevBuf work;    // uint64 (point, view) pairs of the last projection
@@ -94,9 +95,15 @@ struct FuseArgs {
     const float* hyps; int H; int Hpad;
     const float2* rot; int T;
     float* dir_out; float* cost_out; int32_t* idx_out; uint8_t* status_out;
+    int32_t* best_idx; float* best_cost; int32_t* nvs;   // [N] hand-off from argmin to refinement
+    int vblock_q, vblock_c;                              // views staged in shared memory per block
 };
 int hf_fuse_chunk_for(int H);
-cudaError_t hf_launch_fuse(const FuseArgs& a, int hchunk, cudaStream_t s, const char** kname);
+int hf_fuse_vblock_q(int V, int hchunk);
+int hf_fuse_vblock_c(int V);
+cudaError_t hf_launch_argmin(const FuseArgs& a, int hchunk, cudaStream_t s);   // K2
+cudaError_t hf_launch_refine(const FuseArgs& a, cudaStream_t s);               // K3
+cudaError_t hf_launch_fuse(const FuseArgs& a, int hchunk, cudaStream_t s);     // K2 then K3
 
 struct EvalArgs {
     const float* pts; int N;

@@ -5,8 +5,9 @@
 //   k_project       K1, thread per point: projection of the point into every view with the pixel
 //                   index decided in float-float arithmetic, nearest-pixel gather of the orientation
 //                   and confidence maps, view set (visible or top-K) of the point.
-//   k_fuse<HC, KP>  K2 + K3, thread per point: cost of all hypotheses (Eqs. proj_r .. patch_min and
-//                   the view mean), argmin, then T rounds of the six-rotation refinement.
+//   k_argmin<HC,KP> K2, thread per point: cost of all hypotheses (Eqs. proj_r .. patch_min and the
+//                   view mean) and their argmin.
+//   k_refine<KP>    K3, thread per point: T rounds of the six-rotation refinement, final outputs.
 //   k_eval<KP>      cost of caller-given directions (no argmin).
 #include <math.h>
 
@@ -186,15 +187,22 @@ __global__ void k_prep(PrepArgs a) {
         for (int q = 0; q < 3; ++q) a.hyps[3 * m + q] = (float)h[q];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < a.V * a.Hpad; e += blockDim.x) {
-        const int v = e / a.Hpad, m = e % a.Hpad;
+    // hypothesis pairs (m, m+1) interleaved for packed evaluation, q = R_v h:
+    //   qtab[v][m]   = (fx q_x(m), fx q_x(m+1), fx q_z(m), fx q_z(m+1))
+    //   qtab[v][m+1] = (fy q_y(m), fy q_y(m+1), fy q_z(m), fy q_z(m+1))
+    for (int e = threadIdx.x; e < a.V * (a.Hpad / 2); e += blockDim.x) {
+        const int v = e / (a.Hpad / 2), m = 2 * (e % (a.Hpad / 2));
         const float* cam = a.cams + 16 * v;
-        double q[3];
-        for (int r = 0; r < 3; ++r)
-            q[r] = (double)cam[4 + 3 * r] * a.hyps[3 * m] + (double)cam[5 + 3 * r] * a.hyps[3 * m + 1] +
-                   (double)cam[6 + 3 * r] * a.hyps[3 * m + 2];
-        a.qtab[e] = make_float4((float)(cam[0] * q[0]), (float)(cam[0] * q[2]), (float)(cam[1] * q[1]),
-                                (float)(cam[1] * q[2]));
+        double q[2][3];
+        for (int h = 0; h < 2; ++h)
+            for (int r = 0; r < 3; ++r)
+                q[h][r] = (double)cam[4 + 3 * r] * a.hyps[3 * (m + h)] + (double)cam[5 + 3 * r] * a.hyps[3 * (m + h) + 1] +
+                          (double)cam[6 + 3 * r] * a.hyps[3 * (m + h) + 2];
+        const double fx = cam[0], fy = cam[1];
+        a.qtab[(size_t)v * a.Hpad + m] =
+            make_float4((float)(fx * q[0][0]), (float)(fx * q[1][0]), (float)(fx * q[0][2]), (float)(fx * q[1][2]));
+        a.qtab[(size_t)v * a.Hpad + m + 1] =
+            make_float4((float)(fy * q[0][1]), (float)(fy * q[1][1]), (float)(fy * q[0][2]), (float)(fy * q[1][2]));
     }
     for (int v = threadIdx.x; v < a.V; v += blockDim.x) {
         const double fx = a.cams[16 * v], fy = a.cams[16 * v + 1];
@@ -227,24 +235,124 @@ __device__ __forceinline__ void load_patch(const float2* __restrict__ samp, size
     for (int j = 1; j < KP; ++j) s[j] = nb[j] >= 0 ? samp[base + nb[j]] : make_float2(0.0f, 0.0f);
 }
 
+// ---- packed FP32 pairs (sm_100+ fma/mul .f32x2): each lane is rounded exactly like the scalar
+// instruction, so the packed evaluation gives the same bits as view_term() lane by lane.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f32x2 r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Patch terms of two directions in one view: (rx, ry) hold the pair's offsets, SX/SY the patch
+// samples broadcast to both lanes.
+template <int KP>
+__device__ __forceinline__ void view_term2(f32x2 rx, f32x2 ry, const f32x2 (&SX)[KP], const f32x2 (&SY)[KP],
+                                           float thr, float& L0, float& L1) {
+    const f32x2 r2 = fma2(rx, rx, mul2(ry, ry));
+    float m0 = 0.0f, m1 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+        float u0, u1;
+        upk(fma2(rx, SX[j], mul2(ry, SY[j])), u0, u1);
+        m0 = fmaxf(m0, fabsf(u0));
+        m1 = fmaxf(m1, fabsf(u1));
+    }
+    float a0, a1;
+    upk(r2, a0, a1);
+    L0 = a0 >= thr ? m0 * rsqrtf(a0) : 0.0f;
+    L1 = a1 >= thr ? m1 * rsqrtf(a1) : 0.0f;
+}
+
+// ---- shared-memory staging
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+constexpr int kFuseThreads = 128;
+constexpr size_t kQStageBytes = 16384;   // hypothesis-table slice staged per view block
+constexpr int kCamStageViews = 256;      // camera rows staged per view block
+
+// Per-thread double buffer of one view's patch data: item 0 = the point's (a, b), items 1..KP =
+// the patch samples; laid out [stage][item][thread] so a warp reads consecutive 8-byte words.
+template <int KP>
+struct PatchStage {
+    float2 v[2][KP + 1][kFuseThreads];
+};
+
+// Queue the copies of one view's patch data into stage st (one commit group per call, also when
+// the thread has nothing to copy, so that group counting stays uniform).
+template <int KP>
+__device__ __forceinline__ void issue_patch(PatchStage<KP>& sg, int st, const float2* __restrict__ ab,
+                                            const float2* __restrict__ samp, size_t base, int i, const int (&nb)[KP],
+                                            bool active) {
+    const int t = threadIdx.x;
+    if (active) {
+        cp_async8(&sg.v[st][0][t], ab + base + i);
+        cp_async8(&sg.v[st][1][t], samp + base + i);
+#pragma unroll
+        for (int j = 1; j < KP; ++j)
+            if (nb[j] >= 0) cp_async8(&sg.v[st][1 + j][t], samp + base + nb[j]);
+    }
+    cp_async_commit();
+}
+
+template <int KP>
+__device__ __forceinline__ void load_nbrs(const FuseArgs& a, int i, bool active, int (&nb)[KP], PatchStage<KP>& sg) {
+    nb[0] = active ? i : -1;
+#pragma unroll
+    for (int j = 1; j < KP; ++j) nb[j] = (active && (j - 1) < a.k) ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
+    // padded / inactive members read as zero samples in both stages, never overwritten
+#pragma unroll
+    for (int j = 1; j < KP; ++j)
+        if (nb[j] < 0) sg.v[0][1 + j][threadIdx.x] = sg.v[1][1 + j][threadIdx.x] = make_float2(0.0f, 0.0f);
+}
+
+template <int KP>
+__device__ __forceinline__ void stage_samples(const PatchStage<KP>& sg, int st, f32x2 (&SX)[KP], f32x2 (&SY)[KP]) {
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+        const float2 sj = sg.v[st][1 + j][threadIdx.x];
+        SX[j] = pk(sj.x, sj.x);
+        SY[j] = pk(sj.y, sj.y);
+    }
+}
+
+// K2: cost of every hypothesis and the argmin (lowest index on ties), thread per point.  The
+// hypothesis table of HC hypotheses x a block of views sits in shared memory; the next view's
+// patch data is copied in (cp.async) while the current view is evaluated, two hypotheses at a time.
 template <int HC, int KP>
-__global__ void __launch_bounds__(128) k_fuse(FuseArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.N) return;
-    const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
-    if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) {
-        a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
-        if (a.cost_out) a.cost_out[i] = __int_as_float(0x7fc00000);
-        if (a.idx_out) a.idx_out[i] = -1;
-        if (a.status_out) a.status_out[i] = HF_STATUS_BAD_INPUT;
-        return;
+__global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PatchStage<KP>& sg = *reinterpret_cast<PatchStage<KP>*>(smem_raw);
+    float4* qs = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP>));   // [view in block][HC]
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * kFuseThreads + tid;
+    bool active = i < a.N;
+    if (active) {
+        const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
+        if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) {
+            a.nvs[i] = -1;
+            active = false;
+        }
     }
     int nb[KP];
-    nb[0] = i;
-#pragma unroll
-    for (int j = 1; j < KP; ++j) nb[j] = (j - 1) < a.k ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
-
-    // ---- cost of every hypothesis, HC at a time; argmin with the lowest index on ties
+    load_nbrs<KP>(a, i, active, nb, sg);
     float best = INFINITY;
     int bestm = 0, nv = 0;
     for (int c0 = 0; c0 < a.Hpad; c0 += HC) {
@@ -252,21 +360,40 @@ __global__ void __launch_bounds__(128) k_fuse(FuseArgs a) {
 #pragma unroll
         for (int m = 0; m < HC; ++m) acc[m] = 0.0f;
         nv = 0;
-        for (int v = 0; v < a.V; ++v) {
-            const size_t base = (size_t)v * a.N;
-            const float2 r = a.ab[base + i];
-            if (r.x != r.x) continue;
-            ++nv;
-            float2 s[KP];
-            load_patch<KP>(a.samp, base, i, nb, s);
-            const float thr = __ldg(a.vthr + v);
-            const float4* __restrict__ q = a.qtab + (size_t)v * a.Hpad + c0;
+        issue_patch<KP>(sg, 0, a.ab, a.samp, 0, i, nb, active);
+        for (int vb = 0; vb < a.V; vb += a.vblock_q) {
+            const int nvb = min(a.vblock_q, a.V - vb);
+            __syncthreads();
+            for (int e = tid; e < nvb * HC; e += kFuseThreads)
+                qs[e] = a.qtab[(size_t)(vb + e / HC) * a.Hpad + c0 + e % HC];
+            __syncthreads();
+            for (int v = vb; v < vb + nvb; ++v) {
+                if (v + 1 < a.V) issue_patch<KP>(sg, (v + 1) & 1, a.ab, a.samp, (size_t)(v + 1) * a.N, i, nb, active);
+                else cp_async_commit();
+                cp_async_wait1();
+                if (!active) continue;
+                const int st = v & 1;
+                const float2 r = sg.v[st][0][tid];
+                if (r.x != r.x) continue;
+                ++nv;
+                f32x2 SX[KP], SY[KP];
+                stage_samples<KP>(sg, st, SX, SY);
+                const f32x2 na = pk(-r.x, -r.x), nb2 = pk(-r.y, -r.y);
+                const float thr = __ldg(a.vthr + v);
+                const float4* q = qs + (v - vb) * HC;
 #pragma unroll
-            for (int m = 0; m < HC; ++m) {
-                const float4 Q = __ldg(q + m);
-                acc[m] += view_term<KP>(fmaf(-r.x, Q.y, Q.x), fmaf(-r.y, Q.w, Q.z), s, thr);
+                for (int m = 0; m < HC; m += 2) {
+                    // hypotheses m, m+1: rx = fx q_x - a fx q_z, ry = fy q_y - b fy q_z
+                    const float4 QA = q[m], QB = q[m + 1];
+                    float L0, L1;
+                    view_term2<KP>(fma2(na, pk(QA.z, QA.w), pk(QA.x, QA.y)), fma2(nb2, pk(QB.z, QB.w), pk(QB.x, QB.y)),
+                                   SX, SY, thr, L0, L1);
+                    acc[m] += L0;
+                    acc[m + 1] += L1;
+                }
             }
         }
+        cp_async_wait0();
 #pragma unroll
         for (int m = 0; m < HC; ++m) {
             const float c = nv ? 1.0f - acc[m] / (float)nv : 1.0f;
@@ -276,44 +403,98 @@ __global__ void __launch_bounds__(128) k_fuse(FuseArgs a) {
             }
         }
     }
+    if (active) {
+        a.best_idx[i] = bestm;
+        a.best_cost[i] = best;
+        a.nvs[i] = nv;
+    }
+}
 
-    // ---- refinement: +-alpha about x, y, z; move to the first strictly lowest cost; halve alpha
+// K3: T rounds of +-alpha rotations about world x, y, z from the argmin; move to the first strictly
+// lowest cost; halve alpha.  The two candidates of one axis are evaluated as a packed pair.
+template <int KP>
+__global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PatchStage<KP>& sg = *reinterpret_cast<PatchStage<KP>*>(smem_raw);
+    float4* cs4 = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP>));   // [view in block][3]
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * kFuseThreads + tid;
+    const bool inb = i < a.N;
+    const int nv = inb ? a.nvs[i] : 0;
+    if (inb && nv < 0) {
+        a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
+        if (a.cost_out) a.cost_out[i] = __int_as_float(0x7fc00000);
+        if (a.idx_out) a.idx_out[i] = -1;
+        if (a.status_out) a.status_out[i] = HF_STATUS_BAD_INPUT;
+    }
+    const bool active = inb && nv > 0;   // points with no view keep the best hypothesis (all costs 1)
+    int nb[KP];
+    load_nbrs<KP>(a, i, active, nb, sg);
+    const int bestm = (inb && nv >= 0) ? a.best_idx[i] : 0;
+    float best = (inb && nv >= 0) ? a.best_cost[i] : 0.0f;
     float d0 = a.hyps[3 * bestm], d1 = a.hyps[3 * bestm + 1], d2 = a.hyps[3 * bestm + 2];
+    const int nblk = (a.V + a.vblock_c - 1) / a.vblock_c;
     for (int t = 0; t < a.T; ++t) {
-        const float2 cs = a.rot[t];
-        const float c = cs.x, sn = cs.y;
-        float cd[6][3] = {{d0, c * d1 - sn * d2, sn * d1 + c * d2}, {d0, c * d1 + sn * d2, -sn * d1 + c * d2},
-                          {c * d0 + sn * d2, d1, -sn * d0 + c * d2}, {c * d0 - sn * d2, d1, sn * d0 + c * d2},
-                          {c * d0 - sn * d1, sn * d0 + c * d1, d2}, {c * d0 + sn * d1, -sn * d0 + c * d1, d2}};
-        float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        if (nv) {
-            for (int v = 0; v < a.V; ++v) {
-                const size_t base = (size_t)v * a.N;
-                const float2 r = a.ab[base + i];
-                if (r.x != r.x) continue;
-                float2 s[KP];
-                load_patch<KP>(a.samp, base, i, nb, s);
-                const float* cam = a.cams + 16 * v;
-                const float fx = __ldg(cam), fy = __ldg(cam + 1);
-                const float R6 = __ldg(cam + 10), R7 = __ldg(cam + 11), R8 = __ldg(cam + 12);
-                // Z times the projection Jacobian: rows fx (R_0 - a R_2), fy (R_1 - b R_2)
-                const float j0 = fx * fmaf(-r.x, R6, __ldg(cam + 4)), j1 = fx * fmaf(-r.x, R7, __ldg(cam + 5)),
-                            j2 = fx * fmaf(-r.x, R8, __ldg(cam + 6));
-                const float j3 = fy * fmaf(-r.y, R6, __ldg(cam + 7)), j4 = fy * fmaf(-r.y, R7, __ldg(cam + 8)),
-                            j5 = fy * fmaf(-r.y, R8, __ldg(cam + 9));
-                const float thr = __ldg(a.vthr + v);
+        const float2 cr = a.rot[t];
+        const float c = cr.x, sn = cr.y;
+        const float cd[6][3] = {{d0, c * d1 - sn * d2, sn * d1 + c * d2}, {d0, c * d1 + sn * d2, -sn * d1 + c * d2},
+                                {c * d0 + sn * d2, d1, -sn * d0 + c * d2}, {c * d0 - sn * d2, d1, sn * d0 + c * d2},
+                                {c * d0 - sn * d1, sn * d0 + c * d1, d2}, {c * d0 + sn * d1, -sn * d0 + c * d1, d2}};
+        f32x2 CX[3], CY[3], CZ[3];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const float rx = fmaf(j0, cd[q][0], fmaf(j1, cd[q][1], j2 * cd[q][2]));
-                    const float ry = fmaf(j3, cd[q][0], fmaf(j4, cd[q][1], j5 * cd[q][2]));
-                    acc[q] += view_term<KP>(rx, ry, s, thr);
+        for (int q = 0; q < 3; ++q) {
+            CX[q] = pk(cd[2 * q][0], cd[2 * q + 1][0]);
+            CY[q] = pk(cd[2 * q][1], cd[2 * q + 1][1]);
+            CZ[q] = pk(cd[2 * q][2], cd[2 * q + 1][2]);
+        }
+        float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        issue_patch<KP>(sg, 0, a.ab, a.samp, 0, i, nb, active);
+        for (int vb = 0; vb < a.V; vb += a.vblock_c) {
+            const int nvb = min(a.vblock_c, a.V - vb);
+            if (nblk > 1 || t == 0) {
+                __syncthreads();
+                for (int e = tid; e < nvb; e += kFuseThreads) {
+                    const float* cam = a.cams + 16 * (vb + e);
+                    cs4[3 * e] = make_float4(cam[0], cam[1], cam[4], cam[5]);
+                    cs4[3 * e + 1] = make_float4(cam[6], cam[7], cam[8], cam[9]);
+                    cs4[3 * e + 2] = make_float4(cam[10], cam[11], cam[12], a.vthr[vb + e]);
+                }
+                __syncthreads();
+            }
+            for (int v = vb; v < vb + nvb; ++v) {
+                if (v + 1 < a.V) issue_patch<KP>(sg, (v + 1) & 1, a.ab, a.samp, (size_t)(v + 1) * a.N, i, nb, active);
+                else cp_async_commit();
+                cp_async_wait1();
+                if (!active) continue;
+                const int st = v & 1;
+                const float2 r = sg.v[st][0][tid];
+                if (r.x != r.x) continue;
+                f32x2 SX[KP], SY[KP];
+                stage_samples<KP>(sg, st, SX, SY);
+                // staged rows: k0 = (fx, fy, R00, R01), k1 = (R02, R10, R11, R12), k2 = (R20, R21, R22, thr)
+                const float4 k0 = cs4[3 * (v - vb)], k1 = cs4[3 * (v - vb) + 1], k2 = cs4[3 * (v - vb) + 2];
+                // Z times the projection Jacobian: rows fx (R_0 - a R_2), fy (R_1 - b R_2)
+                const float j0 = k0.x * fmaf(-r.x, k2.x, k0.z), j1 = k0.x * fmaf(-r.x, k2.y, k0.w),
+                            j2 = k0.x * fmaf(-r.x, k2.z, k1.x);
+                const float j3 = k0.y * fmaf(-r.y, k2.x, k1.y), j4 = k0.y * fmaf(-r.y, k2.y, k1.z),
+                            j5 = k0.y * fmaf(-r.y, k2.z, k1.w);
+                const f32x2 J0 = pk(j0, j0), J1 = pk(j1, j1), J2 = pk(j2, j2);
+                const f32x2 J3 = pk(j3, j3), J4 = pk(j4, j4), J5 = pk(j5, j5);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {   // the +alpha / -alpha pair of axis q
+                    float L0, L1;
+                    view_term2<KP>(fma2(J0, CX[q], fma2(J1, CY[q], mul2(J2, CZ[q]))),
+                                   fma2(J3, CX[q], fma2(J4, CY[q], mul2(J5, CZ[q]))), SX, SY, k2.w, L0, L1);
+                    acc[2 * q] += L0;
+                    acc[2 * q + 1] += L1;
                 }
             }
         }
+        cp_async_wait0();
         int choice = -1;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-            const float cq = nv ? 1.0f - acc[q] / (float)nv : 1.0f;
+            const float cq = nv > 0 ? 1.0f - acc[q] / (float)nv : 1.0f;
             if (cq < best) {
                 best = cq;
                 choice = q;
@@ -327,14 +508,15 @@ __global__ void __launch_bounds__(128) k_fuse(FuseArgs a) {
                 d2 = cd[q][2];
             }
     }
+    if (!inb || nv < 0) return;
     const float n = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
     d0 /= n;
     d1 /= n;
     d2 /= n;
-    const float sg = fabsf(d2) > 1e-12f ? copysignf(1.0f, d2) : fabsf(d1) > 1e-12f ? copysignf(1.0f, d1) : copysignf(1.0f, d0);
-    a.dir_out[3 * i] = sg * d0;
-    a.dir_out[3 * i + 1] = sg * d1;
-    a.dir_out[3 * i + 2] = sg * d2;
+    const float sgn = fabsf(d2) > 1e-12f ? copysignf(1.0f, d2) : fabsf(d1) > 1e-12f ? copysignf(1.0f, d1) : copysignf(1.0f, d0);
+    a.dir_out[3 * i] = sgn * d0;
+    a.dir_out[3 * i + 1] = sgn * d1;
+    a.dir_out[3 * i + 2] = sgn * d2;
     if (a.cost_out) a.cost_out[i] = best;
     if (a.idx_out) a.idx_out[i] = bestm;
     if (a.status_out) a.status_out[i] = nv ? HF_STATUS_OK : HF_STATUS_NO_VIEWS;
@@ -395,19 +577,35 @@ int kp_for(int k) {
     return 17;
 }
 
-template <int HC>
-cudaError_t launch_fuse_hc(const FuseArgs& a, cudaStream_t s, const char** kname) {
-    const dim3 grid((a.N + 127) / 128), block(128);
-    switch (kp_for(a.k)) {
-        case 1: k_fuse<HC, 1><<<grid, block, 0, s>>>(a); break;
-        case 4: k_fuse<HC, 4><<<grid, block, 0, s>>>(a); break;
-        case 6: k_fuse<HC, 6><<<grid, block, 0, s>>>(a); break;
-        case 9: k_fuse<HC, 9><<<grid, block, 0, s>>>(a); break;
-        case 12: k_fuse<HC, 12><<<grid, block, 0, s>>>(a); break;
-        default: k_fuse<HC, 17><<<grid, block, 0, s>>>(a); break;
+// stage 1: k_argmin, stage 2: k_refine.  Dynamic shared memory above 48 KB needs the function
+// attribute, which is cheap and set on every launch (it is per function and per device).
+template <int HC, int KP>
+cudaError_t launch_fuse_kp(const FuseArgs& a, int stage, cudaStream_t s) {
+    const dim3 grid((a.N + kFuseThreads - 1) / kFuseThreads), block(kFuseThreads);
+    if (stage == 1) {
+        const size_t sm = sizeof(PatchStage<KP>) + (size_t)a.vblock_q * HC * sizeof(float4);
+        cudaError_t e = cudaFuncSetAttribute(k_argmin<HC, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_argmin<HC, KP><<<grid, block, sm, s>>>(a);
+    } else {
+        const size_t sm = sizeof(PatchStage<KP>) + (size_t)a.vblock_c * 3 * sizeof(float4);
+        cudaError_t e = cudaFuncSetAttribute(k_refine<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_refine<KP><<<grid, block, sm, s>>>(a);
     }
-    if (kname) *kname = "k_fuse";
     return cudaGetLastError();
+}
+
+template <int HC>
+cudaError_t launch_fuse_hc(const FuseArgs& a, int stage, cudaStream_t s) {
+    switch (kp_for(a.k)) {
+        case 1: return launch_fuse_kp<HC, 1>(a, stage, s);
+        case 4: return launch_fuse_kp<HC, 4>(a, stage, s);
+        case 6: return launch_fuse_kp<HC, 6>(a, stage, s);
+        case 9: return launch_fuse_kp<HC, 9>(a, stage, s);
+        case 12: return launch_fuse_kp<HC, 12>(a, stage, s);
+        default: return launch_fuse_kp<HC, 17>(a, stage, s);
+    }
 }
 
 }  // namespace
@@ -430,13 +628,26 @@ cudaError_t hf_launch_prep(const PrepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t hf_launch_fuse(const FuseArgs& a, int hchunk, cudaStream_t s, const char** kname) {
+int hf_fuse_vblock_q(int V, int hchunk) {
+    const int vb = (int)(kQStageBytes / ((size_t)hchunk * sizeof(float4)));
+    return vb < 1 ? 1 : (vb < V ? vb : V);
+}
+
+int hf_fuse_vblock_c(int V) { return V < kCamStageViews ? V : kCamStageViews; }
+
+cudaError_t hf_launch_argmin(const FuseArgs& a, int hchunk, cudaStream_t s) {
     switch (hchunk) {
-        case 8: return launch_fuse_hc<8>(a, s, kname);
-        case 16: return launch_fuse_hc<16>(a, s, kname);
-        case 32: return launch_fuse_hc<32>(a, s, kname);
-        default: return launch_fuse_hc<64>(a, s, kname);
+        case 8: return launch_fuse_hc<8>(a, 1, s);
+        case 16: return launch_fuse_hc<16>(a, 1, s);
+        default: return launch_fuse_hc<32>(a, 1, s);
     }
+}
+
+cudaError_t hf_launch_refine(const FuseArgs& a, cudaStream_t s) { return launch_fuse_hc<8>(a, 2, s); }
+
+cudaError_t hf_launch_fuse(const FuseArgs& a, int hchunk, cudaStream_t s) {
+    cudaError_t e = hf_launch_argmin(a, hchunk, s);
+    return e != cudaSuccess ? e : hf_launch_refine(a, s);
 }
 
 cudaError_t hf_launch_eval(const EvalArgs& a, cudaStream_t s) {

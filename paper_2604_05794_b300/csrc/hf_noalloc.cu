@@ -19,6 +19,7 @@ namespace {
 
 // Limits of the static scratch (see the header for the caller-facing statement).
 constexpr long long kMaxPointViews = 1LL << 20;   // N * V
+constexpr long long kMaxPoints = 1LL << 18;       // N
 constexpr int kMaxViews = 1024;                   // V
 constexpr long long kMaxTable = 1LL << 16;        // V * Hpad (hypothesis table entries)
 
@@ -31,10 +32,11 @@ constexpr size_t kHypsBytes = align256(HF_MAX_H * 3 * sizeof(float));
 constexpr size_t kRotBytes = align256(HF_MAX_T * sizeof(float2));
 constexpr size_t kWorkBytes = 256;
 constexpr size_t kErrBytes = 256;
+constexpr size_t kBestBytes = align256(kMaxPoints * 12);   // argmin -> refinement hand-off
 constexpr size_t kScratchBytes =
-    kSampBytes + kAbBytes + kQtabBytes + kVthrBytes + kHypsBytes + kRotBytes + kWorkBytes + kErrBytes;
+    kSampBytes + kAbBytes + kQtabBytes + kVthrBytes + kHypsBytes + kRotBytes + kWorkBytes + kErrBytes + kBestBytes;
 
-// The shared scratch: 17.1 MB, reused (and overwritten) by every call on this device.
+// The shared scratch: 20.2 MB, reused (and overwritten) by every call on this device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -83,6 +85,7 @@ extern "C" int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, in
     const int hc = hf_fuse_chunk_for(H);
     const int Hpad = (H + hc - 1) / hc * hc;
     if ((long long)N * V > kMaxPointViews) return fail(HF_ERR_SHAPE, "N * V exceeds the static scratch limit of 1048576 point-views");
+    if (N > kMaxPoints) return fail(HF_ERR_SHAPE, "N exceeds the static scratch limit of 262144 points");
     if (V > kMaxViews) return fail(HF_ERR_SHAPE, "V exceeds the static scratch limit of 1024 views");
     if ((long long)V * Hpad > kMaxTable) return fail(HF_ERR_SHAPE, "V * H (H rounded up to the hypothesis chunk) exceeds 65536");
     if ((long long)width * height > (1LL << 31)) return fail(HF_ERR_SHAPE, "map larger than 2^31 pixels");
@@ -98,6 +101,7 @@ extern "C" int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, in
     float2* rot = (float2*)(base + kSampBytes + kAbBytes + kQtabBytes + kVthrBytes + kHypsBytes);
     unsigned long long* work = (unsigned long long*)(base + kSampBytes + kAbBytes + kQtabBytes + kVthrBytes + kHypsBytes + kRotBytes);
     uint32_t* errw = (uint32_t*)((unsigned char*)work + kWorkBytes);
+    int32_t* best = (int32_t*)((unsigned char*)errw + kErrBytes);
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
     // the counter and the error word keep the previous call's values: clear them
@@ -113,8 +117,9 @@ extern "C" int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, in
     e = hf_launch_prep(pr, s);
     ProjectArgs pa{xyz, N, cams, V, width, height, angle, conf, conf_dtype == HF_F16 ? 1 : 0, top_k, samp, ab, work};
     if (e == cudaSuccess) e = hf_launch_project(pa, s);
-    FuseArgs fa{xyz, N, nbr, k, cams, V, samp, ab, qtab, vthr, hy, H, Hpad, rot, T, dir_out, cost_out, idx_out, status_out};
-    if (e == cudaSuccess) e = hf_launch_fuse(fa, hc, s, nullptr);
+    FuseArgs fa{xyz, N, nbr, k, cams, V, samp, ab, qtab, vthr, hy, H, Hpad, rot, T, dir_out, cost_out, idx_out, status_out,
+                best, (float*)(best + N), best + 2 * (size_t)N, hf_fuse_vblock_q(V, hc), hf_fuse_vblock_c(V)};
+    if (e == cudaSuccess) e = hf_launch_fuse(fa, hc, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&host_err, errw, sizeof host_err, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(HF_ERR_CUDA, cudaGetErrorString(e));
