@@ -259,20 +259,20 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
 // samples broadcast to both lanes.
 template <int KP>
 __device__ __forceinline__ void view_term2(f32x2 rx, f32x2 ry, const f32x2 (&SX)[KP], const f32x2 (&SY)[KP],
-                                           float thr, float& L0, float& L1) {
+                                           float thr0, float thr1, float& L0, float& L1) {
     const f32x2 r2 = fma2(rx, rx, mul2(ry, ry));
-    float m0 = 0.0f, m1 = 0.0f;
+    float mx0 = 0.0f, mx1 = 0.0f;
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
         float u0, u1;
         upk(fma2(rx, SX[j], mul2(ry, SY[j])), u0, u1);
-        m0 = fmaxf(m0, fabsf(u0));
-        m1 = fmaxf(m1, fabsf(u1));
+        mx0 = fmaxf(mx0, fabsf(u0));
+        mx1 = fmaxf(mx1, fabsf(u1));
     }
     float a0, a1;
     upk(r2, a0, a1);
-    L0 = a0 >= thr ? m0 * rsqrtf(a0) : 0.0f;
-    L1 = a1 >= thr ? m1 * rsqrtf(a1) : 0.0f;
+    L0 = a0 >= thr0 ? mx0 * rsqrtf(a0) : 0.0f;
+    L1 = a1 >= thr1 ? mx1 * rsqrtf(a1) : 0.0f;
 }
 
 // ---- shared-memory staging
@@ -281,24 +281,27 @@ __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 constexpr int kFuseThreads = 128;
 constexpr size_t kQStageBytes = 16384;   // hypothesis-table slice staged per view block
 constexpr int kCamStageViews = 256;      // camera rows staged per view block
 
-// Per-thread double buffer of one view's patch data: item 0 = the point's (a, b), items 1..KP =
-// the patch samples; laid out [stage][item][thread] so a warp reads consecutive 8-byte words.
-template <int KP>
+// Per-thread ring of S views of patch data: item 0 = the point's (a, b), items 1..KP = the patch
+// samples; laid out [stage][item][thread] so a warp reads consecutive 8-byte words.  View v lives
+// in stage v % S and is copied in S - 1 views ahead of its use.
+template <int KP, int S>
 struct PatchStage {
-    float2 v[2][KP + 1][kFuseThreads];
+    float2 v[S][KP + 1][kFuseThreads];
 };
+constexpr int kArgminStages = 2;
+constexpr int kRefineStages = 2;
 
 // Queue the copies of one view's patch data into stage st (one commit group per call, also when
 // the thread has nothing to copy, so that group counting stays uniform).
-template <int KP>
-__device__ __forceinline__ void issue_patch(PatchStage<KP>& sg, int st, const float2* __restrict__ ab,
+template <int KP, int S>
+__device__ __forceinline__ void issue_patch(PatchStage<KP, S>& sg, int st, const float2* __restrict__ ab,
                                             const float2* __restrict__ samp, size_t base, int i, const int (&nb)[KP],
                                             bool active) {
     const int t = threadIdx.x;
@@ -312,19 +315,21 @@ __device__ __forceinline__ void issue_patch(PatchStage<KP>& sg, int st, const fl
     cp_async_commit();
 }
 
-template <int KP>
-__device__ __forceinline__ void load_nbrs(const FuseArgs& a, int i, bool active, int (&nb)[KP], PatchStage<KP>& sg) {
+template <int KP, int S>
+__device__ __forceinline__ void load_nbrs(const FuseArgs& a, int i, bool active, int (&nb)[KP], PatchStage<KP, S>& sg) {
     nb[0] = active ? i : -1;
 #pragma unroll
     for (int j = 1; j < KP; ++j) nb[j] = (active && (j - 1) < a.k) ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
-    // padded / inactive members read as zero samples in both stages, never overwritten
+    // padded / inactive members read as zero samples in every stage, never overwritten
 #pragma unroll
     for (int j = 1; j < KP; ++j)
-        if (nb[j] < 0) sg.v[0][1 + j][threadIdx.x] = sg.v[1][1 + j][threadIdx.x] = make_float2(0.0f, 0.0f);
+        if (nb[j] < 0)
+#pragma unroll
+            for (int st = 0; st < S; ++st) sg.v[st][1 + j][threadIdx.x] = make_float2(0.0f, 0.0f);
 }
 
-template <int KP>
-__device__ __forceinline__ void stage_samples(const PatchStage<KP>& sg, int st, f32x2 (&SX)[KP], f32x2 (&SY)[KP]) {
+template <int KP, int S>
+__device__ __forceinline__ void stage_samples(const PatchStage<KP, S>& sg, int st, f32x2 (&SX)[KP], f32x2 (&SY)[KP]) {
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
         const float2 sj = sg.v[st][1 + j][threadIdx.x];
@@ -339,8 +344,9 @@ __device__ __forceinline__ void stage_samples(const PatchStage<KP>& sg, int st, 
 template <int HC, int KP>
 __global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PatchStage<KP>& sg = *reinterpret_cast<PatchStage<KP>*>(smem_raw);
-    float4* qs = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP>));   // [view in block][HC]
+    constexpr int S = kArgminStages;
+    PatchStage<KP, S>& sg = *reinterpret_cast<PatchStage<KP, S>*>(smem_raw);
+    float4* qs = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP, S>));   // [view in block][HC]
     const int tid = threadIdx.x;
     const int i = blockIdx.x * kFuseThreads + tid;
     bool active = i < a.N;
@@ -352,7 +358,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
         }
     }
     int nb[KP];
-    load_nbrs<KP>(a, i, active, nb, sg);
+    load_nbrs<KP, S>(a, i, active, nb, sg);
     float best = INFINITY;
     int bestm = 0, nv = 0;
     for (int c0 = 0; c0 < a.Hpad; c0 += HC) {
@@ -360,7 +366,9 @@ __global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
 #pragma unroll
         for (int m = 0; m < HC; ++m) acc[m] = 0.0f;
         nv = 0;
-        issue_patch<KP>(sg, 0, a.ab, a.samp, 0, i, nb, active);
+        for (int p = 0; p < S - 1; ++p)
+            if (p < a.V) issue_patch<KP, S>(sg, p, a.ab, a.samp, (size_t)p * a.N, i, nb, active);
+            else cp_async_commit();
         for (int vb = 0; vb < a.V; vb += a.vblock_q) {
             const int nvb = min(a.vblock_q, a.V - vb);
             __syncthreads();
@@ -368,16 +376,17 @@ __global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
                 qs[e] = a.qtab[(size_t)(vb + e / HC) * a.Hpad + c0 + e % HC];
             __syncthreads();
             for (int v = vb; v < vb + nvb; ++v) {
-                if (v + 1 < a.V) issue_patch<KP>(sg, (v + 1) & 1, a.ab, a.samp, (size_t)(v + 1) * a.N, i, nb, active);
+                const int vn = v + S - 1;
+                if (vn < a.V) issue_patch<KP, S>(sg, vn % S, a.ab, a.samp, (size_t)vn * a.N, i, nb, active);
                 else cp_async_commit();
-                cp_async_wait1();
+                cp_async_wait<S - 1>();
                 if (!active) continue;
-                const int st = v & 1;
+                const int st = v % S;
                 const float2 r = sg.v[st][0][tid];
                 if (r.x != r.x) continue;
                 ++nv;
                 f32x2 SX[KP], SY[KP];
-                stage_samples<KP>(sg, st, SX, SY);
+                stage_samples<KP, S>(sg, st, SX, SY);
                 const f32x2 na = pk(-r.x, -r.x), nb2 = pk(-r.y, -r.y);
                 const float thr = __ldg(a.vthr + v);
                 const float4* q = qs + (v - vb) * HC;
@@ -387,13 +396,13 @@ __global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
                     const float4 QA = q[m], QB = q[m + 1];
                     float L0, L1;
                     view_term2<KP>(fma2(na, pk(QA.z, QA.w), pk(QA.x, QA.y)), fma2(nb2, pk(QB.z, QB.w), pk(QB.x, QB.y)),
-                                   SX, SY, thr, L0, L1);
+                                   SX, SY, thr, thr, L0, L1);
                     acc[m] += L0;
                     acc[m + 1] += L1;
                 }
             }
         }
-        cp_async_wait0();
+        cp_async_wait<0>();
 #pragma unroll
         for (int m = 0; m < HC; ++m) {
             const float c = nv ? 1.0f - acc[m] / (float)nv : 1.0f;
@@ -415,8 +424,9 @@ __global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
 template <int KP>
 __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PatchStage<KP>& sg = *reinterpret_cast<PatchStage<KP>*>(smem_raw);
-    float4* cs4 = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP>));   // [view in block][3]
+    constexpr int S = kRefineStages;
+    PatchStage<KP, S>& sg = *reinterpret_cast<PatchStage<KP, S>*>(smem_raw);
+    float4* cs4 = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP, S>));   // [view in block][3]
     const int tid = threadIdx.x;
     const int i = blockIdx.x * kFuseThreads + tid;
     const bool inb = i < a.N;
@@ -429,7 +439,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
     }
     const bool active = inb && nv > 0;   // points with no view keep the best hypothesis (all costs 1)
     int nb[KP];
-    load_nbrs<KP>(a, i, active, nb, sg);
+    load_nbrs<KP, S>(a, i, active, nb, sg);
     const int bestm = (inb && nv >= 0) ? a.best_idx[i] : 0;
     float best = (inb && nv >= 0) ? a.best_cost[i] : 0.0f;
     float d0 = a.hyps[3 * bestm], d1 = a.hyps[3 * bestm + 1], d2 = a.hyps[3 * bestm + 2];
@@ -448,7 +458,9 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
             CZ[q] = pk(cd[2 * q][2], cd[2 * q + 1][2]);
         }
         float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        issue_patch<KP>(sg, 0, a.ab, a.samp, 0, i, nb, active);
+        for (int p = 0; p < S - 1; ++p)
+            if (p < a.V) issue_patch<KP, S>(sg, p, a.ab, a.samp, (size_t)p * a.N, i, nb, active);
+            else cp_async_commit();
         for (int vb = 0; vb < a.V; vb += a.vblock_c) {
             const int nvb = min(a.vblock_c, a.V - vb);
             if (nblk > 1 || t == 0) {
@@ -462,15 +474,16 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
                 __syncthreads();
             }
             for (int v = vb; v < vb + nvb; ++v) {
-                if (v + 1 < a.V) issue_patch<KP>(sg, (v + 1) & 1, a.ab, a.samp, (size_t)(v + 1) * a.N, i, nb, active);
+                const int vn = v + S - 1;
+                if (vn < a.V) issue_patch<KP, S>(sg, vn % S, a.ab, a.samp, (size_t)vn * a.N, i, nb, active);
                 else cp_async_commit();
-                cp_async_wait1();
+                cp_async_wait<S - 1>();
                 if (!active) continue;
-                const int st = v & 1;
+                const int st = v % S;
                 const float2 r = sg.v[st][0][tid];
                 if (r.x != r.x) continue;
                 f32x2 SX[KP], SY[KP];
-                stage_samples<KP>(sg, st, SX, SY);
+                stage_samples<KP, S>(sg, st, SX, SY);
                 // staged rows: k0 = (fx, fy, R00, R01), k1 = (R02, R10, R11, R12), k2 = (R20, R21, R22, thr)
                 const float4 k0 = cs4[3 * (v - vb)], k1 = cs4[3 * (v - vb) + 1], k2 = cs4[3 * (v - vb) + 2];
                 // Z times the projection Jacobian: rows fx (R_0 - a R_2), fy (R_1 - b R_2)
@@ -484,13 +497,13 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
                 for (int q = 0; q < 3; ++q) {   // the +alpha / -alpha pair of axis q
                     float L0, L1;
                     view_term2<KP>(fma2(J0, CX[q], fma2(J1, CY[q], mul2(J2, CZ[q]))),
-                                   fma2(J3, CX[q], fma2(J4, CY[q], mul2(J5, CZ[q]))), SX, SY, k2.w, L0, L1);
+                                   fma2(J3, CX[q], fma2(J4, CY[q], mul2(J5, CZ[q]))), SX, SY, k2.w, k2.w, L0, L1);
                     acc[2 * q] += L0;
                     acc[2 * q + 1] += L1;
                 }
             }
         }
-        cp_async_wait0();
+        cp_async_wait<0>();
         int choice = -1;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
@@ -583,12 +596,12 @@ template <int HC, int KP>
 cudaError_t launch_fuse_kp(const FuseArgs& a, int stage, cudaStream_t s) {
     const dim3 grid((a.N + kFuseThreads - 1) / kFuseThreads), block(kFuseThreads);
     if (stage == 1) {
-        const size_t sm = sizeof(PatchStage<KP>) + (size_t)a.vblock_q * HC * sizeof(float4);
+        const size_t sm = sizeof(PatchStage<KP, kArgminStages>) + (size_t)a.vblock_q * HC * sizeof(float4);
         cudaError_t e = cudaFuncSetAttribute(k_argmin<HC, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         k_argmin<HC, KP><<<grid, block, sm, s>>>(a);
     } else {
-        const size_t sm = sizeof(PatchStage<KP>) + (size_t)a.vblock_c * 3 * sizeof(float4);
+        const size_t sm = sizeof(PatchStage<KP, kRefineStages>) + (size_t)a.vblock_c * 3 * sizeof(float4);
         cudaError_t e = cudaFuncSetAttribute(k_refine<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         k_refine<KP><<<grid, block, sm, s>>>(a);
