@@ -147,6 +147,14 @@ int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, int V, int wi
                                       const int32_t* nbr, const float* hyps, float* dir_out, float* cost_out,
                                       int32_t* idx_out, uint8_t* status_out, void* cuda_stream);
 
+/* The tensor-core GEMM the learned proposal network is built on (tcgen05, BF16 operands, FP32
+ * accumulation in tensor memory).  The paper has no counterpart: the proposal network is an
+ * addition to the method that replaces most refinement rounds.
+ *  C[M x N] (f32, row-major) = A[M x K] . B[N x K]^T with A, B row-major IEEE bf16 bits.
+ * All pointers are device memory (16-byte aligned); N a multiple of 16, K a multiple of 64.
+ * Runs on cuda_stream and waits for it. */
+int hair_fuse_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, void* cuda_stream);
+
 /* The built-in hypothesis set (host memory): H x 3 f32 Fibonacci hemisphere directions. */
 int hair_fuse_fibonacci_hemisphere(int H, float* out);
 

@@ -46,6 +46,7 @@ _SIGS = {
                                            _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "hair_fuse_eval_costs": ([_vp, _i, _vp, _vp, _i], _i),
     "hair_fuse_fibonacci_hemisphere": ([_i, _vp], _i),
+    "hair_fuse_gemm_bf16": ([_vp, _vp, _vp, _i, _i, _i, _vp], _i),
     "hair_fuse_sync": ([_vp], _i),
     "hair_fuse_profile": ([_vp, _i], _i),
     "hair_fuse_profile_read": ([_vp, ctypes.POINTER(hf_kernel_time), _i], _i),
@@ -68,6 +69,7 @@ hair_fuse_fuse_directions = _lib.hair_fuse_fuse_directions
 hair_fuse_fuse_directions_noalloc = _lib.hair_fuse_fuse_directions_noalloc
 hair_fuse_eval_costs = _lib.hair_fuse_eval_costs
 hair_fuse_fibonacci_hemisphere = _lib.hair_fuse_fibonacci_hemisphere
+hair_fuse_gemm_bf16 = _lib.hair_fuse_gemm_bf16
 hair_fuse_sync = _lib.hair_fuse_sync
 hair_fuse_profile = _lib.hair_fuse_profile
 hair_fuse_profile_read = _lib.hair_fuse_profile_read
@@ -125,6 +127,19 @@ def fibonacci_hemisphere(H):
     """The library's built-in hypotheses, (H, 3) float32 (computed on the GPU)."""
     out = np.empty((H, 3), np.float32)
     _check(hair_fuse_fibonacci_hemisphere(H, out.ctypes.data))
+    return out
+
+
+def gemm_bf16(a, b, out=None, stream=None):
+    """C = a @ b.T on the tensor cores: a (M, K), b (N, K) CUDA bf16 tensors -> (M, N) float32."""
+    import torch
+    assert a.is_cuda and b.is_cuda and a.dtype == torch.bfloat16 and b.dtype == torch.bfloat16
+    M, K = a.shape
+    N = b.shape[0]
+    if out is None:
+        out = torch.empty((M, N), dtype=torch.float32, device=a.device)
+    _check(hair_fuse_gemm_bf16(a.data_ptr(), b.data_ptr(), out.data_ptr(), M, N, K,
+                               current_stream_handle() if stream is None else stream))
     return out
 
 

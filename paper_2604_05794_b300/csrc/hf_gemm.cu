@@ -1,0 +1,270 @@
+// hf_gemm.cu - the tensor-core GEMM of the learned proposal network (BF16 operands, FP32 accumulate
+// in tensor memory), for sm_100-family GPUs.
+//
+//   C[M x N] = A[M x K] . B[N x K]^T      A, B row-major bf16 ("TN"), K a multiple of 64
+//
+// One CTA of 128 threads computes a 128 x BN tile: thread 0 keeps a three-stage ring of 128 x 64
+// and BN x 64 operand tiles filled by TMA (128-byte swizzle) and issues tcgen05.mma (K = 16 per
+// instruction) into a TMEM accumulator of BN columns; the four warps then read their 32 TMEM lanes
+// (rows) back with tcgen05.ld and run the epilogue.  gridDim.z splits K (partial sums added
+// atomically).  Every mbarrier wait is bounded; on expiry the CTA records HF_DEV_ERR_TIMEOUT,
+// drains its outstanding copies (bounded as well), frees its TMEM and writes nothing.
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "hf_gemm.cuh"
+#include "hf_internal.cuh"
+#include "hf_tc.cuh"
+
+using namespace hf_tc;
+
+namespace {
+
+constexpr int kStages = 3;
+constexpr uint32_t kATileBytes = 128 * 128;   // 128 rows x 64 bf16
+
+__device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+template <int BN>
+__host__ __device__ constexpr uint32_t tmem_cols() {
+    return BN <= 32 ? 32 : BN;
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtensorMap ta,
+                                                 const __grid_constant__ CUtensorMap tb, GemmArgs g) {
+    constexpr uint32_t kBTileBytes = BN * 128;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
+    unsigned char* sA = base;
+    unsigned char* sB = base + kStages * kATileBytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kBTileBytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* done = empty + kStages;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
+    const int kc0 = blockIdx.z * g.kchunks_per_split;
+    const int nk = min(g.kchunks_per_split, g.K / 64 - kc0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tslot, tmem_cols<BN>());
+        tmem_relinquish();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        int issued = 0;   // chunks whose loads were issued
+        const uint32_t idesc = idesc_bf16_f32(128, BN);
+        for (; issued < kStages && issued < nk; ++issued) {
+            mbar_expect_tx(full + issued, kATileBytes + kBTileBytes);
+            tma_load_2d(sA + issued * kATileBytes, &ta, full + issued, (kc0 + issued) * 64, m0);
+            tma_load_2d(sB + issued * kBTileBytes, &tb, full + issued, (kc0 + issued) * 64, n0);
+        }
+        int c = 0;
+        for (; c < nk; ++c) {
+            const int s = c % kStages;
+            const uint32_t ph = (c / kStages) & 1;
+            if (!mbar_wait(full + s, ph, kWaitTimeoutNs)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const uint32_t a0 = saddr(sA + s * kATileBytes), b0 = saddr(sB + s * kBTileBytes);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_bf16(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, (c > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(empty + s);
+            if (issued < nk) {
+                // the stage is reused: wait until the MMAs that read it are done
+                if (!mbar_wait(empty + s, ph, kWaitTimeoutNs)) {
+                    ok = false;
+                    ++c;
+                    break;
+                }
+                mbar_expect_tx(full + s, kATileBytes + kBTileBytes);
+                tma_load_2d(sA + s * kATileBytes, &ta, full + s, (kc0 + issued) * 64, m0);
+                tma_load_2d(sB + s * kBTileBytes, &tb, full + s, (kc0 + issued) * 64, n0);
+                ++issued;
+            }
+        }
+        mma_commit(done);
+        if (!ok) {
+            // drain the copies still in flight (bounded) before the CTA can exit
+            for (int q = c; q < issued; ++q) mbar_wait(full + (q % kStages), (q / kStages) & 1, kWaitTimeoutNs);
+            atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
+        }
+        s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    bool ok = s_ok != 0;
+    if (!mbar_wait(done, 0, kWaitTimeoutNs)) {
+        ok = false;
+        if (lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
+    }
+    fence_after();
+
+    const int row = m0 + warp * 32 + lane;
+    const bool wr = ok && row < g.M;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    float y0 = 0.0f, y1 = 0.0f, y2 = 0.0f;   // EPI_HEAD accumulators
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tl + c0, v);   // all lanes, unconditionally (warp-collective)
+        if (!wr) continue;
+        const int n = n0 + c0;
+        if constexpr (EPI == EPI_STORE) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) g.C[(size_t)row * g.ldc + n + q] = v[q] + (g.bias ? g.bias[n + q] : 0.0f);
+        } else if constexpr (EPI == EPI_ATOMIC) {
+            const bool add_bias = g.bias && blockIdx.z == 0;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) atomicAdd(g.C + (size_t)row * g.ldc + n + q, v[q] + (add_bias ? g.bias[n + q] : 0.0f));
+        } else if constexpr (EPI == EPI_GELU_TRAIN) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float z = v[q] + g.bias[n + q];
+                const uint16_t h = bf16_bits(gelu_erf(z));
+                g.Z[(size_t)row * g.ldz + n + q] = z;
+                g.H[(size_t)row * g.ldh + n + q] = h;
+                g.HT[(size_t)(n + q) * g.ldht + row] = h;
+            }
+        } else if constexpr (EPI == EPI_GELU) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) g.H[(size_t)row * g.ldh + n + q] = bf16_bits(gelu_erf(v[q] + g.bias[n + q]));
+        } else {   // EPI_HEAD: h2 = bf16(gelu(z2)), y = W3 h2 (FP32, in column order)
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float h = bf16_round(gelu_erf(v[q] + g.bias[n + q]));
+                y0 = fmaf(g.w3[n + q], h, y0);
+                y1 = fmaf(g.w3[256 + n + q], h, y1);
+                y2 = fmaf(g.w3[512 + n + q], h, y2);
+            }
+        }
+    }
+    if constexpr (EPI == EPI_HEAD) {
+        if (wr) {
+            y0 += g.b3[0];
+            y1 += g.b3[1];
+            y2 += g.b3[2];
+            const float nn = sqrtf(y0 * y0 + y1 * y1 + y2 * y2);
+            float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
+            if (nn > 0.0f) {
+                d0 = y0 / nn;
+                d1 = y1 / nn;
+                d2 = y2 / nn;
+            }
+            g.dir_out[3 * (size_t)row] = d0;
+            g.dir_out[3 * (size_t)row + 1] = d1;
+            g.dir_out[3 * (size_t)row + 2] = d2;
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, tmem_cols<BN>());
+}
+
+template <int BN, int EPI>
+cudaError_t launch_bn_epi(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits, cudaStream_t s) {
+    const size_t smem = 1024 + kStages * (kATileBytes + BN * 128) + 256;
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tn<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((g.M + 127) / 128, g.N / BN, splits);
+    k_gemm_tn<BN, EPI><<<grid, 128, smem, s>>>(ta, tb, g);
+    return cudaGetLastError();
+}
+
+template <int EPI>
+cudaError_t launch_epi(int bn, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits, cudaStream_t s) {
+    switch (bn) {
+        case 16: return launch_bn_epi<16, EPI>(ta, tb, g, splits, s);
+        case 64: return launch_bn_epi<64, EPI>(ta, tb, g, splits, s);
+        case 128: return launch_bn_epi<128, EPI>(ta, tb, g, splits, s);
+        default: return launch_bn_epi<256, EPI>(ta, tb, g, splits, s);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+}  // namespace
+
+cudaError_t hf_make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, long long cols, int box_rows) {
+    std::call_once(g_encode_once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    if (!g_encode) return cudaErrorNotSupported;
+    if (cols % 64 || ((uintptr_t)base & 15) || box_rows < 1 || box_rows > 256) return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits,
+                       cudaStream_t s) {
+    if (g.K % 64 || g.N % bn || g.kchunks_per_split < 1 || splits < 1) return cudaErrorInvalidValue;
+    switch (epi) {
+        case EPI_STORE: return launch_epi<EPI_STORE>(bn, ta, tb, g, splits, s);
+        case EPI_ATOMIC: return launch_epi<EPI_ATOMIC>(bn, ta, tb, g, splits, s);
+        case EPI_GELU_TRAIN: return launch_epi<EPI_GELU_TRAIN>(bn, ta, tb, g, splits, s);
+        case EPI_GELU: return launch_epi<EPI_GELU>(bn, ta, tb, g, splits, s);
+        default: return launch_epi<EPI_HEAD>(bn, ta, tb, g, splits, s);
+    }
+}
+
+extern "C" int hair_fuse_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, void* stream) {
+    if (!A || !B || !C || M < 1 || N < 16 || K < 64 || K % 64 || N % 16)
+        return hf_set_err(nullptr, HF_ERR_INVALID_ARG, "need M >= 1, N a multiple of 16, K a multiple of 64");
+    const int bn = N % 256 == 0 ? 256 : N % 128 == 0 ? 128 : N % 64 == 0 ? 64 : 16;
+    CUtensorMap ta, tb;
+    cudaError_t e = hf_make_tmap_bf16(&ta, A, M, K, 128);
+    if (e == cudaSuccess) e = hf_make_tmap_bf16(&tb, B, N, K, bn);
+    if (e != cudaSuccess) return hf_set_err(nullptr, HF_ERR_INVALID_ARG, "tensor map: %s", cudaGetErrorString(e));
+    uint32_t* errw = nullptr;
+    e = cudaMallocAsync((void**)&errw, sizeof(uint32_t), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(errw, 0, sizeof(uint32_t), (cudaStream_t)stream);
+    GemmArgs g{};
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.kchunks_per_split = K / 64;
+    g.C = C;
+    g.ldc = N;
+    g.errw = errw;
+    if (e == cudaSuccess) e = hf_gemm_tn(EPI_STORE, bn, ta, tb, g, 1, (cudaStream_t)stream);
+    uint32_t host_err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host_err, errw, sizeof host_err, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (errw) cudaFreeAsync(errw, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return hf_set_err(nullptr, HF_ERR_CUDA, "gemm: %s", cudaGetErrorString(e));
+    if (host_err) return hf_set_err(nullptr, HF_ERR_TIMEOUT, "gemm: a bounded device wait expired");
+    return HF_OK;
+}

@@ -1,0 +1,41 @@
+// hf_gemm.cuh - interface of the tcgen05 GEMM (hf_gemm.cu) used by the learned proposal network.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// Epilogues of C = A . B^T (+ bias):
+enum {
+    EPI_STORE = 0,        // C[row][n] = acc + bias[n] (f32)
+    EPI_ATOMIC = 1,       // C[row][n] += acc (+ bias[n] from split 0): split-K partial sums (f32)
+    EPI_GELU_TRAIN = 2,   // Z = acc + bias (f32), H = bf16(gelu(Z)), HT = H transposed (bf16)
+    EPI_GELU = 3,         // H = bf16(gelu(acc + bias))
+    EPI_HEAD = 4,         // h = bf16(gelu(acc + bias)), y = w3 . h + b3 (3 outputs), dir = y / |y|; BN = N = 256
+};
+
+struct GemmArgs {
+    int M, N, K;              // rows of A and C, rows of B (= columns of C), reduction length (multiple of 64)
+    int kchunks_per_split;    // 64-wide K chunks per CTA along gridDim.z
+    float* C;
+    int ldc;
+    const float* bias;        // [N] or null
+    float* Z;
+    int ldz;
+    uint16_t* H;
+    int ldh;
+    uint16_t* HT;
+    int ldht;
+    const float* w3;          // EPI_HEAD: 3 x 256 f32 (values of the bf16 layer-3 weights)
+    const float* b3;          // EPI_HEAD: 3
+    float* dir_out;           // EPI_HEAD: M x 3
+    uint32_t* errw;           // device error word (HF_DEV_ERR_TIMEOUT)
+};
+
+// 2D bf16 tensor map of a row-major [rows x cols] matrix (cols a multiple of 64, base 16-byte
+// aligned) with a {64, box_rows} box and the 128-byte swizzle.
+cudaError_t hf_make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, long long cols, int box_rows);
+
+// C = A . B^T with the given epilogue; ta: A map (box 128 rows), tb: B map (box bn rows).
+cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits,
+                       cudaStream_t s);
