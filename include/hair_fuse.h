@@ -155,6 +155,61 @@ int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, int V, int wi
  * Runs on cuda_stream and waits for it. */
 int hair_fuse_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, void* cuda_stream);
 
+/* ------------------------------------------------------------------------------------------------
+ * Learned proposal network.  The paper has no counterpart: a small MLP maps per-point multi-view
+ * orientation features to an initial direction that a short refinement finishes, replacing most of
+ * the hypothesis search; points whose refined proposal costs more than a threshold fall back to the
+ * plain fusion above, which also provides the training targets.
+ *  features x (51, zero-padded to 64, bf16): for the 16 views v_m = floor(m V / 16),
+ *    (sin 2 theta, cos 2 theta, C) at the point's pixel (zeros outside the view), then
+ *    (p - centre) / half_extent of the points' bounding box (half_extent = largest half side);
+ *  network: 64 -> 256 -> 256 -> 3, GELU (erf form) on both hidden layers, BF16 operands, FP32
+ *    accumulation and FP32 master weights; proposal = y / |y|;
+ *  loss per sample 1 - (y_hat . t)^2 (sign-invariant), mean over the batch; Adam (0.9, 0.999, 1e-8).
+ *  Parameter vector (f32, hair_fuse_mlp_param_count() entries): W1 [256 x 64] (columns 51..63 zero),
+ *  b1 [256], W2 [256 x 256], b2 [256], W3 [3 x 256], b3 [3].
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct hf_mlp hf_mlp;
+
+long long hair_fuse_mlp_param_count(void);
+/* Network with training buffers for batches of up to max_batch (a multiple of 128, <= 65536)
+ * samples, working on cuda_stream. */
+int hair_fuse_mlp_create(hf_mlp** out, int max_batch, void* cuda_stream);
+void hair_fuse_mlp_destroy(hf_mlp* mlp);
+/* Uniform(-1/sqrt(fan_in), +1/sqrt(fan_in)) weights and biases from a counter-based hash of seed;
+ * Adam state and step counter reset. */
+int hair_fuse_mlp_init(hf_mlp* mlp, uint64_t seed);
+int hair_fuse_mlp_set_params(hf_mlp* mlp, const float* params, int mem_kind);
+int hair_fuse_mlp_get_params(hf_mlp* mlp, float* params, int mem_kind);
+/* `steps` Adam steps with learning rate lr on batches of `batch` samples drawn with replacement from
+ * X (n_samples x 64 bf16, device) and T (n_samples x 3 f32 unit targets, device); sample b of step s
+ * is hash(seed, s, b) mod n_samples.  use_graph != 0 captures one step in a CUDA graph and replays
+ * it.  loss_out (host, may be NULL) receives the mean loss of each step.  Synchronous. */
+int hair_fuse_mlp_train(hf_mlp* mlp, const uint16_t* X, const float* T, long long n_samples, int batch, int steps,
+                        float lr, uint64_t seed, int use_graph, float* loss_out);
+/* Gradients (host, parameter-vector layout) of the mean loss on the batch the next training step
+ * would draw, without updating anything; the batch itself (xb_out batch x 64 bf16, tb_out batch x 3,
+ * host, may be NULL) and its loss (host, may be NULL) are returned for checking.  Synchronous. */
+int hair_fuse_mlp_grads(hf_mlp* mlp, const uint16_t* X, const float* T, long long n_samples, int batch, uint64_t seed,
+                        float* grads_out, float* loss_out, uint16_t* xb_out, float* tb_out);
+/* Proposals dir_out (n x 3, unit) for features X (n x 64 bf16), both of kind mem_kind. */
+int hair_fuse_mlp_forward(hf_mlp* mlp, const uint16_t* X, int n, float* dir_out, int mem_kind);
+/* Parameters, Adam state and step counter to / from a binary file (magic "HFMLP001"). */
+int hair_fuse_mlp_save(hf_mlp* mlp, const char* path);
+int hair_fuse_mlp_load(hf_mlp* mlp, const char* path);
+const char* hair_fuse_mlp_last_error(const hf_mlp* mlp);
+
+/* Features (N x 64 bf16, kind mem_kind) of the uploaded scene's points. */
+int hair_fuse_features(hf_ctx* ctx, uint16_t* x_out, int mem_kind);
+
+/* Learned fusion of all uploaded points: proposal from the network, then T_short refinement rounds
+ * starting with step alpha_short (radians, halved each round) from it; points whose refined cost
+ * exceeds tau are fused by the plain path (H hypotheses, T rounds) instead and get status
+ * HF_STATUS_FELL_BACK.  Outputs as in hair_fuse_fuse_directions (idx_out = -1 for proposals);
+ * n_fallback (host, may be NULL; reading it synchronises) receives the number of fallback points. */
+int hair_fuse_fuse_learned(hf_ctx* ctx, hf_mlp* mlp, int T_short, float alpha_short, float tau, float* dir_out,
+                           float* cost_out, int32_t* idx_out, uint8_t* status_out, int* n_fallback, int mem_kind);
+
 /* The built-in hypothesis set (host memory): H x 3 f32 Fibonacci hemisphere directions. */
 int hair_fuse_fibonacci_hemisphere(int H, float* out);
 

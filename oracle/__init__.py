@@ -161,3 +161,35 @@ def view_set(scene, i, top_k=0):
 
 def max_threads():
     return int(_load().or_max_threads())
+
+
+def refine(scene, d0, T, alpha0, top_k=0, idx=None, threads=0):
+    """Learned-path oracle step: from start directions d0 (n, 3), the cost and T refinement rounds with
+    first step alpha0 (radians).  Returns dict dir, cost, status, flags, tie_step."""
+    lib = _load()
+    lib.or_refine.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                              ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    d0 = np.ascontiguousarray(d0, np.float64)
+    if idx is None:
+        n, ip = scene.N, None
+    else:
+        idx = np.ascontiguousarray(idx, np.int64)
+        n, ip = len(idx), _p(idx)
+    out = dict(dir=np.empty((n, 3)), cost=np.empty(n), status=np.empty(n, np.uint8), flags=np.empty(n, np.uint8),
+               tie_step=np.empty(n, np.int8))
+    lib.or_refine(ctypes.byref(scene.c), n, ip, _p(d0), T, alpha0, top_k, _p(out["dir"]), _p(out["cost"]),
+                  _p(out["status"]), _p(out["flags"]), _p(out["tie_step"]), threads)
+    return out
+
+
+def features(scene):
+    """Proposal-network features (N, 64) float64 of every point (before bf16 rounding)."""
+    lib = _load()
+    lib.or_features_all.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    pts = scene.points
+    fin = np.all(np.isfinite(pts), axis=1)
+    box = np.concatenate([pts[fin].min(axis=0), pts[fin].max(axis=0)]).astype(np.float64)
+    out = np.empty((scene.N, 64))
+    lib.or_features_all(ctypes.byref(scene.c), _p(box), _p(out))
+    return out

@@ -254,38 +254,12 @@ static int boundary_ambiguous(const or_scene* s, long long i) {
     return 0;
 }
 
-/* Fusion of one point: best hypothesis, then T refinement rounds.
- * Refinement: step alpha_0 = sqrt(2 pi / H) / 2; each round tries d rotated by +alpha, -alpha
- * about world x, then y, then z (in that order), moves to the first strictly lowest cost,
- * then halves alpha.  The result is normalised and its sign made canonical: the first of
- * z, y, x with magnitude above 1e-12 is positive. */
-void or_fuse_point(const or_scene* s, long long i, const double* hyps, int H, int T, int top_k,
-                   double* dir, double* cost, int32_t* idx, uint8_t* status, uint8_t* flags, int8_t* tie_step) {
-    const double* p = s->pts + 3 * i;
-    *flags = 0;
-    *tie_step = -1;
-    if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) {
-        dir[0] = dir[1] = dir[2] = 0.0;
-        *cost = NAN;
-        *idx = -1;
-        *status = OR_BAD_INPUT;
-        return;
-    }
-    unsigned char* mask = (unsigned char*)malloc(s->V);
-    int nv = or_view_set(s, i, top_k, mask);
-    *status = nv ? OR_OK : OR_NO_VIEWS;
-    if (boundary_ambiguous(s, i)) *flags |= OR_FLAG_BOUNDARY;
-    int bm = 0;
-    double bc = INFINITY, second = INFINITY;
-    for (int m = 0; m < H; m++) {
-        double c = or_cost_masked(s, i, hyps + 3 * m, mask);
-        if (c < bc) { second = bc; bc = c; bm = m; }
-        else if (c < second) second = c;
-    }
-    if (H > 1 && near_tie(bc, second)) *flags |= OR_FLAG_IDX_TIE;
-    *idx = bm;
-    double d[3] = {hyps[3 * bm], hyps[3 * bm + 1], hyps[3 * bm + 2]};
-    double alpha = 0.5 * sqrt(2.0 * OR_PI / H);
+/* T rounds of the refinement from direction d0 with cost c0: rotations by +alpha and -alpha about
+ * world x, then y, then z, move to the first strictly lowest cost, halve alpha.  Writes the
+ * normalised direction with canonical sign and its cost; records near-ties for the tests. */
+static void refine_from(const or_scene* s, long long i, const unsigned char* mask, const double* d0, double c0, int T,
+                        double alpha, double* dir, double* cost, uint8_t* flags, int8_t* tie_step) {
+    double d[3] = {d0[0], d0[1], d0[2]}, bc = c0;
     for (int t = 0; t < T; t++) {
         double cs[7], cand[6][3];
         cs[0] = bc;
@@ -317,7 +291,101 @@ void or_fuse_point(const or_scene* s, long long i, const double* hyps, int H, in
     else sg = d[0] < 0 ? -1.0 : 1.0;
     for (int q = 0; q < 3; q++) dir[q] = sg * d[q];
     *cost = bc;
+}
+
+/* Fusion of one point: best hypothesis, then T refinement rounds.
+ * Refinement: step alpha_0 = sqrt(2 pi / H) / 2; each round tries d rotated by +alpha, -alpha
+ * about world x, then y, then z (in that order), moves to the first strictly lowest cost,
+ * then halves alpha.  The result is normalised and its sign made canonical: the first of
+ * z, y, x with magnitude above 1e-12 is positive. */
+void or_fuse_point(const or_scene* s, long long i, const double* hyps, int H, int T, int top_k,
+                   double* dir, double* cost, int32_t* idx, uint8_t* status, uint8_t* flags, int8_t* tie_step) {
+    const double* p = s->pts + 3 * i;
+    *flags = 0;
+    *tie_step = -1;
+    if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) {
+        dir[0] = dir[1] = dir[2] = 0.0;
+        *cost = NAN;
+        *idx = -1;
+        *status = OR_BAD_INPUT;
+        return;
+    }
+    unsigned char* mask = (unsigned char*)malloc(s->V);
+    int nv = or_view_set(s, i, top_k, mask);
+    *status = nv ? OR_OK : OR_NO_VIEWS;
+    if (boundary_ambiguous(s, i)) *flags |= OR_FLAG_BOUNDARY;
+    int bm = 0;
+    double bc = INFINITY, second = INFINITY;
+    for (int m = 0; m < H; m++) {
+        double c = or_cost_masked(s, i, hyps + 3 * m, mask);
+        if (c < bc) { second = bc; bc = c; bm = m; }
+        else if (c < second) second = c;
+    }
+    if (H > 1 && near_tie(bc, second)) *flags |= OR_FLAG_IDX_TIE;
+    *idx = bm;
+    refine_from(s, i, mask, hyps + 3 * bm, bc, T, 0.5 * sqrt(2.0 * OR_PI / H), dir, cost, flags, tie_step);
     free(mask);
+}
+
+/* Learned path, from a given start direction (the proposal): its cost, then T rounds of the same
+ * refinement with first step alpha0; same outputs as or_fuse_point except the index (-1). */
+void or_refine_point(const or_scene* s, long long i, const double* d0, int T, double alpha0, int top_k, double* dir,
+                     double* cost, uint8_t* status, uint8_t* flags, int8_t* tie_step) {
+    const double* p = s->pts + 3 * i;
+    *flags = 0;
+    *tie_step = -1;
+    if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) {
+        dir[0] = dir[1] = dir[2] = 0.0;
+        *cost = NAN;
+        *status = OR_BAD_INPUT;
+        return;
+    }
+    unsigned char* mask = (unsigned char*)malloc(s->V);
+    int nv = or_view_set(s, i, top_k, mask);
+    *status = nv ? OR_OK : OR_NO_VIEWS;
+    if (boundary_ambiguous(s, i)) *flags |= OR_FLAG_BOUNDARY;
+    refine_from(s, i, mask, d0, or_cost_masked(s, i, d0, mask), T, alpha0, dir, cost, flags, tie_step);
+    free(mask);
+}
+
+int or_refine(const or_scene* s, long long n_idx, const long long* idx, const double* d0, int T, double alpha0,
+              int top_k, double* dir, double* cost, uint8_t* status, uint8_t* flags, int8_t* tie_step, int n_threads) {
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long long q = 0; q < n_idx; q++) {
+        long long i = idx ? idx[q] : q;
+        or_refine_point(s, i, d0 + 3 * q, T, alpha0, top_k, dir + 3 * q, cost + q, status + q, flags + q, tie_step + q);
+    }
+    return 0;
+}
+
+/* Features of the proposal network for point i: for the 16 views v_m = floor(m V / 16),
+ * (sin 2 theta, cos 2 theta, C) at the point's pixel, zeros when it projects outside; then the
+ * position (p - centre) / half of the bounding box box = (lo[3], hi[3]), half = largest half side. */
+void or_features(const or_scene* s, long long i, const double* box, double* f) {
+    for (int q = 0; q < 64; q++) f[q] = 0.0;
+    const double* p = s->pts + 3 * i;
+    for (int m = 0; m < 16; m++) {
+        int v = (m * s->V) / 16;
+        double u, vv, a, b;
+        if (!or_project(s->cams + 16 * v, p, s->W, s->H, &u, &vv, &a, &b)) continue;
+        long long px = (long long)floor(vv) * s->W + (long long)floor(u);
+        double th = (double)s->angle[(size_t)v * s->W * s->H + (size_t)px];
+        f[3 * m] = sin(2.0 * th);
+        f[3 * m + 1] = cos(2.0 * th);
+        f[3 * m + 2] = conf_at(s, v, px);
+    }
+    double half = 0.5 * fmax(fmax(box[3] - box[0], box[4] - box[1]), box[5] - box[2]);
+    if (!(half > 0.0)) half = 1.0;
+    for (int q = 0; q < 3; q++) f[48 + q] = isfinite(p[q]) ? (p[q] - 0.5 * (box[q] + box[3 + q])) / half : 0.0;
+}
+
+int or_features_all(const or_scene* s, const double* box, double* out) {
+#pragma omp parallel for schedule(static)
+    for (long long i = 0; i < s->N; i++) or_features(s, i, box, out + 64 * i);
+    return 0;
 }
 
 /* Fusion of the listed points (idx = NULL: all N); hyps H x 3. */

@@ -54,6 +54,21 @@ _SIGS = {
     "hair_fuse_work": ([_vp, ctypes.POINTER(_ll)], _i),
     "hair_fuse_destroy": ([_vp], None),
     "hair_fuse_last_error": ([_vp], ctypes.c_char_p),
+    "hair_fuse_mlp_param_count": ([], _ll),
+    "hair_fuse_mlp_create": ([ctypes.POINTER(_vp), _i, _vp], _i),
+    "hair_fuse_mlp_destroy": ([_vp], None),
+    "hair_fuse_mlp_init": ([_vp, ctypes.c_uint64], _i),
+    "hair_fuse_mlp_set_params": ([_vp, _vp, _i], _i),
+    "hair_fuse_mlp_get_params": ([_vp, _vp, _i], _i),
+    "hair_fuse_mlp_train": ([_vp, _vp, _vp, _ll, _i, _i, ctypes.c_float, ctypes.c_uint64, _i, _vp], _i),
+    "hair_fuse_mlp_grads": ([_vp, _vp, _vp, _ll, _i, ctypes.c_uint64, _vp, _vp, _vp, _vp], _i),
+    "hair_fuse_mlp_forward": ([_vp, _vp, _i, _vp, _i], _i),
+    "hair_fuse_mlp_save": ([_vp, ctypes.c_char_p], _i),
+    "hair_fuse_mlp_load": ([_vp, ctypes.c_char_p], _i),
+    "hair_fuse_mlp_last_error": ([_vp], ctypes.c_char_p),
+    "hair_fuse_features": ([_vp, _vp, _i], _i),
+    "hair_fuse_fuse_learned": ([_vp, _vp, _i, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp, _vp,
+                                ctypes.POINTER(_i), _i], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -77,6 +92,20 @@ hair_fuse_stats = _lib.hair_fuse_stats
 hair_fuse_work = _lib.hair_fuse_work
 hair_fuse_destroy = _lib.hair_fuse_destroy
 hair_fuse_last_error = _lib.hair_fuse_last_error
+hair_fuse_mlp_param_count = _lib.hair_fuse_mlp_param_count
+hair_fuse_mlp_create = _lib.hair_fuse_mlp_create
+hair_fuse_mlp_destroy = _lib.hair_fuse_mlp_destroy
+hair_fuse_mlp_init = _lib.hair_fuse_mlp_init
+hair_fuse_mlp_set_params = _lib.hair_fuse_mlp_set_params
+hair_fuse_mlp_get_params = _lib.hair_fuse_mlp_get_params
+hair_fuse_mlp_train = _lib.hair_fuse_mlp_train
+hair_fuse_mlp_grads = _lib.hair_fuse_mlp_grads
+hair_fuse_mlp_forward = _lib.hair_fuse_mlp_forward
+hair_fuse_mlp_save = _lib.hair_fuse_mlp_save
+hair_fuse_mlp_load = _lib.hair_fuse_mlp_load
+hair_fuse_mlp_last_error = _lib.hair_fuse_mlp_last_error
+hair_fuse_features = _lib.hair_fuse_features
+hair_fuse_fuse_learned = _lib.hair_fuse_fuse_learned
 
 
 class HairFuseError(RuntimeError):
@@ -232,3 +261,106 @@ class HairFuse:
         b, l = _ll(), _ll()
         self._c(hair_fuse_stats(self.h, ctypes.byref(b), ctypes.byref(l)))
         return {"device_bytes": b.value, "launches": l.value}
+
+
+def _mlp_check(rc, h):
+    if rc != HF_OK:
+        msg = hair_fuse_mlp_last_error(h)
+        raise HairFuseError(rc, msg.decode() if msg else "")
+    return rc
+
+
+class ProposalNet:
+    """The learned proposal network (64 -> 256 -> 256 -> 3 MLP on the tensor cores)."""
+
+    def __init__(self, max_batch=8192, stream=None):
+        h = _vp()
+        _check(hair_fuse_mlp_create(ctypes.byref(h), max_batch, current_stream_handle() if stream is None else stream))
+        self.h = h
+        self.max_batch = max_batch
+
+    @staticmethod
+    def param_count():
+        return int(hair_fuse_mlp_param_count())
+
+    def close(self):
+        if getattr(self, "h", None):
+            hair_fuse_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def _c(self, rc):
+        return _mlp_check(rc, self.h)
+
+    def init(self, seed):
+        self._c(hair_fuse_mlp_init(self.h, seed))
+
+    def get_params(self):
+        out = np.empty(self.param_count(), np.float32)
+        self._c(hair_fuse_mlp_get_params(self.h, out.ctypes.data, HF_HOST))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == self.param_count()
+        self._c(hair_fuse_mlp_set_params(self.h, p.ctypes.data, HF_HOST))
+
+    def train(self, X, T, batch, steps, lr, seed, use_graph=True):
+        """X (n, 64) bf16 CUDA tensor, T (n, 3) float32 CUDA tensor; returns the per-step losses."""
+        losses = np.zeros(max(steps, 1), np.float32)
+        self._c(hair_fuse_mlp_train(self.h, X.data_ptr(), T.data_ptr(), X.shape[0], batch, steps, lr, seed,
+                                    1 if use_graph else 0, losses.ctypes.data))
+        return losses[:steps]
+
+    def grads(self, X, T, batch, seed):
+        """(gradients, loss, batch features uint16 (batch, 64), batch targets) of the next batch."""
+        g = np.empty(self.param_count(), np.float32)
+        loss = np.zeros(1, np.float32)
+        xb = np.empty((batch, 64), np.uint16)
+        tb = np.empty((batch, 3), np.float32)
+        self._c(hair_fuse_mlp_grads(self.h, X.data_ptr(), T.data_ptr(), X.shape[0], batch, seed, g.ctypes.data,
+                                    loss.ctypes.data, xb.ctypes.data, tb.ctypes.data))
+        return g, float(loss[0]), xb, tb
+
+    def forward(self, X, out=None):
+        """Proposals (n, 3) for features X (n, 64) bf16 (CUDA tensor or uint16 numpy array)."""
+        n = X.shape[0]
+        if isinstance(X, np.ndarray):
+            out = np.empty((n, 3), np.float32) if out is None else out
+            self._c(hair_fuse_mlp_forward(self.h, np.ascontiguousarray(X).ctypes.data, n, out.ctypes.data, HF_HOST))
+            return out
+        import torch
+        out = torch.empty((n, 3), device=X.device) if out is None else out
+        self._c(hair_fuse_mlp_forward(self.h, X.data_ptr(), n, out.data_ptr(), HF_DEVICE))
+        return out
+
+    def save(self, path):
+        self._c(hair_fuse_mlp_save(self.h, str(path).encode()))
+
+    def load(self, path):
+        self._c(hair_fuse_mlp_load(self.h, str(path).encode()))
+
+
+def _features(self, out):
+    """Proposal-network features (N, 64) bf16 of the uploaded points into out (CUDA bf16/uint16
+    tensor or uint16 numpy array)."""
+    p, kind, _ = _ptr_kind(out)
+    self._c(hair_fuse_features(self.h, p, kind))
+    return out
+
+
+def _fuse_learned(self, net, dir_out, cost_out=None, idx_out=None, status_out=None, T_short=2, alpha_short=0.02,
+                  tau=0.5, count_fallback=True):
+    """Learned fusion into caller buffers; returns the number of fallback points (or None)."""
+    ptrs = [_ptr_kind(x) for x in (dir_out, cost_out, idx_out, status_out)]
+    kind = _same_kind(*[q[1] for q in ptrs])
+    nf = _i(0)
+    self._c(hair_fuse_fuse_learned(self.h, net.h, T_short, alpha_short, tau, *[q[0] for q in ptrs],
+                                   ctypes.byref(nf) if count_fallback else None, kind))
+    return nf.value if count_fallback else None
+
+
+HairFuse.features = _features
+HairFuse.fuse_learned = _fuse_learned

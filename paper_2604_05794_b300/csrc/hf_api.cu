@@ -391,7 +391,7 @@ void hair_fuse_destroy(hf_ctx* c) {
         cudaEventDestroy(r.end);
     }
     DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->pts, &c->nbr, &c->samp, &c->ab, &c->qtab,
-                      &c->vthr, &c->hyps, &c->rot, &c->outs, &c->evald, &c->errw, &c->work, &c->best};
+                      &c->vthr, &c->hyps, &c->rot, &c->outs, &c->evald, &c->errw, &c->work, &c->best, &c->feat, &c->prop, &c->lmisc};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->errw_host) cudaFreeHost(c->errw_host);

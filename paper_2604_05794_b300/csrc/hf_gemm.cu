@@ -139,6 +139,10 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
             const bool add_bias = g.bias && blockIdx.z == 0;
 #pragma unroll
             for (int q = 0; q < 16; ++q) atomicAdd(g.C + (size_t)row * g.ldc + n + q, v[q] + (add_bias ? g.bias[n + q] : 0.0f));
+        } else if constexpr (EPI == EPI_PARTIAL) {
+            float* dst = g.C + (size_t)blockIdx.z * g.split_stride + (size_t)row * g.ldc + n;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) dst[q] = v[q];
         } else if constexpr (EPI == EPI_GELU_TRAIN) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -186,7 +190,11 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
 template <int BN, int EPI>
 cudaError_t launch_bn_epi(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits, cudaStream_t s) {
     const size_t smem = 1024 + kStages * (kATileBytes + BN * 128) + 256;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tn<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the attribute is set outside stream capture (an eager launch comes first)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+        e = cudaFuncSetAttribute(k_gemm_tn<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((g.M + 127) / 128, g.N / BN, splits);
     k_gemm_tn<BN, EPI><<<grid, 128, smem, s>>>(ta, tb, g);
@@ -236,6 +244,7 @@ cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap
         case EPI_ATOMIC: return launch_epi<EPI_ATOMIC>(bn, ta, tb, g, splits, s);
         case EPI_GELU_TRAIN: return launch_epi<EPI_GELU_TRAIN>(bn, ta, tb, g, splits, s);
         case EPI_GELU: return launch_epi<EPI_GELU>(bn, ta, tb, g, splits, s);
+        case EPI_PARTIAL: return launch_epi<EPI_PARTIAL>(bn, ta, tb, g, splits, s);
         default: return launch_epi<EPI_HEAD>(bn, ta, tb, g, splits, s);
     }
 }

@@ -12,6 +12,7 @@ enum {
     EPI_GELU_TRAIN = 2,   // Z = acc + bias (f32), H = bf16(gelu(Z)), HT = H transposed (bf16)
     EPI_GELU = 3,         // H = bf16(gelu(acc + bias))
     EPI_HEAD = 4,         // h = bf16(gelu(acc + bias)), y = w3 . h + b3 (3 outputs), dir = y / |y|; BN = N = 256
+    EPI_PARTIAL = 5,      // C[split z][row][n] = acc: split-K partial tiles, summed afterwards in a fixed order
 };
 
 struct GemmArgs {
@@ -30,6 +31,7 @@ struct GemmArgs {
     const float* b3;          // EPI_HEAD: 3
     float* dir_out;           // EPI_HEAD: M x 3
     uint32_t* errw;           // device error word (HF_DEV_ERR_TIMEOUT)
+    long long split_stride;   // EPI_PARTIAL: elements between the partial tiles of consecutive splits
 };
 
 // 2D bf16 tensor map of a row-major [rows x cols] matrix (cols a multiple of 64, base 16-byte

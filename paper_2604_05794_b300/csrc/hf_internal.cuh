@@ -51,6 +51,9 @@ struct hf_ctx {
     DevBuf evald;   // device copy of eval directions for HF_HOST calls
     DevBuf errw;    // uint32 device error word
     DevBuf work;    // uint64 (point, view) pairs of the last projection
+    DevBuf feat;    // [N x 64] bf16 proposal-network features
+    DevBuf prop;    // [N x 3] proposals
+    DevBuf lmisc;   // bounding box, fallback count, short-refinement steps, fallback list
     uint32_t* errw_host = nullptr;  // pinned read-back slot
     long long launches = 0;
     long long dev_bytes = 0;
@@ -97,6 +100,9 @@ struct FuseArgs {
     float* dir_out; float* cost_out; int32_t* idx_out; uint8_t* status_out;
     int32_t* best_idx; float* best_cost; int32_t* nvs;   // [N] hand-off from argmin to refinement
     int vblock_q, vblock_c;                              // views staged in shared memory per block
+    const int32_t* list; const int* list_count;          // optional: fuse only these points (device count)
+    const float* start_dir;                              // optional [N x 3]: refine from here, not hyps[best_idx]
+    int fell_back;                                       // mark outputs HF_STATUS_FELL_BACK
 };
 int hf_fuse_chunk_for(int H);
 int hf_fuse_vblock_q(int V, int hchunk);
@@ -117,4 +123,21 @@ struct EvalArgs {
 cudaError_t hf_launch_eval(const EvalArgs& a, cudaStream_t s);
 
 cudaError_t hf_launch_fib(int H, float* out, cudaStream_t s);
+
+// learned proposal path
+struct FeatArgs {
+    const float* pts; int N;
+    const float* cams; int V; int W; int H;
+    const float* angle; const void* conf; int conf_f16;
+    const float* box;       // bounding box lo[3], hi[3]
+    uint16_t* x;            // [N x 64] bf16 features
+};
+cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s);
+// cost c_i of a.start_dir and the view count -> a.best_cost, a.nvs (-1 for non-finite points)
+cudaError_t hf_launch_start_cost(const FuseArgs& a, cudaStream_t s);
+// points with a view and cost_out > tau -> list (count must start at 0)
+cudaError_t hf_launch_fallback_select(const float* cost, const int32_t* nvs, int N, float tau, int32_t* list, int* count,
+                                      cudaStream_t s);
+// (cos, sin) of alpha0 / 2^t for t < T, in double then rounded
+cudaError_t hf_launch_rot(float2* rot, int T, double alpha0, cudaStream_t s);
 cudaError_t hf_launch_check_nbr(const int32_t* nbr, long long n, int N, uint32_t* errw, cudaStream_t s);

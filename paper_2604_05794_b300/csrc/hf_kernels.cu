@@ -11,6 +11,8 @@
 //   k_eval<KP>      cost of caller-given directions (no argmin).
 #include <math.h>
 
+#include <cuda_bf16.h>
+
 #include "hf_internal.cuh"
 
 namespace {
@@ -348,8 +350,11 @@ __global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
     PatchStage<KP, S>& sg = *reinterpret_cast<PatchStage<KP, S>*>(smem_raw);
     float4* qs = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP, S>));   // [view in block][HC]
     const int tid = threadIdx.x;
-    const int i = blockIdx.x * kFuseThreads + tid;
-    bool active = i < a.N;
+    const int cnt = a.list ? *a.list_count : a.N;
+    if ((int)blockIdx.x * kFuseThreads >= cnt) return;   // whole block past the list: uniform exit
+    const int t_ = blockIdx.x * kFuseThreads + tid;
+    const int i = t_ < cnt ? (a.list ? a.list[t_] : t_) : -1;
+    bool active = i >= 0;
     if (active) {
         const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
         if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) {
@@ -428,8 +433,11 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
     PatchStage<KP, S>& sg = *reinterpret_cast<PatchStage<KP, S>*>(smem_raw);
     float4* cs4 = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP, S>));   // [view in block][3]
     const int tid = threadIdx.x;
-    const int i = blockIdx.x * kFuseThreads + tid;
-    const bool inb = i < a.N;
+    const int cnt = a.list ? *a.list_count : a.N;
+    if ((int)blockIdx.x * kFuseThreads >= cnt) return;   // whole block past the list: uniform exit
+    const int t_ = blockIdx.x * kFuseThreads + tid;
+    const int i = t_ < cnt ? (a.list ? a.list[t_] : t_) : -1;
+    const bool inb = i >= 0;
     const int nv = inb ? a.nvs[i] : 0;
     if (inb && nv < 0) {
         a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
@@ -440,9 +448,19 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
     const bool active = inb && nv > 0;   // points with no view keep the best hypothesis (all costs 1)
     int nb[KP];
     load_nbrs<KP, S>(a, i, active, nb, sg);
-    const int bestm = (inb && nv >= 0) ? a.best_idx[i] : 0;
+    // start: the argmin hypothesis, or a given direction (the learned proposal; index -1)
+    const int bestm = a.start_dir ? -1 : ((inb && nv >= 0) ? a.best_idx[i] : 0);
     float best = (inb && nv >= 0) ? a.best_cost[i] : 0.0f;
-    float d0 = a.hyps[3 * bestm], d1 = a.hyps[3 * bestm + 1], d2 = a.hyps[3 * bestm + 2];
+    float d0, d1, d2;
+    if (a.start_dir) {
+        d0 = inb ? a.start_dir[3 * i] : 1.0f;
+        d1 = inb ? a.start_dir[3 * i + 1] : 0.0f;
+        d2 = inb ? a.start_dir[3 * i + 2] : 0.0f;
+    } else {
+        d0 = a.hyps[3 * bestm];
+        d1 = a.hyps[3 * bestm + 1];
+        d2 = a.hyps[3 * bestm + 2];
+    }
     const int nblk = (a.V + a.vblock_c - 1) / a.vblock_c;
     for (int t = 0; t < a.T; ++t) {
         const float2 cr = a.rot[t];
@@ -532,7 +550,113 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
     a.dir_out[3 * i + 2] = sgn * d2;
     if (a.cost_out) a.cost_out[i] = best;
     if (a.idx_out) a.idx_out[i] = bestm;
-    if (a.status_out) a.status_out[i] = nv ? HF_STATUS_OK : HF_STATUS_NO_VIEWS;
+    if (a.status_out) a.status_out[i] = a.fell_back ? HF_STATUS_FELL_BACK : (nv ? HF_STATUS_OK : HF_STATUS_NO_VIEWS);
+}
+
+// ------------------------------------------------------------------ learned proposal path
+// Features of one point for the proposal network: for the 16 views v_m = floor(m V / 16),
+// (sin 2 theta, cos 2 theta, C) at the point's pixel (zeros when it projects outside), then the
+// position (p - centre) / half_extent of the point cloud's bounding box; bf16, zero-padded to 64.
+__global__ void __launch_bounds__(128) k_features(FeatArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
+    const size_t npx = (size_t)a.W * a.H;
+    uint16_t f[64];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) f[q] = 0;
+    for (int m = 0; m < 16; ++m) {
+        const int v = (m * a.V) / 16;
+        const float* cam = a.cams + 16 * v;
+        const ff X0 = ff_dot3_plus(cam[4], cam[5], cam[6], p0, p1, p2, cam[13]);
+        const ff X1 = ff_dot3_plus(cam[7], cam[8], cam[9], p0, p1, p2, cam[14]);
+        const ff X2 = ff_dot3_plus(cam[10], cam[11], cam[12], p0, p1, p2, cam[15]);
+        if (!(X2.hi > 1e-6f)) continue;
+        const float fu = ff_floor(ff_affine(cam[0], ff_div(X0, X2), cam[2]));
+        const float fv = ff_floor(ff_affine(cam[1], ff_div(X1, X2), cam[3]));
+        if (!(fu >= 0.0f && fu < (float)a.W && fv >= 0.0f && fv < (float)a.H)) continue;
+        const size_t o = (size_t)v * npx + (size_t)fv * a.W + (size_t)fu;
+        float s2, c2;
+        sincosf(2.0f * a.angle[o], &s2, &c2);
+        f[3 * m] = __bfloat16_as_ushort(__float2bfloat16_rn(s2));
+        f[3 * m + 1] = __bfloat16_as_ushort(__float2bfloat16_rn(c2));
+        f[3 * m + 2] = __bfloat16_as_ushort(__float2bfloat16_rn(load_conf(a.conf, a.conf_f16, o)));
+    }
+    const float* b = a.box;
+    float half = 0.5f * fmaxf(fmaxf(b[3] - b[0], b[4] - b[1]), b[5] - b[2]);
+    if (!(half > 0.0f)) half = 1.0f;
+    const float pc[3] = {p0, p1, p2};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float c = 0.5f * (b[q] + b[3 + q]);
+        const float x = isfinite(pc[q]) ? (pc[q] - c) / half : 0.0f;
+        f[48 + q] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    }
+    uint4* dst = reinterpret_cast<uint4*>(a.x + (size_t)i * 64);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        uint4 w;
+        w.x = f[8 * q] | ((uint32_t)f[8 * q + 1] << 16);
+        w.y = f[8 * q + 2] | ((uint32_t)f[8 * q + 3] << 16);
+        w.z = f[8 * q + 4] | ((uint32_t)f[8 * q + 5] << 16);
+        w.w = f[8 * q + 6] | ((uint32_t)f[8 * q + 7] << 16);
+        dst[q] = w;
+    }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(128) k_start_cost(FuseArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
+    if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) {
+        a.nvs[i] = -1;
+        return;
+    }
+    int nb[KP];
+    nb[0] = i;
+#pragma unroll
+    for (int j = 1; j < KP; ++j) nb[j] = (j - 1) < a.k ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
+    const float d0 = a.start_dir[3 * i], d1 = a.start_dir[3 * i + 1], d2 = a.start_dir[3 * i + 2];
+    float acc = 0.0f;
+    int nv = 0;
+    for (int v = 0; v < a.V; ++v) {
+        const size_t base = (size_t)v * a.N;
+        const float2 r = a.ab[base + i];
+        if (r.x != r.x) continue;
+        ++nv;
+        float2 s[KP];
+        load_patch<KP>(a.samp, base, i, nb, s);
+        const float* cam = a.cams + 16 * v;
+        const float j0 = cam[0] * fmaf(-r.x, cam[10], cam[4]), j1 = cam[0] * fmaf(-r.x, cam[11], cam[5]),
+                    j2 = cam[0] * fmaf(-r.x, cam[12], cam[6]);
+        const float j3 = cam[1] * fmaf(-r.y, cam[10], cam[7]), j4 = cam[1] * fmaf(-r.y, cam[11], cam[8]),
+                    j5 = cam[1] * fmaf(-r.y, cam[12], cam[9]);
+        acc += view_term<KP>(fmaf(j0, d0, fmaf(j1, d1, j2 * d2)), fmaf(j3, d0, fmaf(j4, d1, j5 * d2)), s, a.vthr[v]);
+    }
+    a.best_cost[i] = nv ? 1.0f - acc / (float)nv : 1.0f;
+    a.nvs[i] = nv;
+}
+
+__global__ void k_fallback_select(const float* __restrict__ cost, const int32_t* __restrict__ nvs, int N, float tau,
+                                  int32_t* list, int* count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool want = i < N && nvs[i] > 0 && cost[i] > tau;
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) list[base + __popc(m & ((1u << lane) - 1u))] = i;
+}
+
+__global__ void k_rot(float2* rot, int T, double alpha0) {
+    const int t = threadIdx.x;
+    if (t < T) {
+        const double al = alpha0 / (double)(1u << t);
+        rot[t] = make_float2((float)cos(al), (float)sin(al));
+    }
 }
 
 // ------------------------------------------------------------------ cost of given directions
@@ -595,14 +719,19 @@ int kp_for(int k) {
 template <int HC, int KP>
 cudaError_t launch_fuse_kp(const FuseArgs& a, int stage, cudaStream_t s) {
     const dim3 grid((a.N + kFuseThreads - 1) / kFuseThreads), block(kFuseThreads);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    const bool set_attr = cs == cudaStreamCaptureStatusNone;   // set outside capture only
     if (stage == 1) {
         const size_t sm = sizeof(PatchStage<KP, kArgminStages>) + (size_t)a.vblock_q * HC * sizeof(float4);
-        cudaError_t e = cudaFuncSetAttribute(k_argmin<HC, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = set_attr ? cudaFuncSetAttribute(k_argmin<HC, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                                 : cudaSuccess;
         if (e != cudaSuccess) return e;
         k_argmin<HC, KP><<<grid, block, sm, s>>>(a);
     } else {
         const size_t sm = sizeof(PatchStage<KP, kRefineStages>) + (size_t)a.vblock_c * 3 * sizeof(float4);
-        cudaError_t e = cudaFuncSetAttribute(k_refine<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = set_attr ? cudaFuncSetAttribute(k_refine<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                                 : cudaSuccess;
         if (e != cudaSuccess) return e;
         k_refine<KP><<<grid, block, sm, s>>>(a);
     }
@@ -678,6 +807,36 @@ cudaError_t hf_launch_eval(const EvalArgs& a, cudaStream_t s) {
 
 cudaError_t hf_launch_fib(int H, float* out, cudaStream_t s) {
     k_fib<<<(H + 127) / 128, 128, 0, s>>>(H, out);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s) {
+    k_features<<<(a.N + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_start_cost(const FuseArgs& a, cudaStream_t s) {
+    const dim3 grid((a.N + 127) / 128), block(128);
+    switch (kp_for(a.k)) {
+        case 1: k_start_cost<1><<<grid, block, 0, s>>>(a); break;
+        case 4: k_start_cost<4><<<grid, block, 0, s>>>(a); break;
+        case 6: k_start_cost<6><<<grid, block, 0, s>>>(a); break;
+        case 9: k_start_cost<9><<<grid, block, 0, s>>>(a); break;
+        case 12: k_start_cost<12><<<grid, block, 0, s>>>(a); break;
+        default: k_start_cost<17><<<grid, block, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_fallback_select(const float* cost, const int32_t* nvs, int N, float tau, int32_t* list, int* count,
+                                      cudaStream_t s) {
+    k_fallback_select<<<(N + 255) / 256, 256, 0, s>>>(cost, nvs, N, tau, list, count);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_rot(float2* rot, int T, double alpha0, cudaStream_t s) {
+    if (T <= 0) return cudaSuccess;
+    k_rot<<<1, 32, 0, s>>>(rot, T, alpha0);
     return cudaGetLastError();
 }
 
