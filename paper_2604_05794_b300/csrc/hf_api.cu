@@ -12,24 +12,6 @@
 namespace {
 thread_local std::string g_create_err;
 
-template <class F>
-int run_launch(hf_ctx* c, const char* name, F&& f) {
-    ProfRec rec;
-    if (c->prof) {
-        rec.name = name;
-        cudaEventCreate(&rec.beg);
-        cudaEventCreate(&rec.end);
-        cudaEventRecord(rec.beg, c->stream);
-    }
-    cudaError_t e = f();
-    if (c->prof) {
-        cudaEventRecord(rec.end, c->stream);
-        c->prof_recs.push_back(rec);
-    }
-    c->launches++;
-    if (e != cudaSuccess) return hf_cuda_err(c, e, name);
-    return HF_OK;
-}
 
 cudaMemcpyKind kind_in(int mem_kind) { return mem_kind == HF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
 

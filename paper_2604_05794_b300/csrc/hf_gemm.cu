@@ -22,7 +22,7 @@ using namespace hf_tc;
 
 namespace {
 
-constexpr int kStages = 3;
+constexpr int kMaxStages = 3;   // ring depth: min(3, K chunks per CTA), set at launch
 constexpr uint32_t kATileBytes = 128 * 128;   // 128 rows x 64 bf16
 
 __device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
                                                  const __grid_constant__ CUtensorMap tb, GemmArgs g) {
     constexpr uint32_t kBTileBytes = BN * 128;
     extern __shared__ unsigned char smem_raw[];
+    const int kStages = g.stages;
     unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
     unsigned char* sA = base;
     unsigned char* sB = base + kStages * kATileBytes;
@@ -46,6 +47,7 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
     uint64_t* empty = full + kStages;
     uint64_t* done = empty + kStages;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    float* consts = reinterpret_cast<float*>(tslot + 4);   // bias [BN] (and W3 [3][256], b3 [3] for the head)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
@@ -64,6 +66,10 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
         tmem_alloc(tslot, tmem_cols<BN>());
         tmem_relinquish();
     }
+    if (g.bias)
+        for (int q = threadIdx.x; q < BN; q += blockDim.x) consts[q] = g.bias[n0 + q];
+    if constexpr (EPI == EPI_HEAD)
+        for (int q = threadIdx.x; q < 3 * 256 + 3; q += blockDim.x) consts[BN + q] = q < 768 ? g.w3[q] : g.b3[q - 768];
     fence_before();
     __syncthreads();
     fence_after();
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
         const int n = n0 + c0;
         if constexpr (EPI == EPI_STORE) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) g.C[(size_t)row * g.ldc + n + q] = v[q] + (g.bias ? g.bias[n + q] : 0.0f);
+            for (int q = 0; q < 16; ++q) g.C[(size_t)row * g.ldc + n + q] = v[q] + (g.bias ? consts[c0 + q] : 0.0f);
         } else if constexpr (EPI == EPI_ATOMIC) {
             const bool add_bias = g.bias && blockIdx.z == 0;
 #pragma unroll
@@ -146,7 +152,7 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
         } else if constexpr (EPI == EPI_GELU_TRAIN) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const float z = v[q] + g.bias[n + q];
+                const float z = v[q] + consts[c0 + q];
                 const uint16_t h = bf16_bits(gelu_erf(z));
                 g.Z[(size_t)row * g.ldz + n + q] = z;
                 g.H[(size_t)row * g.ldh + n + q] = h;
@@ -154,22 +160,22 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
             }
         } else if constexpr (EPI == EPI_GELU) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) g.H[(size_t)row * g.ldh + n + q] = bf16_bits(gelu_erf(v[q] + g.bias[n + q]));
+            for (int q = 0; q < 16; ++q) g.H[(size_t)row * g.ldh + n + q] = bf16_bits(gelu_erf(v[q] + consts[c0 + q]));
         } else {   // EPI_HEAD: h2 = bf16(gelu(z2)), y = W3 h2 (FP32, in column order)
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const float h = bf16_round(gelu_erf(v[q] + g.bias[n + q]));
-                y0 = fmaf(g.w3[n + q], h, y0);
-                y1 = fmaf(g.w3[256 + n + q], h, y1);
-                y2 = fmaf(g.w3[512 + n + q], h, y2);
+                const float h = bf16_round(gelu_erf(v[q] + consts[c0 + q]));
+                y0 = fmaf(consts[BN + n + q], h, y0);
+                y1 = fmaf(consts[BN + 256 + n + q], h, y1);
+                y2 = fmaf(consts[BN + 512 + n + q], h, y2);
             }
         }
     }
     if constexpr (EPI == EPI_HEAD) {
         if (wr) {
-            y0 += g.b3[0];
-            y1 += g.b3[1];
-            y2 += g.b3[2];
+            y0 += consts[BN + 768];
+            y1 += consts[BN + 769];
+            y2 += consts[BN + 770];
             const float nn = sqrtf(y0 * y0 + y1 * y1 + y2 * y2);
             float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
             if (nn > 0.0f) {
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
 
 template <int BN, int EPI>
 cudaError_t launch_bn_epi(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits, cudaStream_t s) {
-    const size_t smem = 1024 + kStages * (kATileBytes + BN * 128) + 256;
+    const size_t smem = 1024 + (size_t)g.stages * (kATileBytes + BN * 128) + 256 + (BN + 3 * 256 + 3) * 4;
     // the attribute is set outside stream capture (an eager launch comes first)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(s, &cs);
@@ -239,13 +245,15 @@ cudaError_t hf_make_tmap_bf16(CUtensorMap* map, const void* base, long long rows
 cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits,
                        cudaStream_t s) {
     if (g.K % 64 || g.N % bn || g.kchunks_per_split < 1 || splits < 1) return cudaErrorInvalidValue;
+    GemmArgs ga = g;
+    ga.stages = g.kchunks_per_split < kMaxStages ? g.kchunks_per_split : kMaxStages;
     switch (epi) {
-        case EPI_STORE: return launch_epi<EPI_STORE>(bn, ta, tb, g, splits, s);
-        case EPI_ATOMIC: return launch_epi<EPI_ATOMIC>(bn, ta, tb, g, splits, s);
-        case EPI_GELU_TRAIN: return launch_epi<EPI_GELU_TRAIN>(bn, ta, tb, g, splits, s);
-        case EPI_GELU: return launch_epi<EPI_GELU>(bn, ta, tb, g, splits, s);
-        case EPI_PARTIAL: return launch_epi<EPI_PARTIAL>(bn, ta, tb, g, splits, s);
-        default: return launch_epi<EPI_HEAD>(bn, ta, tb, g, splits, s);
+        case EPI_STORE: return launch_epi<EPI_STORE>(bn, ta, tb, ga, splits, s);
+        case EPI_ATOMIC: return launch_epi<EPI_ATOMIC>(bn, ta, tb, ga, splits, s);
+        case EPI_GELU_TRAIN: return launch_epi<EPI_GELU_TRAIN>(bn, ta, tb, ga, splits, s);
+        case EPI_GELU: return launch_epi<EPI_GELU>(bn, ta, tb, ga, splits, s);
+        case EPI_PARTIAL: return launch_epi<EPI_PARTIAL>(bn, ta, tb, ga, splits, s);
+        default: return launch_epi<EPI_HEAD>(bn, ta, tb, ga, splits, s);
     }
 }
 

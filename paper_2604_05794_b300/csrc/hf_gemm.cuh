@@ -32,6 +32,7 @@ struct GemmArgs {
     float* dir_out;           // EPI_HEAD: M x 3
     uint32_t* errw;           // device error word (HF_DEV_ERR_TIMEOUT)
     long long split_stride;   // EPI_PARTIAL: elements between the partial tiles of consecutive splits
+    int stages;               // set by hf_gemm_tn: operand ring depth
 };
 
 // 2D bf16 tensor map of a row-major [rows x cols] matrix (cols a multiple of 64, base 16-byte

@@ -66,6 +66,26 @@ int hf_set_err(hf_ctx* c, int code, const char* fmt, ...);
 int hf_cuda_err(hf_ctx* c, cudaError_t e, const char* what);
 int hf_ensure(hf_ctx* c, DevBuf& b, size_t bytes);
 
+// Run one launch (f returns its cudaError_t) with optional event timing on the context's stream.
+template <class F>
+int run_launch(hf_ctx* c, const char* name, F&& f) {
+    ProfRec rec;
+    if (c->prof) {
+        rec.name = name;
+        cudaEventCreate(&rec.beg);
+        cudaEventCreate(&rec.end);
+        cudaEventRecord(rec.beg, c->stream);
+    }
+    cudaError_t e = f();
+    if (c->prof) {
+        cudaEventRecord(rec.end, c->stream);
+        c->prof_recs.push_back(rec);
+    }
+    c->launches++;
+    if (e != cudaSuccess) return hf_cuda_err(c, e, name);
+    return HF_OK;
+}
+
 // Kernel-launch helpers (defined in hf_kernels.cu); each returns the launch error -------------
 struct ProjectArgs {
     const float* pts; int N;

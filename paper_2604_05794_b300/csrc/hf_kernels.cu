@@ -438,19 +438,33 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
     const int t_ = blockIdx.x * kFuseThreads + tid;
     const int i = t_ < cnt ? (a.list ? a.list[t_] : t_) : -1;
     const bool inb = i >= 0;
-    const int nv = inb ? a.nvs[i] : 0;
+    // From a given start direction (the learned proposal) the view count and the start cost are
+    // taken in round 0, next to the six candidates; otherwise they come from k_argmin.
+    const bool from_start = a.start_dir != nullptr;
+    int nv = 0;
+    if (inb) {
+        if (from_start && a.T > 0) {
+            const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
+            nv = (isfinite(p0) && isfinite(p1) && isfinite(p2)) ? 0 : -1;
+        } else {   // from k_argmin, or (no rounds) from k_start_cost
+            nv = a.nvs[i];
+        }
+    }
     if (inb && nv < 0) {
         a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
         if (a.cost_out) a.cost_out[i] = __int_as_float(0x7fc00000);
         if (a.idx_out) a.idx_out[i] = -1;
         if (a.status_out) a.status_out[i] = HF_STATUS_BAD_INPUT;
+        if (from_start) a.nvs[i] = -1;
     }
-    const bool active = inb && nv > 0;   // points with no view keep the best hypothesis (all costs 1)
+    // points with no view keep their start (all costs are 1)
+    const bool active = inb && ((from_start && a.T > 0) ? nv == 0 : nv > 0);
     int nb[KP];
     load_nbrs<KP, S>(a, i, active, nb, sg);
     // start: the argmin hypothesis, or a given direction (the learned proposal; index -1)
-    const int bestm = a.start_dir ? -1 : ((inb && nv >= 0) ? a.best_idx[i] : 0);
-    float best = (inb && nv >= 0) ? a.best_cost[i] : 0.0f;
+    const int bestm = from_start ? -1 : ((inb && nv >= 0) ? a.best_idx[i] : 0);
+    float best = ((!from_start || a.T == 0) && inb && nv >= 0) ? a.best_cost[i] : 0.0f;
+    float acc_c = 0.0f;   // round 0 from a start: the start direction's patch terms
     float d0, d1, d2;
     if (a.start_dir) {
         d0 = inb ? a.start_dir[3 * i] : 1.0f;
@@ -503,6 +517,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
                 f32x2 SX[KP], SY[KP];
                 stage_samples<KP, S>(sg, st, SX, SY);
                 // staged rows: k0 = (fx, fy, R00, R01), k1 = (R02, R10, R11, R12), k2 = (R20, R21, R22, thr)
+                const bool centre = from_start && t == 0;
                 const float4 k0 = cs4[3 * (v - vb)], k1 = cs4[3 * (v - vb) + 1], k2 = cs4[3 * (v - vb) + 2];
                 // Z times the projection Jacobian: rows fx (R_0 - a R_2), fy (R_1 - b R_2)
                 const float j0 = k0.x * fmaf(-r.x, k2.x, k0.z), j1 = k0.x * fmaf(-r.x, k2.y, k0.w),
@@ -519,9 +534,18 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
                     acc[2 * q] += L0;
                     acc[2 * q + 1] += L1;
                 }
+                if (centre) {
+                    const f32x2 D0 = pk(d0, d0), D1 = pk(d1, d1), D2 = pk(d2, d2);
+                    float L0, L1;
+                    view_term2<KP>(fma2(J0, D0, fma2(J1, D1, mul2(J2, D2))), fma2(J3, D0, fma2(J4, D1, mul2(J5, D2))), SX,
+                                   SY, k2.w, k2.w, L0, L1);
+                    acc_c += L0;
+                    ++nv;
+                }
             }
         }
         cp_async_wait<0>();
+        if (from_start && t == 0) best = nv > 0 ? 1.0f - acc_c / (float)nv : 1.0f;
         int choice = -1;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
@@ -540,6 +564,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
             }
     }
     if (!inb || nv < 0) return;
+    if (from_start && a.T > 0) a.nvs[i] = nv;
     const float n = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
     d0 /= n;
     d1 /= n;
@@ -565,6 +590,7 @@ __global__ void __launch_bounds__(128) k_features(FeatArgs a) {
     uint16_t f[64];
 #pragma unroll
     for (int q = 0; q < 64; ++q) f[q] = 0;
+#pragma unroll
     for (int m = 0; m < 16; ++m) {
         const int v = (m * a.V) / 16;
         const float* cam = a.cams + 16 * v;

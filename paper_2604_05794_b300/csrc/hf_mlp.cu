@@ -193,10 +193,21 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
 __global__ void k_step_inc(long long* step) { ++*step; }
 
 // ---------------------------------------------------------------- features
-// bounding box of the points: lo (3), hi (3)
-__global__ void k_bbox(const float* __restrict__ pts, int N, float* box) {
+// bounding box of the points: lo (3), hi (3); finite coordinates only.  Block partials are merged
+// with integer atomics on the order-preserving encoding of floats (exact, order independent).
+__device__ __forceinline__ unsigned fkey(float x) {
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fval(unsigned k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k); }
+
+__global__ void k_bbox_init(unsigned* keys) {
+    if (threadIdx.x < 6) keys[threadIdx.x] = threadIdx.x < 3 ? 0xffffffffu : 0u;
+}
+
+__global__ void k_bbox(const float* __restrict__ pts, int N, unsigned* keys) {
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int i = threadIdx.x; i < N; i += blockDim.x)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
         for (int q = 0; q < 3; ++q) {
             const float v = pts[3 * i + q];
             if (isfinite(v)) {
@@ -204,7 +215,6 @@ __global__ void k_bbox(const float* __restrict__ pts, int N, float* box) {
                 hi[q] = fmaxf(hi[q], v);
             }
         }
-    __shared__ float s[6][32];
     for (int q = 0; q < 3; ++q)
         for (int o = 16; o > 0; o >>= 1) {
             lo[q] = fminf(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
@@ -212,15 +222,15 @@ __global__ void k_bbox(const float* __restrict__ pts, int N, float* box) {
         }
     if ((threadIdx.x & 31) == 0)
         for (int q = 0; q < 3; ++q) {
-            s[q][threadIdx.x >> 5] = lo[q];
-            s[3 + q][threadIdx.x >> 5] = hi[q];
+            if (lo[q] <= hi[q]) {
+                atomicMin(keys + q, fkey(lo[q]));
+                atomicMax(keys + 3 + q, fkey(hi[q]));
+            }
         }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        float r = threadIdx.x < 3 ? INFINITY : -INFINITY;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = threadIdx.x < 3 ? fminf(r, s[threadIdx.x][w]) : fmaxf(r, s[threadIdx.x][w]);
-        box[threadIdx.x] = r;
-    }
+}
+
+__global__ void k_bbox_final(const unsigned* keys, float* box) {
+    if (threadIdx.x < 6) box[threadIdx.x] = fval(keys[threadIdx.x]);
 }
 
 }  // namespace
@@ -238,7 +248,10 @@ cudaError_t hf_launch_pack(const float* P, const MlpDev& d, cudaStream_t s) {
 }
 
 cudaError_t hf_launch_bbox(const float* pts, int N, float* box, cudaStream_t s) {
-    k_bbox<<<1, 1024, 0, s>>>(pts, N, box);
+    unsigned* keys = reinterpret_cast<unsigned*>(box + 8);   // 6 keys after the 6 (+2 spare) box floats
+    k_bbox_init<<<1, 32, 0, s>>>(keys);
+    k_bbox<<<296, 256, 0, s>>>(pts, N, keys);
+    k_bbox_final<<<1, 32, 0, s>>>(keys, box);
     return cudaGetLastError();
 }
 

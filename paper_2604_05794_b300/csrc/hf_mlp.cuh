@@ -44,6 +44,7 @@ struct MlpTrain {
 long long hf_mlp_param_count();
 cudaError_t hf_launch_init(float* P, uint64_t seed, cudaStream_t s);
 cudaError_t hf_launch_pack(const float* P, const MlpDev& d, cudaStream_t s);
+// box: 14 floats of device scratch; box[0..5] receives lo[3], hi[3]
 cudaError_t hf_launch_bbox(const float* pts, int N, float* box, cudaStream_t s);
 cudaError_t hf_train_step(const MlpTrain& t, cudaStream_t s);
 cudaError_t hf_mlp_infer(const MlpDev& d, const float* P, const uint16_t* x, int n, uint16_t* h1, float* dir_out,

@@ -477,31 +477,40 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
 
     PrepArgs pr{(const float*)c->cams.p, V, nullptr, H, Hpad, T, (float*)c->hyps.p, (float4*)c->qtab.p,
                 (float*)c->vthr.p, (float2*)c->rot.p, (uint32_t*)c->errw.p};
-    cudaError_t e = hf_launch_prep(pr, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->work.p, 0, 8, s);
+    if ((rc = run_launch(c, "k_prep", [&] { return hf_launch_prep(pr, s); }))) return rc;
+    cudaError_t e = cudaMemsetAsync(c->work.p, 0, 8, s);
+    if (e != cudaSuccess) return hf_cuda_err(c, e, "clear work counter");
     ProjectArgs pa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p,
                    c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, c->cfg.top_k_views, (float2*)c->samp.p, (float2*)c->ab.p,
                    (unsigned long long*)c->work.p};
-    if (e == cudaSuccess) e = hf_launch_project(pa, s);
+    if ((rc = run_launch(c, "k_project", [&] { return hf_launch_project(pa, s); }))) return rc;
     // proposal: features -> network
-    if (e == cudaSuccess) e = hf_launch_bbox((const float*)c->pts.p, N, box, s);
     FeatArgs fa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p, c->conf.p,
                 c->conf_dtype == HF_F16 ? 1 : 0, box, (uint16_t*)c->feat.p};
-    if (e == cudaSuccess) e = hf_launch_features(fa, s);
-    if (e == cudaSuccess) e = hf_mlp_infer(m->d, m->P, (const uint16_t*)c->feat.p, N, m->h1, (float*)c->prop.p,
-                                           (uint32_t*)c->errw.p, s);
+    if ((rc = run_launch(c, "k_features", [&] {
+             cudaError_t e2 = hf_launch_bbox((const float*)c->pts.p, N, box, s);
+             return e2 != cudaSuccess ? e2 : hf_launch_features(fa, s);
+         })))
+        return rc;
+    if ((rc = run_launch(c, "k_mlp", [&] {
+             return hf_mlp_infer(m->d, m->P, (const uint16_t*)c->feat.p, N, m->h1, (float*)c->prop.p,
+                                 (uint32_t*)c->errw.p, s);
+         })))
+        return rc;
     // cost of the proposal, then the short refinement from it
-    if (e == cudaSuccess) e = hf_launch_rot(rot_s, T_short, (double)alpha_short, s);
     FuseArgs fl{(const float*)c->pts.p, N, (const int32_t*)c->nbr.p, c->k, (const float*)c->cams.p, V,
                 (const float2*)c->samp.p, (const float2*)c->ab.p, (const float4*)c->qtab.p, (const float*)c->vthr.p,
                 (const float*)c->hyps.p, H, Hpad, rot_s, T_short, d_dir, d_cost, d_idx, d_status,
                 bi, (float*)(bi + N), bi + 2 * (size_t)N, hf_fuse_vblock_q(V, hc), hf_fuse_vblock_c(V)};
     fl.start_dir = (const float*)c->prop.p;
-    if (e == cudaSuccess) e = hf_launch_start_cost(fl, s);
-    if (e == cudaSuccess) e = hf_launch_refine(fl, s);
+    // with T_short >= 1 the refinement takes the start cost in its first round
+    if ((rc = run_launch(c, "k_start_cost", [&] {
+             cudaError_t e2 = hf_launch_rot(rot_s, T_short, (double)alpha_short, s);
+             return (e2 != cudaSuccess || T_short > 0) ? e2 : hf_launch_start_cost(fl, s);
+         })))
+        return rc;
+    if ((rc = run_launch(c, "k_refine_short", [&] { return hf_launch_refine(fl, s); }))) return rc;
     // points whose refined proposal costs more than tau: the plain fusion on the compacted list
-    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = hf_launch_fallback_select(d_cost, bi + 2 * (size_t)N, N, tau, list, count, s);
     FuseArgs fb = fl;
     fb.start_dir = nullptr;
     fb.rot = (const float2*)c->rot.p;
@@ -509,10 +518,13 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     fb.list = list;
     fb.list_count = count;
     fb.fell_back = 1;
-    if (e == cudaSuccess) e = hf_launch_argmin(fb, hc, s);
-    if (e == cudaSuccess) e = hf_launch_refine(fb, s);
-    c->launches += 11;
-    if (e != cudaSuccess) return hf_cuda_err(c, e, "learned fusion");
+    if ((rc = run_launch(c, "k_fallback_select", [&] {
+             cudaError_t e2 = cudaMemsetAsync(count, 0, sizeof(int), s);
+             return e2 != cudaSuccess ? e2 : hf_launch_fallback_select(d_cost, bi + 2 * (size_t)N, N, tau, list, count, s);
+         })))
+        return rc;
+    if ((rc = run_launch(c, "k_argmin_fallback", [&] { return hf_launch_argmin(fb, hc, s); }))) return rc;
+    if ((rc = run_launch(c, "k_refine_fallback", [&] { return hf_launch_refine(fb, s); }))) return rc;
     if (mem_kind == HF_HOST) {
         e = cudaMemcpyAsync(dir_out, d_dir, (size_t)N * 12, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && cost_out) e = cudaMemcpyAsync(cost_out, d_cost, (size_t)N * 4, cudaMemcpyDeviceToHost, s);
