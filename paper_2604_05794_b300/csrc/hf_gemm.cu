@@ -3,10 +3,11 @@
 //
 //   C[M x N] = A[M x K] . B[N x K]^T      A, B row-major bf16 ("TN"), K a multiple of 64
 //
-// One CTA of 128 threads computes a 128 x BN tile: thread 0 keeps a three-stage ring of 128 x 64
+// One CTA of 256 threads computes a 128 x BN tile: thread 0 keeps a ring of up to three 128 x 64
 // and BN x 64 operand tiles filled by TMA (128-byte swizzle) and issues tcgen05.mma (K = 16 per
-// instruction) into a TMEM accumulator of BN columns; the four warps then read their 32 TMEM lanes
-// (rows) back with tcgen05.ld and run the epilogue.  gridDim.z splits K (partial sums added
+// instruction) into a TMEM accumulator of BN columns; the eight warps then read the TMEM lanes of
+// their quarter (rows) and half of the columns back with tcgen05.ld and run the epilogue, storing
+// 16-byte row pieces.  gridDim.z splits K (partial tiles, or partial sums added
 // atomically).  Every mbarrier wait is bounded; on expiry the CTA records HF_DEV_ERR_TIMEOUT,
 // drains its outstanding copies (bounded as well), frees its TMEM and writes nothing.
 #include <cudaTypedefs.h>
@@ -29,13 +30,38 @@ __device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + e
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
+__device__ __forceinline__ void st_f32x16(float* dst, const float* v, bool vec) {
+    if (vec) {
+        float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) dst[q] = v[q];
+    }
+}
+
+__device__ __forceinline__ void st_bf16x16(uint16_t* dst, const uint16_t* h, bool vec) {
+    if (vec) {
+        uint32_t w[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w[q] = (uint32_t)h[2 * q] | ((uint32_t)h[2 * q + 1] << 16);
+        uint4* d4 = reinterpret_cast<uint4*>(dst);
+        d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) dst[q] = h[q];
+    }
+}
+
 template <int BN>
 __host__ __device__ constexpr uint32_t tmem_cols() {
     return BN <= 32 ? 32 : BN;
 }
 
 template <int BN, int EPI>
-__global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtensorMap ta,
+__global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtensorMap ta,
                                                  const __grid_constant__ CUtensorMap tb, GemmArgs g) {
     constexpr uint32_t kBTileBytes = BN * 128;
     extern __shared__ unsigned char smem_raw[];
@@ -128,54 +154,81 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
     }
     fence_after();
 
-    const int row = m0 + warp * 32 + lane;
+    // eight warps: warp w reads TMEM lane quarter (w & 3), i.e. rows, and column half (w >> 2)
+    const int quarter = warp & 3, half = warp >> 2;
+    const int lrow = quarter * 32 + lane;
+    const int row = m0 + lrow;
     const bool wr = ok && row < g.M;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+    constexpr int kCols = BN >= 32 ? BN / 2 : BN;   // columns per warp
+    const int cbeg = BN >= 32 ? half * kCols : 0;
+    const bool active = BN >= 32 || half == 0;
+    bool vec = false;   // 16-byte row stores when the destination allows them
+    if constexpr (EPI == EPI_STORE || EPI == EPI_PARTIAL)
+        vec = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0) && (g.ldc & 3) == 0 && (g.split_stride & 3) == 0;
+    if constexpr (EPI == EPI_GELU)
+        vec = ((reinterpret_cast<uintptr_t>(g.H) & 15) == 0) && (g.ldh & 7) == 0;
+    if constexpr (EPI == EPI_GELU_TRAIN)
+        vec = ((reinterpret_cast<uintptr_t>(g.H) & 15) == 0) && (g.ldh & 7) == 0 &&
+              ((reinterpret_cast<uintptr_t>(g.Z) & 15) == 0) && (g.ldz & 3) == 0;
     float y0 = 0.0f, y1 = 0.0f, y2 = 0.0f;   // EPI_HEAD accumulators
+    if (active) {
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-        float v[16];
-        tmem_ld16(tl + c0, v);   // all lanes, unconditionally (warp-collective)
-        if (!wr) continue;
-        const int n = n0 + c0;
-        if constexpr (EPI == EPI_STORE) {
+        for (int c0 = cbeg; c0 < cbeg + kCols; c0 += 16) {
+            float v[16];
+            tmem_ld16(tl + c0, v);   // all lanes, unconditionally (warp-collective)
+            if (!wr) continue;
+            const int n = n0 + c0;
+            if constexpr (EPI == EPI_STORE) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) g.C[(size_t)row * g.ldc + n + q] = v[q] + (g.bias ? consts[c0 + q] : 0.0f);
-        } else if constexpr (EPI == EPI_ATOMIC) {
-            const bool add_bias = g.bias && blockIdx.z == 0;
+                for (int q = 0; q < 16; ++q) v[q] += g.bias ? consts[c0 + q] : 0.0f;
+                st_f32x16(g.C + (size_t)row * g.ldc + n, v, vec);
+            } else if constexpr (EPI == EPI_ATOMIC) {
+                const bool add_bias = g.bias && blockIdx.z == 0;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) atomicAdd(g.C + (size_t)row * g.ldc + n + q, v[q] + (add_bias ? g.bias[n + q] : 0.0f));
-        } else if constexpr (EPI == EPI_PARTIAL) {
-            float* dst = g.C + (size_t)blockIdx.z * g.split_stride + (size_t)row * g.ldc + n;
+                for (int q = 0; q < 16; ++q)
+                    atomicAdd(g.C + (size_t)row * g.ldc + n + q, v[q] + (add_bias ? g.bias[n + q] : 0.0f));
+            } else if constexpr (EPI == EPI_PARTIAL) {
+                st_f32x16(g.C + (size_t)blockIdx.z * g.split_stride + (size_t)row * g.ldc + n, v, vec);
+            } else if constexpr (EPI == EPI_GELU_TRAIN) {
+                uint16_t h[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) dst[q] = v[q];
-        } else if constexpr (EPI == EPI_GELU_TRAIN) {
+                for (int q = 0; q < 16; ++q) {
+                    v[q] += consts[c0 + q];
+                    h[q] = bf16_bits(gelu_erf(v[q]));
+                    g.HT[(size_t)(n + q) * g.ldht + row] = h[q];
+                }
+                st_f32x16(g.Z + (size_t)row * g.ldz + n, v, vec);
+                st_bf16x16(g.H + (size_t)row * g.ldh + n, h, vec);
+            } else if constexpr (EPI == EPI_GELU) {
+                uint16_t h[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const float z = v[q] + consts[c0 + q];
-                const uint16_t h = bf16_bits(gelu_erf(z));
-                g.Z[(size_t)row * g.ldz + n + q] = z;
-                g.H[(size_t)row * g.ldh + n + q] = h;
-                g.HT[(size_t)(n + q) * g.ldht + row] = h;
-            }
-        } else if constexpr (EPI == EPI_GELU) {
+                for (int q = 0; q < 16; ++q) h[q] = bf16_bits(gelu_erf(v[q] + consts[c0 + q]));
+                st_bf16x16(g.H + (size_t)row * g.ldh + n, h, vec);
+            } else {   // EPI_HEAD: h2 = bf16(gelu(z2)), y = W3 h2 (FP32, in column order within each half)
 #pragma unroll
-            for (int q = 0; q < 16; ++q) g.H[(size_t)row * g.ldh + n + q] = bf16_bits(gelu_erf(v[q] + consts[c0 + q]));
-        } else {   // EPI_HEAD: h2 = bf16(gelu(z2)), y = W3 h2 (FP32, in column order)
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const float h = bf16_round(gelu_erf(v[q] + consts[c0 + q]));
-                y0 = fmaf(consts[BN + n + q], h, y0);
-                y1 = fmaf(consts[BN + 256 + n + q], h, y1);
-                y2 = fmaf(consts[BN + 512 + n + q], h, y2);
+                for (int q = 0; q < 16; ++q) {
+                    const float h = bf16_round(gelu_erf(v[q] + consts[c0 + q]));
+                    y0 = fmaf(consts[BN + n + q], h, y0);
+                    y1 = fmaf(consts[BN + 256 + n + q], h, y1);
+                    y2 = fmaf(consts[BN + 512 + n + q], h, y2);
+                }
             }
         }
     }
     if constexpr (EPI == EPI_HEAD) {
-        if (wr) {
-            y0 += consts[BN + 768];
-            y1 += consts[BN + 769];
-            y2 += consts[BN + 770];
+        // the second column half hands its partial sums to the first through shared memory
+        float* part = consts + BN + 3 * 256 + 4;
+        if (half == 1) {
+            part[3 * lrow] = y0;
+            part[3 * lrow + 1] = y1;
+            part[3 * lrow + 2] = y2;
+        }
+        __syncthreads();
+        if (half == 0 && wr) {
+            y0 += part[3 * lrow] + consts[BN + 768];
+            y1 += part[3 * lrow + 1] + consts[BN + 769];
+            y2 += part[3 * lrow + 2] + consts[BN + 770];
             const float nn = sqrtf(y0 * y0 + y1 * y1 + y2 * y2);
             float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
             if (nn > 0.0f) {
@@ -195,7 +248,7 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
 
 template <int BN, int EPI>
 cudaError_t launch_bn_epi(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits, cudaStream_t s) {
-    const size_t smem = 1024 + (size_t)g.stages * (kATileBytes + BN * 128) + 256 + (BN + 3 * 256 + 3) * 4;
+    const size_t smem = 1024 + (size_t)g.stages * (kATileBytes + BN * 128) + 256 + (BN + 3 * 256 + 4 + 3 * 128) * 4;
     // the attribute is set outside stream capture (an eager launch comes first)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(s, &cs);
@@ -203,7 +256,7 @@ cudaError_t launch_bn_epi(const CUtensorMap& ta, const CUtensorMap& tb, const Ge
         e = cudaFuncSetAttribute(k_gemm_tn<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((g.M + 127) / 128, g.N / BN, splits);
-    k_gemm_tn<BN, EPI><<<grid, 128, smem, s>>>(ta, tb, g);
+    k_gemm_tn<BN, EPI><<<grid, 256, smem, s>>>(ta, tb, g);
     return cudaGetLastError();
 }
 
@@ -246,7 +299,9 @@ cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap
                        cudaStream_t s) {
     if (g.K % 64 || g.N % bn || g.kchunks_per_split < 1 || splits < 1) return cudaErrorInvalidValue;
     GemmArgs ga = g;
-    ga.stages = g.kchunks_per_split < kMaxStages ? g.kchunks_per_split : kMaxStages;
+    // BN = 256 tiles keep two stages so that two CTAs fit on an SM
+    const int max_stages = bn >= 256 ? 2 : kMaxStages;
+    ga.stages = g.kchunks_per_split < max_stages ? g.kchunks_per_split : max_stages;
     switch (epi) {
         case EPI_STORE: return launch_epi<EPI_STORE>(bn, ta, tb, ga, splits, s);
         case EPI_ATOMIC: return launch_epi<EPI_ATOMIC>(bn, ta, tb, ga, splits, s);
