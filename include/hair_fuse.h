@@ -210,6 +210,74 @@ int hair_fuse_features(hf_ctx* ctx, uint16_t* x_out, int mem_kind);
 int hair_fuse_fuse_learned(hf_ctx* ctx, hf_mlp* mlp, int T_short, float alpha_short, float tau, float* dir_out,
                            float* cost_out, int32_t* idx_out, uint8_t* status_out, int* n_fallback, int mem_kind);
 
+/* ------------------------------------------------------------------------------------------------
+ * Batched serving: the fusion of many uploaded scenes (contexts) of uneven point count, view count
+ * and map size in one submission.  Each stage of the path is ONE persistent launch over the
+ * (scene, tile) items of all scenes, the proposal network (when given) runs once over the feature
+ * rows of all scenes, and the stage sequence is captured in one CUDA graph that every run replays.
+ * A scene's results are bit-identical to hair_fuse_fuse_directions (mlp == NULL, built-in
+ * hypotheses) or hair_fuse_fuse_learned (mlp given) on that scene alone.
+ *
+ * Ownership: the batch keeps pointers to the contexts and to the output buffers; both must outlive
+ * it (and the contexts must not be re-uploaded while it exists).  The batch allocates its own
+ * scratch (features, proposals, hidden activations, fallback lists: about 660 bytes per point of
+ * the batch with a network, none without) and runs on its own stream, ordered after cuda_stream at
+ * every run and ordering cuda_stream after itself.  Train or load the network before creating the
+ * batch.
+ * ------------------------------------------------------------------------------------------------ */
+/* per-kernel (or per-stage) timing record */
+typedef struct {
+    char name[32];
+    int launches;
+    double total_ms;
+} hf_kernel_time;
+typedef struct hf_batch hf_batch;
+
+#define HF_MAX_BATCH_SCENES 64
+
+typedef struct {
+    int T_short;        /* learned: refinement rounds from the proposal, 1..HF_MAX_T */
+    float alpha_short;  /* learned: first rotation step (radians), halved each round */
+    float tau;          /* learned: fallback threshold on the refined proposal's cost */
+    int autotune;       /* 1: at the first run, time the candidate tile shapes on the batch and keep the fastest */
+    int hchunk;         /* hypotheses per chunk of the argmin: 0 = tuned / default, else 8, 16 or 32 */
+    int points_per_cta; /* points per CTA of argmin and refinement: 0 = tuned / default 128, else 64, 128, 256 */
+    int order;          /* scene order of the work list: 0 = tuned / heaviest first, 1 = heaviest first, 2 = as given */
+} hf_batch_cfg;
+
+/* n_scenes (1..HF_MAX_BATCH_SCENES) contexts with views and points uploaded; mlp = NULL for the
+ * plain fusion.  cfg may be NULL (defaults, plain only).  Errors: HF_ERR_INVALID_ARG, _SHAPE,
+ * _NOT_UPLOADED, _OOM, _CUDA (message via hair_fuse_batch_last_error(NULL)). */
+int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int n_scenes, hf_mlp* mlp,
+                           const hf_batch_cfg* cfg, void* cuda_stream);
+/* Device output buffers of scene `scene` (as in hair_fuse_fuse_directions; cost_out is required
+ * with a network).  Must be set for every scene before the first run; changing them re-captures. */
+int hair_fuse_batch_set_outputs(hf_batch* b, int scene, float* dir_out, float* cost_out, int32_t* idx_out,
+                                uint8_t* status_out);
+/* Enqueue one fusion of every scene (asynchronous).  use_graph != 0 replays the captured graph
+ * (captured at the first such call, after one eager run; autotuning, if enabled, runs first). */
+int hair_fuse_batch_run(hf_batch* b, int use_graph);
+/* Wait for the batch and return any error latched on the device. */
+int hair_fuse_batch_sync(hf_batch* b);
+/* Per-scene completion time of the last run in ms after its start (device global timer: the CTA
+ * finishing a scene's last tile stamps it), ms_out[n_scenes], host.  Synchronises. */
+int hair_fuse_batch_latency(hf_batch* b, double* ms_out);
+/* Per-scene fallback counts of the last learned run (0 for the plain fusion), host.  Synchronises. */
+int hair_fuse_batch_fallbacks(hf_batch* b, int* n_out);
+/* The launch shape in use: out4 = {hypothesis chunk, points per CTA of the argmin, points per CTA of
+ * the refinement, heaviest-first order (1) or as given (0)}. */
+int hair_fuse_batch_tuning(const hf_batch* b, int* out4);
+/* One eager run with CUDA events between the stages (synchronous): per-stage records as in
+ * hair_fuse_profile_read (the network's stage counts its two GEMM launches).  Returns the number of
+ * stages (records beyond max_entries are dropped) or a negative error code. */
+int hair_fuse_batch_profile_run(hf_batch* b, hf_kernel_time* out, int max_entries);
+/* Kernel launches issued so far (graph replays counted by their kernels), and from the last run the
+ * (point, view) pairs in the points' view sets of all scenes and, for the learned path, of the
+ * fallback points (any pointer may be NULL; the work counts synchronise). */
+int hair_fuse_batch_stats(hf_batch* b, long long* launches, long long* point_views, long long* fallback_point_views);
+void hair_fuse_batch_destroy(hf_batch* b);
+const char* hair_fuse_batch_last_error(const hf_batch* b);
+
 /* The built-in hypothesis set (host memory): H x 3 f32 Fibonacci hemisphere directions. */
 int hair_fuse_fibonacci_hemisphere(int H, float* out);
 
@@ -219,11 +287,6 @@ int hair_fuse_sync(hf_ctx* ctx);
 /* Per-kernel timing with CUDA events recorded on the context's stream around every launch.
  * hair_fuse_profile(ctx, 1) clears and enables it; hair_fuse_profile_read() synchronises and
  * fills up to max_entries records, returning how many kernels have records. */
-typedef struct {
-    char name[32];
-    int launches;
-    double total_ms;
-} hf_kernel_time;
 int hair_fuse_profile(hf_ctx* ctx, int enable);
 int hair_fuse_profile_read(hf_ctx* ctx, hf_kernel_time* out, int max_entries);
 

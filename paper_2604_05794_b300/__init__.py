@@ -69,6 +69,17 @@ _SIGS = {
     "hair_fuse_features": ([_vp, _vp, _i], _i),
     "hair_fuse_fuse_learned": ([_vp, _vp, _i, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp, _vp,
                                 ctypes.POINTER(_i), _i], _i),
+    "hair_fuse_batch_create": ([ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp, _vp, _vp], _i),
+    "hair_fuse_batch_set_outputs": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
+    "hair_fuse_batch_run": ([_vp, _i], _i),
+    "hair_fuse_batch_sync": ([_vp], _i),
+    "hair_fuse_batch_latency": ([_vp, _vp], _i),
+    "hair_fuse_batch_fallbacks": ([_vp, _vp], _i),
+    "hair_fuse_batch_tuning": ([_vp, _vp], _i),
+    "hair_fuse_batch_profile_run": ([_vp, ctypes.POINTER(hf_kernel_time), _i], _i),
+    "hair_fuse_batch_stats": ([_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll), ctypes.POINTER(_ll)], _i),
+    "hair_fuse_batch_destroy": ([_vp], None),
+    "hair_fuse_batch_last_error": ([_vp], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -106,6 +117,17 @@ hair_fuse_mlp_load = _lib.hair_fuse_mlp_load
 hair_fuse_mlp_last_error = _lib.hair_fuse_mlp_last_error
 hair_fuse_features = _lib.hair_fuse_features
 hair_fuse_fuse_learned = _lib.hair_fuse_fuse_learned
+hair_fuse_batch_create = _lib.hair_fuse_batch_create
+hair_fuse_batch_set_outputs = _lib.hair_fuse_batch_set_outputs
+hair_fuse_batch_run = _lib.hair_fuse_batch_run
+hair_fuse_batch_sync = _lib.hair_fuse_batch_sync
+hair_fuse_batch_latency = _lib.hair_fuse_batch_latency
+hair_fuse_batch_fallbacks = _lib.hair_fuse_batch_fallbacks
+hair_fuse_batch_tuning = _lib.hair_fuse_batch_tuning
+hair_fuse_batch_profile_run = _lib.hair_fuse_batch_profile_run
+hair_fuse_batch_stats = _lib.hair_fuse_batch_stats
+hair_fuse_batch_destroy = _lib.hair_fuse_batch_destroy
+hair_fuse_batch_last_error = _lib.hair_fuse_batch_last_error
 
 
 class HairFuseError(RuntimeError):
@@ -364,3 +386,89 @@ def _fuse_learned(self, net, dir_out, cost_out=None, idx_out=None, status_out=No
 
 HairFuse.features = _features
 HairFuse.fuse_learned = _fuse_learned
+
+
+class hf_batch_cfg(ctypes.Structure):
+    _fields_ = [("T_short", ctypes.c_int), ("alpha_short", ctypes.c_float), ("tau", ctypes.c_float),
+                ("autotune", ctypes.c_int), ("hchunk", ctypes.c_int), ("points_per_cta", ctypes.c_int),
+                ("order", ctypes.c_int)]
+
+
+class Batch:
+    """Batched fusion of several HairFuse contexts (plain, or learned with a ProposalNet): one
+    persistent launch per stage over all scenes, replayed as one CUDA graph."""
+
+    def __init__(self, scenes, net=None, T_short=2, alpha_short=0.02, tau=0.5, autotune=True, hchunk=0,
+                 points_per_cta=0, order=0, stream=None):
+        self.scenes = list(scenes)
+        self.net = net
+        cfg = hf_batch_cfg(T_short, alpha_short, tau, 1 if autotune else 0, hchunk, points_per_cta, order)
+        arr = (_vp * len(self.scenes))(*[sc.h for sc in self.scenes])
+        h = _vp()
+        rc = hair_fuse_batch_create(ctypes.byref(h), arr, len(self.scenes), net.h if net is not None else None,
+                                    ctypes.byref(cfg), current_stream_handle() if stream is None else stream)
+        if rc != HF_OK:
+            msg = hair_fuse_batch_last_error(None)
+            raise HairFuseError(rc, msg.decode() if msg else "")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            hair_fuse_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _c(self, rc):
+        if rc != HF_OK:
+            msg = hair_fuse_batch_last_error(self.h)
+            raise HairFuseError(rc, msg.decode() if msg else "")
+        return rc
+
+    def set_outputs(self, scene, dir_out, cost_out=None, idx_out=None, status_out=None):
+        """CUDA tensors of scene `scene`: dir (N, 3) f32, cost (N,) f32, idx (N,) i32, status (N,) u8."""
+        ptr = [x.data_ptr() if x is not None else None for x in (dir_out, cost_out, idx_out, status_out)]
+        self._c(hair_fuse_batch_set_outputs(self.h, scene, *ptr))
+
+    def run(self, use_graph=True):
+        self._c(hair_fuse_batch_run(self.h, 1 if use_graph else 0))
+
+    def sync(self):
+        self._c(hair_fuse_batch_sync(self.h))
+
+    def latency_ms(self):
+        out = np.zeros(len(self.scenes), np.float64)
+        self._c(hair_fuse_batch_latency(self.h, out.ctypes.data))
+        return out
+
+    def fallbacks(self):
+        out = np.zeros(len(self.scenes), np.int32)
+        self._c(hair_fuse_batch_fallbacks(self.h, out.ctypes.data))
+        return out
+
+    def tuning(self):
+        out = np.zeros(4, np.int32)
+        self._c(hair_fuse_batch_tuning(self.h, out.ctypes.data))
+        return dict(hchunk=int(out[0]), points_per_cta_argmin=int(out[1]), points_per_cta_refine=int(out[2]),
+                    heaviest_first=bool(out[3]))
+
+    def profile_run(self):
+        """One eager run with events between the stages: {stage: (launches, ms)}."""
+        recs = (hf_kernel_time * 16)()
+        n = hair_fuse_batch_profile_run(self.h, recs, 16)
+        if n < 0:
+            self._c(n)
+        return {recs[q].name.decode(): (recs[q].launches, recs[q].total_ms) for q in range(min(n, 16))}
+
+    def stats(self):
+        """launches so far; (point, view) pairs of all points and of the fallback points (last run)."""
+        l, pv, fpv = _ll(0), _ll(0), _ll(0)
+        self._c(hair_fuse_batch_stats(self.h, ctypes.byref(l), ctypes.byref(pv), ctypes.byref(fpv)))
+        return dict(launches=l.value, point_views=pv.value, fallback_point_views=fpv.value)

@@ -1,0 +1,631 @@
+// hf_batch.cu - batched serving: many uploaded scenes of uneven size fused together.
+//
+// Every stage of the fusion (constants, projection + gather, features, proposal network, short
+// refinement, fallback selection, hypothesis argmin, refinement) is ONE launch over all scenes of
+// the batch: a persistent grid takes (scene, tile) items from a global counter (hf_kernels.cu), the
+// proposal network runs once over the concatenated feature rows of all scenes, and the whole stage
+// sequence is captured in one CUDA graph that each run replays.  The tile shape of the cost
+// kernels (hypothesis chunk, points per CTA) and the scene order are picked by timing the
+// candidates on the batch itself (autotuning, first run).  The CTA finishing a scene's last tile
+// stamps the global timer, which gives per-scene completion latencies.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hf_internal.cuh"
+#include "hf_mlp.cuh"
+
+namespace {
+
+// stage slots of the item counters
+enum { ST_PROJECT, ST_FEATURES, ST_SHORT, ST_SELECT, ST_ARGMIN, ST_MAIN, ST_MLP, ST_COUNT };
+const char* const kStageName[ST_COUNT] = {"k_project_batch", "k_features_batch", "k_refine_short_batch", "k_select_batch",
+                                          "k_argmin_batch", "k_refine_batch", "k_mlp"};
+static_assert(ST_COUNT <= 8, "eight item counters");
+
+// device control block (bytes); [0, kZeroEnd) is cleared by k_prep_batch at the start of a run
+constexpr size_t kNextOff = 0;                                   // u32 [ST_COUNT] (padded to 8)
+constexpr size_t kDoneOff = 32;                                  // u32 [2][HF_MAX_BATCH]: short, main
+constexpr size_t kCountOff = kDoneOff + 2 * HF_MAX_BATCH * 4;    // i32 [HF_MAX_BATCH]: fallback list lengths
+constexpr size_t kWorkOff = kCountOff + HF_MAX_BATCH * 4;        // u64 [HF_MAX_BATCH]: (point, view) pairs
+constexpr size_t kStampOff = kWorkOff + HF_MAX_BATCH * 8;        // u64 [2][HF_MAX_BATCH]: completion times
+constexpr size_t kZeroEnd = kStampOff + 2 * HF_MAX_BATCH * 8;
+constexpr size_t kT0Off = kZeroEnd;                              // u64 batch start
+constexpr size_t kBoxOff = kT0Off + 8;                           // u32 [HF_MAX_BATCH][6]
+constexpr size_t kRotOff = kBoxOff + HF_MAX_BATCH * 24;          // float2 [HF_MAX_T]
+constexpr size_t kErrOff = kRotOff + HF_MAX_T * 8;               // u32 error word
+constexpr size_t kCtlBytes = kErrOff + 8;
+static_assert(kWorkOff % 8 == 0 && kStampOff % 8 == 0 && kT0Off % 8 == 0 && kRotOff % 8 == 0, "alignment");
+
+struct BatchScene {
+    hf_ctx* c = nullptr;
+    float* dir = nullptr;
+    float* cost = nullptr;
+    int32_t* idx = nullptr;
+    uint8_t* status = nullptr;
+    long long off = 0;   // first row in the concatenated feature / proposal / list arrays
+    double work = 0.0;   // relative cost of the scene, for heaviest-first ordering
+};
+
+// per-position argument arrays, uploaded as one block
+struct ArgBlock {
+    PrepArgs prep[HF_MAX_BATCH];
+    ProjectArgs proj[HF_MAX_BATCH];
+    FeatArgs feat[HF_MAX_BATCH];
+    FuseArgs shrt[HF_MAX_BATCH];
+    SelectArgs sel[HF_MAX_BATCH];
+    FuseArgs main[HF_MAX_BATCH];
+};
+
+}  // namespace
+
+struct hf_batch {
+    std::vector<BatchScene> sc;
+    std::vector<int> pos;   // position -> scene index
+    hf_mlp* mlp = nullptr;
+    hf_batch_cfg cfg{};
+    cudaStream_t user = nullptr;    // caller's stream (ordering only)
+    cudaStream_t stream = nullptr;  // the batch's own non-blocking stream (captured)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, t_beg = nullptr, t_end = nullptr;
+    int kp = 9, hc = 32, nt_a = 128, nt_r = 128, heavy_first = 1;
+    bool tuned = false, configured = false;
+    long long total = 0;
+    char* ctl = nullptr;
+    ArgBlock* args = nullptr;   // device
+    ArgBlock* args_h = nullptr; // pinned host copy
+    uint16_t* x = nullptr;
+    float* prop = nullptr;
+    uint16_t* h1 = nullptr;
+    int32_t* list = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long launches = 0;   // kernels enqueued (graph replays counted by their kernels)
+    std::string err;
+};
+
+namespace {
+
+int b_err(hf_batch* b, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    b->err = buf;
+    return code;
+}
+
+int b_cuda(hf_batch* b, cudaError_t e, const char* what) {
+    return b_err(b, HF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void drop_graph(hf_batch* b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+}
+
+// Fill and upload the argument arrays for the current tuning choice (hc, order).
+int configure(hf_batch* b) {
+    const int ns = (int)b->sc.size();
+    b->pos.resize(ns);
+    for (int p = 0; p < ns; ++p) b->pos[p] = p;
+    if (b->heavy_first)
+        std::stable_sort(b->pos.begin(), b->pos.end(), [&](int u, int v) { return b->sc[u].work > b->sc[v].work; });
+    const bool learned = b->mlp != nullptr;
+    unsigned* box = reinterpret_cast<unsigned*>(b->ctl + kBoxOff);
+    int* count = reinterpret_cast<int*>(b->ctl + kCountOff);
+    unsigned long long* work = reinterpret_cast<unsigned long long*>(b->ctl + kWorkOff);
+    float2* rot_s = reinterpret_cast<float2*>(b->ctl + kRotOff);
+    uint32_t* errw = reinterpret_cast<uint32_t*>(b->ctl + kErrOff);
+    ArgBlock& A = *b->args_h;
+    std::memset(&A, 0, sizeof A);
+    for (int p = 0; p < ns; ++p) {
+        const BatchScene& s = b->sc[b->pos[p]];
+        hf_ctx* c = s.c;
+        const int N = c->N, V = c->V, H = c->cfg.H, T = c->cfg.T;
+        const int Hpad = (H + b->hc - 1) / b->hc * b->hc;
+        int32_t* bi = (int32_t*)c->best.p;
+        A.prep[p] = PrepArgs{(const float*)c->cams.p, V, nullptr, H, Hpad, T, (float*)c->hyps.p, (float4*)c->qtab.p,
+                             (float*)c->vthr.p, (float2*)c->rot.p, errw};
+        A.proj[p] = ProjectArgs{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh,
+                                (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0,
+                                c->cfg.top_k_views, (float2*)c->samp.p, (float2*)c->ab.p, work + p,
+                                learned ? box + 6 * p : nullptr};
+        A.feat[p] = FeatArgs{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh,
+                             (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, nullptr,
+                             b->x + (size_t)s.off * 64, box + 6 * p};
+        FuseArgs m{(const float*)c->pts.p, N, (const int32_t*)c->nbr.p, c->k, (const float*)c->cams.p, V,
+                   (const float2*)c->samp.p, (const float2*)c->ab.p, (const float4*)c->qtab.p, (const float*)c->vthr.p,
+                   (const float*)c->hyps.p, H, Hpad, (const float2*)c->rot.p, T, s.dir, s.cost, s.idx, s.status,
+                   bi, (float*)(bi + N), bi + 2 * (size_t)N, hf_fuse_vblock_q(V, b->hc), hf_fuse_vblock_c(V)};
+        if (learned) {
+            FuseArgs f = m;
+            f.rot = rot_s;
+            f.T = b->cfg.T_short;
+            f.start_dir = b->prop + (size_t)s.off * 3;
+            A.shrt[p] = f;
+            A.sel[p] = SelectArgs{s.cost, bi + 2 * (size_t)N, N, b->cfg.tau, b->list + s.off, count + p};
+            m.list = b->list + s.off;
+            m.list_count = count + p;
+            m.fell_back = 1;
+        }
+        A.main[p] = m;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->args, b->args_h, sizeof(ArgBlock), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b_cuda(b, e, "upload batch arguments");
+    b->configured = true;
+    return HF_OK;
+}
+
+BatchCtl ctl_for(hf_batch* b, int stage, int stamp_slot) {
+    BatchCtl c{};
+    c.next = reinterpret_cast<unsigned*>(b->ctl + kNextOff) + stage;
+    c.ns = (int)b->sc.size();
+    if (stamp_slot >= 0) {
+        c.done = reinterpret_cast<unsigned*>(b->ctl + kDoneOff) + stamp_slot * HF_MAX_BATCH;
+        c.stamp = reinterpret_cast<unsigned long long*>(b->ctl + kStampOff) + stamp_slot * HF_MAX_BATCH;
+    }
+    return c;
+}
+
+cudaError_t launch_prep(hf_batch* b, bool reset) {
+    BatchReset r{};
+    if (reset) {
+        r.zero = reinterpret_cast<unsigned*>(b->ctl);
+        r.nzero = (int)(kZeroEnd / 4);
+        r.box_keys = reinterpret_cast<unsigned*>(b->ctl + kBoxOff);
+        r.t0 = reinterpret_cast<unsigned long long*>(b->ctl + kT0Off);
+        if (b->mlp) {
+            r.rot_s = reinterpret_cast<float2*>(b->ctl + kRotOff);
+            r.T_short = b->cfg.T_short;
+            r.alpha_short = (double)b->cfg.alpha_short;
+        }
+    }
+    return hf_launch_prep_batch(b->args->prep, (int)b->sc.size(), r, b->stream);
+}
+
+cudaError_t launch_stage(hf_batch* b, int stage) {
+    cudaStream_t s = b->stream;
+    ArgBlock* A = b->args;
+    switch (stage) {
+        case ST_PROJECT: return hf_launch_project_batch(A->proj, ctl_for(b, ST_PROJECT, -1), s);
+        case ST_FEATURES: return hf_launch_features_batch(A->feat, ctl_for(b, ST_FEATURES, -1), s);
+        case ST_MLP:
+            return hf_mlp_infer_rows(b->mlp, b->x, b->total, b->h1, b->prop, reinterpret_cast<uint32_t*>(b->ctl + kErrOff), s);
+        case ST_SHORT: return hf_launch_refine_batch(A->shrt, ctl_for(b, ST_SHORT, 0), b->kp, b->nt_r, s);
+        case ST_SELECT: return hf_launch_select_batch(A->sel, ctl_for(b, ST_SELECT, -1), s);
+        case ST_ARGMIN: return hf_launch_argmin_batch(A->main, ctl_for(b, ST_ARGMIN, -1), b->kp, b->hc, b->nt_a, s);
+        default: return hf_launch_refine_batch(A->main, ctl_for(b, ST_MAIN, 1), b->kp, b->nt_r, s);
+    }
+}
+
+// kernels of one run (the network's two GEMMs included)
+int kernels_per_run(const hf_batch* b) { return b->mlp ? 9 : 4; }
+
+// the whole run: constants (and counter reset), then every stage in order; with ev (profiling,
+// eager only) an event is recorded after the constants and after every stage
+cudaError_t enqueue(hf_batch* b, cudaEvent_t* ev = nullptr, int* stages_out = nullptr, int* n_out = nullptr) {
+    if (ev) cudaEventRecord(ev[0], b->stream);
+    cudaError_t e = launch_prep(b, true);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], b->stream);
+    const bool learned = b->mlp != nullptr;
+    const int plain_stages[] = {ST_PROJECT, ST_ARGMIN, ST_MAIN};
+    const int learned_stages[] = {ST_PROJECT, ST_FEATURES, ST_MLP, ST_SHORT, ST_SELECT, ST_ARGMIN, ST_MAIN};
+    const int* st = learned ? learned_stages : plain_stages;
+    const int n = learned ? 7 : 3;
+    for (int q = 0; q < n && e == cudaSuccess; ++q) {
+        e = launch_stage(b, st[q]);
+        if (ev) cudaEventRecord(ev[2 + q], b->stream);
+    }
+    if (stages_out)
+        for (int q = 0; q < n; ++q) stages_out[q] = st[q];
+    if (n_out) *n_out = n;
+    b->launches += kernels_per_run(b);
+    return e;
+}
+
+// time one stage re-run (its item counter cleared first); min of reps, ms
+int time_stage(hf_batch* b, int stage, int reps, float* ms) {
+    float best = INFINITY;
+    for (int r = 0; r < reps; ++r) {
+        cudaError_t e = cudaMemsetAsync(reinterpret_cast<unsigned*>(b->ctl + kNextOff) + stage, 0, 4, b->stream);
+        // the selection appends to the fallback lists: they start empty
+        if (e == cudaSuccess && stage == ST_SELECT) e = cudaMemsetAsync(b->ctl + kCountOff, 0, HF_MAX_BATCH * 4, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b->t_beg, b->stream);
+        if (e == cudaSuccess) e = launch_stage(b, stage);
+        if (e == cudaSuccess) e = cudaEventRecord(b->t_end, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b->t_end);
+        float t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, b->t_beg, b->t_end);
+        if (e != cudaSuccess) return b_cuda(b, e, "autotune timing");
+        best = std::min(best, t);
+    }
+    *ms = best;
+    return HF_OK;
+}
+
+int run_eager(hf_batch* b) {
+    cudaError_t e = enqueue(b);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b_cuda(b, e, "batch run");
+    return HF_OK;
+}
+
+// Autotuner: candidate tile shapes timed on the batch itself.  The stages are re-run in pipeline
+// order, so every buffer a timed stage reads holds what the full run left there.
+int autotune(hf_batch* b) {
+    int rc;
+    const int hcs[] = {8, 16, 32};
+    const int nts[] = {64, 128, 256};
+    const bool learned = b->mlp != nullptr;
+    if ((rc = configure(b)) || (rc = run_eager(b))) return rc;
+    // refinement: points per CTA (both refinement stages)
+    float best = INFINITY;
+    int best_nt = b->nt_r;
+    for (int nt : nts) {
+        if (b->cfg.points_per_cta && nt != b->cfg.points_per_cta) continue;
+        b->nt_r = nt;
+        float t = 0.0f, t2 = 0.0f;
+        if (learned && (rc = time_stage(b, ST_SHORT, 2, &t2))) return rc;
+        if (learned && (rc = time_stage(b, ST_SELECT, 1, &t))) return rc;   // restores the lists
+        if ((rc = time_stage(b, ST_ARGMIN, 1, &t))) return rc;
+        if ((rc = time_stage(b, ST_MAIN, 2, &t))) return rc;
+        if (t + t2 < best) {
+            best = t + t2;
+            best_nt = nt;
+        }
+    }
+    b->nt_r = best_nt;
+    // argmin: hypothesis chunk x points per CTA (the constants are rebuilt for each chunk)
+    best = INFINITY;
+    int best_hc = b->hc, best_nta = b->nt_a;
+    for (int hc : hcs) {
+        if (b->cfg.hchunk && hc != b->cfg.hchunk) continue;
+        b->hc = hc;
+        if ((rc = configure(b))) return rc;
+        cudaError_t e = launch_prep(b, false);
+        if (e != cudaSuccess) return b_cuda(b, e, "autotune constants");
+        for (int nt : nts) {
+            if (b->cfg.points_per_cta && nt != b->cfg.points_per_cta) continue;
+            b->nt_a = nt;
+            float t = 0.0f;
+            if ((rc = time_stage(b, ST_ARGMIN, 2, &t))) return rc;
+            if (t < best) {
+                best = t;
+                best_hc = hc;
+                best_nta = nt;
+            }
+        }
+    }
+    b->hc = best_hc;
+    b->nt_a = best_nta;
+    // scene order: heaviest first against the given order (full runs)
+    if (!b->cfg.order) {
+        float tt[2] = {0.0f, 0.0f};
+        for (int hf = 0; hf < 2; ++hf) {
+            b->heavy_first = hf;
+            if ((rc = configure(b)) || (rc = run_eager(b))) return rc;
+            cudaError_t e = cudaEventRecord(b->t_beg, b->stream);
+            if (e == cudaSuccess) e = enqueue(b);
+            if (e == cudaSuccess) e = cudaEventRecord(b->t_end, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b->t_end);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&tt[hf], b->t_beg, b->t_end);
+            if (e != cudaSuccess) return b_cuda(b, e, "autotune order");
+        }
+        b->heavy_first = tt[1] <= tt[0] ? 1 : 0;
+    }
+    if ((rc = configure(b)) || (rc = run_eager(b))) return rc;
+    b->tuned = true;
+    return HF_OK;
+}
+
+int check_errw(hf_batch* b) {
+    uint32_t w = 0;
+    cudaError_t e = cudaMemcpyAsync(&w, b->ctl + kErrOff, 4, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b_cuda(b, e, "read device error word");
+    if (w) {
+        cudaMemsetAsync(b->ctl + kErrOff, 0, 4, b->stream);
+        cudaStreamSynchronize(b->stream);
+        if (w & HF_DEV_ERR_TIMEOUT) return b_err(b, HF_ERR_TIMEOUT, "a bounded device wait expired");
+        return b_err(b, HF_ERR_CUDA, "device error word 0x%x", w);
+    }
+    return HF_OK;
+}
+
+thread_local std::string g_batch_create_err;
+
+}  // namespace
+
+extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int n_scenes, hf_mlp* mlp,
+                                      const hf_batch_cfg* cfg, void* cuda_stream) {
+    auto fail = [&](int code, const char* msg) {
+        g_batch_create_err = msg;
+        return code;
+    };
+    if (!out || !scenes) return fail(HF_ERR_INVALID_ARG, "out and scenes are required");
+    *out = nullptr;
+    if (n_scenes < 1 || n_scenes > HF_MAX_BATCH) return fail(HF_ERR_SHAPE, "n_scenes must be in [1, 64]");
+    hf_batch_cfg c{};
+    if (cfg) c = *cfg;
+    if (mlp && (c.T_short < 1 || c.T_short > HF_MAX_T || !(c.alpha_short > 0.0f) || !(c.tau == c.tau)))
+        return fail(HF_ERR_INVALID_ARG, "learned batch: T_short in [1, 24], alpha_short > 0 and a non-NaN tau required");
+    if (c.hchunk && c.hchunk != 8 && c.hchunk != 16 && c.hchunk != 32) return fail(HF_ERR_INVALID_ARG, "hchunk: 0, 8, 16 or 32");
+    if (c.points_per_cta && c.points_per_cta != 64 && c.points_per_cta != 128 && c.points_per_cta != 256)
+        return fail(HF_ERR_INVALID_ARG, "points_per_cta: 0, 64, 128 or 256");
+    if (c.order < 0 || c.order > 2) return fail(HF_ERR_INVALID_ARG, "order: 0, 1 or 2");
+    long long total = 0;
+    int max_k = 0, maxH = 1;
+    for (int s = 0; s < n_scenes; ++s) {
+        hf_ctx* x = scenes[s];
+        if (!x) return fail(HF_ERR_INVALID_ARG, "a scene is null");
+        if (x->V <= 0 || x->N <= 0) return fail(HF_ERR_NOT_UPLOADED, "a scene has no views or no points uploaded");
+        for (int t = 0; t < s; ++t)
+            if (scenes[t] == x) return fail(HF_ERR_INVALID_ARG, "a scene appears twice");
+        total += x->N;
+        max_k = std::max(max_k, x->k);
+        maxH = std::max(maxH, x->cfg.H);
+    }
+    if (total > (1LL << 30)) return fail(HF_ERR_SHAPE, "more than 2^30 points in a batch");
+    hf_batch* b = new hf_batch();
+    b->mlp = mlp;
+    b->cfg = c;
+    b->user = (cudaStream_t)cuda_stream;
+    b->total = total;
+    b->kp = hf_batch_kp_for(max_k);
+    b->hc = c.hchunk ? c.hchunk : hf_fuse_chunk_for(maxH);
+    b->nt_a = b->nt_r = c.points_per_cta ? c.points_per_cta : 128;
+    b->heavy_first = c.order == 2 ? 0 : 1;
+    b->sc.resize(n_scenes);
+    int rc = HF_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->t_beg);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->t_end);
+    if (e == cudaSuccess) e = cudaMalloc(&b->ctl, kCtlBytes);
+    if (e == cudaSuccess) e = cudaMemset(b->ctl, 0, kCtlBytes);
+    if (e == cudaSuccess) e = cudaMalloc(&b->args, sizeof(ArgBlock));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->args_h, sizeof(ArgBlock));
+    if (e == cudaSuccess && mlp) {
+        e = cudaMalloc(&b->x, (size_t)total * 64 * sizeof(uint16_t));
+        if (e == cudaSuccess) e = cudaMalloc(&b->prop, (size_t)total * 3 * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&b->h1, (size_t)total * 256 * sizeof(uint16_t));
+        if (e == cudaSuccess) e = cudaMalloc(&b->list, (size_t)total * sizeof(int32_t));
+    }
+    if (e != cudaSuccess) {
+        hair_fuse_batch_destroy(b);
+        return fail(e == cudaErrorMemoryAllocation ? HF_ERR_OOM : HF_ERR_CUDA, cudaGetErrorString(e));
+    }
+    long long off = 0;
+    for (int s = 0; s < n_scenes && rc == HF_OK; ++s) {
+        hf_ctx* x = scenes[s];
+        BatchScene& bs = b->sc[s];
+        bs.c = x;
+        bs.off = off;
+        off += x->N;
+        // per-(point, view) work: hypotheses, refinement candidates, patch members
+        bs.work = (double)x->V * (x->cfg.H + 6.0 * x->cfg.T) * (x->k + 1);
+        const int N = x->N, V = x->V, T = x->cfg.T;
+        const int Hpad = (x->cfg.H + 31) / 32 * 32;   // room for every hypothesis chunk
+        const size_t vn = (size_t)V * N;
+        if (!rc) rc = hf_ensure(x, x->samp, vn * sizeof(float2));
+        if (!rc) rc = hf_ensure(x, x->ab, vn * sizeof(float2));
+        if (!rc) rc = hf_ensure(x, x->qtab, (size_t)V * Hpad * sizeof(float4));
+        if (!rc) rc = hf_ensure(x, x->vthr, (size_t)V * sizeof(float));
+        if (!rc) rc = hf_ensure(x, x->hyps, (size_t)Hpad * 3 * sizeof(float));
+        if (!rc) rc = hf_ensure(x, x->rot, (size_t)(T > 0 ? T : 1) * sizeof(float2));
+        if (!rc) rc = hf_ensure(x, x->best, (size_t)N * 12);
+        if (!rc && cudaStreamSynchronize(x->stream) != cudaSuccess) rc = HF_ERR_CUDA;   // uploads complete
+        if (rc) g_batch_create_err = "scene " + std::to_string(s) + ": " + x->err;
+    }
+    if (rc == HF_OK && mlp && cudaStreamSynchronize(hf_mlp_stream(mlp)) != cudaSuccess) {
+        rc = HF_ERR_CUDA;
+        g_batch_create_err = "proposal network stream";
+    }
+    if (rc != HF_OK) {
+        hair_fuse_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return HF_OK;
+}
+
+extern "C" int hair_fuse_batch_set_outputs(hf_batch* b, int scene, float* dir_out, float* cost_out, int32_t* idx_out,
+                                           uint8_t* status_out) {
+    if (!b) return HF_ERR_INVALID_ARG;
+    if (scene < 0 || scene >= (int)b->sc.size()) return b_err(b, HF_ERR_INVALID_ARG, "scene %d out of range", scene);
+    if (!dir_out) return b_err(b, HF_ERR_INVALID_ARG, "dir_out is required");
+    if (b->mlp && !cost_out) return b_err(b, HF_ERR_INVALID_ARG, "the learned batch needs cost_out (fallback selection)");
+    BatchScene& s = b->sc[scene];
+    s.dir = dir_out;
+    s.cost = cost_out;
+    s.idx = idx_out;
+    s.status = status_out;
+    b->configured = false;
+    drop_graph(b);
+    return HF_OK;
+}
+
+extern "C" int hair_fuse_batch_run(hf_batch* b, int use_graph) {
+    if (!b) return HF_ERR_INVALID_ARG;
+    for (size_t s = 0; s < b->sc.size(); ++s)
+        if (!b->sc[s].dir) return b_err(b, HF_ERR_INVALID_ARG, "scene %d has no outputs set", (int)s);
+    int rc;
+    // order after the caller's stream
+    cudaError_t e = cudaEventRecord(b->ev_in, b->user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_in, 0);
+    if (e != cudaSuccess) return b_cuda(b, e, "order after the caller's stream");
+    if (b->cfg.autotune && !b->tuned) {
+        if ((rc = autotune(b))) return rc;
+    } else if (!b->configured) {
+        if ((rc = configure(b))) return rc;
+    }
+    if (use_graph) {
+        if (!b->gexec) {
+            // one eager run first: function attributes and grid sizes are settled outside capture
+            if ((rc = run_eager(b))) return rc;
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return b_cuda(b, e, "begin capture");
+            cudaError_t e2 = enqueue(b);
+            b->launches -= kernels_per_run(b);   // captured, not run
+            e = cudaStreamEndCapture(b->stream, &g);
+            if (e2 != cudaSuccess || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return b_cuda(b, e2 != cudaSuccess ? e2 : e, "capture batch");
+            }
+            e = cudaGraphInstantiate(&b->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return b_cuda(b, e, "instantiate batch graph");
+        }
+        e = cudaGraphLaunch(b->gexec, b->stream);
+        b->launches += kernels_per_run(b);
+    } else {
+        e = enqueue(b);
+    }
+    if (e != cudaSuccess) return b_cuda(b, e, "launch batch");
+    e = cudaEventRecord(b->ev_out, b->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->user, b->ev_out, 0);
+    if (e != cudaSuccess) return b_cuda(b, e, "order the caller's stream after the batch");
+    return HF_OK;
+}
+
+extern "C" int hair_fuse_batch_sync(hf_batch* b) {
+    if (!b) return HF_ERR_INVALID_ARG;
+    return check_errw(b);
+}
+
+extern "C" int hair_fuse_batch_latency(hf_batch* b, double* ms_out) {
+    if (!b || !ms_out) return HF_ERR_INVALID_ARG;
+    const int ns = (int)b->sc.size();
+    std::vector<unsigned long long> st(2 * HF_MAX_BATCH + 1);
+    cudaError_t e = cudaMemcpyAsync(st.data(), b->ctl + kStampOff, 2 * HF_MAX_BATCH * 8, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st[2 * HF_MAX_BATCH], b->ctl + kT0Off, 8, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b_cuda(b, e, "read completion stamps");
+    const unsigned long long t0 = st[2 * HF_MAX_BATCH];
+    for (int p = 0; p < ns; ++p) {
+        const unsigned long long done = std::max(st[p], st[HF_MAX_BATCH + p]);
+        ms_out[b->pos[p]] = done > t0 ? (double)(done - t0) * 1e-6 : 0.0;
+    }
+    return HF_OK;
+}
+
+extern "C" int hair_fuse_batch_fallbacks(hf_batch* b, int* n_out) {
+    if (!b || !n_out) return HF_ERR_INVALID_ARG;
+    const int ns = (int)b->sc.size();
+    int cnt[HF_MAX_BATCH];
+    cudaError_t e = cudaMemcpyAsync(cnt, b->ctl + kCountOff, sizeof cnt, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b_cuda(b, e, "read fallback counts");
+    for (int p = 0; p < ns; ++p) n_out[b->pos[p]] = b->mlp ? cnt[p] : 0;
+    return HF_OK;
+}
+
+extern "C" int hair_fuse_batch_tuning(const hf_batch* b, int* out4) {
+    if (!b || !out4) return HF_ERR_INVALID_ARG;
+    out4[0] = b->hc;
+    out4[1] = b->nt_a;
+    out4[2] = b->nt_r;
+    out4[3] = b->heavy_first;
+    return HF_OK;
+}
+
+extern "C" int hair_fuse_batch_profile_run(hf_batch* b, hf_kernel_time* out, int max_entries) {
+    if (!b || (!out && max_entries > 0)) return HF_ERR_INVALID_ARG;
+    for (size_t s = 0; s < b->sc.size(); ++s)
+        if (!b->sc[s].dir) return b_err(b, HF_ERR_INVALID_ARG, "scene %d has no outputs set", (int)s);
+    int rc;
+    if (!b->configured && (rc = configure(b))) return rc;
+    cudaEvent_t ev[10];
+    int made = 0;
+    cudaError_t e = cudaSuccess;
+    for (; made < 10 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+    int st[8], n = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = enqueue(b, ev, st, &n);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    int k = 0;
+    if (e == cudaSuccess) {
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, ev[0], ev[1]);
+        if (k < max_entries) {
+            std::snprintf(out[k].name, sizeof out[k].name, "%s", "k_prep_batch");
+            out[k].launches = 1;
+            out[k].total_ms = t;
+        }
+        ++k;
+        for (int q = 0; q < n; ++q, ++k) {
+            cudaEventElapsedTime(&t, ev[1 + q], ev[2 + q]);
+            if (k < max_entries) {
+                std::snprintf(out[k].name, sizeof out[k].name, "%s", kStageName[st[q]]);
+                out[k].launches = st[q] == ST_MLP ? 2 : 1;
+                out[k].total_ms = t;
+            }
+        }
+    }
+    for (int q = 0; q < made; ++q) cudaEventDestroy(ev[q]);
+    if (e != cudaSuccess) return b_cuda(b, e, "profiled batch run");
+    return k;
+}
+
+extern "C" int hair_fuse_batch_stats(hf_batch* b, long long* launches, long long* point_views,
+                                     long long* fallback_point_views) {
+    if (!b) return HF_ERR_INVALID_ARG;
+    if (launches) *launches = b->launches;
+    if (!point_views && !fallback_point_views) return HF_OK;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b_cuda(b, e, "stream synchronize");
+    const int ns = (int)b->sc.size();
+    std::vector<unsigned long long> work(HF_MAX_BATCH);
+    std::vector<int> cnt(HF_MAX_BATCH);
+    e = cudaMemcpy(work.data(), b->ctl + kWorkOff, HF_MAX_BATCH * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(cnt.data(), b->ctl + kCountOff, HF_MAX_BATCH * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return b_cuda(b, e, "read work counters");
+    long long pv = 0, fpv = 0;
+    for (int p = 0; p < ns; ++p) {
+        pv += (long long)work[p];
+        if (!b->mlp || !fallback_point_views || cnt[p] <= 0) continue;
+        // view-set sizes of the fallback points (the argmin left them in the scene's view counts)
+        const BatchScene& s = b->sc[b->pos[p]];
+        const int N = s.c->N;
+        std::vector<int32_t> lst(cnt[p]), nvs(N);
+        e = cudaMemcpy(lst.data(), b->list + s.off, (size_t)cnt[p] * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(nvs.data(), (int32_t*)s.c->best.p + 2 * (size_t)N, (size_t)N * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return b_cuda(b, e, "read fallback view counts");
+        for (int q = 0; q < cnt[p]; ++q) fpv += nvs[lst[q]] > 0 ? nvs[lst[q]] : 0;
+    }
+    if (point_views) *point_views = pv;
+    if (fallback_point_views) *fallback_point_views = fpv;
+    return HF_OK;
+}
+
+extern "C" void hair_fuse_batch_destroy(hf_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    cudaFree(b->ctl);
+    cudaFree(b->args);
+    if (b->args_h) cudaFreeHost(b->args_h);
+    cudaFree(b->x);
+    cudaFree(b->prop);
+    cudaFree(b->h1);
+    cudaFree(b->list);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->t_beg) cudaEventDestroy(b->t_beg);
+    if (b->t_end) cudaEventDestroy(b->t_end);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+extern "C" const char* hair_fuse_batch_last_error(const hf_batch* b) {
+    return b ? b->err.c_str() : g_batch_create_err.c_str();
+}

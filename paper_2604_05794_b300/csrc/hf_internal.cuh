@@ -94,6 +94,7 @@ struct ProjectArgs {
     int top_k;
     float2* samp; float2* ab;
     unsigned long long* work;   // += number of (point, view) pairs in the view sets
+    unsigned* box_keys;         // optional: bounding-box keys lo[3], hi[3] folded in (see hf_launch_bbox_init)
 };
 cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s);
 
@@ -149,15 +150,51 @@ struct FeatArgs {
     const float* pts; int N;
     const float* cams; int V; int W; int H;
     const float* angle; const void* conf; int conf_f16;
-    const float* box;       // bounding box lo[3], hi[3]
+    const float* box;       // bounding box lo[3], hi[3] (used when box_keys is null)
     uint16_t* x;            // [N x 64] bf16 features
+    const unsigned* box_keys;   // bounding box as order-preserving keys lo[3], hi[3], or null
 };
 cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s);
 // cost c_i of a.start_dir and the view count -> a.best_cost, a.nvs (-1 for non-finite points)
 cudaError_t hf_launch_start_cost(const FuseArgs& a, cudaStream_t s);
+struct SelectArgs {
+    const float* cost; const int32_t* nvs; int N; float tau;
+    int32_t* list; int* count;
+};
 // points with a view and cost_out > tau -> list (count must start at 0)
 cudaError_t hf_launch_fallback_select(const float* cost, const int32_t* nvs, int N, float tau, int32_t* list, int* count,
                                       cudaStream_t s);
 // (cos, sin) of alpha0 / 2^t for t < T, in double then rounded
 cudaError_t hf_launch_rot(float2* rot, int T, double alpha0, cudaStream_t s);
 cudaError_t hf_launch_check_nbr(const int32_t* nbr, long long n, int N, uint32_t* errw, cudaStream_t s);
+
+// ------------------------------------------------------------------ batched scenes (hf_batch.cu)
+#define HF_MAX_BATCH HF_MAX_BATCH_SCENES
+
+// Work distribution of one persistent stage over a batch: next = global item counter (zeroed
+// before the launch); with done set, done[p] counts finished tiles of position p and stamp[p]
+// receives the global timer when its last tile finishes.
+struct BatchCtl {
+    unsigned* next;
+    unsigned* done;
+    unsigned long long* stamp;
+    int ns;
+};
+
+// what k_prep_batch does besides the per-scene constants
+struct BatchReset {
+    unsigned* zero; int nzero;              // words cleared (counters)
+    unsigned* box_keys;                     // [ns][6] set to the empty box, or null
+    float2* rot_s; int T_short; double alpha_short;   // short-refinement steps, or null
+    unsigned long long* t0;                 // batch start time, or null
+};
+
+int hf_batch_kp_for(int k);   // patch width instantiated for the batched kernels (4, 9 or 17)
+cudaError_t hf_launch_prep_batch(const PrepArgs* pr, int ns, const BatchReset& r, cudaStream_t s);
+cudaError_t hf_launch_project_batch(const ProjectArgs* pa, const BatchCtl& c, cudaStream_t s);
+cudaError_t hf_launch_features_batch(const FeatArgs* fe, const BatchCtl& c, cudaStream_t s);
+cudaError_t hf_launch_select_batch(const SelectArgs* sa, const BatchCtl& c, cudaStream_t s);
+// nt: points per CTA (64, 128, 256); hc: hypothesis chunk (8, 16, 32; the scenes' Hpad and
+// vblock_q must be built for it); kp from hf_batch_kp_for(max k)
+cudaError_t hf_launch_argmin_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int hc, int nt, cudaStream_t s);
+cudaError_t hf_launch_refine_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int nt, cudaStream_t s);

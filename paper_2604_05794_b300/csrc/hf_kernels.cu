@@ -89,9 +89,34 @@ __device__ __forceinline__ float load_conf(const void* conf, int f16, size_t o) 
 //   ab[v][i]   = (X/Z, Y/Z) when v is in the point's view set, NaN otherwise.
 // The view set is every view the point projects into, or with top_k > 0 the top_k of them by the
 // confidence at the point's own pixel, ties to the lower view index.
+// Order-preserving integer encoding of floats (exact, order-independent min / max by atomics).
+__device__ __forceinline__ unsigned fkey(float x) {
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fval(unsigned k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k); }
+
+constexpr int kProjectThreads = 128;
+
+// With a.box_keys set, the tile also folds its finite coordinates into the point cloud's bounding
+// box (keys lo[3] from 0xffffffff, hi[3] from 0, per coordinate).
 template <bool TOPK>
-__global__ void __launch_bounds__(128) k_project(ProjectArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
+    const int i = blk * kProjectThreads + threadIdx.x;
+    if (a.box_keys) {
+        const bool in = i < a.N;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float x = in ? a.pts[3 * i + q] : 0.0f;
+            const bool f = in && isfinite(x);
+            const unsigned lo = __reduce_min_sync(0xffffffffu, f ? fkey(x) : 0xffffffffu);
+            const unsigned hi = __reduce_max_sync(0xffffffffu, f ? fkey(x) : 0u);
+            if ((threadIdx.x & 31) == 0 && hi != 0u) {
+                atomicMin(a.box_keys + q, lo);
+                atomicMax(a.box_keys + 3 + q, hi);
+            }
+        }
+    }
     if (i >= a.N) return;
     const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
     const size_t npx = (size_t)a.W * a.H;
@@ -153,6 +178,11 @@ __global__ void __launch_bounds__(128) k_project(ProjectArgs a) {
     if ((threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(a.work, (unsigned long long)tot);
 }
 
+template <bool TOPK>
+__global__ void __launch_bounds__(kProjectThreads) k_project(ProjectArgs a) {
+    project_tile<TOPK>(a, blockIdx.x);
+}
+
 // ------------------------------------------------------------------ per-scene constants
 // Built-in hypothesis m of H: Fibonacci lattice on the upper hemisphere (the cost is
 // sign-invariant, Eq. sim), z_m = 1 - (m + 1/2)/H, azimuth m * pi * (3 - sqrt 5).
@@ -174,7 +204,7 @@ __global__ void k_fib(int H, float* out) {
     }
 }
 
-__global__ void k_prep(PrepArgs a) {
+__device__ __forceinline__ void prep_body(const PrepArgs& a) {
     const double kPi = 3.14159265358979323846;
     for (int m = threadIdx.x; m < a.Hpad; m += blockDim.x) {
         const int src = m < a.H ? m : 0;
@@ -215,6 +245,8 @@ __global__ void k_prep(PrepArgs a) {
         a.rot[t] = make_float2((float)cos(al), (float)sin(al));
     }
 }
+
+__global__ void k_prep(PrepArgs a) { prep_body(a); }
 
 // ------------------------------------------------------------------ K2 + K3
 // Patch term of one direction in one view: r = (rx, ry) is Z times the image offset (the scale
@@ -293,17 +325,17 @@ constexpr int kCamStageViews = 256;      // camera rows staged per view block
 // Per-thread ring of S views of patch data: item 0 = the point's (a, b), items 1..KP = the patch
 // samples; laid out [stage][item][thread] so a warp reads consecutive 8-byte words.  View v lives
 // in stage v % S and is copied in S - 1 views ahead of its use.
-template <int KP, int S>
+template <int KP, int S, int NT>
 struct PatchStage {
-    float2 v[S][KP + 1][kFuseThreads];
+    float2 v[S][KP + 1][NT];
 };
 constexpr int kArgminStages = 2;
 constexpr int kRefineStages = 2;
 
 // Queue the copies of one view's patch data into stage st (one commit group per call, also when
 // the thread has nothing to copy, so that group counting stays uniform).
-template <int KP, int S>
-__device__ __forceinline__ void issue_patch(PatchStage<KP, S>& sg, int st, const float2* __restrict__ ab,
+template <int KP, int S, int NT>
+__device__ __forceinline__ void issue_patch(PatchStage<KP, S, NT>& sg, int st, const float2* __restrict__ ab,
                                             const float2* __restrict__ samp, size_t base, int i, const int (&nb)[KP],
                                             bool active) {
     const int t = threadIdx.x;
@@ -317,8 +349,8 @@ __device__ __forceinline__ void issue_patch(PatchStage<KP, S>& sg, int st, const
     cp_async_commit();
 }
 
-template <int KP, int S>
-__device__ __forceinline__ void load_nbrs(const FuseArgs& a, int i, bool active, int (&nb)[KP], PatchStage<KP, S>& sg) {
+template <int KP, int S, int NT>
+__device__ __forceinline__ void load_nbrs(const FuseArgs& a, int i, bool active, int (&nb)[KP], PatchStage<KP, S, NT>& sg) {
     nb[0] = active ? i : -1;
 #pragma unroll
     for (int j = 1; j < KP; ++j) nb[j] = (active && (j - 1) < a.k) ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
@@ -330,8 +362,8 @@ __device__ __forceinline__ void load_nbrs(const FuseArgs& a, int i, bool active,
             for (int st = 0; st < S; ++st) sg.v[st][1 + j][threadIdx.x] = make_float2(0.0f, 0.0f);
 }
 
-template <int KP, int S>
-__device__ __forceinline__ void stage_samples(const PatchStage<KP, S>& sg, int st, f32x2 (&SX)[KP], f32x2 (&SY)[KP]) {
+template <int KP, int S, int NT>
+__device__ __forceinline__ void stage_samples(const PatchStage<KP, S, NT>& sg, int st, f32x2 (&SX)[KP], f32x2 (&SY)[KP]) {
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
         const float2 sj = sg.v[st][1 + j][threadIdx.x];
@@ -343,16 +375,15 @@ __device__ __forceinline__ void stage_samples(const PatchStage<KP, S>& sg, int s
 // K2: cost of every hypothesis and the argmin (lowest index on ties), thread per point.  The
 // hypothesis table of HC hypotheses x a block of views sits in shared memory; the next view's
 // patch data is copied in (cp.async) while the current view is evaluated, two hypotheses at a time.
-template <int HC, int KP>
-__global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+template <int HC, int KP, int NT>
+__device__ __forceinline__ void argmin_tile(const FuseArgs& a, int blk, unsigned char* smem_raw) {
     constexpr int S = kArgminStages;
-    PatchStage<KP, S>& sg = *reinterpret_cast<PatchStage<KP, S>*>(smem_raw);
-    float4* qs = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP, S>));   // [view in block][HC]
+    PatchStage<KP, S, NT>& sg = *reinterpret_cast<PatchStage<KP, S, NT>*>(smem_raw);
+    float4* qs = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP, S, NT>));   // [view in block][HC]
     const int tid = threadIdx.x;
     const int cnt = a.list ? *a.list_count : a.N;
-    if ((int)blockIdx.x * kFuseThreads >= cnt) return;   // whole block past the list: uniform exit
-    const int t_ = blockIdx.x * kFuseThreads + tid;
+    if (blk * NT >= cnt) return;   // whole block past the list: uniform exit
+    const int t_ = blk * NT + tid;
     const int i = t_ < cnt ? (a.list ? a.list[t_] : t_) : -1;
     bool active = i >= 0;
     if (active) {
@@ -363,7 +394,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
         }
     }
     int nb[KP];
-    load_nbrs<KP, S>(a, i, active, nb, sg);
+    load_nbrs<KP, S, NT>(a, i, active, nb, sg);
     float best = INFINITY;
     int bestm = 0, nv = 0;
     for (int c0 = 0; c0 < a.Hpad; c0 += HC) {
@@ -372,17 +403,17 @@ __global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
         for (int m = 0; m < HC; ++m) acc[m] = 0.0f;
         nv = 0;
         for (int p = 0; p < S - 1; ++p)
-            if (p < a.V) issue_patch<KP, S>(sg, p, a.ab, a.samp, (size_t)p * a.N, i, nb, active);
+            if (p < a.V) issue_patch<KP, S, NT>(sg, p, a.ab, a.samp, (size_t)p * a.N, i, nb, active);
             else cp_async_commit();
         for (int vb = 0; vb < a.V; vb += a.vblock_q) {
             const int nvb = min(a.vblock_q, a.V - vb);
             __syncthreads();
-            for (int e = tid; e < nvb * HC; e += kFuseThreads)
+            for (int e = tid; e < nvb * HC; e += NT)
                 qs[e] = a.qtab[(size_t)(vb + e / HC) * a.Hpad + c0 + e % HC];
             __syncthreads();
             for (int v = vb; v < vb + nvb; ++v) {
                 const int vn = v + S - 1;
-                if (vn < a.V) issue_patch<KP, S>(sg, vn % S, a.ab, a.samp, (size_t)vn * a.N, i, nb, active);
+                if (vn < a.V) issue_patch<KP, S, NT>(sg, vn % S, a.ab, a.samp, (size_t)vn * a.N, i, nb, active);
                 else cp_async_commit();
                 cp_async_wait<S - 1>();
                 if (!active) continue;
@@ -391,7 +422,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
                 if (r.x != r.x) continue;
                 ++nv;
                 f32x2 SX[KP], SY[KP];
-                stage_samples<KP, S>(sg, st, SX, SY);
+                stage_samples<KP, S, NT>(sg, st, SX, SY);
                 const f32x2 na = pk(-r.x, -r.x), nb2 = pk(-r.y, -r.y);
                 const float thr = __ldg(a.vthr + v);
                 const float4* q = qs + (v - vb) * HC;
@@ -424,18 +455,23 @@ __global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
     }
 }
 
+template <int HC, int KP>
+__global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    argmin_tile<HC, KP, kFuseThreads>(a, blockIdx.x, smem_raw);
+}
+
 // K3: T rounds of +-alpha rotations about world x, y, z from the argmin; move to the first strictly
 // lowest cost; halve alpha.  The two candidates of one axis are evaluated as a packed pair.
-template <int KP>
-__global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+template <int KP, int NT>
+__device__ __forceinline__ void refine_tile(const FuseArgs& a, int blk, unsigned char* smem_raw) {
     constexpr int S = kRefineStages;
-    PatchStage<KP, S>& sg = *reinterpret_cast<PatchStage<KP, S>*>(smem_raw);
-    float4* cs4 = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP, S>));   // [view in block][3]
+    PatchStage<KP, S, NT>& sg = *reinterpret_cast<PatchStage<KP, S, NT>*>(smem_raw);
+    float4* cs4 = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP, S, NT>));   // [view in block][3]
     const int tid = threadIdx.x;
     const int cnt = a.list ? *a.list_count : a.N;
-    if ((int)blockIdx.x * kFuseThreads >= cnt) return;   // whole block past the list: uniform exit
-    const int t_ = blockIdx.x * kFuseThreads + tid;
+    if (blk * NT >= cnt) return;   // whole block past the list: uniform exit
+    const int t_ = blk * NT + tid;
     const int i = t_ < cnt ? (a.list ? a.list[t_] : t_) : -1;
     const bool inb = i >= 0;
     // From a given start direction (the learned proposal) the view count and the start cost are
@@ -460,7 +496,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
     // points with no view keep their start (all costs are 1)
     const bool active = inb && ((from_start && a.T > 0) ? nv == 0 : nv > 0);
     int nb[KP];
-    load_nbrs<KP, S>(a, i, active, nb, sg);
+    load_nbrs<KP, S, NT>(a, i, active, nb, sg);
     // start: the argmin hypothesis, or a given direction (the learned proposal; index -1)
     const int bestm = from_start ? -1 : ((inb && nv >= 0) ? a.best_idx[i] : 0);
     float best = ((!from_start || a.T == 0) && inb && nv >= 0) ? a.best_cost[i] : 0.0f;
@@ -491,13 +527,13 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
         }
         float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         for (int p = 0; p < S - 1; ++p)
-            if (p < a.V) issue_patch<KP, S>(sg, p, a.ab, a.samp, (size_t)p * a.N, i, nb, active);
+            if (p < a.V) issue_patch<KP, S, NT>(sg, p, a.ab, a.samp, (size_t)p * a.N, i, nb, active);
             else cp_async_commit();
         for (int vb = 0; vb < a.V; vb += a.vblock_c) {
             const int nvb = min(a.vblock_c, a.V - vb);
             if (nblk > 1 || t == 0) {
                 __syncthreads();
-                for (int e = tid; e < nvb; e += kFuseThreads) {
+                for (int e = tid; e < nvb; e += NT) {
                     const float* cam = a.cams + 16 * (vb + e);
                     cs4[3 * e] = make_float4(cam[0], cam[1], cam[4], cam[5]);
                     cs4[3 * e + 1] = make_float4(cam[6], cam[7], cam[8], cam[9]);
@@ -507,7 +543,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
             }
             for (int v = vb; v < vb + nvb; ++v) {
                 const int vn = v + S - 1;
-                if (vn < a.V) issue_patch<KP, S>(sg, vn % S, a.ab, a.samp, (size_t)vn * a.N, i, nb, active);
+                if (vn < a.V) issue_patch<KP, S, NT>(sg, vn % S, a.ab, a.samp, (size_t)vn * a.N, i, nb, active);
                 else cp_async_commit();
                 cp_async_wait<S - 1>();
                 if (!active) continue;
@@ -515,7 +551,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
                 const float2 r = sg.v[st][0][tid];
                 if (r.x != r.x) continue;
                 f32x2 SX[KP], SY[KP];
-                stage_samples<KP, S>(sg, st, SX, SY);
+                stage_samples<KP, S, NT>(sg, st, SX, SY);
                 // staged rows: k0 = (fx, fy, R00, R01), k1 = (R02, R10, R11, R12), k2 = (R20, R21, R22, thr)
                 const bool centre = from_start && t == 0;
                 const float4 k0 = cs4[3 * (v - vb)], k1 = cs4[3 * (v - vb) + 1], k2 = cs4[3 * (v - vb) + 2];
@@ -578,12 +614,20 @@ __global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
     if (a.status_out) a.status_out[i] = a.fell_back ? HF_STATUS_FELL_BACK : (nv ? HF_STATUS_OK : HF_STATUS_NO_VIEWS);
 }
 
+template <int KP>
+__global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    refine_tile<KP, kFuseThreads>(a, blockIdx.x, smem_raw);
+}
+
 // ------------------------------------------------------------------ learned proposal path
 // Features of one point for the proposal network: for the 16 views v_m = floor(m V / 16),
 // (sin 2 theta, cos 2 theta, C) at the point's pixel (zeros when it projects outside), then the
 // position (p - centre) / half_extent of the point cloud's bounding box; bf16, zero-padded to 64.
-__global__ void __launch_bounds__(128) k_features(FeatArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int kFeatThreads = 128;
+
+__device__ __forceinline__ void features_tile(const FeatArgs& a, int blk) {
+    const int i = blk * kFeatThreads + threadIdx.x;
     if (i >= a.N) return;
     const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
     const size_t npx = (size_t)a.W * a.H;
@@ -608,7 +652,9 @@ __global__ void __launch_bounds__(128) k_features(FeatArgs a) {
         f[3 * m + 1] = __bfloat16_as_ushort(__float2bfloat16_rn(c2));
         f[3 * m + 2] = __bfloat16_as_ushort(__float2bfloat16_rn(load_conf(a.conf, a.conf_f16, o)));
     }
-    const float* b = a.box;
+    float b[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) b[q] = a.box_keys ? fval(a.box_keys[q]) : a.box[q];
     float half = 0.5f * fmaxf(fmaxf(b[3] - b[0], b[4] - b[1]), b[5] - b[2]);
     if (!(half > 0.0f)) half = 1.0f;
     const float pc[3] = {p0, p1, p2};
@@ -629,6 +675,8 @@ __global__ void __launch_bounds__(128) k_features(FeatArgs a) {
         dst[q] = w;
     }
 }
+
+__global__ void __launch_bounds__(kFeatThreads) k_features(FeatArgs a) { features_tile(a, blockIdx.x); }
 
 template <int KP>
 __global__ void __launch_bounds__(128) k_start_cost(FuseArgs a) {
@@ -664,18 +712,21 @@ __global__ void __launch_bounds__(128) k_start_cost(FuseArgs a) {
     a.nvs[i] = nv;
 }
 
-__global__ void k_fallback_select(const float* __restrict__ cost, const int32_t* __restrict__ nvs, int N, float tau,
-                                  int32_t* list, int* count) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool want = i < N && nvs[i] > 0 && cost[i] > tau;
+constexpr int kSelectThreads = 256;
+
+__device__ __forceinline__ void select_tile(const SelectArgs& a, int blk) {
+    const int i = blk * kSelectThreads + threadIdx.x;
+    const bool want = i < a.N && a.nvs[i] > 0 && a.cost[i] > a.tau;
     const unsigned m = __ballot_sync(0xffffffffu, want);
     if (!m) return;
     const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
     int base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(m));
+    if (lane == leader) base = atomicAdd(a.count, __popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (want) list[base + __popc(m & ((1u << lane) - 1u))] = i;
+    if (want) a.list[base + __popc(m & ((1u << lane) - 1u))] = i;
 }
+
+__global__ void __launch_bounds__(kSelectThreads) k_fallback_select(SelectArgs a) { select_tile(a, blockIdx.x); }
 
 __global__ void k_rot(float2* rot, int T, double alpha0) {
     const int t = threadIdx.x;
@@ -729,6 +780,173 @@ __global__ void k_check_nbr(const int32_t* __restrict__ nbr, long long n, int N,
     }
 }
 
+// ------------------------------------------------------------------ batched scenes
+// One persistent grid per stage walks the (scene, tile) items of every scene of a batch, scenes in
+// the order of the argument array: a CTA takes the next item from a global counter, copies that
+// scene's arguments to shared memory when the scene changes, and runs the single-scene tile body,
+// so a batched result is bit-identical to the scene run alone.  With c.done set, the CTA that
+// finishes a scene's last tile stamps the global timer (per-scene completion time).
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int NT, typename Args, typename Count, typename Body>
+__device__ __forceinline__ void batch_tiles(const Args* __restrict__ args, const BatchCtl& c, Count count, Body body) {
+    __shared__ Args sa;
+    __shared__ int pref[HF_MAX_BATCH + 1];
+    __shared__ int s_item, s_pos, s_cur;
+    if (threadIdx.x == 0) {
+        pref[0] = 0;
+        for (int p = 0; p < c.ns; ++p) pref[p + 1] = pref[p] + (count(args[p]) + NT - 1) / NT;
+        s_cur = -1;
+    }
+    for (;;) {
+        __syncthreads();   // the previous item is done with shared memory
+        if (threadIdx.x == 0) {
+            const int t = (int)atomicAdd(c.next, 1u);
+            int p = 0;
+            while (p < c.ns - 1 && t >= pref[p + 1]) ++p;
+            s_item = t;
+            s_pos = p;
+            if (t < pref[c.ns] && p != s_cur) {
+                sa = args[p];
+                s_cur = p;
+            }
+        }
+        __syncthreads();
+        const int t = s_item, p = s_pos;
+        if (t >= pref[c.ns]) break;
+        body(sa, t - pref[p]);
+        if (c.done) {
+            __syncthreads();   // every thread's outputs of the tile are written
+            if (threadIdx.x == 0) {
+                __threadfence();
+                if ((int)atomicAdd(c.done + p, 1u) + 1 == pref[p + 1] - pref[p]) c.stamp[p] = gtimer();
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int fuse_count(const FuseArgs& a) { return a.list ? *a.list_count : a.N; }
+
+template <int HC, int KP, int NT>
+__global__ void __launch_bounds__(NT) k_argmin_batch(const FuseArgs* __restrict__ fa, BatchCtl c) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    batch_tiles<NT>(fa, c, [](const FuseArgs& a) { return fuse_count(a); }, [&](const FuseArgs& a, int blk) { argmin_tile<HC, KP, NT>(a, blk, smem_raw); });
+}
+
+template <int KP, int NT>
+__global__ void __launch_bounds__(NT) k_refine_batch(const FuseArgs* __restrict__ fa, BatchCtl c) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    batch_tiles<NT>(fa, c, [](const FuseArgs& a) { return fuse_count(a); }, [&](const FuseArgs& a, int blk) { refine_tile<KP, NT>(a, blk, smem_raw); });
+}
+
+__global__ void __launch_bounds__(kProjectThreads) k_project_batch(const ProjectArgs* __restrict__ pa, BatchCtl c) {
+    batch_tiles<kProjectThreads>(pa, c, [](const ProjectArgs& a) { return a.N; }, [](const ProjectArgs& a, int blk) {
+        if (a.top_k > 0) project_tile<true>(a, blk);
+        else project_tile<false>(a, blk);
+    });
+}
+
+__global__ void __launch_bounds__(kFeatThreads) k_features_batch(const FeatArgs* __restrict__ fe, BatchCtl c) {
+    batch_tiles<kFeatThreads>(fe, c, [](const FeatArgs& a) { return a.N; },
+                              [](const FeatArgs& a, int blk) { features_tile(a, blk); });
+}
+
+__global__ void __launch_bounds__(kSelectThreads) k_select_batch(const SelectArgs* __restrict__ sa, BatchCtl c) {
+    batch_tiles<kSelectThreads>(sa, c, [](const SelectArgs& a) { return a.N; },
+                                [](const SelectArgs& a, int blk) { select_tile(a, blk); });
+}
+
+// Per-scene constants of every scene (block = scene), the batch's counters cleared, empty bounding
+// boxes, the short-refinement rotation steps, and the batch start time.
+__global__ void k_prep_batch(const PrepArgs* __restrict__ pr, BatchReset r) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && r.t0) *r.t0 = gtimer();
+    prep_body(pr[blockIdx.x]);
+    if (r.box_keys && threadIdx.x < 6) r.box_keys[6 * blockIdx.x + threadIdx.x] = threadIdx.x < 3 ? 0xffffffffu : 0u;
+    if (blockIdx.x == 0) {
+        for (int w = threadIdx.x; w < r.nzero; w += blockDim.x) r.zero[w] = 0u;
+        if (r.rot_s && (int)threadIdx.x < r.T_short) {
+            const double al = r.alpha_short / (double)(1u << threadIdx.x);
+            r.rot_s[threadIdx.x] = make_float2((float)cos(al), (float)sin(al));
+        }
+    }
+}
+
+// persistent grid: resident CTAs per SM x SMs (cached per kernel and shared-memory size)
+template <typename K>
+int persistent_grid(K kernel, int threads, size_t smem) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) per = 1;
+    return per * sms;
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t smem, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return cudaSuccess;   // set by the eager launch before capture
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int HC, int KP, int NT>
+cudaError_t launch_argmin_batch(const FuseArgs* fa, const BatchCtl& c, cudaStream_t s) {
+    const size_t sm = sizeof(PatchStage<KP, kArgminStages, NT>) + kQStageBytes;
+    cudaError_t e = set_smem(k_argmin_batch<HC, KP, NT>, sm, s);
+    if (e != cudaSuccess) return e;
+    static int grid = 0;
+    if (!grid) grid = persistent_grid(k_argmin_batch<HC, KP, NT>, NT, sm);
+    k_argmin_batch<HC, KP, NT><<<grid, NT, sm, s>>>(fa, c);
+    return cudaGetLastError();
+}
+
+template <int KP, int NT>
+cudaError_t launch_refine_batch(const FuseArgs* fa, const BatchCtl& c, cudaStream_t s) {
+    const size_t sm = sizeof(PatchStage<KP, kRefineStages, NT>) + (size_t)kCamStageViews * 3 * sizeof(float4);
+    cudaError_t e = set_smem(k_refine_batch<KP, NT>, sm, s);
+    if (e != cudaSuccess) return e;
+    static int grid = 0;
+    if (!grid) grid = persistent_grid(k_refine_batch<KP, NT>, NT, sm);
+    k_refine_batch<KP, NT><<<grid, NT, sm, s>>>(fa, c);
+    return cudaGetLastError();
+}
+
+template <int HC, int KP>
+cudaError_t launch_argmin_batch_nt(const FuseArgs* fa, const BatchCtl& c, int nt, cudaStream_t s) {
+    switch (nt) {
+        case 64: return launch_argmin_batch<HC, KP, 64>(fa, c, s);
+        case 256: return launch_argmin_batch<HC, KP, 256>(fa, c, s);
+        default: return launch_argmin_batch<HC, KP, 128>(fa, c, s);
+    }
+}
+
+template <int HC>
+cudaError_t launch_argmin_batch_kp(const FuseArgs* fa, const BatchCtl& c, int kp, int nt, cudaStream_t s) {
+    switch (kp) {
+        case 4: return launch_argmin_batch_nt<HC, 4>(fa, c, nt, s);
+        case 9: return launch_argmin_batch_nt<HC, 9>(fa, c, nt, s);
+        default: return launch_argmin_batch_nt<HC, 17>(fa, c, nt, s);
+    }
+}
+
+template <int KP>
+cudaError_t launch_refine_batch_nt(const FuseArgs* fa, const BatchCtl& c, int nt, cudaStream_t s) {
+    switch (nt) {
+        case 64: return launch_refine_batch<KP, 64>(fa, c, s);
+        case 256: return launch_refine_batch<KP, 256>(fa, c, s);
+        default: return launch_refine_batch<KP, 128>(fa, c, s);
+    }
+}
+
 // patch width (k + 1) rounded up to an instantiated size
 int kp_for(int k) {
     const int need = k + 1;
@@ -749,13 +967,13 @@ cudaError_t launch_fuse_kp(const FuseArgs& a, int stage, cudaStream_t s) {
     cudaStreamIsCapturing(s, &cs);
     const bool set_attr = cs == cudaStreamCaptureStatusNone;   // set outside capture only
     if (stage == 1) {
-        const size_t sm = sizeof(PatchStage<KP, kArgminStages>) + (size_t)a.vblock_q * HC * sizeof(float4);
+        const size_t sm = sizeof(PatchStage<KP, kArgminStages, kFuseThreads>) + (size_t)a.vblock_q * HC * sizeof(float4);
         cudaError_t e = set_attr ? cudaFuncSetAttribute(k_argmin<HC, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
                                  : cudaSuccess;
         if (e != cudaSuccess) return e;
         k_argmin<HC, KP><<<grid, block, sm, s>>>(a);
     } else {
-        const size_t sm = sizeof(PatchStage<KP, kRefineStages>) + (size_t)a.vblock_c * 3 * sizeof(float4);
+        const size_t sm = sizeof(PatchStage<KP, kRefineStages, kFuseThreads>) + (size_t)a.vblock_c * 3 * sizeof(float4);
         cudaError_t e = set_attr ? cudaFuncSetAttribute(k_refine<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
                                  : cudaSuccess;
         if (e != cudaSuccess) return e;
@@ -785,7 +1003,7 @@ int hf_fuse_chunk_for(int H) {
 }
 
 cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s) {
-    const dim3 grid((a.N + 127) / 128), block(128);
+    const dim3 grid((a.N + kProjectThreads - 1) / kProjectThreads), block(kProjectThreads);
     if (a.top_k > 0) k_project<true><<<grid, block, 0, s>>>(a);
     else k_project<false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
@@ -837,7 +1055,7 @@ cudaError_t hf_launch_fib(int H, float* out, cudaStream_t s) {
 }
 
 cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s) {
-    k_features<<<(a.N + 127) / 128, 128, 0, s>>>(a);
+    k_features<<<(a.N + kFeatThreads - 1) / kFeatThreads, kFeatThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -856,7 +1074,8 @@ cudaError_t hf_launch_start_cost(const FuseArgs& a, cudaStream_t s) {
 
 cudaError_t hf_launch_fallback_select(const float* cost, const int32_t* nvs, int N, float tau, int32_t* list, int* count,
                                       cudaStream_t s) {
-    k_fallback_select<<<(N + 255) / 256, 256, 0, s>>>(cost, nvs, N, tau, list, count);
+    const SelectArgs a{cost, nvs, N, tau, list, count};
+    k_fallback_select<<<(N + kSelectThreads - 1) / kSelectThreads, kSelectThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -871,4 +1090,49 @@ cudaError_t hf_launch_check_nbr(const int32_t* nbr, long long n, int N, uint32_t
     const long long blocks = (n + 255) / 256;
     k_check_nbr<<<(unsigned)(blocks < 1184 ? blocks : 1184), 256, 0, s>>>(nbr, n, N, errw);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ batched launchers
+int hf_batch_kp_for(int k) { return k + 1 <= 4 ? 4 : (k + 1 <= 9 ? 9 : 17); }
+
+cudaError_t hf_launch_prep_batch(const PrepArgs* pr, int ns, const BatchReset& r, cudaStream_t s) {
+    k_prep_batch<<<ns, 256, 0, s>>>(pr, r);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_project_batch(const ProjectArgs* pa, const BatchCtl& c, cudaStream_t s) {
+    static int grid = 0;
+    if (!grid) grid = persistent_grid(k_project_batch, kProjectThreads, 0);
+    k_project_batch<<<grid, kProjectThreads, 0, s>>>(pa, c);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_features_batch(const FeatArgs* fe, const BatchCtl& c, cudaStream_t s) {
+    static int grid = 0;
+    if (!grid) grid = persistent_grid(k_features_batch, kFeatThreads, 0);
+    k_features_batch<<<grid, kFeatThreads, 0, s>>>(fe, c);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_select_batch(const SelectArgs* sa, const BatchCtl& c, cudaStream_t s) {
+    static int grid = 0;
+    if (!grid) grid = persistent_grid(k_select_batch, kSelectThreads, 0);
+    k_select_batch<<<grid, kSelectThreads, 0, s>>>(sa, c);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_argmin_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int hc, int nt, cudaStream_t s) {
+    switch (hc) {
+        case 8: return launch_argmin_batch_kp<8>(fa, c, kp, nt, s);
+        case 16: return launch_argmin_batch_kp<16>(fa, c, kp, nt, s);
+        default: return launch_argmin_batch_kp<32>(fa, c, kp, nt, s);
+    }
+}
+
+cudaError_t hf_launch_refine_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int nt, cudaStream_t s) {
+    switch (kp) {
+        case 4: return launch_refine_batch_nt<4>(fa, c, nt, s);
+        case 9: return launch_refine_batch_nt<9>(fa, c, nt, s);
+        default: return launch_refine_batch_nt<17>(fa, c, nt, s);
+    }
 }

@@ -247,6 +247,11 @@ cudaError_t hf_launch_pack(const float* P, const MlpDev& d, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t hf_launch_bbox_init(unsigned* keys, cudaStream_t s) {
+    k_bbox_init<<<1, 32, 0, s>>>(keys);
+    return cudaGetLastError();
+}
+
 cudaError_t hf_launch_bbox(const float* pts, int N, float* box, cudaStream_t s) {
     unsigned* keys = reinterpret_cast<unsigned*>(box + 8);   // 6 keys after the 6 (+2 spare) box floats
     k_bbox_init<<<1, 32, 0, s>>>(keys);

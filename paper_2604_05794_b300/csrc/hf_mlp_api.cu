@@ -477,21 +477,23 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
 
     PrepArgs pr{(const float*)c->cams.p, V, nullptr, H, Hpad, T, (float*)c->hyps.p, (float4*)c->qtab.p,
                 (float*)c->vthr.p, (float2*)c->rot.p, (uint32_t*)c->errw.p};
-    if ((rc = run_launch(c, "k_prep", [&] { return hf_launch_prep(pr, s); }))) return rc;
+    unsigned* box_keys = reinterpret_cast<unsigned*>(box + 8);
+    if ((rc = run_launch(c, "k_prep", [&] {
+             cudaError_t e2 = hf_launch_prep(pr, s);
+             return e2 != cudaSuccess ? e2 : hf_launch_bbox_init(box_keys, s);
+         })))
+        return rc;
     cudaError_t e = cudaMemsetAsync(c->work.p, 0, 8, s);
     if (e != cudaSuccess) return hf_cuda_err(c, e, "clear work counter");
+    // the projection also folds the points into the bounding box the features are normalised by
     ProjectArgs pa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p,
                    c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, c->cfg.top_k_views, (float2*)c->samp.p, (float2*)c->ab.p,
-                   (unsigned long long*)c->work.p};
+                   (unsigned long long*)c->work.p, box_keys};
     if ((rc = run_launch(c, "k_project", [&] { return hf_launch_project(pa, s); }))) return rc;
     // proposal: features -> network
     FeatArgs fa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p, c->conf.p,
-                c->conf_dtype == HF_F16 ? 1 : 0, box, (uint16_t*)c->feat.p};
-    if ((rc = run_launch(c, "k_features", [&] {
-             cudaError_t e2 = hf_launch_bbox((const float*)c->pts.p, N, box, s);
-             return e2 != cudaSuccess ? e2 : hf_launch_features(fa, s);
-         })))
-        return rc;
+                c->conf_dtype == HF_F16 ? 1 : 0, nullptr, (uint16_t*)c->feat.p, box_keys};
+    if ((rc = run_launch(c, "k_features", [&] { return hf_launch_features(fa, s); }))) return rc;
     if ((rc = run_launch(c, "k_mlp", [&] {
              return hf_mlp_infer(m->d, m->P, (const uint16_t*)c->feat.p, N, m->h1, (float*)c->prop.p,
                                  (uint32_t*)c->errw.p, s);
@@ -540,3 +542,11 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     if (mem_kind == HF_HOST || n_fallback) return hair_fuse_sync(c);
     return HF_OK;
 }
+
+cudaError_t hf_mlp_infer_rows(hf_mlp* m, const uint16_t* x, long long n, uint16_t* h1, float* dir_out, uint32_t* errw,
+                              cudaStream_t s) {
+    if (n <= 0 || n > 0x7fffffffLL) return cudaErrorInvalidValue;
+    return hf_mlp_infer(m->d, m->P, x, (int)n, h1, dir_out, errw, s);
+}
+
+cudaStream_t hf_mlp_stream(hf_mlp* m) { return m->stream; }

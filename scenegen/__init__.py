@@ -121,6 +121,25 @@ def _cstruct(cfg):
     return c
 
 
+def serving_batch(first_seed=200, n=16):
+    """Scene configurations of an uneven serving batch (keyword arguments of make_scene): scene s
+    draws, from its own seed, N log-uniform in [50k, 1M] (strands of 50 segments, one point per
+    segment), V uniform in {16, ..., 64} and maps from {512x512, 1024x1024, 1920x1080} (focal length
+    scaled with the width so the field of view stays that of the full preset; fp16 confidence at
+    1920x1080); otherwise the full preset (orbit, 0.5 deg pose noise, H = 64, k = 8, T = 8)."""
+    import math
+    sizes = [(512, 512), (1024, 1024), (1920, 1080)]
+    out = []
+    for s in range(first_seed, first_seed + n):
+        rng = np.random.default_rng(s)
+        N = math.exp(rng.uniform(math.log(5e4), math.log(1e6)))
+        V = int(rng.integers(16, 65))
+        W, H = sizes[int(rng.integers(0, 3))]
+        out.append(dict(preset="full", seed=s, n_strands=max(1, int(round(N / 50))), V=V, width=W, height=H,
+                        f=1300.0 * W / 1920.0, conf_f16=(W == 1920)))
+    return out
+
+
 def make_scene(preset="tiny", seed=None, exact_maps=False, strand_maps=True, knn=True, **over):
     """Generate one scene.  Returns a dict of numpy arrays and sizes:
 

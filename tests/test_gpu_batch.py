@@ -1,0 +1,170 @@
+"""Batched serving: several scenes of uneven size fused in one submission give, scene by scene,
+exactly the results of the same scene fused alone (plain and learned paths), whatever launch shape
+the batch runs with, eagerly or as a replayed CUDA graph; spot checks against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.mlp as om
+import scenegen
+from helpers import compare
+
+pytestmark = pytest.mark.gpu
+
+
+def _scenes():
+    """Four small scenes that differ in point count, views, map size and dtype, k, H, T, top-K."""
+    return [
+        (scenegen.make_scene("tiny"), dict(H=32, T=4, top_k=0)),
+        (scenegen.make_scene("mid", seed=11, n_strands=150, width=512, height=512, f=600.0), dict(H=64, T=8, top_k=0)),
+        (scenegen.make_scene("full", seed=12, n_strands=120, V=16, width=640, height=360, f=433.0),
+         dict(H=48, T=6, top_k=5)),
+        (scenegen.make_scene("mid", seed=13, n_strands=40, V=24, width=512, height=512, f=600.0),
+         dict(H=64, T=8, top_k=0)),
+    ]
+
+
+@pytest.fixture(scope="module")
+def scenes():
+    return _scenes()
+
+
+def _ctx(sc, o):
+    import paper_2604_05794_b300 as hf
+    f = hf.HairFuse(o["H"], sc["k"], o["T"], top_k_views=o["top_k"])
+    f.upload_views(sc["cams"], sc["angle"], sc["conf"])
+    f.upload_points(sc["points"], sc["nbr"])
+    return f
+
+
+def _outs(N):
+    import torch
+    return (torch.empty((N, 3), device="cuda"), torch.empty(N, device="cuda"),
+            torch.empty(N, dtype=torch.int32, device="cuda"), torch.empty(N, dtype=torch.uint8, device="cuda"))
+
+
+def _host(o):
+    return [x.cpu().numpy() for x in o]
+
+
+def _alone_plain(ctxs, scenes):
+    res = []
+    for f, (sc, _) in zip(ctxs, scenes):
+        o = _outs(sc["N"])
+        f.fuse(*o)
+        f.sync()
+        res.append(_host(o))
+    return res
+
+
+def _equal(a, b):
+    for x, y in zip(a, b):
+        assert x.dtype == y.dtype and np.array_equal(x.view(np.uint8), y.view(np.uint8))
+
+
+@pytest.mark.parametrize("shape", [dict(autotune=True), dict(autotune=False, hchunk=8, points_per_cta=64, order=2),
+                                   dict(autotune=False, hchunk=16, points_per_cta=256, order=1),
+                                   dict(autotune=False, hchunk=32, points_per_cta=128, order=0)])
+def test_plain_batch_equals_alone(scenes, shape):
+    import torch
+
+    import paper_2604_05794_b300 as hf
+    ctxs = [_ctx(sc, o) for sc, o in scenes]
+    want = _alone_plain(ctxs, scenes)
+    outs = [_outs(sc["N"]) for sc, _ in scenes]
+    with hf.Batch(ctxs, **shape) as b:
+        for s, o in enumerate(outs):
+            b.set_outputs(s, *o)
+        for use_graph in (False, True, True):
+            for o in outs:
+                for x in o:
+                    x.zero_()
+            b.run(use_graph=use_graph)
+            b.sync()
+            for s in range(len(scenes)):
+                _equal(_host(outs[s]), want[s])
+        lat = b.latency_ms()
+        assert np.all(lat > 0) and np.all(np.isfinite(lat))
+        assert np.all(b.fallbacks() == 0)
+        t = b.tuning()
+        assert t["hchunk"] in (8, 16, 32) and t["points_per_cta_argmin"] in (64, 128, 256)
+        if not shape["autotune"]:
+            assert t["hchunk"] == shape["hchunk"] and t["points_per_cta_refine"] == shape["points_per_cta"]
+    torch.cuda.synchronize()
+    for f in ctxs:
+        f.close()
+
+
+def test_learned_batch_equals_alone(scenes):
+    import paper_2604_05794_b300 as hf
+    net = hf.ProposalNet(1024)
+    net.set_params(om.init(5).astype(np.float32))
+    Ts, al, tau = 2, 0.05, 0.3
+    ctxs = [_ctx(sc, o) for sc, o in scenes]
+    want, nf_want = [], []
+    for f, (sc, _) in zip(ctxs, scenes):
+        o = _outs(sc["N"])
+        nf_want.append(f.fuse_learned(net, *o, T_short=Ts, alpha_short=al, tau=tau))
+        want.append(_host(o))
+    assert sum(nf_want) > 0 and sum(nf_want) < sum(sc["N"] for sc, _ in scenes)
+    outs = [_outs(sc["N"]) for sc, _ in scenes]
+    with hf.Batch(ctxs, net=net, T_short=Ts, alpha_short=al, tau=tau, autotune=True) as b:
+        for s, o in enumerate(outs):
+            b.set_outputs(s, *o)
+        for use_graph in (False, True, True):
+            for o in outs:
+                for x in o:
+                    x.zero_()
+            b.run(use_graph=use_graph)
+            b.sync()
+            for s in range(len(scenes)):
+                _equal(_host(outs[s]), want[s])
+            assert list(b.fallbacks()) == nf_want
+        assert np.all(b.latency_ms() > 0)
+    for f in ctxs:
+        f.close()
+
+
+def test_batch_matches_oracle_sample(scenes):
+    """A sample of the batched plain result of every scene against the FP64 oracle."""
+    import paper_2604_05794_b300 as hf
+    ctxs = [_ctx(sc, o) for sc, o in scenes]
+    outs = [_outs(sc["N"]) for sc, _ in scenes]
+    with hf.Batch(ctxs, autotune=False) as b:
+        for s, o in enumerate(outs):
+            b.set_outputs(s, *o)
+        b.run(use_graph=True)
+        b.sync()
+        for s, (sc, o) in enumerate(scenes):
+            osc = oracle.Scene.from_dict(sc)
+            sel = np.linspace(0, sc["N"] - 1, 60).astype(np.int64)
+            hyps = hf.fibonacci_hemisphere(o["H"])
+            orc = oracle.fuse(osc, hyps, o["T"], idx=sel, top_k=o["top_k"])
+            d, c, i, st = _host(outs[s])
+            compare(dict(dir=d, cost=c, idx=i, status=st), orc, sel, osc, hyps, o["H"], top_k=o["top_k"],
+                    strict_frac=0.95)
+    for f in ctxs:
+        f.close()
+
+
+def test_batch_rejects_bad_arguments(scenes):
+    import paper_2604_05794_b300 as hf
+    sc, o = scenes[0]
+    f = _ctx(sc, o)
+    with pytest.raises(hf.HairFuseError):
+        hf.Batch([])
+    with pytest.raises(hf.HairFuseError):
+        hf.Batch([f, f])
+    empty = hf.HairFuse(32, 5, 4)
+    with pytest.raises(hf.HairFuseError):
+        hf.Batch([f, empty])
+    net = hf.ProposalNet(1024)
+    with pytest.raises(hf.HairFuseError):
+        hf.Batch([f], net=net, T_short=0)
+    with hf.Batch([f]) as b:
+        with pytest.raises(hf.HairFuseError):
+            b.run()   # outputs not set
+        with pytest.raises(hf.HairFuseError):
+            b.set_outputs(3, *_outs(sc["N"]))
+    empty.close()
+    f.close()
