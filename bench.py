@@ -1,11 +1,21 @@
 """Benchmark of the multi-view hair direction fusion on B300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload full|mid|tiny]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload serving16|full|mid|tiny]
 
-One step = one pass of the whole fusion path (per-scene constants, projection + gather, cost of
-every hypothesis, argmin, refinement) over every point of a resident synthetic scene shaped like the
-paper's outer point clouds (default: 1,000,000 points, 64 views of 1920x1080, H = 64, k = 8, T = 8).
-Rank 0 prints one JSON line.  Under torchrun each rank fuses its own scene (independent problems,
+Default workload (serving16): the learned + batched form against the plain form on an uneven batch
+of 16 synthetic scenes (50k-1M points, 16-64 views, 512x512 to 1920x1080 maps, H = 64, k = 8,
+T = 8).  One step = one fusion of every point of every scene: for the learned + batched form, one
+replay of the batch's CUDA graph (per-stage persistent launches over all scenes: constants,
+projection + gather, features, proposal network, short refinement, fallback selection, argmin and
+refinement of the fallback points); for the plain form, the plain fusion of the scenes one after
+another.  The proposal network is trained on the GPU first (library kernels, four scenes shaped like
+the full workload) and its fallback threshold calibrated on a training scene.
+
+--workload full|mid|tiny: the plain fusion of one resident scene (full: 1,000,000 points, 64 views
+of 1920x1080).
+
+Rank 0 prints one JSON line.  Under torchrun each rank fuses its own scenes (independent problems,
 weak scaling, no data-path collective); timing is the max over ranks.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
@@ -26,6 +36,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fused points/s at median angle err ≤2° vs FP64 oracle; learned+batched vs plain"
 WORKLOADS = {
+    "serving16": "batched serving: 16 scenes (seeds 200-215), points log-uniform in [50k, 1M], views uniform in "
+                 "{16..64}, maps from {512x512, 1024x1024, 1920x1080}, full-preset geometry (orbit, 0.5 deg pose "
+                 "noise), H=64, k=8, T=8; learned proposal (trained on 4 full-like scenes, 2M samples, 20k Adam "
+                 "steps, batch 8192, lr 1e-3) + 2 refinement rounds + plain fallback, against the plain fusion "
+                 "of the scenes one by one",
     "full": "plain fusion, full: 1,000,000 points (20,000 strands x 50 segments), 64 views 1920x1080, "
             "f32 angle + fp16 confidence, 0.5 deg pose noise, H=64, k=8, T=8",
     "mid": "plain fusion, mid: 200,000 points, 32 views 1024x1024 with 10% outlier pixels, H=64, k=8, T=8",
@@ -51,10 +66,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="full", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="serving16", choices=list(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--accuracy-sample", type=int, default=400)
+    ap.add_argument("--accuracy-sample", type=int, default=0,
+                    help="oracle sample for the accuracy check (default 400 points; 50,000 across the serving batch)")
     return ap.parse_args()
 
 
@@ -165,27 +181,38 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    sc = make_workload(args.workload)
-    H, T = sc["cfg"]["H"], sc["cfg"]["T"]
-    osc = oracle.Scene.from_dict(sc)
-    hyps = oracle.fibonacci_hemisphere(H)
+    scenes = serving_scenes(200) if args.workload == "serving16" else [make_workload(args.workload)]
+    osc = [oracle.Scene.from_dict(sc) for sc in scenes]
+    hyps = {sc["cfg"]["H"]: oracle.fibonacci_hemisphere(sc["cfg"]["H"]) for sc in scenes}
+    Ntot = sum(sc["N"] for sc in scenes)
+
+    def fuse_sample(n_total):
+        """The oracle's plain fusion of about n_total points spread over the scenes in proportion
+        to their point counts (evenly spaced in each); returns the number fused."""
+        n = 0
+        for o, sc in zip(osc, scenes):
+            m = max(1, int(n_total * sc["N"] / Ntot))
+            oracle.fuse(o, hyps[sc["cfg"]["H"]], sc["cfg"]["T"], idx=np.linspace(0, sc["N"] - 1, m).astype(np.int64))
+            n += m
+        return n
+
+    fuse_sample(64)                                      # thread start-up
+    t0 = time.perf_counter()
+    n_probe = fuse_sample(512)
+    per_pt = (time.perf_counter() - t0) / n_probe
     # bounded sample per step so that warmup + steps finish within a few minutes
-    probe = np.arange(0, sc["N"], max(1, sc["N"] // 512))
-    oracle.fuse(osc, hyps, T, idx=probe[:64])             # thread start-up
-    t0 = time.perf_counter()
-    oracle.fuse(osc, hyps, T, idx=probe)
-    per_pt = (time.perf_counter() - t0) / len(probe)
     budget = 90.0 / max(1, args.steps + args.warmup)
-    n = int(min(sc["N"], max(64, budget / max(per_pt, 1e-9))))
-    sel = np.linspace(0, sc["N"] - 1, n).astype(np.int64)
+    n = int(min(Ntot, max(64, budget / max(per_pt, 1e-9))))
     for _ in range(args.warmup):
-        oracle.fuse(osc, hyps, T, idx=sel[: max(1, n // 8)])
+        fuse_sample(max(1, n // 8))
     t0 = time.perf_counter()
+    done = 0
     for _ in range(args.steps):
-        oracle.fuse(osc, hyps, T, idx=sel)
+        done += fuse_sample(n)
     dt = time.perf_counter() - t0
-    value = n * args.steps / dt
-    sample = f"{n} of {sc['N']} points per step, evenly spaced; FP64 C + OpenMP"
+    value = done / dt
+    sample = (f"{done // max(1, args.steps)} of {Ntot} points per step, spread over {len(scenes)} scene(s) in "
+              "proportion to their point counts, evenly spaced; FP64 C + OpenMP, plain fusion")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -299,7 +326,7 @@ def run_ours(args):
             "clocks": clk}
 
     if rank == 0:
-        line["accuracy"] = accuracy(sc, Hh, T, out_dir.cpu().numpy(), args.accuracy_sample)
+        line["accuracy"] = accuracy(sc, Hh, T, out_dir.cpu().numpy(), args.accuracy_sample or 400)
     # end to end through the C ABI with pinned host buffers, copies inside the timed region
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(a).pin_memory()
@@ -343,10 +370,341 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------- serving workload
+SERVING_T_SHORT, SERVING_ALPHA = 2, 0.08   # short refinement from the proposal
+TRAIN_SEEDS, TRAIN_SAMPLES, TRAIN_STEPS, TRAIN_BATCH, TRAIN_LR = (100, 101, 102, 103), 500_000, 20000, 8192, 1e-3
+MLP_FLOP_PER_POINT = 2 * (51 * 256 + 256 * 256 + 256 * 3)   # forward, unpadded inputs
+
+
+def serving_scenes(first_seed):
+    import scenegen
+    return [scenegen.make_scene(**c) for c in scenegen.serving_batch(first_seed)]
+
+
+def train_proposal(dev, seed_offset):
+    """Proposal network trained on the GPU by the library (targets: the plain GPU fusion of four
+    full-like scenes), fallback threshold calibrated on the first of them."""
+    import torch
+
+    import scenegen
+    from paper_2604_05794_b300 import learned as L
+    t0 = time.perf_counter()
+    seeds = [s + seed_offset for s in TRAIN_SEEDS]
+    X, Tg = L.training_set(lambda s: scenegen.make_scene("full", seed=s), seeds, TRAIN_SAMPLES, 64, 8, dev)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    net, losses = L.train(X, Tg, steps=TRAIN_STEPS, batch=TRAIN_BATCH, lr=TRAIN_LR)
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    n_samples = int(X.shape[0])
+    del X, Tg
+    cal = scenegen.make_scene("full", seed=seeds[0])
+    tau, info = L.calibrate_tau(cal, net, 64, 8, SERVING_T_SHORT, SERVING_ALPHA, dev, median_deg=1.8, p95_deg=7.5)
+    return net, tau, {"samples": n_samples, "scenes": seeds, "steps": TRAIN_STEPS, "batch": TRAIN_BATCH,
+                      "lr": TRAIN_LR, "loss_first50": float(np.mean(losses[:50])),
+                      "loss_last200": float(np.mean(losses[-200:])), "data_s": round(t1 - t0, 2),
+                      "train_s": round(t2 - t1, 2), "tau": tau, "T_short": SERVING_T_SHORT,
+                      "alpha_short": SERVING_ALPHA, "calibration": "largest tau keeping median <= 1.8 deg and "
+                      "p95 <= 7.5 deg against the plain fusion on training scene %d" % seeds[0],
+                      "calibration_fallback_frac": float(np.mean(info["cost"] > tau))}
+
+
+def serving_accuracy(scenes, outs_learned, outs_plain, n_total):
+    """Angular error of the learned + batched and of the plain directions against the FP64 oracle on
+    a sample spread over the scenes in proportion to their point counts."""
+    import oracle
+    import paper_2604_05794_b300 as hf
+    Ntot = sum(sc["N"] for sc in scenes)
+    errs_l, errs_p, n = [], [], 0
+    t0 = time.perf_counter()
+    for sc, ol, op in zip(scenes, outs_learned, outs_plain):
+        m = max(8, int(round(n_total * sc["N"] / Ntot)))
+        sel = np.linspace(0, sc["N"] - 1, m).astype(np.int64)
+        H, T = sc["cfg"]["H"], sc["cfg"]["T"]
+        orc = oracle.fuse(oracle.Scene.from_dict(sc), hf.fibonacci_hemisphere(H), T, idx=sel)
+        ok = orc["status"] == 0
+        for out, errs in ((ol, errs_l), (op, errs_p)):
+            a, b = out[sel][ok].astype(np.float64), orc["dir"][ok]
+            errs.append(np.degrees(np.arctan2(np.linalg.norm(np.cross(a, b), axis=1), np.abs(np.sum(a * b, axis=1)))))
+        n += m
+    el, ep = np.concatenate(errs_l), np.concatenate(errs_p)
+    return {"vs": "FP64 oracle (plain fusion)", "sample": n, "oracle_s": round(time.perf_counter() - t0, 1),
+            "median_deg": float(np.median(el)), "p95_deg": float(np.percentile(el, 95)),
+            "within_2deg": float(np.mean(el <= 2.0)),
+            "plain": {"median_deg": float(np.median(ep)), "p95_deg": float(np.percentile(ep, 95)),
+                      "within_0p1deg": float(np.mean(ep <= 0.1))}}
+
+
+def serving_cpu_baseline(scenes, budget_s=15.0):
+    """The FP64 oracle (plain fusion) on the host cores over a bounded sample of the batch's points."""
+    import oracle
+    import paper_2604_05794_b300 as hf
+    osc = [oracle.Scene.from_dict(sc) for sc in scenes]
+    hyps = hf.fibonacci_hemisphere(64)
+    Ntot = sum(sc["N"] for sc in scenes)
+    oracle.fuse(osc[0], hyps, 8, idx=np.arange(64))   # thread start-up
+
+    def run(per_pt_total):
+        n = 0
+        for o, sc in zip(osc, scenes):
+            m = max(1, int(per_pt_total * sc["N"] / Ntot))
+            oracle.fuse(o, hyps, sc["cfg"]["T"], idx=np.linspace(0, sc["N"] - 1, m).astype(np.int64))
+            n += m
+        return n
+
+    m = 1024
+    while True:   # grow the probe until it takes a measurable share of the budget
+        t0 = time.perf_counter()
+        n = run(m)
+        dt = time.perf_counter() - t0
+        if dt >= 0.15 * budget_s or m >= Ntot:
+            break
+        m *= 4
+    if dt < 0.5 * budget_s and m < Ntot:
+        m = int(min(Ntot, m * budget_s / max(dt, 1e-3)))
+        t0 = time.perf_counter()
+        n = run(m)
+        dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "points/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{n} of {Ntot} points of the 16-scene batch, spread in proportion to the scenes' point "
+                      f"counts, evenly spaced in each; FP64 C + OpenMP, plain fusion, {dt:.1f} s"}
+
+
+def stage_rooflines(kt, ms_step, scenes, st, T_short):
+    """Per-stage rooflines of the learned + batched run from one profiled eager run (stage times) and
+    the work counters of the library (point-views of all points and of the fallback points)."""
+    peak_alu = SM_COUNT * FP32_LANES_PER_SM * 2032.0e6
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        bf16 = float(pk.get("bf16_tflops_sustained") or pk["bf16_tflops"])
+        bf16_src = "of measured: MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"
+    except (OSError, KeyError, ValueError, TypeError):
+        bf16, bf16_src = 1400.0, "of fallback: 1.4 PFLOP/s sustained bf16"
+    k, H, T = 8, 64, 8
+    per_member = 3 * (k + 1) + 6
+    Ntot = sum(sc["N"] for sc in scenes)
+    proj_bytes = sum((4 + sc["conf"].itemsize + 16) * sc["N"] * sc["V"] + 12 * sc["N"] for sc in scenes)
+    feat_bytes = sum((16 * (4 + sc["conf"].itemsize) + 12 + 128) * sc["N"] for sc in scenes)
+    pv, fpv = st["point_views"], st["fallback_point_views"]
+    work = {
+        "k_project_batch": ("hbm", proj_bytes, "(4 + conf bytes + 16) B per (point, view) + 12 B per point"),
+        "k_features_batch": ("hbm", feat_bytes, "16 x (4 + conf bytes) B gathered + 12 B in + 128 B out per point"),
+        "k_mlp": ("tensor", MLP_FLOP_PER_POINT * Ntot, f"{MLP_FLOP_PER_POINT} FLOP per point (51-256-256-3)"),
+        "k_refine_short_batch": ("alu", (6 * T_short + 1) * per_member * pv,
+                                 f"{6 * T_short + 1} directions x {per_member} FP32 ops per (point, view), "
+                                 f"{pv} point-views"),
+        "k_argmin_batch": ("alu", H * per_member * fpv, f"{H} x {per_member} ops per fallback (point, view), {fpv}"),
+        "k_refine_batch": ("alu", 6 * T * per_member * fpv, f"{6 * T} x {per_member} ops per fallback (point, view)"),
+    }
+    out = {}
+    for name, (bound, amount, how) in work.items():
+        if name not in kt:
+            continue
+        sec = kt[name][1] / 1e3
+        if bound == "alu":
+            ach, peak, unit, src = amount / sec / 1e12, peak_alu / 1e12, "TFLOP/s", \
+                "derived: 148 SMs x 128 FP32 lanes x 2032 MHz (1 op per lane per clock)"
+        elif bound == "tensor":
+            ach, peak, unit, src = amount / sec / 1e12, bf16, "TFLOP/s", bf16_src
+        else:
+            ach, peak, unit, src = amount / sec / 1e9, HBM_GBS, "GB/s", "of measured: MEASURED_PEAKS.json hbm_gbs"
+        out[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                     "traffic": None, "kernel": name, "peak_source": src, "work": how,
+                     "ms": kt[name][1], "share": kt[name][1] / ms_step}
+    return out
+
+
+def run_serving(args):
+    import torch
+
+    import paper_2604_05794_b300 as hf
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    stream = torch.cuda.current_stream(dev)
+    t_setup = time.perf_counter()
+    net, tau, train_info = train_proposal(dev, 1000 * rank)
+    scenes = serving_scenes(200 + 1000 * rank)
+    Ntot = sum(sc["N"] for sc in scenes)
+    ctxs, outs_p, outs_l, outs_pb = [], [], [], []
+
+    def outs(N):
+        return (torch.empty((N, 3), device=dev), torch.empty(N, device=dev),
+                torch.empty(N, dtype=torch.int32, device=dev), torch.empty(N, dtype=torch.uint8, device=dev))
+
+    for sc in scenes:
+        f = hf.HairFuse(sc["cfg"]["H"], sc["k"], sc["cfg"]["T"], 0, stream=stream.cuda_stream)
+        f.upload_views(sc["cams"], sc["angle"], sc["conf"])
+        f.upload_points(sc["points"], sc["nbr"])
+        ctxs.append(f)
+        outs_p.append(outs(sc["N"]))
+        outs_l.append(outs(sc["N"]))
+        outs_pb.append(outs(sc["N"]))
+    K, W = args.steps, max(3, args.warmup)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(step, k):
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(k):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        if pg:
+            t = torch.tensor([ms], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # plain fusion, scene after scene (the comparison)
+    def plain_step():
+        for f, o in zip(ctxs, outs_p):
+            f.fuse(*o)
+
+    for _ in range(W):
+        plain_step()
+    ms_plain = timed(plain_step, K)
+    torch.cuda.synchronize(dev)
+    e0, evs = ev(), [ev() for _ in ctxs]
+    e0.record(stream)
+    for f, o, e in zip(ctxs, outs_p, evs):
+        f.fuse(*o)
+        e.record(stream)
+    torch.cuda.synchronize(dev)
+    lat_plain = np.array([e0.elapsed_time(e) for e in evs])
+
+    # plain fusion, batched (no network)
+    bp = hf.Batch(ctxs, autotune=True, stream=stream.cuda_stream)
+    for s_, o in enumerate(outs_pb):
+        bp.set_outputs(s_, *o)
+    bp.run()
+    for _ in range(W):
+        bp.run()
+    ms_pb = timed(bp.run, K)
+    lat_pb = bp.latency_ms()
+    tune_pb = bp.tuning()
+
+    # learned + batched (the measured form)
+    bl = hf.Batch(ctxs, net=net, T_short=SERVING_T_SHORT, alpha_short=SERVING_ALPHA, tau=tau, autotune=True,
+                  stream=stream.cuda_stream)
+    for s_, o in enumerate(outs_l):
+        bl.set_outputs(s_, *o)
+    bl.run()
+    for _ in range(W):
+        bl.run()
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(cvd.split(",")[local] if cvd else str(local))
+    launches0 = bl.stats()["launches"]
+    clocks.start()
+    time.sleep(0.3)
+    ms_l = timed(bl.run, K)
+    clk = clocks.stop()
+    launches = bl.stats()["launches"] - launches0
+    lat_l = bl.latency_ms()
+    fb = bl.fallbacks()
+    tune_l = bl.tuning()
+    kt = bl.profile_run()
+    st = bl.stats()
+    bl.run()
+    torch.cuda.synchronize(dev)
+    setup_s = time.perf_counter() - t_setup
+    value = Ntot * world * K / (ms_l / 1e3)
+    plain_value = Ntot * world * K / (ms_plain / 1e3)
+    ms_prof = sum(v[1] for v in kt.values())
+    rooflines = stage_rooflines(kt, ms_prof, scenes, st, SERVING_T_SHORT)
+    dom = max(rooflines, key=lambda x: rooflines[x]["share"])
+    q = lambda a, p: float(np.percentile(a, p))
+    line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_l / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (bf16 tensor-core network)", "data": "synthetic",
+            "config": {"workload": WORKLOADS["serving16"], "scenes": len(scenes), "points": Ntot,
+                       "views": [sc["V"] for sc in scenes], "maps": [f"{sc['W']}x{sc['H']}" for sc in scenes],
+                       "form": "learned+batched", "H": 64, "k": 8, "T": 8,
+                       "l2": "inputs larger than L2 (orientation+confidence maps "
+                             f"{sum(sc['angle'].nbytes + sc['conf'].nbytes for sc in scenes) / 1e9:.1f} GB re-read "
+                             "every step)",
+                       "parallelism": f"independent scene batches per rank x{world}"},
+            "plain": {"value": plain_value, "unit": "points/s", "ms_per_step": ms_plain / K,
+                      "form": "plain fusion, scenes one by one",
+                      "latency_ms": {"p50": q(lat_plain, 50), "p95": q(lat_plain, 95)}},
+            "plain_batched": {"value": Ntot * world * K / (ms_pb / 1e3), "ms_per_step": ms_pb / K,
+                              "latency_ms": {"p50": q(lat_pb, 50), "p95": q(lat_pb, 95)}, "tuning": tune_pb},
+            "speedup_vs_plain": value / plain_value,
+            "latency_ms": {"p50": q(lat_l, 50), "p95": q(lat_l, 95), "per_scene": [round(x, 3) for x in lat_l],
+                           "source": "device global-timer stamp when a scene's last tile finishes"},
+            "learned": dict(train_info, fallback_frac=float(fb.sum() / Ntot), tuning=tune_l),
+            "roofline": dict(rooflines[dom]), "rooflines": rooflines,
+            "kernels": {n_: {"launches": v[0], "ms": v[1], "share": v[1] / ms_prof} for n_, v in kt.items()},
+            "gpu_launches": launches, "clocks": clk, "setup_s": round(setup_s, 1)}
+    if rank == 0:
+        acc = serving_accuracy(scenes, [o[0].cpu().numpy() for o in outs_l], [o[0].cpu().numpy() for o in outs_p],
+                               args.accuracy_sample or 50000)
+        line["accuracy"] = acc
+        line["accepted"] = bool(acc["median_deg"] <= 2.0)
+    # end to end through the C ABI: every step uploads every scene from pinned host memory, runs the
+    # batch's graph and reads the outputs back
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        host_in = [tuple(pin(sc[x]) for x in ("cams", "angle", "conf", "points", "nbr")) for sc in scenes]
+        host_out = [tuple(torch.empty_like(x, device="cpu").pin_memory() for x in o) for o in outs_l]
+
+        def e2e_step():
+            for f, (c_, a_, cf, p_, n_) in zip(ctxs, host_in):
+                f.upload_views(c_, a_, cf)
+                f.upload_points(p_, n_)
+            bl.run()
+            for o, h in zip(outs_l, host_out):
+                for x, y in zip(o, h):
+                    y.copy_(x, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        e2e_step()
+        n_e2e = max(1, min(K, 3))
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        dt = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([dt], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = sum(x.numel() * x.element_size() for t_ in host_in for x in t_)
+        d2h = sum(x.numel() * x.element_size() for t_ in host_out for x in t_)
+        line["e2e"] = {"value": Ntot * world * n_e2e / dt, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
+                       "path": "hair_fuse_upload_views/points of every scene (HF_HOST, pinned) + "
+                               "hair_fuse_batch_run (graph) + device-to-host copy of all outputs"}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = serving_cpu_baseline(scenes)
+    bl.close()
+    bp.close()
+    for f in ctxs:
+        f.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving16":
+        run_serving(args)
     else:
         run_ours(args)
 
