@@ -69,6 +69,14 @@ def parse():
     ap.add_argument("--workload", default="serving16", choices=list(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--net", default=None, help="serving16: load the proposal network from this file instead of "
+                    "training it (profiling runs)")
+    ap.add_argument("--save-net", default=None, help="serving16: save the trained proposal network here")
+    ap.add_argument("--tau", type=float, default=None, help="serving16 with --net: fallback threshold (skips "
+                    "the calibration)")
+    ap.add_argument("--scenes", default="16", help="serving16: number of scenes of the batch, or a comma list of "
+                    "their indices (profiling runs)")
+    ap.add_argument("--only-learned", action="store_true", help="serving16: skip the plain comparison runs")
     ap.add_argument("--accuracy-sample", type=int, default=0,
                     help="oracle sample for the accuracy check (default 400 points; 50,000 across the serving batch)")
     return ap.parse_args()
@@ -79,6 +87,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def reduce_over_ranks(x, pg, dev, op="max"):
+    """x combined over the ranks of the process group (max for times, sum for work); x itself
+    without one.  dev: the device of the collective's tensor (cuda for NCCL, cpu for gloo)."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX if op == "max" else pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def rank_first_seed(rank):
+    """First seed of the serving batch of a rank: every rank fuses its own independent scenes."""
+    return 200 + 1000 * rank
 
 
 class ClockSampler:
@@ -280,12 +304,9 @@ def run_ours(args):
     kt = f.profile_read()
     f.profile(False)
     launches = f.stats()["launches"] - launches0
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_over_ranks(ms, pg, dev)
     f.sync()
-    value = N * world * args.steps / (ms / 1e3)
+    value = reduce_over_ranks(N, pg, dev, "sum") * args.steps / (ms / 1e3)
 
     # rooflines: the cost kernels are FP32-issue bound, the projection/gather kernel HBM bound
     peak_alu = SM_COUNT * FP32_LANES_PER_SM * 2032.0e6
@@ -349,14 +370,10 @@ def run_ours(args):
         n_e2e = max(1, min(args.steps, 5))
         for _ in range(n_e2e):
             e2e_step()
-        dt = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([dt], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = reduce_over_ranks(time.perf_counter() - t0, pg, dev)
         h2d = sum(x.numel() * x.element_size() for x in (h_cams, h_ang, h_conf, h_pts, h_nbr))
         d2h = N * (12 + 4 + 4 + 1)
-        line["e2e"] = {"value": N * world * n_e2e / dt, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+        line["e2e"] = {"value": reduce_over_ranks(N, pg, dev, "sum") * n_e2e / dt, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
                        "path": "hair_fuse_upload_views/points + fuse_directions with HF_HOST pinned buffers"}
         f2.close()
@@ -376,9 +393,14 @@ TRAIN_SEEDS, TRAIN_SAMPLES, TRAIN_STEPS, TRAIN_BATCH, TRAIN_LR = (100, 101, 102,
 MLP_FLOP_PER_POINT = 2 * (51 * 256 + 256 * 256 + 256 * 3)   # forward, unpadded inputs
 
 
-def serving_scenes(first_seed):
+def serving_scenes(first_seed, pick="16"):
     import scenegen
-    return [scenegen.make_scene(**c) for c in scenegen.serving_batch(first_seed)]
+    cfgs = scenegen.serving_batch(first_seed)
+    if "," in str(pick):
+        cfgs = [cfgs[int(q)] for q in str(pick).split(",")]
+    else:
+        cfgs = cfgs[: int(pick)]
+    return [scenegen.make_scene(**c) for c in cfgs]
 
 
 def train_proposal(dev, seed_offset):
@@ -470,6 +492,14 @@ def serving_cpu_baseline(scenes, budget_s=15.0):
                       f"counts, evenly spaced in each; FP64 C + OpenMP, plain fusion, {dt:.1f} s"}
 
 
+# DRAM bytes (read + write) per work unit of the batched cost kernels, from one ncu --set full capture
+# of the 4-scene serving batch (profiles/k_refine_batch_k_argmin_batch_serving4_ncu.md); a full launch's
+# traffic is scaled from it by the units the launch processes.  Re-take it whenever these kernels change.
+DRAM_BYTES_PER_UNIT = {"k_refine_batch": (773.682 + 14.088) * 1e6 / 15816683,        # per fallback point-view
+                       "k_argmin_batch": (553.947 + 15.963) * 1e6 / 15816683,        # per fallback point-view
+                       "k_refine_short_batch": (424.331 + 17.417) * 1e6 / 19911750}  # per point-view
+
+
 def stage_rooflines(kt, ms_step, scenes, st, T_short):
     """Per-stage rooflines of the learned + batched run from one profiled eager run (stage times) and
     the work counters of the library (point-views of all points and of the fallback points)."""
@@ -487,6 +517,7 @@ def stage_rooflines(kt, ms_step, scenes, st, T_short):
     proj_bytes = sum((4 + sc["conf"].itemsize + 16) * sc["N"] * sc["V"] + 12 * sc["N"] for sc in scenes)
     feat_bytes = sum((16 * (4 + sc["conf"].itemsize) + 12 + 128) * sc["N"] for sc in scenes)
     pv, fpv = st["point_views"], st["fallback_point_views"]
+    units = {"k_refine_batch": fpv, "k_argmin_batch": fpv, "k_refine_short_batch": pv}
     work = {
         "k_project_batch": ("hbm", proj_bytes, "(4 + conf bytes + 16) B per (point, view) + 12 B per point"),
         "k_features_batch": ("hbm", feat_bytes, "16 x (4 + conf bytes) B gathered + 12 B in + 128 B out per point"),
@@ -509,9 +540,13 @@ def stage_rooflines(kt, ms_step, scenes, st, T_short):
             ach, peak, unit, src = amount / sec / 1e12, bf16, "TFLOP/s", bf16_src
         else:
             ach, peak, unit, src = amount / sec / 1e9, HBM_GBS, "GB/s", "of measured: MEASURED_PEAKS.json hbm_gbs"
+        traffic = DRAM_BYTES_PER_UNIT[name] * units[name] if name in DRAM_BYTES_PER_UNIT else None
         out[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                     "traffic": None, "kernel": name, "peak_source": src, "work": how,
-                     "ms": kt[name][1], "share": kt[name][1] / ms_step}
+                     "traffic": traffic, "kernel": name, "peak_source": src, "work": how,
+                     "units": units.get(name, Ntot), "ms": kt[name][1], "share": kt[name][1] / ms_step}
+        if traffic is not None:
+            out[name]["traffic_source"] = ("DRAM read+write bytes per unit from the ncu capture of the 4-scene batch, "
+                                           "x units of this launch")
     return out
 
 
@@ -529,8 +564,23 @@ def run_serving(args):
         pg = dist
     stream = torch.cuda.current_stream(dev)
     t_setup = time.perf_counter()
-    net, tau, train_info = train_proposal(dev, 1000 * rank)
-    scenes = serving_scenes(200 + 1000 * rank)
+    if args.net:
+        net = hf.ProposalNet(TRAIN_BATCH)
+        net.load(args.net)
+        if args.tau is not None:
+            tau, train_info = args.tau, {"loaded": args.net, "tau": args.tau}
+        else:
+            import scenegen
+            from paper_2604_05794_b300 import learned as L
+            tau, _ = L.calibrate_tau(scenegen.make_scene("full", seed=TRAIN_SEEDS[0] + rank_first_seed(rank) - 200),
+                                     net, 64, 8,
+                                     SERVING_T_SHORT, SERVING_ALPHA, dev, median_deg=1.8, p95_deg=7.5)
+            train_info = {"loaded": args.net, "tau": tau}
+    else:
+        net, tau, train_info = train_proposal(dev, rank_first_seed(rank) - 200)
+    if args.save_net:
+        net.save(args.save_net)
+    scenes = serving_scenes(rank_first_seed(rank), args.scenes)
     Ntot = sum(sc["N"] for sc in scenes)
     ctxs, outs_p, outs_l, outs_pb = [], [], [], []
 
@@ -559,40 +609,37 @@ def run_serving(args):
             step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1)
-        if pg:
-            t = torch.tensor([ms], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return reduce_over_ranks(e0.elapsed_time(e1), pg, dev)
 
     # plain fusion, scene after scene (the comparison)
     def plain_step():
         for f, o in zip(ctxs, outs_p):
             f.fuse(*o)
 
-    for _ in range(W):
-        plain_step()
-    ms_plain = timed(plain_step, K)
-    torch.cuda.synchronize(dev)
-    e0, evs = ev(), [ev() for _ in ctxs]
-    e0.record(stream)
-    for f, o, e in zip(ctxs, outs_p, evs):
-        f.fuse(*o)
-        e.record(stream)
-    torch.cuda.synchronize(dev)
-    lat_plain = np.array([e0.elapsed_time(e) for e in evs])
+    bp = None
+    if not args.only_learned:
+        for _ in range(W):
+            plain_step()
+        ms_plain = timed(plain_step, K)
+        torch.cuda.synchronize(dev)
+        e0, evs = ev(), [ev() for _ in ctxs]
+        e0.record(stream)
+        for f, o, e in zip(ctxs, outs_p, evs):
+            f.fuse(*o)
+            e.record(stream)
+        torch.cuda.synchronize(dev)
+        lat_plain = np.array([e0.elapsed_time(e) for e in evs])
 
-    # plain fusion, batched (no network)
-    bp = hf.Batch(ctxs, autotune=True, stream=stream.cuda_stream)
-    for s_, o in enumerate(outs_pb):
-        bp.set_outputs(s_, *o)
-    bp.run()
-    for _ in range(W):
+        # plain fusion, batched (no network)
+        bp = hf.Batch(ctxs, autotune=True, stream=stream.cuda_stream)
+        for s_, o in enumerate(outs_pb):
+            bp.set_outputs(s_, *o)
         bp.run()
-    ms_pb = timed(bp.run, K)
-    lat_pb = bp.latency_ms()
-    tune_pb = bp.tuning()
+        for _ in range(W):
+            bp.run()
+        ms_pb = timed(bp.run, K)
+        lat_pb = bp.latency_ms()
+        tune_pb = bp.tuning()
 
     # learned + batched (the measured form)
     bl = hf.Batch(ctxs, net=net, T_short=SERVING_T_SHORT, alpha_short=SERVING_ALPHA, tau=tau, autotune=True,
@@ -618,8 +665,9 @@ def run_serving(args):
     bl.run()
     torch.cuda.synchronize(dev)
     setup_s = time.perf_counter() - t_setup
-    value = Ntot * world * K / (ms_l / 1e3)
-    plain_value = Ntot * world * K / (ms_plain / 1e3)
+    Nall = reduce_over_ranks(Ntot, pg, dev, "sum")   # points of all ranks' batches
+    value = Nall * K / (ms_l / 1e3)
+    plain_value = Nall * K / (ms_plain / 1e3) if bp is not None else None
     ms_prof = sum(v[1] for v in kt.values())
     rooflines = stage_rooflines(kt, ms_prof, scenes, st, SERVING_T_SHORT)
     dom = max(rooflines, key=lambda x: rooflines[x]["share"])
@@ -627,26 +675,28 @@ def run_serving(args):
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_l / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (bf16 tensor-core network)", "data": "synthetic",
-            "config": {"workload": WORKLOADS["serving16"], "scenes": len(scenes), "points": Ntot,
+            "config": {"workload": WORKLOADS["serving16"], "scenes": len(scenes), "scenes_arg": args.scenes,
+                       "points": Ntot,
                        "views": [sc["V"] for sc in scenes], "maps": [f"{sc['W']}x{sc['H']}" for sc in scenes],
                        "form": "learned+batched", "H": 64, "k": 8, "T": 8,
                        "l2": "inputs larger than L2 (orientation+confidence maps "
                              f"{sum(sc['angle'].nbytes + sc['conf'].nbytes for sc in scenes) / 1e9:.1f} GB re-read "
                              "every step)",
                        "parallelism": f"independent scene batches per rank x{world}"},
-            "plain": {"value": plain_value, "unit": "points/s", "ms_per_step": ms_plain / K,
-                      "form": "plain fusion, scenes one by one",
-                      "latency_ms": {"p50": q(lat_plain, 50), "p95": q(lat_plain, 95)}},
-            "plain_batched": {"value": Ntot * world * K / (ms_pb / 1e3), "ms_per_step": ms_pb / K,
-                              "latency_ms": {"p50": q(lat_pb, 50), "p95": q(lat_pb, 95)}, "tuning": tune_pb},
-            "speedup_vs_plain": value / plain_value,
+            "plain": None if bp is None else {
+                "value": plain_value, "unit": "points/s", "ms_per_step": ms_plain / K,
+                "form": "plain fusion, scenes one by one", "latency_ms": {"p50": q(lat_plain, 50), "p95": q(lat_plain, 95)}},
+            "plain_batched": None if bp is None else {
+                "value": Nall * K / (ms_pb / 1e3), "ms_per_step": ms_pb / K,
+                "latency_ms": {"p50": q(lat_pb, 50), "p95": q(lat_pb, 95)}, "tuning": tune_pb},
+            "speedup_vs_plain": value / plain_value if bp is not None else None,
             "latency_ms": {"p50": q(lat_l, 50), "p95": q(lat_l, 95), "per_scene": [round(x, 3) for x in lat_l],
                            "source": "device global-timer stamp when a scene's last tile finishes"},
             "learned": dict(train_info, fallback_frac=float(fb.sum() / Ntot), tuning=tune_l),
             "roofline": dict(rooflines[dom]), "rooflines": rooflines,
             "kernels": {n_: {"launches": v[0], "ms": v[1], "share": v[1] / ms_prof} for n_, v in kt.items()},
             "gpu_launches": launches, "clocks": clk, "setup_s": round(setup_s, 1)}
-    if rank == 0:
+    if rank == 0 and bp is not None:
         acc = serving_accuracy(scenes, [o[0].cpu().numpy() for o in outs_l], [o[0].cpu().numpy() for o in outs_p],
                                args.accuracy_sample or 50000)
         line["accuracy"] = acc
@@ -675,21 +725,18 @@ def run_serving(args):
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             e2e_step()
-        dt = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([dt], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = reduce_over_ranks(time.perf_counter() - t0, pg, dev)
         h2d = sum(x.numel() * x.element_size() for t_ in host_in for x in t_)
         d2h = sum(x.numel() * x.element_size() for t_ in host_out for x in t_)
-        line["e2e"] = {"value": Ntot * world * n_e2e / dt, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+        line["e2e"] = {"value": Nall * n_e2e / dt, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
                        "path": "hair_fuse_upload_views/points of every scene (HF_HOST, pinned) + "
                                "hair_fuse_batch_run (graph) + device-to-host copy of all outputs"}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = serving_cpu_baseline(scenes)
     bl.close()
-    bp.close()
+    if bp is not None:
+        bp.close()
     for f in ctxs:
         f.close()
     if rank == 0:
