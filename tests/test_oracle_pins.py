@@ -288,6 +288,49 @@ def test_refinement_descends_and_reports_own_cost(tiny):
     assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-14)
 
 
+def test_refine_from_start_keeps_the_exact_tangent(tiny):
+    """Learned-path refinement from a given start: on point-splatted exact maps the true tangent
+    costs 0 and nothing is strictly lower, so a start at the tangent stays there (up to the
+    canonical sign) with cost 0, for any step size; a start rotated away by a few degrees is
+    pulled back to within the last step of the tangent."""
+    se = oracle.Scene.from_dict(tiny, exact=True)
+    N, V = tiny["N"], tiny["V"]
+    vis = np.array([[oracle.project(tiny["cams"][v], tiny["points"][i], tiny["W"], tiny["H"])[0]
+                     for v in range(V)] for i in range(N)])
+    owns = np.nonzero(np.all((tiny["owner"].T == 1) | (vis == 0), axis=1) & (vis.sum(1) >= 2))[0][:200]
+    t = tiny["tangents"][owns].astype(np.float64)
+    for alpha in (0.02, 0.2):
+        r = oracle.refine(se, t, 4, alpha, idx=owns)
+        assert np.all(r["cost"] <= 1e-12)
+        assert np.allclose(np.abs(np.sum(r["dir"] * t, axis=1)), 1.0, atol=1e-12)
+    # a small rotation about a random axis perpendicular to the tangent
+    ax = np.cross(t, rand_unit(len(t)))
+    ax /= np.linalg.norm(ax, axis=1, keepdims=True)
+    ang = np.radians(3.0)
+    start = t * np.cos(ang) + np.cross(ax, t) * np.sin(ang)
+    r = oracle.refine(se, start, 8, np.radians(4.0), idx=owns)
+    c0 = oracle.eval_costs(se, start[:, None, :], idx=owns)[:, 0]
+    assert np.all(r["cost"] <= c0)
+    err = np.degrees(np.arccos(np.clip(np.abs(np.sum(r["dir"] * t, axis=1)), 0, 1)))
+    assert np.median(err) < 4.0 * 2.0 ** -7 * 2
+
+
+def test_refine_from_argmin_hypothesis_is_the_fused_refinement(tiny):
+    """Started at the argmin hypothesis with the hypothesis-derived first step 1/2 sqrt(2 pi / H),
+    the learned-path refinement reproduces the plain fusion's refinement exactly (same rotation
+    order, halving and sign rule)."""
+    sc = oracle.Scene.from_dict(tiny)
+    H = 32
+    hyps = oracle.fibonacci_hemisphere(H)
+    idx = np.arange(0, tiny["N"], 7)
+    fused = oracle.fuse(sc, hyps, T=4, idx=idx)
+    start = oracle.fuse(sc, hyps, T=0, idx=idx)
+    r = oracle.refine(sc, hyps[start["idx"]], 4, 0.5 * np.sqrt(2 * np.pi / H), idx=idx)
+    ok = fused["status"] == oracle.OK
+    assert np.array_equal(r["dir"][ok], fused["dir"][ok])
+    assert np.array_equal(r["cost"][ok], fused["cost"][ok])
+
+
 def test_dense_sphere_bounds_the_fused_cost(tiny):
     """Brute force over a 20,000-direction Fibonacci hemisphere on a 50-point slice: no fused
     cost lies below the dense minimum by more than the cost change over one grid spacing, and
