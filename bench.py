@@ -388,7 +388,7 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------- serving workload
-SERVING_T_SHORT, SERVING_ALPHA = 2, 0.08   # short refinement from the proposal
+SERVING_T_SHORT, SERVING_ALPHA = 2, 0.16   # short refinement from the proposal
 TRAIN_SEEDS, TRAIN_SAMPLES, TRAIN_STEPS, TRAIN_BATCH, TRAIN_LR = (100, 101, 102, 103), 500_000, 20000, 8192, 1e-3
 MLP_FLOP_PER_POINT = 2 * (51 * 256 + 256 * 256 + 256 * 3)   # forward, unpadded inputs
 

@@ -242,7 +242,8 @@ typedef struct {
     int autotune;       /* 1: at the first run, time the candidate tile shapes on the batch and keep the fastest */
     int hchunk;         /* hypotheses per chunk of the argmin: 0 = tuned / default, else 8, 16 or 32 */
     int points_per_cta; /* points per CTA of argmin and refinement: 0 = tuned / default 128, else 64, 128, 256 */
-    int order;          /* scene order of the work list: 0 = tuned / heaviest first, 1 = heaviest first, 2 = as given */
+    int order;          /* scene order of the work list: 0 = tuned (heaviest or lightest first), 1 = heaviest
+                         * first, 2 = as given, 3 = lightest first (small scenes complete early) */
 } hf_batch_cfg;
 
 /* n_scenes (1..HF_MAX_BATCH_SCENES) contexts with views and points uploaded; mlp = NULL for the
@@ -265,7 +266,7 @@ int hair_fuse_batch_latency(hf_batch* b, double* ms_out);
 /* Per-scene fallback counts of the last learned run (0 for the plain fusion), host.  Synchronises. */
 int hair_fuse_batch_fallbacks(hf_batch* b, int* n_out);
 /* The launch shape in use: out4 = {hypothesis chunk, points per CTA of the argmin, points per CTA of
- * the refinement, heaviest-first order (1) or as given (0)}. */
+ * the refinement, scene order (1 heaviest first, 2 as given, 3 lightest first)}. */
 int hair_fuse_batch_tuning(const hf_batch* b, int* out4);
 /* One eager run with CUDA events between the stages (synchronous): per-stage records as in
  * hair_fuse_profile_read (the network's stage counts its two GEMM launches).  Returns the number of

@@ -373,7 +373,7 @@ def _features(self, out):
     return out
 
 
-def _fuse_learned(self, net, dir_out, cost_out=None, idx_out=None, status_out=None, T_short=2, alpha_short=0.02,
+def _fuse_learned(self, net, dir_out, cost_out=None, idx_out=None, status_out=None, T_short=2, alpha_short=0.16,
                   tau=0.5, count_fallback=True):
     """Learned fusion into caller buffers; returns the number of fallback points (or None)."""
     ptrs = [_ptr_kind(x) for x in (dir_out, cost_out, idx_out, status_out)]
@@ -398,7 +398,7 @@ class Batch:
     """Batched fusion of several HairFuse contexts (plain, or learned with a ProposalNet): one
     persistent launch per stage over all scenes, replayed as one CUDA graph."""
 
-    def __init__(self, scenes, net=None, T_short=2, alpha_short=0.02, tau=0.5, autotune=True, hchunk=0,
+    def __init__(self, scenes, net=None, T_short=2, alpha_short=0.16, tau=0.5, autotune=True, hchunk=0,
                  points_per_cta=0, order=0, stream=None):
         self.scenes = list(scenes)
         self.net = net
@@ -457,7 +457,7 @@ class Batch:
         out = np.zeros(4, np.int32)
         self._c(hair_fuse_batch_tuning(self.h, out.ctypes.data))
         return dict(hchunk=int(out[0]), points_per_cta_argmin=int(out[1]), points_per_cta_refine=int(out[2]),
-                    heaviest_first=bool(out[3]))
+                    order={1: "heaviest first", 2: "as given", 3: "lightest first"}.get(int(out[3]), "?"))
 
     def profile_run(self):
         """One eager run with events between the stages: {stage: (launches, ms)}."""

@@ -71,7 +71,7 @@ struct hf_batch {
     cudaStream_t user = nullptr;    // caller's stream (ordering only)
     cudaStream_t stream = nullptr;  // the batch's own non-blocking stream (captured)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, t_beg = nullptr, t_end = nullptr;
-    int kp = 9, hc = 32, nt_a = 128, nt_r = 128, heavy_first = 1;
+    int kp = 9, hc = 32, nt_a = 128, nt_r = 128, order = 1;   // order: 1 heaviest first, 2 as given, 3 lightest first
     bool tuned = false, configured = false;
     long long total = 0;
     char* ctl = nullptr;
@@ -112,8 +112,12 @@ int configure(hf_batch* b) {
     const int ns = (int)b->sc.size();
     b->pos.resize(ns);
     for (int p = 0; p < ns; ++p) b->pos[p] = p;
-    if (b->heavy_first)
-        std::stable_sort(b->pos.begin(), b->pos.end(), [&](int u, int v) { return b->sc[u].work > b->sc[v].work; });
+    // per-point work x points: the scene's share of a stage
+    auto load = [&](int u) { return b->sc[u].work * (double)b->sc[u].c->N; };
+    if (b->order == 1)
+        std::stable_sort(b->pos.begin(), b->pos.end(), [&](int u, int v) { return load(u) > load(v); });
+    else if (b->order == 3)
+        std::stable_sort(b->pos.begin(), b->pos.end(), [&](int u, int v) { return load(u) < load(v); });
     const bool learned = b->mlp != nullptr;
     unsigned* box = reinterpret_cast<unsigned*>(b->ctl + kBoxOff);
     int* count = reinterpret_cast<int*>(b->ctl + kCountOff);
@@ -304,20 +308,22 @@ int autotune(hf_batch* b) {
     }
     b->hc = best_hc;
     b->nt_a = best_nta;
-    // scene order: heaviest first against the given order (full runs)
+    // scene order: heaviest first (best balance at the end of a stage) against lightest first (small
+    // scenes complete early); lightest first unless it costs more than 1 % of throughput
     if (!b->cfg.order) {
         float tt[2] = {0.0f, 0.0f};
-        for (int hf = 0; hf < 2; ++hf) {
-            b->heavy_first = hf;
+        const int modes[2] = {1, 3};
+        for (int q = 0; q < 2; ++q) {
+            b->order = modes[q];
             if ((rc = configure(b)) || (rc = run_eager(b))) return rc;
             cudaError_t e = cudaEventRecord(b->t_beg, b->stream);
             if (e == cudaSuccess) e = enqueue(b);
             if (e == cudaSuccess) e = cudaEventRecord(b->t_end, b->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(b->t_end);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&tt[hf], b->t_beg, b->t_end);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&tt[q], b->t_beg, b->t_end);
             if (e != cudaSuccess) return b_cuda(b, e, "autotune order");
         }
-        b->heavy_first = tt[1] <= tt[0] ? 1 : 0;
+        b->order = tt[1] <= 1.01f * tt[0] ? 3 : 1;
     }
     if ((rc = configure(b)) || (rc = run_eager(b))) return rc;
     b->tuned = true;
@@ -358,7 +364,7 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
     if (c.hchunk && c.hchunk != 8 && c.hchunk != 16 && c.hchunk != 32) return fail(HF_ERR_INVALID_ARG, "hchunk: 0, 8, 16 or 32");
     if (c.points_per_cta && c.points_per_cta != 64 && c.points_per_cta != 128 && c.points_per_cta != 256)
         return fail(HF_ERR_INVALID_ARG, "points_per_cta: 0, 64, 128 or 256");
-    if (c.order < 0 || c.order > 2) return fail(HF_ERR_INVALID_ARG, "order: 0, 1 or 2");
+    if (c.order < 0 || c.order > 3) return fail(HF_ERR_INVALID_ARG, "order: 0, 1, 2 or 3");
     long long total = 0;
     int max_k = 0, maxH = 1;
     for (int s = 0; s < n_scenes; ++s) {
@@ -380,7 +386,7 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
     b->kp = hf_batch_kp_for(max_k);
     b->hc = c.hchunk ? c.hchunk : hf_fuse_chunk_for(maxH);
     b->nt_a = b->nt_r = c.points_per_cta ? c.points_per_cta : 128;
-    b->heavy_first = c.order == 2 ? 0 : 1;
+    b->order = c.order ? c.order : 1;
     b->sc.resize(n_scenes);
     int rc = HF_OK;
     cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
@@ -533,7 +539,7 @@ extern "C" int hair_fuse_batch_tuning(const hf_batch* b, int* out4) {
     out4[0] = b->hc;
     out4[1] = b->nt_a;
     out4[2] = b->nt_r;
-    out4[3] = b->heavy_first;
+    out4[3] = b->order;
     return HF_OK;
 }
 

@@ -63,7 +63,8 @@ def _equal(a, b):
 
 
 @pytest.mark.parametrize("shape", [dict(autotune=True), dict(autotune=False, hchunk=8, points_per_cta=64, order=2),
-                                   dict(autotune=False, hchunk=16, points_per_cta=256, order=1),
+                                   dict(autotune=False, hchunk=16, points_per_cta=256, order=3),
+                                   dict(autotune=False, hchunk=8, points_per_cta=128, order=1),
                                    dict(autotune=False, hchunk=32, points_per_cta=128, order=0)])
 def test_plain_batch_equals_alone(scenes, shape):
     import torch
