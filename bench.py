@@ -495,9 +495,8 @@ def serving_cpu_baseline(scenes, budget_s=15.0):
 # DRAM bytes (read + write) per work unit of the batched cost kernels, from one ncu --set full capture
 # of the 4-scene serving batch (profiles/k_refine_batch_k_argmin_batch_serving4_ncu.md); a full launch's
 # traffic is scaled from it by the units the launch processes.  Re-take it whenever these kernels change.
-DRAM_BYTES_PER_UNIT = {"k_refine_batch": (773.682 + 14.088) * 1e6 / 15816683,        # per fallback point-view
-                       "k_argmin_batch": (553.947 + 15.963) * 1e6 / 15816683,        # per fallback point-view
-                       "k_refine_short_batch": (424.331 + 17.417) * 1e6 / 19911750}  # per point-view
+DRAM_BYTES_PER_UNIT = {"k_refine_batch": (773.682 + 14.088) * 1e6 / 15816683,   # per fallback point-view
+                       "k_argmin_batch": (553.947 + 15.963) * 1e6 / 15816683}   # per fallback point-view
 
 
 def stage_rooflines(kt, ms_step, scenes, st, T_short):
@@ -517,14 +516,17 @@ def stage_rooflines(kt, ms_step, scenes, st, T_short):
     proj_bytes = sum((4 + sc["conf"].itemsize + 16) * sc["N"] * sc["V"] + 12 * sc["N"] for sc in scenes)
     feat_bytes = sum((16 * (4 + sc["conf"].itemsize) + 12 + 128) * sc["N"] for sc in scenes)
     pv, fpv = st["point_views"], st["fallback_point_views"]
-    units = {"k_refine_batch": fpv, "k_argmin_batch": fpv, "k_refine_short_batch": pv}
+    apv = pv - fpv   # point-views of the accepted proposals
+    units = {"k_refine_batch": fpv, "k_argmin_batch": fpv, "k_refine_short_batch": apv, "k_start_select_batch": pv}
     work = {
         "k_project_batch": ("hbm", proj_bytes, "(4 + conf bytes + 16) B per (point, view) + 12 B per point"),
         "k_features_batch": ("hbm", feat_bytes, "16 x (4 + conf bytes) B gathered + 12 B in + 128 B out per point"),
         "k_mlp": ("tensor", MLP_FLOP_PER_POINT * Ntot, f"{MLP_FLOP_PER_POINT} FLOP per point (51-256-256-3)"),
-        "k_refine_short_batch": ("alu", (6 * T_short + 1) * per_member * pv,
-                                 f"{6 * T_short + 1} directions x {per_member} FP32 ops per (point, view), "
+        "k_start_select_batch": ("alu", per_member * pv, f"1 direction x {per_member} FP32 ops per (point, view), "
                                  f"{pv} point-views"),
+        "k_refine_short_batch": ("alu", (6 * T_short + 1) * per_member * apv,
+                                 f"{6 * T_short + 1} directions x {per_member} FP32 ops per accepted (point, view), "
+                                 f"{apv} point-views"),
         "k_argmin_batch": ("alu", H * per_member * fpv, f"{H} x {per_member} ops per fallback (point, view), {fpv}"),
         "k_refine_batch": ("alu", 6 * T * per_member * fpv, f"{6 * T} x {per_member} ops per fallback (point, view)"),
     }

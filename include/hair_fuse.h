@@ -202,11 +202,12 @@ const char* hair_fuse_mlp_last_error(const hf_mlp* mlp);
 /* Features (N x 64 bf16, kind mem_kind) of the uploaded scene's points. */
 int hair_fuse_features(hf_ctx* ctx, uint16_t* x_out, int mem_kind);
 
-/* Learned fusion of all uploaded points: proposal from the network, then T_short refinement rounds
- * starting with step alpha_short (radians, halved each round) from it; points whose refined cost
- * exceeds tau are fused by the plain path (H hypotheses, T rounds) instead and get status
- * HF_STATUS_FELL_BACK.  Outputs as in hair_fuse_fuse_directions (idx_out = -1 for proposals);
- * n_fallback (host, may be NULL; reading it synchronises) receives the number of fallback points. */
+/* Learned fusion of all uploaded points: proposal from the network and its cost c_i; points whose
+ * proposal cost exceeds tau are fused by the plain path (H hypotheses, T rounds) and get status
+ * HF_STATUS_FELL_BACK; the others get T_short refinement rounds from the proposal, starting with
+ * step alpha_short (radians, halved each round).  Outputs as in hair_fuse_fuse_directions
+ * (idx_out = -1 for refined proposals); n_fallback (host, may be NULL; reading it synchronises)
+ * receives the number of fallback points. */
 int hair_fuse_fuse_learned(hf_ctx* ctx, hf_mlp* mlp, int T_short, float alpha_short, float tau, float* dir_out,
                            float* cost_out, int32_t* idx_out, uint8_t* status_out, int* n_fallback, int mem_kind);
 
@@ -238,7 +239,7 @@ typedef struct hf_batch hf_batch;
 typedef struct {
     int T_short;        /* learned: refinement rounds from the proposal, 1..HF_MAX_T */
     float alpha_short;  /* learned: first rotation step (radians), halved each round */
-    float tau;          /* learned: fallback threshold on the refined proposal's cost */
+    float tau;          /* learned: fallback threshold on the proposal's cost */
     int autotune;       /* 1: at the first run, time the candidate tile shapes on the batch and keep the fastest */
     int hchunk;         /* hypotheses per chunk of the argmin: 0 = tuned / default, else 8, 16 or 32 */
     int points_per_cta; /* points per CTA of argmin and refinement: 0 = tuned / default 128, else 64, 128, 256 */

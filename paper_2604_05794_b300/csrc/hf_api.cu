@@ -56,7 +56,8 @@ int run_project(hf_ctx* c) {
     if (e != cudaSuccess) return hf_cuda_err(c, e, "clear work counter");
     ProjectArgs pa{(const float*)c->pts.p, c->N, (const float*)c->cams.p, c->V, c->W, c->Hh,
                    (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, c->cfg.top_k_views,
-                   (float2*)c->samp.p, (float2*)c->ab.p, (unsigned long long*)c->work.p};
+                   (float2*)c->samp.p, (float2*)c->ab.p, (unsigned long long*)c->work.p, nullptr,
+                   (const float2*)c->amap.p};
     return run_launch(c, "k_project", [&] { return hf_launch_project(pa, c->stream); });
 }
 }  // namespace
@@ -153,11 +154,18 @@ int hair_fuse_upload_views(hf_ctx* c, int V, int width, int height, const float*
     if ((rc = hf_ensure(c, c->cams, (size_t)V * 16 * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->angle, npx * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->conf, npx * cb))) return rc;
+    if ((rc = hf_ensure(c, c->amap, npx * sizeof(float2)))) return rc;
     cudaError_t e = cudaMemcpyAsync(c->cams.p, cams, (size_t)V * 16 * sizeof(float), kind_in(mem_kind), c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->angle.p, angle, npx * sizeof(float), kind_in(mem_kind), c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->conf.p, conf, npx * cb, kind_in(mem_kind), c->stream);
-    if (e == cudaSuccess && mem_kind == HF_HOST) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return hf_cuda_err(c, e, "upload views");
+    // the kernels gather (angle, confidence) pairs: one interleaved copy makes each an 8-byte read
+    if ((rc = run_launch(c, "k_interleave", [&] {
+             return hf_launch_interleave((const float*)c->angle.p, c->conf.p, conf_dtype == HF_F16 ? 1 : 0, npx,
+                                         (float2*)c->amap.p, c->stream);
+         })))
+        return rc;
+    if (mem_kind == HF_HOST && (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return hf_cuda_err(c, e, "upload views");
     c->V = V;
     c->W = width;
     c->Hh = height;
@@ -372,7 +380,7 @@ void hair_fuse_destroy(hf_ctx* c) {
         cudaEventDestroy(r.beg);
         cudaEventDestroy(r.end);
     }
-    DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->pts, &c->nbr, &c->samp, &c->ab, &c->qtab,
+    DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->amap, &c->pts, &c->nbr, &c->samp, &c->ab, &c->qtab,
                       &c->vthr, &c->hyps, &c->rot, &c->outs, &c->evald, &c->errw, &c->work, &c->best, &c->feat, &c->prop, &c->lmisc};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);

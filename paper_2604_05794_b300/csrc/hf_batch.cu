@@ -23,15 +23,16 @@ namespace {
 
 // stage slots of the item counters
 enum { ST_PROJECT, ST_FEATURES, ST_SHORT, ST_SELECT, ST_ARGMIN, ST_MAIN, ST_MLP, ST_COUNT };
-const char* const kStageName[ST_COUNT] = {"k_project_batch", "k_features_batch", "k_refine_short_batch", "k_select_batch",
-                                          "k_argmin_batch", "k_refine_batch", "k_mlp"};
+const char* const kStageName[ST_COUNT] = {"k_project_batch", "k_features_batch", "k_refine_short_batch",
+                                          "k_start_select_batch", "k_argmin_batch", "k_refine_batch", "k_mlp"};
 static_assert(ST_COUNT <= 8, "eight item counters");
 
 // device control block (bytes); [0, kZeroEnd) is cleared by k_prep_batch at the start of a run
 constexpr size_t kNextOff = 0;                                   // u32 [ST_COUNT] (padded to 8)
 constexpr size_t kDoneOff = 32;                                  // u32 [2][HF_MAX_BATCH]: short, main
 constexpr size_t kCountOff = kDoneOff + 2 * HF_MAX_BATCH * 4;    // i32 [HF_MAX_BATCH]: fallback list lengths
-constexpr size_t kWorkOff = kCountOff + HF_MAX_BATCH * 4;        // u64 [HF_MAX_BATCH]: (point, view) pairs
+constexpr size_t kAccOff = kCountOff + HF_MAX_BATCH * 4;         // i32 [HF_MAX_BATCH]: accepted list lengths
+constexpr size_t kWorkOff = kAccOff + HF_MAX_BATCH * 4;          // u64 [HF_MAX_BATCH]: (point, view) pairs
 constexpr size_t kStampOff = kWorkOff + HF_MAX_BATCH * 8;        // u64 [2][HF_MAX_BATCH]: completion times
 constexpr size_t kZeroEnd = kStampOff + 2 * HF_MAX_BATCH * 8;
 constexpr size_t kT0Off = kZeroEnd;                              // u64 batch start
@@ -57,7 +58,7 @@ struct ArgBlock {
     ProjectArgs proj[HF_MAX_BATCH];
     FeatArgs feat[HF_MAX_BATCH];
     FuseArgs shrt[HF_MAX_BATCH];
-    SelectArgs sel[HF_MAX_BATCH];
+    StartSelectArgs ssel[HF_MAX_BATCH];
     FuseArgs main[HF_MAX_BATCH];
 };
 
@@ -80,7 +81,8 @@ struct hf_batch {
     uint16_t* x = nullptr;
     float* prop = nullptr;
     uint16_t* h1 = nullptr;
-    int32_t* list = nullptr;
+    int32_t* list = nullptr;       // fallback points, per scene from its row offset
+    int32_t* acc_list = nullptr;   // accepted proposals, likewise
     cudaGraphExec_t gexec = nullptr;
     long long launches = 0;   // kernels enqueued (graph replays counted by their kernels)
     std::string err;
@@ -121,6 +123,7 @@ int configure(hf_batch* b) {
     const bool learned = b->mlp != nullptr;
     unsigned* box = reinterpret_cast<unsigned*>(b->ctl + kBoxOff);
     int* count = reinterpret_cast<int*>(b->ctl + kCountOff);
+    int* acc = reinterpret_cast<int*>(b->ctl + kAccOff);
     unsigned long long* work = reinterpret_cast<unsigned long long*>(b->ctl + kWorkOff);
     float2* rot_s = reinterpret_cast<float2*>(b->ctl + kRotOff);
     uint32_t* errw = reinterpret_cast<uint32_t*>(b->ctl + kErrOff);
@@ -137,21 +140,27 @@ int configure(hf_batch* b) {
         A.proj[p] = ProjectArgs{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh,
                                 (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0,
                                 c->cfg.top_k_views, (float2*)c->samp.p, (float2*)c->ab.p, work + p,
-                                learned ? box + 6 * p : nullptr};
+                                learned ? box + 6 * p : nullptr, (const float2*)c->amap.p};
         A.feat[p] = FeatArgs{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh,
                              (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, nullptr,
-                             b->x + (size_t)s.off * 64, box + 6 * p};
+                             b->x + (size_t)s.off * 64, box + 6 * p, (const float2*)c->amap.p};
         FuseArgs m{(const float*)c->pts.p, N, (const int32_t*)c->nbr.p, c->k, (const float*)c->cams.p, V,
                    (const float2*)c->samp.p, (const float2*)c->ab.p, (const float4*)c->qtab.p, (const float*)c->vthr.p,
                    (const float*)c->hyps.p, H, Hpad, (const float2*)c->rot.p, T, s.dir, s.cost, s.idx, s.status,
                    bi, (float*)(bi + N), bi + 2 * (size_t)N, hf_fuse_vblock_q(V, b->hc), hf_fuse_vblock_c(V)};
         if (learned) {
-            FuseArgs f = m;
+            // the proposal's cost sorts the points into the fallback and the accepted list
+            FuseArgs sel = m;
+            sel.start_dir = b->prop + (size_t)s.off * 3;
+            sel.list = b->list + s.off;
+            sel.list_count = count + p;
+            A.ssel[p] = StartSelectArgs{sel, b->cfg.tau, b->acc_list + s.off, acc + p};
+            FuseArgs f = sel;
             f.rot = rot_s;
             f.T = b->cfg.T_short;
-            f.start_dir = b->prop + (size_t)s.off * 3;
+            f.list = b->acc_list + s.off;
+            f.list_count = acc + p;
             A.shrt[p] = f;
-            A.sel[p] = SelectArgs{s.cost, bi + 2 * (size_t)N, N, b->cfg.tau, b->list + s.off, count + p};
             m.list = b->list + s.off;
             m.list_count = count + p;
             m.fell_back = 1;
@@ -201,7 +210,7 @@ cudaError_t launch_stage(hf_batch* b, int stage) {
         case ST_MLP:
             return hf_mlp_infer_rows(b->mlp, b->x, b->total, b->h1, b->prop, reinterpret_cast<uint32_t*>(b->ctl + kErrOff), s);
         case ST_SHORT: return hf_launch_refine_batch(A->shrt, ctl_for(b, ST_SHORT, 0), b->kp, b->nt_r, s);
-        case ST_SELECT: return hf_launch_select_batch(A->sel, ctl_for(b, ST_SELECT, -1), s);
+        case ST_SELECT: return hf_launch_start_select_batch(A->ssel, ctl_for(b, ST_SELECT, -1), b->kp, s);
         case ST_ARGMIN: return hf_launch_argmin_batch(A->main, ctl_for(b, ST_ARGMIN, -1), b->kp, b->hc, b->nt_a, s);
         default: return hf_launch_refine_batch(A->main, ctl_for(b, ST_MAIN, 1), b->kp, b->nt_r, s);
     }
@@ -219,7 +228,7 @@ cudaError_t enqueue(hf_batch* b, cudaEvent_t* ev = nullptr, int* stages_out = nu
     if (ev) cudaEventRecord(ev[1], b->stream);
     const bool learned = b->mlp != nullptr;
     const int plain_stages[] = {ST_PROJECT, ST_ARGMIN, ST_MAIN};
-    const int learned_stages[] = {ST_PROJECT, ST_FEATURES, ST_MLP, ST_SHORT, ST_SELECT, ST_ARGMIN, ST_MAIN};
+    const int learned_stages[] = {ST_PROJECT, ST_FEATURES, ST_MLP, ST_SELECT, ST_SHORT, ST_ARGMIN, ST_MAIN};
     const int* st = learned ? learned_stages : plain_stages;
     const int n = learned ? 7 : 3;
     for (int q = 0; q < n && e == cudaSuccess; ++q) {
@@ -238,8 +247,8 @@ int time_stage(hf_batch* b, int stage, int reps, float* ms) {
     float best = INFINITY;
     for (int r = 0; r < reps; ++r) {
         cudaError_t e = cudaMemsetAsync(reinterpret_cast<unsigned*>(b->ctl + kNextOff) + stage, 0, 4, b->stream);
-        // the selection appends to the fallback lists: they start empty
-        if (e == cudaSuccess && stage == ST_SELECT) e = cudaMemsetAsync(b->ctl + kCountOff, 0, HF_MAX_BATCH * 4, b->stream);
+        // the selection appends to the fallback and accepted lists: they start empty
+        if (e == cudaSuccess && stage == ST_SELECT) e = cudaMemsetAsync(b->ctl + kCountOff, 0, 2 * HF_MAX_BATCH * 4, b->stream);
         if (e == cudaSuccess) e = cudaEventRecord(b->t_beg, b->stream);
         if (e == cudaSuccess) e = launch_stage(b, stage);
         if (e == cudaSuccess) e = cudaEventRecord(b->t_end, b->stream);
@@ -276,7 +285,6 @@ int autotune(hf_batch* b) {
         b->nt_r = nt;
         float t = 0.0f, t2 = 0.0f;
         if (learned && (rc = time_stage(b, ST_SHORT, 2, &t2))) return rc;
-        if (learned && (rc = time_stage(b, ST_SELECT, 1, &t))) return rc;   // restores the lists
         if ((rc = time_stage(b, ST_ARGMIN, 1, &t))) return rc;
         if ((rc = time_stage(b, ST_MAIN, 2, &t))) return rc;
         if (t + t2 < best) {
@@ -403,6 +411,7 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
         if (e == cudaSuccess) e = cudaMalloc(&b->prop, (size_t)total * 3 * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&b->h1, (size_t)total * 256 * sizeof(uint16_t));
         if (e == cudaSuccess) e = cudaMalloc(&b->list, (size_t)total * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&b->acc_list, (size_t)total * sizeof(int32_t));
     }
     if (e != cudaSuccess) {
         hair_fuse_batch_destroy(b);
@@ -624,6 +633,7 @@ extern "C" void hair_fuse_batch_destroy(hf_batch* b) {
     cudaFree(b->prop);
     cudaFree(b->h1);
     cudaFree(b->list);
+    cudaFree(b->acc_list);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->t_beg) cudaEventDestroy(b->t_beg);

@@ -36,6 +36,7 @@ struct hf_ctx {
     // views
     int V = 0, W = 0, Hh = 0, conf_dtype = HF_F32;
     DevBuf cams, angle, conf;
+    DevBuf amap;    // [V][H][W] float2 (angle, confidence as f32): one 8-byte read per gathered pixel
     // points
     int N = 0, k = 0;
     DevBuf pts, nbr;
@@ -95,8 +96,12 @@ struct ProjectArgs {
     float2* samp; float2* ab;
     unsigned long long* work;   // += number of (point, view) pairs in the view sets
     unsigned* box_keys;         // optional: bounding-box keys lo[3], hi[3] folded in (see hf_launch_bbox_init)
+    const float2* amap;         // optional: interleaved (angle, confidence) maps, read instead of angle / conf
 };
 cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s);
+// out[i] = (angle[i], conf[i] as f32) for npx pixels
+cudaError_t hf_launch_interleave(const float* angle, const void* conf, int conf_f16, size_t npx, float2* out,
+                                 cudaStream_t s);
 
 struct PrepArgs {
     const float* cams; int V;
@@ -153,17 +158,19 @@ struct FeatArgs {
     const float* box;       // bounding box lo[3], hi[3] (used when box_keys is null)
     uint16_t* x;            // [N x 64] bf16 features
     const unsigned* box_keys;   // bounding box as order-preserving keys lo[3], hi[3], or null
+    const float2* amap;         // optional: interleaved (angle, confidence) maps, read instead of angle / conf
 };
 cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s);
-// cost c_i of a.start_dir and the view count -> a.best_cost, a.nvs (-1 for non-finite points)
-cudaError_t hf_launch_start_cost(const FuseArgs& a, cudaStream_t s);
-struct SelectArgs {
-    const float* cost; const int32_t* nvs; int N; float tau;
-    int32_t* list; int* count;
+// Cost c_i of f.start_dir and the view count -> f.best_cost, f.nvs (-1 for non-finite points, whose
+// BAD_INPUT outputs are written here); points with a view and c_i > tau are appended to f.list
+// (count *f.list_count), the other finite points to acc_list (*acc_count); counts start at 0.
+struct StartSelectArgs {
+    FuseArgs f;
+    float tau;
+    int32_t* acc_list;
+    int* acc_count;
 };
-// points with a view and cost_out > tau -> list (count must start at 0)
-cudaError_t hf_launch_fallback_select(const float* cost, const int32_t* nvs, int N, float tau, int32_t* list, int* count,
-                                      cudaStream_t s);
+cudaError_t hf_launch_start_select(const StartSelectArgs& a, cudaStream_t s);
 // (cos, sin) of alpha0 / 2^t for t < T, in double then rounded
 cudaError_t hf_launch_rot(float2* rot, int T, double alpha0, cudaStream_t s);
 cudaError_t hf_launch_check_nbr(const int32_t* nbr, long long n, int N, uint32_t* errw, cudaStream_t s);
@@ -193,7 +200,7 @@ int hf_batch_kp_for(int k);   // patch width instantiated for the batched kernel
 cudaError_t hf_launch_prep_batch(const PrepArgs* pr, int ns, const BatchReset& r, cudaStream_t s);
 cudaError_t hf_launch_project_batch(const ProjectArgs* pa, const BatchCtl& c, cudaStream_t s);
 cudaError_t hf_launch_features_batch(const FeatArgs* fe, const BatchCtl& c, cudaStream_t s);
-cudaError_t hf_launch_select_batch(const SelectArgs* sa, const BatchCtl& c, cudaStream_t s);
+cudaError_t hf_launch_start_select_batch(const StartSelectArgs* sa, const BatchCtl& c, int kp, cudaStream_t s);
 // nt: points per CTA (64, 128, 256); hc: hypothesis chunk (8, 16, 32; the scenes' Hpad and
 // vblock_q must be built for it); kp from hf_batch_kp_for(max k)
 cudaError_t hf_launch_argmin_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int hc, int nt, cudaStream_t s);

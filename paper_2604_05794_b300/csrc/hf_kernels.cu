@@ -124,45 +124,74 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
     float topc[HF_MAX_TOPK];
     int topv[HF_MAX_TOPK];
     int ntop = 0, nset = 0;
-    for (int v = 0; v < a.V; ++v) {
-        const float* cam = a.cams + 16 * v;
-        const float fx = __ldg(cam), fy = __ldg(cam + 1), cx = __ldg(cam + 2), cy = __ldg(cam + 3);
-        ff X0 = ff_dot3_plus(__ldg(cam + 4), __ldg(cam + 5), __ldg(cam + 6), p0, p1, p2, __ldg(cam + 13));
-        ff X1 = ff_dot3_plus(__ldg(cam + 7), __ldg(cam + 8), __ldg(cam + 9), p0, p1, p2, __ldg(cam + 14));
-        ff X2 = ff_dot3_plus(__ldg(cam + 10), __ldg(cam + 11), __ldg(cam + 12), p0, p1, p2, __ldg(cam + 15));
-        bool vis = X2.hi > 1e-6f;
-        float2 s = make_float2(0.0f, 0.0f), r = make_float2(qnan, qnan);
-        if (vis) {
-            ff ra = ff_div(X0, X2), rb = ff_div(X1, X2);
-            float fu = ff_floor(ff_affine(fx, ra, cx));
-            float fv = ff_floor(ff_affine(fy, rb, cy));
-            vis = fu >= 0.0f && fu < (float)a.W && fv >= 0.0f && fv < (float)a.H;
-            if (vis) {
-                const size_t o = (size_t)v * npx + (size_t)fv * a.W + (size_t)fu;
-                const float th = __ldg(a.angle + o);
-                const float C = load_conf(a.conf, a.conf_f16, o);
+    // views in groups of four: the pixel decisions first, then the four gathers in flight together
+    constexpr int G = 4;
+    for (int v0 = 0; v0 < a.V; v0 += G) {
+        long long off[G];
+        float ra_[G], rb_[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            off[q] = -1;
+            ra_[q] = rb_[q] = qnan;
+            const int v = v0 + q;
+            if (v >= a.V) continue;
+            const float* cam = a.cams + 16 * v;
+            const float fx = __ldg(cam), fy = __ldg(cam + 1), cx = __ldg(cam + 2), cy = __ldg(cam + 3);
+            const ff X0 = ff_dot3_plus(__ldg(cam + 4), __ldg(cam + 5), __ldg(cam + 6), p0, p1, p2, __ldg(cam + 13));
+            const ff X1 = ff_dot3_plus(__ldg(cam + 7), __ldg(cam + 8), __ldg(cam + 9), p0, p1, p2, __ldg(cam + 14));
+            const ff X2 = ff_dot3_plus(__ldg(cam + 10), __ldg(cam + 11), __ldg(cam + 12), p0, p1, p2, __ldg(cam + 15));
+            if (!(X2.hi > 1e-6f)) continue;
+            const ff ra = ff_div(X0, X2), rb = ff_div(X1, X2);
+            const float fu = ff_floor(ff_affine(fx, ra, cx));
+            const float fv = ff_floor(ff_affine(fy, rb, cy));
+            if (!(fu >= 0.0f && fu < (float)a.W && fv >= 0.0f && fv < (float)a.H)) continue;
+            off[q] = (long long)((size_t)v * npx + (size_t)fv * a.W + (size_t)fu);
+            ra_[q] = ra.hi;
+            rb_[q] = rb.hi;
+        }
+        float th[G], C[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            th[q] = C[q] = 0.0f;
+            if (off[q] < 0) continue;
+            if (a.amap) {
+                const float2 t = __ldg(a.amap + off[q]);
+                th[q] = t.x;
+                C[q] = t.y;
+            } else {
+                th[q] = __ldg(a.angle + off[q]);
+                C[q] = load_conf(a.conf, a.conf_f16, (size_t)off[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int v = v0 + q;
+            if (v >= a.V) break;
+            float2 sv = make_float2(0.0f, 0.0f), r = make_float2(qnan, qnan);
+            if (off[q] >= 0) {
                 float sn, cs;
-                sincosf(th, &sn, &cs);
-                s = make_float2(C * cs, C * sn);
-                r = make_float2(ra.hi, rb.hi);
+                sincosf(th[q], &sn, &cs);
+                sv = make_float2(C[q] * cs, C[q] * sn);
+                r = make_float2(ra_[q], rb_[q]);
                 ++nset;
                 if (TOPK) {
                     // keep the top_k (conf desc, view asc); later views need a strictly larger conf
-                    if (ntop < a.top_k || C > topc[ntop - 1]) {
+                    const float c = C[q];
+                    if (ntop < a.top_k || c > topc[ntop - 1]) {
                         int pos = ntop < a.top_k ? ntop++ : ntop - 1;
-                        while (pos > 0 && C > topc[pos - 1]) {
+                        while (pos > 0 && c > topc[pos - 1]) {
                             topc[pos] = topc[pos - 1];
                             topv[pos] = topv[pos - 1];
                             --pos;
                         }
-                        topc[pos] = C;
+                        topc[pos] = c;
                         topv[pos] = v;
                     }
                 }
             }
+            a.samp[(size_t)v * a.N + i] = sv;
+            a.ab[(size_t)v * a.N + i] = r;
         }
-        a.samp[(size_t)v * a.N + i] = s;
-        a.ab[(size_t)v * a.N + i] = r;
     }
     if (TOPK) {
         for (int v = 0; v < a.V; ++v) {
@@ -181,6 +210,12 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
 template <bool TOPK>
 __global__ void __launch_bounds__(kProjectThreads) k_project(ProjectArgs a) {
     project_tile<TOPK>(a, blockIdx.x);
+}
+
+__global__ void k_interleave(const float* __restrict__ angle, const void* __restrict__ conf, int f16, size_t npx,
+                             float2* __restrict__ out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npx; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = make_float2(angle[i], load_conf(conf, f16, i));
 }
 
 // ------------------------------------------------------------------ per-scene constants
@@ -482,7 +517,7 @@ __device__ __forceinline__ void refine_tile(const FuseArgs& a, int blk, unsigned
         if (from_start && a.T > 0) {
             const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
             nv = (isfinite(p0) && isfinite(p1) && isfinite(p2)) ? 0 : -1;
-        } else {   // from k_argmin, or (no rounds) from k_start_cost
+        } else {   // from k_argmin, or (no rounds) from k_start_select
             nv = a.nvs[i];
         }
     }
@@ -634,10 +669,13 @@ __device__ __forceinline__ void features_tile(const FeatArgs& a, int blk) {
     uint16_t f[64];
 #pragma unroll
     for (int q = 0; q < 64; ++q) f[q] = 0;
+    // all 16 pixel decisions first, then the 16 gathers in flight together, then the features
+    long long off[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
         const int v = (m * a.V) / 16;
         const float* cam = a.cams + 16 * v;
+        off[m] = -1;
         const ff X0 = ff_dot3_plus(cam[4], cam[5], cam[6], p0, p1, p2, cam[13]);
         const ff X1 = ff_dot3_plus(cam[7], cam[8], cam[9], p0, p1, p2, cam[14]);
         const ff X2 = ff_dot3_plus(cam[10], cam[11], cam[12], p0, p1, p2, cam[15]);
@@ -645,12 +683,31 @@ __device__ __forceinline__ void features_tile(const FeatArgs& a, int blk) {
         const float fu = ff_floor(ff_affine(cam[0], ff_div(X0, X2), cam[2]));
         const float fv = ff_floor(ff_affine(cam[1], ff_div(X1, X2), cam[3]));
         if (!(fu >= 0.0f && fu < (float)a.W && fv >= 0.0f && fv < (float)a.H)) continue;
-        const size_t o = (size_t)v * npx + (size_t)fv * a.W + (size_t)fu;
+        off[m] = (long long)((size_t)v * npx + (size_t)fv * a.W + (size_t)fu);
+    }
+    float th[16], C[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        th[m] = 0.0f;
+        C[m] = 0.0f;
+        if (off[m] < 0) continue;
+        if (a.amap) {
+            const float2 t = __ldg(a.amap + off[m]);
+            th[m] = t.x;
+            C[m] = t.y;
+        } else {
+            th[m] = a.angle[off[m]];
+            C[m] = load_conf(a.conf, a.conf_f16, (size_t)off[m]);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        if (off[m] < 0) continue;
         float s2, c2;
-        sincosf(2.0f * a.angle[o], &s2, &c2);
+        sincosf(2.0f * th[m], &s2, &c2);
         f[3 * m] = __bfloat16_as_ushort(__float2bfloat16_rn(s2));
         f[3 * m + 1] = __bfloat16_as_ushort(__float2bfloat16_rn(c2));
-        f[3 * m + 2] = __bfloat16_as_ushort(__float2bfloat16_rn(load_conf(a.conf, a.conf_f16, o)));
+        f[3 * m + 2] = __bfloat16_as_ushort(__float2bfloat16_rn(C[m]));
     }
     float b[6];
 #pragma unroll
@@ -678,55 +735,92 @@ __device__ __forceinline__ void features_tile(const FeatArgs& a, int blk) {
 
 __global__ void __launch_bounds__(kFeatThreads) k_features(FeatArgs a) { features_tile(a, blockIdx.x); }
 
+// Cost c_i of the proposal (a.start_dir) and the fallback decision: points with a view and
+// c_i > tau go to the fallback list (a.list), the others to the accepted list (s.acc_list), in
+// the order warps append them; non-finite points get their BAD_INPUT outputs here and no list.
+// best_cost / nvs receive c_i and |V_i| (the refinement's zero-round outputs).
+constexpr int kStartThreads = 128;
+
+// One direction per view: the next view's (a, b) and patch samples are loaded while the current
+// view is evaluated (register double buffering; loads of views outside V_i are harmless reads).
 template <int KP>
-__global__ void __launch_bounds__(128) k_start_cost(FuseArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.N) return;
-    const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
-    if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) {
-        a.nvs[i] = -1;
-        return;
+__device__ __forceinline__ void start_select_tile(const StartSelectArgs& s, int blk) {
+    const FuseArgs& a = s.f;
+    const int tid = threadIdx.x;
+    const int i = blk * kStartThreads + tid;
+    const bool in = i < a.N;
+    bool bad = false;
+    if (in) {
+        const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
+        bad = !(isfinite(p0) && isfinite(p1) && isfinite(p2));
     }
-    int nb[KP];
-    nb[0] = i;
-#pragma unroll
-    for (int j = 1; j < KP; ++j) nb[j] = (j - 1) < a.k ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
-    const float d0 = a.start_dir[3 * i], d1 = a.start_dir[3 * i + 1], d2 = a.start_dir[3 * i + 2];
+    const bool active = in && !bad;
     float acc = 0.0f;
     int nv = 0;
-    for (int v = 0; v < a.V; ++v) {
-        const size_t base = (size_t)v * a.N;
-        const float2 r = a.ab[base + i];
-        if (r.x != r.x) continue;
-        ++nv;
-        float2 s[KP];
-        load_patch<KP>(a.samp, base, i, nb, s);
-        const float* cam = a.cams + 16 * v;
-        const float j0 = cam[0] * fmaf(-r.x, cam[10], cam[4]), j1 = cam[0] * fmaf(-r.x, cam[11], cam[5]),
-                    j2 = cam[0] * fmaf(-r.x, cam[12], cam[6]);
-        const float j3 = cam[1] * fmaf(-r.y, cam[10], cam[7]), j4 = cam[1] * fmaf(-r.y, cam[11], cam[8]),
-                    j5 = cam[1] * fmaf(-r.y, cam[12], cam[9]);
-        acc += view_term<KP>(fmaf(j0, d0, fmaf(j1, d1, j2 * d2)), fmaf(j3, d0, fmaf(j4, d1, j5 * d2)), s, a.vthr[v]);
+    if (active) {
+        int nb[KP];
+        nb[0] = i;
+#pragma unroll
+        for (int j = 1; j < KP; ++j) nb[j] = (j - 1) < a.k ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
+        const float d0 = a.start_dir[3 * i], d1 = a.start_dir[3 * i + 1], d2 = a.start_dir[3 * i + 2];
+        float2 rn = a.ab[i];
+        float2 sn[KP];
+        load_patch<KP>(a.samp, 0, i, nb, sn);
+        for (int v = 0; v < a.V; ++v) {
+            const float2 r = rn;
+            float2 sm[KP];
+#pragma unroll
+            for (int j = 0; j < KP; ++j) sm[j] = sn[j];
+            if (v + 1 < a.V) {
+                const size_t nxt = (size_t)(v + 1) * a.N;
+                rn = a.ab[nxt + i];
+                load_patch<KP>(a.samp, nxt, i, nb, sn);
+            }
+            if (r.x != r.x) continue;
+            ++nv;
+            const float* cam = a.cams + 16 * v;
+            // Z times the projection Jacobian, rounded as in the refinement's round 0
+            const float j0 = cam[0] * fmaf(-r.x, cam[10], cam[4]), j1 = cam[0] * fmaf(-r.x, cam[11], cam[5]),
+                        j2 = cam[0] * fmaf(-r.x, cam[12], cam[6]);
+            const float j3 = cam[1] * fmaf(-r.y, cam[10], cam[7]), j4 = cam[1] * fmaf(-r.y, cam[11], cam[8]),
+                        j5 = cam[1] * fmaf(-r.y, cam[12], cam[9]);
+            acc += view_term<KP>(fmaf(j0, d0, fmaf(j1, d1, j2 * d2)), fmaf(j3, d0, fmaf(j4, d1, j5 * d2)), sm,
+                                 a.vthr[v]);
+        }
     }
-    a.best_cost[i] = nv ? 1.0f - acc / (float)nv : 1.0f;
-    a.nvs[i] = nv;
+    const float c0 = nv ? 1.0f - acc / (float)nv : 1.0f;
+    if (active) {
+        a.best_cost[i] = c0;
+        a.nvs[i] = nv;
+    } else if (in) {
+        a.nvs[i] = -1;
+        a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
+        if (a.cost_out) a.cost_out[i] = __int_as_float(0x7fc00000);
+        if (a.idx_out) a.idx_out[i] = -1;
+        if (a.status_out) a.status_out[i] = HF_STATUS_BAD_INPUT;
+    }
+    const bool fb = active && nv > 0 && c0 > s.tau;
+    const bool ok = active && !fb;
+    const int lane = tid & 31;
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {   // warp-aggregated appends: fallback, then accepted
+        const bool want = q == 0 ? fb : ok;
+        const unsigned m = __ballot_sync(0xffffffffu, want);
+        if (!m) continue;
+        const int leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(q == 0 ? const_cast<int*>(a.list_count) : s.acc_count, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (want) (q == 0 ? const_cast<int32_t*>(a.list) : s.acc_list)[base + __popc(m & below)] = i;
+    }
 }
 
-constexpr int kSelectThreads = 256;
-
-__device__ __forceinline__ void select_tile(const SelectArgs& a, int blk) {
-    const int i = blk * kSelectThreads + threadIdx.x;
-    const bool want = i < a.N && a.nvs[i] > 0 && a.cost[i] > a.tau;
-    const unsigned m = __ballot_sync(0xffffffffu, want);
-    if (!m) return;
-    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(a.count, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (want) a.list[base + __popc(m & ((1u << lane) - 1u))] = i;
+template <int KP>
+__global__ void __launch_bounds__(kStartThreads) k_start_select(StartSelectArgs s) {
+    start_select_tile<KP>(s, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kSelectThreads) k_fallback_select(SelectArgs a) { select_tile(a, blockIdx.x); }
 
 __global__ void k_rot(float2* rot, int T, double alpha0) {
     const int t = threadIdx.x;
@@ -855,9 +949,11 @@ __global__ void __launch_bounds__(kFeatThreads) k_features_batch(const FeatArgs*
                               [](const FeatArgs& a, int blk) { features_tile(a, blk); });
 }
 
-__global__ void __launch_bounds__(kSelectThreads) k_select_batch(const SelectArgs* __restrict__ sa, BatchCtl c) {
-    batch_tiles<kSelectThreads>(sa, c, [](const SelectArgs& a) { return a.N; },
-                                [](const SelectArgs& a, int blk) { select_tile(a, blk); });
+template <int KP>
+__global__ void __launch_bounds__(kStartThreads) k_start_select_batch(const StartSelectArgs* __restrict__ sa,
+                                                                      BatchCtl c) {
+    batch_tiles<kStartThreads>(sa, c, [](const StartSelectArgs& a) { return a.f.N; },
+                               [](const StartSelectArgs& a, int blk) { start_select_tile<KP>(a, blk); });
 }
 
 // Per-scene constants of every scene (block = scene), the batch's counters cleared, empty bounding
@@ -1009,6 +1105,14 @@ cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t hf_launch_interleave(const float* angle, const void* conf, int conf_f16, size_t npx, float2* out,
+                                 cudaStream_t s) {
+    if (!npx) return cudaSuccess;
+    const size_t blocks = (npx + 255) / 256;
+    k_interleave<<<(unsigned)(blocks < 148 * 16 ? blocks : 148 * 16), 256, 0, s>>>(angle, conf, conf_f16, npx, out);
+    return cudaGetLastError();
+}
+
 cudaError_t hf_launch_prep(const PrepArgs& a, cudaStream_t s) {
     k_prep<<<1, 256, 0, s>>>(a);
     return cudaGetLastError();
@@ -1059,25 +1163,23 @@ cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t hf_launch_start_cost(const FuseArgs& a, cudaStream_t s) {
-    const dim3 grid((a.N + 127) / 128), block(128);
-    switch (kp_for(a.k)) {
-        case 1: k_start_cost<1><<<grid, block, 0, s>>>(a); break;
-        case 4: k_start_cost<4><<<grid, block, 0, s>>>(a); break;
-        case 6: k_start_cost<6><<<grid, block, 0, s>>>(a); break;
-        case 9: k_start_cost<9><<<grid, block, 0, s>>>(a); break;
-        case 12: k_start_cost<12><<<grid, block, 0, s>>>(a); break;
-        default: k_start_cost<17><<<grid, block, 0, s>>>(a); break;
-    }
+template <int KP>
+cudaError_t launch_start_select(const StartSelectArgs& a, cudaStream_t s) {
+    k_start_select<KP><<<(a.f.N + kStartThreads - 1) / kStartThreads, kStartThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t hf_launch_fallback_select(const float* cost, const int32_t* nvs, int N, float tau, int32_t* list, int* count,
-                                      cudaStream_t s) {
-    const SelectArgs a{cost, nvs, N, tau, list, count};
-    k_fallback_select<<<(N + kSelectThreads - 1) / kSelectThreads, kSelectThreads, 0, s>>>(a);
-    return cudaGetLastError();
+cudaError_t hf_launch_start_select(const StartSelectArgs& a, cudaStream_t s) {
+    switch (kp_for(a.f.k)) {
+        case 1: return launch_start_select<1>(a, s);
+        case 4: return launch_start_select<4>(a, s);
+        case 6: return launch_start_select<6>(a, s);
+        case 9: return launch_start_select<9>(a, s);
+        case 12: return launch_start_select<12>(a, s);
+        default: return launch_start_select<17>(a, s);
+    }
 }
+
 
 cudaError_t hf_launch_rot(float2* rot, int T, double alpha0, cudaStream_t s) {
     if (T <= 0) return cudaSuccess;
@@ -1114,11 +1216,20 @@ cudaError_t hf_launch_features_batch(const FeatArgs* fe, const BatchCtl& c, cuda
     return cudaGetLastError();
 }
 
-cudaError_t hf_launch_select_batch(const SelectArgs* sa, const BatchCtl& c, cudaStream_t s) {
+template <int KP>
+cudaError_t launch_start_select_batch(const StartSelectArgs* sa, const BatchCtl& c, cudaStream_t s) {
     static int grid = 0;
-    if (!grid) grid = persistent_grid(k_select_batch, kSelectThreads, 0);
-    k_select_batch<<<grid, kSelectThreads, 0, s>>>(sa, c);
+    if (!grid) grid = persistent_grid(k_start_select_batch<KP>, kStartThreads, 0);
+    k_start_select_batch<KP><<<grid, kStartThreads, 0, s>>>(sa, c);
     return cudaGetLastError();
+}
+
+cudaError_t hf_launch_start_select_batch(const StartSelectArgs* sa, const BatchCtl& c, int kp, cudaStream_t s) {
+    switch (kp) {
+        case 4: return launch_start_select_batch<4>(sa, c, s);
+        case 9: return launch_start_select_batch<9>(sa, c, s);
+        default: return launch_start_select_batch<17>(sa, c, s);
+    }
 }
 
 cudaError_t hf_launch_argmin_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int hc, int nt, cudaStream_t s) {

@@ -425,7 +425,7 @@ extern "C" int hair_fuse_features(hf_ctx* c, uint16_t* x_out, int mem_kind) {
     uint16_t* x = mem_kind == HF_HOST ? (uint16_t*)c->feat.p : x_out;
     cudaError_t e = hf_launch_bbox((const float*)c->pts.p, c->N, box, c->stream);
     FeatArgs fa{(const float*)c->pts.p, c->N, (const float*)c->cams.p, c->V, c->W, c->Hh, (const float*)c->angle.p,
-                c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, box, x};
+                c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, box, x, nullptr, (const float2*)c->amap.p};
     if (e == cudaSuccess) e = hf_launch_features(fa, c->stream);
     c->launches += 2;
     if (e == cudaSuccess && mem_kind == HF_HOST)
@@ -464,9 +464,11 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     if ((rc = ensure_h1(m, N))) return rc;
     char* lm = (char*)c->lmisc.p;
     float* box = (float*)lm;
-    int* count = (int*)(lm + 64);
+    int* count = (int*)(lm + 64);       // fallback points
+    int* acc_count = (int*)(lm + 68);   // accepted proposals
     float2* rot_s = (float2*)(lm + 128);
     int32_t* list = (int32_t*)(lm + 256 + 64 * 8);
+    int32_t* acc_list = list + N;
     char* so = (char*)c->outs.p;
     float* d_dir = mem_kind == HF_HOST ? (float*)so : dir_out;
     float* d_cost = (mem_kind == HF_HOST || !cost_out) ? (float*)(so + (size_t)N * 12) : cost_out;
@@ -488,11 +490,11 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     // the projection also folds the points into the bounding box the features are normalised by
     ProjectArgs pa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p,
                    c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, c->cfg.top_k_views, (float2*)c->samp.p, (float2*)c->ab.p,
-                   (unsigned long long*)c->work.p, box_keys};
+                   (unsigned long long*)c->work.p, box_keys, (const float2*)c->amap.p};
     if ((rc = run_launch(c, "k_project", [&] { return hf_launch_project(pa, s); }))) return rc;
     // proposal: features -> network
     FeatArgs fa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p, c->conf.p,
-                c->conf_dtype == HF_F16 ? 1 : 0, nullptr, (uint16_t*)c->feat.p, box_keys};
+                c->conf_dtype == HF_F16 ? 1 : 0, nullptr, (uint16_t*)c->feat.p, box_keys, (const float2*)c->amap.p};
     if ((rc = run_launch(c, "k_features", [&] { return hf_launch_features(fa, s); }))) return rc;
     if ((rc = run_launch(c, "k_mlp", [&] {
              return hf_mlp_infer(m->d, m->P, (const uint16_t*)c->feat.p, N, m->h1, (float*)c->prop.p,
@@ -505,26 +507,26 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
                 (const float*)c->hyps.p, H, Hpad, rot_s, T_short, d_dir, d_cost, d_idx, d_status,
                 bi, (float*)(bi + N), bi + 2 * (size_t)N, hf_fuse_vblock_q(V, hc), hf_fuse_vblock_c(V)};
     fl.start_dir = (const float*)c->prop.p;
-    // with T_short >= 1 the refinement takes the start cost in its first round
-    if ((rc = run_launch(c, "k_start_cost", [&] {
-             cudaError_t e2 = hf_launch_rot(rot_s, T_short, (double)alpha_short, s);
-             return (e2 != cudaSuccess || T_short > 0) ? e2 : hf_launch_start_cost(fl, s);
+    // the proposal's cost decides: above tau -> the plain fusion (fallback list), else the short
+    // refinement from the proposal (accepted list)
+    fl.list = list;
+    fl.list_count = count;
+    const StartSelectArgs ss{fl, tau, acc_list, acc_count};
+    if ((rc = run_launch(c, "k_start_select", [&] {
+             cudaError_t e2 = cudaMemsetAsync(count, 0, 2 * sizeof(int), s);
+             if (e2 == cudaSuccess) e2 = hf_launch_rot(rot_s, T_short, (double)alpha_short, s);
+             return e2 != cudaSuccess ? e2 : hf_launch_start_select(ss, s);
          })))
         return rc;
-    if ((rc = run_launch(c, "k_refine_short", [&] { return hf_launch_refine(fl, s); }))) return rc;
-    // points whose refined proposal costs more than tau: the plain fusion on the compacted list
+    FuseArgs fs = fl;
+    fs.list = acc_list;
+    fs.list_count = acc_count;
+    if ((rc = run_launch(c, "k_refine_short", [&] { return hf_launch_refine(fs, s); }))) return rc;
     FuseArgs fb = fl;
     fb.start_dir = nullptr;
     fb.rot = (const float2*)c->rot.p;
     fb.T = T;
-    fb.list = list;
-    fb.list_count = count;
     fb.fell_back = 1;
-    if ((rc = run_launch(c, "k_fallback_select", [&] {
-             cudaError_t e2 = cudaMemsetAsync(count, 0, sizeof(int), s);
-             return e2 != cudaSuccess ? e2 : hf_launch_fallback_select(d_cost, bi + 2 * (size_t)N, N, tau, list, count, s);
-         })))
-        return rc;
     if ((rc = run_launch(c, "k_argmin_fallback", [&] { return hf_launch_argmin(fb, hc, s); }))) return rc;
     if ((rc = run_launch(c, "k_refine_fallback", [&] { return hf_launch_refine(fb, s); }))) return rc;
     if (mem_kind == HF_HOST) {

@@ -3,7 +3,7 @@
 The network is trained on directions the plain fusion itself produces: for each training scene the
 plain GPU fusion gives the targets and the library computes the features; a seeded subset of the
 points forms the training set.  The fallback threshold tau is calibrated on a training scene so that
-the points it accepts stay close to the plain result.
+the points it accepts (proposal cost at most tau, then refined) stay close to the plain result.
 """
 import numpy as np
 
@@ -76,19 +76,36 @@ def learned_no_fallback(sc, net, H, T, T_short, alpha_short, dev):
     return d, c
 
 
+def proposal_costs(sc, net, H, T, dev):
+    """(proposals (N, 3), their costs (N,)) of a scene: the quantity the fallback threshold applies to."""
+    import torch
+    t = scene_tensors(sc, dev)
+    N = sc["N"]
+    with HairFuse(H, sc["k"], T) as f:
+        f.upload_views(t["cams"], t["angle"], t["conf"])
+        f.upload_points(t["points"], t["nbr"])
+        x = f.features(torch.empty((N, 64), dtype=torch.int16, device=dev))
+        prop = net.forward(x)
+        c0 = torch.empty((N, 1), device=dev)
+        f.eval_costs(prop.view(N, 1, 3).contiguous(), c0)
+        f.sync()
+    return prop, c0[:, 0]
+
+
 def calibrate_tau(sc, net, H, T, T_short, alpha_short, dev, median_deg=1.0, p95_deg=5.0):
-    """Largest tau (fewest fallbacks) whose accepted points, with fallback points counted as exact,
-    keep the angular error against the plain fusion within median_deg and p95_deg."""
+    """Largest tau on the proposal cost (fewest fallbacks) for which the accepted points, refined
+    from their proposals, with fallback points counted as exact, keep the angular error against the
+    plain fusion within median_deg and p95_deg."""
     plain, plain_cost, _ = plain_and_features(sc, H, T, dev)
-    d, c = learned_no_fallback(sc, net, H, T, T_short, alpha_short, dev)
+    d, _ = learned_no_fallback(sc, net, H, T, T_short, alpha_short, dev)
+    _, c0 = proposal_costs(sc, net, H, T, dev)
     err = angle_deg(d.cpu().numpy(), plain.cpu().numpy())
-    cost = c.cpu().numpy()
-    order = np.argsort(cost)
+    cost = c0.cpu().numpy()
     best = float(np.min(cost)) - 1e-6
-    for q in np.linspace(1.0, 0.0, 201):
+    for q in np.linspace(1.0, 0.0, 401):
         tau = float(np.quantile(cost, q))
         e = np.where(cost <= tau, err, 0.0)
         if np.median(e) <= median_deg and np.percentile(e, 95) <= p95_deg:
             best = tau
             break
-    return best, dict(err=err, cost=cost, plain_cost=plain_cost.cpu().numpy(), order=order)
+    return best, dict(err=err, cost=cost, plain_cost=plain_cost.cpu().numpy())

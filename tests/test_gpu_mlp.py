@@ -146,7 +146,8 @@ def test_learned_fusion_matches_oracle(tiny):
     Xo = om.from_bits(om.bf16_bits(oracle.features(osc)))
     prop_o, _ = om.forward(P, Xo)
     ref_o = oracle.refine(osc, prop_o, Ts, alpha_s)
-    tau = float(np.median(ref_o["cost"]))
+    c0_o = oracle.eval_costs(osc, prop_o[:, None, :])[:, 0]   # the proposal's own cost decides
+    tau = float(np.median(c0_o))
     out = dict(dir=np.empty((N, 3), np.float32), cost=np.empty(N, np.float32), idx=np.empty(N, np.int32),
                status=np.empty(N, np.uint8))
     with hf.HairFuse(H, tiny["k"], T) as f:
@@ -157,10 +158,10 @@ def test_learned_fusion_matches_oracle(tiny):
     fell = out["status"] == hf.HF_STATUS_FELL_BACK
     assert nf == int(fell.sum()) and 0.2 < fell.mean() < 0.8
     # the branch taken agrees with the oracle's except near the threshold
-    decided = np.abs(ref_o["cost"] - tau) > 1e-4
-    assert np.mean((fell == (ref_o["cost"] > tau))[decided]) > 0.99
+    decided = np.abs(c0_o - tau) > 1e-4
+    assert np.mean((fell == (c0_o > tau))[decided]) > 0.99
     # fallback points: the plain fusion (same checks as the plain parity tests)
-    fb = np.nonzero(fell & decided & (ref_o["cost"] > tau))[0]
+    fb = np.nonzero(fell & decided & (c0_o > tau))[0]
     hyps = hf.fibonacci_hemisphere(H)
     orc = oracle.fuse(osc, hyps, T, idx=fb)
     gpu = {k: v for k, v in out.items()}
