@@ -27,6 +27,23 @@ constexpr int kMaxStages = 3;   // ring depth: min(3, K chunks per CTA), set at 
 constexpr uint32_t kATileBytes = 128 * 128;   // 128 rows x 64 bf16
 
 __device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26: for z >= 0,
+// erf z = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-z^2), t = 1 / (1 + p z), with
+// |error| <= 1.5e-7; odd in z.  Hardware reciprocal and exponential (about 1e-6 more).  Used by
+// the inference epilogues, where the result is rounded to bf16 (relative spacing 3.9e-3).
+__device__ __forceinline__ float erf_as(float x) {
+    const float z = fabsf(x);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
+    float p = fmaf(1.061405429f, t, -1.453152027f);
+    p = fmaf(p, t, 1.421413741f);
+    p = fmaf(p, t, -0.284496736f);
+    p = fmaf(p, t, 0.254829592f);
+    const float r = fmaf(-p * t, __expf(-z * z), 1.0f);
+    return copysignf(r, x);
+}
+
+__device__ __forceinline__ float gelu_as(float x) { return 0.5f * x * (1.0f + erf_as(x * 0.70710678118654752f)); }
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
@@ -203,12 +220,12 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
             } else if constexpr (EPI == EPI_GELU) {
                 uint16_t h[16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) h[q] = bf16_bits(gelu_erf(v[q] + consts[c0 + q]));
+                for (int q = 0; q < 16; ++q) h[q] = bf16_bits(gelu_as(v[q] + consts[c0 + q]));
                 st_bf16x16(g.H + (size_t)row * g.ldh + n, h, vec);
             } else {   // EPI_HEAD: h2 = bf16(gelu(z2)), y = W3 h2 (FP32, in column order within each half)
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const float h = bf16_round(gelu_erf(v[q] + consts[c0 + q]));
+                    const float h = bf16_round(gelu_as(v[q] + consts[c0 + q]));
                     y0 = fmaf(consts[BN + n + q], h, y0);
                     y1 = fmaf(consts[BN + 256 + n + q], h, y1);
                     y2 = fmaf(consts[BN + 512 + n + q], h, y2);
