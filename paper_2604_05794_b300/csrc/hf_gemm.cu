@@ -263,6 +263,243 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
     if (warp == 0) tmem_dealloc(tmem, tmem_cols<BN>());
 }
 
+// ---------------------------------------------------------------- persistent inference GEMM
+// C = A . B^T with N = 256 and K <= 256 for the proposal network's inference (EPI_GELU, EPI_HEAD):
+// one CTA per SM walks the 128-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...  B (the layer's
+// weights, K/64 chunks of 256 x 64) stays in shared memory; A streams through a three-stage TMA
+// ring; the accumulator is double-buffered in tensor memory (2 x 256 columns), so the MMAs of the
+// next tile run while the epilogue drains the previous one.  Warp 16 (one thread) issues the TMA
+// loads and the MMAs; warps 0-7 drain the even tiles (buffer 0), warps 8-15 the odd ones (buffer
+// 1): warp w reads TMEM lane quarter w % 4 (rows) and column half (w / 4) % 2.  For the head, the
+// second column half hands its partial 256->3 sums to the first through shared memory (two
+// mbarriers per group).  All waits are bounded; on expiry the CTA records HF_DEV_ERR_TIMEOUT and
+// winds down.
+constexpr int kPStages = 3;
+constexpr int kPThreads = 17 * 32;
+constexpr uint32_t kPBChunk = 256 * 128;   // 256 rows x 64 bf16
+
+template <int EPI>
+__global__ void __launch_bounds__(kPThreads, 1) k_gemm_persist(const __grid_constant__ CUtensorMap ta,
+                                                               const __grid_constant__ CUtensorMap tb, GemmArgs g) {
+    extern __shared__ unsigned char smem_raw[];
+    const int nk = g.K / 64;
+    unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
+    unsigned char* sB = base;                                  // nk x 32 KB
+    unsigned char* sA = sB + nk * kPBChunk;                     // kPStages x 16 KB
+    uint64_t* afull = reinterpret_cast<uint64_t*>(sA + kPStages * kATileBytes);
+    uint64_t* aempty = afull + kPStages;
+    uint64_t* bfull = aempty + kPStages;
+    uint64_t* accf = bfull + 1;    // [2] MMA -> epilogue group
+    uint64_t* acce = accf + 2;     // [2] epilogue group (8 warps) -> MMA
+    uint64_t* hbar = acce + 2;     // [2] head: second column half wrote its partial sums (4 warps)
+    uint64_t* hfree = hbar + 2;    // [2] head: first column half read them (4 warps)
+    uint64_t* done = hfree + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    float* consts = reinterpret_cast<float*>(tslot + 4);   // bias [256] (and W3 [3][256], b3 [3] for the head)
+    float* part = consts + 256 + 3 * 256 + 4;              // head: [2 groups][128 rows][3]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles = (g.M + 127) / 128;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kPStages; ++s) {
+            mbar_init(afull + s, 1);
+            mbar_init(aempty + s, 1);
+        }
+        mbar_init(bfull, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf + b, 1);
+            mbar_init(acce + b, 8);
+            mbar_init(hbar + b, 4);
+            mbar_init(hfree + b, 4);
+        }
+        mbar_init(done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tslot, 512);
+        tmem_relinquish();
+    }
+    for (int q = threadIdx.x; q < 256; q += blockDim.x) consts[q] = g.bias ? g.bias[q] : 0.0f;
+    if constexpr (EPI == EPI_HEAD)
+        for (int q = threadIdx.x; q < 3 * 256 + 3; q += blockDim.x) consts[256 + q] = q < 768 ? g.w3[q] : g.b3[q - 768];
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 16) {
+        if (lane == 0) {
+            bool ok = true;
+            const uint32_t idesc = idesc_bf16_f32(128, 256);
+            const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+            const long long total = (long long)my_tiles * nk;
+            long long g_load = 0, g_use = 0;
+            // the weights, once
+            mbar_expect_tx(bfull, nk * kPBChunk);
+            for (int c = 0; c < nk; ++c) tma_load_2d(sB + c * kPBChunk, &tb, bfull, c * 64, 0);
+            auto top_up = [&]() -> bool {   // keep up to kPStages A chunks in flight
+                while (g_load < total && g_load < g_use + kPStages) {
+                    const int s = (int)(g_load % kPStages);
+                    if (!mbar_wait(aempty + s, (uint32_t)(((g_load / kPStages) & 1) ^ 1), kWaitTimeoutNs)) return false;
+                    const int t = blockIdx.x + (int)(g_load / nk) * gridDim.x, c = (int)(g_load % nk);
+                    mbar_expect_tx(afull + s, kATileBytes);
+                    tma_load_2d(sA + s * kATileBytes, &ta, afull + s, c * 64, t * 128);
+                    ++g_load;
+                }
+                return true;
+            };
+            ok = top_up() && mbar_wait(bfull, 0, kWaitTimeoutNs);
+            int lt = 0;
+            for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x, ++lt) {
+                const int b = lt & 1;
+                if (!mbar_wait(acce + b, (uint32_t)(((lt >> 1) & 1) ^ 1), kWaitTimeoutNs)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                for (int c = 0; c < nk; ++c) {
+                    if (!top_up()) {
+                        ok = false;
+                        break;
+                    }
+                    const int s = (int)(g_use % kPStages);
+                    if (!mbar_wait(afull + s, (uint32_t)((g_use / kPStages) & 1), kWaitTimeoutNs)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t a0 = saddr(sA + s * kATileBytes), b0 = saddr(sB + c * kPBChunk);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_bf16(tmem + b * 256, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
+                                 (c > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(aempty + s);
+                    ++g_use;
+                }
+                if (!ok) break;
+                mma_commit(accf + b);
+            }
+            // wind down: every issued MMA complete, every issued copy landed (bounded)
+            mma_commit(done);
+            mbar_wait(done, 0, kWaitTimeoutNs);
+            for (long long q = g_use; q < g_load; ++q)
+                mbar_wait(afull + (int)(q % kPStages), (uint32_t)((q / kPStages) & 1), kWaitTimeoutNs);
+            if (!ok) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
+        }
+    } else {
+        const int grp = warp >> 3, quarter = warp & 3, half = (warp >> 2) & 1;
+        const int lrow = quarter * 32 + lane;
+        const uint32_t tl = tmem + (uint32_t)grp * 256 + ((uint32_t)(quarter * 32) << 16) + (uint32_t)half * 128;
+        const bool vec = ((reinterpret_cast<uintptr_t>(g.H) & 15) == 0) && (g.ldh & 7) == 0;
+        float* pg = part + grp * 128 * 3;
+        int k = 0;   // this group's tile count
+        for (int t = blockIdx.x + grp * gridDim.x; t < tiles; t += 2 * gridDim.x, ++k) {
+            if (!mbar_wait(accf + grp, (uint32_t)(k & 1), kWaitTimeoutNs)) {
+                if (lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
+                break;
+            }
+            fence_after();
+            const int row = t * 128 + lrow;
+            const bool wr = row < g.M;
+            const int cbase = half * 128;
+            float y0 = 0.0f, y1 = 0.0f, y2 = 0.0f;
+            // the next 16 columns are in flight from tensor memory while these are processed
+            uint32_t nxt[16];
+            tmem_ld16_issue(tl, nxt);
+            tmem_ld_wait(nxt);
+#pragma unroll 2
+            for (int c0 = 0; c0 < 128; c0 += 16) {
+                float v[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(nxt[q]);
+                if (c0 + 16 < 128) tmem_ld16_issue(tl + c0 + 16, nxt);
+                const int n = cbase + c0;
+                if constexpr (EPI == EPI_GELU) {
+                    uint16_t h[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) h[q] = bf16_bits(gelu_as(v[q] + consts[n + q]));
+                    if (wr) st_bf16x16(g.H + (size_t)row * g.ldh + n, h, vec);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float h = bf16_round(gelu_as(v[q] + consts[n + q]));
+                        y0 = fmaf(consts[256 + n + q], h, y0);
+                        y1 = fmaf(consts[512 + n + q], h, y1);
+                        y2 = fmaf(consts[768 + n + q], h, y2);
+                    }
+                }
+                if (c0 + 16 < 128) tmem_ld_wait(nxt);
+            }
+            // the buffer is drained: the MMAs of a later tile may overwrite it
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce + grp);
+            if constexpr (EPI == EPI_HEAD) {
+                if (half == 1) {
+                    // hand the partial sums over (once the first half has read the previous ones)
+                    if (!mbar_wait(hfree + grp, (uint32_t)((k & 1) ^ 1), kWaitTimeoutNs)) {
+                        if (lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
+                        break;
+                    }
+                    pg[3 * lrow] = y0;
+                    pg[3 * lrow + 1] = y1;
+                    pg[3 * lrow + 2] = y2;
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(hbar + grp);
+                } else {
+                    if (!mbar_wait(hbar + grp, (uint32_t)(k & 1), kWaitTimeoutNs)) {
+                        if (lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
+                        break;
+                    }
+                    y0 += pg[3 * lrow] + consts[1024];
+                    y1 += pg[3 * lrow + 1] + consts[1025];
+                    y2 += pg[3 * lrow + 2] + consts[1026];
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(hfree + grp);
+                    if (wr) {
+                        const float nn = sqrtf(y0 * y0 + y1 * y1 + y2 * y2);
+                        float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
+                        if (nn > 0.0f) {
+                            d0 = y0 / nn;
+                            d1 = y1 / nn;
+                            d2 = y2 / nn;
+                        }
+                        g.dir_out[3 * (size_t)row] = d0;
+                        g.dir_out[3 * (size_t)row + 1] = d1;
+                        g.dir_out[3 * (size_t)row + 2] = d2;
+                    }
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+template <int EPI>
+cudaError_t launch_persist(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t s) {
+    // at least 120 KB, so that one CTA holds an SM (it allocates all 512 tensor-memory columns)
+    size_t smem = 1024 + (size_t)(g.K / 64) * kPBChunk + kPStages * kATileBytes + 256 +
+                  (256 + 3 * 256 + 4 + 2 * 128 * 3) * 4;
+    if (smem < 120 * 1024) smem = 120 * 1024;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+        e = cudaFuncSetAttribute(k_gemm_persist<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const int tiles = (g.M + 127) / 128;
+    k_gemm_persist<EPI><<<tiles < sms ? tiles : sms, kPThreads, smem, s>>>(ta, tb, g);
+    return cudaGetLastError();
+}
+
 template <int BN, int EPI>
 cudaError_t launch_bn_epi(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits, cudaStream_t s) {
     const size_t smem = 1024 + (size_t)g.stages * (kATileBytes + BN * 128) + 256 + (BN + 3 * 256 + 4 + 3 * 128) * 4;
@@ -327,6 +564,11 @@ cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap
         case EPI_PARTIAL: return launch_epi<EPI_PARTIAL>(bn, ta, tb, ga, splits, s);
         default: return launch_epi<EPI_HEAD>(bn, ta, tb, ga, splits, s);
     }
+}
+
+cudaError_t hf_gemm_persist(int epi, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t s) {
+    if (g.N != 256 || g.K % 64 || g.K < 64 || g.K > 256 || g.M < 1) return cudaErrorInvalidValue;
+    return epi == EPI_HEAD ? launch_persist<EPI_HEAD>(ta, tb, g, s) : launch_persist<EPI_GELU>(ta, tb, g, s);
 }
 
 extern "C" int hair_fuse_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, void* stream) {

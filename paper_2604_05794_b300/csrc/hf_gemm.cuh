@@ -42,3 +42,8 @@ cudaError_t hf_make_tmap_bf16(CUtensorMap* map, const void* base, long long rows
 // C = A . B^T with the given epilogue; ta: A map (box 128 rows), tb: B map (box bn rows).
 cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits,
                        cudaStream_t s);
+
+// The proposal network's inference layers (EPI_GELU or EPI_HEAD only, N = 256, K = 64..256): a
+// persistent kernel (one CTA per SM, weights resident in shared memory, double-buffered tensor
+// memory accumulator); ta: A map (box 128 rows), tb: B map (box 256 rows).
+cudaError_t hf_gemm_persist(int epi, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t s);

@@ -329,9 +329,9 @@ cudaError_t hf_mlp_infer(const MlpDev& d, const float* P, const uint16_t* x, int
     if (e != cudaSuccess) return e;
     GemmArgs g{};
     g.errw = errw; g.M = n; g.N = kHid; g.K = kIn; g.kchunks_per_split = 1; g.bias = P + kB1; g.H = h1; g.ldh = kHid;
-    if ((e = hf_gemm_tn(EPI_GELU, 256, tx, tw1, g, 1, s))) return e;
+    if ((e = hf_gemm_persist(EPI_GELU, tx, tw1, g, s))) return e;
     GemmArgs g2{};
     g2.errw = errw; g2.M = n; g2.N = kHid; g2.K = kHid; g2.kchunks_per_split = kHid / 64; g2.bias = P + kB2;
     g2.w3 = d.w3f; g2.b3 = P + kB3; g2.dir_out = dir_out;
-    return hf_gemm_tn(EPI_HEAD, 256, th1, tw2, g2, 1, s);
+    return hf_gemm_persist(EPI_HEAD, th1, tw2, g2, s);
 }
