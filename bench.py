@@ -41,6 +41,10 @@ WORKLOADS = {
                  "noise), H=64, k=8, T=8; learned proposal (trained on 4 full-like scenes, 2M samples, 20k Adam "
                  "steps, batch 8192, lr 1e-3) + 2 refinement rounds + plain fallback, against the plain fusion "
                  "of the scenes one by one",
+    "learned": "learned proposal on one full-workload scene (seed 104: 1,000,000 points, 64 views 1920x1080, "
+               "fp16 confidence): network trained on 4 full-like scenes (2M samples, 20k Adam steps, batch 8192, "
+               "lr 1e-3), proposal cost against a calibrated tau, 2 refinement rounds for accepted proposals, "
+               "the plain fusion (H=64, T=8) for the others; against the plain fusion of the same scene",
     "full": "plain fusion, full: 1,000,000 points (20,000 strands x 50 segments), 64 views 1920x1080, "
             "f32 angle + fp16 confidence, 0.5 deg pose noise, H=64, k=8, T=8",
     "mid": "plain fusion, mid: 200,000 points, 32 views 1024x1024 with 10% outlier pixels, H=64, k=8, T=8",
@@ -67,6 +71,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="serving16", choices=list(WORKLOADS))
+    ap.add_argument("--partition", action="store_true", help="full/mid/tiny under torchrun: every rank uploads "
+                    "the same scene and fuses its own point range (strong scaling) instead of its own scene")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--net", default=None, help="serving16: load the proposal network from this file instead of "
@@ -98,6 +104,13 @@ def reduce_over_ranks(x, pg, dev, op="max"):
     t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
     pg.all_reduce(t, op=pg.ReduceOp.MAX if op == "max" else pg.ReduceOp.SUM)
     return float(t.item())
+
+
+def rank_range(n, rank, world):
+    """Contiguous point range [lo, hi) of a rank when one scene is split over the ranks (sizes differ
+    by at most one; the ranges tile [0, n) in rank order)."""
+    lo = n * rank // world
+    return lo, n * (rank + 1) // world
 
 
 def rank_first_seed(rank):
@@ -185,13 +198,15 @@ def cpu_baseline(sc, H, T, budget_s=15.0):
                       f"{dt:.1f} s"}
 
 
-def accuracy(sc, H, T, gpu_dir, n_sample):
-    """Angular error of the GPU directions against the FP64 oracle on a stratified sample."""
+def accuracy(sc, H, T, gpu_dir, n_sample, lo=0, hi=None):
+    """Angular error of the GPU directions against the FP64 oracle on a stratified sample of the
+    points lo .. hi - 1."""
     import oracle
     osc = oracle.Scene.from_dict(sc)
     import paper_2604_05794_b300 as hf
     hyps = hf.fibonacci_hemisphere(H)
-    sel = np.linspace(0, sc["N"] - 1, n_sample).astype(np.int64)
+    hi = sc["N"] if hi is None else hi
+    sel = np.linspace(lo, hi - 1, n_sample).astype(np.int64)
     orc = oracle.fuse(osc, hyps, T, idx=sel)
     a, b = gpu_dir[sel].astype(np.float64), orc["dir"]
     ang = np.degrees(np.arctan2(np.linalg.norm(np.cross(a, b), axis=1), np.abs(np.sum(a * b, axis=1))))
@@ -205,7 +220,13 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    scenes = serving_scenes(200) if args.workload == "serving16" else [make_workload(args.workload)]
+    if args.workload == "serving16":
+        scenes = serving_scenes(200)
+    elif args.workload == "learned":
+        import scenegen
+        scenes = [scenegen.make_scene("full", seed=104)]
+    else:
+        scenes = [make_workload(args.workload)]
     osc = [oracle.Scene.from_dict(sc) for sc in scenes]
     hyps = {sc["cfg"]["H"]: oracle.fibonacci_hemisphere(sc["cfg"]["H"]) for sc in scenes}
     Ntot = sum(sc["N"] for sc in scenes)
@@ -259,7 +280,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    sc = make_workload(args.workload, seed_offset=100 * rank)
+    sc = make_workload(args.workload, seed_offset=0 if args.partition else 100 * rank)
     N, V, H, W, k = sc["N"], sc["V"], sc["H"], sc["W"], sc["k"]
     Hh, T = sc["cfg"]["H"], sc["cfg"]["T"]
     stream = torch.cuda.current_stream(dev)
@@ -271,13 +292,18 @@ def run_ours(args):
     nbr = torch.from_numpy(sc["nbr"]).to(dev)
     f.upload_views(cams, ang, conf)
     f.upload_points(pts, nbr)
-    out_dir = torch.empty((N, 3), device=dev)
-    out_cost = torch.empty(N, device=dev)
-    out_idx = torch.empty(N, dtype=torch.int32, device=dev)
-    out_st = torch.empty(N, dtype=torch.uint8, device=dev)
+    lo, hi = rank_range(N, rank, world) if args.partition else (0, N)
+    R = hi - lo   # points this rank fuses
+    out_dir = torch.empty((R, 3), device=dev)
+    out_cost = torch.empty(R, device=dev)
+    out_idx = torch.empty(R, dtype=torch.int32, device=dev)
+    out_st = torch.empty(R, dtype=torch.uint8, device=dev)
 
     def step():
-        f.fuse(out_dir, out_cost, out_idx, out_st)
+        if args.partition:
+            f.fuse_range(lo, R, out_dir, out_cost, out_idx, out_st)
+        else:
+            f.fuse(out_dir, out_cost, out_idx, out_st)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -306,7 +332,10 @@ def run_ours(args):
     launches = f.stats()["launches"] - launches0
     ms = reduce_over_ranks(ms, pg, dev)
     f.sync()
-    value = reduce_over_ranks(N, pg, dev, "sum") * args.steps / (ms / 1e3)
+    # whole-job points: one shared scene when partitioned, every rank's own scene otherwise
+    value = (N if args.partition else reduce_over_ranks(N, pg, dev, "sum")) * args.steps / (ms / 1e3)
+    if args.partition:
+        point_views = point_views * R // N   # the range's share of the projection's work count
 
     # rooflines: the cost kernels are FP32-issue bound, the projection/gather kernel HBM bound
     peak_alu = SM_COUNT * FP32_LANES_PER_SM * 2032.0e6
@@ -337,31 +366,38 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong" if args.partition else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "points": N, "views": V, "map": f"{W}x{H}",
                        "H": Hh, "k": k, "T": T, "form": "plain",
                        "l2": "inputs larger than L2 (orientation+confidence maps "
                              f"{(sc['angle'].nbytes + sc['conf'].nbytes) / 1e6:.0f} MB re-read every step)",
-                       "parallelism": f"independent scenes per rank x{world}"},
+                       "parallelism": (f"one scene, point range per rank x{world}" if args.partition
+                                       else f"independent scenes per rank x{world}")},
             "roofline": roofline, "rooflines": rooflines, "kernels": kernels, "gpu_launches": launches,
             "clocks": clk}
 
     if rank == 0:
-        line["accuracy"] = accuracy(sc, Hh, T, out_dir.cpu().numpy(), args.accuracy_sample or 400)
+        full_dir = np.zeros((N, 3), np.float32)
+        full_dir[lo:hi] = out_dir.cpu().numpy()
+        line["accuracy"] = accuracy(sc, Hh, T, full_dir, args.accuracy_sample or 400, lo, hi)
     # end to end through the C ABI with pinned host buffers, copies inside the timed region
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(a).pin_memory()
         h_cams, h_ang, h_conf, h_pts, h_nbr = (pin(sc[x]) for x in ("cams", "angle", "conf", "points", "nbr"))
-        h_dir = torch.empty((N, 3)).pin_memory()
-        h_cost = torch.empty(N).pin_memory()
-        h_idx = torch.empty(N, dtype=torch.int32).pin_memory()
-        h_st = torch.empty(N, dtype=torch.uint8).pin_memory()
+        h_dir = torch.empty((R, 3)).pin_memory()
+        h_cost = torch.empty(R).pin_memory()
+        h_idx = torch.empty(R, dtype=torch.int32).pin_memory()
+        h_st = torch.empty(R, dtype=torch.uint8).pin_memory()
         f2 = hf.HairFuse(Hh, k, T, 0, stream=stream.cuda_stream)
 
         def e2e_step():
             f2.upload_views(h_cams, h_ang, h_conf)
             f2.upload_points(h_pts, h_nbr)
-            f2.fuse(h_dir, h_cost, h_idx, h_st)
+            if args.partition:
+                f2.fuse_range(lo, R, h_dir, h_cost, h_idx, h_st)
+            else:
+                f2.fuse(h_dir, h_cost, h_idx, h_st)
 
         e2e_step()
         if pg:
@@ -372,8 +408,9 @@ def run_ours(args):
             e2e_step()
         dt = reduce_over_ranks(time.perf_counter() - t0, pg, dev)
         h2d = sum(x.numel() * x.element_size() for x in (h_cams, h_ang, h_conf, h_pts, h_nbr))
-        d2h = N * (12 + 4 + 4 + 1)
-        line["e2e"] = {"value": reduce_over_ranks(N, pg, dev, "sum") * n_e2e / dt, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+        d2h = R * (12 + 4 + 4 + 1)
+        e2e_points = N if args.partition else reduce_over_ranks(N, pg, dev, "sum")
+        line["e2e"] = {"value": e2e_points * n_e2e / dt, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
                        "path": "hair_fuse_upload_views/points + fuse_directions with HF_HOST pinned buffers"}
         f2.close()
@@ -495,8 +532,11 @@ def serving_cpu_baseline(scenes, budget_s=15.0):
 # DRAM bytes (read + write) per work unit of the batched cost kernels, from one ncu --set full capture
 # of the 4-scene serving batch (profiles/k_refine_batch_k_argmin_batch_serving4_ncu.md); a full launch's
 # traffic is scaled from it by the units the launch processes.  Re-take it whenever these kernels change.
-DRAM_BYTES_PER_UNIT = {"k_refine_batch": (773.682 + 14.088) * 1e6 / 15816683,   # per fallback point-view
-                       "k_argmin_batch": (553.947 + 15.963) * 1e6 / 15816683}   # per fallback point-view
+DRAM_BYTES_PER_UNIT = {"k_refine_batch": (1022.566 + 12.861) * 1e6 / 14635443,      # per fallback point-view
+                       "k_argmin_batch": (600.096 + 15.433) * 1e6 / 14635443,       # per fallback point-view
+                       "k_refine_short_batch": (401.193 + 8.197) * 1e6 / 5276307,   # per accepted point-view
+                       "k_start_select_batch": (439.860 + 9.251) * 1e6 / 19911750,  # per point-view
+                       "k_project_batch": (176.747 + 283.276) * 1e6 / 19911750}     # per point-view
 
 
 def stage_rooflines(kt, ms_step, scenes, st, T_short):
@@ -518,6 +558,7 @@ def stage_rooflines(kt, ms_step, scenes, st, T_short):
     pv, fpv = st["point_views"], st["fallback_point_views"]
     apv = pv - fpv   # point-views of the accepted proposals
     units = {"k_refine_batch": fpv, "k_argmin_batch": fpv, "k_refine_short_batch": apv, "k_start_select_batch": pv}
+    traffic_units = dict(units, k_project_batch=pv)
     work = {
         "k_project_batch": ("hbm", proj_bytes, "(4 + conf bytes + 16) B per (point, view) + 12 B per point"),
         "k_features_batch": ("hbm", feat_bytes, "16 x (4 + conf bytes) B gathered + 12 B in + 128 B out per point"),
@@ -542,7 +583,7 @@ def stage_rooflines(kt, ms_step, scenes, st, T_short):
             ach, peak, unit, src = amount / sec / 1e12, bf16, "TFLOP/s", bf16_src
         else:
             ach, peak, unit, src = amount / sec / 1e9, HBM_GBS, "GB/s", "of measured: MEASURED_PEAKS.json hbm_gbs"
-        traffic = DRAM_BYTES_PER_UNIT[name] * units[name] if name in DRAM_BYTES_PER_UNIT else None
+        traffic = DRAM_BYTES_PER_UNIT[name] * traffic_units[name] if name in DRAM_BYTES_PER_UNIT else None
         out[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
                      "traffic": traffic, "kernel": name, "peak_source": src, "work": how,
                      "units": units.get(name, Ntot), "ms": kt[name][1], "share": kt[name][1] / ms_step}
@@ -748,12 +789,145 @@ def run_serving(args):
         pg.destroy_process_group()
 
 
+def run_learned(args):
+    """configs' learned form on one scene: the proposal path against the plain fusion, single GPU
+    (each rank its own scene under torchrun)."""
+    import torch
+
+    import paper_2604_05794_b300 as hf
+    import scenegen
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    stream = torch.cuda.current_stream(dev)
+    off = rank_first_seed(rank) - 200
+    net, tau, train_info = train_proposal(dev, off)
+    sc = scenegen.make_scene("full", seed=104 + off)
+    N, V, k = sc["N"], sc["V"], sc["k"]
+    H, T = sc["cfg"]["H"], sc["cfg"]["T"]
+    f = hf.HairFuse(H, k, T, 0, stream=stream.cuda_stream)
+    f.upload_views(sc["cams"], sc["angle"], sc["conf"])
+    f.upload_points(sc["points"], sc["nbr"])
+    mk = lambda: (torch.empty((N, 3), device=dev), torch.empty(N, device=dev),
+                  torch.empty(N, dtype=torch.int32, device=dev), torch.empty(N, dtype=torch.uint8, device=dev))
+    o_l, o_p = mk(), mk()
+    K, W = args.steps, max(3, args.warmup)
+    learned = lambda: f.fuse_learned(net, *o_l, T_short=SERVING_T_SHORT, alpha_short=SERVING_ALPHA, tau=tau,
+                                     count_fallback=False)
+    plain = lambda: f.fuse(*o_p)
+
+    def timed(step):
+        for _ in range(W):
+            step()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return reduce_over_ranks(e0.elapsed_time(e1), pg, dev)
+
+    ms_p = timed(plain)
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(cvd.split(",")[local] if cvd else str(local))
+    launches0 = f.stats()["launches"]
+    clocks.start()
+    time.sleep(0.3)
+    ms_l = timed(learned)
+    clk = clocks.stop()
+    launches = (f.stats()["launches"] - launches0) * K // (K + W)
+    n_fb = f.fuse_learned(net, *o_l, T_short=SERVING_T_SHORT, alpha_short=SERVING_ALPHA, tau=tau)
+    point_views = f.work()
+    lw = f.learned_work()
+    f.profile(True)
+    learned()
+    kt = f.profile_read()
+    f.profile(False)
+    Nall = reduce_over_ranks(N, pg, dev, "sum")
+    value, plain_value = Nall * K / (ms_l / 1e3), Nall * K / (ms_p / 1e3)
+    ms_prof = sum(v[1] for v in kt.values())
+    # per-stage rooflines from the exact work of this scene (the same units as the batched line)
+    st = {"point_views": point_views, "fallback_point_views": lw["fallback_point_views"]}
+    names = {"k_project": "k_project_batch", "k_features": "k_features_batch", "k_mlp": "k_mlp",
+             "k_start_select": "k_start_select_batch", "k_refine_short": "k_refine_short_batch",
+             "k_argmin_fallback": "k_argmin_batch", "k_refine_fallback": "k_refine_batch"}
+    kt_b = {names[n_]: v for n_, v in kt.items() if n_ in names}
+    rb = stage_rooflines(kt_b, ms_prof, [sc], st, SERVING_T_SHORT)
+    back = {v: n_ for n_, v in names.items()}
+    rooflines = {}
+    for n_b, r in rb.items():
+        r = dict(r, kernel=back[n_b])
+        if n_b in DRAM_BYTES_PER_UNIT:   # per-unit traffic was taken on the batched kernels
+            r["traffic"] = None
+            r.pop("traffic_source", None)
+        rooflines[back[n_b]] = r
+    kernels = {n_: {"launches": v[0], "ms": v[1], "share": v[1] / ms_prof} for n_, v in kt.items()}
+    dom = max(rooflines, key=lambda x: rooflines[x]["share"])
+    line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_l / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (bf16 tensor-core network)", "data": "synthetic",
+            "config": {"workload": WORKLOADS["learned"], "points": N, "views": V, "map": f"{sc['W']}x{sc['H']}",
+                       "form": "learned", "H": H, "k": k, "T": T, "T_short": SERVING_T_SHORT,
+                       "alpha_short": SERVING_ALPHA, "l2": "inputs larger than L2 (maps re-read every step)",
+                       "parallelism": f"independent scenes per rank x{world}"},
+            "plain": {"value": plain_value, "unit": "points/s", "ms_per_step": ms_p / K},
+            "speedup_vs_plain": value / plain_value, "learned": dict(train_info, fallback_frac=n_fb / N),
+            "roofline": dict(rooflines[dom]), "rooflines": rooflines, "kernels": kernels, "gpu_launches": launches,
+            "clocks": clk}
+    if rank == 0:
+        acc = serving_accuracy([sc], [o_l[0].cpu().numpy()], [o_p[0].cpu().numpy()], args.accuracy_sample or 50000)
+        line["accuracy"] = acc
+        line["accepted"] = bool(acc["median_deg"] <= 2.0)
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        hin = [pin(sc[x]) for x in ("cams", "angle", "conf", "points", "nbr")]
+        hout = [torch.empty((N, 3)).pin_memory(), torch.empty(N).pin_memory(),
+                torch.empty(N, dtype=torch.int32).pin_memory(), torch.empty(N, dtype=torch.uint8).pin_memory()]
+        f2 = hf.HairFuse(H, k, T, 0, stream=stream.cuda_stream)
+
+        def e2e_step():
+            f2.upload_views(*hin[:3])
+            f2.upload_points(*hin[3:])
+            f2.fuse_learned(net, *hout, T_short=SERVING_T_SHORT, alpha_short=SERVING_ALPHA, tau=tau,
+                            count_fallback=False)
+
+        e2e_step()
+        n_e2e = max(1, min(K, 3))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        dt = reduce_over_ranks(time.perf_counter() - t0, pg, dev)
+        line["e2e"] = {"value": Nall * n_e2e / dt, "unit": "points/s",
+                       "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in hin)),
+                       "d2h_bytes_per_step": int(sum(x.numel() * x.element_size() for x in hout)), "steps": n_e2e,
+                       "path": "hair_fuse_upload_views/points + fuse_learned with HF_HOST pinned buffers"}
+        f2.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc, H, T)
+    f.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serving16":
         run_serving(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 
