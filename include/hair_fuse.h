@@ -117,6 +117,15 @@ int hair_fuse_upload_points(hf_ctx* ctx, int N, const float* xyz, const int32_t*
 int hair_fuse_fuse_directions(hf_ctx* ctx, const float* hyps, float* dir_out, float* cost_out, int32_t* idx_out,
                               uint8_t* status_out, int mem_kind);
 
+/* Fusion of the points first .. first + count - 1 only: the partition hook for spreading one scene
+ * over several GPUs (each uploads the whole scene, so the range's neighbours are available, and
+ * fuses its own range).  Every point is projected; the hypothesis argmin and the refinement run on
+ * the range.  Outputs have count rows: row q holds point first + q, with exactly the values
+ * hair_fuse_fuse_directions gives that point.  Errors as there, plus HF_ERR_INVALID_ARG for a range
+ * outside [0, N). */
+int hair_fuse_fuse_range(hf_ctx* ctx, int first, int count, const float* hyps, float* dir_out, float* cost_out,
+                         int32_t* idx_out, uint8_t* status_out, int mem_kind);
+
 /* Evaluate the cost c_i(d) of M given directions for every point (no argmin, no refinement).
  *  dirs: N x M x 3 f32 (any non-zero length; the cost is scale- and sign-invariant),
  *  cost_out: N x M f32.  Both of kind mem_kind. */
@@ -279,6 +288,10 @@ int hair_fuse_batch_profile_run(hf_batch* b, hf_kernel_time* out, int max_entrie
 int hair_fuse_batch_stats(hf_batch* b, long long* launches, long long* point_views, long long* fallback_point_views);
 void hair_fuse_batch_destroy(hf_batch* b);
 const char* hair_fuse_batch_last_error(const hf_batch* b);
+
+/* Work of the last hair_fuse_fuse_learned call (synchronises): the (point, view) pairs in the view
+ * sets of the fallback points and of the accepted (refined) proposals (either pointer may be NULL). */
+int hair_fuse_learned_work(hf_ctx* ctx, long long* fallback_point_views, long long* accepted_point_views);
 
 /* The built-in hypothesis set (host memory): H x 3 f32 Fibonacci hemisphere directions. */
 int hair_fuse_fibonacci_hemisphere(int H, float* out);

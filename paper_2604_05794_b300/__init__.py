@@ -44,6 +44,7 @@ _SIGS = {
     "hair_fuse_fuse_directions": ([_vp, _vp, _vp, _vp, _vp, _vp, _i], _i),
     "hair_fuse_fuse_directions_noalloc": ([ctypes.POINTER(hf_config), _i, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp,
                                            _vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "hair_fuse_fuse_range": ([_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _i], _i),
     "hair_fuse_eval_costs": ([_vp, _i, _vp, _vp, _i], _i),
     "hair_fuse_fibonacci_hemisphere": ([_i, _vp], _i),
     "hair_fuse_gemm_bf16": ([_vp, _vp, _vp, _i, _i, _i, _vp], _i),
@@ -69,6 +70,7 @@ _SIGS = {
     "hair_fuse_features": ([_vp, _vp, _i], _i),
     "hair_fuse_fuse_learned": ([_vp, _vp, _i, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp, _vp,
                                 ctypes.POINTER(_i), _i], _i),
+    "hair_fuse_learned_work": ([_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll)], _i),
     "hair_fuse_batch_create": ([ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp, _vp, _vp], _i),
     "hair_fuse_batch_set_outputs": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
     "hair_fuse_batch_run": ([_vp, _i], _i),
@@ -93,6 +95,7 @@ hair_fuse_upload_views = _lib.hair_fuse_upload_views
 hair_fuse_upload_points = _lib.hair_fuse_upload_points
 hair_fuse_fuse_directions = _lib.hair_fuse_fuse_directions
 hair_fuse_fuse_directions_noalloc = _lib.hair_fuse_fuse_directions_noalloc
+hair_fuse_fuse_range = _lib.hair_fuse_fuse_range
 hair_fuse_eval_costs = _lib.hair_fuse_eval_costs
 hair_fuse_fibonacci_hemisphere = _lib.hair_fuse_fibonacci_hemisphere
 hair_fuse_gemm_bf16 = _lib.hair_fuse_gemm_bf16
@@ -117,6 +120,7 @@ hair_fuse_mlp_load = _lib.hair_fuse_mlp_load
 hair_fuse_mlp_last_error = _lib.hair_fuse_mlp_last_error
 hair_fuse_features = _lib.hair_fuse_features
 hair_fuse_fuse_learned = _lib.hair_fuse_fuse_learned
+hair_fuse_learned_work = _lib.hair_fuse_learned_work
 hair_fuse_batch_create = _lib.hair_fuse_batch_create
 hair_fuse_batch_set_outputs = _lib.hair_fuse_batch_set_outputs
 hair_fuse_batch_run = _lib.hair_fuse_batch_run
@@ -253,6 +257,12 @@ class HairFuse:
         kind = _same_kind(*[p[1] for p in ptrs])
         self._c(hair_fuse_fuse_directions(self.h, *[p[0] for p in ptrs], kind))
 
+    def fuse_range(self, first, count, dir_out, cost_out=None, idx_out=None, status_out=None, hyps=None):
+        """Fuse points first .. first + count - 1 into caller buffers of count rows."""
+        ptrs = [_ptr_kind(x) for x in (hyps, dir_out, cost_out, idx_out, status_out)]
+        kind = _same_kind(*[p[1] for p in ptrs])
+        self._c(hair_fuse_fuse_range(self.h, first, count, *[p[0] for p in ptrs], kind))
+
     def eval_costs(self, dirs, cost_out):
         """Costs (N,M) of the directions dirs (N,M,3)."""
         pd, k1, _ = _ptr_kind(dirs)
@@ -384,8 +394,16 @@ def _fuse_learned(self, net, dir_out, cost_out=None, idx_out=None, status_out=No
     return nf.value if count_fallback else None
 
 
+def _learned_work(self):
+    """(point, view) pairs of the fallback points and of the accepted proposals, last learned fusion."""
+    fb, ac = _ll(0), _ll(0)
+    self._c(hair_fuse_learned_work(self.h, ctypes.byref(fb), ctypes.byref(ac)))
+    return dict(fallback_point_views=fb.value, accepted_point_views=ac.value)
+
+
 HairFuse.features = _features
 HairFuse.fuse_learned = _fuse_learned
+HairFuse.learned_work = _learned_work
 
 
 class hf_batch_cfg(ctypes.Structure):

@@ -197,13 +197,26 @@ int hair_fuse_upload_points(hf_ctx* c, int N, const float* xyz, const int32_t* n
     return HF_OK;
 }
 
-int hair_fuse_fuse_directions(hf_ctx* c, const float* hyps, float* dir_out, float* cost_out, int32_t* idx_out,
-                              uint8_t* status_out, int mem_kind) {
+namespace {
+
+// Fusion of the points first .. first + count - 1 (all points when ranged is false): every point is
+// projected (the range's neighbours need their samples), the argmin and refinement run on the range,
+// and outputs are written to rows 0 .. count - 1.
+int fuse_impl(hf_ctx* c, const float* hyps, bool ranged, int first, int count, float* dir_out, float* cost_out,
+              int32_t* idx_out, uint8_t* status_out, int mem_kind) {
     int rc;
     if ((rc = ready(c))) return rc;
     if ((rc = check_kind(c, mem_kind))) return rc;
     if (!dir_out) return hf_set_err(c, HF_ERR_INVALID_ARG, "dir_out is required");
-    const int H = c->cfg.H, T = c->cfg.T, V = c->V, N = c->N;
+    const int H = c->cfg.H, T = c->cfg.T, V = c->V;
+    if (ranged && (first < 0 || count < 0 || (long long)first + count > c->N))
+        return hf_set_err(c, HF_ERR_INVALID_ARG, "range [%d, %d + %d) outside [0, %d)", first, first, count, c->N);
+    if (!ranged) {
+        first = 0;
+        count = c->N;
+    }
+    if (count == 0) return HF_OK;
+    const int N = c->N, R = count;
     const int hc = hf_fuse_chunk_for(H);
     const int Hpad = (H + hc - 1) / hc * hc;
     const float* hyps_dev = nullptr;
@@ -233,13 +246,13 @@ int hair_fuse_fuse_directions(hf_ctx* c, const float* hyps, float* dir_out, floa
     int32_t* d_idx = idx_out;
     uint8_t* d_status = status_out;
     if (mem_kind == HF_HOST) {
-        const size_t bytes = (size_t)N * (3 * sizeof(float) + sizeof(float) + sizeof(int32_t) + 1);
+        const size_t bytes = (size_t)R * (3 * sizeof(float) + sizeof(float) + sizeof(int32_t) + 1);
         if ((rc = hf_ensure(c, c->outs, bytes))) return rc;
         char* base = (char*)c->outs.p;
         d_dir = (float*)base;
-        d_cost = cost_out ? (float*)(base + (size_t)N * 12) : nullptr;
-        d_idx = idx_out ? (int32_t*)(base + (size_t)N * 16) : nullptr;
-        d_status = status_out ? (uint8_t*)(base + (size_t)N * 20) : nullptr;
+        d_cost = cost_out ? (float*)(base + (size_t)R * 12) : nullptr;
+        d_idx = idx_out ? (int32_t*)(base + (size_t)R * 16) : nullptr;
+        d_status = status_out ? (uint8_t*)(base + (size_t)R * 20) : nullptr;
     }
     if ((rc = hf_ensure(c, c->best, (size_t)N * 12))) return rc;
     int32_t* bi = (int32_t*)c->best.p;
@@ -247,17 +260,38 @@ int hair_fuse_fuse_directions(hf_ctx* c, const float* hyps, float* dir_out, floa
                 (const float2*)c->samp.p, (const float2*)c->ab.p, (const float4*)c->qtab.p, (const float*)c->vthr.p,
                 (const float*)c->hyps.p, H, Hpad, (const float2*)c->rot.p, T, d_dir, d_cost, d_idx, d_status,
                 bi, (float*)(bi + N), bi + 2 * (size_t)N, hf_fuse_vblock_q(V, hc), hf_fuse_vblock_c(V)};
+    if (ranged) {
+        if ((rc = hf_ensure(c, c->rlist, 16 + (size_t)R * sizeof(int32_t)))) return rc;
+        int* cnt = (int*)c->rlist.p;
+        int32_t* lst = (int32_t*)((char*)c->rlist.p + 16);
+        if ((rc = run_launch(c, "k_iota", [&] { return hf_launch_iota(lst, cnt, first, R, c->stream); }))) return rc;
+        fa.list = lst;
+        fa.list_count = cnt;
+        fa.out_first = first;
+    }
     if ((rc = run_launch(c, "k_argmin", [&] { return hf_launch_argmin(fa, hc, c->stream); }))) return rc;
     if ((rc = run_launch(c, "k_refine", [&] { return hf_launch_refine(fa, c->stream); }))) return rc;
     if (mem_kind == HF_HOST) {
-        cudaError_t e = cudaMemcpyAsync(dir_out, d_dir, (size_t)N * 12, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess && cost_out) e = cudaMemcpyAsync(cost_out, d_cost, (size_t)N * 4, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess && idx_out) e = cudaMemcpyAsync(idx_out, d_idx, (size_t)N * 4, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess && status_out) e = cudaMemcpyAsync(status_out, d_status, (size_t)N, cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e = cudaMemcpyAsync(dir_out, d_dir, (size_t)R * 12, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && cost_out) e = cudaMemcpyAsync(cost_out, d_cost, (size_t)R * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && idx_out) e = cudaMemcpyAsync(idx_out, d_idx, (size_t)R * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && status_out) e = cudaMemcpyAsync(status_out, d_status, (size_t)R, cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) return hf_cuda_err(c, e, "copy outputs");
         return sync_and_check(c);
     }
     return HF_OK;
+}
+
+}  // namespace
+
+int hair_fuse_fuse_directions(hf_ctx* c, const float* hyps, float* dir_out, float* cost_out, int32_t* idx_out,
+                              uint8_t* status_out, int mem_kind) {
+    return fuse_impl(c, hyps, false, 0, 0, dir_out, cost_out, idx_out, status_out, mem_kind);
+}
+
+int hair_fuse_fuse_range(hf_ctx* c, int first, int count, const float* hyps, float* dir_out, float* cost_out,
+                         int32_t* idx_out, uint8_t* status_out, int mem_kind) {
+    return fuse_impl(c, hyps, true, first, count, dir_out, cost_out, idx_out, status_out, mem_kind);
 }
 
 int hair_fuse_eval_costs(hf_ctx* c, int M, const float* dirs, float* cost_out, int mem_kind) {

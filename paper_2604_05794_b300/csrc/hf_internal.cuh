@@ -55,6 +55,7 @@ struct hf_ctx {
     DevBuf feat;    // [N x 64] bf16 proposal-network features
     DevBuf prop;    // [N x 3] proposals
     DevBuf lmisc;   // bounding box, fallback count, short-refinement steps, fallback list
+    DevBuf rlist;   // point range of hair_fuse_fuse_range: count, then the indices
     uint32_t* errw_host = nullptr;  // pinned read-back slot
     long long launches = 0;
     long long dev_bytes = 0;
@@ -99,6 +100,8 @@ struct ProjectArgs {
     const float2* amap;         // optional: interleaved (angle, confidence) maps, read instead of angle / conf
 };
 cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s);
+// list[q] = first + q for q < n, *count = n
+cudaError_t hf_launch_iota(int32_t* list, int* count, int first, int n, cudaStream_t s);
 // out[i] = (angle[i], conf[i] as f32) for npx pixels
 cudaError_t hf_launch_interleave(const float* angle, const void* conf, int conf_f16, size_t npx, float2* out,
                                  cudaStream_t s);
@@ -129,6 +132,7 @@ struct FuseArgs {
     const int32_t* list; const int* list_count;          // optional: fuse only these points (device count)
     const float* start_dir;                              // optional [N x 3]: refine from here, not hyps[best_idx]
     int fell_back;                                       // mark outputs HF_STATUS_FELL_BACK
+    int out_first;   // outputs of point i go to row i - out_first (0: point-indexed)
 };
 int hf_fuse_chunk_for(int H);
 int hf_fuse_vblock_q(int V, int hchunk);

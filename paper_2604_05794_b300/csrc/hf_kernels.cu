@@ -212,6 +212,12 @@ __global__ void __launch_bounds__(kProjectThreads) k_project(ProjectArgs a) {
     project_tile<TOPK>(a, blockIdx.x);
 }
 
+__global__ void k_iota(int32_t* list, int* count, int first, int n) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) list[q] = first + q;
+    if (q == 0) *count = n;
+}
+
 __global__ void k_interleave(const float* __restrict__ angle, const void* __restrict__ conf, int f16, size_t npx,
                              float2* __restrict__ out) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npx; i += (size_t)gridDim.x * blockDim.x)
@@ -522,10 +528,11 @@ __device__ __forceinline__ void refine_tile(const FuseArgs& a, int blk, unsigned
         }
     }
     if (inb && nv < 0) {
-        a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
-        if (a.cost_out) a.cost_out[i] = __int_as_float(0x7fc00000);
-        if (a.idx_out) a.idx_out[i] = -1;
-        if (a.status_out) a.status_out[i] = HF_STATUS_BAD_INPUT;
+        const int o = i - a.out_first;   // output row
+        a.dir_out[3 * o] = a.dir_out[3 * o + 1] = a.dir_out[3 * o + 2] = 0.0f;
+        if (a.cost_out) a.cost_out[o] = __int_as_float(0x7fc00000);
+        if (a.idx_out) a.idx_out[o] = -1;
+        if (a.status_out) a.status_out[o] = HF_STATUS_BAD_INPUT;
         if (from_start) a.nvs[i] = -1;
     }
     // points with no view keep their start (all costs are 1)
@@ -641,12 +648,13 @@ __device__ __forceinline__ void refine_tile(const FuseArgs& a, int blk, unsigned
     d1 /= n;
     d2 /= n;
     const float sgn = fabsf(d2) > 1e-12f ? copysignf(1.0f, d2) : fabsf(d1) > 1e-12f ? copysignf(1.0f, d1) : copysignf(1.0f, d0);
-    a.dir_out[3 * i] = sgn * d0;
-    a.dir_out[3 * i + 1] = sgn * d1;
-    a.dir_out[3 * i + 2] = sgn * d2;
-    if (a.cost_out) a.cost_out[i] = best;
-    if (a.idx_out) a.idx_out[i] = bestm;
-    if (a.status_out) a.status_out[i] = a.fell_back ? HF_STATUS_FELL_BACK : (nv ? HF_STATUS_OK : HF_STATUS_NO_VIEWS);
+    const int o = i - a.out_first;   // output row
+    a.dir_out[3 * o] = sgn * d0;
+    a.dir_out[3 * o + 1] = sgn * d1;
+    a.dir_out[3 * o + 2] = sgn * d2;
+    if (a.cost_out) a.cost_out[o] = best;
+    if (a.idx_out) a.idx_out[o] = bestm;
+    if (a.status_out) a.status_out[o] = a.fell_back ? HF_STATUS_FELL_BACK : (nv ? HF_STATUS_OK : HF_STATUS_NO_VIEWS);
 }
 
 template <int KP>
@@ -793,11 +801,12 @@ __device__ __forceinline__ void start_select_tile(const StartSelectArgs& s, int 
         a.best_cost[i] = c0;
         a.nvs[i] = nv;
     } else if (in) {
+        const int o = i - a.out_first;   // output row
         a.nvs[i] = -1;
-        a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
-        if (a.cost_out) a.cost_out[i] = __int_as_float(0x7fc00000);
-        if (a.idx_out) a.idx_out[i] = -1;
-        if (a.status_out) a.status_out[i] = HF_STATUS_BAD_INPUT;
+        a.dir_out[3 * o] = a.dir_out[3 * o + 1] = a.dir_out[3 * o + 2] = 0.0f;
+        if (a.cost_out) a.cost_out[o] = __int_as_float(0x7fc00000);
+        if (a.idx_out) a.idx_out[o] = -1;
+        if (a.status_out) a.status_out[o] = HF_STATUS_BAD_INPUT;
     }
     const bool fb = active && nv > 0 && c0 > s.tau;
     const bool ok = active && !fb;
@@ -1102,6 +1111,11 @@ cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s) {
     const dim3 grid((a.N + kProjectThreads - 1) / kProjectThreads), block(kProjectThreads);
     if (a.top_k > 0) k_project<true><<<grid, block, 0, s>>>(a);
     else k_project<false><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_iota(int32_t* list, int* count, int first, int n, cudaStream_t s) {
+    k_iota<<<(n + 255) / 256 > 0 ? (n + 255) / 256 : 1, 256, 0, s>>>(list, count, first, n);
     return cudaGetLastError();
 }
 

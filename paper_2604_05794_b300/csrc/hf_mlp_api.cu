@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "hf_gemm.cuh"
 #include "hf_internal.cuh"
@@ -552,3 +553,28 @@ cudaError_t hf_mlp_infer_rows(hf_mlp* m, const uint16_t* x, long long n, uint16_
 }
 
 cudaStream_t hf_mlp_stream(hf_mlp* m) { return m->stream; }
+
+extern "C" int hair_fuse_learned_work(hf_ctx* c, long long* fallback_point_views, long long* accepted_point_views) {
+    if (!c) return HF_ERR_INVALID_ARG;
+    if (c->N <= 0 || !c->lmisc.p || !c->best.p) return hf_set_err(c, HF_ERR_NOT_UPLOADED, "no learned fusion has run");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return hf_cuda_err(c, e, "stream synchronize");
+    const int N = c->N;
+    const char* lm = (const char*)c->lmisc.p;
+    int cnt[2] = {0, 0};
+    e = cudaMemcpy(cnt, lm + 64, sizeof cnt, cudaMemcpyDeviceToHost);
+    std::vector<int32_t> nvs(N), lst((size_t)cnt[0] + cnt[1]);
+    if (e == cudaSuccess) e = cudaMemcpy(nvs.data(), (const int32_t*)c->best.p + 2 * (size_t)N, (size_t)N * 4, cudaMemcpyDeviceToHost);
+    const int32_t* list = (const int32_t*)(lm + 256 + 64 * 8);
+    if (e == cudaSuccess && cnt[0] > 0) e = cudaMemcpy(lst.data(), list, (size_t)cnt[0] * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && cnt[1] > 0) e = cudaMemcpy(lst.data() + cnt[0], list + N, (size_t)cnt[1] * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return hf_cuda_err(c, e, "read view counts");
+    long long fb = 0, ac = 0;
+    for (int q = 0; q < cnt[0] + cnt[1]; ++q) {
+        const int32_t v = nvs[lst[q]];
+        (q < cnt[0] ? fb : ac) += v > 0 ? v : 0;
+    }
+    if (fallback_point_views) *fallback_point_views = fb;
+    if (accepted_point_views) *accepted_point_views = ac;
+    return HF_OK;
+}
