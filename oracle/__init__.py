@@ -193,3 +193,59 @@ def features(scene):
     out = np.empty((scene.N, 64))
     lib.or_features_all(ctypes.byref(scene.c), _p(box), _p(out))
     return out
+
+
+FLAG_MEDOID_TIE, FLAG_SEL_TIE, FLAG_DEPTH_EDGE = 8, 16, 32
+
+
+class _FpmvoCfg(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("S", ctypes.c_int), ("P", ctypes.c_int), ("lambda_px", ctypes.c_double),
+                ("delta", ctypes.c_double), ("eps_vis", ctypes.c_double)]
+
+
+def backproject(cam, u, v, z):
+    """World point at camera depth z on the ray through pixel (u, v) (inverse projection, Eq. 3)."""
+    lib = _load()
+    lib.or_backproject.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_void_p]
+    c = np.ascontiguousarray(cam, np.float64)
+    out = np.empty(3)
+    lib.or_backproject(_p(c), u, v, z, _p(out))
+    return out
+
+
+def medoid(dirs, w):
+    """(index, best score, runner-up score) of the weighted medoid of unit directions (n, 3)."""
+    lib = _load()
+    lib.or_medoid.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.or_medoid.restype = ctypes.c_int
+    d = np.ascontiguousarray(dirs, np.float64)
+    ww = np.ascontiguousarray(w, np.float64)
+    b, s = ctypes.c_double(), ctypes.c_double()
+    i = lib.or_medoid(len(ww), _p(d), _p(ww), ctypes.byref(b), ctypes.byref(s))
+    return i, b.value, s.value
+
+
+def fpmvo(scene, depth, K=5, S=5, P=5, lambda_px=4.0, delta=0.005, eps_vis=0.02, idx=None, threads=0):
+    """The paper's FPMVO step (Sec. 3.1.1-3.1.3) for the points idx: candidates from depth samples
+    around pixel-offset points, medoid fusion per depth layer over the top-K views, P x P patch
+    consistency.  depth: (V, H, W) f32 camera-space depth maps (+inf where no hair).  Returns dict
+    dir (n, 3), cost (n,), sel (n,) chosen depth layer, status (n,), flags (n,)."""
+    lib = _load()
+    lib.or_fpmvo.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_int]
+    dep = np.ascontiguousarray(depth, np.float32)
+    cfg = _FpmvoCfg(K, S, P, lambda_px, delta, eps_vis)
+    if idx is None:
+        n, ip = scene.N, None
+    else:
+        idx = np.ascontiguousarray(idx, np.int64)
+        n, ip = len(idx), _p(idx)
+    out = dict(dir=np.empty((n, 3)), cost=np.empty(n), sel=np.empty(n, np.int32), status=np.empty(n, np.uint8),
+               flags=np.empty(n, np.uint8))
+    rc = lib.or_fpmvo(ctypes.byref(scene.c), _p(dep), ctypes.byref(cfg), n, ip, _p(out["dir"]), _p(out["cost"]),
+                      _p(out["sel"]), _p(out["status"]), _p(out["flags"]), threads)
+    if rc != 0:
+        raise ValueError("fpmvo: K and S in [1, 16], P odd")
+    return out

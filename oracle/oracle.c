@@ -412,3 +412,232 @@ int or_max_threads(void) {
     return 1;
 #endif
 }
+
+/* ==============================================================================================
+ * FPMVO as the paper states it (Sec. 3.1.1-3.1.3): candidate directions from depth samples
+ * around pixel-offset points, medoid fusion per depth layer over the top-K views, and the
+ * patch-based consistency over a P x P pixel patch.  Readings (listed in the design notes):
+ *  - depth maps hold the camera-space depth Z of the front-most hair, +inf where none; a view
+ *    sees point i when it projects inside the image and X_z <= D_v(pixel) + eps_vis;
+ *  - the offset pixel is u_i^v + lambda (cos theta, sin theta) with theta the map's angle at u_i^v
+ *    (Eq. 1); its depth is read at its nearest pixel; S samples z + delta_s, delta_s spread evenly
+ *    over [-Delta, Delta] including both ends (Eq. 2); back-projection through the continuous
+ *    offset pixel (Eq. 3); a view whose offset pixel leaves the image or has no depth gives none;
+ *  - candidate directions are unit vectors (the squared norm in Dir(p) read as the norm);
+ *  - top-K views by the confidence at the point's pixel, ties to the lower view; the weight of a
+ *    view's candidates is that confidence; the medoid sum includes the candidate itself; if the
+ *    weights sum to 0 every candidate scores 0 and the first is taken;
+ *  - Eq. proj_r with the finite fused offset point; r normalised; the patch is the P x P pixels
+ *    centred on the point's pixel (pixels outside the image skipped); the per-view maxima are
+ *    averaged over the top-K views; the highest average wins, lowest s on ties; the output
+ *    direction is normalised with the canonical sign and its cost is 1 - that average.
+ * ============================================================================================== */
+typedef struct {
+    int K, S, P;
+    double lambda_px, delta, eps_vis;
+} or_fpmvo_cfg;
+
+enum { OR_FLAG_MEDOID_TIE = 8, OR_FLAG_SEL_TIE = 16, OR_FLAG_DEPTH_EDGE = 32 };
+
+/* Inverse projection (Eq. 3): the world point at camera depth z on the ray through pixel (u, v). */
+void or_backproject(const double* cam, double u, double v, double z, double* p) {
+    const double X[3] = {(u - cam[2]) * z / cam[0], (v - cam[3]) * z / cam[1], z};
+    double Y[3] = {X[0] - cam[13], X[1] - cam[14], X[2] - cam[15]};
+    for (int c = 0; c < 3; c++) p[c] = cam[4 + c] * Y[0] + cam[7 + c] * Y[1] + cam[10 + c] * Y[2];
+}
+
+/* Medoid of n unit directions with weights w (Eq. G, sigma, argmax): index of the largest
+ * sum_j w_j |<d_i, d_j>| / sum_j w_j, first on ties; *second receives the runner-up score. */
+int or_medoid(int n, const double* d, const double* w, double* best_score, double* second) {
+    double wsum = 0.0;
+    for (int j = 0; j < n; j++) wsum += w[j];
+    int bi = -1;
+    double bs = -1.0, sc2 = -1.0;
+    for (int i = 0; i < n; i++) {
+        double acc = 0.0;
+        for (int j = 0; j < n; j++)
+            acc += w[j] * fabs(d[3 * i] * d[3 * j] + d[3 * i + 1] * d[3 * j + 1] + d[3 * i + 2] * d[3 * j + 2]);
+        const double sig = wsum > 0.0 ? acc / wsum : 0.0;
+        if (sig > bs) {
+            sc2 = bs;
+            bs = sig;
+            bi = i;
+        } else if (sig > sc2) {
+            sc2 = sig;
+        }
+    }
+    if (best_score) *best_score = bs;
+    if (second) *second = sc2;
+    return bi;
+}
+
+static double map_depth(const float* depth, const or_scene* s, int v, long long px) {
+    return (double)depth[(size_t)v * s->W * s->H + (size_t)px];
+}
+
+void or_fpmvo_point(const or_scene* s, const float* depth, const or_fpmvo_cfg* c, long long i, double* dir,
+                    double* cost, int32_t* sel, uint8_t* status, uint8_t* flags) {
+    const double* p = s->pts + 3 * i;
+    *flags = 0;
+    *sel = -1;
+    *cost = 1.0;
+    dir[0] = dir[1] = dir[2] = 0.0;
+    if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) {
+        *status = OR_BAD_INPUT;
+        *cost = NAN;
+        return;
+    }
+    const int V = s->V, K = c->K, S = c->S;
+    /* visible views: bounds and depth test */
+    int* vv_ = (int*)malloc(sizeof(int) * V);
+    double* vc = (double*)malloc(sizeof(double) * V);
+    double* vu = (double*)malloc(sizeof(double) * 2 * V);
+    int nvis = 0;
+    for (int v = 0; v < V; v++) {
+        const double* cam = s->cams + 16 * v;
+        double u, w, a, b;
+        if (!or_project(cam, p, s->W, s->H, &u, &w, &a, &b)) continue;
+        if (fabs(u - floor(u + 0.5)) < 1e-6 || fabs(w - floor(w + 0.5)) < 1e-6) *flags |= OR_FLAG_BOUNDARY;
+        const double Z = cam[10] * p[0] + cam[11] * p[1] + cam[12] * p[2] + cam[15];
+        const long long px = (long long)floor(w) * s->W + (long long)floor(u);
+        const double D = map_depth(depth, s, v, px);
+        if (fabs(Z - (D + c->eps_vis)) < 1e-5) *flags |= OR_FLAG_DEPTH_EDGE;
+        if (!(Z <= D + c->eps_vis)) continue;
+        vv_[nvis] = v;
+        vc[nvis] = conf_at(s, v, px);
+        vu[2 * nvis] = u;
+        vu[2 * nvis + 1] = w;
+        ++nvis;
+    }
+    /* top-K by confidence, ties to the lower view (selection keeps the view order on ties) */
+    int tk[16], nk = 0;
+    unsigned char* used = (unsigned char*)calloc(nvis > 0 ? nvis : 1, 1);
+    for (; nk < K && nk < nvis; nk++) {
+        int bj = -1;
+        for (int j = 0; j < nvis; j++)
+            if (!used[j] && (bj < 0 || vc[j] > vc[bj])) bj = j;
+        used[bj] = 1;
+        tk[nk] = bj;
+    }
+    free(used);
+    if (nk == 0) {
+        *status = OR_NO_VIEWS;
+        free(vv_), free(vc), free(vu);
+        return;
+    }
+    /* candidates: cand[j][s] offset points and unit directions */
+    double* off = (double*)malloc(sizeof(double) * 3 * nk * S);
+    double* dd = (double*)malloc(sizeof(double) * 3 * nk * S);
+    unsigned char* ok = (unsigned char*)calloc(nk * S, 1);
+    for (int j = 0; j < nk; j++) {
+        const int q = tk[j], v = vv_[q];
+        const double* cam = s->cams + 16 * v;
+        const long long px = (long long)floor(vu[2 * q + 1]) * s->W + (long long)floor(vu[2 * q]);
+        const double th = (double)s->angle[(size_t)v * s->W * s->H + (size_t)px];
+        const double ux = vu[2 * q] + c->lambda_px * cos(th), uy = vu[2 * q + 1] + c->lambda_px * sin(th);
+        if (fabs(ux - floor(ux + 0.5)) < 1e-5 || fabs(uy - floor(uy + 0.5)) < 1e-5) *flags |= OR_FLAG_BOUNDARY;
+        if (!(ux >= 0.0 && ux < (double)s->W && uy >= 0.0 && uy < (double)s->H)) continue;
+        const double z = map_depth(depth, s, v, (long long)floor(uy) * s->W + (long long)floor(ux));
+        if (!isfinite(z)) continue;
+        for (int k = 0; k < S; k++) {
+            const double zs = z + (S > 1 ? -c->delta + 2.0 * c->delta * k / (S - 1) : 0.0);
+            double* o = off + 3 * (j * S + k);
+            or_backproject(cam, ux, uy, zs, o);
+            const double e[3] = {o[0] - p[0], o[1] - p[1], o[2] - p[2]};
+            const double n = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            if (!(n > 1e-12)) continue;
+            for (int r = 0; r < 3; r++) dd[3 * (j * S + k) + r] = e[r] / n;
+            ok[j * S + k] = 1;
+        }
+    }
+    /* per depth layer: medoid, then the patch consistency of its offset point */
+    double best = -1.0, second = -1.0;
+    int bs = -1;
+    double bdir[3] = {0.0, 0.0, 0.0};
+    const int h = c->P / 2;
+    for (int k = 0; k < S; k++) {
+        double cd[3 * 16], cw[16], co[3 * 16];
+        int n = 0;
+        for (int j = 0; j < nk; j++) {
+            if (!ok[j * S + k]) continue;
+            for (int r = 0; r < 3; r++) {
+                cd[3 * n + r] = dd[3 * (j * S + k) + r];
+                co[3 * n + r] = off[3 * (j * S + k) + r];
+            }
+            cw[n] = vc[tk[j]];
+            ++n;
+        }
+        if (n == 0) continue;
+        double m1, m2;
+        const int mi = or_medoid(n, cd, cw, &m1, &m2);
+        if (n > 1 && m1 - m2 < 1e-5) *flags |= OR_FLAG_MEDOID_TIE;
+        const double* pf = co + 3 * mi;
+        double Lsum = 0.0;
+        for (int j = 0; j < nk; j++) {
+            const int q = tk[j], v = vv_[q];
+            const double* cam = s->cams + 16 * v;
+            double uf, wf, a, b;
+            or_project(cam, pf, s->W, s->H, &uf, &wf, &a, &b);
+            const double Zf = cam[10] * pf[0] + cam[11] * pf[1] + cam[12] * pf[2] + cam[15];
+            if (!(Zf > 1e-6)) continue;
+            const double r[2] = {uf - vu[2 * q], wf - vu[2 * q + 1]};
+            const double rn2 = r[0] * r[0] + r[1] * r[1];
+            const double Z = cam[10] * p[0] + cam[11] * p[1] + cam[12] * p[2] + cam[15];
+            const double e[3] = {pf[0] - p[0], pf[1] - p[1], pf[2] - p[2]};
+            const double en2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+            if (!(rn2 * Z * Z >= 1e-20 * (cam[0] * cam[0] + cam[1] * cam[1]) * en2)) continue;
+            const double rn = sqrt(rn2);
+            const long long x0 = (long long)floor(vu[2 * q]), y0 = (long long)floor(vu[2 * q + 1]);
+            double Lv = 0.0;
+            for (int dy = -h; dy <= h; dy++)
+                for (int dx = -h; dx <= h; dx++) {
+                    const long long x = x0 + dx, y = y0 + dy;
+                    if (x < 0 || y < 0 || x >= s->W || y >= s->H) continue;
+                    const long long px = y * s->W + x;
+                    const double th = (double)s->angle[(size_t)v * s->W * s->H + (size_t)px];
+                    const double L = conf_at(s, v, px) * fabs((r[0] / rn) * cos(th) + (r[1] / rn) * sin(th));
+                    if (L > Lv) Lv = L;
+                }
+            Lsum += Lv;
+        }
+        const double Lbar = Lsum / nk;
+        if (Lbar > best) {
+            second = best;
+            best = Lbar;
+            bs = k;
+            const double e[3] = {pf[0] - p[0], pf[1] - p[1], pf[2] - p[2]};
+            const double en = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            for (int r = 0; r < 3; r++) bdir[r] = e[r] / en;
+        } else if (Lbar > second) {
+            second = Lbar;
+        }
+    }
+    if (bs < 0) {
+        *status = OR_NO_VIEWS;
+    } else {
+        if (second >= 0.0 && best - second < 2e-6) *flags |= OR_FLAG_SEL_TIE;
+        const double sg = fabs(bdir[2]) > 1e-12 ? (bdir[2] > 0 ? 1.0 : -1.0)
+                          : fabs(bdir[1]) > 1e-12 ? (bdir[1] > 0 ? 1.0 : -1.0)
+                                                  : (bdir[0] >= 0 ? 1.0 : -1.0);
+        for (int r = 0; r < 3; r++) dir[r] = sg * bdir[r];
+        *cost = 1.0 - best;
+        *sel = bs;
+        *status = OR_OK;
+    }
+    free(off), free(dd), free(ok);
+    free(vv_), free(vc), free(vu);
+}
+
+int or_fpmvo(const or_scene* s, const float* depth, const or_fpmvo_cfg* c, long long n_idx, const long long* idx,
+             double* dir, double* cost, int32_t* sel, uint8_t* status, uint8_t* flags, int n_threads) {
+    if (c->K < 1 || c->K > 16 || c->S < 1 || c->S > 16 || c->P < 1 || !(c->P & 1)) return -1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long long q = 0; q < n_idx; q++) {
+        long long i = idx ? idx[q] : q;
+        or_fpmvo_point(s, depth, c, i, dir + 3 * q, cost + q, sel + q, status + q, flags + q);
+    }
+    return 0;
+}

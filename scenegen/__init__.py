@@ -74,7 +74,7 @@ def _load():
         lib.sg_make_points.argtypes = [p(SgConfig), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.sg_make_cameras.argtypes = [p(SgConfig), ctypes.c_void_p, ctypes.c_void_p]
         lib.sg_render_strand_maps.argtypes = [p(SgConfig), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                              ctypes.c_void_p, ctypes.c_int]
+                                              ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
         lib.sg_render_exact_maps.argtypes = [p(SgConfig), ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.sg_knn.argtypes = [ctypes.c_longlong, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
@@ -140,7 +140,7 @@ def serving_batch(first_seed=200, n=16):
     return out
 
 
-def make_scene(preset="tiny", seed=None, exact_maps=False, strand_maps=True, knn=True, **over):
+def make_scene(preset="tiny", seed=None, exact_maps=False, strand_maps=True, knn=True, depth=False, **over):
     """Generate one scene.  Returns a dict of numpy arrays and sizes:
 
     points (N,3) f32, tangents (N,3) f32 unit, strand_id (N,) i32,
@@ -148,7 +148,9 @@ def make_scene(preset="tiny", seed=None, exact_maps=False, strand_maps=True, knn
     cams_clean (V,16) f32 - the cameras the maps were rendered with,
     angle (V,H,W) f32 in [0, pi), conf (V,H,W) f32 or f16 in [0, 1],
     exact_angle/exact_conf/owner (if exact_maps): point-splatted maps of the true tangents,
-    nbr (N,k) i32 - k nearest other points, nearest first, ties to the lower index.
+    nbr (N,k) i32 - k nearest other points, nearest first, ties to the lower index,
+    depth (V,H,W) f32 (if depth) - camera-space depth Z of the front-most rendered strand, +inf where
+    no strand covers the pixel (the renderer's z-buffer, depth interpolated linearly along segments).
     Camera record: fx, fy, cx, cy, R (3x3 row-major world->camera), t (3); pixel axes +u right, +v down.
     """
     lib = _load()
@@ -169,9 +171,12 @@ def make_scene(preset="tiny", seed=None, exact_maps=False, strand_maps=True, knn
     if strand_maps:
         angle = np.empty((V, H, W), np.float32)
         conf = np.empty((V, H, W), np.float16 if cfg["conf_f16"] else np.float32)
+        dep = np.empty((V, H, W), np.float32) if depth else None
         lib.sg_render_strand_maps(ctypes.byref(c), _ptr(verts), _ptr(cams_clean), _ptr(angle), _ptr(conf),
-                                  1 if cfg["conf_f16"] else 0)
+                                  1 if cfg["conf_f16"] else 0, _ptr(dep))
         out["angle"], out["conf"] = angle, conf
+        if depth:
+            out["depth"] = dep
     if exact_maps:
         ea = np.empty((V, H, W), np.float32)
         ec = np.empty((V, H, W), np.float32)

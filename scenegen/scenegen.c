@@ -307,7 +307,7 @@ static void cam_apply(const float* cam, const double* p, double* X) {
  * on covered pixels, 0 elsewhere; then a fraction of pixels is replaced by outliers.
  * verts: n_strands x (n_segments+1) x 3 (f32), cams: the CLEAN cameras. */
 int sg_render_strand_maps(const sg_config* c, const float* verts, const float* cams,
-                          float* angle, void* conf, int conf_f16) {
+                          float* angle, void* conf, int conf_f16, float* depth) {
     const int W = c->width, H = c->height, ns = c->n_segments;
     const size_t npx = (size_t)W * H;
 #pragma omp parallel
@@ -373,6 +373,8 @@ int sg_render_strand_maps(const sg_config* c, const float* verts, const float* c
             } else {
                 memcpy((float*)conf + npx * v, cf, sizeof(float) * npx);
             }
+            /* the z-buffer: camera-space depth of the front-most strand, +inf where none */
+            if (depth) memcpy(depth + npx * v, zb, sizeof(float) * npx);
         }
         free(zb);
         free(cf);
