@@ -39,7 +39,8 @@ def build():
 def _load():
     global _lib
     if _lib is None:
-        if not os.path.exists(_LIB_PATH):
+        src = os.path.join(_HERE, "oracle.c")
+        if not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
             build()
         lib = ctypes.CDLL(_LIB_PATH)
         vp, ll, i32 = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int
@@ -226,15 +227,18 @@ def medoid(dirs, w):
     return i, b.value, s.value
 
 
-def fpmvo(scene, depth, K=5, S=5, P=5, lambda_px=4.0, delta=0.005, eps_vis=0.02, idx=None, threads=0):
+def fpmvo(scene, depth, K=5, S=5, P=5, lambda_px=4.0, delta=0.005, eps_vis=0.02, idx=None, threads=0,
+          layers=False):
     """The paper's FPMVO step (Sec. 3.1.1-3.1.3) for the points idx: candidates from depth samples
     around pixel-offset points, medoid fusion per depth layer over the top-K views, P x P patch
     consistency.  depth: (V, H, W) f32 camera-space depth maps (+inf where no hair).  Returns dict
-    dir (n, 3), cost (n,), sel (n,) chosen depth layer, status (n,), flags (n,)."""
+    dir (n, 3), cost (n,), sel (n,) chosen depth layer, status (n,), flags (n,); with layers=True
+    also layer_L (n, S), every layer's mean consistency (-1 without candidates), and layer_dir
+    (n, S, 3), its fused direction."""
     lib = _load()
     lib.or_fpmvo.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                             ctypes.c_int]
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
     dep = np.ascontiguousarray(depth, np.float32)
     cfg = _FpmvoCfg(K, S, P, lambda_px, delta, eps_vis)
     if idx is None:
@@ -244,8 +248,12 @@ def fpmvo(scene, depth, K=5, S=5, P=5, lambda_px=4.0, delta=0.005, eps_vis=0.02,
         n, ip = len(idx), _p(idx)
     out = dict(dir=np.empty((n, 3)), cost=np.empty(n), sel=np.empty(n, np.int32), status=np.empty(n, np.uint8),
                flags=np.empty(n, np.uint8))
+    lp = ld = None
+    if layers:
+        out["layer_L"], out["layer_dir"] = np.empty((n, S)), np.empty((n, S, 3))
+        lp, ld = _p(out["layer_L"]), _p(out["layer_dir"])
     rc = lib.or_fpmvo(ctypes.byref(scene.c), _p(dep), ctypes.byref(cfg), n, ip, _p(out["dir"]), _p(out["cost"]),
-                      _p(out["sel"]), _p(out["status"]), _p(out["flags"]), threads)
+                      _p(out["sel"]), _p(out["status"]), _p(out["flags"]), lp, ld, threads)
     if rc != 0:
         raise ValueError("fpmvo: K and S in [1, 16], P odd")
     return out

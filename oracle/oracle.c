@@ -439,11 +439,19 @@ typedef struct {
 
 enum { OR_FLAG_MEDOID_TIE = 8, OR_FLAG_SEL_TIE = 16, OR_FLAG_DEPTH_EDGE = 32 };
 
-/* Inverse projection (Eq. 3): the world point at camera depth z on the ray through pixel (u, v). */
+/* Inverse projection (Eq. 3): the world point at camera depth z on the ray through pixel (u, v),
+ * p = R^-1 (X - t).  The inverse is the true 3 x 3 inverse (adjugate over determinant), not R^T:
+ * a rotation stored in single precision is orthonormal only to ~1e-7, and R^T would move the
+ * point off the ray by that much times |p|, which is not small beside a pixel-sized offset. */
 void or_backproject(const double* cam, double u, double v, double z, double* p) {
+    const double* R = cam + 4;
     const double X[3] = {(u - cam[2]) * z / cam[0], (v - cam[3]) * z / cam[1], z};
-    double Y[3] = {X[0] - cam[13], X[1] - cam[14], X[2] - cam[15]};
-    for (int c = 0; c < 3; c++) p[c] = cam[4 + c] * Y[0] + cam[7 + c] * Y[1] + cam[10 + c] * Y[2];
+    const double Y[3] = {X[0] - cam[13], X[1] - cam[14], X[2] - cam[15]};
+    const double a[9] = {R[4] * R[8] - R[5] * R[7], R[2] * R[7] - R[1] * R[8], R[1] * R[5] - R[2] * R[4],
+                         R[5] * R[6] - R[3] * R[8], R[0] * R[8] - R[2] * R[6], R[2] * R[3] - R[0] * R[5],
+                         R[3] * R[7] - R[4] * R[6], R[1] * R[6] - R[0] * R[7], R[0] * R[4] - R[1] * R[3]};
+    const double det = R[0] * a[0] + R[1] * a[3] + R[2] * a[6];
+    for (int c = 0; c < 3; c++) p[c] = (a[3 * c] * Y[0] + a[3 * c + 1] * Y[1] + a[3 * c + 2] * Y[2]) / det;
 }
 
 /* Medoid of n unit directions with weights w (Eq. G, sigma, argmax): index of the largest
@@ -471,13 +479,29 @@ int or_medoid(int n, const double* d, const double* w, double* best_score, doubl
     return bi;
 }
 
+/* The output sign convention: positive z, else positive y, else non-negative x. */
+static void canonical_sign(const double* d, double* out) {
+    const double sg = fabs(d[2]) > 1e-12 ? (d[2] > 0 ? 1.0 : -1.0)
+                      : fabs(d[1]) > 1e-12 ? (d[1] > 0 ? 1.0 : -1.0)
+                                           : (d[0] >= 0 ? 1.0 : -1.0);
+    for (int r = 0; r < 3; r++) out[r] = sg * d[r];
+}
+
 static double map_depth(const float* depth, const or_scene* s, int v, long long px) {
     return (double)depth[(size_t)v * s->W * s->H + (size_t)px];
 }
 
+/* One point.  layer_L (S values) and layer_dir (S x 3), when not NULL, receive every depth layer's
+ * mean consistency (-1 where the layer has no candidate) and its fused direction with the canonical
+ * sign, so that a caller can check a result taken among near-tied layers. */
 void or_fpmvo_point(const or_scene* s, const float* depth, const or_fpmvo_cfg* c, long long i, double* dir,
-                    double* cost, int32_t* sel, uint8_t* status, uint8_t* flags) {
+                    double* cost, int32_t* sel, uint8_t* status, uint8_t* flags, double* layer_L, double* layer_dir) {
     const double* p = s->pts + 3 * i;
+    if (layer_L)
+        for (int k = 0; k < c->S; k++) {
+            layer_L[k] = -1.0;
+            layer_dir[3 * k] = layer_dir[3 * k + 1] = layer_dir[3 * k + 2] = 0.0;
+        }
     *flags = 0;
     *sel = -1;
     *cost = 1.0;
@@ -601,6 +625,13 @@ void or_fpmvo_point(const or_scene* s, const float* depth, const or_fpmvo_cfg* c
             Lsum += Lv;
         }
         const double Lbar = Lsum / nk;
+        if (layer_L) {
+            const double e[3] = {pf[0] - p[0], pf[1] - p[1], pf[2] - p[2]};
+            const double en = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            const double u[3] = {e[0] / en, e[1] / en, e[2] / en};
+            layer_L[k] = Lbar;
+            canonical_sign(u, layer_dir + 3 * k);
+        }
         if (Lbar > best) {
             second = best;
             best = Lbar;
@@ -616,10 +647,7 @@ void or_fpmvo_point(const or_scene* s, const float* depth, const or_fpmvo_cfg* c
         *status = OR_NO_VIEWS;
     } else {
         if (second >= 0.0 && best - second < 2e-6) *flags |= OR_FLAG_SEL_TIE;
-        const double sg = fabs(bdir[2]) > 1e-12 ? (bdir[2] > 0 ? 1.0 : -1.0)
-                          : fabs(bdir[1]) > 1e-12 ? (bdir[1] > 0 ? 1.0 : -1.0)
-                                                  : (bdir[0] >= 0 ? 1.0 : -1.0);
-        for (int r = 0; r < 3; r++) dir[r] = sg * bdir[r];
+        canonical_sign(bdir, dir);
         *cost = 1.0 - best;
         *sel = bs;
         *status = OR_OK;
@@ -629,7 +657,8 @@ void or_fpmvo_point(const or_scene* s, const float* depth, const or_fpmvo_cfg* c
 }
 
 int or_fpmvo(const or_scene* s, const float* depth, const or_fpmvo_cfg* c, long long n_idx, const long long* idx,
-             double* dir, double* cost, int32_t* sel, uint8_t* status, uint8_t* flags, int n_threads) {
+             double* dir, double* cost, int32_t* sel, uint8_t* status, uint8_t* flags, double* layer_L,
+             double* layer_dir, int n_threads) {
     if (c->K < 1 || c->K > 16 || c->S < 1 || c->S > 16 || c->P < 1 || !(c->P & 1)) return -1;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -637,7 +666,8 @@ int or_fpmvo(const or_scene* s, const float* depth, const or_fpmvo_cfg* c, long 
 #pragma omp parallel for schedule(dynamic, 16)
     for (long long q = 0; q < n_idx; q++) {
         long long i = idx ? idx[q] : q;
-        or_fpmvo_point(s, depth, c, i, dir + 3 * q, cost + q, sel + q, status + q, flags + q);
+        or_fpmvo_point(s, depth, c, i, dir + 3 * q, cost + q, sel + q, status + q, flags + q,
+                       layer_L ? layer_L + (size_t)q * c->S : NULL, layer_L ? layer_dir + (size_t)3 * q * c->S : NULL);
     }
     return 0;
 }

@@ -22,8 +22,12 @@ def look_at_cam(center, f=600.0, W=512, H=512):
 
 
 def test_backprojection_inverts_projection():
-    for _ in range(50):
+    for q in range(50):
         cam = look_at_cam(RNG.normal(size=3) * 3 + [0, 0, 0.1])
+        if q % 2:
+            # a matrix that is not orthonormal (a rotation stored in single precision is not exactly
+            # either): the inverse projection must still land on the point, so R^T will not do
+            cam[4:13] = (cam[4:13].reshape(3, 3) @ np.diag([1.01, 0.98, 1.0])).ravel()
         p = RNG.normal(size=3) * 0.3
         u, v = oracle.project(cam, p, 512, 512)[1:3]
         R = cam[4:13].reshape(3, 3)
@@ -142,6 +146,23 @@ def test_degenerate_points():
     far[np.isinf(far)] = 0.5
     r = oracle.fpmvo(oracle.Scene.from_dict(sc), np.minimum(far, 0.5), delta=0.01)
     assert np.all(r["status"][1:] == oracle.NO_VIEWS)
+
+
+def test_layer_outputs():
+    """Per-layer results: the best layer is the output, and the depth samples are laid out evenly
+    over [-Delta, Delta], so 3 samples are the first, middle and last of 5 and 1 is the middle."""
+    sc = scenegen.make_scene("tiny", depth=True)
+    scene = oracle.Scene.from_dict(sc)
+    r5 = oracle.fpmvo(scene, sc["depth"], S=5, delta=0.02, layers=True)
+    r3 = oracle.fpmvo(scene, sc["depth"], S=3, delta=0.02, layers=True)
+    r1 = oracle.fpmvo(scene, sc["depth"], S=1, delta=0.02, layers=True)
+    ok = r5["status"] == oracle.OK
+    assert ok.mean() > 0.8
+    assert np.array_equal(np.max(r5["layer_L"][ok], axis=1), 1.0 - r5["cost"][ok])
+    assert np.array_equal(r5["layer_dir"][ok, r5["sel"][ok]], r5["dir"][ok])
+    assert np.array_equal(r3["layer_L"], r5["layer_L"][:, [0, 2, 4]])
+    assert np.array_equal(r1["layer_L"][:, 0], r5["layer_L"][:, 2])
+    assert np.array_equal(r3["layer_dir"], r5["layer_dir"][:, [0, 2, 4]])
 
 
 def test_scene_runs_and_flags_are_rare():
