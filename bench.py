@@ -49,7 +49,11 @@ WORKLOADS = {
             "f32 angle + fp16 confidence, 0.5 deg pose noise, H=64, k=8, T=8",
     "mid": "plain fusion, mid: 200,000 points, 32 views 1024x1024 with 10% outlier pixels, H=64, k=8, T=8",
     "tiny": "plain fusion, tiny: 2,000 points, 8 views 256x256, H=32, k=5, T=4",
+    "fpmvo": "the paper's FPMVO step on the full scene (seed 2: 1,000,000 points, 64 views 1920x1080, f32 angle + "
+             "fp16 confidence, depth maps from the renderer's z-buffer): K=5 top views, S=5 depth samples over "
+             "[-0.0046, 0.0046], P=5 patch, lambda=4 px, depth-test tolerance 0.02",
 }
+FPMVO_CFG = dict(K=5, S=5, P=5, lambda_px=4.0, delta=0.0046, eps_vis=0.02)
 SM_COUNT, FP32_LANES_PER_SM = 148, 128
 
 
@@ -73,6 +77,8 @@ def parse():
     ap.add_argument("--workload", default="serving16", choices=list(WORKLOADS))
     ap.add_argument("--partition", action="store_true", help="full/mid/tiny under torchrun: every rank uploads "
                     "the same scene and fuses its own point range (strong scaling) instead of its own scene")
+    ap.add_argument("--fpmvo-scene", default="full", choices=["full", "mid"],
+                    help="fpmvo: the scene preset (mid: the small case for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--net", default=None, help="serving16: load the proposal network from this file instead of "
@@ -220,6 +226,8 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
+    if args.workload == "fpmvo":
+        return run_reference_fpmvo(args, world)
     if args.workload == "serving16":
         scenes = serving_scenes(200)
     elif args.workload == "learned":
@@ -262,6 +270,39 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "points_per_step": n},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_fpmvo(args, world):
+    """The FP64 oracle's FPMVO on the host cores, a bounded evenly spaced sample of the scene per step."""
+    import oracle
+    import scenegen
+    cfg = dict(FPMVO_CFG, eps_vis=float(np.float32(FPMVO_CFG["eps_vis"])))
+    sc = scenegen.make_scene("full", seed=scenegen.PRESET_SEEDS["full"], depth=True)
+    osc = oracle.Scene.from_dict(sc)
+    N = sc["N"]
+    run = lambda n: oracle.fpmvo(osc, sc["depth"], idx=np.linspace(0, N - 1, n).astype(np.int64), **cfg)
+    run(64)
+    t0 = time.perf_counter()
+    run(1024)
+    per_pt = (time.perf_counter() - t0) / 1024
+    n = int(min(N, max(64, 90.0 / max(1, args.steps + args.warmup) / max(per_pt, 1e-9))))
+    for _ in range(args.warmup):
+        run(max(1, n // 8))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run(n)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    sample = f"{n} of {N} points per step, evenly spaced; FP64 C + OpenMP FPMVO"
+    line = {"impl": "reference", "metric": "FPMVO points/s (depth-sample candidates, medoid fusion, patch "
+            "consistency)", "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["fpmvo"], "points_per_step": n, **cfg},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -920,10 +961,188 @@ def run_learned(args):
         pg.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------- FPMVO workload
+def fpmvo_units(sc, cfg):
+    """Exact work counts of one FPMVO pass, for the roofline: views in front of the camera and inside
+    the image per point (each tested against its depth map), views passing the test, and the top
+    views used (min(K, visible)); computed on the host in float64 (pixel edges aside)."""
+    P = sc["points"].astype(np.float64)
+    W, H, V = sc["W"], sc["H"], sc["V"]
+    dep = sc["depth"].reshape(V, -1)
+    inside = np.zeros(sc["N"], np.int64)
+    visible = np.zeros(sc["N"], np.int64)
+    for v in range(V):
+        cam = sc["cams"][v].astype(np.float64)
+        X = P @ cam[4:13].reshape(3, 3).T + cam[13:16]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = np.floor(cam[0] * X[:, 0] / X[:, 2] + cam[2])
+            w = np.floor(cam[1] * X[:, 1] / X[:, 2] + cam[3])
+        ok = (X[:, 2] > 1e-6) & (u >= 0) & (u < W) & (w >= 0) & (w < H)
+        inside += ok
+        px = (np.where(ok, w, 0) * W + np.where(ok, u, 0)).astype(np.int64)
+        visible += ok & (X[:, 2] <= dep[v][px] + cfg["eps_vis"])
+    top = np.minimum(visible, cfg["K"])
+    return {"inside_pv": int(inside.sum()), "visible_pv": int(visible.sum()), "top_pv": int(top.sum())}
+
+
+def fpmvo_bytes(u, N, cfg, conf_bytes):
+    """Algorithmic bytes of one pass: per in-image view the depth value (4 B) and, where visible, the
+    confidence; per top view the angle at the point's pixel and the depth at the offset pixel (4 + 4 B)
+    and the P x P patch of angle + confidence; the point (12 B) and the outputs (21 B)."""
+    P2 = cfg["P"] * cfg["P"]
+    return (4 * u["inside_pv"] + conf_bytes * u["visible_pv"] + u["top_pv"] * (8 + P2 * (4 + conf_bytes))
+            + 33 * N)
+
+
+def fpmvo_cpu_baseline(sc, cfg, budget_s=15.0):
+    import oracle
+    osc = oracle.Scene.from_dict(sc)
+    probe = np.arange(0, sc["N"], max(1, sc["N"] // 1024))
+    oracle.fpmvo(osc, sc["depth"], idx=probe[:64], **cfg)
+    t0 = time.perf_counter()
+    oracle.fpmvo(osc, sc["depth"], idx=probe, **cfg)
+    per_pt = (time.perf_counter() - t0) / len(probe)
+    n = int(min(sc["N"], max(len(probe), budget_s / max(per_pt, 1e-9))))
+    sel = np.linspace(0, sc["N"] - 1, n).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.fpmvo(osc, sc["depth"], idx=sel, **cfg)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "points/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{n} of {sc['N']} points, evenly spaced, FP64 C + OpenMP FPMVO, {dt:.1f} s"}
+
+
+def fpmvo_accuracy(sc, cfg, d, c, s, n_sample):
+    """Agreement with the FP64 oracle on a stratified sample: the layer, the angle and the cost."""
+    import oracle
+    sel = np.linspace(0, sc["N"] - 1, n_sample).astype(np.int64)
+    orc = oracle.fpmvo(oracle.Scene.from_dict(sc), sc["depth"], idx=sel, **cfg)
+    ok = orc["status"] == 0
+    a, b = d[sel].astype(np.float64), orc["dir"]
+    ang = np.degrees(np.arctan2(np.linalg.norm(np.cross(a, b), axis=1), np.abs(np.sum(a * b, axis=1))))[ok]
+    return {"median_deg": float(np.median(ang)), "p99_deg": float(np.percentile(ang, 99)),
+            "same_layer": float(np.mean(s[sel][ok] == orc["sel"][ok])),
+            "max_cost_err": float(np.max(np.abs(c[sel][ok] - orc["cost"][ok]))), "sample": int(n_sample)}
+
+
+def run_fpmvo(args):
+    import torch
+
+    import paper_2604_05794_b300 as hf
+    import scenegen
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    cfg = dict(FPMVO_CFG, eps_vis=float(np.float32(FPMVO_CFG["eps_vis"])))
+    sc = scenegen.make_scene(args.fpmvo_scene, seed=scenegen.PRESET_SEEDS[args.fpmvo_scene] + 100 * rank, depth=True)
+    N, V, W, H = sc["N"], sc["V"], sc["W"], sc["H"]
+    stream = torch.cuda.current_stream(dev)
+    f = hf.HairFuse(8, sc["k"], 0, stream=stream.cuda_stream)
+    gpu = {x: torch.from_numpy(sc[x]).to(dev) for x in ("cams", "angle", "conf", "points", "nbr", "depth")}
+    f.upload_views(gpu["cams"], gpu["angle"], gpu["conf"])
+    f.upload_points(gpu["points"], gpu["nbr"])
+    f.upload_depth(gpu["depth"])
+    out = (torch.empty((N, 3), device=dev), torch.empty(N, device=dev), torch.empty(N, dtype=torch.int32, device=dev),
+           torch.empty(N, dtype=torch.uint8, device=dev))
+    step = lambda: f.fpmvo(*out, **cfg)
+    Wm = max(3, args.warmup)
+    for _ in range(Wm):
+        step()
+    f.sync()
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(cvd.split(",")[local] if cvd else str(local))
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = f.stats()["launches"]
+    f.profile(True)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    kt = f.profile_read()
+    f.profile(False)
+    launches = f.stats()["launches"] - launches0
+    ms = reduce_over_ranks(ms, pg, dev)
+    value = reduce_over_ranks(N, pg, dev, "sum") * args.steps / (ms / 1e3)
+    units = fpmvo_units(sc, cfg)
+    n_, t_ = kt["k_fpmvo"]
+    sec = t_ / n_ / 1e3
+    byt = fpmvo_bytes(units, N, cfg, sc["conf"].itemsize)
+    ach = byt / sec / 1e9
+    roofline = {"bound": "hbm", "achieved": ach, "peak": HBM_GBS, "unit": "GB/s", "frac": ach / HBM_GBS,
+                "traffic": None, "kernel": "k_fpmvo", "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs",
+                "work": f"{byt / N:.0f} algorithmic B per point ({units['inside_pv']} in-image point-views, "
+                        f"{units['visible_pv']} visible, {units['top_pv']} top views per pass)",
+                "share": t_ / ms}
+    line = {"metric": "FPMVO points/s (depth-sample candidates, medoid fusion, patch consistency)", "value": value,
+            "unit": "points/s", "n_gpus": world, "steps": args.steps, "warmup": Wm, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["fpmvo"] if args.fpmvo_scene == "full" else
+                       f"FPMVO on the {args.fpmvo_scene} scene (profiling case)", "points": N, "views": V,
+                       "map": f"{W}x{H}", **cfg,
+                       "l2": "inputs larger than L2 (angle, confidence and depth maps "
+                             f"{(sc['angle'].nbytes + sc['conf'].nbytes + sc['depth'].nbytes) / 1e6:.0f} MB)",
+                       "parallelism": f"independent scenes per rank x{world}"},
+            "roofline": roofline, "units": units,
+            "kernels": {k_: {"launches": v[0], "ms_per_launch": v[1] / max(1, v[0]), "share": v[1] / ms}
+                        for k_, v in kt.items()},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        d, c, s_ = (x.cpu().numpy() for x in out[:3])
+        line["accuracy"] = fpmvo_accuracy(sc, cfg, d, c, s_, args.accuracy_sample or 2000)
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        hin = {x: pin(sc[x]) for x in ("cams", "angle", "conf", "points", "nbr", "depth")}
+        hout = (torch.empty((N, 3)).pin_memory(), torch.empty(N).pin_memory(),
+                torch.empty(N, dtype=torch.int32).pin_memory(), torch.empty(N, dtype=torch.uint8).pin_memory())
+        f2 = hf.HairFuse(8, sc["k"], 0, stream=stream.cuda_stream)
+
+        def e2e_step():
+            f2.upload_views(hin["cams"], hin["angle"], hin["conf"])
+            f2.upload_points(hin["points"], hin["nbr"])
+            f2.upload_depth(hin["depth"])
+            f2.fpmvo(*hout, **cfg)
+
+        e2e_step()
+        n_e2e = max(1, min(args.steps, 5))
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        dt = reduce_over_ranks(time.perf_counter() - t0, pg, dev)
+        line["e2e"] = {"value": reduce_over_ranks(N, pg, dev, "sum") * n_e2e / dt, "unit": "points/s",
+                       "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in hin.values())),
+                       "d2h_bytes_per_step": int(sum(x.numel() * x.element_size() for x in hout)), "steps": n_e2e,
+                       "path": "hair_fuse_upload_views/points/depth + hair_fuse_fpmvo with HF_HOST pinned buffers"}
+        f2.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = fpmvo_cpu_baseline(sc, cfg)
+    f.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "fpmvo":
+        run_fpmvo(args)
     elif args.workload == "serving16":
         run_serving(args)
     elif args.workload == "learned":

@@ -126,6 +126,45 @@ int hair_fuse_fuse_directions(hf_ctx* ctx, const float* hyps, float* dir_out, fl
 int hair_fuse_fuse_range(hf_ctx* ctx, int first, int count, const float* hyps, float* dir_out, float* cost_out,
                          int32_t* idx_out, uint8_t* status_out, int mem_kind);
 
+/* ------------------------------------------------------------------------------------------------
+ * The paper's own FPMVO step (Sec. 3.1.1-3.1.3), from depth maps instead of a hypothesis set:
+ *  - view v sees point i when it projects inside the image and X_z <= D_v(pixel) + eps_vis
+ *    (D_v: camera-space depth of the front-most hair, +inf where none);
+ *  - candidates (Eqs. 1-3): the pixel u_i^v + lambda_px (cos theta, sin theta) with theta the angle at
+ *    u_i^v, its depth z (nearest pixel), S depths z + delta_s spread evenly over [-delta, delta]
+ *    (both ends included), back-projected through the offset pixel; unit directions from p_i;
+ *  - medoid fusion (Eqs. G, sigma): for each depth layer s, over the top-K views by the confidence
+ *    at u_i^v (ties to the lower view), the candidate with the largest
+ *    sum_j w_j |<d_i, d_j>| / sum_j w_j (w_j = that confidence), first on ties;
+ *  - patch consistency (Eqs. proj_r, sim, patchloss, patch_min, final_dout): each layer's fused
+ *    offset point is reprojected into the top-K views, r = Pi_v(p_f) - Pi_v(p_i) normalised, the
+ *    largest C |<r, O>| over the P x P pixels around u_i^v, averaged over the views; the best layer
+ *    wins (lowest on ties); the direction p_f - p_i normalised with the canonical sign of
+ *    hair_fuse_fuse_directions; cost = 1 - that average; sel = the layer (-1 if none).
+ * Status: OK, NO_VIEWS (no view sees the point or no view yields a candidate: direction 0, cost 1),
+ * BAD_INPUT (non-finite point).  Limits: 1 <= K <= 8, K * S <= 32, P odd in [1, 7].
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct {
+    int K;              /* top-K views */
+    int S;              /* depth samples per view */
+    int P;              /* patch side in pixels (odd) */
+    float lambda_px;    /* pixel offset along the orientation */
+    float delta;        /* half range of the depth samples (scene units) */
+    float eps_vis;      /* depth-test tolerance (scene units) */
+} hf_fpmvo_cfg;
+
+/* Depth maps of the uploaded views: V x H x W f32 (kind mem_kind), copied into the context; the
+ * caller keeps ownership of depth.  Upload the views first (HF_ERR_NOT_UPLOADED otherwise);
+ * uploading new views requires new depth maps. */
+int hair_fuse_upload_depth(hf_ctx* ctx, const float* depth, int mem_kind);
+/* FPMVO of every uploaded point into dir_out (N x 3), cost_out (N), sel_out (N int32, may be NULL),
+ * status_out (N, may be NULL), all of kind mem_kind and owned by the caller; asynchronous on the
+ * context's stream for HF_DEVICE outputs.  Errors: HF_ERR_NOT_UPLOADED without views, points or
+ * depth maps of the current views; HF_ERR_INVALID_ARG for a configuration outside the limits above
+ * (or lambda_px, delta, eps_vis negative or not finite); CUDA failures as in every other call. */
+int hair_fuse_fpmvo(hf_ctx* ctx, const hf_fpmvo_cfg* cfg, float* dir_out, float* cost_out, int32_t* sel_out,
+                    uint8_t* status_out, int mem_kind);
+
 /* Evaluate the cost c_i(d) of M given directions for every point (no argmin, no refinement).
  *  dirs: N x M x 3 f32 (any non-zero length; the cost is scale- and sign-invariant),
  *  cost_out: N x M f32.  Both of kind mem_kind. */

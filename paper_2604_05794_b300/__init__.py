@@ -31,6 +31,11 @@ class hf_config(ctypes.Structure):
                 ("fallback_tau", ctypes.c_float), ("flags", ctypes.c_int)]
 
 
+class hf_fpmvo_cfg(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("S", ctypes.c_int), ("P", ctypes.c_int), ("lambda_px", ctypes.c_float),
+                ("delta", ctypes.c_float), ("eps_vis", ctypes.c_float)]
+
+
 class hf_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double)]
 
@@ -45,6 +50,8 @@ _SIGS = {
     "hair_fuse_fuse_directions_noalloc": ([ctypes.POINTER(hf_config), _i, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp,
                                            _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "hair_fuse_fuse_range": ([_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _i], _i),
+    "hair_fuse_upload_depth": ([_vp, _vp, _i], _i),
+    "hair_fuse_fpmvo": ([_vp, _vp, _vp, _vp, _vp, _vp, _i], _i),
     "hair_fuse_eval_costs": ([_vp, _i, _vp, _vp, _i], _i),
     "hair_fuse_fibonacci_hemisphere": ([_i, _vp], _i),
     "hair_fuse_gemm_bf16": ([_vp, _vp, _vp, _i, _i, _i, _vp], _i),
@@ -96,6 +103,8 @@ hair_fuse_upload_points = _lib.hair_fuse_upload_points
 hair_fuse_fuse_directions = _lib.hair_fuse_fuse_directions
 hair_fuse_fuse_directions_noalloc = _lib.hair_fuse_fuse_directions_noalloc
 hair_fuse_fuse_range = _lib.hair_fuse_fuse_range
+hair_fuse_upload_depth = _lib.hair_fuse_upload_depth
+hair_fuse_fpmvo = _lib.hair_fuse_fpmvo
 hair_fuse_eval_costs = _lib.hair_fuse_eval_costs
 hair_fuse_fibonacci_hemisphere = _lib.hair_fuse_fibonacci_hemisphere
 hair_fuse_gemm_bf16 = _lib.hair_fuse_gemm_bf16
@@ -262,6 +271,19 @@ class HairFuse:
         ptrs = [_ptr_kind(x) for x in (hyps, dir_out, cost_out, idx_out, status_out)]
         kind = _same_kind(*[p[1] for p in ptrs])
         self._c(hair_fuse_fuse_range(self.h, first, count, *[p[0] for p in ptrs], kind))
+
+    def upload_depth(self, depth):
+        """Depth maps (V, H, W) f32 of the uploaded views (host array or CUDA tensor)."""
+        p, kind, _keep = _ptr_kind(depth)
+        self._c(hair_fuse_upload_depth(self.h, p, kind))
+
+    def fpmvo(self, dir_out, cost_out=None, sel_out=None, status_out=None, K=5, S=5, P=5, lambda_px=4.0,
+              delta=0.005, eps_vis=0.02):
+        """The paper's FPMVO step (depth-sample candidates, medoid fusion, P x P patch consistency)."""
+        cfg = hf_fpmvo_cfg(K, S, P, lambda_px, delta, eps_vis)
+        ptrs = [_ptr_kind(x) for x in (dir_out, cost_out, sel_out, status_out)]
+        kind = _same_kind(*[q[1] for q in ptrs])
+        self._c(hair_fuse_fpmvo(self.h, ctypes.byref(cfg), *[q[0] for q in ptrs], kind))
 
     def eval_costs(self, dirs, cost_out):
         """Costs (N,M) of the directions dirs (N,M,3)."""

@@ -170,6 +170,7 @@ int hair_fuse_upload_views(hf_ctx* c, int V, int width, int height, const float*
     c->W = width;
     c->Hh = height;
     c->conf_dtype = conf_dtype;
+    ++c->views_gen;
     return HF_OK;
 }
 
@@ -414,7 +415,7 @@ void hair_fuse_destroy(hf_ctx* c) {
         cudaEventDestroy(r.beg);
         cudaEventDestroy(r.end);
     }
-    DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->amap, &c->pts, &c->nbr, &c->samp, &c->ab, &c->qtab,
+    DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->amap, &c->depth, &c->dmap, &c->vmap, &c->rlist, &c->pts, &c->nbr, &c->samp, &c->ab, &c->qtab,
                       &c->vthr, &c->hyps, &c->rot, &c->outs, &c->evald, &c->errw, &c->work, &c->best, &c->feat, &c->prop, &c->lmisc};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);

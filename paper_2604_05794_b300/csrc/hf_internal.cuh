@@ -56,6 +56,11 @@ struct hf_ctx {
     DevBuf prop;    // [N x 3] proposals
     DevBuf lmisc;   // bounding box, fallback count, short-refinement steps, fallback list
     DevBuf rlist;   // point range of hair_fuse_fuse_range: count, then the indices
+    DevBuf depth;   // [V][H][W] f32 staging of host depth maps (FPMVO), +inf where no hair
+    DevBuf dmap;    // [V][H][W] float2 (depth, confidence) for FPMVO's depth test and view selection
+    DevBuf vmap;    // [V][H][W] float2 C (cos theta, sin theta) for FPMVO's patches
+    long long views_gen = 0;   // bumped by every view upload
+    long long depth_gen = -1;  // views_gen the FPMVO maps were built for
     uint32_t* errw_host = nullptr;  // pinned read-back slot
     long long launches = 0;
     long long dev_bytes = 0;
@@ -209,3 +214,19 @@ cudaError_t hf_launch_start_select_batch(const StartSelectArgs* sa, const BatchC
 // vblock_q must be built for it); kp from hf_batch_kp_for(max k)
 cudaError_t hf_launch_argmin_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int hc, int nt, cudaStream_t s);
 cudaError_t hf_launch_refine_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int nt, cudaStream_t s);
+
+// ------------------------------------------------------------------ FPMVO (hf_fpmvo.cu)
+#define HF_FPMVO_MAX_K 8
+struct FpmvoArgs {
+    const float* pts; int N;
+    const float* cams; int V; int W; int H;
+    const float2* amap;     // (angle, confidence)
+    const float2* dmap;     // (depth, confidence)
+    const float2* vmap;     // C (cos theta, sin theta)
+    int K, S, P;
+    float lambda, delta, eps;
+    float* dir_out; float* cost_out; int32_t* sel_out; uint8_t* status_out;
+};
+cudaError_t hf_launch_fpmvo(const FpmvoArgs& a, cudaStream_t s);
+cudaError_t hf_launch_fpmvo_maps(const float* depth, const float2* amap, size_t npx, float2* dmap, float2* vmap,
+                                 cudaStream_t s);
