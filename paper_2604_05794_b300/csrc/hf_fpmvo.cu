@@ -1,19 +1,24 @@
-// hf_fpmvo.cu - the paper's FPMVO step on the GPU (Sec. 3.1.1-3.1.3), warp per point:
+// hf_fpmvo.cu - the paper's FPMVO step on the GPU (Sec. 3.1.1-3.1.3) in two kernels.
 //
-//   lanes over views   visibility (frustum, bounds, depth test against the depth map) and the
-//                      confidence at the point's pixel; then the top-K views (K warp argmaxes);
-//   lane j < K         pixel offset u + lambda O(u) of view j (Eq. 1) and the depth there;
-//   lane s K + j       candidate of view j at depth sample s (Eqs. 2-3), a unit direction;
-//   group s            medoid of its K candidates (similarity |<d_i, d_j>|, confidence weights);
-//   lane s K + j       patch consistency of layer s's fused offset point in view j: Eq. proj_r
-//                      with the finite offset, Eqs. sim and patchloss over the P x P patch around
-//                      the point's pixel (staged once per view in shared memory), Eq. patch_min;
+// k_fpmvo_views, a thread per point (the lanes of a warp hold consecutive points along the strands,
+// so their gathers meet nearby pixels of one view at a time):
+//   every view         pixel decision, (depth, confidence) gather, depth test; the top-K views;
+//   every top view     the pixel offset u + lambda O(u) (Eq. 1) and the depth there, written as a
+//                      record for the second kernel.
+// k_fpmvo_fuse, a warp per point:
+//   lane (j, dy)       a row of the P x P patch of C (cos theta, sin theta) around the point's pixel;
+//   lane s nk + j      candidate of top view j at depth sample s (Eqs. 2-3), a unit direction;
+//   group s            medoid of its candidates (similarity |<d_i, d_j>|, confidence weights);
+//   lane s nk + j      patch consistency of layer s's fused offset point in view j: Eq. proj_r
+//                      with the finite offset, Eqs. sim and patchloss over the patch, Eq. patch_min;
 //   lane 0             mean over the views per layer, the best layer (Eq. final_dout), outputs.
 //
-// Pixel decisions (the point's pixel and the offset pixel) use float-float arithmetic, as in the
-// projection kernel, so they agree with an exact evaluation except within ~1e-10 px of an edge.
+// Pixel and depth-test decisions are taken in FP32 where a proven bound on its rounding error
+// leaves them unambiguous and in float-float otherwise, so they agree with an exact evaluation
+// except within ~1e-10 px (or depth units) of an edge.
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "hf_ff.cuh"
 #include "hf_internal.cuh"
@@ -22,7 +27,6 @@ using namespace hf_ff;
 
 namespace {
 
-constexpr int kFpWarps = 4;   // points per CTA
 constexpr float kU = 5.9604645e-8f;   // 2^-24, the unit roundoff of FP32
 
 // FP32 projection of p into a view together with a bound on its rounding error, so that a pixel or
@@ -109,15 +113,156 @@ __device__ __forceinline__ int view_pixel(const float* cam, float p0, float p1, 
     return (int)fv * W + (int)fu;
 }
 
-// Phase 2 of k_fpmvo for one point, by one warp: the candidates from its top views, medoid fusion per
-// depth layer, patch consistency and the outputs.  tkv / tkc: its nk top views and their
-// confidences; patch: K x P x P float2 of shared memory; px: K pixel slots of shared memory.
+// Top-K insertion: (key descending, view ascending) over K slots, the last slot dropping out.  The
+// order is total, so an entry pushed down by the new one keeps its place among equal keys.
+template <int K>
+__device__ __forceinline__ void top_insert(uint32_t (&tk)[K], int (&tv)[K], uint32_t key, int v) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        if (key > tk[q] || (key == tk[q] && v < tv[q])) {
+            const uint32_t k2 = tk[q];
+            const int v2 = tv[q];
+            tk[q] = key;
+            tv[q] = v;
+            key = k2;
+            v = v2;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ k_fpmvo_views: a thread per point
+// Every view's pixel decision and (depth, confidence) gather, the depth test, the top-K views, and
+// per top view the pixel offset and the depth there (Eq. 1).  The threads of a warp hold
+// consecutive points, which lie along the same strands, so each of their gathers goes to nearby
+// pixels of the same view; two views per step keep two gathers in flight.  Output per point: the
+// number of top views (-1 for a non-finite point) and one record of three 16-byte words per top
+// view (see FpmvoArgs).
+constexpr int kViewsThreads = 128;
+template <int K>
+__global__ void __launch_bounds__(kViewsThreads, 9) k_fpmvo_views(FpmvoArgs a) {
+    __shared__ int s_tv[kViewsThreads][HF_FPMVO_MAX_K];
+    __shared__ float s_tc[kViewsThreads][HF_FPMVO_MAX_K];
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * kViewsThreads + t;
+    if (i >= a.N) return;
+    const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
+    if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) {
+        a.nk[i] = -1;
+        return;
+    }
+    const float a0 = fabsf(p0), a1 = fabsf(p1), a2 = fabsf(p2);
+    const size_t npx = (size_t)a.W * a.H;
+    uint32_t tk[K];
+    int tv[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        tk[q] = 0u;
+        tv[q] = 0;
+    }
+    constexpr int G = 2;
+    for (int v0 = 0; v0 < a.V; v0 += G) {
+        int pix[G];
+        FastProj f[G];
+        bool hf[G];
+#pragma unroll
+        for (int r = 0; r < G; ++r) {
+            ff zff;
+            pix[r] = v0 + r < a.V ? view_pixel(a.cams + 16 * (v0 + r), p0, p1, p2, a0, a1, a2, a.W, a.H, f[r], zff,
+                                               hf[r])
+                                  : -1;
+        }
+        float2 dc[G];
+#pragma unroll
+        for (int r = 0; r < G; ++r)
+            dc[r] = pix[r] >= 0 ? __ldg(a.dmap + (size_t)(v0 + r) * npx + pix[r]) : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int r = 0; r < G; ++r) {
+            if (pix[r] < 0) continue;
+            int vis = hf[r] ? -1 : depth_test_fast(f[r].Z, f[r].eZ, dc[r].x, a.eps);
+            if (vis < 0) {   // float-float depth (recomputed: rare, and cheaper than keeping it live)
+                const float* cam = a.cams + 16 * (v0 + r);
+                vis = depth_test_ff(ff_dot3_plus(cam[10], cam[11], cam[12], p0, p1, p2, cam[15]), dc[r].x, a.eps);
+            }
+            if (vis) top_insert(tk, tv, conf_key(dc[r].y), v0 + r);
+        }
+    }
+    int nk = 0;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        if (tk[q] != 0u) {
+            s_tv[t][q] = tv[q];
+            s_tc[t][q] = __uint_as_float(tk[q] - 1u);
+            nk = q + 1;
+        }
+    }
+    // per top view: the point's pixel position, its float-float depth, the offset pixel and its depth
+    for (int q = 0; q < nk; ++q) {
+        const int v = s_tv[t][q];
+        const float* cam = a.cams + 16 * v;
+        const FastProj f = fast_project(cam, p0, p1, p2, a0, a1, a2);
+        const ff X2 = ff_dot3_plus(cam[10], cam[11], cam[12], p0, p1, p2, cam[15]);
+        float fu, fv;
+        const bool su = sure_floor(f.uf, f.mu, fu);
+        const bool sure = sure_floor(f.wf, f.mw, fv) && su;
+        ff u = {f.uf, 0.0f}, w = {f.wf, 0.0f};
+        bool have_uw = false;
+        if (!sure) {
+            const ff X0 = ff_dot3_plus(cam[4], cam[5], cam[6], p0, p1, p2, cam[13]);
+            const ff X1 = ff_dot3_plus(cam[7], cam[8], cam[9], p0, p1, p2, cam[14]);
+            u = ff_affine(cam[0], ff_div(X0, X2), cam[2]);
+            w = ff_affine(cam[1], ff_div(X1, X2), cam[3]);
+            fu = ff_floor(u);
+            fv = ff_floor(w);
+            have_uw = true;
+        }
+        const float th = __ldg(&a.amap[(size_t)v * npx + (size_t)((int)fv * a.W + (int)fu)].x);
+        float sn, cs;
+        sincosf(th, &sn, &cs);
+        const float lc = a.lambda * cs, ls = a.lambda * sn;
+        // the offset pixel floor(u + lambda cos theta), floor(w + lambda sin theta)
+        float gx, gy;
+        bool osure = false;
+        if (!have_uw) {
+            const float ux = f.uf + lc, uy = f.wf + ls;
+            const bool sx = sure_floor(ux, fmaf(fabsf(ux), 1.2e-7f, f.mu), gx);
+            osure = sure_floor(uy, fmaf(fabsf(uy), 1.2e-7f, f.mw), gy) && sx;
+        }
+        if (!osure) {
+            if (!have_uw) {
+                const ff X0 = ff_dot3_plus(cam[4], cam[5], cam[6], p0, p1, p2, cam[13]);
+                const ff X1 = ff_dot3_plus(cam[7], cam[8], cam[9], p0, p1, p2, cam[14]);
+                u = ff_affine(cam[0], ff_div(X0, X2), cam[2]);
+                w = ff_affine(cam[1], ff_div(X1, X2), cam[3]);
+            }
+            gx = ff_floor(ff_add(u, ff{lc, 0.0f}));
+            gy = ff_floor(ff_add(w, ff{ls, 0.0f}));
+        }
+        float zc = __int_as_float(0x7f800000);   // no depth outside the image
+        if (gx >= 0.0f && gx < (float)a.W && gy >= 0.0f && gy < (float)a.H)
+            zc = __ldg(&a.dmap[(size_t)v * npx + (size_t)((int)gy * a.W + (int)gx)].x);
+        float4* r = a.rec + ((size_t)i * a.K + q) * 3;
+        r[0] = make_float4(__int_as_float(v), s_tc[t][q], fu, fv);
+        r[1] = make_float4(u.hi + u.lo, w.hi + w.lo, lc, ls);
+        r[2] = make_float4(X2.hi, X2.lo, zc, 0.0f);
+    }
+    a.nk[i] = nk;
+}
+
+// ------------------------------------------------------------------ k_fpmvo_fuse: a warp per point
+// From the records of the point's top views: the P x P patches (each lane loads a patch row), the
+// candidates of Eqs. 2-3 (lane c = s nk + j: view j, depth sample s), the medoid of each depth layer
+// (Eqs. G, sigma), the patch consistency of each layer's fused offset point in each top view (Eqs.
+// proj_r, sim, patchloss, patch_min), the mean over the views, the best layer and the outputs.
+constexpr int kFuseWarps = 4;
+__constant__ int c_div256[HF_FPMVO_MAX_K + 1] = {0, 256, 128, 86, 64, 52, 43, 37, 32};   // ceil(256 / n)
+// One point of k_fpmvo_fuse, by one warp.  nk: its number of top views; R0, R1, R2: lane j < nk
+// holds the record of top view j; cand, offs, slot0, patch: the warp's shared memory.
 template <int P>
-__device__ __forceinline__ void fpmvo_point(const FpmvoArgs& a, int i, int nk, const int* tkv, const float* tkc,
-                                            float2* patch, int (*px)[2], int lane) {
+__device__ __forceinline__ void fuse_point(const FpmvoArgs& a, int i, int nk, const float4& R0, const float4& R1,
+                                           const float4& R2, float4* cand, float4* offs, float4* slot0, float2* patch,
+                                           int lane) {
     constexpr int P2 = P * P, h = P / 2;
     const int S = a.S;
-    const size_t npx = (size_t)a.W * a.H;
     if (nk <= 0) {   // -1: non-finite point; 0: no view sees it
         if (lane == 0) {
             a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
@@ -127,152 +272,80 @@ __device__ __forceinline__ void fpmvo_point(const FpmvoArgs& a, int i, int nk, c
         }
         return;
     }
-    const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
-    const float a0 = fabsf(p0), a1 = fabsf(p1), a2 = fabsf(p2);
-    // ---- per top view: the point's pixel and the offset pixel's depth (Eq. 1)
-    // lane j keeps: the point's pixel position (u, w), its camera depth Zp (float-float), the offset
-    // lambda (cos theta, sin theta) and the depth z at the offset pixel.  The angle read at the
-    // point's pixel and the patch reads below are issued together; then the offset pixel's depth.
-    float pu = 0.0f, pw = 0.0f, zph = 0.0f, zpl = 0.0f, lc = 0.0f, ls = 0.0f, zc = 0.0f;
-    bool vok = false;
-    FastProj ft;
-    ff u = {0.0f, 0.0f}, w = {0.0f, 0.0f}, X2 = {0.0f, 0.0f};
-    bool sure = true;
-    float th = 0.0f;
-    const float* tcam = a.cams + 16 * tkv[lane < nk ? lane : 0];
-    const size_t tbase = (size_t)tkv[lane < nk ? lane : 0] * npx;
-    if (lane < nk) {
-        const float* cam = tcam;
-        ft = fast_project(cam, p0, p1, p2, a0, a1, a2);
-        X2 = ff_dot3_plus(cam[10], cam[11], cam[12], p0, p1, p2, cam[15]);   // for the offsets
-        float fu, fv;
-        const bool su = sure_floor(ft.uf, ft.mu, fu);
-        sure = sure_floor(ft.wf, ft.mw, fv) && su;
-        u = ff{ft.uf, 0.0f};
-        w = ff{ft.wf, 0.0f};
-        if (!sure) {
-            const ff X0 = ff_dot3_plus(cam[4], cam[5], cam[6], p0, p1, p2, cam[13]);
-            const ff X1 = ff_dot3_plus(cam[7], cam[8], cam[9], p0, p1, p2, cam[14]);
-            u = ff_affine(cam[0], ff_div(X0, X2), cam[2]);
-            w = ff_affine(cam[1], ff_div(X1, X2), cam[3]);
-            fu = ff_floor(u);
-            fv = ff_floor(w);
-        }
-        px[lane][0] = (int)fu;
-        px[lane][1] = (int)fv;
-        th = __ldg(&a.amap[tbase + (size_t)((int)fv * a.W + (int)fu)].x);
-    }
+    const size_t npx = (size_t)a.W * a.H;
+    if (lane < nk) slot0[lane] = R0;
     __syncwarp();
-    // the P x P patch of every top view: C (cos theta, sin theta), 0 outside the image; up to 128
-    // elements per pass, four loads per lane in flight
-    constexpr int kPatchRegs = 4;
-    const int npatch = nk * P2;
-    float2 pv[kPatchRegs];
+    // patch rows: lane (j, dy) loads P pixels of C (cos theta, sin theta), 0 outside the image
+    for (int row = lane; row < nk * P; row += 32) {
+        const int j = row / P, dy = row - j * P;
+        const float4 r0 = slot0[j];
+        const int v = __float_as_int(r0.x);
+        const int x0 = (int)r0.z - h;
+        const int y = (int)r0.w + dy - h;
+        float2 pv[P];
+        const bool yin = y >= 0 && y < a.H;
+        const float2* base = a.vmap + (size_t)v * npx + (size_t)(yin ? y : 0) * a.W;
 #pragma unroll
-    for (int r = 0; r < kPatchRegs; ++r) {
-        const int e = lane + 32 * r;
-        pv[r] = make_float2(0.0f, 0.0f);
-        if (e < npatch) {
-            const int j = e / P2, q = e - j * P2;
-            const int x = px[j][0] + (q % P) - h, y = px[j][1] + (q / P) - h;
-            if (x >= 0 && y >= 0 && x < a.W && y < a.H)
-                pv[r] = __ldg(a.vmap + (size_t)tkv[j] * npx + (size_t)(y * a.W + x));
+        for (int dx = 0; dx < P; ++dx) {
+            const int x = x0 + dx;
+            pv[dx] = yin && x >= 0 && x < a.W ? __ldg(base + x) : make_float2(0.0f, 0.0f);
         }
-    }
-    if (lane < nk) {
-        float sn, cs;
-        sincosf(th, &sn, &cs);
-        lc = a.lambda * cs;
-        ls = a.lambda * sn;
-        // the offset pixel floor(u + lambda cos theta), floor(w + lambda sin theta)
-        float gx, gy;
-        bool osure = false;
-        if (sure) {
-            const float ux = ft.uf + lc, uy = ft.wf + ls;
-            const bool sx = sure_floor(ux, fmaf(fabsf(ux), 1.2e-7f, ft.mu), gx);
-            osure = sure_floor(uy, fmaf(fabsf(uy), 1.2e-7f, ft.mw), gy) && sx;
-        }
-        if (!osure) {
-            if (sure) {   // the point's pixel was decided in FP32: its float-float position now
-                const float* cam = tcam;
-                const ff X0 = ff_dot3_plus(cam[4], cam[5], cam[6], p0, p1, p2, cam[13]);
-                const ff X1 = ff_dot3_plus(cam[7], cam[8], cam[9], p0, p1, p2, cam[14]);
-                u = ff_affine(cam[0], ff_div(X0, X2), cam[2]);
-                w = ff_affine(cam[1], ff_div(X1, X2), cam[3]);
-            }
-            gx = ff_floor(ff_add(u, ff{lc, 0.0f}));
-            gy = ff_floor(ff_add(w, ff{ls, 0.0f}));
-        }
-        pu = u.hi + u.lo;
-        pw = w.hi + w.lo;
-        zph = X2.hi;
-        zpl = X2.lo;
-        if (gx >= 0.0f && gx < (float)a.W && gy >= 0.0f && gy < (float)a.H)
-            zc = __ldg(&a.dmap[tbase + (size_t)((int)gy * a.W + (int)gx)].x);
-        else
-            zc = __int_as_float(0x7f800000);   // no depth outside the image
-    }
 #pragma unroll
-    for (int r = 0; r < kPatchRegs; ++r)
-        if (lane + 32 * r < npatch) patch[lane + 32 * r] = pv[r];
-    for (int e = lane + 32 * kPatchRegs; e < npatch; e += 32) {   // larger K x P x P
-        const int j = e / P2, q = e - j * P2;
-        const int x = px[j][0] + (q % P) - h, y = px[j][1] + (q / P) - h;
-        float2 sv = make_float2(0.0f, 0.0f);
-        if (x >= 0 && y >= 0 && x < a.W && y < a.H)
-            sv = __ldg(a.vmap + (size_t)tkv[j] * npx + (size_t)(y * a.W + x));
-        patch[e] = sv;
+        for (int dx = 0; dx < P; ++dx) patch[j * P2 + dy * P + dx] = pv[dx];
     }
-    vok = lane < nk && isfinite(zc);
-    __syncwarp();
-    // ---- candidates (Eqs. 2-3): lane c = s K + j
+    // ---- candidates (Eqs. 2-3)
     const int nc = nk * S;
-    const int s = lane / nk, j = lane - s * nk;   // meaningful for lane < nc
+    // s = lane / nk as (lane ceil(256 / nk)) >> 8, exact for lane < 32 and nk <= 8
+    const int s = (lane * c_div256[nk]) >> 8, j = lane - s * nk;   // meaningful for lane < nc
     const int srcj = lane < nc ? j : 0;
-    const float bu = __shfl_sync(0xffffffffu, pu, srcj), bw = __shfl_sync(0xffffffffu, pw, srcj);
-    const float bzh = __shfl_sync(0xffffffffu, zph, srcj), bzl = __shfl_sync(0xffffffffu, zpl, srcj);
-    const float blc = __shfl_sync(0xffffffffu, lc, srcj), bls = __shfl_sync(0xffffffffu, ls, srcj);
-    const float bz = __shfl_sync(0xffffffffu, zc, srcj);
-    const bool bok = __shfl_sync(0xffffffffu, (int)vok, srcj) != 0;
-    float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, wj = 0.0f;
+    const int vj = __float_as_int(__shfl_sync(0xffffffffu, R0.x, srcj));
+    // the camera of view j: (fx, fy, cx, cy), R rows, t
+    const float4* cq = reinterpret_cast<const float4*>(a.cams) + 4 * vj;
+    const float4 c0 = __ldg(cq), c1 = __ldg(cq + 1), c2 = __ldg(cq + 2), c3 = __ldg(cq + 3);
+    const float fx = c0.x, fy = c0.y, cx = c0.z, cy = c0.w;
+    const float r00 = c1.x, r01 = c1.y, r02 = c1.z, r10 = c1.w, r11 = c2.x, r12 = c2.y, r20 = c2.z, r21 = c2.w,
+                r22 = c3.x, t0 = c3.y, t1 = c3.z;
+    const float wj = __shfl_sync(0xffffffffu, R0.y, srcj);
+    const float bu = __shfl_sync(0xffffffffu, R1.x, srcj), bw = __shfl_sync(0xffffffffu, R1.y, srcj);
+    const float blc = __shfl_sync(0xffffffffu, R1.z, srcj), bls = __shfl_sync(0xffffffffu, R1.w, srcj);
+    const float bzh = __shfl_sync(0xffffffffu, R2.x, srcj), bzl = __shfl_sync(0xffffffffu, R2.y, srcj);
+    const float bz = __shfl_sync(0xffffffffu, R2.z, srcj);
+    float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
     bool cok = false;
-    if (lane < nc && bok) {
-        const float* cam = a.cams + 16 * tkv[j];
-        const float ds = S > 1 ? -a.delta + 2.0f * a.delta * (float)s / (float)(S - 1) : 0.0f;
+    float4 cd = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (lane < nc && isfinite(bz)) {
+        const float ds = a.ds[s];
         const float zs = bz + ds;
         // the offset in camera coordinates without cancellation: with Zp the point's depth,
         // X_cand - X_p = ((lambda c zs + (u - cx)(zs - Zp)) / fx, (lambda s zs + (w - cy)(zs - Zp)) / fy,
         // zs - Zp), and zs - Zp = (z - Zp.hi) - Zp.lo + delta_s (the first difference is exact)
         const float dz = __fadd_rn(__fsub_rn(__fsub_rn(bz, bzh), bzl), ds);
-        const float Y0 = fmaf(blc, zs, (bu - cam[2]) * dz) / cam[0];
-        const float Y1 = fmaf(bls, zs, (bw - cam[3]) * dz) / cam[1];
+        const float Y0 = __fdividef(fmaf(blc, zs, (bu - cx) * dz), fx);
+        const float Y1 = __fdividef(fmaf(bls, zs, (bw - cy) * dz), fy);
         // world offset e = R^T Y
-        e0 = fmaf(cam[4], Y0, fmaf(cam[7], Y1, cam[10] * dz));
-        e1 = fmaf(cam[5], Y0, fmaf(cam[8], Y1, cam[11] * dz));
-        e2 = fmaf(cam[6], Y0, fmaf(cam[9], Y1, cam[12] * dz));
-        const float n = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
-        if (n > 1e-12f) {
-            const float rn = 1.0f / n;
-            d0 = e0 * rn;
-            d1 = e1 * rn;
-            d2 = e2 * rn;
+        e0 = fmaf(r00, Y0, fmaf(r10, Y1, r20 * dz));
+        e1 = fmaf(r01, Y0, fmaf(r11, Y1, r21 * dz));
+        e2 = fmaf(r02, Y0, fmaf(r12, Y1, r22 * dz));
+        const float n2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+        if (n2 > 1e-24f) {
+            const float rn = rsqrtf(n2);
+            cd = make_float4(e0 * rn, e1 * rn, e2 * rn, wj);
             cok = true;
         }
-        wj = tkc[j];
     }
-    // ---- medoid of group s: sigma = sum_k w_k |<d, d_k>| / sum_k w_k over the group's valid candidates
+    cand[lane] = cd;   // an invalid candidate has weight 0 and adds nothing below
+    offs[lane] = make_float4(e0, e1, e2, 0.0f);
+    __syncwarp();
+    // ---- medoid of group s: sigma = sum_k w_k |<d, d_k>| / sum_k w_k over the group's candidates
+    // (the members of a group share the denominator, so the numerators decide; a zero weight sum
+    // makes every numerator 0 and the first candidate wins, as sigma = 0 would)
     const int g0 = lane < nc ? s * nk : 0;
-    float num = 0.0f, den = 0.0f;
+    float num = 0.0f;
     for (int k = 0; k < nk; ++k) {
-        const float q0 = __shfl_sync(0xffffffffu, d0, g0 + k), q1 = __shfl_sync(0xffffffffu, d1, g0 + k);
-        const float q2 = __shfl_sync(0xffffffffu, d2, g0 + k), qw = __shfl_sync(0xffffffffu, wj, g0 + k);
-        const bool qk = __shfl_sync(0xffffffffu, (int)cok, g0 + k) != 0;
-        if (qk) {
-            num += qw * fabsf(fmaf(d0, q0, fmaf(d1, q1, d2 * q2)));
-            den += qw;
-        }
+        const float4 q = cand[g0 + k];
+        num = fmaf(q.w, fabsf(fmaf(cd.x, q.x, fmaf(cd.y, q.y, cd.z * q.z))), num);
     }
-    const float sigma = cok ? (den > 0.0f ? num / den : 0.0f) : -1.0f;
+    const float sigma = cok ? num : -1.0f;
     int med = -1;   // lane of the group's medoid
     float msig = -1.0f;
     for (int k = 0; k < nk; ++k) {
@@ -284,27 +357,25 @@ __device__ __forceinline__ void fpmvo_point(const FpmvoArgs& a, int i, int nk, c
     }
     const bool layer_ok = lane < nc && msig >= 0.0f;
     // the fused offset point of layer s, as an offset from p
-    const int msrc = med >= 0 ? med : 0;
-    const float f0 = __shfl_sync(0xffffffffu, e0, msrc), f1 = __shfl_sync(0xffffffffu, e1, msrc);
-    const float f2 = __shfl_sync(0xffffffffu, e2, msrc);
-    // ---- patch consistency of layer s in view j (Eqs. proj_r, sim, patchloss, patch_min)
+    const float4 fo = offs[med >= 0 ? med : 0];
+    // ---- patch consistency of layer s in view j
     float Lv = 0.0f;
     if (layer_ok) {
-        const float* cam = a.cams + 16 * tkv[j];
-        const float X0 = fmaf(cam[4], p0, fmaf(cam[5], p1, fmaf(cam[6], p2, cam[13])));
-        const float X1 = fmaf(cam[7], p0, fmaf(cam[8], p1, fmaf(cam[9], p2, cam[14])));
-        const float Z = fmaf(cam[10], p0, fmaf(cam[11], p1, fmaf(cam[12], p2, cam[15])));
-        const float q0 = fmaf(cam[4], f0, fmaf(cam[5], f1, cam[6] * f2));
-        const float q1 = fmaf(cam[7], f0, fmaf(cam[8], f1, cam[9] * f2));
-        const float q2 = fmaf(cam[10], f0, fmaf(cam[11], f1, cam[12] * f2));
+        const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
+        const float X0 = fmaf(r00, p0, fmaf(r01, p1, fmaf(r02, p2, t0)));
+        const float X1 = fmaf(r10, p0, fmaf(r11, p1, fmaf(r12, p2, t1)));
+        const float Z = bzh;
+        const float q0 = fmaf(r00, fo.x, fmaf(r01, fo.y, r02 * fo.z));
+        const float q1 = fmaf(r10, fo.x, fmaf(r11, fo.y, r12 * fo.z));
+        const float q2 = fmaf(r20, fo.x, fmaf(r21, fo.y, r22 * fo.z));
         const float Zf = Z + q2;
         if (Zf > 1e-6f) {
-            // Pi(p + f) - Pi(p) without cancellation: fx (Z q_x - X_x q_z) / (Z Z_f)
-            const float rden = 1.0f / (Z * Zf);
-            const float rx = cam[0] * fmaf(Z, q0, -X0 * q2) * rden, ry = cam[1] * fmaf(Z, q1, -X1 * q2) * rden;
+            // Pi(p + f) - Pi(p) = fx (Z q_x - X_x q_z) / (Z Z_f), ...: the positive factor 1 / (Z Z_f)
+            // drops out of the normalised direction and moves to the other side of the degeneracy test
+            const float rx = fx * fmaf(Z, q0, -X0 * q2), ry = fy * fmaf(Z, q1, -X1 * q2);
             const float rn2 = fmaf(rx, rx, ry * ry);
-            const float en2 = fmaf(f0, f0, fmaf(f1, f1, f2 * f2));
-            if (rn2 * Z * Z >= 1e-20f * fmaf(cam[0], cam[0], cam[1] * cam[1]) * en2) {
+            const float en2 = fmaf(fo.x, fo.x, fmaf(fo.y, fo.y, fo.z * fo.z));
+            if (rn2 >= 1e-20f * fmaf(fx, fx, fy * fy) * en2 * (Zf * Zf)) {
                 const float inv = rsqrtf(rn2);
                 const float ux = rx * inv, uy = ry * inv;
                 const float2* pt = patch + j * P2;
@@ -317,9 +388,10 @@ __device__ __forceinline__ void fpmvo_point(const FpmvoArgs& a, int i, int nk, c
         }
     }
     // mean over the views of layer s, in view order
+    // (every layer divides by the same nk, so the sums decide; lane 0 divides the best one)
     float lsum = 0.0f;
     for (int k = 0; k < nk; ++k) lsum += __shfl_sync(0xffffffffu, Lv, g0 + k);
-    const float lbar = layer_ok ? lsum / (float)nk : -1.0f;
+    const float lbar = layer_ok ? lsum : -1.0f;
     // ---- the best layer (lowest s on ties) and the outputs
     float best = -1.0f;
     int bs = -1;
@@ -330,9 +402,8 @@ __device__ __forceinline__ void fpmvo_point(const FpmvoArgs& a, int i, int nk, c
             bs = q;
         }
     }
-    const int osrc = bs >= 0 ? bs * nk : 0;
-    const float o0 = __shfl_sync(0xffffffffu, f0, osrc), o1 = __shfl_sync(0xffffffffu, f1, osrc);
-    const float o2 = __shfl_sync(0xffffffffu, f2, osrc);
+    // the best layer's fused offset: that of the medoid lane of group bs
+    const int osrc = __shfl_sync(0xffffffffu, med, bs >= 0 ? bs * nk : 0);
     if (lane == 0) {
         if (bs < 0) {
             a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
@@ -340,123 +411,50 @@ __device__ __forceinline__ void fpmvo_point(const FpmvoArgs& a, int i, int nk, c
             if (a.sel_out) a.sel_out[i] = -1;
             if (a.status_out) a.status_out[i] = HF_STATUS_NO_VIEWS;
         } else {
-            const float n = sqrtf(o0 * o0 + o1 * o1 + o2 * o2);
-            const float x0 = o0 / n, x1 = o1 / n, x2 = o2 / n;
+            const float4 o = offs[osrc >= 0 ? osrc : 0];
+            const float rn = rsqrtf(fmaf(o.x, o.x, fmaf(o.y, o.y, o.z * o.z)));
+            const float x0 = o.x * rn, x1 = o.y * rn, x2 = o.z * rn;
             const float sgn = fabsf(x2) > 1e-12f ? copysignf(1.0f, x2)
                               : fabsf(x1) > 1e-12f ? copysignf(1.0f, x1) : copysignf(1.0f, x0);
             a.dir_out[3 * i] = sgn * x0;
             a.dir_out[3 * i + 1] = sgn * x1;
             a.dir_out[3 * i + 2] = sgn * x2;
-            if (a.cost_out) a.cost_out[i] = 1.0f - best;
+            if (a.cost_out) a.cost_out[i] = 1.0f - best / (float)nk;
             if (a.sel_out) a.sel_out[i] = bs;
             if (a.status_out) a.status_out[i] = HF_STATUS_OK;
         }
     }
 }
 
-
-// Top-K insertion: (key descending, view ascending) over kTopSlots slots, the last slot dropping
-// out.  The order is total, so an entry pushed down by the new one keeps its place among equal keys.
-constexpr int kTopSlots = HF_FPMVO_MAX_K;
-__device__ __forceinline__ void top_insert(uint32_t (&tk)[kTopSlots], int (&tv)[kTopSlots], uint32_t key, int v) {
-#pragma unroll
-    for (int q = 0; q < kTopSlots; ++q) {
-        if (key > tk[q] || (key == tk[q] && v < tv[q])) {
-            const uint32_t k2 = tk[q];
-            const int v2 = tv[q];
-            tk[q] = key;
-            tv[q] = v;
-            key = k2;
-            v = v2;
-        }
-    }
-}
-
-// Phase 1, a thread per point: every view's pixel decision and (depth, confidence) gather, the
-// depth test and the top-K views.  The threads of a warp hold consecutive points, which lie along
-// the same strands, so each of their gathers goes to nearby pixels of the same view.  Two views
-// per step keep two gathers in flight.  Phase 2, a warp per point: fpmvo_point.
-constexpr int kFpThreads = kFpWarps * 32;
 template <int P>
-__global__ void __launch_bounds__(kFpThreads, 8) k_fpmvo(FpmvoArgs a) {
+__global__ void __launch_bounds__(kFuseWarps * 32) k_fpmvo_fuse(FpmvoArgs a) {
     constexpr int P2 = P * P;
-    extern __shared__ __align__(16) float2 fp_patch[];   // [kFpWarps][K * P2]
-    __shared__ int s_tv[kFpThreads][HF_FPMVO_MAX_K];
-    __shared__ float s_tc[kFpThreads][HF_FPMVO_MAX_K];
-    __shared__ int s_nk[kFpThreads];
-    __shared__ int s_px[kFpWarps][HF_FPMVO_MAX_K][2];
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int i0 = blockIdx.x * kFpThreads;
-    {
-        const int i = i0 + t;
-        int nk = 0;
-        if (i < a.N) {
-            const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
-            if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) {
-                nk = -1;
-            } else {
-                const float a0 = fabsf(p0), a1 = fabsf(p1), a2 = fabsf(p2);
-                const size_t npx = (size_t)a.W * a.H;
-                uint32_t tk[kTopSlots];
-                int tv[kTopSlots];
-#pragma unroll
-                for (int q = 0; q < kTopSlots; ++q) {
-                    tk[q] = 0u;
-                    tv[q] = 0;
-                }
-                constexpr int G = 2;
-                for (int v0 = 0; v0 < a.V; v0 += G) {
-                    int pix[G];
-                    FastProj f[G];
-                    ff zff[G];
-                    bool hf[G];
-#pragma unroll
-                    for (int r = 0; r < G; ++r)
-                        pix[r] = v0 + r < a.V ? view_pixel(a.cams + 16 * (v0 + r), p0, p1, p2, a0, a1, a2, a.W, a.H,
-                                                           f[r], zff[r], hf[r])
-                                              : -1;
-                    float2 dc[G];
-#pragma unroll
-                    for (int r = 0; r < G; ++r)
-                        dc[r] = pix[r] >= 0 ? __ldg(a.dmap + (size_t)(v0 + r) * npx + pix[r]) : make_float2(0.0f, 0.0f);
-#pragma unroll
-                    for (int r = 0; r < G; ++r) {
-                        if (pix[r] < 0) continue;
-                        int vis = hf[r] ? -1 : depth_test_fast(f[r].Z, f[r].eZ, dc[r].x, a.eps);
-                        if (vis < 0) {
-                            const float* cam = a.cams + 16 * (v0 + r);
-                            if (!hf[r]) zff[r] = ff_dot3_plus(cam[10], cam[11], cam[12], p0, p1, p2, cam[15]);
-                            vis = depth_test_ff(zff[r], dc[r].x, a.eps);
-                        }
-                        if (vis) top_insert(tk, tv, conf_key(dc[r].y), v0 + r);
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < kTopSlots; ++q) {
-                    if (q < a.K && tk[q] != 0u) {
-                        s_tv[t][q] = tv[q];
-                        s_tc[t][q] = __uint_as_float(tk[q] - 1u);
-                        nk = q + 1;
-                    }
-                }
-            }
-        }
-        s_nk[t] = nk;
+    extern __shared__ __align__(16) float4 fu_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kFuseWarps + warp;
+    if (i >= a.N) return;   // whole warp
+    const int K = a.K;
+    // per warp: 32 candidates (unit direction, weight), 32 offsets e, the first record word of each
+    // top view, K x P2 patch float2
+    float4* cand = fu_smem + (size_t)warp * (64 + HF_FPMVO_MAX_K + (K * P2 + 1) / 2);
+    float4* offs = cand + 32;
+    float4* slot0 = offs + 32;
+    float2* patch = reinterpret_cast<float2*>(slot0 + HF_FPMVO_MAX_K);
+    const int nk = a.nk[i];
+    float4 R0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), R1 = R0, R2 = R0;
+    if (lane < nk) {
+        const float4* r = a.rec + ((size_t)i * K + lane) * 3;
+        R0 = __ldg(r);
+        R1 = __ldg(r + 1);
+        R2 = __ldg(r + 2);
     }
-    __syncthreads();
-    float2* patch = fp_patch + (size_t)warp * a.K * P2;
-    for (int q = 0; q < 32; ++q) {
-        const int tt = warp * 32 + q, i = i0 + tt;
-        if (i >= a.N) break;
-        fpmvo_point<P>(a, i, s_nk[tt], s_tv[tt], s_tc[tt], patch, s_px[warp], lane);
-        __syncwarp();
-    }
+    fuse_point<P>(a, i, nk, R0, R1, R2, cand, offs, slot0, patch, lane);
 }
 
 template <int P>
-cudaError_t launch_fpmvo(const FpmvoArgs& a, cudaStream_t s) {
-    const size_t smem = (size_t)kFpWarps * a.K * P * P * sizeof(float2);
-    k_fpmvo<P><<<(a.N + kFpThreads - 1) / kFpThreads, kFpThreads, smem, s>>>(a);
+cudaError_t launch_fpmvo_fuse(const FpmvoArgs& a, cudaStream_t s) {
+    const size_t smem = (size_t)kFuseWarps * (64 + HF_FPMVO_MAX_K + (a.K * P * P + 1) / 2) * sizeof(float4);
+    k_fpmvo_fuse<P><<<(a.N + kFuseWarps - 1) / kFuseWarps, kFuseWarps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -476,12 +474,26 @@ __global__ void k_fpmvo_maps(const float* __restrict__ depth, const float2* __re
 }  // namespace
 
 cudaError_t hf_launch_fpmvo(const FpmvoArgs& a, cudaStream_t s) {
-    switch (a.P) {
-        case 1: return launch_fpmvo<1>(a, s);
-        case 3: return launch_fpmvo<3>(a, s);
-        case 5: return launch_fpmvo<5>(a, s);
-        case 7: return launch_fpmvo<7>(a, s);
+    if (a.P != 1 && a.P != 3 && a.P != 5 && a.P != 7) return cudaErrorInvalidValue;
+    const unsigned vb = (unsigned)((a.N + kViewsThreads - 1) / kViewsThreads);
+    switch (a.K) {
+        case 1: k_fpmvo_views<1><<<vb, kViewsThreads, 0, s>>>(a); break;
+        case 2: k_fpmvo_views<2><<<vb, kViewsThreads, 0, s>>>(a); break;
+        case 3: k_fpmvo_views<3><<<vb, kViewsThreads, 0, s>>>(a); break;
+        case 4: k_fpmvo_views<4><<<vb, kViewsThreads, 0, s>>>(a); break;
+        case 5: k_fpmvo_views<5><<<vb, kViewsThreads, 0, s>>>(a); break;
+        case 6: k_fpmvo_views<6><<<vb, kViewsThreads, 0, s>>>(a); break;
+        case 7: k_fpmvo_views<7><<<vb, kViewsThreads, 0, s>>>(a); break;
+        case 8: k_fpmvo_views<8><<<vb, kViewsThreads, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    switch (a.P) {
+        case 1: return launch_fpmvo_fuse<1>(a, s);
+        case 3: return launch_fpmvo_fuse<3>(a, s);
+        case 5: return launch_fpmvo_fuse<5>(a, s);
+        default: return launch_fpmvo_fuse<7>(a, s);
     }
 }
 
@@ -548,9 +560,17 @@ extern "C" int hair_fuse_fpmvo(hf_ctx* c, const hf_fpmvo_cfg* cfg, float* dir_ou
         d_sel = sel_out ? (int32_t*)(base + (size_t)N * 16) : nullptr;
         d_st = status_out ? (uint8_t*)(base + (size_t)N * 20) : nullptr;
     }
+    const size_t nk_bytes = ((size_t)N * sizeof(int) + 255) & ~(size_t)255;
+    // depth samples delta_s = -Delta + 2 Delta s / (S - 1), s = 0 .. S-1 (0 for S = 1), in double
+    float ds[32];
+    for (int q = 0; q < 32; ++q)
+        ds[q] = q < g.S && g.S > 1 ? (float)(-(double)g.delta + 2.0 * (double)g.delta * q / (g.S - 1)) : 0.0f;
+    if ((rc = hf_ensure(c, c->fprec, nk_bytes + (size_t)N * g.K * 3 * sizeof(float4)))) return rc;
     FpmvoArgs a{(const float*)c->pts.p, N, (const float*)c->cams.p, c->V, c->W, c->Hh, (const float2*)c->amap.p,
-                (const float2*)c->dmap.p, (const float2*)c->vmap.p, g.K, g.S, g.P, g.lambda_px, g.delta, g.eps_vis,
+                (const float2*)c->dmap.p, (const float2*)c->vmap.p, (int*)c->fprec.p,
+                (float4*)((char*)c->fprec.p + nk_bytes), g.K, g.S, g.P, g.lambda_px, g.delta, g.eps_vis,
                 d_dir, d_cost, d_sel, d_st};
+    memcpy(a.ds, ds, sizeof(ds));
     if ((rc = run_launch(c, "k_fpmvo", [&] { return hf_launch_fpmvo(a, c->stream); }))) return rc;
     if (mem_kind == HF_HOST) {
         cudaError_t e = cudaMemcpyAsync(dir_out, d_dir, (size_t)N * 12, cudaMemcpyDeviceToHost, c->stream);
