@@ -6,7 +6,7 @@
 //   every top view     the pixel offset u + lambda O(u) (Eq. 1) and the depth there, written as a
 //                      record for the second kernel.
 // k_fpmvo_fuse, a warp per point:
-//   lane (j, dy)       a row of the P x P patch of C (cos theta, sin theta) around the point's pixel;
+//   lane e             element e of the P x P patches of C (cos theta, sin theta) around the pixel;
 //   lane s nk + j      candidate of top view j at depth sample s (Eqs. 2-3), a unit direction;
 //   group s            medoid of its candidates (similarity |<d_i, d_j>|, confidence weights);
 //   lane s nk + j      patch consistency of layer s's fused offset point in view j: Eq. proj_r
@@ -130,13 +130,22 @@ __device__ __forceinline__ void top_insert(uint32_t (&tk)[K], int (&tv)[K], uint
     }
 }
 
+// Zero records q0 .. K-1 of point i (the fusion kernel loads all K); record 0 carries nk in its
+// last word either way.
+__device__ __forceinline__ void write_empty_records(const FpmvoArgs& a, int i, int q0, int nk) {
+    for (int q = q0; q < a.K; ++q) {
+        float4* r = a.rec + ((size_t)i * a.K + q) * 3;
+        r[0] = r[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        r[2] = make_float4(0.0f, 0.0f, 0.0f, q == 0 ? __int_as_float(nk) : 0.0f);
+    }
+}
+
 // ------------------------------------------------------------------ k_fpmvo_views: a thread per point
 // Every view's pixel decision and (depth, confidence) gather, the depth test, the top-K views, and
 // per top view the pixel offset and the depth there (Eq. 1).  The threads of a warp hold
 // consecutive points, which lie along the same strands, so each of their gathers goes to nearby
-// pixels of the same view; two views per step keep two gathers in flight.  Output per point: the
-// number of top views (-1 for a non-finite point) and one record of three 16-byte words per top
-// view (see FpmvoArgs).
+// pixels of the same view; two views per step keep two gathers in flight.  Output per point: K
+// records of three 16-byte words, one per top view and zeros past the last (see FpmvoArgs).
 constexpr int kViewsThreads = 128;
 template <int K>
 __global__ void __launch_bounds__(kViewsThreads, 9) k_fpmvo_views(FpmvoArgs a) {
@@ -147,7 +156,7 @@ __global__ void __launch_bounds__(kViewsThreads, 9) k_fpmvo_views(FpmvoArgs a) {
     if (i >= a.N) return;
     const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
     if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) {
-        a.nk[i] = -1;
+        write_empty_records(a, i, 0, -1);
         return;
     }
     const float a0 = fabsf(p0), a1 = fabsf(p1), a2 = fabsf(p2);
@@ -243,26 +252,29 @@ __global__ void __launch_bounds__(kViewsThreads, 9) k_fpmvo_views(FpmvoArgs a) {
         float4* r = a.rec + ((size_t)i * a.K + q) * 3;
         r[0] = make_float4(__int_as_float(v), s_tc[t][q], fu, fv);
         r[1] = make_float4(u.hi + u.lo, w.hi + w.lo, lc, ls);
-        r[2] = make_float4(X2.hi, X2.lo, zc, 0.0f);
+        r[2] = make_float4(X2.hi, X2.lo, zc, __int_as_float(nk));
     }
-    a.nk[i] = nk;
+    write_empty_records(a, i, nk, nk);
 }
 
 // ------------------------------------------------------------------ k_fpmvo_fuse: a warp per point
 // From the records of the point's top views: the P x P patches (each lane loads a patch row), the
-// candidates of Eqs. 2-3 (lane c = s nk + j: view j, depth sample s), the medoid of each depth layer
+// candidates of Eqs. 2-3 (lane c = s K + j: top view j, depth sample s), the medoid of each depth layer
 // (Eqs. G, sigma), the patch consistency of each layer's fused offset point in each top view (Eqs.
 // proj_r, sim, patchloss, patch_min), the mean over the views, the best layer and the outputs.
 constexpr int kFuseWarps = 4;
 __constant__ int c_div256[HF_FPMVO_MAX_K + 1] = {0, 256, 128, 86, 64, 52, 43, 37, 32};   // ceil(256 / n)
-// One point of k_fpmvo_fuse, by one warp.  nk: its number of top views; R0, R1, R2: lane j < nk
-// holds the record of top view j; cand, offs, slot0, patch: the warp's shared memory.
-template <int P>
+// One point of k_fpmvo_fuse, by one warp.  nk: its number of top views; R0, R1, R2: lane j < K
+// holds the record of top view j (zeros for j >= nk); cand, offs, slot0, patch: the warp's shared
+// memory.  KT, ST: K and S when fixed at compile time (the paper's configuration), 0 to read them.
+// Lane groups are K wide whatever nk is: a lane j >= nk has no candidate (weight 0, so it adds
+// nothing to the weighted sums) and a patch term of 0 (so the view sums are those over nk views).
+template <int P, int KT, int ST>
 __device__ __forceinline__ void fuse_point(const FpmvoArgs& a, int i, int nk, const float4& R0, const float4& R1,
                                            const float4& R2, float4* cand, float4* offs, float4* slot0, float2* patch,
                                            int lane) {
     constexpr int P2 = P * P, h = P / 2;
-    const int S = a.S;
+    const int K = KT ? KT : a.K, S = ST ? ST : a.S;
     if (nk <= 0) {   // -1: non-finite point; 0: no view sees it
         if (lane == 0) {
             a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
@@ -273,30 +285,36 @@ __device__ __forceinline__ void fuse_point(const FpmvoArgs& a, int i, int nk, co
         return;
     }
     const size_t npx = (size_t)a.W * a.H;
+    const float p0 = __ldg(a.pts + 3 * i), p1 = __ldg(a.pts + 3 * i + 1), p2 = __ldg(a.pts + 3 * i + 2);
     if (lane < nk) slot0[lane] = R0;
     __syncwarp();
-    // patch rows: lane (j, dy) loads P pixels of C (cos theta, sin theta), 0 outside the image
-    for (int row = lane; row < nk * P; row += 32) {
-        const int j = row / P, dy = row - j * P;
-        const float4 r0 = slot0[j];
-        const int v = __float_as_int(r0.x);
-        const int x0 = (int)r0.z - h;
-        const int y = (int)r0.w + dy - h;
-        float2 pv[P];
-        const bool yin = y >= 0 && y < a.H;
-        const float2* base = a.vmap + (size_t)v * npx + (size_t)(yin ? y : 0) * a.W;
+    // the P x P patches of C (cos theta, sin theta) around the point's pixel in every top view, 0
+    // outside the image: consecutive lanes take consecutive pixels of a row, four loads in flight
+    const int npatch = nk * P2;
+    for (int e0 = 0; e0 < npatch; e0 += 128) {
+        float2 pv[4];
 #pragma unroll
-        for (int dx = 0; dx < P; ++dx) {
-            const int x = x0 + dx;
-            pv[dx] = yin && x >= 0 && x < a.W ? __ldg(base + x) : make_float2(0.0f, 0.0f);
+        for (int r = 0; r < 4; ++r) {
+            const int e = e0 + lane + 32 * r;
+            pv[r] = make_float2(0.0f, 0.0f);
+            if (e < npatch) {
+                const int j = e / P2, q = e - j * P2;
+                const int dy = q / P, dx = q - dy * P;
+                const float4 r0 = slot0[j];
+                const int x = (int)r0.z + dx - h, y = (int)r0.w + dy - h;
+                if (x >= 0 && y >= 0 && x < a.W && y < a.H)
+                    pv[r] = __ldg(a.vmap + (size_t)__float_as_int(r0.x) * npx + (size_t)(y * a.W + x));
+            }
         }
 #pragma unroll
-        for (int dx = 0; dx < P; ++dx) patch[j * P2 + dy * P + dx] = pv[dx];
+        for (int r = 0; r < 4; ++r)
+            if (e0 + lane + 32 * r < npatch) patch[e0 + lane + 32 * r] = pv[r];
     }
     // ---- candidates (Eqs. 2-3)
-    const int nc = nk * S;
-    // s = lane / nk as (lane ceil(256 / nk)) >> 8, exact for lane < 32 and nk <= 8
-    const int s = (lane * c_div256[nk]) >> 8, j = lane - s * nk;   // meaningful for lane < nc
+    const int nc = K * S;
+    // s = lane / K (as (lane ceil(256 / K)) >> 8 when K is not fixed: exact for lane < 32, K <= 8)
+    const int s = KT ? lane / KT : (lane * c_div256[K]) >> 8, j = lane - s * K;   // meaningful for lane < nc
+    const bool cand_lane = lane < nc && j < nk;
     const int srcj = lane < nc ? j : 0;
     const int vj = __float_as_int(__shfl_sync(0xffffffffu, R0.x, srcj));
     // the camera of view j: (fx, fy, cx, cy), R rows, t
@@ -313,7 +331,7 @@ __device__ __forceinline__ void fuse_point(const FpmvoArgs& a, int i, int nk, co
     float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
     bool cok = false;
     float4 cd = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (lane < nc && isfinite(bz)) {
+    if (cand_lane && isfinite(bz)) {
         const float ds = a.ds[s];
         const float zs = bz + ds;
         // the offset in camera coordinates without cancellation: with Zp the point's depth,
@@ -339,29 +357,30 @@ __device__ __forceinline__ void fuse_point(const FpmvoArgs& a, int i, int nk, co
     // ---- medoid of group s: sigma = sum_k w_k |<d, d_k>| / sum_k w_k over the group's candidates
     // (the members of a group share the denominator, so the numerators decide; a zero weight sum
     // makes every numerator 0 and the first candidate wins, as sigma = 0 would)
-    const int g0 = lane < nc ? s * nk : 0;
+    const int g0 = lane < nc ? s * K : 0;
     float num = 0.0f;
-    for (int k = 0; k < nk; ++k) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
         const float4 q = cand[g0 + k];
         num = fmaf(q.w, fabsf(fmaf(cd.x, q.x, fmaf(cd.y, q.y, cd.z * q.z))), num);
     }
     const float sigma = cok ? num : -1.0f;
     int med = -1;   // lane of the group's medoid
     float msig = -1.0f;
-    for (int k = 0; k < nk; ++k) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
         const float sk = __shfl_sync(0xffffffffu, sigma, g0 + k);
         if (sk > msig) {
             msig = sk;
             med = g0 + k;
         }
     }
-    const bool layer_ok = lane < nc && msig >= 0.0f;
+    const bool layer_ok = lane < nc && msig >= 0.0f;   // the layer has a candidate
     // the fused offset point of layer s, as an offset from p
     const float4 fo = offs[med >= 0 ? med : 0];
     // ---- patch consistency of layer s in view j
     float Lv = 0.0f;
-    if (layer_ok) {
-        const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
+    if (layer_ok && j < nk) {
         const float X0 = fmaf(r00, p0, fmaf(r01, p1, fmaf(r02, p2, t0)));
         const float X1 = fmaf(r10, p0, fmaf(r11, p1, fmaf(r12, p2, t1)));
         const float Z = bzh;
@@ -390,20 +409,22 @@ __device__ __forceinline__ void fuse_point(const FpmvoArgs& a, int i, int nk, co
     // mean over the views of layer s, in view order
     // (every layer divides by the same nk, so the sums decide; lane 0 divides the best one)
     float lsum = 0.0f;
-    for (int k = 0; k < nk; ++k) lsum += __shfl_sync(0xffffffffu, Lv, g0 + k);
+#pragma unroll
+    for (int k = 0; k < K; ++k) lsum += __shfl_sync(0xffffffffu, Lv, g0 + k);
     const float lbar = layer_ok ? lsum : -1.0f;
     // ---- the best layer (lowest s on ties) and the outputs
     float best = -1.0f;
     int bs = -1;
+#pragma unroll
     for (int q = 0; q < S; ++q) {
-        const float lq = __shfl_sync(0xffffffffu, lbar, q * nk < nc ? q * nk : 0);
+        const float lq = __shfl_sync(0xffffffffu, lbar, q * K);
         if (lq > best) {
             best = lq;
             bs = q;
         }
     }
     // the best layer's fused offset: that of the medoid lane of group bs
-    const int osrc = __shfl_sync(0xffffffffu, med, bs >= 0 ? bs * nk : 0);
+    const int osrc = __shfl_sync(0xffffffffu, med, bs >= 0 ? bs * K : 0);
     if (lane == 0) {
         if (bs < 0) {
             a.dir_out[3 * i] = a.dir_out[3 * i + 1] = a.dir_out[3 * i + 2] = 0.0f;
@@ -426,7 +447,7 @@ __device__ __forceinline__ void fuse_point(const FpmvoArgs& a, int i, int nk, co
     }
 }
 
-template <int P>
+template <int P, int KT, int ST>
 __global__ void __launch_bounds__(kFuseWarps * 32) k_fpmvo_fuse(FpmvoArgs a) {
     constexpr int P2 = P * P;
     extern __shared__ __align__(16) float4 fu_smem[];
@@ -440,21 +461,22 @@ __global__ void __launch_bounds__(kFuseWarps * 32) k_fpmvo_fuse(FpmvoArgs a) {
     float4* offs = cand + 32;
     float4* slot0 = offs + 32;
     float2* patch = reinterpret_cast<float2*>(slot0 + HF_FPMVO_MAX_K);
-    const int nk = a.nk[i];
+    // every point has K records, so they load without waiting for the count (in record 0)
     float4 R0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), R1 = R0, R2 = R0;
-    if (lane < nk) {
+    if (lane < K) {
         const float4* r = a.rec + ((size_t)i * K + lane) * 3;
         R0 = __ldg(r);
         R1 = __ldg(r + 1);
         R2 = __ldg(r + 2);
     }
-    fuse_point<P>(a, i, nk, R0, R1, R2, cand, offs, slot0, patch, lane);
+    const int nk = __float_as_int(__shfl_sync(0xffffffffu, R2.w, 0));
+    fuse_point<P, KT, ST>(a, i, nk, R0, R1, R2, cand, offs, slot0, patch, lane);
 }
 
-template <int P>
+template <int P, int KT = 0, int ST = 0>
 cudaError_t launch_fpmvo_fuse(const FpmvoArgs& a, cudaStream_t s) {
     const size_t smem = (size_t)kFuseWarps * (64 + HF_FPMVO_MAX_K + (a.K * P * P + 1) / 2) * sizeof(float4);
-    k_fpmvo_fuse<P><<<(a.N + kFuseWarps - 1) / kFuseWarps, kFuseWarps * 32, smem, s>>>(a);
+    k_fpmvo_fuse<P, KT, ST><<<(a.N + kFuseWarps - 1) / kFuseWarps, kFuseWarps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -492,7 +514,7 @@ cudaError_t hf_launch_fpmvo(const FpmvoArgs& a, cudaStream_t s) {
     switch (a.P) {
         case 1: return launch_fpmvo_fuse<1>(a, s);
         case 3: return launch_fpmvo_fuse<3>(a, s);
-        case 5: return launch_fpmvo_fuse<5>(a, s);
+        case 5: return a.K == 5 && a.S == 5 ? launch_fpmvo_fuse<5, 5, 5>(a, s) : launch_fpmvo_fuse<5>(a, s);
         default: return launch_fpmvo_fuse<7>(a, s);
     }
 }
@@ -560,15 +582,13 @@ extern "C" int hair_fuse_fpmvo(hf_ctx* c, const hf_fpmvo_cfg* cfg, float* dir_ou
         d_sel = sel_out ? (int32_t*)(base + (size_t)N * 16) : nullptr;
         d_st = status_out ? (uint8_t*)(base + (size_t)N * 20) : nullptr;
     }
-    const size_t nk_bytes = ((size_t)N * sizeof(int) + 255) & ~(size_t)255;
     // depth samples delta_s = -Delta + 2 Delta s / (S - 1), s = 0 .. S-1 (0 for S = 1), in double
     float ds[32];
     for (int q = 0; q < 32; ++q)
         ds[q] = q < g.S && g.S > 1 ? (float)(-(double)g.delta + 2.0 * (double)g.delta * q / (g.S - 1)) : 0.0f;
-    if ((rc = hf_ensure(c, c->fprec, nk_bytes + (size_t)N * g.K * 3 * sizeof(float4)))) return rc;
+    if ((rc = hf_ensure(c, c->fprec, (size_t)N * g.K * 3 * sizeof(float4)))) return rc;
     FpmvoArgs a{(const float*)c->pts.p, N, (const float*)c->cams.p, c->V, c->W, c->Hh, (const float2*)c->amap.p,
-                (const float2*)c->dmap.p, (const float2*)c->vmap.p, (int*)c->fprec.p,
-                (float4*)((char*)c->fprec.p + nk_bytes), g.K, g.S, g.P, g.lambda_px, g.delta, g.eps_vis,
+                (const float2*)c->dmap.p, (const float2*)c->vmap.p, (float4*)c->fprec.p, g.K, g.S, g.P, g.lambda_px, g.delta, g.eps_vis,
                 d_dir, d_cost, d_sel, d_st};
     memcpy(a.ds, ds, sizeof(ds));
     if ((rc = run_launch(c, "k_fpmvo", [&] { return hf_launch_fpmvo(a, c->stream); }))) return rc;

@@ -59,7 +59,7 @@ struct hf_ctx {
     DevBuf depth;   // [V][H][W] f32 staging of host depth maps (FPMVO), +inf where no hair
     DevBuf dmap;    // [V][H][W] float2 (depth, confidence) for FPMVO's depth test and view selection
     DevBuf vmap;    // [V][H][W] float2 C (cos theta, sin theta) for FPMVO's patches
-    DevBuf fprec;   // FPMVO scratch: [N] top-view counts, then [N][K][3] float4 top-view records
+    DevBuf fprec;   // FPMVO scratch: [N][K][3] float4 top-view records
     long long views_gen = 0;   // bumped by every view upload
     long long depth_gen = -1;  // views_gen the FPMVO maps were built for
     uint32_t* errw_host = nullptr;  // pinned read-back slot
@@ -224,10 +224,11 @@ struct FpmvoArgs {
     const float2* amap;     // (angle, confidence)
     const float2* dmap;     // (depth, confidence)
     const float2* vmap;     // C (cos theta, sin theta)
-    // scratch between the two kernels: top views per point (-1 non-finite point) and per top view
-    // three 16-byte words: (view, confidence, pixel x, pixel y), (u, w, lambda cos theta,
-    // lambda sin theta), (Zp hi, Zp lo, z at the offset pixel (+inf if none), 0)
-    int* nk; float4* rec;
+    // scratch between the two kernels: K records per point of three 16-byte words, one per top view
+    // and zeros past the last: (view, confidence, pixel x, pixel y), (u, w, lambda cos theta,
+    // lambda sin theta), (Zp hi, Zp lo, z at the offset pixel (+inf if none), n); n of record 0 is
+    // the number of top views (-1 for a non-finite point)
+    float4* rec;
     int K, S, P;
     float lambda, delta, eps;
     float* dir_out; float* cost_out; int32_t* sel_out; uint8_t* status_out;
