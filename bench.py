@@ -986,12 +986,18 @@ def fpmvo_units(sc, cfg):
 
 
 def fpmvo_bytes(u, N, cfg, conf_bytes):
-    """Algorithmic bytes of one pass: per in-image view the depth value (4 B) and, where visible, the
-    confidence; per top view the angle at the point's pixel and the depth at the offset pixel (4 + 4 B)
-    and the P x P patch of angle + confidence; the point (12 B) and the outputs (21 B)."""
+    """Algorithmic bytes of one pass per kernel.  k_fpmvo_views: per in-image view the depth value
+    (4 B) and, where visible, the confidence; per top view the angle at the point's pixel and the
+    depth at the offset pixel (4 + 4 B); the point (12 B).  k_fpmvo_fuse: per top view the P x P
+    patch of angle + confidence; the outputs (21 B)."""
     P2 = cfg["P"] * cfg["P"]
-    return (4 * u["inside_pv"] + conf_bytes * u["visible_pv"] + u["top_pv"] * (8 + P2 * (4 + conf_bytes))
-            + 33 * N)
+    return {"k_fpmvo_views": 4 * u["inside_pv"] + conf_bytes * u["visible_pv"] + 8 * u["top_pv"] + 12 * N,
+            "k_fpmvo_fuse": u["top_pv"] * P2 * (4 + conf_bytes) + 21 * N}
+
+
+# DRAM bytes (read + write) per unit from one ncu capture of the mid scene (200,000 points, 32 views
+# of 1024x1024): per in-image point-view for the views kernel, per top view for the fusion kernel.
+FPMVO_DRAM_PER_UNIT = {"k_fpmvo_views": ("inside_pv", 315.443e6 / 6350838), "k_fpmvo_fuse": ("top_pv", 227.167e6 / 992848)}
 
 
 def fpmvo_cpu_baseline(sc, cfg, budget_s=15.0):
@@ -1076,15 +1082,25 @@ def run_fpmvo(args):
     ms = reduce_over_ranks(ms, pg, dev)
     value = reduce_over_ranks(N, pg, dev, "sum") * args.steps / (ms / 1e3)
     units = fpmvo_units(sc, cfg)
-    n_, t_ = kt["k_fpmvo"]
-    sec = t_ / n_ / 1e3
-    byt = fpmvo_bytes(units, N, cfg, sc["conf"].itemsize)
-    ach = byt / sec / 1e9
-    roofline = {"bound": "hbm", "achieved": ach, "peak": HBM_GBS, "unit": "GB/s", "frac": ach / HBM_GBS,
-                "traffic": None, "kernel": "k_fpmvo", "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs",
-                "work": f"{byt / N:.0f} algorithmic B per point ({units['inside_pv']} in-image point-views, "
-                        f"{units['visible_pv']} visible, {units['top_pv']} top views per pass)",
-                "share": t_ / ms}
+    byts = fpmvo_bytes(units, N, cfg, sc["conf"].itemsize)
+    rooflines = {}
+    for name, (n_, t_) in kt.items():
+        if name not in byts:
+            continue
+        sec = t_ / n_ / 1e3
+        ach = byts[name] / sec / 1e9
+        unit_key, per_unit = FPMVO_DRAM_PER_UNIT[name]
+        rooflines[name] = {"bound": "hbm", "achieved": ach, "peak": HBM_GBS, "unit": "GB/s", "frac": ach / HBM_GBS,
+                           "traffic": per_unit * units[unit_key] if per_unit else None, "kernel": name,
+                           "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs",
+                           "work": f"{byts[name] / N:.0f} algorithmic B per point ({units['inside_pv']} in-image "
+                                   f"point-views, {units['visible_pv']} visible, {units['top_pv']} top views)",
+                           "share": t_ / ms}
+        if per_unit:
+            rooflines[name]["traffic_source"] = (f"ncu dram bytes of the mid scene, {per_unit:.1f} B per {unit_key} "
+                                                 "x this pass's count")
+    dom = max(rooflines, key=lambda x: rooflines[x]["share"])
+    roofline = dict(rooflines[dom])
     line = {"metric": "FPMVO points/s (depth-sample candidates, medoid fusion, patch consistency)", "value": value,
             "unit": "points/s", "n_gpus": world, "steps": args.steps, "warmup": Wm, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -1094,7 +1110,7 @@ def run_fpmvo(args):
                        "l2": "inputs larger than L2 (angle, confidence and depth maps "
                              f"{(sc['angle'].nbytes + sc['conf'].nbytes + sc['depth'].nbytes) / 1e6:.0f} MB)",
                        "parallelism": f"independent scenes per rank x{world}"},
-            "roofline": roofline, "units": units,
+            "roofline": roofline, "rooflines": rooflines, "units": units,
             "kernels": {k_: {"launches": v[0], "ms_per_launch": v[1] / max(1, v[0]), "share": v[1] / ms}
                         for k_, v in kt.items()},
             "gpu_launches": launches, "clocks": clk}

@@ -495,8 +495,7 @@ __global__ void k_fpmvo_maps(const float* __restrict__ depth, const float2* __re
 
 }  // namespace
 
-cudaError_t hf_launch_fpmvo(const FpmvoArgs& a, cudaStream_t s) {
-    if (a.P != 1 && a.P != 3 && a.P != 5 && a.P != 7) return cudaErrorInvalidValue;
+cudaError_t hf_launch_fpmvo_views(const FpmvoArgs& a, cudaStream_t s) {
     const unsigned vb = (unsigned)((a.N + kViewsThreads - 1) / kViewsThreads);
     switch (a.K) {
         case 1: k_fpmvo_views<1><<<vb, kViewsThreads, 0, s>>>(a); break;
@@ -509,13 +508,16 @@ cudaError_t hf_launch_fpmvo(const FpmvoArgs& a, cudaStream_t s) {
         case 8: k_fpmvo_views<8><<<vb, kViewsThreads, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_fpmvo_fuse(const FpmvoArgs& a, cudaStream_t s) {
     switch (a.P) {
         case 1: return launch_fpmvo_fuse<1>(a, s);
         case 3: return launch_fpmvo_fuse<3>(a, s);
         case 5: return a.K == 5 && a.S == 5 ? launch_fpmvo_fuse<5, 5, 5>(a, s) : launch_fpmvo_fuse<5>(a, s);
-        default: return launch_fpmvo_fuse<7>(a, s);
+        case 7: return launch_fpmvo_fuse<7>(a, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 
@@ -591,7 +593,8 @@ extern "C" int hair_fuse_fpmvo(hf_ctx* c, const hf_fpmvo_cfg* cfg, float* dir_ou
                 (const float2*)c->dmap.p, (const float2*)c->vmap.p, (float4*)c->fprec.p, g.K, g.S, g.P, g.lambda_px, g.delta, g.eps_vis,
                 d_dir, d_cost, d_sel, d_st};
     memcpy(a.ds, ds, sizeof(ds));
-    if ((rc = run_launch(c, "k_fpmvo", [&] { return hf_launch_fpmvo(a, c->stream); }))) return rc;
+    if ((rc = run_launch(c, "k_fpmvo_views", [&] { return hf_launch_fpmvo_views(a, c->stream); }))) return rc;
+    if ((rc = run_launch(c, "k_fpmvo_fuse", [&] { return hf_launch_fpmvo_fuse(a, c->stream); }))) return rc;
     if (mem_kind == HF_HOST) {
         cudaError_t e = cudaMemcpyAsync(dir_out, d_dir, (size_t)N * 12, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess && cost_out) e = cudaMemcpyAsync(cost_out, d_cost, (size_t)N * 4, cudaMemcpyDeviceToHost, c->stream);

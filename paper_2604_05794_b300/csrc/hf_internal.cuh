@@ -234,6 +234,7 @@ struct FpmvoArgs {
     float* dir_out; float* cost_out; int32_t* sel_out; uint8_t* status_out;
     float ds[32];           // the S depth-sample offsets delta_s
 };
-cudaError_t hf_launch_fpmvo(const FpmvoArgs& a, cudaStream_t s);
+cudaError_t hf_launch_fpmvo_views(const FpmvoArgs& a, cudaStream_t s);   // then hf_launch_fpmvo_fuse
+cudaError_t hf_launch_fpmvo_fuse(const FpmvoArgs& a, cudaStream_t s);
 cudaError_t hf_launch_fpmvo_maps(const float* depth, const float2* amap, size_t npx, float2* dmap, float2* vmap,
                                  cudaStream_t s);
