@@ -29,18 +29,22 @@ class _Scene(ctypes.Structure):
 _lib = None
 
 
+_SOURCES = ("oracle.c", "phg.c")
+
+
 def build():
-    """Compile liboracle.so next to this file (gcc -O2, OpenMP)."""
+    """Compile liboracle.so next to this file (gcc -O2, OpenMP, no floating-point contraction: the
+    single-precision parts round once per written operation)."""
     import subprocess
-    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", _LIB_PATH,
-                           os.path.join(_HERE, "oracle.c"), "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", _LIB_PATH,
+                           *[os.path.join(_HERE, f) for f in _SOURCES], "-lm"])
 
 
 def _load():
     global _lib
     if _lib is None:
-        src = os.path.join(_HERE, "oracle.c")
-        if not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+        newest = max(os.path.getmtime(os.path.join(_HERE, f)) for f in _SOURCES)
+        if not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
             build()
         lib = ctypes.CDLL(_LIB_PATH)
         vp, ll, i32 = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int
@@ -257,3 +261,97 @@ def fpmvo(scene, depth, K=5, S=5, P=5, lambda_px=4.0, delta=0.005, eps_vis=0.02,
     if rc != 0:
         raise ValueError("fpmvo: K and S in [1, 16], P odd")
     return out
+
+
+# ---------------------------------------------------------------------------- Parallel Hair Growing
+class _PhgCfg(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("voxel", ctypes.c_float), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("step", ctypes.c_float), ("max_steps", ctypes.c_int),
+                ("root_steps", ctypes.c_int), ("cos_turn", ctypes.c_float), ("occ_cap", ctypes.c_int),
+                ("batch", ctypes.c_int), ("link_dist", ctypes.c_float), ("link_cos", ctypes.c_float)]
+
+
+PHG_MAXLEN, PHG_OUTSIDE, PHG_EMPTY, PHG_CROWDED, PHG_TURN, PHG_NO_ROOT = 1, 2, 3, 4, 5, 6
+
+
+def phg_cfg(origin, voxel, dims, step, max_steps, root_steps, cos_turn, occ_cap, batch, link_dist, link_cos):
+    c = _PhgCfg()
+    c.origin[:] = [float(np.float32(x)) for x in origin]
+    c.voxel, (c.nx, c.ny, c.nz), c.step = voxel, [int(x) for x in dims], step
+    c.max_steps, c.root_steps, c.cos_turn, c.occ_cap, c.batch = max_steps, root_steps, cos_turn, occ_cap, batch
+    c.link_dist, c.link_cos = link_dist, link_cos
+    return c
+
+
+def phg_voxel(cfg, p):
+    """Voxel index of the f32 point p (-1 outside the grid)."""
+    lib = _load()
+    lib.or_phg_voxel.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.or_phg_voxel.restype = ctypes.c_longlong
+    q = np.ascontiguousarray(p, np.float32)
+    return lib.or_phg_voxel(ctypes.byref(cfg), _p(q))
+
+
+def phg_orient_one(t6, count):
+    """Orientation of one voxel from its six fixed-point tensor sums (int64) and point count."""
+    lib = _load()
+    lib.or_phg_orient_one.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    lib.or_phg_orient_one.restype = None
+    t = np.ascontiguousarray(t6, np.int64)
+    out = np.empty(3, np.float32)
+    lib.or_phg_orient_one(_p(t), count, _p(out))
+    return out
+
+
+def phg_splat(cfg, pts, dirs, valid=None):
+    """Step A: occupancy counts (nvox,) and fixed-point tensor sums (nvox, 6)."""
+    lib = _load()
+    lib.or_phg_splat.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p]
+    lib.or_phg_splat.restype = None
+    nvox = cfg.nx * cfg.ny * cfg.nz
+    p = np.ascontiguousarray(pts, np.float32)
+    d = np.ascontiguousarray(dirs, np.float32)
+    v = None if valid is None else np.ascontiguousarray(valid, np.uint8)
+    occ = np.empty(nvox, np.int32)
+    T = np.empty((nvox, 6), np.int64)
+    lib.or_phg_splat(ctypes.byref(cfg), len(p), _p(p), _p(d), None if v is None else _p(v), _p(occ), _p(T))
+    return occ, T
+
+
+def phg(cfg, pts, dirs, seeds, normals, valid=None, seg_cap=None):
+    """Steps A to E of the Parallel Hair Growing consumer.  Returns a dict: occ (nvox,), ori (nvox, 3),
+    crowd (nvox,) strands per voxel at the end; guide strands: gverts (S, L+1, 3), glen (S,), gstop (S,),
+    gtan (S, 3); segments (K of them): sverts (K, 2L+1, 3), slen (K,), svox (K,) seed voxels,
+    stan (K, 2, 3) outward tangents at (start, end); label (S + K,) component labels."""
+    lib = _load()
+    lib.or_phg_run.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p]
+    lib.or_phg_run.restype = ctypes.c_longlong
+    nvox = cfg.nx * cfg.ny * cfg.nz
+    L = cfg.max_steps
+    p = np.ascontiguousarray(pts, np.float32)
+    d = np.ascontiguousarray(dirs, np.float32)
+    v = None if valid is None else np.ascontiguousarray(valid, np.uint8)
+    sd = np.ascontiguousarray(seeds, np.float32)
+    nm = np.ascontiguousarray(normals, np.float32)
+    S = len(sd)
+    cap = nvox if seg_cap is None else seg_cap
+    o = dict(occ=np.empty(nvox, np.int32), ori=np.empty((nvox, 3), np.float32), crowd=np.empty(nvox, np.int32),
+             gverts=np.zeros((S, L + 1, 3), np.float32), glen=np.empty(S, np.int32), gstop=np.empty(S, np.int32),
+             gtan=np.empty((S, 3), np.float32), sverts=np.zeros((cap, 2 * L + 1, 3), np.float32),
+             slen=np.empty(cap, np.int32), svox=np.empty(cap, np.int64), stan=np.zeros((cap, 2, 3), np.float32),
+             label=np.empty(S + cap, np.int32))
+    K = lib.or_phg_run(ctypes.byref(cfg), len(p), _p(p), _p(d), None if v is None else _p(v), S, _p(sd), _p(nm),
+                       _p(o["occ"]), _p(o["ori"]), _p(o["crowd"]), _p(o["gverts"]), _p(o["glen"]), _p(o["gstop"]),
+                       _p(o["gtan"]), cap, _p(o["sverts"]), _p(o["slen"]), _p(o["svox"]), _p(o["stan"]),
+                       _p(o["label"]))
+    if K < 0:
+        raise ValueError("phg: more segment seeds than seg_cap")
+    for key in ("sverts", "slen", "svox", "stan"):
+        o[key] = o[key][:K]
+    o["label"] = o["label"][:S + K]
+    return o
