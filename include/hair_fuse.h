@@ -165,6 +165,74 @@ int hair_fuse_upload_depth(hf_ctx* ctx, const float* depth, int mem_kind);
 int hair_fuse_fpmvo(hf_ctx* ctx, const hf_fpmvo_cfg* cfg, float* dir_out, float* cost_out, int32_t* sel_out,
                     uint8_t* status_out, int mem_kind);
 
+/* ------------------------------------------------------------------------------------------------
+ * The paper's Parallel Hair Growing consumer (Sec. 3.2): from fused points with directions to
+ * strands.  All decisions that turn positions into voxels are single-precision with one rounding per
+ * operation (no fused contraction beyond the written FMAs), so results are reproducible bit for bit.
+ *  A  volumes: voxel c(p) = floor((p - origin) / voxel) per axis (outside the nx x ny x nz grid: no
+ *     voxel); occ[c] = number of valid points in c; T[c] = sum of rint(2^30 fl(d_a d_b)) (int64);
+ *  B  ori[c] = dominant eigenvector of T[c] (12 rounds of power iteration from the column with the
+ *     largest diagonal, sign z > 0, else y > 0, else x > 0), 0 for an empty voxel;
+ *  C  guide strands from S scalp seeds h with normals n, in batches of `batch` seeds: d = n; per step
+ *     stop outside the grid; in an empty voxel go on along d only while no occupied voxel was met and
+ *     fewer than root_steps steps were taken (a guide that meets none has no strand), else stop; stop
+ *     where crowd[c] >= occ_cap; o = ori[c] turned to <o, d> >= 0, stop if <o, d> < cos_turn; d = o;
+ *     p += step d; at most max_steps steps.  crowd[c] (deferred occupancy) counts the strands of
+ *     earlier batches that entered c: it is updated after each batch;
+ *  D  segments: every occupied voxel with crowd 0 after the guides seeds one at its centre, in voxel
+ *     order and in batches (a seed whose voxel an earlier batch entered is skipped: 0 vertices),
+ *     traced along -ori and +ori by the rules of C without the empty walk; vertices run from the end
+ *     of the backward half through the seed to the end of the forward half;
+ *  E  linking (Eq. segment_connection): every strand end (a guide tip; both segment ends; outward
+ *     tangent t = the last step's direction) takes the nearest end q of another segment with
+ *     |p - p_q| < link_dist and <t, -t_q> > link_cos (squared distances compared, ties to the lower
+ *     q); joined strands form connected components labelled by their lowest strand index (guides
+ *     0 .. S-1, then segments S .. S+K-1).
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct {
+    float origin[3];      /* grid corner (scene units) */
+    float voxel;          /* voxel edge > 0 */
+    int nx, ny, nz;       /* grid size, (nx + 2)(ny + 2)(nz + 2) < 2^31 */
+    float step;           /* tracing step, 0 < step <= voxel */
+    int max_steps;        /* steps per trace, 1 .. 4096 */
+    int root_steps;       /* empty-voxel steps a guide may take before its first occupied voxel */
+    float cos_turn;       /* smallest cosine between consecutive step directions */
+    int occ_cap;          /* strands of earlier batches that close a voxel, >= 1 */
+    int batch;            /* seeds per batch, >= 1 */
+    float link_dist;      /* delta_d, 0 .. 8 voxel */
+    float link_cos;       /* cos(delta_theta) */
+} hf_phg_cfg;
+
+enum { HF_PHG_MAXLEN = 1, HF_PHG_OUTSIDE = 2, HF_PHG_EMPTY = 3, HF_PHG_CROWDED = 4, HF_PHG_TURN = 5,
+       HF_PHG_NO_ROOT = 6 };   /* why a trace stopped */
+
+typedef struct {          /* caller-owned outputs, all of the call's mem_kind */
+    int32_t* occ;         /* nvox = nx ny nz points per voxel (index (z ny + y) nx + x) */
+    float* ori;           /* nvox x 3 voxel orientations */
+    int32_t* crowd;       /* nvox strands that entered each voxel, at the end (may be NULL) */
+    float* gverts;        /* S x (max_steps + 1) x 3 guide-strand vertices, the seed first */
+    int32_t* glen;        /* S vertex counts (0: no strand) */
+    int32_t* gstop;       /* S stop reasons HF_PHG_* (may be NULL) */
+    float* gtan;          /* S x 3 tip tangents (may be NULL) */
+    long long seg_cap;    /* capacity of the segment arrays */
+    float* sverts;        /* seg_cap x (2 max_steps + 1) x 3 segment vertices */
+    int32_t* slen;        /* seg_cap vertex counts (0: skipped seed) */
+    int64_t* svox;        /* seg_cap seed voxels (may be NULL) */
+    float* stan;          /* seg_cap x 2 x 3 outward tangents at the start and the end (may be NULL) */
+    int32_t* label;       /* S + seg_cap component labels */
+    long long* n_seg;     /* 1: the number K of segment seeds */
+} hf_phg_out;
+
+/* The consumer, A to E, on the context's stream (it synchronises once to learn K and once per
+ * component round).  pts, dirs: N x 3 f32 points and unit directions (P_out and P_in fused); valid:
+ * N u8 (non-zero = use the point; may be NULL); seeds, normals: S x 3 f32.  All pointers of kind
+ * mem_kind; inputs are read during the call, outputs written by its end.  Errors: HF_ERR_INVALID_ARG
+ * for a configuration outside the limits above or a missing array; HF_ERR_SHAPE when K exceeds
+ * seg_cap (n_seg still receives K) or S + seg_cap >= 2^31; CUDA failures as elsewhere. */
+int hair_fuse_phg(hf_ctx* ctx, const hf_phg_cfg* cfg, long long N, const float* pts, const float* dirs,
+                  const uint8_t* valid, long long S, const float* seeds, const float* normals, hf_phg_out* out,
+                  int mem_kind);
+
 /* Evaluate the cost c_i(d) of M given directions for every point (no argmin, no refinement).
  *  dirs: N x M x 3 f32 (any non-zero length; the cost is scale- and sign-invariant),
  *  cost_out: N x M f32.  Both of kind mem_kind. */

@@ -36,6 +36,24 @@ class hf_fpmvo_cfg(ctypes.Structure):
                 ("delta", ctypes.c_float), ("eps_vis", ctypes.c_float)]
 
 
+class hf_phg_cfg(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("voxel", ctypes.c_float), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("step", ctypes.c_float), ("max_steps", ctypes.c_int),
+                ("root_steps", ctypes.c_int), ("cos_turn", ctypes.c_float), ("occ_cap", ctypes.c_int),
+                ("batch", ctypes.c_int), ("link_dist", ctypes.c_float), ("link_cos", ctypes.c_float)]
+
+
+class hf_phg_out(ctypes.Structure):
+    _fields_ = [("occ", ctypes.c_void_p), ("ori", ctypes.c_void_p), ("crowd", ctypes.c_void_p),
+                ("gverts", ctypes.c_void_p), ("glen", ctypes.c_void_p), ("gstop", ctypes.c_void_p),
+                ("gtan", ctypes.c_void_p), ("seg_cap", ctypes.c_longlong), ("sverts", ctypes.c_void_p),
+                ("slen", ctypes.c_void_p), ("svox", ctypes.c_void_p), ("stan", ctypes.c_void_p),
+                ("label", ctypes.c_void_p), ("n_seg", ctypes.c_void_p)]
+
+
+PHG_MAXLEN, PHG_OUTSIDE, PHG_EMPTY, PHG_CROWDED, PHG_TURN, PHG_NO_ROOT = 1, 2, 3, 4, 5, 6
+
+
 class hf_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double)]
 
@@ -53,6 +71,8 @@ _SIGS = {
     "hair_fuse_upload_depth": ([_vp, _vp, _i], _i),
     "hair_fuse_fpmvo": ([_vp, _vp, _vp, _vp, _vp, _vp, _i], _i),
     "hair_fuse_eval_costs": ([_vp, _i, _vp, _vp, _i], _i),
+    "hair_fuse_phg": ([_vp, ctypes.POINTER(hf_phg_cfg), _ll, _vp, _vp, _vp, _ll, _vp, _vp, ctypes.POINTER(hf_phg_out),
+                       _i], _i),
     "hair_fuse_fibonacci_hemisphere": ([_i, _vp], _i),
     "hair_fuse_gemm_bf16": ([_vp, _vp, _vp, _i, _i, _i, _vp], _i),
     "hair_fuse_sync": ([_vp], _i),
@@ -106,6 +126,7 @@ hair_fuse_fuse_range = _lib.hair_fuse_fuse_range
 hair_fuse_upload_depth = _lib.hair_fuse_upload_depth
 hair_fuse_fpmvo = _lib.hair_fuse_fpmvo
 hair_fuse_eval_costs = _lib.hair_fuse_eval_costs
+hair_fuse_phg = _lib.hair_fuse_phg
 hair_fuse_fibonacci_hemisphere = _lib.hair_fuse_fibonacci_hemisphere
 hair_fuse_gemm_bf16 = _lib.hair_fuse_gemm_bf16
 hair_fuse_sync = _lib.hair_fuse_sync
@@ -284,6 +305,42 @@ class HairFuse:
         ptrs = [_ptr_kind(x) for x in (dir_out, cost_out, sel_out, status_out)]
         kind = _same_kind(*[q[1] for q in ptrs])
         self._c(hair_fuse_fpmvo(self.h, ctypes.byref(cfg), *[q[0] for q in ptrs], kind))
+
+    def phg(self, cfg, pts, dirs, seeds, normals, valid=None, seg_cap=None, device=None):
+        """The Parallel Hair Growing consumer (hair_fuse_phg).  cfg: hf_phg_cfg; inputs numpy arrays
+        or CUDA tensors (one kind).  Outputs are allocated here, of the inputs' kind: a dict like the
+        oracle's (occ, ori, crowd, gverts, glen, gstop, gtan, sverts, slen, svox, stan, label, n_seg)
+        with the segment arrays cut to the K segments."""
+        ins = [_ptr_kind(x) for x in (pts, dirs, valid, seeds, normals)]
+        kind = _same_kind(*[q[1] for q in ins])
+        N, S = int(pts.shape[0]), int(seeds.shape[0])
+        nvox = cfg.nx * cfg.ny * cfg.nz
+        L = cfg.max_steps
+        cap = nvox if seg_cap is None else int(seg_cap)
+        if kind == HF_DEVICE:
+            import torch
+            dev = pts.device
+            mk = lambda shape, dt: torch.zeros(shape, dtype=dt, device=dev)
+            i32, f32, i64 = torch.int32, torch.float32, torch.int64
+        else:
+            mk = lambda shape, dt: np.zeros(shape, dtype=dt)
+            i32, f32, i64 = np.int32, np.float32, np.int64
+        o = dict(occ=mk(nvox, i32), ori=mk((nvox, 3), f32), crowd=mk(nvox, i32), gverts=mk((S, L + 1, 3), f32),
+                 glen=mk(S, i32), gstop=mk(S, i32), gtan=mk((S, 3), f32), sverts=mk((cap, 2 * L + 1, 3), f32),
+                 slen=mk(cap, i32), svox=mk(cap, i64), stan=mk((cap, 2, 3), f32), label=mk(S + cap, i32),
+                 n_seg=mk(1, i64))
+        ptr = {k: _ptr_kind(v)[0] for k, v in o.items()}
+        out = hf_phg_out(ptr["occ"], ptr["ori"], ptr["crowd"], ptr["gverts"], ptr["glen"], ptr["gstop"], ptr["gtan"],
+                         cap, ptr["sverts"], ptr["slen"], ptr["svox"], ptr["stan"], ptr["label"], ptr["n_seg"])
+        self._c(hair_fuse_phg(self.h, ctypes.byref(cfg), N, ins[0][0], ins[1][0], ins[2][0], S, ins[3][0], ins[4][0],
+                              ctypes.byref(out), kind))
+        if kind == HF_DEVICE:
+            self.sync()
+        K = int(o["n_seg"][0])
+        for k in ("sverts", "slen", "svox", "stan"):
+            o[k] = o[k][:K]
+        o["label"] = o["label"][:S + K]
+        return o
 
     def eval_costs(self, dirs, cost_out):
         """Costs (N,M) of the directions dirs (N,M,3)."""
