@@ -49,11 +49,17 @@ WORKLOADS = {
             "f32 angle + fp16 confidence, 0.5 deg pose noise, H=64, k=8, T=8",
     "mid": "plain fusion, mid: 200,000 points, 32 views 1024x1024 with 10% outlier pixels, H=64, k=8, T=8",
     "tiny": "plain fusion, tiny: 2,000 points, 8 views 256x256, H=32, k=5, T=4",
+    "phg": "the paper's Parallel Hair Growing consumer on the full scene's strands (seed 2: 1,000,000 points, "
+           "tangents with N(0, 0.1) noise renormalised; 20,000 scalp seeds at the strand roots): voxel 0.02, step "
+           "0.01, 64 steps, 4 root steps, turn cos 0.5, 4 strands per voxel, batches of 32768 seeds, link 0.03 / "
+           "cos 0.7",
     "fpmvo": "the paper's FPMVO step on the full scene (seed 2: 1,000,000 points, 64 views 1920x1080, f32 angle + "
              "fp16 confidence, depth maps from the renderer's z-buffer): K=5 top views, S=5 depth samples over "
              "[-0.0046, 0.0046], P=5 patch, lambda=4 px, depth-test tolerance 0.02",
 }
 FPMVO_CFG = dict(K=5, S=5, P=5, lambda_px=4.0, delta=0.0046, eps_vis=0.02)
+PHG_CFG = dict(voxel=0.02, step=0.01, max_steps=64, root_steps=4, cos_turn=0.5, occ_cap=4, batch=32768, link_dist=0.03,
+               link_cos=0.7)
 SM_COUNT, FP32_LANES_PER_SM = 148, 128
 
 
@@ -77,6 +83,7 @@ def parse():
     ap.add_argument("--workload", default="serving16", choices=list(WORKLOADS))
     ap.add_argument("--partition", action="store_true", help="full/mid/tiny under torchrun: every rank uploads "
                     "the same scene and fuses its own point range (strong scaling) instead of its own scene")
+    ap.add_argument("--phg-strands", type=int, default=0, help="phg: strands of the scene (0: the full preset's)")
     ap.add_argument("--fpmvo-scene", default="full", choices=["full", "mid"],
                     help="fpmvo: the scene preset (mid: the small case for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -228,6 +235,8 @@ def run_reference(args):
     import oracle
     if args.workload == "fpmvo":
         return run_reference_fpmvo(args, world)
+    if args.workload == "phg":
+        return run_reference_phg(args, world)
     if args.workload == "serving16":
         scenes = serving_scenes(200)
     elif args.workload == "learned":
@@ -305,6 +314,30 @@ def run_reference_fpmvo(args, world):
             "config": {"workload": WORKLOADS["fpmvo"], "points_per_step": n, **cfg},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": sample},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_phg(args, world):
+    """The oracle of the PHG consumer on the host, one scene of 400 strands of the same preset per step
+    (single-threaded: its batches are sequential by construction)."""
+    phg_cpu(400)
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.warmup):
+        phg_cpu(400)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        n += phg_cpu(400)[1]
+    dt = time.perf_counter() - t0
+    value = n / dt
+    line = {"impl": "reference", "metric": "PHG input points/s (volumes, guide strands, segments, linking)",
+            "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (int64 fixed-point sums)", "data": "synthetic",
+            "config": {"workload": WORKLOADS["phg"], "points_per_step": n // max(1, args.steps), **PHG_CFG},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
+                             "sample": "a 400-strand scene of the same preset and parameters per step"},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -1153,10 +1186,170 @@ def run_fpmvo(args):
         pg.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------- PHG workload
+def phg_inputs(n_strands=0, seed=2, noise=0.1):
+    """Points, noisy unit directions, scalp seeds and normals of the full preset's strands."""
+    import scenegen
+    over = dict(n_strands=n_strands) if n_strands else {}
+    sc = scenegen.make_scene("full", seed=seed, strand_maps=False, knn=False, **over)
+    rng = np.random.default_rng(seed)
+    d = sc["tangents"] + rng.normal(size=sc["tangents"].shape).astype(np.float32) * np.float32(noise)
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    roots = np.ascontiguousarray(sc["verts"][:, 0], np.float32)
+    normals = (roots / np.linalg.norm(roots, axis=1, keepdims=True)).astype(np.float32)
+    pts = np.ascontiguousarray(sc["points"], np.float32)
+    lo = pts.min(0) - 2 * PHG_CFG["voxel"]
+    dims = np.ceil((pts.max(0) + 2 * PHG_CFG["voxel"] - lo) / PHG_CFG["voxel"]).astype(int)
+    return pts, d, roots, normals, lo.astype(np.float32), dims
+
+
+def phg_cfgs(lo, dims):
+    import ctypes
+
+    import oracle
+    import paper_2604_05794_b300 as hf
+    c = PHG_CFG
+    args = (c["voxel"], *[int(x) for x in dims], c["step"], c["max_steps"], c["root_steps"], c["cos_turn"], c["occ_cap"],
+            c["batch"], c["link_dist"], c["link_cos"])
+    return hf.hf_phg_cfg((ctypes.c_float * 3)(*[float(x) for x in lo]), *args), oracle.phg_cfg(lo, c["voxel"], dims,
+                                                                                              *args[4:])
+
+
+def phg_cpu(n_strands, steps=1):
+    """The oracle on a scene of n_strands strands (the same preset and parameters): points/s."""
+    import oracle
+    pts, d, roots, normals, lo, dims = phg_inputs(n_strands)
+    _, oc = phg_cfgs(lo, dims)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.phg(oc, pts, d, roots, normals, seg_cap=len(pts))
+    dt = time.perf_counter() - t0
+    return len(pts) * steps / dt, len(pts), dt
+
+
+def run_phg(args):
+    import torch
+
+    import paper_2604_05794_b300 as hf
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    pts, d, roots, normals, lo, dims = phg_inputs(args.phg_strands, seed=2 + 100 * rank)
+    gc, _ = phg_cfgs(lo, dims)
+    N, S = len(pts), len(roots)
+    nvox = int(np.prod(dims))
+    cap = min(nvox, N)
+    stream = torch.cuda.current_stream(dev)
+    f = hf.HairFuse(8, 0, 0, stream=stream.cuda_stream)
+    g_in = [torch.from_numpy(x).to(dev) for x in (pts, d, roots, normals)]
+    outs = f.phg_outputs(gc, S, cap, dev)
+    step = lambda: f.phg(gc, *g_in, outputs=outs, cut=False)
+    Wm = max(3, args.warmup)
+    for _ in range(Wm):
+        step()
+    f.sync()
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(cvd.split(",")[local] if cvd else str(local))
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = f.stats()["launches"]
+    f.profile(True)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    kt = f.profile_read()
+    f.profile(False)
+    launches = f.stats()["launches"] - launches0
+    ms = reduce_over_ranks(ms, pg, dev)
+    value = reduce_over_ranks(N, pg, dev, "sum") * args.steps / (ms / 1e3)
+    K = int(outs["n_seg"][0])
+    glen = outs["glen"].cpu().numpy()
+    slen = outs["slen"][:K].cpu().numpy()
+    label = outs["label"][:S + K].cpu().numpy()
+    occ = outs["occ"].cpu().numpy()
+    # algorithmic work per kernel: the splat reads a point and direction (24 B) and adds 28 B of counts
+    # and tensor sums; every trace step reads a voxel's count, crowd and orientation (20 B)
+    steps_taken = int(np.maximum(glen - 1, 0).sum() + np.maximum(slen - 1, 0).sum())
+    ktime = {k_: v[1] for k_, v in kt.items()}
+    total_kms = sum(ktime.values())
+    work = {"k_phg_splat": (N * (24 + 28), "B"), "k_phg_orient": (nvox * (4 + 48 + 12), "B"),
+            "k_phg_trace_guides": (int(np.maximum(glen - 1, 0).sum()) * 20, "B"),
+            "k_phg_trace_segments": (int(np.maximum(slen - 1, 0).sum()) * 20, "B")}
+    rooflines = {}
+    for name, (byt, _) in work.items():
+        if name not in kt:
+            continue
+        n_, t_ = kt[name]
+        ach = byt * n_ / args.steps / (t_ / 1e3) / 1e9 if t_ > 0 else 0.0
+        rooflines[name] = {"bound": "hbm", "achieved": ach, "peak": HBM_GBS, "unit": "GB/s", "frac": ach / HBM_GBS,
+                           "traffic": None, "kernel": name, "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs",
+                           "share": t_ / total_kms}
+    dom = max(rooflines, key=lambda x: rooflines[x]["share"])
+    line = {"metric": "PHG input points/s (volumes, guide strands, segments, linking)", "value": value,
+            "unit": "points/s", "n_gpus": world, "steps": args.steps, "warmup": Wm, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (int64 fixed-point sums)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["phg"], "points": N, "seeds": S, "grid": [int(x) for x in dims],
+                       "voxels": nvox, **PHG_CFG, "l2": f"grid state {nvox * 80 / 1e6:.0f} MB rebuilt every step",
+                       "parallelism": f"independent scenes per rank x{world}"},
+            "result": {"occupied_voxels": int((occ > 0).sum()), "guides_grown": int((glen > 1).sum()),
+                       "guide_mean_vertices": float(glen[glen > 0].mean()) if (glen > 0).any() else 0.0,
+                       "segment_seeds": K, "segments_grown": int((slen > 1).sum()), "trace_steps": steps_taken,
+                       "components": int(len(np.unique(label)))},
+            "roofline": dict(rooflines[dom]), "rooflines": rooflines,
+            "kernels": {k_: {"launches": v[0], "ms": v[1], "share": v[1] / total_kms} for k_, v in kt.items()},
+            "gpu_launches": launches, "clocks": clk}
+    if not args.no_e2e:
+        f2 = hf.HairFuse(8, 0, 0, stream=stream.cuda_stream)
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        h_in = [pin(x) for x in (pts, d, roots, normals)]
+        h_out = {k_: torch.zeros(v.shape, dtype=v.dtype).pin_memory() for k_, v in outs.items()}
+        e2e = lambda: f2.phg(gc, *h_in, outputs=h_out, cut=False)
+        e2e()
+        n_e2e = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e()
+        dt = reduce_over_ranks(time.perf_counter() - t0, pg, dev)
+        d2h = sum(v.numel() * v.element_size() for k_, v in h_out.items() if k_ not in ("sverts", "svox", "stan", "slen"))
+        d2h += K * (4 + 8 + 24 + 12 * (2 * gc.max_steps + 1))
+        line["e2e"] = {"value": reduce_over_ranks(N, pg, dev, "sum") * n_e2e / dt, "unit": "points/s",
+                       "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in h_in)),
+                       "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
+                       "path": "hair_fuse_phg with HF_HOST pinned buffers (inputs in, volumes and strands out)"}
+        f2.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        v, n, dt = phg_cpu(400)
+        line["cpu_baseline"] = {"value": v, "unit": "points/s", "cores": 1, "kind": "oracle",
+                                "sample": f"the oracle (single-threaded C) on the same preset with 400 strands "
+                                          f"({n} points, same parameters), {dt:.1f} s"}
+    f.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "phg":
+        run_phg(args)
     elif args.workload == "fpmvo":
         run_fpmvo(args)
     elif args.workload == "serving16":

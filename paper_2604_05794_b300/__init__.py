@@ -306,29 +306,35 @@ class HairFuse:
         kind = _same_kind(*[q[1] for q in ptrs])
         self._c(hair_fuse_fpmvo(self.h, ctypes.byref(cfg), *[q[0] for q in ptrs], kind))
 
-    def phg(self, cfg, pts, dirs, seeds, normals, valid=None, seg_cap=None, device=None):
-        """The Parallel Hair Growing consumer (hair_fuse_phg).  cfg: hf_phg_cfg; inputs numpy arrays
-        or CUDA tensors (one kind).  Outputs are allocated here, of the inputs' kind: a dict like the
-        oracle's (occ, ori, crowd, gverts, glen, gstop, gtan, sverts, slen, svox, stan, label, n_seg)
-        with the segment arrays cut to the K segments."""
-        ins = [_ptr_kind(x) for x in (pts, dirs, valid, seeds, normals)]
-        kind = _same_kind(*[q[1] for q in ins])
-        N, S = int(pts.shape[0]), int(seeds.shape[0])
+    def phg_outputs(self, cfg, S, seg_cap, device=None):
+        """Zeroed output arrays for phg (numpy, or CUDA tensors on `device`)."""
         nvox = cfg.nx * cfg.ny * cfg.nz
         L = cfg.max_steps
-        cap = nvox if seg_cap is None else int(seg_cap)
-        if kind == HF_DEVICE:
+        if device is not None:
             import torch
-            dev = pts.device
-            mk = lambda shape, dt: torch.zeros(shape, dtype=dt, device=dev)
+            mk = lambda shape, dt: torch.zeros(shape, dtype=dt, device=device)
             i32, f32, i64 = torch.int32, torch.float32, torch.int64
         else:
             mk = lambda shape, dt: np.zeros(shape, dtype=dt)
             i32, f32, i64 = np.int32, np.float32, np.int64
-        o = dict(occ=mk(nvox, i32), ori=mk((nvox, 3), f32), crowd=mk(nvox, i32), gverts=mk((S, L + 1, 3), f32),
-                 glen=mk(S, i32), gstop=mk(S, i32), gtan=mk((S, 3), f32), sverts=mk((cap, 2 * L + 1, 3), f32),
-                 slen=mk(cap, i32), svox=mk(cap, i64), stan=mk((cap, 2, 3), f32), label=mk(S + cap, i32),
-                 n_seg=mk(1, i64))
+        return dict(occ=mk(nvox, i32), ori=mk((nvox, 3), f32), crowd=mk(nvox, i32), gverts=mk((S, L + 1, 3), f32),
+                    glen=mk(S, i32), gstop=mk(S, i32), gtan=mk((S, 3), f32), sverts=mk((seg_cap, 2 * L + 1, 3), f32),
+                    slen=mk(seg_cap, i32), svox=mk(seg_cap, i64), stan=mk((seg_cap, 2, 3), f32),
+                    label=mk(S + seg_cap, i32), n_seg=mk(1, i64))
+
+    def phg(self, cfg, pts, dirs, seeds, normals, valid=None, seg_cap=None, outputs=None, cut=True):
+        """The Parallel Hair Growing consumer (hair_fuse_phg).  cfg: hf_phg_cfg; inputs numpy arrays
+        or CUDA tensors (one kind).  Outputs (of the inputs' kind) are `outputs` (from phg_outputs) or
+        allocated here: a dict like the oracle's (occ, ori, crowd, gverts, glen, gstop, gtan, sverts,
+        slen, svox, stan, label, n_seg), the segment arrays cut to the K segments unless cut=False."""
+        ins = [_ptr_kind(x) for x in (pts, dirs, valid, seeds, normals)]
+        kind = _same_kind(*[q[1] for q in ins])
+        N, S = int(pts.shape[0]), int(seeds.shape[0])
+        if outputs is None:
+            cap = cfg.nx * cfg.ny * cfg.nz if seg_cap is None else int(seg_cap)
+            outputs = self.phg_outputs(cfg, S, cap, pts.device if kind == HF_DEVICE else None)
+        o = dict(outputs)
+        cap = int(o["slen"].shape[0])
         ptr = {k: _ptr_kind(v)[0] for k, v in o.items()}
         out = hf_phg_out(ptr["occ"], ptr["ori"], ptr["crowd"], ptr["gverts"], ptr["glen"], ptr["gstop"], ptr["gtan"],
                          cap, ptr["sverts"], ptr["slen"], ptr["svox"], ptr["stan"], ptr["label"], ptr["n_seg"])
@@ -336,10 +342,11 @@ class HairFuse:
                               ctypes.byref(out), kind))
         if kind == HF_DEVICE:
             self.sync()
-        K = int(o["n_seg"][0])
-        for k in ("sverts", "slen", "svox", "stan"):
-            o[k] = o[k][:K]
-        o["label"] = o["label"][:S + K]
+        if cut:
+            K = int(o["n_seg"][0])
+            for k in ("sverts", "slen", "svox", "stan"):
+                o[k] = o[k][:K]
+            o["label"] = o["label"][:S + K]
         return o
 
     def eval_costs(self, dirs, cost_out):

@@ -38,14 +38,18 @@ __device__ __forceinline__ long long phg_voxel(const hf_phg_cfg& g, float p0, fl
     return ((long long)(int)floorf(q2) * g.ny + (int)floorf(q1)) * g.nx + (int)floorf(q0);
 }
 
-// the cell of the linking grid: the voxel grid with one more layer on every side
-__device__ __forceinline__ int3 phg_cell(const hf_phg_cfg& g, float p0, float p1, float p2) {
-    const float q0 = __fdiv_rn(__fsub_rn(p0, g.origin[0]), g.voxel);
-    const float q1 = __fdiv_rn(__fsub_rn(p1, g.origin[1]), g.voxel);
-    const float q2 = __fdiv_rn(__fsub_rn(p2, g.origin[2]), g.voxel);
-    const int c0 = (int)fminf(fmaxf(floorf(q0) + 1.0f, 0.0f), (float)(g.nx + 1));
-    const int c1 = (int)fminf(fmaxf(floorf(q1) + 1.0f, 0.0f), (float)(g.ny + 1));
-    const int c2 = (int)fminf(fmaxf(floorf(q2) + 1.0f, 0.0f), (float)(g.nz + 1));
+// The linking grid: cells of edge `cell` >= 1.01 link_dist (so every end within link_dist of a
+// point lies in one of the 27 cells around it), covering the voxel grid and one voxel beyond it on
+// every side (every strand end lies within one step of the voxel grid); cells clamp at the border.
+struct LinkGrid {
+    float o0, o1, o2, cell;
+    int nx, ny, nz;
+};
+__device__ __forceinline__ int3 phg_cell(const LinkGrid& G, float p0, float p1, float p2) {
+    const float q0 = (p0 - G.o0) / G.cell, q1 = (p1 - G.o1) / G.cell, q2 = (p2 - G.o2) / G.cell;
+    const int c0 = (int)fminf(fmaxf(floorf(q0), 0.0f), (float)(G.nx - 1));
+    const int c1 = (int)fminf(fmaxf(floorf(q1), 0.0f), (float)(G.ny - 1));
+    const int c2 = (int)fminf(fmaxf(floorf(q2), 0.0f), (float)(G.nz - 1));
     return make_int3(c0, c1, c2);
 }
 
@@ -71,7 +75,7 @@ __global__ void k_phg_splat(hf_phg_cfg g, long long n, const float* __restrict__
 
 // ------------------------------------------------------------------ B: orientation
 __global__ void k_phg_orient(long long nvox, const int* __restrict__ occ, const long long* __restrict__ T,
-                             float* __restrict__ ori) {
+                             float* __restrict__ ori, float4* __restrict__ vrec) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nvox;
          c += (long long)gridDim.x * blockDim.x) {
         float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f;
@@ -115,28 +119,35 @@ __global__ void k_phg_orient(long long nvox, const int* __restrict__ occ, const 
         ori[3 * c] = o0;
         ori[3 * c + 1] = o1;
         ori[3 * c + 2] = o2;
+        vrec[c] = make_float4(o0, o1, o2, __int_as_float(occ[c]));   // one 16-byte read per trace step
     }
 }
 
 // ------------------------------------------------------------------ C, D: tracing
-// One trace: vertex k goes to out[3 dir k] (dir = +1 or -1); returns the vertex count (0 for a
-// guide that met no occupied voxel); *dl the last step's direction; *stop the reason.
-__device__ int phg_trace(const hf_phg_cfg& g, const int* __restrict__ occ, const float* __restrict__ ori,
-                         const int* __restrict__ crowd, float p0, float p1, float p2, float d0, float d1, float d2,
-                         int walk, float* out, int dir, float* dl, int* stop) {
+// One trace: vertex k goes to out[3 dir k] and its voxel (-1 outside) to vox[dir k] (dir = +1 or
+// -1); returns the vertex count (0 for a guide that met no occupied voxel); *dl the last step's
+// direction; *stop the reason.  vrec[c] = (orientation, point count as int bits).
+__device__ int phg_trace(const hf_phg_cfg& g, const float4* __restrict__ vrec, const int* __restrict__ crowd,
+                         float p0, float p1, float p2, float d0, float d1, float d2, int walk, float* out, int* vox,
+                         int dir, float* dl, int* stop) {
     int nv = 1;
     bool met = walk == 0;
     out[0] = p0;
     out[1] = p1;
     out[2] = p2;
     int st = HF_PHG_MAXLEN;
-    for (int t = 0; t < g.max_steps; ++t) {
-        const long long c = phg_voxel(g, p0, p1, p2);
+    long long c = -1;
+    int t = 0;
+    for (; t < g.max_steps; ++t) {
+        c = phg_voxel(g, p0, p1, p2);
+        vox[dir * (nv - 1)] = (int)c;
         if (c < 0) {
             st = met ? HF_PHG_OUTSIDE : HF_PHG_NO_ROOT;
             break;
         }
-        if (occ[c] == 0) {
+        const float4 vr = vrec[c];
+        const int cr = crowd[c];
+        if (__float_as_int(vr.w) == 0) {
             if (!met && t < walk) {
                 p0 = __fmaf_rn(g.step, d0, p0);
                 p1 = __fmaf_rn(g.step, d1, p1);
@@ -151,11 +162,11 @@ __device__ int phg_trace(const hf_phg_cfg& g, const int* __restrict__ occ, const
             break;
         }
         met = true;
-        if (crowd[c] >= g.occ_cap) {
+        if (cr >= g.occ_cap) {
             st = HF_PHG_CROWDED;
             break;
         }
-        float o0 = ori[3 * c], o1 = ori[3 * c + 1], o2 = ori[3 * c + 2];
+        float o0 = vr.x, o1 = vr.y, o2 = vr.z;
         float sd = __fmaf_rn(o0, d0, __fmaf_rn(o1, d1, __fmul_rn(o2, d2)));
         if (sd < 0.0f) {
             o0 = -o0;
@@ -178,6 +189,7 @@ __device__ int phg_trace(const hf_phg_cfg& g, const int* __restrict__ occ, const
         v[1] = p1;
         v[2] = p2;
     }
+    if (t == g.max_steps) vox[dir * (nv - 1)] = (int)phg_voxel(g, p0, p1, p2);   // the last vertex's voxel
     if (!met) nv = 0;
     dl[0] = d0;
     dl[1] = d1;
@@ -186,60 +198,74 @@ __device__ int phg_trace(const hf_phg_cfg& g, const int* __restrict__ occ, const
     return nv;
 }
 
-__global__ void k_phg_trace_guides(hf_phg_cfg g, const int* __restrict__ occ, const float* __restrict__ ori,
-                                   const int* __restrict__ crowd, long long b0, long long b1,
-                                   const float* __restrict__ seeds, const float* __restrict__ normals,
-                                   float* __restrict__ gverts, int* __restrict__ glen, int* __restrict__ gstop,
-                                   float* __restrict__ gtan) {
+// bvox: per strand of the batch, the voxels of its vertices (stride vstride)
+__global__ void k_phg_trace_guides(hf_phg_cfg g, const float4* __restrict__ vrec, const int* __restrict__ crowd,
+                                   long long b0, long long b1, const float* __restrict__ seeds,
+                                   const float* __restrict__ normals, float* __restrict__ gverts,
+                                   int* __restrict__ glen, int* __restrict__ gstop, float* __restrict__ gtan,
+                                   int* __restrict__ bvox, int vstride) {
     const long long i = b0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= b1) return;
     int stop;
-    glen[i] = phg_trace(g, occ, ori, crowd, seeds[3 * i], seeds[3 * i + 1], seeds[3 * i + 2], normals[3 * i],
+    glen[i] = phg_trace(g, vrec, crowd, seeds[3 * i], seeds[3 * i + 1], seeds[3 * i + 2], normals[3 * i],
                         normals[3 * i + 1], normals[3 * i + 2], g.root_steps,
-                        gverts + (size_t)3 * (g.max_steps + 1) * i, 1, gtan + 3 * i, &stop);
+                        gverts + (size_t)3 * (g.max_steps + 1) * i, bvox + (size_t)vstride * (i - b0), 1,
+                        gtan + 3 * i, &stop);
     gstop[i] = stop;
 }
 
-__global__ void k_phg_trace_segments(hf_phg_cfg g, const int* __restrict__ occ, const float* __restrict__ ori,
-                                     const int* __restrict__ crowd, long long b0, long long b1,
-                                     const long long* __restrict__ svox, float* __restrict__ sverts,
-                                     int* __restrict__ slen, float* __restrict__ stan) {
-    const long long k = b0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (k >= b1) return;
+// Two neighbouring lanes per seed: the even lane traces the backward half (written from the middle
+// slot down), the odd lane the forward half (from the middle slot up); the odd lane then moves the
+// polyline to the front.
+__global__ void k_phg_trace_segments(hf_phg_cfg g, const float4* __restrict__ vrec, const int* __restrict__ crowd,
+                                     long long b0, long long b1, const long long* __restrict__ svox,
+                                     float* __restrict__ sverts, int* __restrict__ slen, float* __restrict__ stan,
+                                     int* __restrict__ bvox, int vstride) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long k = b0 + (tid >> 1);
+    const int half = (int)(tid & 1);
+    if (k >= b1) return;   // both lanes of a pair
+    const unsigned pm = 3u << (threadIdx.x & 30);
     const int L = g.max_steps;
     float* sv = sverts + (size_t)3 * (2 * L + 1) * k;
+    int* bv = bvox + (size_t)vstride * (k - b0);
     float* tn = stan + 6 * k;
     const long long c = svox[k];
     if (crowd[c] > 0) {   // an earlier batch reached this voxel
-        slen[k] = 0;
-        for (int q = 0; q < 6; ++q) tn[q] = 0.0f;
+        if (half) slen[k] = 0;
+        for (int q = 0; q < 3; ++q) tn[3 * half + q] = 0.0f;
         return;
     }
     const long long cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / ((long long)g.nx * g.ny);
     const float s0 = __fmaf_rn(__fadd_rn((float)cx, 0.5f), g.voxel, g.origin[0]);
     const float s1 = __fmaf_rn(__fadd_rn((float)cy, 0.5f), g.voxel, g.origin[1]);
     const float s2 = __fmaf_rn(__fadd_rn((float)cz, 0.5f), g.voxel, g.origin[2]);
-    const float f0 = ori[3 * c], f1 = ori[3 * c + 1], f2 = ori[3 * c + 2];
+    const float4 vr = vrec[c];
+    const float sg = half ? 1.0f : -1.0f;
     int stop;
-    // the backward half from the middle slot down, the forward half from the middle slot up
-    const int nb = phg_trace(g, occ, ori, crowd, s0, s1, s2, -f0, -f1, -f2, 0, sv + 3 * L, -1, tn, &stop);
-    const int nf = phg_trace(g, occ, ori, crowd, s0, s1, s2, f0, f1, f2, 0, sv + 3 * L, 1, tn + 3, &stop);
-    const int first = L - nb + 1, n = nb + nf - 1;
-    for (int q = 0; q < 3 * n; ++q) sv[q] = sv[3 * first + q];   // to the front (first >= 0, upward copy)
-    slen[k] = n;
+    const int nh = phg_trace(g, vrec, crowd, s0, s1, s2, sg * vr.x, sg * vr.y, sg * vr.z, 0, sv + 3 * L, bv + L,
+                             half ? 1 : -1, tn + 3 * half, &stop);
+    const int nb = __shfl_sync(pm, nh, threadIdx.x & 30);
+    __syncwarp(pm);   // both halves written
+    if (half) {
+        const int first = L - nb + 1, n = nb + nh - 1;
+        for (int q = 0; q < 3 * n; ++q) sv[q] = sv[3 * first + q];   // to the front (first >= 0, upward copy)
+        for (int q = 0; q < n; ++q) bv[q] = bv[first + q];
+        slen[k] = n;
+    }
 }
 
-// Deferred occupancy: one more strand in every voxel a polyline of [b0, b1) entered.
-__global__ void k_phg_count(hf_phg_cfg g, const int* __restrict__ occ, const float* __restrict__ verts,
-                            long long stride, const int* __restrict__ len, long long b0, long long b1,
-                            int* __restrict__ crowd) {
+// Deferred occupancy: one more strand in every occupied voxel a polyline of [b0, b1) entered
+// (consecutive vertices in one voxel count once).
+__global__ void k_phg_count(const int* __restrict__ occ, const int* __restrict__ len, long long b0, long long b1,
+                            const int* __restrict__ bvox, int vstride, int* __restrict__ crowd) {
     const long long i = b0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= b1) return;
-    const float* v = verts + (size_t)stride * i;
-    long long last = -1;
+    const int* v = bvox + (size_t)vstride * (i - b0);
+    int last = -1;
     for (int k = 0; k < len[i]; ++k) {
-        const long long c = phg_voxel(g, v[3 * k], v[3 * k + 1], v[3 * k + 2]);
-        if (c >= 0 && occ[c] > 0 && c != last) atomicAdd(crowd + c, 1);
+        const int c = v[k];
+        if (c >= 0 && c != last && occ[c] > 0) atomicAdd(crowd + c, 1);
         last = c;
     }
 }
@@ -343,12 +369,12 @@ __device__ __forceinline__ bool end_of(long long e, long long S, int L, const fl
     return true;
 }
 
-__device__ __forceinline__ long long cell_index(const hf_phg_cfg& g, int3 c) {
-    return ((long long)c.z * (g.ny + 2) + c.y) * (g.nx + 2) + c.x;
+__device__ __forceinline__ long long cell_index(const LinkGrid& G, int3 c) {
+    return ((long long)c.z * G.ny + c.y) * G.nx + c.x;
 }
 
 // segment ends per cell
-__global__ void k_phg_bin(hf_phg_cfg g, long long S, long long K, const float* __restrict__ sverts,
+__global__ void k_phg_bin(hf_phg_cfg g, LinkGrid G, long long S, long long K, const float* __restrict__ sverts,
                           const int* __restrict__ slen, int* __restrict__ ccount) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= 2 * K) return;
@@ -356,7 +382,7 @@ __global__ void k_phg_bin(hf_phg_cfg g, long long S, long long K, const float* _
     const int n = slen[k];
     if (n <= 0) return;
     const float* p = sverts + (size_t)3 * (2 * g.max_steps + 1) * k + ((q & 1) ? 3 * (n - 1) : 0);
-    atomicAdd(ccount + cell_index(g, phg_cell(g, p[0], p[1], p[2])), 1);
+    atomicAdd(ccount + cell_index(G, phg_cell(G, p[0], p[1], p[2])), 1);
 }
 
 // exclusive scan of the cell counts: per block of kScanBlock cells, then the block offsets added
@@ -384,25 +410,31 @@ __global__ void k_phg_scan_add(int* __restrict__ a, long long n, const int* __re
     if (i < n) a[i] += boff[i / kScanBlock];
 }
 
-__global__ void k_phg_put(hf_phg_cfg g, long long K, const float* __restrict__ sverts, const int* __restrict__ slen,
-                          const int* __restrict__ cstart, int* __restrict__ cursor, int* __restrict__ list) {
+// each segment end into its cell's slice of the list, with what the queries need: (position, end
+// index) and (outward tangent, strand index)
+__global__ void k_phg_put(hf_phg_cfg g, LinkGrid G, long long S, long long K, const float* __restrict__ sverts,
+                          const int* __restrict__ slen, const float* __restrict__ stan, const int* __restrict__ cstart,
+                          int* __restrict__ cursor, float4* __restrict__ list) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= 2 * K) return;
     const long long k = q >> 1;
     const int n = slen[k];
     if (n <= 0) return;
     const float* p = sverts + (size_t)3 * (2 * g.max_steps + 1) * k + ((q & 1) ? 3 * (n - 1) : 0);
-    const long long c = cell_index(g, phg_cell(g, p[0], p[1], p[2]));
-    list[cstart[c] + atomicAdd(cursor + c, 1)] = (int)q;   // order within a cell does not matter below
+    const float* t = stan + 6 * k + 3 * (q & 1);
+    const long long c = cell_index(G, phg_cell(G, p[0], p[1], p[2]));
+    const long long slot = cstart[c] + atomicAdd(cursor + c, 1);   // order within a cell does not matter below
+    list[2 * slot] = make_float4(p[0], p[1], p[2], __int_as_float((int)q));
+    list[2 * slot + 1] = make_float4(t[0], t[1], t[2], __int_as_float((int)(S + k)));
 }
 
 // every strand end: the nearest compatible end of another segment (Eq. segment_connection), ties
 // to the lower end
-__global__ void k_phg_link(hf_phg_cfg g, long long S, long long K, int R, const float* __restrict__ gverts,
+__global__ void k_phg_link(hf_phg_cfg g, LinkGrid G, long long S, long long K, const float* __restrict__ gverts,
                            const int* __restrict__ glen, const float* __restrict__ gtan,
                            const float* __restrict__ sverts, const int* __restrict__ slen,
                            const float* __restrict__ stan, const int* __restrict__ cstart,
-                           const int* __restrict__ ccount, const int* __restrict__ list,
+                           const int* __restrict__ ccount, const float4* __restrict__ list,
                            long long* __restrict__ match) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= S + 2 * K) return;
@@ -413,23 +445,21 @@ __global__ void k_phg_link(hf_phg_cfg g, long long S, long long K, int R, const 
         const float pe0 = me.p[0], pe1 = me.p[1], pe2 = me.p[2];
         const float te0 = me.t[0], te1 = me.t[1], te2 = me.t[2];
         const float L2 = __fmul_rn(g.link_dist, g.link_dist);
-        const int3 c = phg_cell(g, pe0, pe1, pe2);
+        const int3 c = phg_cell(G, pe0, pe1, pe2);
         float bd = 0.0f;
-        for (int z = max(c.z - R, 0); z <= min(c.z + R, g.nz + 1); ++z)
-            for (int y = max(c.y - R, 0); y <= min(c.y + R, g.ny + 1); ++y)
-                for (int x = max(c.x - R, 0); x <= min(c.x + R, g.nx + 1); ++x) {
-                    const long long ci = cell_index(g, make_int3(x, y, z));
+        for (int z = max(c.z - 1, 0); z <= min(c.z + 1, G.nz - 1); ++z)
+            for (int y = max(c.y - 1, 0); y <= min(c.y + 1, G.ny - 1); ++y)
+                for (int x = max(c.x - 1, 0); x <= min(c.x + 1, G.nx - 1); ++x) {
+                    const long long ci = cell_index(G, make_int3(x, y, z));
                     const int s0 = cstart[ci], n = ccount[ci];
                     for (int u = 0; u < n; ++u) {
-                        const long long q = list[s0 + u];
-                        EndRef o;
-                        end_of(S + q, S, L, gverts, glen, gtan, sverts, slen, stan, o);
-                        if (o.strand == me.strand) continue;
-                        const float dx = __fsub_rn(pe0, o.p[0]), dy = __fsub_rn(pe1, o.p[1]),
-                                    dz = __fsub_rn(pe2, o.p[2]);
+                        const float4 cp = list[2 * (s0 + u)], ct = list[2 * (s0 + u) + 1];
+                        if (__float_as_int(ct.w) == me.strand) continue;
+                        const long long q = __float_as_int(cp.w);
+                        const float dx = __fsub_rn(pe0, cp.x), dy = __fsub_rn(pe1, cp.y), dz = __fsub_rn(pe2, cp.z);
                         const float d2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
                         if (!(d2 < L2)) continue;
-                        const float dt = __fmaf_rn(te0, o.t[0], __fmaf_rn(te1, o.t[1], __fmul_rn(te2, o.t[2])));
+                        const float dt = __fmaf_rn(te0, ct.x, __fmaf_rn(te1, ct.y, __fmul_rn(te2, ct.z)));
                         if (!(-dt > g.link_cos)) continue;
                         if (best < 0 || d2 < bd || (d2 == bd && q < best)) {
                             best = q;
@@ -508,9 +538,22 @@ extern "C" int hair_fuse_phg(hf_ctx* c, const hf_phg_cfg* cfg, long long N, cons
         (out->seg_cap > 0 && (!out->slen || !out->sverts)) || !out->label || !out->n_seg)
         return hf_set_err(c, HF_ERR_INVALID_ARG, "phg: null or negative argument");
     if (S + out->seg_cap >= (1LL << 31)) return hf_set_err(c, HF_ERR_SHAPE, "phg: more than 2^31 strands");
+    if (nvox >= (1LL << 31) || (double)nvox * (2 * g.max_steps + 1) > 1e15)
+        return hf_set_err(c, HF_ERR_SHAPE, "phg: grid too large");
     const int L = g.max_steps;
     const long long cap = out->seg_cap;
-    const int R = (int)floorf(g.link_dist / g.voxel) + 1;
+    // the linking grid: cells of at least 1.01 link_dist over the voxel grid and one voxel around it
+    LinkGrid G;
+    G.cell = fmaxf(g.voxel, 1.01f * g.link_dist);
+    G.o0 = g.origin[0] - g.voxel;
+    G.o1 = g.origin[1] - g.voxel;
+    G.o2 = g.origin[2] - g.voxel;
+    G.nx = (int)ceil((double)(g.nx + 2) * g.voxel / G.cell) + 1;
+    G.ny = (int)ceil((double)(g.ny + 2) * g.voxel / G.cell) + 1;
+    G.nz = (int)ceil((double)(g.nz + 2) * g.voxel / G.cell) + 1;
+    const long long nlc = (long long)G.nx * G.ny * G.nz;
+    const long long bmax = g.batch < (S > cap ? S : cap) ? g.batch : (S > cap ? S : cap);   // strands per batch
+    const int vstride = 2 * L + 1;
     // scratch: device copies of host arrays, the tensors, the scans and the links
     struct Part {
         size_t off, bytes;
@@ -522,10 +565,11 @@ extern "C" int hair_fuse_phg(hf_ctx* c, const hf_phg_cfg* cfg, long long N, cons
         return p;
     };
     const bool host = mem_kind == HF_HOST;
-    const long long nblk_v = (nvox + kScanBlock - 1) / kScanBlock, nblk_c = (ncell + kScanBlock - 1) / kScanBlock;
+    const long long nblk_v = (nvox + kScanBlock - 1) / kScanBlock, nblk_c = (nlc + kScanBlock - 1) / kScanBlock;
     const Part pT = part(sizeof(long long) * 6 * nvox), pCrowd = part(out->crowd && !host ? 0 : sizeof(int) * nvox),
                pB = part(sizeof(int) * (size_t)(nblk_v > nblk_c ? nblk_v : nblk_c)), pTot = part(sizeof(long long)),
-               pCnt = part(sizeof(int) * ncell), pCur = part(sizeof(int) * ncell), pList = part(sizeof(int) * 2 * cap),
+               pCnt = part(sizeof(int) * nlc), pCur = part(sizeof(int) * nlc), pList = part(sizeof(float4) * 4 * cap),
+               pVrec = part(sizeof(float4) * nvox), pBvox = part(sizeof(int) * vstride * (size_t)(bmax > 0 ? bmax : 1)),
                pMatch = part(sizeof(long long) * (S + 2 * cap)), pChg = part(sizeof(int)),
                pGstop = part(out->gstop && !host ? 0 : sizeof(int) * S),
                pGtan = part(out->gtan && !host ? 0 : sizeof(float) * 3 * S),
@@ -581,6 +625,8 @@ extern "C" int hair_fuse_phg(hf_ctx* c, const hf_phg_cfg* cfg, long long N, cons
     long long* svox = out->svox && !host ? (long long*)out->svox : (long long*)at(pSvox);
     float* stan = out->stan && !host ? out->stan : (float*)at(pStan);
     long long* T = (long long*)at(pT);
+    float4* vrec = (float4*)at(pVrec);
+    int* bvox = (int*)at(pBvox);
     int* bsum = (int*)at(pB);
     long long* tot = (long long*)at(pTot);
     // A, B
@@ -595,7 +641,7 @@ extern "C" int hair_fuse_phg(hf_ctx* c, const hf_phg_cfg* cfg, long long N, cons
                   })))
         return rc;
     if ((rc = run_launch(c, "k_phg_orient", [&] {
-             k_phg_orient<<<grid_for(nvox, kThreads), kThreads, 0, st>>>(nvox, occ, T, ori);
+             k_phg_orient<<<grid_for(nvox, kThreads), kThreads, 0, st>>>(nvox, occ, T, ori, vrec);
              return cudaGetLastError();
          })))
         return rc;
@@ -603,14 +649,14 @@ extern "C" int hair_fuse_phg(hf_ctx* c, const hf_phg_cfg* cfg, long long N, cons
     for (long long b0 = 0; b0 < S; b0 += g.batch) {
         const long long b1 = b0 + g.batch < S ? b0 + g.batch : S;
         if ((rc = run_launch(c, "k_phg_trace_guides", [&] {
-                 k_phg_trace_guides<<<grid_all(b1 - b0, 128), 128, 0, st>>>(g, occ, ori, crowd, b0, b1, d_seeds,
-                                                                           d_normals, gverts, glen, gstop, gtan);
+                 k_phg_trace_guides<<<grid_all(b1 - b0, 128), 128, 0, st>>>(g, vrec, crowd, b0, b1, d_seeds,
+                                                                           d_normals, gverts, glen, gstop, gtan, bvox,
+                                                                           vstride);
                  return cudaGetLastError();
              })))
             return rc;
         if ((rc = run_launch(c, "k_phg_count", [&] {
-                 k_phg_count<<<grid_all(b1 - b0, 128), 128, 0, st>>>(g, occ, gverts, 3LL * (L + 1), glen, b0, b1,
-                                                                    crowd);
+                 k_phg_count<<<grid_all(b1 - b0, 128), 128, 0, st>>>(occ, glen, b0, b1, bvox, vstride, crowd);
                  return cudaGetLastError();
              })))
             return rc;
@@ -644,14 +690,13 @@ extern "C" int hair_fuse_phg(hf_ctx* c, const hf_phg_cfg* cfg, long long N, cons
     for (long long b0 = 0; b0 < K; b0 += g.batch) {
         const long long b1 = b0 + g.batch < K ? b0 + g.batch : K;
         if ((rc = run_launch(c, "k_phg_trace_segments", [&] {
-                 k_phg_trace_segments<<<grid_all(b1 - b0, 128), 128, 0, st>>>(g, occ, ori, crowd, b0, b1, svox,
-                                                                             sverts, slen, stan);
+                 k_phg_trace_segments<<<grid_all(2 * (b1 - b0), 128), 128, 0, st>>>(g, vrec, crowd, b0, b1, svox,
+                                                                             sverts, slen, stan, bvox, vstride);
                  return cudaGetLastError();
              })))
             return rc;
         if ((rc = run_launch(c, "k_phg_count", [&] {
-                 k_phg_count<<<grid_all(b1 - b0, 128), 128, 0, st>>>(g, occ, sverts, 3LL * (2 * L + 1), slen, b0, b1,
-                                                                    crowd);
+                 k_phg_count<<<grid_all(b1 - b0, 128), 128, 0, st>>>(occ, slen, b0, b1, bvox, vstride, crowd);
                  return cudaGetLastError();
              })))
             return rc;
@@ -659,37 +704,37 @@ extern "C" int hair_fuse_phg(hf_ctx* c, const hf_phg_cfg* cfg, long long N, cons
     // E: bin the segment ends, link every end, components
     int* ccount = (int*)at(pCnt);
     int* cstart = (int*)at(pCur);   // the counts' exclusive scan
-    int* list = (int*)at(pList);
+    float4* list = (float4*)at(pList);
     long long* match = (long long*)at(pMatch);
     int* changed = (int*)at(pChg);
     const long long nends = S + 2 * K, nstr = S + K;
-    e = cudaMemsetAsync(ccount, 0, sizeof(int) * ncell, st);
+    e = cudaMemsetAsync(ccount, 0, sizeof(int) * nlc, st);
     if (e != cudaSuccess) return hf_cuda_err(c, e, "phg link clear");
     if (K > 0 && (rc = run_launch(c, "k_phg_bin", [&] {
-                      k_phg_bin<<<grid_all(2 * K, kThreads), kThreads, 0, st>>>(g, S, K, sverts, slen, ccount);
+                      k_phg_bin<<<grid_all(2 * K, kThreads), kThreads, 0, st>>>(g, G, S, K, sverts, slen, ccount);
                       return cudaGetLastError();
                   })))
         return rc;
-    e = cudaMemcpyAsync(cstart, ccount, sizeof(int) * ncell, cudaMemcpyDeviceToDevice, st);
+    e = cudaMemcpyAsync(cstart, ccount, sizeof(int) * nlc, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return hf_cuda_err(c, e, "phg link scan");
     if ((rc = run_launch(c, "k_phg_scan_cells", [&] {
-             k_phg_scan_blocks<<<(unsigned)nblk_c, kThreads, 0, st>>>(cstart, ncell, bsum);
+             k_phg_scan_blocks<<<(unsigned)nblk_c, kThreads, 0, st>>>(cstart, nlc, bsum);
              k_phg_scan_top<<<1, kThreads, 0, st>>>(bsum, nblk_c, tot);
-             k_phg_scan_add<<<grid_all(ncell, kThreads), kThreads, 0, st>>>(cstart, ncell, bsum);
+             k_phg_scan_add<<<grid_all(nlc, kThreads), kThreads, 0, st>>>(cstart, nlc, bsum);
              return cudaGetLastError();
          })))
         return rc;
     // the cursor reuses the counts
-    e = cudaMemsetAsync(ccount, 0, sizeof(int) * ncell, st);
+    e = cudaMemsetAsync(ccount, 0, sizeof(int) * nlc, st);
     if (e != cudaSuccess) return hf_cuda_err(c, e, "phg link clear");
     if (K > 0 && (rc = run_launch(c, "k_phg_put", [&] {
-                      k_phg_put<<<grid_all(2 * K, kThreads), kThreads, 0, st>>>(g, K, sverts, slen, cstart, ccount,
-                                                                              list);
+                      k_phg_put<<<grid_all(2 * K, kThreads), kThreads, 0, st>>>(g, G, S, K, sverts, slen, stan,
+                                                                              cstart, ccount, list);
                       return cudaGetLastError();
                   })))
         return rc;
     if (nends > 0 && (rc = run_launch(c, "k_phg_link", [&] {
-                          k_phg_link<<<grid_all(nends, 128), 128, 0, st>>>(g, S, K, R, gverts, glen, gtan, sverts,
+                          k_phg_link<<<grid_all(nends, 128), 128, 0, st>>>(g, G, S, K, gverts, glen, gtan, sverts,
                                                                          slen, stan, cstart, ccount, list, match);
                           return cudaGetLastError();
                       })))
@@ -706,9 +751,12 @@ extern "C" int hair_fuse_phg(hf_ctx* c, const hf_phg_cfg* cfg, long long N, cons
             e = cudaMemsetAsync(changed, 0, sizeof(int), st);
             if (e != cudaSuccess) return hf_cuda_err(c, e, "phg components");
             if ((rc = run_launch(c, "k_phg_hook", [&] {
-                     if (nends > 0)
-                         k_phg_hook<<<grid_all(nends, kThreads), kThreads, 0, st>>>(S, nends, match, label, changed);
-                     k_phg_jump<<<grid_all(nstr, kThreads), kThreads, 0, st>>>(nstr, label, changed);
+                     for (int rep = 0; rep < 3; ++rep) {   // three passes per read of the flag
+                         if (nends > 0)
+                             k_phg_hook<<<grid_all(nends, kThreads), kThreads, 0, st>>>(S, nends, match, label,
+                                                                                        changed);
+                         k_phg_jump<<<grid_all(nstr, kThreads), kThreads, 0, st>>>(nstr, label, changed);
+                     }
                      return cudaGetLastError();
                  })))
                 return rc;
