@@ -29,7 +29,7 @@ class _Scene(ctypes.Structure):
 _lib = None
 
 
-_SOURCES = ("oracle.c", "phg.c")
+_SOURCES = ("oracle.c", "phg.c", "gabor.c")
 
 
 def build():
@@ -355,3 +355,46 @@ def phg(cfg, pts, dirs, seeds, normals, valid=None, seg_cap=None):
         o[key] = o[key][:K]
     o["label"] = o["label"][:S + K]
     return o
+
+
+# ---------------------------------------------------------------------------- Gabor orientation maps
+GABOR = dict(n_theta=64, r=7, sa=2.5, sb=1.5, lam=4.0)
+
+
+def bf16(x):
+    """Round f32 values to bfloat16 (nearest even), returned as f32."""
+    lib = _load()
+    lib.or_bf16.argtypes = [ctypes.c_float]
+    lib.or_bf16.restype = ctypes.c_float
+    return np.array([lib.or_bf16(float(v)) for v in np.ravel(x)], np.float32).reshape(np.shape(x))
+
+
+def gabor_bank(n_theta=64, r=7, sa=2.5, sb=1.5, lam=4.0):
+    """(n_theta, 2, 2r+1, 2r+1) f32 bfloat16-valued kernels: even (zero-mean) and odd per orientation."""
+    lib = _load()
+    lib.or_gabor_bank.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_void_p]
+    lib.or_gabor_bank.restype = None
+    w = 2 * r + 1
+    out = np.empty((n_theta, 2, w, w), np.float32)
+    lib.or_gabor_bank(n_theta, r, sa, sb, lam, _p(out))
+    return out
+
+
+def gabor_pixels(img, idx=None, n_theta=64, r=7, sa=2.5, sb=1.5, lam=4.0):
+    """Orientation index, angle, confidence and near-tie flag at the pixels idx (flat) of one (H, W) image."""
+    lib = _load()
+    lib.or_gabor_pixels.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.or_gabor_pixels.restype = None
+    im = np.ascontiguousarray(img, np.float32)
+    H, W = im.shape
+    bank = gabor_bank(n_theta, r, sa, sb, lam)
+    idx = np.arange(H * W, dtype=np.int64) if idx is None else np.ascontiguousarray(idx, np.int64)
+    n = len(idx)
+    out = dict(k=np.empty(n, np.int32), theta=np.empty(n, np.float32), conf=np.empty(n, np.float32),
+               flag=np.empty(n, np.uint8))
+    lib.or_gabor_pixels(_p(im), H, W, n_theta, r, _p(bank), n, _p(idx), _p(out["k"]), _p(out["theta"]),
+                        _p(out["conf"]), _p(out["flag"]))
+    return out

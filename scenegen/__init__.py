@@ -212,3 +212,19 @@ def subset_scene(scene, idx):
     out["nbr"] = knn_of(out["points"], k) if k > 0 else np.zeros((len(idx), 0), np.int32)
     out.pop("owner", None)
     return out
+
+
+def strand_images(scene, blur=0.8, noise=0.02, seed=0):
+    """Grayscale views of the rendered strands, (V, H, W) f32 in [0, 1]: the strand coverage of the
+    rasterised maps (confidence > 0) blurred by a Gaussian of `blur` px, scaled to a unit maximum per
+    view, plus N(0, noise) pixel noise from `seed`, clipped to [0, 1]."""
+    from scipy.ndimage import gaussian_filter
+    conf = np.asarray(scene["conf"], np.float32)
+    rng = np.random.default_rng(seed)
+    out = np.empty(conf.shape, np.float32)
+    for v in range(conf.shape[0]):
+        im = gaussian_filter((conf[v] > 0).astype(np.float32), blur)
+        m = im.max()
+        im = im / m if m > 0 else im
+        out[v] = np.clip(im + rng.normal(size=im.shape).astype(np.float32) * np.float32(noise), 0.0, 1.0)
+    return out
