@@ -233,6 +233,36 @@ int hair_fuse_phg(hf_ctx* ctx, const hf_phg_cfg* cfg, long long N, const float* 
                   const uint8_t* valid, long long S, const float* seeds, const float* normals, hf_phg_out* out,
                   int mem_kind);
 
+/* ------------------------------------------------------------------------------------------------
+ * Orientation and confidence maps from images with Gabor filters (Sec. 3.1: O and C extracted
+ * "using Gabor filters"; the bank and the response below are readings of an unspecified step):
+ *  bank   64 orientations theta_k = k pi / 64 on a 15 x 15 window of offsets (u right, v down);
+ *         along a = u cos + v sin, across b = -u sin + v cos; envelope exp(-a^2 / (2 sigma_along^2)
+ *         - b^2 / (2 sigma_across^2)); even kernel envelope cos(2 pi b / lambda) minus its window
+ *         mean, odd kernel envelope sin(2 pi b / lambda); both rounded to bfloat16;
+ *  F_k    sqrt(e_k^2 + o_k^2) of the window correlations with the image rounded to bfloat16 (zero
+ *         outside), accumulated in FP32 on the tensor cores;
+ *  theta  theta_k* for the largest F_k (first on ties), in [0, pi) in pixel axes (the angle maps'
+ *         convention); C = 1 - mean_k F_k / F_k* (0 where all F are 0).
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct {
+    int n_theta;          /* 64 */
+    int radius;           /* 7: a 15 x 15 window */
+    float sigma_along;    /* envelope along the strand (px) */
+    float sigma_across;   /* envelope across (px) */
+    float lambda;         /* wavelength across the strand (px) */
+} hf_gabor_cfg;
+
+/* The bank as f32 values of its bfloat16 kernels: out[k][0 even, 1 odd][v][u], 64 x 2 x 15 x 15 (host
+ * memory).  HF_ERR_INVALID_ARG for a configuration other than the above. */
+int hair_fuse_gabor_bank(const hf_gabor_cfg* cfg, float* out);
+/* Maps of V images (V x H x W f32) into theta_out and conf_out (V x H x W f32), all of kind
+ * mem_kind (caller-owned); asynchronous for HF_DEVICE.  The maps can be passed to
+ * hair_fuse_upload_views.  Errors: HF_ERR_INVALID_ARG (configuration, sizes, null arrays),
+ * HF_ERR_SHAPE (more than 2^31 padded pixels), HF_ERR_TIMEOUT (a bounded device wait expired). */
+int hair_fuse_gabor(hf_ctx* ctx, const hf_gabor_cfg* cfg, int V, int H, int W, const float* images, float* theta_out,
+                    float* conf_out, int mem_kind);
+
 /* Evaluate the cost c_i(d) of M given directions for every point (no argmin, no refinement).
  *  dirs: N x M x 3 f32 (any non-zero length; the cost is scale- and sign-invariant),
  *  cost_out: N x M f32.  Both of kind mem_kind. */

@@ -54,6 +54,14 @@ class hf_phg_out(ctypes.Structure):
 PHG_MAXLEN, PHG_OUTSIDE, PHG_EMPTY, PHG_CROWDED, PHG_TURN, PHG_NO_ROOT = 1, 2, 3, 4, 5, 6
 
 
+class hf_gabor_cfg(ctypes.Structure):
+    _fields_ = [("n_theta", ctypes.c_int), ("radius", ctypes.c_int), ("sigma_along", ctypes.c_float),
+                ("sigma_across", ctypes.c_float), ("lambda_", ctypes.c_float)]
+
+
+GABOR_DEFAULT = dict(n_theta=64, radius=7, sigma_along=2.5, sigma_across=1.5, lambda_=4.0)
+
+
 class hf_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double)]
 
@@ -71,6 +79,8 @@ _SIGS = {
     "hair_fuse_upload_depth": ([_vp, _vp, _i], _i),
     "hair_fuse_fpmvo": ([_vp, _vp, _vp, _vp, _vp, _vp, _i], _i),
     "hair_fuse_eval_costs": ([_vp, _i, _vp, _vp, _i], _i),
+    "hair_fuse_gabor": ([_vp, ctypes.POINTER(hf_gabor_cfg), _i, _i, _i, _vp, _vp, _vp, _i], _i),
+    "hair_fuse_gabor_bank": ([ctypes.POINTER(hf_gabor_cfg), _vp], _i),
     "hair_fuse_phg": ([_vp, ctypes.POINTER(hf_phg_cfg), _ll, _vp, _vp, _vp, _ll, _vp, _vp, ctypes.POINTER(hf_phg_out),
                        _i], _i),
     "hair_fuse_fibonacci_hemisphere": ([_i, _vp], _i),
@@ -127,6 +137,19 @@ hair_fuse_upload_depth = _lib.hair_fuse_upload_depth
 hair_fuse_fpmvo = _lib.hair_fuse_fpmvo
 hair_fuse_eval_costs = _lib.hair_fuse_eval_costs
 hair_fuse_phg = _lib.hair_fuse_phg
+hair_fuse_gabor = _lib.hair_fuse_gabor
+hair_fuse_gabor_bank = _lib.hair_fuse_gabor_bank
+
+
+def gabor_cfg(**kw):
+    return hf_gabor_cfg(**dict(GABOR_DEFAULT, **kw))
+
+
+def gabor_bank(**kw):
+    """The Gabor bank (64, 2, 15, 15) f32 (bfloat16 values), host only."""
+    out = np.empty((64, 2, 15, 15), np.float32)
+    _check(hair_fuse_gabor_bank(ctypes.byref(gabor_cfg(**kw)), out.ctypes.data))
+    return out
 hair_fuse_fibonacci_hemisphere = _lib.hair_fuse_fibonacci_hemisphere
 hair_fuse_gemm_bf16 = _lib.hair_fuse_gemm_bf16
 hair_fuse_sync = _lib.hair_fuse_sync
@@ -348,6 +371,22 @@ class HairFuse:
                 o[k] = o[k][:K]
             o["label"] = o["label"][:S + K]
         return o
+
+    def gabor(self, images, theta_out=None, conf_out=None, **kw):
+        """Orientation and confidence maps (hair_fuse_gabor) of images (V, H, W) f32, numpy or CUDA tensor;
+        outputs allocated like the input unless given."""
+        V, H, W = (int(x) for x in images.shape)
+        if theta_out is None:
+            if isinstance(images, np.ndarray):
+                theta_out, conf_out = np.empty((V, H, W), np.float32), np.empty((V, H, W), np.float32)
+            else:
+                import torch
+                theta_out = torch.empty((V, H, W), dtype=torch.float32, device=images.device)
+                conf_out = torch.empty((V, H, W), dtype=torch.float32, device=images.device)
+        ptrs = [_ptr_kind(x) for x in (images, theta_out, conf_out)]
+        kind = _same_kind(*[q[1] for q in ptrs])
+        self._c(hair_fuse_gabor(self.h, ctypes.byref(gabor_cfg(**kw)), V, H, W, *[q[0] for q in ptrs], kind))
+        return theta_out, conf_out
 
     def eval_costs(self, dirs, cost_out):
         """Costs (N,M) of the directions dirs (N,M,3)."""

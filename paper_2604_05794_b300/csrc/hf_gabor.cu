@@ -1,0 +1,368 @@
+// hf_gabor.cu - orientation and confidence maps from images with a Gabor filter bank (the step
+// before the fusion, Sec. 3.1: O and C "using Gabor filters"), on the tensor cores.
+//
+// The bank: 64 orientations theta_k = k pi / 64, a 15 x 15 window (offsets u right, v down), along
+// a = u cos + v sin, across b = -u sin + v cos, envelope exp(-a^2 / 2 sa^2 - b^2 / 2 sb^2); even
+// kernel envelope cos(2 pi b / lambda) minus its window mean, odd kernel envelope sin(2 pi b /
+// lambda); bfloat16.  Per pixel F_k = sqrt(e_k^2 + o_k^2) of the window correlations (zero outside
+// the image), theta = theta_k* for the largest F (first on ties), C = 1 - mean F / F_k*.
+//
+// As a GEMM: D[pixel][filter] = sum over the 15 window rows dy and 16 taps dx of
+// J[row of pixel + dy][dx] . B[dy][filter][dx], with J[y'][x][dx] = I(y' - 7, x + dx - 7) (bf16,
+// zero outside, tap 15 zero) built once per image by k_gabor_prep.  k_gabor: a persistent CTA per
+// SM; one thread streams, for every tile of 128 consecutive pixels of an image row, the 15 boxes
+// of J rows (32-byte rows, 32-byte swizzle: one box is one K = 16 MMA step) through a ring in
+// shared memory with TMA and issues 15 tcgen05.mma (M = 128 pixels, N = 128 filters: 64 even then
+// 64 odd) against the bank held in shared memory; the accumulator is double-buffered in tensor
+// memory; four warps read a pixel each per lane and reduce its 64 energies to the angle and the
+// confidence.  Every mbarrier wait is bounded (2 s): on expiry the CTA records HF_DEV_ERR_TIMEOUT,
+// drains its copies and returns.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "hf_gemm.cuh"
+#include "hf_internal.cuh"
+#include "hf_tc.cuh"
+
+using namespace hf_tc;
+
+namespace {
+
+constexpr int kGOri = 64, kGR = 7, kGWin = 15, kGTaps = 16, kGN = 128;
+constexpr int kGBox = 128 * kGTaps * 2;   // bytes of one box: 128 rows x 32 bytes
+constexpr int kGRing = 40;                // boxes in flight
+constexpr int kGThreads = 160;            // warps 0-3 epilogue, warp 4 copies and MMAs
+constexpr float kPiF = 3.14159265358979f;
+
+struct GaborArgs {
+    int V, H, W, Hp, Wt, tx;   // images, rows, columns, padded rows, padded columns, tiles per row
+    long long tiles;
+    float* theta;
+    float* conf;
+    uint32_t* errw;
+};
+
+__device__ __forceinline__ uint16_t bf16_bits_rn(float x) {
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+    u = (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+    return (uint16_t)u;
+}
+
+// J[v][y'][x][0..15] = bf16(I[v][y' - 7][x + dx - 7]) (0 outside the image; tap 15 is 0)
+__global__ void k_gabor_prep(const float* __restrict__ img, int V, int H, int W, int Hp, int Wt,
+                             uint4* __restrict__ J) {
+    const long long n = (long long)V * Hp * Wt;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % Wt);
+        const long long vy = i / Wt;
+        const int yp = (int)(vy % Hp), v = (int)(vy / Hp);
+        const int y = yp - kGR;
+        uint32_t w[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            uint16_t h[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int dx = 2 * q + r, xx = x + dx - kGR;
+                float val = 0.0f;
+                if (dx < kGWin && y >= 0 && y < H && xx >= 0 && xx < W) val = img[((size_t)v * H + y) * W + xx];
+                h[r] = bf16_bits_rn(val);
+            }
+            w[q] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+        }
+        J[2 * i] = make_uint4(w[0], w[1], w[2], w[3]);
+        J[2 * i + 1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+__global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ CUtensorMap tj,
+                                                        const __grid_constant__ CUtensorMap tb, GaborArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
+    unsigned char* sB = base;                      // 15 boxes: the bank, one window row each
+    unsigned char* sA = sB + kGWin * kGBox;        // kGRing boxes of J
+    uint64_t* afull = reinterpret_cast<uint64_t*>(sA + kGRing * kGBox);
+    uint64_t* aempty = afull + kGRing;
+    uint64_t* bfull = aempty + kGRing;
+    uint64_t* accf = bfull + 1;   // [2] MMA -> epilogue
+    uint64_t* acce = accf + 2;    // [2] epilogue (4 warps) -> MMA
+    uint64_t* done = acce + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGRing; ++s) {
+            mbar_init(afull + s, 1);
+            mbar_init(aempty + s, 1);
+        }
+        mbar_init(bfull, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf + b, 1);
+            mbar_init(acce + b, 4);
+        }
+        mbar_init(done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tslot, 256);
+        tmem_relinquish();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    const long long tiles = a.tiles;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            bool ok = true;
+            const uint32_t idesc = idesc_bf16_f32(128, kGN);
+            const long long my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+            const long long total = my_tiles * kGWin;
+            long long g_load = 0, g_use = 0;
+            mbar_expect_tx(bfull, kGWin * kGBox);
+            for (int dy = 0; dy < kGWin; ++dy) tma_load_2d(sB + dy * kGBox, &tb, bfull, 0, dy * kGN);
+            auto top_up = [&]() -> bool {   // keep up to kGRing boxes in flight
+                while (g_load < total && g_load < g_use + kGRing) {
+                    const int s = (int)(g_load % kGRing);
+                    if (!mbar_wait(aempty + s, (uint32_t)(((g_load / kGRing) & 1) ^ 1), kWaitTimeoutNs)) return false;
+                    const long long t = blockIdx.x + (g_load / kGWin) * gridDim.x;
+                    const int dy = (int)(g_load % kGWin);
+                    const long long row = t / a.tx;   // image row over all images
+                    const int v = (int)(row / a.H), y = (int)(row % a.H), tx = (int)(t % a.tx);
+                    const long long jrow = ((long long)v * a.Hp + y + dy) * a.Wt + (long long)tx * 128;
+                    mbar_expect_tx(afull + s, kGBox);
+                    tma_load_2d(sA + s * kGBox, &tj, afull + s, 0, (int)jrow);
+                    ++g_load;
+                }
+                return true;
+            };
+            ok = top_up() && mbar_wait(bfull, 0, kWaitTimeoutNs);
+            long long lt = 0;
+            for (long long t = blockIdx.x; ok && t < tiles; t += gridDim.x, ++lt) {
+                const int b = (int)(lt & 1);
+                if (!mbar_wait(acce + b, (uint32_t)(((lt >> 1) & 1) ^ 1), kWaitTimeoutNs)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                for (int dy = 0; dy < kGWin; ++dy) {
+                    if (!top_up()) {
+                        ok = false;
+                        break;
+                    }
+                    const int s = (int)(g_use % kGRing);
+                    if (!mbar_wait(afull + s, (uint32_t)((g_use / kGRing) & 1), kWaitTimeoutNs)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    mma_bf16(tmem + b * kGN, sdesc_sw32(saddr(sA + s * kGBox)), sdesc_sw32(saddr(sB + dy * kGBox)),
+                             idesc, dy > 0 ? 1u : 0u);
+                    mma_commit(aempty + s);
+                    ++g_use;
+                }
+                if (!ok) break;
+                mma_commit(accf + b);
+            }
+            // wind down: every issued MMA complete, every issued copy landed (bounded)
+            mma_commit(done);
+            mbar_wait(done, 0, kWaitTimeoutNs);
+            for (long long q = g_use; q < g_load; ++q)
+                mbar_wait(afull + (int)(q % kGRing), (uint32_t)((q / kGRing) & 1), kWaitTimeoutNs);
+            if (!ok) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
+        }
+    } else {
+        // warp w reads tensor-memory lanes 32 w .. 32 w + 31: pixel 32 w + lane of the tile
+        const uint32_t tl0 = tmem + ((uint32_t)(warp * 32) << 16);
+        long long k = 0;
+        for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++k) {
+            const int b = (int)(k & 1);
+            if (!mbar_wait(accf + b, (uint32_t)((k >> 1) & 1), kWaitTimeoutNs)) {
+                if (lane == 0) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
+                break;
+            }
+            fence_after();
+            const uint32_t tl = tl0 + (uint32_t)b * kGN;
+            float best2 = -1.0f, sum = 0.0f;
+            int kb = 0;
+#pragma unroll 1
+            for (int c = 0; c < kGOri; c += 16) {
+                uint32_t ev[16], od[16];
+                tmem_ld16_issue(tl + c, ev);
+                tmem_ld16_issue(tl + kGOri + c, od);
+                tmem_ld_wait(ev);
+                tmem_ld_wait(od);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float e = __uint_as_float(ev[q]), o = __uint_as_float(od[q]);
+                    const float f2 = fmaf(e, e, o * o);
+                    sum += sqrtf(f2);
+                    if (f2 > best2) {
+                        best2 = f2;
+                        kb = c + q;
+                    }
+                }
+            }
+            // the buffer is drained: the MMAs of a later tile may overwrite it
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce + b);
+            const long long row = t / a.tx;
+            const int v = (int)(row / a.H), y = (int)(row % a.H);
+            const int x = (int)(t % a.tx) * 128 + warp * 32 + lane;
+            if (x < a.W) {
+                const float best = sqrtf(best2);
+                const size_t o = ((size_t)v * a.H + y) * a.W + x;
+                a.theta[o] = (float)kb * (kPiF / (float)kGOri);
+                a.conf[o] = best > 0.0f ? 1.0f - sum * (1.0f / (float)kGOri) / best : 0.0f;
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+uint16_t bf16_host(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+    return (uint16_t)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+
+// The bank as bf16 bits: out[k][0 even / 1 odd][v][u], k < 64, v, u < 15.
+void gabor_bank(const hf_gabor_cfg& g, std::vector<uint16_t>& out) {
+    const int w = kGWin, n = w * w;
+    out.assign((size_t)kGOri * 2 * n, 0);
+    std::vector<double> ev(n);
+    for (int k = 0; k < kGOri; ++k) {
+        const double th = 3.14159265358979323846 * k / kGOri, c = cos(th), s = sin(th);
+        double mean = 0.0;
+        for (int v = -kGR; v <= kGR; ++v)
+            for (int u = -kGR; u <= kGR; ++u) {
+                const double aa = u * c + v * s, bb = -u * s + v * c;
+                const double env = exp(-aa * aa / (2.0 * g.sigma_along * g.sigma_along) -
+                                       bb * bb / (2.0 * g.sigma_across * g.sigma_across));
+                const int q = (v + kGR) * w + (u + kGR);
+                ev[q] = env * cos(2.0 * 3.14159265358979323846 * bb / g.lambda);
+                mean += ev[q];
+                out[(size_t)(2 * k + 1) * n + q] = bf16_host((float)(env * sin(2.0 * 3.14159265358979323846 * bb / g.lambda)));
+            }
+        mean /= n;
+        for (int q = 0; q < n; ++q) out[(size_t)(2 * k) * n + q] = bf16_host((float)(ev[q] - mean));
+    }
+}
+
+bool cfg_ok(const hf_gabor_cfg* g) {
+    return g && g->n_theta == kGOri && g->radius == kGR && isfinite(g->sigma_along) && g->sigma_along > 0.0f &&
+           isfinite(g->sigma_across) && g->sigma_across > 0.0f && isfinite(g->lambda) && g->lambda > 0.0f;
+}
+
+int sync_check_errw(hf_ctx* c) {
+    uint32_t w = 0;
+    cudaError_t e = cudaMemcpyAsync(&w, c->errw.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return hf_cuda_err(c, e, "gabor");
+    if (w) {
+        cudaMemsetAsync(c->errw.p, 0, sizeof(uint32_t), c->stream);
+        cudaStreamSynchronize(c->stream);
+        return hf_set_err(c, (w & HF_DEV_ERR_TIMEOUT) ? HF_ERR_TIMEOUT : HF_ERR_CUDA, "gabor: device error word 0x%x", w);
+    }
+    return HF_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" int hair_fuse_gabor_bank(const hf_gabor_cfg* cfg, float* out) {
+    if (!cfg_ok(cfg) || !out) return HF_ERR_INVALID_ARG;
+    std::vector<uint16_t> b;
+    gabor_bank(*cfg, b);
+    for (size_t q = 0; q < b.size(); ++q) {
+        const uint32_t u = (uint32_t)b[q] << 16;
+        memcpy(out + q, &u, 4);
+    }
+    return HF_OK;
+}
+
+extern "C" int hair_fuse_gabor(hf_ctx* c, const hf_gabor_cfg* cfg, int V, int H, int W, const float* images,
+                               float* theta_out, float* conf_out, int mem_kind) {
+    if (!c) return HF_ERR_INVALID_ARG;
+    if (!cfg_ok(cfg))
+        return hf_set_err(c, HF_ERR_INVALID_ARG, "gabor: n_theta 64, radius 7, positive finite sigmas and lambda");
+    if (mem_kind != HF_HOST && mem_kind != HF_DEVICE) return hf_set_err(c, HF_ERR_INVALID_ARG, "bad mem_kind");
+    if (V < 1 || H < 1 || W < 1 || !images || !theta_out || !conf_out)
+        return hf_set_err(c, HF_ERR_INVALID_ARG, "gabor: V, H, W >= 1 and non-null arrays");
+    const int Hp = H + 2 * kGR, tx = (W + 127) / 128, Wt = tx * 128;
+    const long long jrows = (long long)V * Hp * Wt;
+    if (jrows >= (1LL << 31) - 1) return hf_set_err(c, HF_ERR_SHAPE, "gabor: more than 2^31 padded pixels");
+    const size_t npx = (size_t)V * H * W;
+    int rc;
+    // scratch: J, the bank, staged host images and outputs
+    const size_t jbytes = (size_t)jrows * 32, bbytes = (size_t)kGWin * kGN * kGTaps * 2;
+    const size_t ibytes = mem_kind == HF_HOST ? npx * 4 : 0, obytes = mem_kind == HF_HOST ? 2 * npx * 4 : 0;
+    auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+    if ((rc = hf_ensure(c, c->gabor, al(jbytes) + al(bbytes) + al(ibytes) + al(obytes)))) return rc;
+    char* base = (char*)c->gabor.p;
+    uint4* J = (uint4*)base;
+    uint16_t* Bd = (uint16_t*)(base + al(jbytes));
+    const float* img = images;
+    float *th = theta_out, *cf = conf_out;
+    cudaStream_t st = c->stream;
+    cudaError_t e = cudaSuccess;
+    if (mem_kind == HF_HOST) {
+        float* di = (float*)(base + al(jbytes) + al(bbytes));
+        e = cudaMemcpyAsync(di, images, npx * 4, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return hf_cuda_err(c, e, "gabor images");
+        img = di;
+        th = (float*)(base + al(jbytes) + al(bbytes) + al(ibytes));
+        cf = th + npx;
+    }
+    // the bank as B[dy][filter n][dx]: n < 64 even kernel of orientation n, n >= 64 odd of n - 64
+    std::vector<uint16_t> bank;
+    gabor_bank(*cfg, bank);
+    std::vector<uint16_t> B((size_t)kGWin * kGN * kGTaps, 0);
+    for (int dy = 0; dy < kGWin; ++dy)
+        for (int n = 0; n < kGN; ++n)
+            for (int dx = 0; dx < kGWin; ++dx) {
+                const int k = n % kGOri, ph = n / kGOri;
+                B[((size_t)dy * kGN + n) * kGTaps + dx] = bank[((size_t)(2 * k + ph) * kGWin + dy) * kGWin + dx];
+            }
+    e = cudaMemcpyAsync(Bd, B.data(), bbytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // B is a host vector about to go out of scope
+    if (e != cudaSuccess) return hf_cuda_err(c, e, "gabor bank");
+    CUtensorMap tj, tb;
+    if ((e = hf_make_tmap_bf16_rows32(&tj, J, jrows, 128)) != cudaSuccess ||
+        (e = hf_make_tmap_bf16_rows32(&tb, Bd, (long long)kGWin * kGN, 128)) != cudaSuccess)
+        return hf_cuda_err(c, e, "gabor tensor maps");
+    if ((rc = run_launch(c, "k_gabor_prep", [&] {
+             const long long blocks = (jrows + 255) / 256;
+             k_gabor_prep<<<(unsigned)(blocks < 148 * 32 ? blocks : 148 * 32), 256, 0, st>>>(img, V, H, W, Hp, Wt, J);
+             return cudaGetLastError();
+         })))
+        return rc;
+    GaborArgs ga{V, H, W, Hp, Wt, tx, (long long)V * H * tx, th, cf, (uint32_t*)c->errw.p};
+    const size_t smem = 1024 + (size_t)(kGWin + kGRing) * kGBox + (2 * kGRing + 6) * 8 + 16;
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    if ((rc = run_launch(c, "k_gabor", [&] {
+             cudaError_t e2 = cudaFuncSetAttribute(k_gabor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+             if (e2 != cudaSuccess) return e2;
+             const long long grid = ga.tiles < sms ? ga.tiles : sms;
+             k_gabor<<<(unsigned)grid, kGThreads, smem, st>>>(tj, tb, ga);
+             return cudaGetLastError();
+         })))
+        return rc;
+    if (mem_kind == HF_HOST) {
+        e = cudaMemcpyAsync(theta_out, th, npx * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(conf_out, cf, npx * 4, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return hf_cuda_err(c, e, "gabor outputs");
+        return sync_check_errw(c);
+    }
+    return HF_OK;
+}

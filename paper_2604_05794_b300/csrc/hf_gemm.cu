@@ -549,6 +549,26 @@ cudaError_t hf_make_tmap_bf16(CUtensorMap* map, const void* base, long long rows
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t hf_make_tmap_bf16_rows32(CUtensorMap* map, const void* base, long long rows, int box_rows) {
+    std::call_once(g_encode_once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    if (!g_encode) return cudaErrorNotSupported;
+    if (((uintptr_t)base & 15) || box_rows < 1 || box_rows > 256 || rows < 1) return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {16, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {32};
+    const cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits,
                        cudaStream_t s) {
     if (g.K % 64 || g.N % bn || g.kchunks_per_split < 1 || splits < 1) return cudaErrorInvalidValue;

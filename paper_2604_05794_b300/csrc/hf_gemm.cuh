@@ -39,6 +39,10 @@ struct GemmArgs {
 // aligned) with a {64, box_rows} box and the 128-byte swizzle.
 cudaError_t hf_make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, long long cols, int box_rows);
 
+// 2D bf16 tensor map of a row-major [rows x 16] matrix (32-byte rows, base 16-byte aligned) with a
+// {16, box_rows} box and the 32-byte swizzle: one box is one K = 16 step of a tcgen05 operand.
+cudaError_t hf_make_tmap_bf16_rows32(CUtensorMap* map, const void* base, long long rows, int box_rows);
+
 // C = A . B^T with the given epilogue; ta: A map (box 128 rows), tb: B map (box bn rows).
 cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits,
                        cudaStream_t s);

@@ -128,6 +128,13 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t smem_addr) {
     return (uint64_t)((smem_addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
+// The same for a K-major tile of 32-byte rows (16 bf16: one MMA K step) stored with the 32-byte
+// swizzle, as a TMA load with box {16, R} and CU_TENSOR_MAP_SWIZZLE_32B writes it: groups of 8 rows
+// 256 bytes apart, swizzle mode 32B.
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t smem_addr) {
+    return (uint64_t)((smem_addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
+}
 // Instruction descriptor: kind::f16 with bf16 A and B, f32 accumulator, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);

@@ -1,0 +1,77 @@
+"""GPU parity of the Gabor orientation / confidence maps (hair_fuse_gabor, tensor cores) against the
+CPU oracle on the same seeded images: the orientation index wherever the oracle's two largest
+responses are not tied within 1e-4, the confidence within the FP32-accumulation tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+
+pytestmark = pytest.mark.gpu
+
+RNG = np.random.default_rng(9)
+
+
+def run(images, device=True):
+    import torch
+
+    import paper_2604_05794_b300 as hf
+    with hf.HairFuse(8, 0, 0) as f:
+        if device:
+            th, cf = f.gabor(torch.from_numpy(np.ascontiguousarray(images)).cuda())
+            f.sync()
+            return th.cpu().numpy(), cf.cpu().numpy()
+        return f.gabor(np.ascontiguousarray(images))
+
+
+def compare(images, th, cf, v, idx, min_unique=0.7):
+    o = oracle.gabor_pixels(images[v], idx)
+    k = np.rint(th[v].ravel()[idx] * 64 / np.pi).astype(int) % 64
+    ok = o["flag"] == 0
+    assert ok.mean() > min_unique
+    assert np.array_equal(k[ok], o["k"][ok]), np.nonzero(k[ok] != o["k"][ok])[0][:10]
+    assert np.allclose(th[v].ravel()[idx][ok], o["theta"][ok], atol=1e-6)
+    c = cf[v].ravel()[idx]
+    assert np.all(np.abs(c - o["conf"]) <= 2e-4 + 2e-3 * (o["conf"] < 0.01)), np.max(np.abs(c - o["conf"]))
+    return ok.mean()
+
+
+def test_tiny_scene_views_every_pixel():
+    sc = scenegen.make_scene("tiny")
+    im = scenegen.strand_images(sc, seed=1)
+    th, cf = run(im)
+    for v in (0, 5):
+        compare(im, th, cf, v, np.arange(im.shape[1] * im.shape[2]))
+    # the maps find the strands: on covered pixels the angle is near the rendered one
+    cov = sc["conf"] > 0
+    d = np.abs((th - sc["angle"] + np.pi / 2) % np.pi - np.pi / 2)[cov]
+    assert np.median(np.degrees(d)) < 15.0   # random angles would give 45
+
+
+def test_ragged_sizes_and_random_images():
+    for V, H, W in ((2, 37, 131), (1, 200, 256), (3, 16, 1)):
+        im = RNG.random((V, H, W)).astype(np.float32)
+        im[0, :, : W // 2] = 0.0
+        th, cf = run(im)
+        for v in range(V):   # the zeroed half and a one-column image tie everywhere
+            compare(im, th, cf, v, np.arange(H * W), min_unique=0.0 if W == 1 else 0.3)
+
+
+def test_full_view_sampled_and_host_path():
+    sc = scenegen.make_scene("full", seed=2, knn=False)
+    im = scenegen.strand_images({"conf": sc["conf"][:2]}, seed=2)
+    th, cf = run(im)
+    idx = np.linspace(0, im.shape[1] * im.shape[2] - 1, 4000).astype(np.int64)
+    for v in range(2):
+        compare(im, th, cf, v, idx)
+    th2, cf2 = run(im, device=False)
+    assert np.array_equal(th, th2) and np.array_equal(cf, cf2)
+
+
+def test_gabor_arguments():
+    import paper_2604_05794_b300 as hf
+    im = np.zeros((1, 8, 8), np.float32)
+    with hf.HairFuse(8, 0, 0) as f:
+        for kw in (dict(n_theta=32), dict(radius=5), dict(sigma_along=0.0), dict(lambda_=float("nan"))):
+            with pytest.raises(hf.HairFuseError):
+                f.gabor(im, **kw)
