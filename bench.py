@@ -53,6 +53,9 @@ WORKLOADS = {
            "tangents with N(0, 0.1) noise renormalised; 20,000 scalp seeds at the strand roots): voxel 0.02, step "
            "0.01, 64 steps, 4 root steps, turn cos 0.5, 4 strands per voxel, batches of 32768 seeds, link 0.03 / "
            "cos 0.7",
+    "gabor": "orientation and confidence maps of the full scene's 64 views (1920x1080 grayscale strand images, "
+             "seed 2: rendered coverage blurred by 0.8 px plus N(0, 0.02) noise) with a 64-orientation even/odd "
+             "Gabor bank, 15x15 window, sigma 2.5 / 1.5 px, wavelength 4 px; bf16 tensor-core correlations",
     "fpmvo": "the paper's FPMVO step on the full scene (seed 2: 1,000,000 points, 64 views 1920x1080, f32 angle + "
              "fp16 confidence, depth maps from the renderer's z-buffer): K=5 top views, S=5 depth samples over "
              "[-0.0046, 0.0046], P=5 patch, lambda=4 px, depth-test tolerance 0.02",
@@ -84,6 +87,8 @@ def parse():
     ap.add_argument("--partition", action="store_true", help="full/mid/tiny under torchrun: every rank uploads "
                     "the same scene and fuses its own point range (strong scaling) instead of its own scene")
     ap.add_argument("--phg-strands", type=int, default=0, help="phg: strands of the scene (0: the full preset's)")
+    ap.add_argument("--gabor-views", type=int, default=64, help="gabor: views of the full scene (the small case "
+                    "for profiler captures: 4)")
     ap.add_argument("--fpmvo-scene", default="full", choices=["full", "mid"],
                     help="fpmvo: the scene preset (mid: the small case for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -237,6 +242,8 @@ def run_reference(args):
         return run_reference_fpmvo(args, world)
     if args.workload == "phg":
         return run_reference_phg(args, world)
+    if args.workload == "gabor":
+        return run_reference_gabor(args, world)
     if args.workload == "serving16":
         scenes = serving_scenes(200)
     elif args.workload == "learned":
@@ -1186,6 +1193,158 @@ def run_fpmvo(args):
         pg.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------- Gabor workload
+GABOR_FLOP_PER_PIXEL = 2 * 128 * 15 * 16     # the MMAs as issued: 128 filters x 15 window rows x 16 taps
+GABOR_USEFUL_FLOP_PER_PIXEL = 2 * 128 * 225  # the 15 x 15 window
+
+
+def gabor_images(views=64, seed=2):
+    import scenegen
+    sc = scenegen.make_scene("full", seed=seed, knn=False)
+    return scenegen.strand_images({"conf": sc["conf"][:views]}, seed=seed), sc
+
+
+def run_gabor(args):
+    import torch
+
+    import oracle
+    import paper_2604_05794_b300 as hf
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    im, sc = gabor_images(views=args.gabor_views, seed=2 + 100 * rank)
+    V, H, W = im.shape
+    npx = V * H * W
+    stream = torch.cuda.current_stream(dev)
+    f = hf.HairFuse(8, 0, 0, stream=stream.cuda_stream)
+    g_im = torch.from_numpy(im).to(dev)
+    th = torch.empty((V, H, W), device=dev)
+    cf = torch.empty((V, H, W), device=dev)
+    step = lambda: f.gabor(g_im, th, cf)
+    Wm = max(3, args.warmup)
+    for _ in range(Wm):
+        step()
+    f.sync()
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(cvd.split(",")[local] if cvd else str(local))
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = f.stats()["launches"]
+    f.profile(True)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    kt = f.profile_read()
+    f.profile(False)
+    launches = f.stats()["launches"] - launches0
+    ms = reduce_over_ranks(ms, pg, dev)
+    value = reduce_over_ranks(npx, pg, dev, "sum") * args.steps / (ms / 1e3) / 1e6
+    n_, t_ = kt["k_gabor"]
+    sec = t_ / n_ / 1e3
+    ach = npx * GABOR_FLOP_PER_PIXEL / sec / 1e12
+    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1800.0
+    tot = sum(v[1] for v in kt.values())
+    roofline = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "k_gabor",
+                "peak_source": "of measured: MEASURED_PEAKS.json bf16_tflops (burst cuBLAS bf16)",
+                "work": f"{GABOR_FLOP_PER_PIXEL} FLOP per pixel as issued (128 filters x 15 rows x 16 taps; "
+                        f"{GABOR_USEFUL_FLOP_PER_PIXEL} in the 15x15 window) x {npx} pixels",
+                "share": t_ / tot}
+    nb, tb = kt["k_gabor_prep"]
+    prep = {"bound": "hbm", "achieved": npx * 4 + V * (H + 14) * (-(-W // 128) * 128) * 32 / (tb / nb / 1e3) / 1e9,
+            "kernel": "k_gabor_prep", "share": tb / tot}
+    prep["achieved"] = (npx * 4 + V * (H + 14) * (-(-W // 128) * 128) * 32) / (tb / nb / 1e3) / 1e9
+    prep.update(peak=HBM_GBS, unit="GB/s", frac=prep["achieved"] / HBM_GBS, traffic=None,
+                work="4 B per image pixel read, 32 B per padded window row written")
+    line = {"metric": "Gabor orientation/confidence maps, megapixels/s", "value": value, "unit": "Mpx/s",
+            "n_gpus": world, "steps": args.steps, "warmup": Wm, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 x bf16 -> f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["gabor"], "views": V, "size": f"{W}x{H}", "pixels": npx,
+                       "l2": f"images {im.nbytes / 1e6:.0f} MB and window rows "
+                             f"{V * (H + 14) * (-(-W // 128) * 128) * 32 / 1e9:.1f} GB per step",
+                       "parallelism": f"independent view sets per rank x{world}"},
+            "roofline": roofline, "rooflines": {"k_gabor": roofline, "k_gabor_prep": prep},
+            "kernels": {k_: {"launches": v[0], "ms": v[1], "share": v[1] / tot} for k_, v in kt.items()},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        thn, cfn = th.cpu().numpy(), cf.cpu().numpy()
+        cov = sc["conf"][:V] > 0
+        d = np.degrees(np.abs((thn - sc["angle"][:V] + np.pi / 2) % np.pi - np.pi / 2))[cov]
+        idx = np.linspace(0, H * W - 1, args.accuracy_sample or 2000).astype(np.int64)
+        o = oracle.gabor_pixels(im[0], idx)
+        ok = o["flag"] == 0
+        kk = np.rint(thn[0].ravel()[idx] * 64 / np.pi).astype(int) % 64
+        line["accuracy"] = {"median_deg_vs_rendered": float(np.median(d)), "p90_deg_vs_rendered": float(np.percentile(d, 90)),
+                            "oracle_index_match": float(np.mean(kk[ok] == o["k"][ok])), "oracle_unique": float(ok.mean()),
+                            "max_conf_err": float(np.max(np.abs(cfn[0].ravel()[idx] - o["conf"]))), "sample": len(idx)}
+    if not args.no_e2e:
+        h_im = torch.from_numpy(im).pin_memory()
+        h_th = torch.empty((V, H, W)).pin_memory()
+        h_cf = torch.empty((V, H, W)).pin_memory()
+        f.gabor(h_im, h_th, h_cf)
+        n_e2e = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            f.gabor(h_im, h_th, h_cf)
+        dt = reduce_over_ranks(time.perf_counter() - t0, pg, dev)
+        line["e2e"] = {"value": reduce_over_ranks(npx, pg, dev, "sum") * n_e2e / dt / 1e6, "unit": "Mpx/s",
+                       "h2d_bytes_per_step": int(h_im.numel() * 4), "d2h_bytes_per_step": int(2 * npx * 4),
+                       "steps": n_e2e, "path": "hair_fuse_gabor with HF_HOST pinned buffers"}
+    if rank == 0 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        n_s = 3000
+        oracle.gabor_pixels(im[0], np.linspace(0, H * W - 1, n_s).astype(np.int64))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n_s / dt / 1e6, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{n_s} evenly spaced pixels of view 0 (single-threaded C, double sums), "
+                                          f"{dt:.1f} s"}
+    f.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def run_reference_gabor(args, world):
+    import oracle
+    im, _ = gabor_images(views=1)
+    H, W = im.shape[1:]
+    n = 3000
+    run = lambda: oracle.gabor_pixels(im[0], np.linspace(0, H * W - 1, n).astype(np.int64))
+    for _ in range(args.warmup):
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": "Gabor orientation/confidence maps, megapixels/s", "value": value,
+            "unit": "Mpx/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 sums of bf16 values", "data": "synthetic",
+            "config": {"workload": WORKLOADS["gabor"], "pixels_per_step": n},
+            "cpu_baseline": {"value": value, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} evenly spaced pixels of view 0 per step"},
+            "e2e": {"value": value, "unit": "Mpx/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------- PHG workload
 def phg_inputs(n_strands=0, seed=2, noise=0.1):
     """Points, noisy unit directions, scalp seeds and normals of the full preset's strands."""
@@ -1350,6 +1509,8 @@ def main():
         run_reference(args)
     elif args.workload == "phg":
         run_phg(args)
+    elif args.workload == "gabor":
+        run_gabor(args)
     elif args.workload == "fpmvo":
         run_fpmvo(args)
     elif args.workload == "serving16":

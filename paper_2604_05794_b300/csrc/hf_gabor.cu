@@ -10,12 +10,13 @@
 // As a GEMM: D[pixel][filter] = sum over the 15 window rows dy and 16 taps dx of
 // J[row of pixel + dy][dx] . B[dy][filter][dx], with J[y'][x][dx] = I(y' - 7, x + dx - 7) (bf16,
 // zero outside, tap 15 zero) built once per image by k_gabor_prep.  k_gabor: a persistent CTA per
-// SM; one thread streams, for every tile of 128 consecutive pixels of an image row, the 15 boxes
-// of J rows (32-byte rows, 32-byte swizzle: one box is one K = 16 MMA step) through a ring in
-// shared memory with TMA and issues 15 tcgen05.mma (M = 128 pixels, N = 128 filters: 64 even then
-// 64 odd) against the bank held in shared memory; the accumulator is double-buffered in tensor
-// memory; four warps read a pixel each per lane and reduce its 64 energies to the angle and the
-// confidence.  Every mbarrier wait is bounded (2 s): on expiry the CTA records HF_DEV_ERR_TIMEOUT,
+// SM walks down runs of rows of 128-column strips; one warp streams the J rows of the strip (one
+// TMA box each: 128 rows of 32 bytes, 32-byte swizzle, one K = 16 MMA step) through a ring in
+// shared memory, each J row loaded once, and another, for every output row (a tile of 128 pixels),
+// issues 15 tcgen05.mma (M = 128 pixels, N = 128 filters: 64 even then 64 odd) over the sliding window of
+// the 15 J rows it needs, against the bank held in shared memory; four accumulators in tensor memory serve four
+// epilogue groups of four warps, which read a pixel per lane and reduce its 64 energies to the
+// angle and the confidence.  Every mbarrier wait is bounded (2 s): on expiry the CTA records HF_DEV_ERR_TIMEOUT,
 // drains its copies and returns.
 #include <math.h>
 #include <stdint.h>
@@ -34,16 +35,35 @@ namespace {
 constexpr int kGOri = 64, kGR = 7, kGWin = 15, kGTaps = 16, kGN = 128;
 constexpr int kGBox = 128 * kGTaps * 2;   // bytes of one box: 128 rows x 32 bytes
 constexpr int kGRing = 40;                // boxes in flight
-constexpr int kGThreads = 160;            // warps 0-3 epilogue, warp 4 copies and MMAs
+constexpr int kGGroups = 4;               // epilogue groups of four warps, one accumulator buffer each
+constexpr int kGThreads = (4 * kGGroups + 2) * 32;   // warps 0-15 epilogue, 16 copies, 17 MMAs
 constexpr float kPiF = 3.14159265358979f;
 
 struct GaborArgs {
     int V, H, W, Hp, Wt, tx;   // images, rows, columns, padded rows, padded columns, tiles per row
-    long long tiles;
+    int chunk, nch;            // rows per unit, units per column strip
+    int units;                 // V x tx x nch work units: (image, 128-column strip, run of rows)
     float* theta;
     float* conf;
     uint32_t* errw;
 };
+
+// A work unit: the output rows [y0, y0 + n) of one 128-column strip of one image; its J rows are the
+// padded rows y0 .. y0 + n + 13 of the strip.
+struct Unit {
+    long long jrow0;   // J row of padded row y0, column 128 tx
+    int v, y0, n, tx;
+};
+__device__ __forceinline__ Unit unit_of(const GaborArgs& a, int u) {
+    Unit r;
+    const int ch = u % a.nch, st = u / a.nch;
+    r.tx = st % a.tx;
+    r.v = st / a.tx;
+    r.y0 = ch * a.chunk;
+    r.n = min(a.chunk, a.H - r.y0);
+    r.jrow0 = ((long long)r.v * a.Hp + r.y0) * a.Wt + (long long)r.tx * 128;
+    return r;
+}
 
 __device__ __forceinline__ uint16_t bf16_bits_rn(float x) {
     uint32_t u = __float_as_uint(x);
@@ -88,9 +108,9 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
     uint64_t* afull = reinterpret_cast<uint64_t*>(sA + kGRing * kGBox);
     uint64_t* aempty = afull + kGRing;
     uint64_t* bfull = aempty + kGRing;
-    uint64_t* accf = bfull + 1;   // [2] MMA -> epilogue
-    uint64_t* acce = accf + 2;    // [2] epilogue (4 warps) -> MMA
-    uint64_t* done = acce + 2;
+    uint64_t* accf = bfull + 1;         // [kGGroups] MMA -> epilogue group
+    uint64_t* acce = accf + kGGroups;   // [kGGroups] epilogue group (4 warps) -> MMA
+    uint64_t* done = acce + kGGroups;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -99,7 +119,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
             mbar_init(aempty + s, 1);
         }
         mbar_init(bfull, 1);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kGGroups; ++b) {
             mbar_init(accf + b, 1);
             mbar_init(acce + b, 4);
         }
@@ -107,86 +127,107 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
         fence_mbar_init();
     }
     if (warp == 0) {
-        tmem_alloc(tslot, 256);
+        tmem_alloc(tslot, 512);
         tmem_relinquish();
     }
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
-    const long long tiles = a.tiles;
-
-    if (warp == 4) {
+    // The CTA takes units blockIdx.x, + gridDim.x, ...; down a unit, output row y uses the J rows
+    // y .. y + 14 of the sliding window, so every J row is loaded once and freed after the last
+    // output row that uses it.  Boxes are numbered in load order; box q lives in ring slot
+    // q % kGRing.  Warp 16 loads, warp 17 issues the MMAs, warps 0-15 read the accumulators.
+    if (warp == 4 * kGGroups) {
         if (lane == 0) {
             bool ok = true;
-            const uint32_t idesc = idesc_bf16_f32(128, kGN);
-            const long long my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-            const long long total = my_tiles * kGWin;
-            long long g_load = 0, g_use = 0;
+            long long q = 0;
             mbar_expect_tx(bfull, kGWin * kGBox);
             for (int dy = 0; dy < kGWin; ++dy) tma_load_2d(sB + dy * kGBox, &tb, bfull, 0, dy * kGN);
-            auto top_up = [&]() -> bool {   // keep up to kGRing boxes in flight
-                while (g_load < total && g_load < g_use + kGRing) {
-                    const int s = (int)(g_load % kGRing);
-                    if (!mbar_wait(aempty + s, (uint32_t)(((g_load / kGRing) & 1) ^ 1), kWaitTimeoutNs)) return false;
-                    const long long t = blockIdx.x + (g_load / kGWin) * gridDim.x;
-                    const int dy = (int)(g_load % kGWin);
-                    const long long row = t / a.tx;   // image row over all images
-                    const int v = (int)(row / a.H), y = (int)(row % a.H), tx = (int)(t % a.tx);
-                    const long long jrow = ((long long)v * a.Hp + y + dy) * a.Wt + (long long)tx * 128;
-                    mbar_expect_tx(afull + s, kGBox);
-                    tma_load_2d(sA + s * kGBox, &tj, afull + s, 0, (int)jrow);
-                    ++g_load;
-                }
-                return true;
-            };
-            ok = top_up() && mbar_wait(bfull, 0, kWaitTimeoutNs);
-            long long lt = 0;
-            for (long long t = blockIdx.x; ok && t < tiles; t += gridDim.x, ++lt) {
-                const int b = (int)(lt & 1);
-                if (!mbar_wait(acce + b, (uint32_t)(((lt >> 1) & 1) ^ 1), kWaitTimeoutNs)) {
-                    ok = false;
-                    break;
-                }
-                fence_after();
-                for (int dy = 0; dy < kGWin; ++dy) {
-                    if (!top_up()) {
+            int sl = 0, ph = 0;
+            for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
+                const Unit U = unit_of(a, u);
+                for (int r = 0; r < U.n + kGWin - 1; ++r, ++q) {
+                    if (!mbar_wait(aempty + sl, (uint32_t)(ph ^ 1), kWaitTimeoutNs)) {
                         ok = false;
                         break;
                     }
-                    const int s = (int)(g_use % kGRing);
-                    if (!mbar_wait(afull + s, (uint32_t)((g_use / kGRing) & 1), kWaitTimeoutNs)) {
+                    mbar_expect_tx(afull + sl, kGBox);
+                    tma_load_2d(sA + sl * kGBox, &tj, afull + sl, 0, (int)(U.jrow0 + (long long)r * a.Wt));
+                    if (++sl == kGRing) {
+                        sl = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            // every copy this warp issued has landed before the CTA leaves (bounded): the last
+            // box of each slot is the one in flight
+            for (long long p = q - 1; p >= 0 && p >= q - kGRing; --p)
+                mbar_wait(afull + (int)(p % kGRing), (uint32_t)((p / kGRing) & 1), kWaitTimeoutNs);
+            if (!ok) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
+        }
+    } else if (warp == 4 * kGGroups + 1) {
+        if (lane == 0) {
+            bool ok = mbar_wait(bfull, 0, kWaitTimeoutNs);
+            const uint32_t idesc = idesc_bf16_f32(128, kGN);
+            long long base = 0, lt = 0;
+            for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
+                const Unit U = unit_of(a, u);
+                for (int y = 0; y < U.n; ++y, ++lt) {
+                    const int b = (int)(lt % kGGroups);   // the epilogue group that takes this tile
+                    if (!mbar_wait(acce + b, (uint32_t)(((lt / kGGroups) & 1) ^ 1), kWaitTimeoutNs)) {
                         ok = false;
                         break;
                     }
+                    // the J rows this output row meets for the first time: all 15 at the unit's first
+                    // row, then only the newest (the others were waited for by earlier rows)
+                    for (int dy = y == 0 ? 0 : kGWin - 1; dy < kGWin; ++dy) {
+                        const long long bx = base + y + dy;
+                        if (!mbar_wait(afull + (int)(bx % kGRing), (uint32_t)((bx / kGRing) & 1), kWaitTimeoutNs)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    if (!ok) break;
                     fence_after();
-                    mma_bf16(tmem + b * kGN, sdesc_sw32(saddr(sA + s * kGBox)), sdesc_sw32(saddr(sB + dy * kGBox)),
-                             idesc, dy > 0 ? 1u : 0u);
-                    mma_commit(aempty + s);
-                    ++g_use;
+                    int sl = (int)((base + y) % kGRing);
+                    for (int dy = 0; dy < kGWin; ++dy) {
+                        mma_bf16(tmem + b * kGN, sdesc_sw32(saddr(sA + sl * kGBox)), sdesc_sw32(saddr(sB + dy * kGBox)),
+                                 idesc, dy > 0 ? 1u : 0u);
+                        if (++sl == kGRing) sl = 0;
+                    }
+                    mma_commit(accf + b);
+                    mma_commit(aempty + (int)((base + y) % kGRing));   // J row y: its last use
                 }
                 if (!ok) break;
-                mma_commit(accf + b);
+                for (int r = 0; r < kGWin - 1; ++r)   // the unit's last 14 J rows
+                    mma_commit(aempty + (int)((base + U.n + r) % kGRing));
+                base += U.n + kGWin - 1;
             }
-            // wind down: every issued MMA complete, every issued copy landed (bounded)
+            // wind down: every issued MMA complete (bounded)
             mma_commit(done);
             mbar_wait(done, 0, kWaitTimeoutNs);
-            for (long long q = g_use; q < g_load; ++q)
-                mbar_wait(afull + (int)(q % kGRing), (uint32_t)((q / kGRing) & 1), kWaitTimeoutNs);
             if (!ok) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
         }
     } else {
-        // warp w reads tensor-memory lanes 32 w .. 32 w + 31: pixel 32 w + lane of the tile
-        const uint32_t tl0 = tmem + ((uint32_t)(warp * 32) << 16);
-        long long k = 0;
-        for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++k) {
-            const int b = (int)(k & 1);
-            if (!mbar_wait(accf + b, (uint32_t)((k >> 1) & 1), kWaitTimeoutNs)) {
+        // group g = warp / 4 takes this CTA's tiles g, g + 4, ... (in the producer's order: unit by
+        // unit, row by row), in tensor-memory buffer g; warp w reads lanes 32 (w % 4) .. + 31: pixel
+        // 32 (w % 4) + lane of the tile
+        const int grp = warp >> 2, quarter = warp & 3;
+        const uint32_t tl = tmem + (uint32_t)grp * kGN + ((uint32_t)(quarter * 32) << 16);
+        int u = blockIdx.x, y = grp;
+        Unit U = u < a.units ? unit_of(a, u) : Unit{};
+        while (u < a.units && y >= U.n) {   // units shorter than the offset (tiny images)
+            y -= U.n;
+            u += gridDim.x;
+            if (u < a.units) U = unit_of(a, u);
+        }
+        for (long long k = 0; u < a.units; ++k) {
+            if (!mbar_wait_idle(accf + grp, (uint32_t)(k & 1), kWaitTimeoutNs)) {
                 if (lane == 0) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
                 break;
             }
             fence_after();
-            const uint32_t tl = tl0 + (uint32_t)b * kGN;
             float best2 = -1.0f, sum = 0.0f;
             int kb = 0;
 #pragma unroll 1
@@ -200,7 +241,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                 for (int q = 0; q < 16; ++q) {
                     const float e = __uint_as_float(ev[q]), o = __uint_as_float(od[q]);
                     const float f2 = fmaf(e, e, o * o);
-                    sum += sqrtf(f2);
+                    sum += f2 > 0.0f ? f2 * rsqrtf(f2) : 0.0f;   // F_k; the argmax compares F_k^2
                     if (f2 > best2) {
                         best2 = f2;
                         kb = c + q;
@@ -210,22 +251,26 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
             // the buffer is drained: the MMAs of a later tile may overwrite it
             fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acce + b);
-            const long long row = t / a.tx;
-            const int v = (int)(row / a.H), y = (int)(row % a.H);
-            const int x = (int)(t % a.tx) * 128 + warp * 32 + lane;
+            if (lane == 0) mbar_arrive(acce + grp);
+            const int x = U.tx * 128 + quarter * 32 + lane;
             if (x < a.W) {
                 const float best = sqrtf(best2);
-                const size_t o = ((size_t)v * a.H + y) * a.W + x;
+                const size_t o = ((size_t)U.v * a.H + U.y0 + y) * a.W + x;
                 a.theta[o] = (float)kb * (kPiF / (float)kGOri);
                 a.conf[o] = best > 0.0f ? 1.0f - sum * (1.0f / (float)kGOri) / best : 0.0f;
+            }
+            y += kGGroups;   // this group's next tile
+            while (u < a.units && y >= U.n) {
+                y -= U.n;
+                u += gridDim.x;
+                if (u < a.units) U = unit_of(a, u);
             }
         }
     }
     fence_before();
     __syncthreads();
     fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 uint16_t bf16_host(float x) {
@@ -346,14 +391,22 @@ extern "C" int hair_fuse_gabor(hf_ctx* c, const hf_gabor_cfg* cfg, int V, int H,
              return cudaGetLastError();
          })))
         return rc;
-    GaborArgs ga{V, H, W, Hp, Wt, tx, (long long)V * H * tx, th, cf, (uint32_t*)c->errw.p};
-    const size_t smem = 1024 + (size_t)(kGWin + kGRing) * kGBox + (2 * kGRing + 6) * 8 + 16;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    // runs of rows: enough units for eight per SM, each run at least 64 rows where the image allows
+    const long long strips = (long long)V * tx;
+    int nch = (int)((8LL * sms + strips - 1) / strips);
+    nch = nch < 1 ? 1 : (nch > (H + 63) / 64 ? (H + 63) / 64 : nch);
+    nch = nch < 1 ? 1 : nch;
+    const int chunk = (H + nch - 1) / nch;
+    nch = (H + chunk - 1) / chunk;
+    if (strips * nch >= (1LL << 31)) return hf_set_err(c, HF_ERR_SHAPE, "gabor: too many work units");
+    GaborArgs ga{V, H, W, Hp, Wt, tx, chunk, nch, (int)(strips * nch), th, cf, (uint32_t*)c->errw.p};
+    const size_t smem = 1024 + (size_t)(kGWin + kGRing) * kGBox + (2 * kGRing + 2 + 2 * kGGroups) * 8 + 16;
     if ((rc = run_launch(c, "k_gabor", [&] {
              cudaError_t e2 = cudaFuncSetAttribute(k_gabor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
              if (e2 != cudaSuccess) return e2;
-             const long long grid = ga.tiles < sms ? ga.tiles : sms;
+             const long long grid = ga.units < sms ? ga.units : sms;
              k_gabor<<<(unsigned)grid, kGThreads, smem, st>>>(tj, tb, ga);
              return cudaGetLastError();
          })))

@@ -50,6 +50,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t
     return true;
 }
 
+// The same wait for threads that have nothing else to do: between tests the thread sleeps, so a
+// warp that waits long does not take issue slots from the warps that work.
+__device__ __forceinline__ bool mbar_wait_idle(uint64_t* b, uint32_t parity, uint64_t timeout_ns) {
+    if (mbar_try(b, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try(b, parity)) {
+        __nanosleep(200);
+        if (globaltimer() - t0 > timeout_ns) return false;
+    }
+    return true;
+}
+
 // 2D TMA tile load (x = innermost coordinate in elements, y = row) completing on bar.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
     asm volatile(
