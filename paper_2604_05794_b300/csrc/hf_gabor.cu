@@ -72,30 +72,40 @@ __device__ __forceinline__ uint16_t bf16_bits_rn(float x) {
     return (uint16_t)u;
 }
 
-// J[v][y'][x][0..15] = bf16(I[v][y' - 7][x + dx - 7]) (0 outside the image; tap 15 is 0)
+// J[v][y'][x][0..15] = bf16(I[v][y' - 7][x + dx - 7]) (0 outside the image; tap 15 is 0).  A warp
+// takes 32 consecutive x of one padded row: it reads the 46 image values they need once and each
+// lane gathers its 15 taps by shuffles, then writes its 32 bytes (the warp 1 KB, contiguous).
 __global__ void k_gabor_prep(const float* __restrict__ img, int V, int H, int W, int Hp, int Wt,
                              uint4* __restrict__ J) {
-    const long long n = (long long)V * Hp * Wt;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % Wt);
-        const long long vy = i / Wt;
-        const int yp = (int)(vy % Hp), v = (int)(vy / Hp);
-        const int y = yp - kGR;
-        uint32_t w[8];
+    const int lane = threadIdx.x & 31;
+    const long long segs = (long long)Wt / 32, nw = (long long)V * Hp * segs;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < nw;
+         w += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int seg = (int)(w % segs);
+        const long long vy = w / segs;
+        const int yp = (int)(vy % Hp), v = (int)(vy / Hp), y = yp - kGR;
+        const int x0 = seg * 32;
+        const bool row_in = y >= 0 && y < H;
+        const float* src = img + ((size_t)v * H + (row_in ? y : 0)) * W;
+        const int xa = x0 - kGR + lane, xb = xa + 32;
+        const float va = row_in && xa >= 0 && xa < W ? __ldg(src + xa) : 0.0f;
+        const float vb = row_in && lane < 2 * kGR && xb < W ? __ldg(src + xb) : 0.0f;
+        uint32_t wd[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             uint16_t h[2];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                const int dx = 2 * q + r, xx = x + dx - kGR;
-                float val = 0.0f;
-                if (dx < kGWin && y >= 0 && y < H && xx >= 0 && xx < W) val = img[((size_t)v * H + y) * W + xx];
-                h[r] = bf16_bits_rn(val);
+                const int dx = 2 * q + r, sidx = lane + dx;   // the value of x + dx - 7
+                const float lo = __shfl_sync(0xffffffffu, va, sidx & 31);
+                const float hi = __shfl_sync(0xffffffffu, vb, sidx & 31);
+                h[r] = dx < kGWin ? bf16_bits_rn(sidx < 32 ? lo : hi) : (uint16_t)0;
             }
-            w[q] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+            wd[q] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
         }
-        J[2 * i] = make_uint4(w[0], w[1], w[2], w[3]);
-        J[2 * i + 1] = make_uint4(w[4], w[5], w[6], w[7]);
+        const long long i = vy * Wt + x0 + lane;
+        J[2 * i] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        J[2 * i + 1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
     }
 }
 
