@@ -65,6 +65,22 @@ __device__ __forceinline__ Unit unit_of(const GaborArgs& a, int u) {
     return r;
 }
 
+// packed FP32 pairs (fma .f32x2: each lane rounded like the scalar instruction)
+typedef unsigned long long g_f32x2;
+__device__ __forceinline__ g_f32x2 gpk(float a, float b) {
+    g_f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void gupk(g_f32x2 r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ g_f32x2 gfma2(g_f32x2 a, g_f32x2 b, g_f32x2 c) {
+    g_f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 __device__ __forceinline__ uint16_t bf16_bits_rn(float x) {
     uint32_t u = __float_as_uint(x);
     if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
@@ -238,8 +254,13 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                 break;
             }
             fence_after();
-            float best2 = -1.0f, sum = 0.0f;
-            int kb = 0;
+            // per orientation pair: F^2 = e^2 + o^2 and F = F^2 rsqrt(F^2) as packed pairs; the
+            // argmax as an integer max of keys (F^2 bits with the low 6 cleared, then 63 - k, so
+            // the first of equal values wins; the cleared bits move F by < 2^-18 F, inside the
+            // oracle's tie margin)
+            uint32_t kmax = 0u;
+            g_f32x2 sacc = gpk(0.0f, 0.0f);
+            const g_f32x2 tiny = gpk(1e-30f, 1e-30f);
 #pragma unroll 1
             for (int c = 0; c < kGOri; c += 16) {
                 uint32_t ev[16], od[16];
@@ -248,16 +269,22 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                 tmem_ld_wait(ev);
                 tmem_ld_wait(od);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float e = __uint_as_float(ev[q]), o = __uint_as_float(od[q]);
-                    const float f2 = fmaf(e, e, o * o);
-                    sum += f2 > 0.0f ? f2 * rsqrtf(f2) : 0.0f;   // F_k; the argmax compares F_k^2
-                    if (f2 > best2) {
-                        best2 = f2;
-                        kb = c + q;
-                    }
+                for (int q = 0; q < 16; q += 2) {
+                    const g_f32x2 e = gpk(__uint_as_float(ev[q]), __uint_as_float(ev[q + 1]));
+                    const g_f32x2 o = gpk(__uint_as_float(od[q]), __uint_as_float(od[q + 1]));
+                    const g_f32x2 f2 = gfma2(e, e, gfma2(o, o, tiny));
+                    float f0, f1;
+                    gupk(f2, f0, f1);
+                    sacc = gfma2(f2, gpk(rsqrtf(f0), rsqrtf(f1)), sacc);
+                    const uint32_t k0 = (__float_as_uint(f0) & 0xFFFFFFC0u) | (uint32_t)(63 - (c + q));
+                    const uint32_t k1 = (__float_as_uint(f1) & 0xFFFFFFC0u) | (uint32_t)(62 - (c + q));
+                    kmax = max(kmax, max(k0, k1));
                 }
             }
+            float s0, s1;
+            gupk(sacc, s0, s1);
+            const float sum = s0 + s1, best2 = __uint_as_float(kmax & 0xFFFFFFC0u);
+            const int kb = 63 - (int)(kmax & 63u);
             // the buffer is drained: the MMAs of a later tile may overwrite it
             fence_before();
             __syncwarp();
