@@ -1264,21 +1264,14 @@ def run_gabor(args):
                 "work": f"{GABOR_FLOP_PER_PIXEL} FLOP per pixel as issued (128 filters x 15 rows x 16 taps; "
                         f"{GABOR_USEFUL_FLOP_PER_PIXEL} in the 15x15 window) x {npx} pixels",
                 "share": t_ / tot}
-    nb, tb = kt["k_gabor_prep"]
-    prep = {"bound": "hbm", "achieved": npx * 4 + V * (H + 14) * (-(-W // 128) * 128) * 32 / (tb / nb / 1e3) / 1e9,
-            "kernel": "k_gabor_prep", "share": tb / tot}
-    prep["achieved"] = (npx * 4 + V * (H + 14) * (-(-W // 128) * 128) * 32) / (tb / nb / 1e3) / 1e9
-    prep.update(peak=HBM_GBS, unit="GB/s", frac=prep["achieved"] / HBM_GBS, traffic=None,
-                work="4 B per image pixel read, 32 B per padded window row written")
     line = {"metric": "Gabor orientation/confidence maps, megapixels/s", "value": value, "unit": "Mpx/s",
             "n_gpus": world, "steps": args.steps, "warmup": Wm, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 x bf16 -> f32",
             "data": "synthetic",
             "config": {"workload": WORKLOADS["gabor"], "views": V, "size": f"{W}x{H}", "pixels": npx,
-                       "l2": f"images {im.nbytes / 1e6:.0f} MB and window rows "
-                             f"{V * (H + 14) * (-(-W // 128) * 128) * 32 / 1e9:.1f} GB per step",
+                       "l2": f"images {im.nbytes / 1e6:.0f} MB read every step (larger than L2)",
                        "parallelism": f"independent view sets per rank x{world}"},
-            "roofline": roofline, "rooflines": {"k_gabor": roofline, "k_gabor_prep": prep},
+            "roofline": roofline, "rooflines": {"k_gabor": roofline},
             "kernels": {k_: {"launches": v[0], "ms": v[1], "share": v[1] / tot} for k_, v in kt.items()},
             "gpu_launches": launches, "clocks": clk}
     if rank == 0:

@@ -8,15 +8,16 @@
 // the image), theta = theta_k* for the largest F (first on ties), C = 1 - mean F / F_k*.
 //
 // As a GEMM: D[pixel][filter] = sum over the 15 window rows dy and 16 taps dx of
-// J[row of pixel + dy][dx] . B[dy][filter][dx], with J[y'][x][dx] = I(y' - 7, x + dx - 7) (bf16,
-// zero outside, tap 15 zero) built once per image by k_gabor_prep.  k_gabor: a persistent CTA per
-// SM walks down runs of rows of 128-column strips; one warp streams the J rows of the strip (one
-// TMA box each: 128 rows of 32 bytes, 32-byte swizzle, one K = 16 MMA step) through a ring in
-// shared memory, each J row loaded once, and another, for every output row (a tile of 128 pixels),
-// issues 15 tcgen05.mma (M = 128 pixels, N = 128 filters: 64 even then 64 odd) over the sliding window of
-// the 15 J rows it needs, against the bank held in shared memory; four accumulators in tensor memory serve four
-// epilogue groups of four warps, which read a pixel per lane and reduce its 64 energies to the
-// angle and the confidence.  Every mbarrier wait is bounded (2 s): on expiry the CTA records HF_DEV_ERR_TIMEOUT,
+// A_r[pixel][dx] . B[dy][filter][dx], with A_r[pixel][dx] = I(r - 7, pixel + dx - 7) the "window row"
+// r = row + dy of the pixel's run (bf16, zero outside the image, tap 15 zero).  k_gabor: a
+// persistent CTA per SM walks down runs of rows of 128-column strips; four builder warps write each
+// window row of the strip once into a ring in shared memory (128 pixels x 16 taps, K-major without
+// swizzle: one box is one K = 16 MMA step), and an MMA warp issues, for every output row (a tile of
+// 128 pixels), 15 tcgen05.mma (M = 128 pixels, N = 128 filters: 64 even then 64 odd) over the
+// sliding window of the 15 window rows it needs, against the bank held in shared memory (loaded
+// once with TMA, 32-byte swizzle); four accumulators in tensor memory serve four epilogue groups of
+// four warps, which read a pixel per lane and reduce its 64 energies to the angle and the
+// confidence.  Every mbarrier wait is bounded (2 s): on expiry the CTA records HF_DEV_ERR_TIMEOUT,
 // drains its copies and returns.
 #include <math.h>
 #include <stdint.h>
@@ -36,22 +37,24 @@ constexpr int kGOri = 64, kGR = 7, kGWin = 15, kGTaps = 16, kGN = 128;
 constexpr int kGBox = 128 * kGTaps * 2;   // bytes of one box: 128 rows x 32 bytes
 constexpr int kGRing = 40;                // boxes in flight
 constexpr int kGGroups = 4;               // epilogue groups of four warps, one accumulator buffer each
-constexpr int kGThreads = (4 * kGGroups + 2) * 32;   // warps 0-15 epilogue, 16 copies, 17 MMAs
+constexpr int kGBuild = 4;                // builder warps: a thread per pixel row of a box
+constexpr int kGThreads = (4 * kGGroups + kGBuild + 1) * 32;   // warps 0-15 epilogue, 16-19 build, 20 MMAs
+constexpr int kGMmaWarp = 4 * kGGroups + kGBuild;
 constexpr float kPiF = 3.14159265358979f;
 
 struct GaborArgs {
     int V, H, W, Hp, Wt, tx;   // images, rows, columns, padded rows, padded columns, tiles per row
     int chunk, nch;            // rows per unit, units per column strip
     int units;                 // V x tx x nch work units: (image, 128-column strip, run of rows)
+    const float* img;          // V x H x W
     float* theta;
     float* conf;
     uint32_t* errw;
 };
 
-// A work unit: the output rows [y0, y0 + n) of one 128-column strip of one image; its J rows are the
-// padded rows y0 .. y0 + n + 13 of the strip.
+// A work unit: the output rows [y0, y0 + n) of one 128-column strip of one image; its window rows are
+// the padded rows y0 .. y0 + n + 13 of the strip (image rows y0 - 7 .. y0 + n + 6).
 struct Unit {
-    long long jrow0;   // J row of padded row y0, column 128 tx
     int v, y0, n, tx;
 };
 __device__ __forceinline__ Unit unit_of(const GaborArgs& a, int u) {
@@ -61,7 +64,6 @@ __device__ __forceinline__ Unit unit_of(const GaborArgs& a, int u) {
     r.v = st / a.tx;
     r.y0 = ch * a.chunk;
     r.n = min(a.chunk, a.H - r.y0);
-    r.jrow0 = ((long long)r.v * a.Hp + r.y0) * a.Wt + (long long)r.tx * 128;
     return r;
 }
 
@@ -88,49 +90,11 @@ __device__ __forceinline__ uint16_t bf16_bits_rn(float x) {
     return (uint16_t)u;
 }
 
-// J[v][y'][x][0..15] = bf16(I[v][y' - 7][x + dx - 7]) (0 outside the image; tap 15 is 0).  A warp
-// takes 32 consecutive x of one padded row: it reads the 46 image values they need once and each
-// lane gathers its 15 taps by shuffles, then writes its 32 bytes (the warp 1 KB, contiguous).
-__global__ void k_gabor_prep(const float* __restrict__ img, int V, int H, int W, int Hp, int Wt,
-                             uint4* __restrict__ J) {
-    const int lane = threadIdx.x & 31;
-    const long long segs = (long long)Wt / 32, nw = (long long)V * Hp * segs;
-    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < nw;
-         w += ((long long)gridDim.x * blockDim.x) >> 5) {
-        const int seg = (int)(w % segs);
-        const long long vy = w / segs;
-        const int yp = (int)(vy % Hp), v = (int)(vy / Hp), y = yp - kGR;
-        const int x0 = seg * 32;
-        const bool row_in = y >= 0 && y < H;
-        const float* src = img + ((size_t)v * H + (row_in ? y : 0)) * W;
-        const int xa = x0 - kGR + lane, xb = xa + 32;
-        const float va = row_in && xa >= 0 && xa < W ? __ldg(src + xa) : 0.0f;
-        const float vb = row_in && lane < 2 * kGR && xb < W ? __ldg(src + xb) : 0.0f;
-        uint32_t wd[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            uint16_t h[2];
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int dx = 2 * q + r, sidx = lane + dx;   // the value of x + dx - 7
-                const float lo = __shfl_sync(0xffffffffu, va, sidx & 31);
-                const float hi = __shfl_sync(0xffffffffu, vb, sidx & 31);
-                h[r] = dx < kGWin ? bf16_bits_rn(sidx < 32 ? lo : hi) : (uint16_t)0;
-            }
-            wd[q] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
-        }
-        const long long i = vy * Wt + x0 + lane;
-        J[2 * i] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-        J[2 * i + 1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
-    }
-}
-
-__global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ CUtensorMap tj,
-                                                        const __grid_constant__ CUtensorMap tb, GaborArgs a) {
+__global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ CUtensorMap tb, GaborArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
     unsigned char* sB = base;                      // 15 boxes: the bank, one window row each
-    unsigned char* sA = sB + kGWin * kGBox;        // kGRing boxes of J
+    unsigned char* sA = sB + kGWin * kGBox;        // kGRing boxes of window rows
     uint64_t* afull = reinterpret_cast<uint64_t*>(sA + kGRing * kGBox);
     uint64_t* aempty = afull + kGRing;
     uint64_t* bfull = aempty + kGRing;
@@ -160,39 +124,62 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
-    // The CTA takes units blockIdx.x, + gridDim.x, ...; down a unit, output row y uses the J rows
-    // y .. y + 14 of the sliding window, so every J row is loaded once and freed after the last
-    // output row that uses it.  Boxes are numbered in load order; box q lives in ring slot
-    // q % kGRing.  Warp 16 loads, warp 17 issues the MMAs, warps 0-15 read the accumulators.
-    if (warp == 4 * kGGroups) {
-        if (lane == 0) {
-            bool ok = true;
-            long long q = 0;
+    // The CTA takes units blockIdx.x, + gridDim.x, ...; down a unit, output row y uses the window
+    // rows y .. y + 14, so every window row is built once and freed after the last output row that
+    // uses it.  Boxes are numbered in build order; box q lives in ring slot q % kGRing.  Warps 16-19
+    // build, warp 20 issues the MMAs, warps 0-15 read the accumulators.
+    if (warp >= 4 * kGGroups && warp < kGMmaWarp) {
+        // Builders: the box of padded row r of a unit is its 128 pixels x 16 taps, taps
+        // I(r - 7, x + dx - 7) in bf16 (0 outside, tap 15 = 0), written K-major without swizzle:
+        // pixel p's taps 0-7 at (p / 8) 256 + (p % 8) 16 bytes, taps 8-15 128 bytes further.
+        // Thread 0 waits for the slot; the named barrier 1 orders the 128 builders around it.
+        __shared__ int s_ok;
+        const int p = threadIdx.x - 4 * kGGroups * 32;
+        if (p == 0) {
             mbar_expect_tx(bfull, kGWin * kGBox);
             for (int dy = 0; dy < kGWin; ++dy) tma_load_2d(sB + dy * kGBox, &tb, bfull, 0, dy * kGN);
-            int sl = 0, ph = 0;
-            for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
-                const Unit U = unit_of(a, u);
-                for (int r = 0; r < U.n + kGWin - 1; ++r, ++q) {
-                    if (!mbar_wait(aempty + sl, (uint32_t)(ph ^ 1), kWaitTimeoutNs)) {
-                        ok = false;
-                        break;
+        }
+        int sl = 0, ph = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
+            const Unit U = unit_of(a, u);
+            const int x = U.tx * 128 + p;
+            for (int r = 0; r < U.n + kGWin - 1; ++r) {
+                if (p == 0) s_ok = mbar_wait_idle(aempty + sl, (uint32_t)(ph ^ 1), kWaitTimeoutNs) ? 1 : 0;
+                asm volatile("bar.sync 1, %0;" ::"r"(kGBuild * 32) : "memory");
+                if (!s_ok) {
+                    ok = false;
+                    break;
+                }
+                const int yi = U.y0 + r - kGR;
+                const float* src = a.img + ((size_t)U.v * a.H + (yi >= 0 && yi < a.H ? yi : 0)) * a.W;
+                const bool row_in = yi >= 0 && yi < a.H;
+                uint32_t w[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    uint16_t h[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int dx = 2 * q + e, xx = x + dx - kGR;
+                        const float val = dx < kGWin && row_in && xx >= 0 && xx < a.W ? __ldg(src + xx) : 0.0f;
+                        h[e] = bf16_bits_rn(val);
                     }
-                    mbar_expect_tx(afull + sl, kGBox);
-                    tma_load_2d(sA + sl * kGBox, &tj, afull + sl, 0, (int)(U.jrow0 + (long long)r * a.Wt));
-                    if (++sl == kGRing) {
-                        sl = 0;
-                        ph ^= 1;
-                    }
+                    w[q] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+                }
+                unsigned char* dst = sA + sl * kGBox + (p >> 3) * 256 + (p & 7) * 16;
+                *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(dst + 128) = make_uint4(w[4], w[5], w[6], w[7]);
+                fence_proxy_async();   // the tensor cores read what these stores wrote
+                asm volatile("bar.sync 1, %0;" ::"r"(kGBuild * 32) : "memory");
+                if (p == 0) mbar_arrive(afull + sl);
+                if (++sl == kGRing) {
+                    sl = 0;
+                    ph ^= 1;
                 }
             }
-            // every copy this warp issued has landed before the CTA leaves (bounded): the last
-            // box of each slot is the one in flight
-            for (long long p = q - 1; p >= 0 && p >= q - kGRing; --p)
-                mbar_wait(afull + (int)(p % kGRing), (uint32_t)((p / kGRing) & 1), kWaitTimeoutNs);
-            if (!ok) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
         }
-    } else if (warp == 4 * kGGroups + 1) {
+        if (!ok && p == 0) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
+    } else if (warp == kGMmaWarp) {
         if (lane == 0) {
             bool ok = mbar_wait(bfull, 0, kWaitTimeoutNs);
             const uint32_t idesc = idesc_bf16_f32(128, kGN);
@@ -205,7 +192,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                         ok = false;
                         break;
                     }
-                    // the J rows this output row meets for the first time: all 15 at the unit's first
+                    // the window rows this output row meets first: all 15 at the unit's first
                     // row, then only the newest (the others were waited for by earlier rows)
                     for (int dy = y == 0 ? 0 : kGWin - 1; dy < kGWin; ++dy) {
                         const long long bx = base + y + dy;
@@ -218,15 +205,15 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                     fence_after();
                     int sl = (int)((base + y) % kGRing);
                     for (int dy = 0; dy < kGWin; ++dy) {
-                        mma_bf16(tmem + b * kGN, sdesc_sw32(saddr(sA + sl * kGBox)), sdesc_sw32(saddr(sB + dy * kGBox)),
-                                 idesc, dy > 0 ? 1u : 0u);
+                        mma_bf16(tmem + b * kGN, sdesc_none(saddr(sA + sl * kGBox), 128, 256),
+                                 sdesc_sw32(saddr(sB + dy * kGBox)), idesc, dy > 0 ? 1u : 0u);
                         if (++sl == kGRing) sl = 0;
                     }
                     mma_commit(accf + b);
-                    mma_commit(aempty + (int)((base + y) % kGRing));   // J row y: its last use
+                    mma_commit(aempty + (int)((base + y) % kGRing));   // window row y: its last use
                 }
                 if (!ok) break;
-                for (int r = 0; r < kGWin - 1; ++r)   // the unit's last 14 J rows
+                for (int r = 0; r < kGWin - 1; ++r)   // the unit's last 14 window rows
                     mma_commit(aempty + (int)((base + U.n + r) % kGRing));
                 base += U.n + kGWin - 1;
             }
@@ -381,28 +368,26 @@ extern "C" int hair_fuse_gabor(hf_ctx* c, const hf_gabor_cfg* cfg, int V, int H,
     if (V < 1 || H < 1 || W < 1 || !images || !theta_out || !conf_out)
         return hf_set_err(c, HF_ERR_INVALID_ARG, "gabor: V, H, W >= 1 and non-null arrays");
     const int Hp = H + 2 * kGR, tx = (W + 127) / 128, Wt = tx * 128;
-    const long long jrows = (long long)V * Hp * Wt;
-    if (jrows >= (1LL << 31) - 1) return hf_set_err(c, HF_ERR_SHAPE, "gabor: more than 2^31 padded pixels");
+    if ((long long)V * Hp * Wt >= (1LL << 31) - 1) return hf_set_err(c, HF_ERR_SHAPE, "gabor: more than 2^31 padded pixels");
     const size_t npx = (size_t)V * H * W;
     int rc;
-    // scratch: J, the bank, staged host images and outputs
-    const size_t jbytes = (size_t)jrows * 32, bbytes = (size_t)kGWin * kGN * kGTaps * 2;
+    // scratch: the bank, staged host images and outputs
+    const size_t bbytes = (size_t)kGWin * kGN * kGTaps * 2;
     const size_t ibytes = mem_kind == HF_HOST ? npx * 4 : 0, obytes = mem_kind == HF_HOST ? 2 * npx * 4 : 0;
     auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
-    if ((rc = hf_ensure(c, c->gabor, al(jbytes) + al(bbytes) + al(ibytes) + al(obytes)))) return rc;
+    if ((rc = hf_ensure(c, c->gabor, al(bbytes) + al(ibytes) + al(obytes)))) return rc;
     char* base = (char*)c->gabor.p;
-    uint4* J = (uint4*)base;
-    uint16_t* Bd = (uint16_t*)(base + al(jbytes));
+    uint16_t* Bd = (uint16_t*)base;
     const float* img = images;
     float *th = theta_out, *cf = conf_out;
     cudaStream_t st = c->stream;
     cudaError_t e = cudaSuccess;
     if (mem_kind == HF_HOST) {
-        float* di = (float*)(base + al(jbytes) + al(bbytes));
+        float* di = (float*)(base + al(bbytes));
         e = cudaMemcpyAsync(di, images, npx * 4, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return hf_cuda_err(c, e, "gabor images");
         img = di;
-        th = (float*)(base + al(jbytes) + al(bbytes) + al(ibytes));
+        th = (float*)(base + al(bbytes) + al(ibytes));
         cf = th + npx;
     }
     // the bank as B[dy][filter n][dx]: n < 64 even kernel of orientation n, n >= 64 odd of n - 64
@@ -418,16 +403,9 @@ extern "C" int hair_fuse_gabor(hf_ctx* c, const hf_gabor_cfg* cfg, int V, int H,
     e = cudaMemcpyAsync(Bd, B.data(), bbytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // B is a host vector about to go out of scope
     if (e != cudaSuccess) return hf_cuda_err(c, e, "gabor bank");
-    CUtensorMap tj, tb;
-    if ((e = hf_make_tmap_bf16_rows32(&tj, J, jrows, 128)) != cudaSuccess ||
-        (e = hf_make_tmap_bf16_rows32(&tb, Bd, (long long)kGWin * kGN, 128)) != cudaSuccess)
-        return hf_cuda_err(c, e, "gabor tensor maps");
-    if ((rc = run_launch(c, "k_gabor_prep", [&] {
-             const long long blocks = (jrows + 255) / 256;
-             k_gabor_prep<<<(unsigned)(blocks < 148 * 32 ? blocks : 148 * 32), 256, 0, st>>>(img, V, H, W, Hp, Wt, J);
-             return cudaGetLastError();
-         })))
-        return rc;
+    CUtensorMap tb;
+    if ((e = hf_make_tmap_bf16_rows32(&tb, Bd, (long long)kGWin * kGN, 128)) != cudaSuccess)
+        return hf_cuda_err(c, e, "gabor tensor map");
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     // runs of rows: enough units for eight per SM, each run at least 64 rows where the image allows
@@ -438,13 +416,13 @@ extern "C" int hair_fuse_gabor(hf_ctx* c, const hf_gabor_cfg* cfg, int V, int H,
     const int chunk = (H + nch - 1) / nch;
     nch = (H + chunk - 1) / chunk;
     if (strips * nch >= (1LL << 31)) return hf_set_err(c, HF_ERR_SHAPE, "gabor: too many work units");
-    GaborArgs ga{V, H, W, Hp, Wt, tx, chunk, nch, (int)(strips * nch), th, cf, (uint32_t*)c->errw.p};
+    GaborArgs ga{V, H, W, Hp, Wt, tx, chunk, nch, (int)(strips * nch), img, th, cf, (uint32_t*)c->errw.p};
     const size_t smem = 1024 + (size_t)(kGWin + kGRing) * kGBox + (2 * kGRing + 2 + 2 * kGGroups) * 8 + 16;
     if ((rc = run_launch(c, "k_gabor", [&] {
              cudaError_t e2 = cudaFuncSetAttribute(k_gabor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
              if (e2 != cudaSuccess) return e2;
              const long long grid = ga.units < sms ? ga.units : sms;
-             k_gabor<<<(unsigned)grid, kGThreads, smem, st>>>(tj, tb, ga);
+             k_gabor<<<(unsigned)grid, kGThreads, smem, st>>>(tb, ga);
              return cudaGetLastError();
          })))
         return rc;

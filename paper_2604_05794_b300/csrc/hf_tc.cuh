@@ -147,6 +147,12 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t smem_addr) {
     return (uint64_t)((smem_addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
 }
+// The same for a K-major tile without swizzle: core matrices of 8 rows x 16 bytes (rows 16 bytes
+// apart), lbo bytes between core matrices adjacent in K, sbo bytes between 8-row groups.
+__device__ __forceinline__ uint64_t sdesc_none(uint32_t smem_addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((smem_addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
 // Instruction descriptor: kind::f16 with bf16 A and B, f32 accumulator, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
