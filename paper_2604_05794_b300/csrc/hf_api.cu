@@ -415,7 +415,7 @@ void hair_fuse_destroy(hf_ctx* c) {
         cudaEventDestroy(r.beg);
         cudaEventDestroy(r.end);
     }
-    DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->amap, &c->depth, &c->dmap, &c->vmap, &c->fprec, &c->phg, &c->gabor, &c->rlist, &c->pts, &c->nbr, &c->samp, &c->ab, &c->qtab,
+    DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->amap, &c->depth, &c->dmap, &c->vmap, &c->fprec, &c->phg, &c->gabor, &c->gbank, &c->rlist, &c->pts, &c->nbr, &c->samp, &c->ab, &c->qtab,
                       &c->vthr, &c->hyps, &c->rot, &c->outs, &c->evald, &c->errw, &c->work, &c->best, &c->feat, &c->prop, &c->lmisc};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);

@@ -11,14 +11,15 @@
 // A_r[pixel][dx] . B[dy][filter][dx], with A_r[pixel][dx] = I(r - 7, pixel + dx - 7) the "window row"
 // r = row + dy of the pixel's run (bf16, zero outside the image, tap 15 zero).  k_gabor: a
 // persistent CTA per SM walks down runs of rows of 128-column strips; four builder warps write each
-// window row of the strip once into a ring in shared memory (128 pixels x 16 taps, K-major without
-// swizzle: one box is one K = 16 MMA step), and an MMA warp issues, for every output row (a tile of
-// 128 pixels), 15 tcgen05.mma (M = 128 pixels, N = 128 filters: 64 even then 64 odd) over the
-// sliding window of the 15 window rows it needs, against the bank held in shared memory (loaded
-// once with TMA, 32-byte swizzle); four accumulators in tensor memory serve four epilogue groups of
-// four warps, which read a pixel per lane and reduce its 64 energies to the angle and the
-// confidence.  Every mbarrier wait is bounded (2 s): on expiry the CTA records HF_DEV_ERR_TIMEOUT,
-// drains its copies and returns.
+// window row of the strip once, straight from the image, into a ring of 16 boxes in tensor memory
+// (lane = pixel, 8 columns of bf16 pairs: one box is the A operand of one K = 16 MMA step), and an
+// MMA warp issues, for every output row (a tile of 128 pixels), 15 tcgen05.mma (M = 128 pixels,
+// N = 128 filters: 64 even then 64 odd; A from tensor memory, B from shared memory) over the sliding
+// window of the 15 window rows it needs, against the bank held in shared memory (loaded once with
+// TMA, 32-byte swizzle).  With A in tensor memory an MMA reads only the 4 KB bank box from shared
+// memory.  Three accumulators in tensor memory serve three epilogue groups of four warps, which
+// read a pixel per lane and reduce its 64 energies to the angle and the confidence.  Every mbarrier
+// wait is bounded (2 s): on expiry the CTA records HF_DEV_ERR_TIMEOUT, drains its MMAs and returns.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -34,11 +35,15 @@ using namespace hf_tc;
 namespace {
 
 constexpr int kGOri = 64, kGR = 7, kGWin = 15, kGTaps = 16, kGN = 128;
-constexpr int kGBox = 128 * kGTaps * 2;   // bytes of one box: 128 rows x 32 bytes
-constexpr int kGRing = 40;                // boxes in flight
-constexpr int kGGroups = 4;               // epilogue groups of four warps, one accumulator buffer each
-constexpr int kGBuild = 4;                // builder warps: a thread per pixel row of a box
-constexpr int kGThreads = (4 * kGGroups + kGBuild + 1) * 32;   // warps 0-15 epilogue, 16-19 build, 20 MMAs
+constexpr int kGBox = 128 * kGTaps * 2;   // bytes of one bank box: 128 filters x 32 bytes
+constexpr int kGGroups = 3;               // epilogue groups of four warps, one accumulator each
+constexpr int kGRing = 16;                // window-row boxes held in tensor memory (a power of two)
+constexpr int kGBoxCols = kGTaps / 2;     // tensor-memory columns of one window-row box (2 bf16 each)
+constexpr int kGACol = kGGroups * kGN;    // first tensor-memory column of the ring
+static_assert(kGACol + kGRing * kGBoxCols <= 512, "accumulators and ring exceed the 512 tensor-memory columns");
+static_assert((kGRing & (kGRing - 1)) == 0 && kGRing >= kGWin + 1, "ring: a power of two above the window");
+constexpr int kGBuild = 4;                // builder warps: a thread per pixel row (tensor-memory lane) of a box
+constexpr int kGThreads = (4 * kGGroups + kGBuild + 1) * 32;   // epilogue warps, builders, the MMA warp
 constexpr int kGMmaWarp = 4 * kGGroups + kGBuild;
 constexpr float kPiF = 3.14159265358979f;
 
@@ -83,19 +88,28 @@ __device__ __forceinline__ g_f32x2 gfma2(g_f32x2 a, g_f32x2 b, g_f32x2 c) {
     return d;
 }
 
-__device__ __forceinline__ uint16_t bf16_bits_rn(float x) {
-    uint32_t u = __float_as_uint(x);
-    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
-    u = (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
-    return (uint16_t)u;
+// The 15 taps I(r - 7, x + dx - 7), dx < 15, of pixel column x in padded row r of unit U (0 outside).
+__device__ __forceinline__ void load_taps(const GaborArgs& a, const Unit& U, int r, int x, float (&t)[kGWin]) {
+    const int yi = U.y0 + r - kGR;
+    const bool row_in = yi >= 0 && yi < a.H;
+    const float* src = a.img + ((size_t)U.v * a.H + (row_in ? yi : 0)) * a.W;
+    if (row_in && x >= kGR && x + kGR < a.W) {   // the whole window inside the image
+#pragma unroll
+        for (int dx = 0; dx < kGWin; ++dx) t[dx] = __ldg(src + x + dx - kGR);
+    } else {
+#pragma unroll
+        for (int dx = 0; dx < kGWin; ++dx) {
+            const int xx = x + dx - kGR;
+            t[dx] = row_in && xx >= 0 && xx < a.W ? __ldg(src + xx) : 0.0f;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ CUtensorMap tb, GaborArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
     unsigned char* sB = base;                      // 15 boxes: the bank, one window row each
-    unsigned char* sA = sB + kGWin * kGBox;        // kGRing boxes of window rows
-    uint64_t* afull = reinterpret_cast<uint64_t*>(sA + kGRing * kGBox);
+    uint64_t* afull = reinterpret_cast<uint64_t*>(sB + kGWin * kGBox);
     uint64_t* aempty = afull + kGRing;
     uint64_t* bfull = aempty + kGRing;
     uint64_t* accf = bfull + 1;         // [kGGroups] MMA -> epilogue group
@@ -105,7 +119,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kGRing; ++s) {
-            mbar_init(afull + s, 1);
+            mbar_init(afull + s, kGBuild);
             mbar_init(aempty + s, 1);
         }
         mbar_init(bfull, 1);
@@ -124,71 +138,73 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
-    // The CTA takes units blockIdx.x, + gridDim.x, ...; down a unit, output row y uses the window
-    // rows y .. y + 14, so every window row is built once and freed after the last output row that
-    // uses it.  Boxes are numbered in build order; box q lives in ring slot q % kGRing.  Warps 16-19
-    // build, warp 20 issues the MMAs, warps 0-15 read the accumulators.
+    // Tensor memory: columns 128 g .. 128 g + 127 accumulate the tiles of epilogue group g; columns
+    // kGACol + 8 s .. + 7 hold ring slot s, a window-row box as the MMAs' A operand (lane = pixel,
+    // two bf16 taps per column, tap 0 in the low half).  The CTA takes units blockIdx.x, +
+    // gridDim.x, ...; down a unit, output row y uses the window rows y .. y + 14, so every window
+    // row is built once and freed after the last output row that uses it.  Boxes are numbered in
+    // build order; box q lives in slot q % kGRing.
     if (warp >= 4 * kGGroups && warp < kGMmaWarp) {
-        // Builders: the box of padded row r of a unit is its 128 pixels x 16 taps, taps
-        // I(r - 7, x + dx - 7) in bf16 (0 outside, tap 15 = 0), written K-major without swizzle:
-        // pixel p's taps 0-7 at (p / 8) 256 + (p % 8) 16 bytes, taps 8-15 128 bytes further.
-        // Thread 0 waits for the slot; the named barrier 1 orders the 128 builders around it.
-        __shared__ int s_ok;
-        const int p = threadIdx.x - 4 * kGGroups * 32;
-        if (p == 0) {
+        // Builder warp q writes lanes 32 q .. 32 q + 31 of every box (a warp reaches only its own
+        // quarter of the lanes): taps in bf16 (round to nearest even), tap 15 zero.  The taps of the
+        // next box are loaded before the wait for the slot of this one.
+        const int q = warp & 3, p = q * 32 + lane;
+        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)kGACol;
+        if (q == 0 && lane == 0) {
             mbar_expect_tx(bfull, kGWin * kGBox);
             for (int dy = 0; dy < kGWin; ++dy) tma_load_2d(sB + dy * kGBox, &tb, bfull, 0, dy * kGN);
         }
-        int sl = 0, ph = 0;
-        bool ok = true;
-        for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
-            const Unit U = unit_of(a, u);
-            const int x = U.tx * 128 + p;
-            for (int r = 0; r < U.n + kGWin - 1; ++r) {
-                if (p == 0) s_ok = mbar_wait_idle(aempty + sl, (uint32_t)(ph ^ 1), kWaitTimeoutNs) ? 1 : 0;
-                asm volatile("bar.sync 1, %0;" ::"r"(kGBuild * 32) : "memory");
-                if (!s_ok) {
-                    ok = false;
-                    break;
-                }
-                const int yi = U.y0 + r - kGR;
-                const float* src = a.img + ((size_t)U.v * a.H + (yi >= 0 && yi < a.H ? yi : 0)) * a.W;
-                const bool row_in = yi >= 0 && yi < a.H;
-                uint32_t w[8];
+        int u = blockIdx.x, r = 0, sl = 0;
+        uint32_t ph = 0;
+        Unit U = u < a.units ? unit_of(a, u) : Unit{};
+        bool have = u < a.units, ok = true;
+        float t[kGWin];
+        if (have) load_taps(a, U, 0, U.tx * 128 + p, t);
+        while (have) {
+            uint32_t w[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    uint16_t h[2];
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int dx = 2 * q + e, xx = x + dx - kGR;
-                        const float val = dx < kGWin && row_in && xx >= 0 && xx < a.W ? __ldg(src + xx) : 0.0f;
-                        h[e] = bf16_bits_rn(val);
-                    }
-                    w[q] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
-                }
-                unsigned char* dst = sA + sl * kGBox + (p >> 3) * 256 + (p & 7) * 16;
-                *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-                *reinterpret_cast<uint4*>(dst + 128) = make_uint4(w[4], w[5], w[6], w[7]);
-                fence_proxy_async();   // the tensor cores read what these stores wrote
-                asm volatile("bar.sync 1, %0;" ::"r"(kGBuild * 32) : "memory");
-                if (p == 0) mbar_arrive(afull + sl);
-                if (++sl == kGRing) {
-                    sl = 0;
-                    ph ^= 1;
-                }
+            for (int k = 0; k < 8; ++k) {   // two taps per cvt: tap 2k in the low half
+                const float hi = 2 * k + 1 < kGWin ? t[2 * k + 1] : 0.0f;
+                asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w[k]) : "f"(hi), "f"(t[2 * k]));
             }
+            if (++r == U.n + kGWin - 1) {
+                r = 0;
+                u += gridDim.x;
+                if (u < a.units) U = unit_of(a, u);
+            }
+            const bool next = u < a.units;
+            if (next) load_taps(a, U, r, U.tx * 128 + p, t);
+            uint32_t okw = 1;
+            if (lane == 0) okw = mbar_wait(aempty + sl, ph ^ 1u, kWaitTimeoutNs) ? 1u : 0u;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            tmem_st8(tq + (uint32_t)(sl * kGBoxCols), w);
+            tmem_st_wait();
+            fence_before();   // the MMAs read what these stores wrote
+            __syncwarp();
+            if (lane == 0) mbar_arrive(afull + sl);
+            if (++sl == kGRing) {
+                sl = 0;
+                ph ^= 1u;
+            }
+            have = next;
         }
-        if (!ok && p == 0) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
+        if (!ok && lane == 0) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
     } else if (warp == kGMmaWarp) {
         if (lane == 0) {
             bool ok = mbar_wait(bfull, 0, kWaitTimeoutNs);
             const uint32_t idesc = idesc_bf16_f32(128, kGN);
-            long long base = 0, lt = 0;
+            long long base = 0;   // box number of the unit's first window row
+            int b = 0;            // the epilogue group (accumulator) of the next tile
+            uint32_t accph = 0;   // parity of that accumulator's use
             for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
                 const Unit U = unit_of(a, u);
-                for (int y = 0; y < U.n; ++y, ++lt) {
-                    const int b = (int)(lt % kGGroups);   // the epilogue group that takes this tile
-                    if (!mbar_wait(acce + b, (uint32_t)(((lt / kGGroups) & 1) ^ 1), kWaitTimeoutNs)) {
+                for (int y = 0; y < U.n; ++y) {
+                    if (!mbar_wait(acce + b, accph ^ 1u, kWaitTimeoutNs)) {
                         ok = false;
                         break;
                     }
@@ -196,25 +212,29 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                     // row, then only the newest (the others were waited for by earlier rows)
                     for (int dy = y == 0 ? 0 : kGWin - 1; dy < kGWin; ++dy) {
                         const long long bx = base + y + dy;
-                        if (!mbar_wait(afull + (int)(bx % kGRing), (uint32_t)((bx / kGRing) & 1), kWaitTimeoutNs)) {
+                        if (!mbar_wait(afull + (int)(bx & (kGRing - 1)), (uint32_t)((bx / kGRing) & 1), kWaitTimeoutNs)) {
                             ok = false;
                             break;
                         }
                     }
                     if (!ok) break;
                     fence_after();
-                    int sl = (int)((base + y) % kGRing);
+                    int sl = (int)((base + y) & (kGRing - 1));
                     for (int dy = 0; dy < kGWin; ++dy) {
-                        mma_bf16(tmem + b * kGN, sdesc_none(saddr(sA + sl * kGBox), 128, 256),
-                                 sdesc_sw32(saddr(sB + dy * kGBox)), idesc, dy > 0 ? 1u : 0u);
-                        if (++sl == kGRing) sl = 0;
+                        mma_bf16_ts(tmem + (uint32_t)(b * kGN), tmem + (uint32_t)(kGACol + sl * kGBoxCols),
+                                    sdesc_sw32(saddr(sB + dy * kGBox)), idesc, dy > 0 ? 1u : 0u);
+                        sl = (sl + 1) & (kGRing - 1);
                     }
                     mma_commit(accf + b);
-                    mma_commit(aempty + (int)((base + y) % kGRing));   // window row y: its last use
+                    mma_commit(aempty + (int)((base + y) & (kGRing - 1)));   // window row y: its last use
+                    if (++b == kGGroups) {
+                        b = 0;
+                        accph ^= 1u;
+                    }
                 }
                 if (!ok) break;
                 for (int r = 0; r < kGWin - 1; ++r)   // the unit's last 14 window rows
-                    mma_commit(aempty + (int)((base + U.n + r) % kGRing));
+                    mma_commit(aempty + (int)((base + U.n + r) & (kGRing - 1)));
                 base += U.n + kGWin - 1;
             }
             // wind down: every issued MMA complete (bounded)
@@ -223,7 +243,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
             if (!ok) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
         }
     } else {
-        // group g = warp / 4 takes this CTA's tiles g, g + 4, ... (in the producer's order: unit by
+        // group g = warp / 4 takes this CTA's tiles g, g + 3, ... (in the producer's order: unit by
         // unit, row by row), in tensor-memory buffer g; warp w reads lanes 32 (w % 4) .. + 31: pixel
         // 32 (w % 4) + lane of the tile
         const int grp = warp >> 2, quarter = warp & 3;
@@ -371,38 +391,47 @@ extern "C" int hair_fuse_gabor(hf_ctx* c, const hf_gabor_cfg* cfg, int V, int H,
     if ((long long)V * Hp * Wt >= (1LL << 31) - 1) return hf_set_err(c, HF_ERR_SHAPE, "gabor: more than 2^31 padded pixels");
     const size_t npx = (size_t)V * H * W;
     int rc;
-    // scratch: the bank, staged host images and outputs
-    const size_t bbytes = (size_t)kGWin * kGN * kGTaps * 2;
+    // scratch: staged host images and outputs
     const size_t ibytes = mem_kind == HF_HOST ? npx * 4 : 0, obytes = mem_kind == HF_HOST ? 2 * npx * 4 : 0;
-    auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
-    if ((rc = hf_ensure(c, c->gabor, al(bbytes) + al(ibytes) + al(obytes)))) return rc;
-    char* base = (char*)c->gabor.p;
-    uint16_t* Bd = (uint16_t*)base;
     const float* img = images;
     float *th = theta_out, *cf = conf_out;
     cudaStream_t st = c->stream;
     cudaError_t e = cudaSuccess;
     if (mem_kind == HF_HOST) {
-        float* di = (float*)(base + al(bbytes));
+        auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+        if ((rc = hf_ensure(c, c->gabor, al(ibytes) + obytes))) return rc;
+        float* di = (float*)c->gabor.p;
         e = cudaMemcpyAsync(di, images, npx * 4, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return hf_cuda_err(c, e, "gabor images");
         img = di;
-        th = (float*)(base + al(bbytes) + al(ibytes));
+        th = (float*)((char*)c->gabor.p + al(ibytes));
         cf = th + npx;
     }
-    // the bank as B[dy][filter n][dx]: n < 64 even kernel of orientation n, n >= 64 odd of n - 64
-    std::vector<uint16_t> bank;
-    gabor_bank(*cfg, bank);
-    std::vector<uint16_t> B((size_t)kGWin * kGN * kGTaps, 0);
-    for (int dy = 0; dy < kGWin; ++dy)
-        for (int n = 0; n < kGN; ++n)
-            for (int dx = 0; dx < kGWin; ++dx) {
-                const int k = n % kGOri, ph = n / kGOri;
-                B[((size_t)dy * kGN + n) * kGTaps + dx] = bank[((size_t)(2 * k + ph) * kGWin + dy) * kGWin + dx];
-            }
-    e = cudaMemcpyAsync(Bd, B.data(), bbytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // B is a host vector about to go out of scope
-    if (e != cudaSuccess) return hf_cuda_err(c, e, "gabor bank");
+    // the bank as B[dy][filter n][dx] (n < 64 even kernel of orientation n, n >= 64 odd of n - 64),
+    // built on the host once per (sigma along, sigma across, lambda) and kept on the device
+    const size_t bbytes = (size_t)kGWin * kGN * kGTaps * 2;
+    const float key[3] = {cfg->sigma_along, cfg->sigma_across, cfg->lambda};
+    if (!c->gbank_ok || memcmp(key, c->gbank_key, sizeof key) != 0) {
+        c->gbank_ok = false;
+        if ((rc = hf_ensure(c, c->gbank, bbytes))) return rc;
+        std::vector<uint16_t> bank;
+        gabor_bank(*cfg, bank);
+        std::vector<uint16_t> B((size_t)kGWin * kGN * kGTaps, 0);
+        for (int dy = 0; dy < kGWin; ++dy)
+            for (int n = 0; n < kGN; ++n)
+                for (int dx = 0; dx < kGWin; ++dx) {
+                    const int k = n % kGOri, ph = n / kGOri;
+                    B[((size_t)dy * kGN + n) * kGTaps + dx] = bank[((size_t)(2 * k + ph) * kGWin + dy) * kGWin + dx];
+                }
+        // stream-ordered after any launch still reading the previous bank; B is a host vector
+        // about to go out of scope, so wait for the copy
+        e = cudaMemcpyAsync(c->gbank.p, B.data(), bbytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return hf_cuda_err(c, e, "gabor bank");
+        memcpy(c->gbank_key, key, sizeof key);
+        c->gbank_ok = true;
+    }
+    const uint16_t* Bd = (const uint16_t*)c->gbank.p;
     CUtensorMap tb;
     if ((e = hf_make_tmap_bf16_rows32(&tb, Bd, (long long)kGWin * kGN, 128)) != cudaSuccess)
         return hf_cuda_err(c, e, "gabor tensor map");
@@ -417,7 +446,10 @@ extern "C" int hair_fuse_gabor(hf_ctx* c, const hf_gabor_cfg* cfg, int V, int H,
     nch = (H + chunk - 1) / chunk;
     if (strips * nch >= (1LL << 31)) return hf_set_err(c, HF_ERR_SHAPE, "gabor: too many work units");
     GaborArgs ga{V, H, W, Hp, Wt, tx, chunk, nch, (int)(strips * nch), img, th, cf, (uint32_t*)c->errw.p};
-    const size_t smem = 1024 + (size_t)(kGWin + kGRing) * kGBox + (2 * kGRing + 2 + 2 * kGGroups) * 8 + 16;
+    // the bank and the barriers need about 62 KB; asking for more keeps a second CTA off the SM (each
+    // takes all 512 tensor-memory columns)
+    size_t smem = 1024 + (size_t)kGWin * kGBox + (2 * kGRing + 2 + 2 * kGGroups) * 8 + 16;
+    smem = smem < 160 * 1024 ? 160 * 1024 : smem;
     if ((rc = run_launch(c, "k_gabor", [&] {
              cudaError_t e2 = cudaFuncSetAttribute(k_gabor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
              if (e2 != cudaSuccess) return e2;

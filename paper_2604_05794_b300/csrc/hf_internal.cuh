@@ -61,7 +61,10 @@ struct hf_ctx {
     DevBuf vmap;    // [V][H][W] float2 C (cos theta, sin theta) for FPMVO's patches
     DevBuf fprec;   // FPMVO scratch: [N][K][3] float4 top-view records
     DevBuf phg;     // Parallel Hair Growing scratch: tensors, scans, links, staged host arrays
-    DevBuf gabor;   // Gabor maps scratch: the bf16 window rows J, the bank, staged host arrays
+    DevBuf gabor;   // Gabor maps scratch: staged host images and outputs
+    DevBuf gbank;   // the Gabor bank B[dy][filter][dx] bf16, built for gbank_key (sigma along, across, lambda)
+    float gbank_key[3] = {0.0f, 0.0f, 0.0f};
+    bool gbank_ok = false;
     long long views_gen = 0;   // bumped by every view upload
     long long depth_gen = -1;  // views_gen the FPMVO maps were built for
     uint32_t* errw_host = nullptr;  // pinned read-back slot
