@@ -72,20 +72,11 @@ __device__ __forceinline__ Unit unit_of(const GaborArgs& a, int u) {
     return r;
 }
 
-// packed FP32 pairs (fma .f32x2: each lane rounded like the scalar instruction)
-typedef unsigned long long g_f32x2;
-__device__ __forceinline__ g_f32x2 gpk(float a, float b) {
-    g_f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+// MUFU reciprocal square root without the subnormal path (every argument here is >= 1e-30, normal).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
-}
-__device__ __forceinline__ void gupk(g_f32x2 r, float& a, float& b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ g_f32x2 gfma2(g_f32x2 a, g_f32x2 b, g_f32x2 c) {
-    g_f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
 }
 
 // The 15 taps I(r - 7, x + dx - 7), dx < 15, of pixel column x in padded row r of unit U (0 outside).
@@ -196,37 +187,37 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
         if (!ok && lane == 0) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
     } else if (warp == kGMmaWarp) {
         if (lane == 0) {
+            // The issue sequence of a tile is straight-line code with compile-time operand offsets:
+            // anything more between two MMAs measurably slows their issue.
             bool ok = mbar_wait(bfull, 0, kWaitTimeoutNs);
-            const uint32_t idesc = idesc_bf16_f32(128, kGN);
-            long long base = 0;   // box number of the unit's first window row
+            const uint32_t idesc = idesc_bf16_f32(128, kGN), sBa = saddr(sB), ta = tmem + (uint32_t)kGACol;
+            uint32_t base = 0;    // box number of the unit's first window row (per CTA: below 2^31)
             int b = 0;            // the epilogue group (accumulator) of the next tile
             uint32_t accph = 0;   // parity of that accumulator's use
             for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
                 const Unit U = unit_of(a, u);
                 for (int y = 0; y < U.n; ++y) {
-                    if (!mbar_wait(acce + b, accph ^ 1u, kWaitTimeoutNs)) {
-                        ok = false;
-                        break;
-                    }
-                    // the window rows this output row meets first: all 15 at the unit's first
-                    // row, then only the newest (the others were waited for by earlier rows)
-                    for (int dy = y == 0 ? 0 : kGWin - 1; dy < kGWin; ++dy) {
-                        const long long bx = base + y + dy;
-                        if (!mbar_wait(afull + (int)(bx & (kGRing - 1)), (uint32_t)((bx / kGRing) & 1), kWaitTimeoutNs)) {
-                            ok = false;
-                            break;
-                        }
+                    if (!(ok = mbar_wait(acce + b, accph ^ 1u, kWaitTimeoutNs))) break;
+                    // The window rows this output row meets first: the first 14 at the unit's
+                    // first row (later rows met them earlier), then, before the last MMA only,
+                    // the newest; the 14 MMAs before it give its builders their time.
+                    for (int dy = 0; ok && y == 0 && dy < kGWin - 1; ++dy) {
+                        const uint32_t bx = base + (uint32_t)dy;
+                        ok = mbar_wait(afull + (bx & (kGRing - 1)), (bx / kGRing) & 1u, kWaitTimeoutNs);
                     }
                     if (!ok) break;
                     fence_after();
-                    int sl = (int)((base + y) & (kGRing - 1));
-                    for (int dy = 0; dy < kGWin; ++dy) {
-                        mma_bf16_ts(tmem + (uint32_t)(b * kGN), tmem + (uint32_t)(kGACol + sl * kGBoxCols),
-                                    sdesc_sw32(saddr(sB + dy * kGBox)), idesc, dy > 0 ? 1u : 0u);
-                        sl = (sl + 1) & (kGRing - 1);
-                    }
+                    const uint32_t d = tmem + (uint32_t)(b * kGN), s0 = base + (uint32_t)y;
+#pragma unroll
+                    for (int dy = 0; dy < kGWin - 1; ++dy)
+                        mma_bf16_ts(d, ta + ((s0 + (uint32_t)dy) & (kGRing - 1)) * kGBoxCols,
+                                    sdesc_sw32(sBa + (uint32_t)(dy * kGBox)), idesc, dy > 0 ? 1u : 0u);
+                    const uint32_t bx = s0 + (uint32_t)(kGWin - 1);
+                    if (!(ok = mbar_wait(afull + (bx & (kGRing - 1)), (bx / kGRing) & 1u, kWaitTimeoutNs))) break;
+                    mma_bf16_ts(d, ta + (bx & (kGRing - 1)) * kGBoxCols, sdesc_sw32(sBa + (uint32_t)((kGWin - 1) * kGBox)),
+                                idesc, 1u);
                     mma_commit(accf + b);
-                    mma_commit(aempty + (int)((base + y) & (kGRing - 1)));   // window row y: its last use
+                    mma_commit(aempty + (s0 & (kGRing - 1)));   // window row y: its last use
                     if (++b == kGGroups) {
                         b = 0;
                         accph ^= 1u;
@@ -234,8 +225,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                 }
                 if (!ok) break;
                 for (int r = 0; r < kGWin - 1; ++r)   // the unit's last 14 window rows
-                    mma_commit(aempty + (int)((base + U.n + r) & (kGRing - 1)));
-                base += U.n + kGWin - 1;
+                    mma_commit(aempty + ((base + (uint32_t)(U.n + r)) & (kGRing - 1)));
+                base += (uint32_t)(U.n + kGWin - 1);
             }
             // wind down: every issued MMA complete (bounded)
             mma_commit(done);
@@ -261,41 +252,54 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                 break;
             }
             fence_after();
-            // per orientation pair: F^2 = e^2 + o^2 and F = F^2 rsqrt(F^2) as packed pairs; the
-            // argmax as an integer max of keys (F^2 bits with the low 6 cleared, then 63 - k, so
-            // the first of equal values wins; the cleared bits move F by < 2^-18 F, inside the
-            // oracle's tie margin)
-            uint32_t kmax = 0u;
-            g_f32x2 sacc = gpk(0.0f, 0.0f);
-            const g_f32x2 tiny = gpk(1e-30f, 1e-30f);
-#pragma unroll 1
-            for (int c = 0; c < kGOri; c += 16) {
-                uint32_t ev[16], od[16];
-                tmem_ld16_issue(tl + c, ev);
-                tmem_ld16_issue(tl + kGOri + c, od);
-                tmem_ld_wait(ev);
-                tmem_ld_wait(od);
+            // per orientation: F^2 = e^2 + o^2 (+ 1e-30, so that the reciprocal root stays finite)
+            // and F = F^2 rsqrt(F^2) in scalar FMAs; the argmax as an integer max of keys (F^2 bits
+            // with the low 6 cleared, then 63 - k, so the first of equal values wins; the cleared
+            // bits move F by < 2^-18 F, inside the oracle's tie margin).  Two chains of sums and
+            // maxima; the next 16 orientations load from tensor memory while these reduce, and the
+            // accumulator is released to the MMAs as soon as its last columns are in registers.
+            uint32_t kmax0 = 0u, kmax1 = 0u;
+            float sacc0 = 0.0f, sacc1 = 0.0f;
+            uint32_t ev[2][16], od[2][16];
+            tmem_ld16_issue(tl, ev[0]);
+            tmem_ld16_issue(tl + kGOri, od[0]);
+            tmem_ld_wait(ev[0]);
+            tmem_ld_wait(od[0]);
+            constexpr int kCh = kGOri / 16;
+#pragma unroll
+            for (int ch = 0; ch < kCh; ++ch) {
+                const int cur = ch & 1, c = ch * 16;
+                if (ch + 1 < kCh) {
+                    tmem_ld16_issue(tl + c + 16, ev[cur ^ 1]);
+                    tmem_ld16_issue(tl + kGOri + c + 16, od[cur ^ 1]);
+                }
 #pragma unroll
                 for (int q = 0; q < 16; q += 2) {
-                    const g_f32x2 e = gpk(__uint_as_float(ev[q]), __uint_as_float(ev[q + 1]));
-                    const g_f32x2 o = gpk(__uint_as_float(od[q]), __uint_as_float(od[q + 1]));
-                    const g_f32x2 f2 = gfma2(e, e, gfma2(o, o, tiny));
-                    float f0, f1;
-                    gupk(f2, f0, f1);
-                    sacc = gfma2(f2, gpk(rsqrtf(f0), rsqrtf(f1)), sacc);
+                    const float e0 = __uint_as_float(ev[cur][q]), o0 = __uint_as_float(od[cur][q]);
+                    const float e1 = __uint_as_float(ev[cur][q + 1]), o1 = __uint_as_float(od[cur][q + 1]);
+                    const float f0 = fmaf(e0, e0, fmaf(o0, o0, 1e-30f)), f1 = fmaf(e1, e1, fmaf(o1, o1, 1e-30f));
+                    sacc0 = fmaf(f0, rsqrt_ftz(f0), sacc0);
+                    sacc1 = fmaf(f1, rsqrt_ftz(f1), sacc1);
                     const uint32_t k0 = (__float_as_uint(f0) & 0xFFFFFFC0u) | (uint32_t)(63 - (c + q));
                     const uint32_t k1 = (__float_as_uint(f1) & 0xFFFFFFC0u) | (uint32_t)(62 - (c + q));
-                    kmax = max(kmax, max(k0, k1));
+                    if ((q >> 1) & 1)
+                        kmax1 = max(kmax1, max(k0, k1));
+                    else
+                        kmax0 = max(kmax0, max(k0, k1));
+                }
+                if (ch + 1 < kCh) {
+                    tmem_ld_wait(ev[cur ^ 1]);
+                    tmem_ld_wait(od[cur ^ 1]);
+                    if (ch + 2 == kCh) {   // every column read: later MMAs may overwrite the buffer
+                        fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acce + grp);
+                    }
                 }
             }
-            float s0, s1;
-            gupk(sacc, s0, s1);
-            const float sum = s0 + s1, best2 = __uint_as_float(kmax & 0xFFFFFFC0u);
+            const uint32_t kmax = max(kmax0, kmax1);
+            const float sum = sacc0 + sacc1, best2 = __uint_as_float(kmax & 0xFFFFFFC0u);
             const int kb = 63 - (int)(kmax & 63u);
-            // the buffer is drained: the MMAs of a later tile may overwrite it
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acce + grp);
             const int x = U.tx * 128 + quarter * 32 + lane;
             if (x < a.W) {
                 const float best = sqrtf(best2);

@@ -62,6 +62,18 @@ __device__ __forceinline__ bool mbar_wait_idle(uint64_t* b, uint32_t parity, uin
     return true;
 }
 
+// One lane of a converged warp: true in exactly one lane.  A warp that runs an MMA loop together
+// and issues through the elected lane keeps the loop's operands warp-uniform.
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred = 0;
+    asm volatile("{\n\t.reg .pred p;\n\telect.sync _|p, 0xffffffff;\n\tselp.u32 %0, 1, 0, p;\n}" : "=r"(pred));
+    return pred != 0;
+}
+// mbar_wait by a whole warp, with one verdict for all lanes.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, uint64_t timeout_ns) {
+    return __all_sync(0xffffffffu, mbar_wait(b, parity, timeout_ns)) != 0;
+}
+
 // 2D TMA tile load (x = innermost coordinate in elements, y = row) completing on bar.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
     asm volatile(
