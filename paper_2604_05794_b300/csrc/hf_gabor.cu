@@ -100,23 +100,19 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
     unsigned char* sB = base;                      // 15 boxes: the bank, one window row each
-    uint64_t* afull = reinterpret_cast<uint64_t*>(sB + kGWin * kGBox);
-    uint64_t* aempty = afull + kGRing;
+    uint64_t* aempty = reinterpret_cast<uint64_t*>(sB + kGWin * kGBox);   // [kGRing] MMAs -> builders
     uint64_t* bfull = aempty + kGRing;
-    uint64_t* accf = bfull + 1;         // [kGGroups] MMA -> epilogue group
-    uint64_t* acce = accf + kGGroups;   // [kGGroups] epilogue group (4 warps) -> MMA
-    uint64_t* done = acce + kGGroups;
+    uint64_t* accf = bfull + 1;           // [kGGroups] MMA -> epilogue group
+    uint64_t* tready = accf + kGGroups;   // [kGGroups] epilogue group + builders -> MMA
+    uint64_t* done = tready + kGGroups;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kGRing; ++s) {
-            mbar_init(afull + s, kGBuild);
-            mbar_init(aempty + s, 1);
-        }
+        for (int s = 0; s < kGRing; ++s) mbar_init(aempty + s, 1);
         mbar_init(bfull, 1);
         for (int b = 0; b < kGGroups; ++b) {
             mbar_init(accf + b, 1);
-            mbar_init(acce + b, 4);
+            mbar_init(tready + b, 4 + kGBuild);
         }
         mbar_init(done, 1);
         fence_mbar_init();
@@ -145,7 +141,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
             mbar_expect_tx(bfull, kGWin * kGBox);
             for (int dy = 0; dy < kGWin; ++dy) tma_load_2d(sB + dy * kGBox, &tb, bfull, 0, dy * kGN);
         }
-        int u = blockIdx.x, r = 0, sl = 0;
+        int u = blockIdx.x, r = 0, sl = 0, tb = 0;
         uint32_t ph = 0;
         Unit U = u < a.units ? unit_of(a, u) : Unit{};
         bool have = u < a.units, ok = true;
@@ -158,6 +154,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                 const float hi = 2 * k + 1 < kGWin ? t[2 * k + 1] : 0.0f;
                 asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w[k]) : "f"(hi), "f"(t[2 * k]));
             }
+            const int rb = r;   // the box being written: padded row rb of its unit
             if (++r == U.n + kGWin - 1) {
                 r = 0;
                 u += gridDim.x;
@@ -177,7 +174,10 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
             tmem_st_wait();
             fence_before();   // the MMAs read what these stores wrote
             __syncwarp();
-            if (lane == 0) mbar_arrive(afull + sl);
+            if (rb >= kGWin - 1) {   // the newest window row of the unit's output row rb - 14
+                if (lane == 0) mbar_arrive(tready + tb);
+                tb = tb + 1 == kGGroups ? 0 : tb + 1;
+            }
             if (++sl == kGRing) {
                 sl = 0;
                 ph ^= 1u;
@@ -197,27 +197,19 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
             for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
                 const Unit U = unit_of(a, u);
                 for (int y = 0; y < U.n; ++y) {
-                    if (!(ok = mbar_wait(acce + b, accph ^ 1u, kWaitTimeoutNs))) break;
-                    // The window rows this output row meets first: the first 14 at the unit's
-                    // first row (later rows met them earlier), then, before the last MMA only,
-                    // the newest; the 14 MMAs before it give its builders their time.
-                    for (int dy = 0; ok && y == 0 && dy < kGWin - 1; ++dy) {
-                        const uint32_t bx = base + (uint32_t)dy;
-                        ok = mbar_wait(afull + (bx & (kGRing - 1)), (bx / kGRing) & 1u, kWaitTimeoutNs);
-                    }
-                    if (!ok) break;
+                    // One wait per tile: its accumulator drained by the epilogue group and its
+                    // newest window row (box base + y + 14, hence every older one) written by all
+                    // four builders.  Each extra wait here would stall the tensor pipe.
+                    if (!(ok = mbar_wait(tready + b, accph, kWaitTimeoutNs))) break;
                     fence_after();
                     const uint32_t d = tmem + (uint32_t)(b * kGN), s0 = base + (uint32_t)y;
+                    mma_bf16_ts(d, ta + (s0 & (kGRing - 1)) * kGBoxCols, sdesc_sw32(sBa), idesc, 0u);
+                    mma_commit(aempty + (s0 & (kGRing - 1)));   // window row y: that was its last use
 #pragma unroll
-                    for (int dy = 0; dy < kGWin - 1; ++dy)
+                    for (int dy = 1; dy < kGWin; ++dy)
                         mma_bf16_ts(d, ta + ((s0 + (uint32_t)dy) & (kGRing - 1)) * kGBoxCols,
-                                    sdesc_sw32(sBa + (uint32_t)(dy * kGBox)), idesc, dy > 0 ? 1u : 0u);
-                    const uint32_t bx = s0 + (uint32_t)(kGWin - 1);
-                    if (!(ok = mbar_wait(afull + (bx & (kGRing - 1)), (bx / kGRing) & 1u, kWaitTimeoutNs))) break;
-                    mma_bf16_ts(d, ta + (bx & (kGRing - 1)) * kGBoxCols, sdesc_sw32(sBa + (uint32_t)((kGWin - 1) * kGBox)),
-                                idesc, 1u);
+                                    sdesc_sw32(sBa + (uint32_t)(dy * kGBox)), idesc, 1u);
                     mma_commit(accf + b);
-                    mma_commit(aempty + (s0 & (kGRing - 1)));   // window row y: its last use
                     if (++b == kGGroups) {
                         b = 0;
                         accph ^= 1u;
@@ -246,6 +238,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
             u += gridDim.x;
             if (u < a.units) U = unit_of(a, u);
         }
+        if (lane == 0) mbar_arrive(tready + grp);   // the accumulator starts out free
         for (long long k = 0; u < a.units; ++k) {
             if (!mbar_wait_idle(accf + grp, (uint32_t)(k & 1), kWaitTimeoutNs)) {
                 if (lane == 0) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
@@ -293,7 +286,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                     if (ch + 2 == kCh) {   // every column read: later MMAs may overwrite the buffer
                         fence_before();
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(acce + grp);
+                        if (lane == 0) mbar_arrive(tready + grp);
                     }
                 }
             }
@@ -452,7 +445,7 @@ extern "C" int hair_fuse_gabor(hf_ctx* c, const hf_gabor_cfg* cfg, int V, int H,
     GaborArgs ga{V, H, W, Hp, Wt, tx, chunk, nch, (int)(strips * nch), img, th, cf, (uint32_t*)c->errw.p};
     // the bank and the barriers need about 62 KB; asking for more keeps a second CTA off the SM (each
     // takes all 512 tensor-memory columns)
-    size_t smem = 1024 + (size_t)kGWin * kGBox + (2 * kGRing + 2 + 2 * kGGroups) * 8 + 16;
+    size_t smem = 1024 + (size_t)kGWin * kGBox + (kGRing + 2 + 2 * kGGroups) * 8 + 16;
     smem = smem < 160 * 1024 ? 160 * 1024 : smem;
     if ((rc = run_launch(c, "k_gabor", [&] {
              cudaError_t e2 = cudaFuncSetAttribute(k_gabor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
