@@ -72,6 +72,28 @@ __device__ __forceinline__ Unit unit_of(const GaborArgs& a, int u) {
     return r;
 }
 
+// packed FP32 pairs (fma .f32x2: each lane rounded like the scalar instruction); a pair read from
+// tensor memory already sits in adjacent registers
+typedef unsigned long long g_f32x2;
+__device__ __forceinline__ g_f32x2 gpk(float a, float b) {
+    g_f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void gupk(g_f32x2 r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ g_f32x2 gfma2(g_f32x2 a, g_f32x2 b, g_f32x2 c) {
+    g_f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// three-input maximum (one instruction)
+__device__ __forceinline__ float gmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
 // MUFU reciprocal square root without the subnormal path (every argument here is >= 1e-30, normal).
 __device__ __forceinline__ float rsqrt_ftz(float x) {
     float r;
@@ -246,13 +268,16 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
             }
             fence_after();
             // per orientation: F^2 = e^2 + o^2 (+ 1e-30, so that the reciprocal root stays finite)
-            // and F = F^2 rsqrt(F^2) in scalar FMAs; the argmax as an integer max of keys (F^2 bits
-            // with the low 6 cleared, then 63 - k, so the first of equal values wins; the cleared
-            // bits move F by < 2^-18 F, inside the oracle's tie margin).  Two chains of sums and
-            // maxima; the next 16 orientations load from tensor memory while these reduce, and the
-            // accumulator is released to the MMAs as soon as its last columns are in registers.
-            uint32_t kmax0 = 0u, kmax1 = 0u;
+            // in packed pairs and F = F^2 rsqrt(F^2) in scalar FMAs; the argmax as a maximum of
+            // keys: F^2 bits with the low 6 cleared, then 63 - k (the first of equal values wins;
+            // the cleared bits move F by < 2^-18 F, inside the oracle's tie margin).  F^2 >= 1e-30
+            // is a positive normal float, and so is its key, so keys order as floats: one
+            // three-input max per pair.  Two chains of sums and maxima; the next 16 orientations
+            // load from tensor memory while these reduce, and the accumulator is released to the
+            // MMAs as soon as its last columns are in registers.
+            float kmax0 = 0.0f, kmax1 = 0.0f;
             float sacc0 = 0.0f, sacc1 = 0.0f;
+            const g_f32x2 tiny = gpk(1e-30f, 1e-30f);
             uint32_t ev[2][16], od[2][16];
             tmem_ld16_issue(tl, ev[0]);
             tmem_ld16_issue(tl + kGOri, od[0]);
@@ -268,17 +293,18 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                 }
 #pragma unroll
                 for (int q = 0; q < 16; q += 2) {
-                    const float e0 = __uint_as_float(ev[cur][q]), o0 = __uint_as_float(od[cur][q]);
-                    const float e1 = __uint_as_float(ev[cur][q + 1]), o1 = __uint_as_float(od[cur][q + 1]);
-                    const float f0 = fmaf(e0, e0, fmaf(o0, o0, 1e-30f)), f1 = fmaf(e1, e1, fmaf(o1, o1, 1e-30f));
+                    const g_f32x2 e = gpk(__uint_as_float(ev[cur][q]), __uint_as_float(ev[cur][q + 1]));
+                    const g_f32x2 o = gpk(__uint_as_float(od[cur][q]), __uint_as_float(od[cur][q + 1]));
+                    float f0, f1;
+                    gupk(gfma2(e, e, gfma2(o, o, tiny)), f0, f1);
                     sacc0 = fmaf(f0, rsqrt_ftz(f0), sacc0);
                     sacc1 = fmaf(f1, rsqrt_ftz(f1), sacc1);
-                    const uint32_t k0 = (__float_as_uint(f0) & 0xFFFFFFC0u) | (uint32_t)(63 - (c + q));
-                    const uint32_t k1 = (__float_as_uint(f1) & 0xFFFFFFC0u) | (uint32_t)(62 - (c + q));
+                    const float k0 = __uint_as_float((__float_as_uint(f0) & 0xFFFFFFC0u) | (uint32_t)(63 - (c + q)));
+                    const float k1 = __uint_as_float((__float_as_uint(f1) & 0xFFFFFFC0u) | (uint32_t)(62 - (c + q)));
                     if ((q >> 1) & 1)
-                        kmax1 = max(kmax1, max(k0, k1));
+                        kmax1 = gmax3(kmax1, k0, k1);
                     else
-                        kmax0 = max(kmax0, max(k0, k1));
+                        kmax0 = gmax3(kmax0, k0, k1);
                 }
                 if (ch + 1 < kCh) {
                     tmem_ld_wait(ev[cur ^ 1]);
@@ -290,7 +316,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                     }
                 }
             }
-            const uint32_t kmax = max(kmax0, kmax1);
+            const uint32_t kmax = __float_as_uint(fmaxf(kmax0, kmax1));
             const float sum = sacc0 + sacc1, best2 = __uint_as_float(kmax & 0xFFFFFFC0u);
             const int kb = 63 - (int)(kmax & 63u);
             const int x = U.tx * 128 + quarter * 32 + lane;
