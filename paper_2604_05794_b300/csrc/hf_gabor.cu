@@ -208,23 +208,25 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
         }
         if (!ok && lane == 0) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
     } else if (warp == kGMmaWarp) {
-        if (lane == 0) {
-            // The issue sequence of a tile is straight-line code with compile-time operand offsets:
-            // anything more between two MMAs measurably slows their issue.
-            bool ok = mbar_wait(bfull, 0, kWaitTimeoutNs);
-            const uint32_t idesc = idesc_bf16_f32(128, kGN), sBa = saddr(sB), ta = tmem + (uint32_t)kGACol;
-            uint32_t base = 0;    // box number of the unit's first window row (per CTA: below 2^31)
-            int b = 0;            // the epilogue group (accumulator) of the next tile
-            uint32_t accph = 0;   // parity of that accumulator's use
-            for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
-                const Unit U = unit_of(a, u);
-                for (int y = 0; y < U.n; ++y) {
-                    // One wait per tile: its accumulator drained by the epilogue group and its
-                    // newest window row (box base + y + 14, hence every older one) written by all
-                    // four builders.  Each extra wait here would stall the tensor pipe.
-                    if (!(ok = mbar_wait(tready + b, accph, kWaitTimeoutNs))) break;
-                    fence_after();
-                    const uint32_t d = tmem + (uint32_t)(b * kGN), s0 = base + (uint32_t)y;
+        // The whole warp runs the loop (its values stay warp-uniform) and the elected lane issues:
+        // a loop run by one lane alone issues several times slower while the epilogue warps
+        // compute.  The issue sequence of a tile is straight-line code with compile-time operand
+        // offsets and one barrier wait; each extra wait between MMAs stalls the tensor pipe.
+        bool ok = __shfl_sync(0xffffffffu, mbar_wait(bfull, 0, kWaitTimeoutNs) ? 1 : 0, 0) != 0;
+        const uint32_t idesc = idesc_bf16_f32(128, kGN), sBa = saddr(sB), ta = tmem + (uint32_t)kGACol;
+        uint32_t base = 0;    // box number of the unit's first window row (per CTA: below 2^31)
+        int b = 0;            // the epilogue group (accumulator) of the next tile
+        uint32_t accph = 0;   // parity of that accumulator's use
+        for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
+            const Unit U = unit_of(a, u);
+            for (int y = 0; y < U.n; ++y) {
+                // one wait per tile: its accumulator drained by the epilogue group and its newest
+                // window row (box base + y + 14, hence every older one) written by all builders
+                ok = __shfl_sync(0xffffffffu, mbar_wait(tready + b, accph, kWaitTimeoutNs) ? 1 : 0, 0) != 0;
+                if (!ok) break;
+                fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * kGN), s0 = base + (uint32_t)y;
+                if (elect_one()) {
                     mma_bf16_ts(d, ta + (s0 & (kGRing - 1)) * kGBoxCols, sdesc_sw32(sBa), idesc, 0u);
                     mma_commit(aempty + (s0 & (kGRing - 1)));   // window row y: that was its last use
 #pragma unroll
@@ -232,21 +234,25 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gabor(const __grid_constant__ 
                         mma_bf16_ts(d, ta + ((s0 + (uint32_t)dy) & (kGRing - 1)) * kGBoxCols,
                                     sdesc_sw32(sBa + (uint32_t)(dy * kGBox)), idesc, 1u);
                     mma_commit(accf + b);
-                    if (++b == kGGroups) {
-                        b = 0;
-                        accph ^= 1u;
-                    }
                 }
-                if (!ok) break;
+                __syncwarp();
+                if (++b == kGGroups) {
+                    b = 0;
+                    accph ^= 1u;
+                }
+            }
+            if (!ok) break;
+            if (elect_one())
                 for (int r = 0; r < kGWin - 1; ++r)   // the unit's last 14 window rows
                     mma_commit(aempty + ((base + (uint32_t)(U.n + r)) & (kGRing - 1)));
-                base += (uint32_t)(U.n + kGWin - 1);
-            }
-            // wind down: every issued MMA complete (bounded)
-            mma_commit(done);
-            mbar_wait(done, 0, kWaitTimeoutNs);
-            if (!ok) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
+            __syncwarp();
+            base += (uint32_t)(U.n + kGWin - 1);
         }
+        // wind down: every issued MMA complete (bounded)
+        if (elect_one()) mma_commit(done);
+        __syncwarp();
+        mbar_wait(done, 0, kWaitTimeoutNs);
+        if (!ok && lane == 0) atomicOr(a.errw, HF_DEV_ERR_TIMEOUT);
     } else {
         // group g = warp / 4 takes this CTA's tiles g, g + 3, ... (in the producer's order: unit by
         // unit, row by row), in tensor-memory buffer g; warp w reads lanes 32 (w % 4) .. + 31: pixel
