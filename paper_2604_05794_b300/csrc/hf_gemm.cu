@@ -328,64 +328,77 @@ __global__ void __launch_bounds__(kPThreads, 1) k_gemm_persist(const __grid_cons
     const uint32_t tmem = *tslot;
 
     if (warp == 16) {
-        if (lane == 0) {
-            bool ok = true;
-            const uint32_t idesc = idesc_bf16_f32(128, 256);
-            const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-            const long long total = (long long)my_tiles * nk;
-            long long g_load = 0, g_use = 0;
-            // the weights, once
+        // The whole warp runs the producer / MMA loop (its values stay warp-uniform); the elected
+        // lane issues the copies and the MMAs, and lane 0's verdict on each wait holds for all.  A
+        // loop run by one lane alone issues several times slower while the epilogue warps compute.
+        auto agree = [](bool x) { return __shfl_sync(0xffffffffu, x ? 1 : 0, 0) != 0; };
+        bool ok = true;
+        const uint32_t idesc = idesc_bf16_f32(128, 256);
+        const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        const long long total = (long long)my_tiles * nk;
+        long long g_load = 0, g_use = 0;
+        // the weights, once
+        if (elect_one()) {
             mbar_expect_tx(bfull, nk * kPBChunk);
             for (int c = 0; c < nk; ++c) tma_load_2d(sB + c * kPBChunk, &tb, bfull, c * 64, 0);
-            auto top_up = [&]() -> bool {   // keep up to kPStages A chunks in flight
-                while (g_load < total && g_load < g_use + kPStages) {
-                    const int s = (int)(g_load % kPStages);
-                    if (!mbar_wait(aempty + s, (uint32_t)(((g_load / kPStages) & 1) ^ 1), kWaitTimeoutNs)) return false;
-                    const int t = blockIdx.x + (int)(g_load / nk) * gridDim.x, c = (int)(g_load % nk);
+        }
+        __syncwarp();
+        auto top_up = [&]() -> bool {   // keep up to kPStages A chunks in flight
+            while (g_load < total && g_load < g_use + kPStages) {
+                const int s = (int)(g_load % kPStages);
+                if (!agree(mbar_wait(aempty + s, (uint32_t)(((g_load / kPStages) & 1) ^ 1), kWaitTimeoutNs))) return false;
+                const int t = blockIdx.x + (int)(g_load / nk) * gridDim.x, c = (int)(g_load % nk);
+                if (elect_one()) {
                     mbar_expect_tx(afull + s, kATileBytes);
                     tma_load_2d(sA + s * kATileBytes, &ta, afull + s, c * 64, t * 128);
-                    ++g_load;
                 }
-                return true;
-            };
-            ok = top_up() && mbar_wait(bfull, 0, kWaitTimeoutNs);
-            int lt = 0;
-            for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x, ++lt) {
-                const int b = lt & 1;
-                if (!mbar_wait(acce + b, (uint32_t)(((lt >> 1) & 1) ^ 1), kWaitTimeoutNs)) {
+                __syncwarp();
+                ++g_load;
+            }
+            return true;
+        };
+        ok = top_up() && agree(mbar_wait(bfull, 0, kWaitTimeoutNs));
+        int lt = 0;
+        for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x, ++lt) {
+            const int b = lt & 1;
+            if (!agree(mbar_wait(acce + b, (uint32_t)(((lt >> 1) & 1) ^ 1), kWaitTimeoutNs))) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            for (int c = 0; c < nk; ++c) {
+                if (!top_up()) {
+                    ok = false;
+                    break;
+                }
+                const int s = (int)(g_use % kPStages);
+                if (!agree(mbar_wait(afull + s, (uint32_t)((g_use / kPStages) & 1), kWaitTimeoutNs))) {
                     ok = false;
                     break;
                 }
                 fence_after();
-                for (int c = 0; c < nk; ++c) {
-                    if (!top_up()) {
-                        ok = false;
-                        break;
-                    }
-                    const int s = (int)(g_use % kPStages);
-                    if (!mbar_wait(afull + s, (uint32_t)((g_use / kPStages) & 1), kWaitTimeoutNs)) {
-                        ok = false;
-                        break;
-                    }
-                    fence_after();
-                    const uint32_t a0 = saddr(sA + s * kATileBytes), b0 = saddr(sB + c * kPBChunk);
+                const uint32_t a0 = saddr(sA + s * kATileBytes), b0 = saddr(sB + c * kPBChunk);
+                if (elect_one()) {
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                         mma_bf16(tmem + b * 256, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
                                  (c > 0 || kk > 0) ? 1u : 0u);
                     mma_commit(aempty + s);
-                    ++g_use;
                 }
-                if (!ok) break;
-                mma_commit(accf + b);
+                __syncwarp();
+                ++g_use;
             }
-            // wind down: every issued MMA complete, every issued copy landed (bounded)
-            mma_commit(done);
-            mbar_wait(done, 0, kWaitTimeoutNs);
-            for (long long q = g_use; q < g_load; ++q)
-                mbar_wait(afull + (int)(q % kPStages), (uint32_t)((q / kPStages) & 1), kWaitTimeoutNs);
-            if (!ok) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
+            if (!ok) break;
+            if (elect_one()) mma_commit(accf + b);
+            __syncwarp();
         }
+        // wind down: every issued MMA complete, every issued copy landed (bounded)
+        if (elect_one()) mma_commit(done);
+        __syncwarp();
+        mbar_wait(done, 0, kWaitTimeoutNs);
+        for (long long q = g_use; q < g_load; ++q)
+            mbar_wait(afull + (int)(q % kPStages), (uint32_t)((q / kPStages) & 1), kWaitTimeoutNs);
+        if (!ok && lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
     } else {
         const int grp = warp >> 3, quarter = warp & 3, half = (warp >> 2) & 1;
         const int lrow = quarter * 32 + lane;
