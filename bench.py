@@ -1196,6 +1196,10 @@ def run_fpmvo(args):
 # ---------------------------------------------------------------------------- Gabor workload
 GABOR_FLOP_PER_PIXEL = 2 * 128 * 15 * 16     # the MMAs as issued: 128 filters x 15 window rows x 16 taps
 GABOR_USEFUL_FLOP_PER_PIXEL = 2 * 128 * 225  # the 15 x 15 window
+# DRAM bytes per pixel of k_gabor (dram__bytes_read.sum + dram__bytes_write.sum of one launch on 4 views,
+# 46.6 MB / 8.29 M pixels): the image read once (4 bytes), the outputs partly still in L2 at the end
+# of so small a launch; scaled to a full launch by the pixel count
+GABOR_DRAM_PER_PIXEL = (33.278208e6 + 13.347072e6) / (4 * 1920 * 1080)
 
 
 def gabor_images(views=64, seed=2):
@@ -1254,15 +1258,18 @@ def run_gabor(args):
     value = reduce_over_ranks(npx, pg, dev, "sum") * args.steps / (ms / 1e3) / 1e6
     n_, t_ = kt["k_gabor"]
     sec = t_ / n_ / 1e3
-    ach = npx * GABOR_FLOP_PER_PIXEL / sec / 1e12
+    ach = npx * GABOR_USEFUL_FLOP_PER_PIXEL / sec / 1e12   # algorithmic: the 15 x 15 window
+    issued = npx * GABOR_FLOP_PER_PIXEL / sec / 1e12
     peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1800.0
     tot = sum(v[1] for v in kt.values())
     roofline = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": "k_gabor",
+                "traffic": GABOR_DRAM_PER_PIXEL * npx, "traffic_source": "ncu on 4 views, scaled by pixels",
+                "kernel": "k_gabor",
                 "peak_source": "of measured: MEASURED_PEAKS.json bf16_tflops (burst cuBLAS bf16)",
-                "work": f"{GABOR_FLOP_PER_PIXEL} FLOP per pixel as issued (128 filters x 15 rows x 16 taps; "
-                        f"{GABOR_USEFUL_FLOP_PER_PIXEL} in the 15x15 window) x {npx} pixels",
+                "work": f"{GABOR_USEFUL_FLOP_PER_PIXEL} FLOP per pixel (128 filters x the 15x15 window) x {npx} pixels; "
+                        f"the MMAs issue {GABOR_FLOP_PER_PIXEL} per pixel (16 taps per row, the 16th zero)",
+                "issued_tflops": issued,
                 "share": t_ / tot}
     line = {"metric": "Gabor orientation/confidence maps, megapixels/s", "value": value, "unit": "Mpx/s",
             "n_gpus": world, "steps": args.steps, "warmup": Wm, "ms_per_step": ms / args.steps,
@@ -1300,7 +1307,7 @@ def run_gabor(args):
                        "steps": n_e2e, "path": "hair_fuse_gabor with HF_HOST pinned buffers"}
     if rank == 0 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
-        n_s = 3000
+        n_s = 300000   # about 10 s of the single-threaded oracle
         oracle.gabor_pixels(im[0], np.linspace(0, H * W - 1, n_s).astype(np.int64))
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": n_s / dt / 1e6, "unit": "Mpx/s", "cores": 1, "kind": "oracle",

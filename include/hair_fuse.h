@@ -257,7 +257,9 @@ typedef struct {
  * memory).  HF_ERR_INVALID_ARG for a configuration other than the above. */
 int hair_fuse_gabor_bank(const hf_gabor_cfg* cfg, float* out);
 /* Maps of V images (V x H x W f32) into theta_out and conf_out (V x H x W f32), all of kind
- * mem_kind (caller-owned); asynchronous for HF_DEVICE.  The maps can be passed to
+ * mem_kind (caller-owned); asynchronous for HF_DEVICE (the first call with a new sigma / lambda
+ * builds the bank on the host and waits for its upload; the context keeps it).  Device scratch:
+ * none for HF_DEVICE, the staged images and maps for HF_HOST.  The maps can be passed to
  * hair_fuse_upload_views.  Errors: HF_ERR_INVALID_ARG (configuration, sizes, null arrays),
  * HF_ERR_SHAPE (more than 2^31 padded pixels), HF_ERR_TIMEOUT (a bounded device wait expired). */
 int hair_fuse_gabor(hf_ctx* ctx, const hf_gabor_cfg* cfg, int V, int H, int W, const float* images, float* theta_out,
