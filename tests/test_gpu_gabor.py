@@ -57,6 +57,18 @@ def test_ragged_sizes_and_random_images():
             compare(im, th, cf, v, np.arange(H * W), min_unique=0.0 if W == 1 else 0.3)
 
 
+
+def test_unit_boundaries_and_short_units():
+    """One-row images (a CTA's tiles fewer than its accumulators), hundreds of two-row images (a CTA
+    walks many units, the window-row ring and the per-tile barrier cross every unit boundary), and a
+    tall single strip cut into runs of rows (several units per strip)."""
+    for V, H, W, sample in ((3, 1, 7, 0), (300, 2, 130, 0), (1, 1080, 128, 6000)):
+        im = RNG.random((V, H, W)).astype(np.float32)
+        th, cf = run(im)
+        for v in sorted({0, V // 2, V - 1}):
+            idx = np.arange(H * W) if not sample else np.linspace(0, H * W - 1, sample).astype(np.int64)
+            compare(im, th, cf, v, idx, min_unique=0.3)
+
 def test_full_view_sampled_and_host_path():
     sc = scenegen.make_scene("full", seed=2, knn=False)
     im = scenegen.strand_images({"conf": sc["conf"][:2]}, seed=2)
