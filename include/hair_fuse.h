@@ -27,6 +27,11 @@
  *    mem_kind HF_DEVICE: pointers are device memory of the current device; the work is queued on
  *    the context's stream and the call returns without waiting.  Device inputs must stay valid
  *    until the stream has consumed them; outputs are valid once the stream reaches that point.
+ *    mem_kind HF_HOST_ASYNC (hair_fuse_upload_views and hair_fuse_upload_points only): pinned host
+ *    memory copied on the context's stream without waiting, so that a caller can overlap the
+ *    upload of one scene set with the work of another on a second stream.  The caller keeps the
+ *    buffers unchanged until the stream has consumed them (hair_fuse_sync(), or any later
+ *    synchronising call on the context).  Pageable memory makes the copy synchronous (CUDA's rule).
  *  - Uploads copy into buffers the context owns; the caller keeps ownership of its own buffers.
  *  - Errors found on the device (a bad hypothesis, a timed-out wait) are latched in the context
  *    and returned by the next synchronising call (an HF_HOST call or hair_fuse_sync()).
@@ -53,6 +58,7 @@ extern "C" {
 /* memory kinds */
 #define HF_HOST 0
 #define HF_DEVICE 1
+#define HF_HOST_ASYNC 2
 
 /* confidence map element types */
 #define HF_F32 0

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhairfuse.so")
 
 HF_OK, HF_ERR_INVALID_ARG, HF_ERR_NOT_UPLOADED, HF_ERR_OOM, HF_ERR_CUDA, HF_ERR_TIMEOUT, HF_ERR_SHAPE = 0, -1, -2, -3, -4, -5, -6
-HF_HOST, HF_DEVICE = 0, 1
+HF_HOST, HF_DEVICE, HF_HOST_ASYNC = 0, 1, 2
 HF_F32, HF_F16 = 0, 1
 HF_STATUS_OK, HF_STATUS_NO_VIEWS, HF_STATUS_BAD_INPUT, HF_STATUS_FELL_BACK = 0, 1, 2, 3
 
@@ -284,14 +284,20 @@ class HairFuse:
     def set_stream(self, stream):
         self._c(hair_fuse_set_stream(self.h, stream))
 
-    def upload_views(self, cams, angle, conf):
-        """cams (V,16) f32, angle (V,H,W) f32, conf (V,H,W) f32 or f16."""
+    def upload_views(self, cams, angle, conf, asynchronous=False):
+        """cams (V,16) f32, angle (V,H,W) f32, conf (V,H,W) f32 or f16.  asynchronous=True (pinned
+        torch CPU tensors only, HF_HOST_ASYNC): the copies are queued on the context's stream and
+        the call returns at once; keep the tensors unchanged until the stream has consumed them."""
         V, Hh, W = angle.shape
         cdt = HF_F16 if str(conf.dtype).endswith("float16") else HF_F32
         pc, k1, a = _ptr_kind(cams)
         pa, k2, b = _ptr_kind(angle)
         pf, k3, c = _ptr_kind(conf)
         kind = _same_kind(k1, k2, k3)
+        if asynchronous:
+            if kind != HF_HOST or not all(getattr(x, "is_pinned", lambda: False)() for x in (cams, angle, conf)):
+                raise ValueError("asynchronous uploads take pinned torch CPU tensors")
+            kind = HF_HOST_ASYNC
         self._c(hair_fuse_upload_views(self.h, V, W, Hh, pc, pa, pf, cdt, kind))
         self.V = V
         self._keep = [a, b, c]

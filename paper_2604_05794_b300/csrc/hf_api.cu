@@ -13,10 +13,17 @@ namespace {
 thread_local std::string g_create_err;
 
 
-cudaMemcpyKind kind_in(int mem_kind) { return mem_kind == HF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+cudaMemcpyKind kind_in(int mem_kind) { return mem_kind == HF_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 
 int check_kind(hf_ctx* c, int mem_kind) {
     if (mem_kind != HF_HOST && mem_kind != HF_DEVICE) return hf_set_err(c, HF_ERR_INVALID_ARG, "mem_kind must be HF_HOST or HF_DEVICE");
+    return HF_OK;
+}
+
+// Uploads also take HF_HOST_ASYNC: pinned host memory copied without waiting.
+int check_upload_kind(hf_ctx* c, int mem_kind) {
+    if (mem_kind != HF_HOST && mem_kind != HF_DEVICE && mem_kind != HF_HOST_ASYNC)
+        return hf_set_err(c, HF_ERR_INVALID_ARG, "mem_kind must be HF_HOST, HF_DEVICE or HF_HOST_ASYNC");
     return HF_OK;
 }
 
@@ -144,7 +151,7 @@ int hair_fuse_upload_views(hf_ctx* c, int V, int width, int height, const float*
                            const void* conf, int conf_dtype, int mem_kind) {
     if (!c) return HF_ERR_INVALID_ARG;
     int rc;
-    if ((rc = check_kind(c, mem_kind))) return rc;
+    if ((rc = check_upload_kind(c, mem_kind))) return rc;
     if (V < 1 || width < 1 || height < 1) return hf_set_err(c, HF_ERR_INVALID_ARG, "V, width, height must be >= 1");
     if (!cams || !angle || !conf) return hf_set_err(c, HF_ERR_INVALID_ARG, "null view pointer");
     if (conf_dtype != HF_F32 && conf_dtype != HF_F16) return hf_set_err(c, HF_ERR_INVALID_ARG, "conf_dtype must be HF_F32 or HF_F16");
@@ -177,7 +184,7 @@ int hair_fuse_upload_views(hf_ctx* c, int V, int width, int height, const float*
 int hair_fuse_upload_points(hf_ctx* c, int N, const float* xyz, const int32_t* nbr, int mem_kind) {
     if (!c) return HF_ERR_INVALID_ARG;
     int rc;
-    if ((rc = check_kind(c, mem_kind))) return rc;
+    if ((rc = check_upload_kind(c, mem_kind))) return rc;
     const int k = c->cfg.k;
     if (N < 1) return hf_set_err(c, HF_ERR_INVALID_ARG, "N must be >= 1");
     if (k >= N) return hf_set_err(c, HF_ERR_INVALID_ARG, "k=%d must be < N=%d", k, N);

@@ -169,3 +169,38 @@ def test_batch_rejects_bad_arguments(scenes):
             b.set_outputs(3, *_outs(sc["N"]))
     empty.close()
     f.close()
+
+
+def test_asynchronous_uploads_two_streams():
+    """HF_HOST_ASYNC: pinned uploads queued without waiting, two contexts on two streams taking
+    turns (the serving pipeline), give the same bits as the synchronous upload; pageable arrays
+    are refused."""
+    import torch
+
+    import paper_2604_05794_b300 as hf
+    sc = scenegen.make_scene("mid", seed=21, n_strands=60, V=12, width=512, height=512, f=600.0)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h = [pin(sc[x]) for x in ("cams", "angle", "conf", "points", "nbr")]
+    N = sc["N"]
+    ref = np.empty((N, 3), np.float32)
+    with hf.HairFuse(32, sc["k"], 4) as f:
+        f.upload_views(sc["cams"], sc["angle"], sc["conf"])
+        f.upload_points(sc["points"], sc["nbr"])
+        f.fuse(ref)
+        with pytest.raises(ValueError):
+            f.upload_views(sc["cams"], sc["angle"], sc["conf"], asynchronous=True)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ctxs = [hf.HairFuse(32, sc["k"], 4, stream=s.cuda_stream) for s in streams]
+    outs = [torch.empty((N, 3), device="cuda") for _ in streams]
+    try:
+        for rep in range(3):
+            for f, o in zip(ctxs, outs):
+                f.upload_views(h[0], h[1], h[2], asynchronous=True)
+                f.upload_points(h[3], h[4])
+                f.fuse(o)
+        torch.cuda.synchronize()
+        for o in outs:
+            assert np.array_equal(o.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+    finally:
+        for f in ctxs:
+            f.close()
