@@ -27,7 +27,7 @@
  *    mem_kind HF_DEVICE: pointers are device memory of the current device; the work is queued on
  *    the context's stream and the call returns without waiting.  Device inputs must stay valid
  *    until the stream has consumed them; outputs are valid once the stream reaches that point.
- *    mem_kind HF_HOST_ASYNC (hair_fuse_upload_views and hair_fuse_upload_points only): pinned host
+ *    mem_kind HF_HOST_ASYNC (hair_fuse_upload_views, hair_fuse_upload_points, hair_fuse_gabor): pinned host
  *    memory copied on the context's stream without waiting, so that a caller can overlap the
  *    upload of one scene set with the work of another on a second stream.  The caller keeps the
  *    buffers unchanged until the stream has consumed them (hair_fuse_sync(), or any later
@@ -265,7 +265,9 @@ int hair_fuse_gabor_bank(const hf_gabor_cfg* cfg, float* out);
 /* Maps of V images (V x H x W f32) into theta_out and conf_out (V x H x W f32), all of kind
  * mem_kind (caller-owned); asynchronous for HF_DEVICE (the first call with a new sigma / lambda
  * builds the bank on the host and waits for its upload; the context keeps it).  Device scratch:
- * none for HF_DEVICE, the staged images and maps for HF_HOST.  The maps can be passed to
+ * none for HF_DEVICE, the staged images and maps for HF_HOST and HF_HOST_ASYNC (with HF_HOST_ASYNC
+ * the images are copied in, the maps computed and copied out on the context's stream without
+ * waiting; a device error is reported by the next synchronising call).  The maps can be passed to
  * hair_fuse_upload_views.  Errors: HF_ERR_INVALID_ARG (configuration, sizes, null arrays),
  * HF_ERR_SHAPE (more than 2^31 padded pixels), HF_ERR_TIMEOUT (a bounded device wait expired). */
 int hair_fuse_gabor(hf_ctx* ctx, const hf_gabor_cfg* cfg, int V, int H, int W, const float* images, float* theta_out,

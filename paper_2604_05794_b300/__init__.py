@@ -378,9 +378,11 @@ class HairFuse:
             o["label"] = o["label"][:S + K]
         return o
 
-    def gabor(self, images, theta_out=None, conf_out=None, **kw):
+    def gabor(self, images, theta_out=None, conf_out=None, asynchronous=False, **kw):
         """Orientation and confidence maps (hair_fuse_gabor) of images (V, H, W) f32, numpy or CUDA tensor;
-        outputs allocated like the input unless given."""
+        outputs allocated like the input unless given.  asynchronous=True (pinned torch CPU tensors,
+        HF_HOST_ASYNC): copies and kernel are queued on the context's stream and the call returns at
+        once; keep the buffers until the stream has consumed them."""
         V, H, W = (int(x) for x in images.shape)
         if theta_out is None:
             if isinstance(images, np.ndarray):
@@ -391,6 +393,10 @@ class HairFuse:
                 conf_out = torch.empty((V, H, W), dtype=torch.float32, device=images.device)
         ptrs = [_ptr_kind(x) for x in (images, theta_out, conf_out)]
         kind = _same_kind(*[q[1] for q in ptrs])
+        if asynchronous:
+            if kind != HF_HOST or not all(getattr(x, "is_pinned", lambda: False)() for x in (images, theta_out, conf_out)):
+                raise ValueError("asynchronous Gabor maps take pinned torch CPU tensors")
+            kind = HF_HOST_ASYNC
         self._c(hair_fuse_gabor(self.h, ctypes.byref(gabor_cfg(**kw)), V, H, W, *[q[0] for q in ptrs], kind))
         return theta_out, conf_out
 

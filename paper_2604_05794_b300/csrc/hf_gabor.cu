@@ -413,7 +413,9 @@ extern "C" int hair_fuse_gabor(hf_ctx* c, const hf_gabor_cfg* cfg, int V, int H,
     if (!c) return HF_ERR_INVALID_ARG;
     if (!cfg_ok(cfg))
         return hf_set_err(c, HF_ERR_INVALID_ARG, "gabor: n_theta 64, radius 7, positive finite sigmas and lambda");
-    if (mem_kind != HF_HOST && mem_kind != HF_DEVICE) return hf_set_err(c, HF_ERR_INVALID_ARG, "bad mem_kind");
+    if (mem_kind != HF_HOST && mem_kind != HF_DEVICE && mem_kind != HF_HOST_ASYNC)
+        return hf_set_err(c, HF_ERR_INVALID_ARG, "bad mem_kind");
+    const bool staged = mem_kind != HF_DEVICE;   // host images and maps go through device staging
     if (V < 1 || H < 1 || W < 1 || !images || !theta_out || !conf_out)
         return hf_set_err(c, HF_ERR_INVALID_ARG, "gabor: V, H, W >= 1 and non-null arrays");
     const int Hp = H + 2 * kGR, tx = (W + 127) / 128, Wt = tx * 128;
@@ -421,12 +423,12 @@ extern "C" int hair_fuse_gabor(hf_ctx* c, const hf_gabor_cfg* cfg, int V, int H,
     const size_t npx = (size_t)V * H * W;
     int rc;
     // scratch: staged host images and outputs
-    const size_t ibytes = mem_kind == HF_HOST ? npx * 4 : 0, obytes = mem_kind == HF_HOST ? 2 * npx * 4 : 0;
+    const size_t ibytes = staged ? npx * 4 : 0, obytes = staged ? 2 * npx * 4 : 0;
     const float* img = images;
     float *th = theta_out, *cf = conf_out;
     cudaStream_t st = c->stream;
     cudaError_t e = cudaSuccess;
-    if (mem_kind == HF_HOST) {
+    if (staged) {
         auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
         if ((rc = hf_ensure(c, c->gabor, al(ibytes) + obytes))) return rc;
         float* di = (float*)c->gabor.p;
@@ -487,11 +489,11 @@ extern "C" int hair_fuse_gabor(hf_ctx* c, const hf_gabor_cfg* cfg, int V, int H,
              return cudaGetLastError();
          })))
         return rc;
-    if (mem_kind == HF_HOST) {
+    if (staged) {
         e = cudaMemcpyAsync(theta_out, th, npx * 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(conf_out, cf, npx * 4, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return hf_cuda_err(c, e, "gabor outputs");
-        return sync_check_errw(c);
+        if (mem_kind == HF_HOST) return sync_check_errw(c);
     }
     return HF_OK;
 }

@@ -87,3 +87,28 @@ def test_gabor_arguments():
         for kw in (dict(n_theta=32), dict(radius=5), dict(sigma_along=0.0), dict(lambda_=float("nan"))):
             with pytest.raises(hf.HairFuseError):
                 f.gabor(im, **kw)
+
+
+def test_asynchronous_chunks_two_streams():
+    """HF_HOST_ASYNC: chunks of views on two contexts / streams taking turns give the maps of one
+    synchronous call bit for bit; pageable buffers are refused."""
+    import torch
+
+    import paper_2604_05794_b300 as hf
+    im = RNG.random((7, 64, 200)).astype(np.float32)
+    th, cf = run(im, device=False)
+    h_im = torch.from_numpy(im).pin_memory()
+    h_th = torch.empty(im.shape).pin_memory()
+    h_cf = torch.empty(im.shape).pin_memory()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    fs = [hf.HairFuse(8, 0, 0, stream=s.cuda_stream) for s in streams]
+    try:
+        with pytest.raises(ValueError):
+            fs[0].gabor(im, np.empty_like(im), np.empty_like(im), asynchronous=True)
+        for q, v0 in enumerate(range(0, 7, 2)):
+            fs[q & 1].gabor(h_im[v0:v0 + 2], h_th[v0:v0 + 2], h_cf[v0:v0 + 2], asynchronous=True)
+        torch.cuda.synchronize()
+        assert np.array_equal(h_th.numpy(), th) and np.array_equal(h_cf.numpy(), cf)
+    finally:
+        for f in fs:
+            f.close()
