@@ -20,7 +20,8 @@ enum : int {
     WAIT_START = 2,  // one mbarrier wait (on a completed phase) before each tile
     WAIT_LAST = 4,   // one more before each tile's last MMA
     WARP = 8,        // the whole warp runs the loop, the elected lane issues (else lane 0 alone)
-    MATH = 16,       // warps 1-15 compute while warp 0 issues
+    MATH = 16,       // warps 2-15 compute while warp 0 issues (warp 1 too unless GATE)
+    GATE = 32,       // warp 1 does the per-tile mbarrier wait and meets warp 0 at a named barrier
 };
 
 __device__ __forceinline__ float rsq(float x) {
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(512, 1) k_probe(int tiles, unsigned long long*
         int b = 0;
         if (MODE & WARP) {
             for (int t = 0; t < tiles; ++t) {
+                if (MODE & GATE) asm volatile("bar.sync 1, 64;" ::: "memory");   // warp 1 waited for us
                 if (MODE & WAIT_START) ok &= mbar_wait(ready, 1, kWaitTimeoutNs);
                 fence_after();
                 if (elect_one()) ok &= issue_tile<MODE>(tmem, sBa, sAa, bars, ready, (uint32_t)t, b);
@@ -105,6 +107,14 @@ __global__ void __launch_bounds__(512, 1) k_probe(int tiles, unsigned long long*
             out[blockIdx.x] = clock64() - t0;
             *stop = 1;
         }
+    } else if ((MODE & GATE) && warp == 1) {
+        // the same number of named-barrier meetings as warp 0's tiles, so neither can be left waiting
+        bool ok = true;
+        for (int t = 0; t < tiles; ++t) {
+            ok &= mbar_wait(ready, 1, kWaitTimeoutNs);
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+        }
+        if (!ok && lane == 0) atomicOr(err, 1u);
     } else if (MODE & MATH) {
         // an epilogue-like mix per step: FMAs, a reciprocal root, a key and a maximum
         float s0 = 0.0f, k0 = 0.0f, x = 1.0f + lane;
@@ -163,6 +173,8 @@ int main() {
     run<A_SMEM | WAIT_START>("A in shared memory, one wait per tile", sms, out, sink, err);
     run<WAIT_START | MATH>("one wait, 15 warps computing, lane 0 issues", sms, out, sink, err);
     run<WAIT_START | MATH | WARP>("one wait, 15 warps computing, warp runs loop + elect.sync", sms, out, sink, err);
+    run<GATE | WARP>("wait in a gate warp, bar.sync per tile", sms, out, sink, err);
+    run<GATE | MATH | WARP>("wait in a gate warp, bar.sync per tile, 14 warps computing", sms, out, sink, err);
     unsigned herr = 0;
     cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
     printf("wait failures: %u\n", herr);
