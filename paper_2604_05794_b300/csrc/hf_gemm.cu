@@ -44,6 +44,52 @@ __device__ __forceinline__ float erf_as(float x) {
 }
 
 __device__ __forceinline__ float gelu_as(float x) { return 0.5f * x * (1.0f + erf_as(x * 0.70710678118654752f)); }
+
+// The same GELU for two values at once: the scalings, the polynomial and the products as packed
+// FP32 pairs (each lane rounded like the scalar instruction), the reciprocal, the exponential and
+// the sign per value.  The polynomial is evaluated with negated coefficients, so q = -p exactly.
+typedef unsigned long long g2_t;
+__device__ __forceinline__ g2_t g2(float a, float b) {
+    g2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void g2u(g2_t r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ g2_t g2fma(g2_t a, g2_t b, g2_t c) {
+    g2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ g2_t g2mul(g2_t a, g2_t b) {
+    g2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ g2_t g2add(g2_t a, g2_t b) {
+    g2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ void gelu_as2(float xa, float xb, float& ga, float& gb) {
+    const g2_t X = g2(xa, xb);
+    float s0, s1;
+    g2u(g2mul(X, g2(0.70710678118654752f, 0.70710678118654752f)), s0, s1);
+    const float z0 = fabsf(s0), z1 = fabsf(s1);
+    const g2_t Z = g2(z0, z1);
+    float u0, u1;
+    g2u(g2fma(g2(0.3275911f, 0.3275911f), Z, g2(1.0f, 1.0f)), u0, u1);
+    const g2_t T = g2(__fdividef(1.0f, u0), __fdividef(1.0f, u1));
+    g2_t Q = g2fma(g2(-1.061405429f, -1.061405429f), T, g2(1.453152027f, 1.453152027f));
+    Q = g2fma(Q, T, g2(-1.421413741f, -1.421413741f));
+    Q = g2fma(Q, T, g2(0.284496736f, 0.284496736f));
+    Q = g2fma(Q, T, g2(-0.254829592f, -0.254829592f));
+    float e0, e1;
+    g2u(g2mul(g2(-z0, -z1), Z), e0, e1);
+    float r0, r1;
+    g2u(g2fma(g2mul(Q, T), g2(__expf(e0), __expf(e1)), g2(1.0f, 1.0f)), r0, r1);
+    const g2_t ERF = g2(copysignf(r0, s0), copysignf(r1, s1));
+    g2u(g2mul(g2mul(g2(0.5f, 0.5f), X), g2add(g2(1.0f, 1.0f), ERF)), ga, gb);
+}
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
@@ -430,15 +476,25 @@ __global__ void __launch_bounds__(kPThreads, 1) k_gemm_persist(const __grid_cons
                 if constexpr (EPI == EPI_GELU) {
                     uint16_t h[16];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) h[q] = bf16_bits(gelu_as(v[q] + consts[n + q]));
+                    for (int q = 0; q < 16; q += 2) {
+                        float ga, gb;
+                        gelu_as2(v[q] + consts[n + q], v[q + 1] + consts[n + q + 1], ga, gb);
+                        h[q] = bf16_bits(ga);
+                        h[q + 1] = bf16_bits(gb);
+                    }
                     if (wr) st_bf16x16(g.H + (size_t)row * g.ldh + n, h, vec);
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const float h = bf16_round(gelu_as(v[q] + consts[n + q]));
-                        y0 = fmaf(consts[256 + n + q], h, y0);
-                        y1 = fmaf(consts[512 + n + q], h, y1);
-                        y2 = fmaf(consts[768 + n + q], h, y2);
+                    for (int q = 0; q < 16; q += 2) {
+                        float ga, gb;
+                        gelu_as2(v[q] + consts[n + q], v[q + 1] + consts[n + q + 1], ga, gb);
+                        const float h0 = bf16_round(ga), h1 = bf16_round(gb);
+                        y0 = fmaf(consts[256 + n + q], h0, y0);
+                        y1 = fmaf(consts[512 + n + q], h0, y1);
+                        y2 = fmaf(consts[768 + n + q], h0, y2);
+                        y0 = fmaf(consts[256 + n + q + 1], h1, y0);
+                        y1 = fmaf(consts[512 + n + q + 1], h1, y1);
+                        y2 = fmaf(consts[768 + n + q + 1], h1, y2);
                     }
                 }
                 if (c0 + 16 < 128) tmem_ld_wait(nxt);
