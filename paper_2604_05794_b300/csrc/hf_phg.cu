@@ -11,7 +11,7 @@
 //   k_phg_flags/_scan/_write   the segment seeds (occupied voxels no strand entered) in voxel order
 //   k_phg_trace_segments a thread per seed of a batch (both halves); k_phg_count as above
 //   k_phg_bin/_scan/_put the segment ends binned by cell; k_phg_link a thread per strand end (nearest
-//                        compatible segment end); k_phg_hook / k_phg_jump the connected components
+//                        compatible segment end); k_phg_union / k_phg_flatten the connected components
 //
 // Every quantity that decides a voxel or a stop is computed in single precision with one rounding
 // per written operation (__fadd_rn, __fmul_rn, __fmaf_rn, __fdiv_rn, __fsqrt_rn: no contraction),
@@ -471,34 +471,56 @@ __global__ void k_phg_link(hf_phg_cfg g, LinkGrid G, long long S, long long K, c
     match[e] = best;
 }
 
-// connected components: hook the larger root under the smaller, then jump to the roots
-__global__ void k_phg_hook(long long S, long long nends, const long long* __restrict__ match, int* __restrict__ label,
-                           int* __restrict__ changed) {
-    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= nends || match[e] < 0) return;
-    const long long a = e < S ? e : S + ((e - S) >> 1), b = S + (match[e] >> 1);
-    const int la = label[a], lb = label[b];
-    if (la < lb) {
-        atomicMin(label + lb, la);
-        *changed = 1;
-    } else if (lb < la) {
-        atomicMin(label + la, lb);
-        *changed = 1;
+// Connected components as a lock-free union-find over the links.  Every parent pointer points to a
+// smaller index (a link hooks the larger root under the smaller with a compare-and-swap, and path
+// halving only shortens such chains), so each component's root is its smallest member whatever the
+// order of the threads: label = the component minimum, the oracle's labels exactly.
+__device__ __forceinline__ int uf_find(int* __restrict__ p, int x) {
+    for (int it = 0; it < (1 << 20); ++it) {   // chains are short; the cap only bounds the loop
+        const int q = p[x];
+        if (q == x) return x;
+        const int r = p[q];
+        if (r != q) p[x] = r;   // halve: x now points to its grandparent (a smaller index)
+        x = r;
     }
+    return x;
 }
 
-// every label to its root (64 hops per launch; a longer chain asks for another round)
-__global__ void k_phg_jump(long long n, int* __restrict__ label, int* __restrict__ changed) {
+__global__ void k_phg_union(long long S, long long nends, const long long* __restrict__ match, int* __restrict__ label,
+                            int* __restrict__ failed) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= nends || match[e] < 0) return;
+    int a = (int)(e < S ? e : S + ((e - S) >> 1)), b = (int)(S + (match[e] >> 1));
+    for (int it = 0; it < (1 << 20); ++it) {
+        a = uf_find(label, a);
+        b = uf_find(label, b);
+        if (a == b) return;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicCAS(label + b, b, a);   // hook root b under the smaller root a
+        if (old == b) return;
+        b = old;   // b was hooked meanwhile: retry from its new parent
+    }
+    *failed = 1;
+}
+
+// every label to its root (after the unions: the structure no longer changes)
+__global__ void k_phg_flatten(long long n, int* __restrict__ label, int* __restrict__ failed) {
     const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (x >= n) return;
     int l = label[x];
-    for (int it = 0; it < 64; ++it) {
+    for (int it = 0; it < (1 << 20); ++it) {
         const int m = label[l];
-        if (m == l) break;
+        if (m == l) {
+            label[x] = l;
+            return;
+        }
         l = m;
     }
-    label[x] = l;
-    if (label[l] != l) *changed = 1;
+    *failed = 1;
 }
 
 __global__ void k_phg_iota(long long n, int* __restrict__ label) {
@@ -745,27 +767,20 @@ extern "C" int hair_fuse_phg(hf_ctx* c, const hf_phg_cfg* cfg, long long N, cons
                  return cudaGetLastError();
              })))
             return rc;
-        int it = 0;
-        for (; it < 4096; ++it) {
-            int h = 0;
-            e = cudaMemsetAsync(changed, 0, sizeof(int), st);
-            if (e != cudaSuccess) return hf_cuda_err(c, e, "phg components");
-            if ((rc = run_launch(c, "k_phg_hook", [&] {
-                     for (int rep = 0; rep < 3; ++rep) {   // three passes per read of the flag
-                         if (nends > 0)
-                             k_phg_hook<<<grid_all(nends, kThreads), kThreads, 0, st>>>(S, nends, match, label,
-                                                                                        changed);
-                         k_phg_jump<<<grid_all(nstr, kThreads), kThreads, 0, st>>>(nstr, label, changed);
-                     }
-                     return cudaGetLastError();
-                 })))
-                return rc;
-            e = cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return hf_cuda_err(c, e, "phg components");
-            if (!h) break;
-        }
-        if (it == 4096) return hf_set_err(c, HF_ERR_CUDA, "phg: components did not settle");
+        e = cudaMemsetAsync(changed, 0, sizeof(int), st);
+        if (e != cudaSuccess) return hf_cuda_err(c, e, "phg components");
+        if ((rc = run_launch(c, "k_phg_union", [&] {
+                 if (nends > 0)
+                     k_phg_union<<<grid_all(nends, kThreads), kThreads, 0, st>>>(S, nends, match, label, changed);
+                 k_phg_flatten<<<grid_all(nstr, kThreads), kThreads, 0, st>>>(nstr, label, changed);
+                 return cudaGetLastError();
+             })))
+            return rc;
+        int h = 0;
+        e = cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return hf_cuda_err(c, e, "phg components");
+        if (h) return hf_set_err(c, HF_ERR_CUDA, "phg: a union-find chain exceeded its bound");
     }
     if (host) {
         struct Cp {
