@@ -77,3 +77,27 @@ def test_quarter_turn_and_flat_images():
     flat = np.full((40, 40), 0.6, np.float32)
     c = oracle.gabor_pixels(flat, np.array([20 * 40 + 20]))
     assert c["conf"][0] < 0.99
+
+
+def test_correlations_against_scipy():
+    """The window correlation written out in the oracle equals scipy's 2-D correlation (zero fill,
+    window centred) of the bf16 image with each kernel of the bank; the orientation index, the
+    angle and the confidence follow from those responses by their definitions."""
+    from scipy.signal import correlate2d
+    H, W = 40, 37
+    img = oracle.bf16(RNG.random((H, W)).astype(np.float32)).astype(np.float64)
+    b = oracle.gabor_bank().astype(np.float64)
+    F = np.empty((64, H, W))
+    for k in range(64):
+        e = correlate2d(img, b[k, 0], mode="same", boundary="fill", fillvalue=0.0)
+        o = correlate2d(img, b[k, 1], mode="same", boundary="fill", fillvalue=0.0)
+        F[k] = np.sqrt(e * e + o * o)
+    r = oracle.gabor_pixels(img.astype(np.float32), np.arange(H * W))
+    Fs = np.sort(F, axis=0)
+    unique = (Fs[-1] - Fs[-2]).ravel() >= 1e-4
+    assert np.array_equal(r["flag"] == 0, unique)
+    kb = np.argmax(F, axis=0).ravel()
+    assert unique.mean() > 0.9 and np.array_equal(r["k"][unique], kb[unique])
+    assert np.allclose(r["theta"][unique], (np.pi * kb / 64)[unique], atol=1e-6)
+    conf = 1.0 - F.mean(axis=0) / F.max(axis=0)
+    assert np.allclose(r["conf"], conf.ravel(), atol=2e-7, rtol=0)
