@@ -868,7 +868,7 @@ def run_serving(args):
         path = ("hair_fuse_upload_views (HF_HOST_ASYNC, pinned) + hair_fuse_upload_points of every scene, "
                 "hair_fuse_batch_run (graph), device-to-host copy of all outputs; two scene sets on two "
                 "streams take turns")
-        n_e2e = max(2, min(K, 6))
+        n_e2e = max(2, min(K, 10))   # enough steps that filling and draining the pipeline weigh little
         if pg:
             pg.barrier()
         t0 = time.perf_counter()
