@@ -256,18 +256,18 @@ __global__ void k_phg_trace_segments(hf_phg_cfg g, const float4* __restrict__ vr
 }
 
 // Deferred occupancy: one more strand in every occupied voxel a polyline of [b0, b1) entered
-// (consecutive vertices in one voxel count once).
+// (consecutive vertices in one voxel count once).  A thread per vertex slot (vstride per polyline):
+// vertex k counts when it is a voxel other than vertex k - 1's; the integer sums do not depend on
+// the order.
 __global__ void k_phg_count(const int* __restrict__ occ, const int* __restrict__ len, long long b0, long long b1,
                             const int* __restrict__ bvox, int vstride, int* __restrict__ crowd) {
-    const long long i = b0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= b1) return;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long i = b0 + t / vstride;
+    const int k = (int)(t % vstride);
+    if (i >= b1 || k >= len[i]) return;
     const int* v = bvox + (size_t)vstride * (i - b0);
-    int last = -1;
-    for (int k = 0; k < len[i]; ++k) {
-        const int c = v[k];
-        if (c >= 0 && c != last && occ[c] > 0) atomicAdd(crowd + c, 1);
-        last = c;
-    }
+    const int c = v[k];
+    if (c >= 0 && (k == 0 || v[k - 1] != c) && occ[c] > 0) atomicAdd(crowd + c, 1);
 }
 
 // ------------------------------------------------------------------ ordered compaction and scans
@@ -678,7 +678,7 @@ extern "C" int hair_fuse_phg(hf_ctx* c, const hf_phg_cfg* cfg, long long N, cons
              })))
             return rc;
         if ((rc = run_launch(c, "k_phg_count", [&] {
-                 k_phg_count<<<grid_all(b1 - b0, 128), 128, 0, st>>>(occ, glen, b0, b1, bvox, vstride, crowd);
+                 k_phg_count<<<grid_all((b1 - b0) * vstride, 128), 128, 0, st>>>(occ, glen, b0, b1, bvox, vstride, crowd);
                  return cudaGetLastError();
              })))
             return rc;
@@ -718,7 +718,7 @@ extern "C" int hair_fuse_phg(hf_ctx* c, const hf_phg_cfg* cfg, long long N, cons
              })))
             return rc;
         if ((rc = run_launch(c, "k_phg_count", [&] {
-                 k_phg_count<<<grid_all(b1 - b0, 128), 128, 0, st>>>(occ, slen, b0, b1, bvox, vstride, crowd);
+                 k_phg_count<<<grid_all((b1 - b0) * vstride, 128), 128, 0, st>>>(occ, slen, b0, b1, bvox, vstride, crowd);
                  return cudaGetLastError();
              })))
             return rc;
