@@ -285,10 +285,10 @@ int hair_fuse_eval_costs(hf_ctx* ctx, int M, const float* dirs, float* cost_out,
  *  - All pointers are device memory of the current device: cams, angle, conf, xyz, nbr and hyps
  *    (NULL = built-in set) as in those calls; dir_out (required), cost_out, idx_out, status_out
  *    (each may be NULL) as in hair_fuse_fuse_directions.  cfg gives H, k, T and top_k_views.
- *  - The scratch between the kernels is one static device array of 20.2 MB inside this library,
- *    which every GPU that loads the library holds until the process exits.  Limits: N * V <=
- *    1,048,576, N <= 262,144, V <= 1024, V * Hpad <= 65,536 (Hpad = H rounded up to 8, 16 or 32);
- *    larger inputs are rejected with HF_ERR_SHAPE before any work is queued.
+ *  - The scratch between the kernels is one static device array of 16,794,368 bytes (16.0 MiB)
+ *    inside this library, which every GPU that loads the library holds until the process exits.
+ *    Limits: N * V <= 1,048,576, N <= 262,144, V <= 1024; larger inputs are rejected with
+ *    HF_ERR_SHAPE before any work is queued.
  *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress, with
  *    that device current); make that first call before any stream capture.
  *  - Every call on a device shares the one array and leaves its contents behind; the call clears
@@ -396,9 +396,8 @@ typedef struct {
     int T_short;        /* learned: refinement rounds from the proposal, 1..HF_MAX_T */
     float alpha_short;  /* learned: first rotation step (radians), halved each round */
     float tau;          /* learned: fallback threshold on the proposal's cost */
-    int autotune;       /* 1: at the first run, time the candidate tile shapes on the batch and keep the fastest */
-    int hchunk;         /* hypotheses per chunk of the argmin: 0 = tuned / default, else 8, 16 or 32 */
-    int points_per_cta; /* points per CTA of argmin and refinement: 0 = tuned / default 128, else 64, 128, 256 */
+    int autotune;       /* 1: at the first run, time the candidate launch shapes on the batch and keep the fastest */
+    int cta_threads;    /* threads per CTA of the cost kernels: 0 = tuned / default 128, else 64, 128, 256 */
     int order;          /* scene order of the work list: 0 = tuned (heaviest or lightest first), 1 = heaviest
                          * first, 2 = as given, 3 = lightest first (small scenes complete early) */
 } hf_batch_cfg;
@@ -422,9 +421,9 @@ int hair_fuse_batch_sync(hf_batch* b);
 int hair_fuse_batch_latency(hf_batch* b, double* ms_out);
 /* Per-scene fallback counts of the last learned run (0 for the plain fusion), host.  Synchronises. */
 int hair_fuse_batch_fallbacks(hf_batch* b, int* n_out);
-/* The launch shape in use: out4 = {hypothesis chunk, points per CTA of the argmin, points per CTA of
- * the refinement, scene order (1 heaviest first, 2 as given, 3 lightest first)}. */
-int hair_fuse_batch_tuning(const hf_batch* b, int* out4);
+/* The launch shape in use: out2 = {threads per CTA of the cost kernels, scene order (1 heaviest first,
+ * 2 as given, 3 lightest first)}. */
+int hair_fuse_batch_tuning(const hf_batch* b, int* out2);
 /* One eager run with CUDA events between the stages (synchronous): per-stage records as in
  * hair_fuse_profile_read (the network's stage counts its two GEMM launches).  Returns the number of
  * stages (records beyond max_entries are dropped) or a negative error code. */
@@ -442,6 +441,41 @@ int hair_fuse_learned_work(hf_ctx* ctx, long long* fallback_point_views, long lo
 
 /* The built-in hypothesis set (host memory): H x 3 f32 Fibonacci hemisphere directions. */
 int hair_fuse_fibonacci_hemisphere(int H, float* out);
+
+/* FP32 issue-rate microbenchmark: the measured peak that the cost kernels' rooflines divide by.
+ * The paper has no counterpart.  kind selects the instruction timed:
+ *   HF_ISSUE_FFMA      scalar fma.rn.f32 (1 operation per lane)
+ *   HF_ISSUE_FFMA2     packed fma.rn.f32x2 (2 operations per lane)
+ *   HF_ISSUE_FMUL2     packed mul.rn.f32x2 (2 operations per lane)
+ *   HF_ISSUE_FMAX_ABS  max(|x|, y) as the patch maximum writes it
+ *   HF_ISSUE_FMAX3     three-input max.f32 (2 operations)
+ *   HF_ISSUE_PATCH     the patch term's inner step for two directions and one patch member:
+ *                      mul.rn.f32x2 + fma.rn.f32x2 + two max of |x| (2 evaluations, counted as
+ *                      3 operations each: multiply, multiply-add, maximum)
+ *   HF_ISSUE_FMAX3_ABS three-input max.f32 of a running maximum and two absolute values (2 operations)
+ *   HF_ISSUE_PATCH3    the patch term's inner step for two directions and two patch members:
+ *                      2 mul.rn.f32x2 + 2 fma.rn.f32x2 + two three-input maxima of |x| (4
+ *                      evaluations, 12 operations)
+ *   HF_ISSUE_PATCH3S   HF_ISSUE_PATCH3 with scalar products: 4 mul.rn.f32 + 4 fma.rn.f32 + two
+ *                      three-input maxima of |x| (4 evaluations, 12 operations)
+ * Each thread of a full-occupancy grid of 256-thread CTAs runs iters x 16 steps of 8 independent
+ * chains; one short untimed launch precedes the timed one (CUDA events on cuda_stream, a cudaStream_t;
+ * the call waits for it and allocates a small result buffer).  Outputs (host): instr_out = thread-level
+ * instructions of the kind issued (4 per step for HF_ISSUE_PATCH, 6 for HF_ISSUE_PATCH3, 10 for
+ * HF_ISSUE_PATCH3S), ops_out =
+ * operations as above,
+ * ms_out = the timed launch's duration; instr_out and ops_out may be NULL.
+ * Errors: HF_ERR_INVALID_ARG (unknown kind, iters < 1, null ms_out), HF_ERR_OOM, HF_ERR_CUDA. */
+#define HF_ISSUE_FFMA 0
+#define HF_ISSUE_FFMA2 1
+#define HF_ISSUE_FMUL2 2
+#define HF_ISSUE_FMAX_ABS 3
+#define HF_ISSUE_FMAX3 4
+#define HF_ISSUE_PATCH 5
+#define HF_ISSUE_FMAX3_ABS 6
+#define HF_ISSUE_PATCH3 7
+#define HF_ISSUE_PATCH3S 8
+int hair_fuse_issue_rate(int kind, int iters, void* cuda_stream, double* instr_out, double* ops_out, float* ms_out);
 
 /* Wait for the context's stream and return any error latched on the device. */
 int hair_fuse_sync(hf_ctx* ctx);

@@ -119,6 +119,8 @@ _SIGS = {
     "hair_fuse_batch_stats": ([_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll), ctypes.POINTER(_ll)], _i),
     "hair_fuse_batch_destroy": ([_vp], None),
     "hair_fuse_batch_last_error": ([_vp], ctypes.c_char_p),
+    "hair_fuse_issue_rate": ([_i, _i, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_float)], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -185,6 +187,13 @@ hair_fuse_batch_profile_run = _lib.hair_fuse_batch_profile_run
 hair_fuse_batch_stats = _lib.hair_fuse_batch_stats
 hair_fuse_batch_destroy = _lib.hair_fuse_batch_destroy
 hair_fuse_batch_last_error = _lib.hair_fuse_batch_last_error
+hair_fuse_issue_rate = _lib.hair_fuse_issue_rate
+
+HF_ISSUE_FFMA, HF_ISSUE_FFMA2, HF_ISSUE_FMUL2, HF_ISSUE_FMAX_ABS, HF_ISSUE_FMAX3, HF_ISSUE_PATCH = 0, 1, 2, 3, 4, 5
+HF_ISSUE_FMAX3_ABS, HF_ISSUE_PATCH3, HF_ISSUE_PATCH3S = 6, 7, 8
+ISSUE_KINDS = {"ffma": HF_ISSUE_FFMA, "ffma2": HF_ISSUE_FFMA2, "fmul2": HF_ISSUE_FMUL2,
+               "fmax_abs": HF_ISSUE_FMAX_ABS, "fmax3": HF_ISSUE_FMAX3, "patch": HF_ISSUE_PATCH,
+               "fmax3_abs": HF_ISSUE_FMAX3_ABS, "patch3": HF_ISSUE_PATCH3, "patch3s": HF_ISSUE_PATCH3S}
 
 
 class HairFuseError(RuntimeError):
@@ -236,6 +245,19 @@ def fibonacci_hemisphere(H):
     out = np.empty((H, 3), np.float32)
     _check(hair_fuse_fibonacci_hemisphere(H, out.ctypes.data))
     return out
+
+
+def issue_rate(kind, iters=4096, stream=None):
+    """One timed launch of the FP32 issue-rate microbenchmark (``kind`` a key of ISSUE_KINDS):
+    dict(instr, ops, ms, instr_per_s, ops_per_s).  Synchronous."""
+    instr, ops, ms = ctypes.c_double(), ctypes.c_double(), ctypes.c_float()
+    rc = hair_fuse_issue_rate(ISSUE_KINDS[kind], iters, current_stream_handle() if stream is None else stream,
+                              ctypes.byref(instr), ctypes.byref(ops), ctypes.byref(ms))
+    if rc != HF_OK:
+        raise HairFuseError(rc, f"issue-rate probe {kind} failed")
+    sec = ms.value * 1e-3
+    return dict(instr=instr.value, ops=ops.value, ms=ms.value, instr_per_s=instr.value / sec,
+                ops_per_s=ops.value / sec)
 
 
 def gemm_bf16(a, b, out=None, stream=None):
@@ -545,19 +567,18 @@ HairFuse.learned_work = _learned_work
 
 class hf_batch_cfg(ctypes.Structure):
     _fields_ = [("T_short", ctypes.c_int), ("alpha_short", ctypes.c_float), ("tau", ctypes.c_float),
-                ("autotune", ctypes.c_int), ("hchunk", ctypes.c_int), ("points_per_cta", ctypes.c_int),
-                ("order", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("cta_threads", ctypes.c_int), ("order", ctypes.c_int)]
 
 
 class Batch:
     """Batched fusion of several HairFuse contexts (plain, or learned with a ProposalNet): one
     persistent launch per stage over all scenes, replayed as one CUDA graph."""
 
-    def __init__(self, scenes, net=None, T_short=2, alpha_short=0.16, tau=0.5, autotune=True, hchunk=0,
-                 points_per_cta=0, order=0, stream=None):
+    def __init__(self, scenes, net=None, T_short=2, alpha_short=0.16, tau=0.5, autotune=True, cta_threads=0,
+                 order=0, stream=None):
         self.scenes = list(scenes)
         self.net = net
-        cfg = hf_batch_cfg(T_short, alpha_short, tau, 1 if autotune else 0, hchunk, points_per_cta, order)
+        cfg = hf_batch_cfg(T_short, alpha_short, tau, 1 if autotune else 0, cta_threads, order)
         arr = (_vp * len(self.scenes))(*[sc.h for sc in self.scenes])
         h = _vp()
         rc = hair_fuse_batch_create(ctypes.byref(h), arr, len(self.scenes), net.h if net is not None else None,
@@ -609,10 +630,10 @@ class Batch:
         return out
 
     def tuning(self):
-        out = np.zeros(4, np.int32)
+        out = np.zeros(2, np.int32)
         self._c(hair_fuse_batch_tuning(self.h, out.ctypes.data))
-        return dict(hchunk=int(out[0]), points_per_cta_argmin=int(out[1]), points_per_cta_refine=int(out[2]),
-                    order={1: "heaviest first", 2: "as given", 3: "lightest first"}.get(int(out[3]), "?"))
+        return dict(cta_threads=int(out[0]),
+                    order={1: "heaviest first", 2: "as given", 3: "lightest first"}.get(int(out[1]), "?"))
 
     def profile_run(self):
         """One eager run with events between the stages: {stage: (launches, ms)}."""

@@ -54,16 +54,16 @@ int ready(hf_ctx* c) {
 
 // K1 over the uploaded scene into the context's scratch
 int run_project(hf_ctx* c) {
-    const size_t vn = (size_t)c->V * c->N;
+    const int Vs = hf_samp_stride(c->V), Vw = hf_mask_words(c->V);
     int rc;
-    if ((rc = hf_ensure(c, c->samp, vn * sizeof(float2)))) return rc;
-    if ((rc = hf_ensure(c, c->ab, vn * sizeof(float2)))) return rc;
+    if ((rc = hf_ensure(c, c->samp, (size_t)c->N * Vs * sizeof(float2)))) return rc;
+    if ((rc = hf_ensure(c, c->vmask, (size_t)c->N * Vw * sizeof(unsigned long long)))) return rc;
     if ((rc = hf_ensure(c, c->work, sizeof(unsigned long long)))) return rc;
     cudaError_t e = cudaMemsetAsync(c->work.p, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return hf_cuda_err(c, e, "clear work counter");
     ProjectArgs pa{(const float*)c->pts.p, c->N, (const float*)c->cams.p, c->V, c->W, c->Hh,
                    (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, c->cfg.top_k_views,
-                   (float2*)c->samp.p, (float2*)c->ab.p, (unsigned long long*)c->work.p, nullptr,
+                   (float2*)c->samp.p, (unsigned long long*)c->vmask.p, (unsigned long long*)c->work.p, nullptr,
                    (const float2*)c->amap.p};
     return run_launch(c, "k_project", [&] { return hf_launch_project(pa, c->stream); });
 }
@@ -103,6 +103,29 @@ int hf_ensure(hf_ctx* c, DevBuf& b, size_t bytes) {
     b.cap = bytes;
     c->dev_bytes += (long long)bytes;
     return HF_OK;
+}
+
+CostArgs hf_cost_args(const hf_ctx* c) {
+    CostArgs a{};
+    a.pts = (const float*)c->pts.p;
+    a.N = c->N;
+    a.nbr = (const int32_t*)c->nbr.p;
+    a.k = c->k;
+    a.cams = (const float*)c->cams.p;
+    a.V = c->V;
+    a.samp = (const float2*)c->samp.p;
+    a.Vs = hf_samp_stride(c->V);
+    a.vmask = (const unsigned long long*)c->vmask.p;
+    a.Vw = hf_mask_words(c->V);
+    a.vthr = (const float*)c->vthr.p;
+    a.hyps = (const float*)c->hyps.p;
+    a.H = c->cfg.H;
+    a.Hpad = hf_hpad(c->cfg.H);
+    a.rot = (const float2*)c->rot.p;
+    a.T = c->cfg.T;
+    const int tk = c->cfg.top_k_views;
+    a.L = hf_cost_lanes(tk > 0 && tk < c->V ? tk : c->V, c->k);
+    return a;
 }
 
 extern "C" {
@@ -224,9 +247,8 @@ int fuse_impl(hf_ctx* c, const float* hyps, bool ranged, int first, int count, f
         count = c->N;
     }
     if (count == 0) return HF_OK;
-    const int N = c->N, R = count;
-    const int hc = hf_fuse_chunk_for(H);
-    const int Hpad = (H + hc - 1) / hc * hc;
+    const int R = count;
+    const int Hpad = hf_hpad(H);
     const float* hyps_dev = nullptr;
     if (hyps && mem_kind == HF_HOST) {
         for (int m = 0; m < H; ++m) {
@@ -241,12 +263,11 @@ int fuse_impl(hf_ctx* c, const float* hyps, bool ranged, int first, int count, f
     } else if (hyps) {
         hyps_dev = hyps;
     }
-    if ((rc = hf_ensure(c, c->qtab, (size_t)V * Hpad * sizeof(float4)))) return rc;
     if ((rc = hf_ensure(c, c->vthr, (size_t)V * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->hyps, (size_t)Hpad * 3 * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->rot, (size_t)(T > 0 ? T : 1) * sizeof(float2)))) return rc;
-    PrepArgs pr{(const float*)c->cams.p, V, hyps_dev, H, Hpad, T, (float*)c->hyps.p, (float4*)c->qtab.p,
-                (float*)c->vthr.p, (float2*)c->rot.p, (uint32_t*)c->errw.p};
+    PrepArgs pr{(const float*)c->cams.p, V, hyps_dev, H, Hpad, T, (float*)c->hyps.p, (float*)c->vthr.p,
+                (float2*)c->rot.p, (uint32_t*)c->errw.p};
     if ((rc = run_launch(c, "k_prep", [&] { return hf_launch_prep(pr, c->stream); }))) return rc;
     if ((rc = run_project(c))) return rc;
 
@@ -262,12 +283,11 @@ int fuse_impl(hf_ctx* c, const float* hyps, bool ranged, int first, int count, f
         d_idx = idx_out ? (int32_t*)(base + (size_t)R * 16) : nullptr;
         d_status = status_out ? (uint8_t*)(base + (size_t)R * 20) : nullptr;
     }
-    if ((rc = hf_ensure(c, c->best, (size_t)N * 12))) return rc;
-    int32_t* bi = (int32_t*)c->best.p;
-    FuseArgs fa{(const float*)c->pts.p, N, (const int32_t*)c->nbr.p, c->k, (const float*)c->cams.p, V,
-                (const float2*)c->samp.p, (const float2*)c->ab.p, (const float4*)c->qtab.p, (const float*)c->vthr.p,
-                (const float*)c->hyps.p, H, Hpad, (const float2*)c->rot.p, T, d_dir, d_cost, d_idx, d_status,
-                bi, (float*)(bi + N), bi + 2 * (size_t)N, hf_fuse_vblock_q(V, hc), hf_fuse_vblock_c(V)};
+    CostArgs fa = hf_cost_args(c);
+    fa.dir_out = d_dir;
+    fa.cost_out = d_cost;
+    fa.idx_out = d_idx;
+    fa.status_out = d_status;
     if (ranged) {
         if ((rc = hf_ensure(c, c->rlist, 16 + (size_t)R * sizeof(int32_t)))) return rc;
         int* cnt = (int*)c->rlist.p;
@@ -277,8 +297,7 @@ int fuse_impl(hf_ctx* c, const float* hyps, bool ranged, int first, int count, f
         fa.list_count = cnt;
         fa.out_first = first;
     }
-    if ((rc = run_launch(c, "k_argmin", [&] { return hf_launch_argmin(fa, hc, c->stream); }))) return rc;
-    if ((rc = run_launch(c, "k_refine", [&] { return hf_launch_refine(fa, c->stream); }))) return rc;
+    if ((rc = run_launch(c, "k_fuse", [&] { return hf_launch_fuse(fa, c->stream); }))) return rc;
     if (mem_kind == HF_HOST) {
         cudaError_t e = cudaMemcpyAsync(dir_out, d_dir, (size_t)R * 12, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess && cost_out) e = cudaMemcpyAsync(cost_out, d_cost, (size_t)R * 4, cudaMemcpyDeviceToHost, c->stream);
@@ -308,14 +327,13 @@ int hair_fuse_eval_costs(hf_ctx* c, int M, const float* dirs, float* cost_out, i
     if ((rc = check_kind(c, mem_kind))) return rc;
     if (M < 1 || !dirs || !cost_out) return hf_set_err(c, HF_ERR_INVALID_ARG, "M >= 1 and non-null dirs, cost_out required");
     const int V = c->V, N = c->N;
+    // thresholds (and the hypotheses, unused here) come from the prep kernel
+    const int Hpad = hf_hpad(c->cfg.H);
     if ((rc = hf_ensure(c, c->vthr, (size_t)V * sizeof(float)))) return rc;
-    // thresholds (and a throw-away hypothesis table) come from the prep kernel
-    const int hc = hf_fuse_chunk_for(c->cfg.H), Hpad = (c->cfg.H + hc - 1) / hc * hc;
-    if ((rc = hf_ensure(c, c->qtab, (size_t)V * Hpad * sizeof(float4)))) return rc;
     if ((rc = hf_ensure(c, c->hyps, (size_t)Hpad * 3 * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->rot, (size_t)(c->cfg.T > 0 ? c->cfg.T : 1) * sizeof(float2)))) return rc;
-    PrepArgs pr{(const float*)c->cams.p, V, nullptr, c->cfg.H, Hpad, c->cfg.T, (float*)c->hyps.p, (float4*)c->qtab.p,
-                (float*)c->vthr.p, (float2*)c->rot.p, (uint32_t*)c->errw.p};
+    PrepArgs pr{(const float*)c->cams.p, V, nullptr, c->cfg.H, Hpad, c->cfg.T, (float*)c->hyps.p, (float*)c->vthr.p,
+                (float2*)c->rot.p, (uint32_t*)c->errw.p};
     if ((rc = run_launch(c, "k_prep", [&] { return hf_launch_prep(pr, c->stream); }))) return rc;
     if ((rc = run_project(c))) return rc;
     const float* d_dirs = dirs;
@@ -329,8 +347,7 @@ int hair_fuse_eval_costs(hf_ctx* c, int M, const float* dirs, float* cost_out, i
         d_dirs = (const float*)c->evald.p;
         d_cost = (float*)c->outs.p;
     }
-    EvalArgs ea{(const float*)c->pts.p, N, (const int32_t*)c->nbr.p, c->k, (const float*)c->cams.p, V,
-                (const float2*)c->samp.p, (const float2*)c->ab.p, (const float*)c->vthr.p, d_dirs, M, d_cost};
+    EvalArgs ea{hf_cost_args(c), d_dirs, M, d_cost};
     if ((rc = run_launch(c, "k_eval", [&] { return hf_launch_eval(ea, c->stream); }))) return rc;
     if (mem_kind == HF_HOST) {
         cudaError_t e = cudaMemcpyAsync(cost_out, d_cost, nd * 4, cudaMemcpyDeviceToHost, c->stream);
@@ -422,8 +439,8 @@ void hair_fuse_destroy(hf_ctx* c) {
         cudaEventDestroy(r.beg);
         cudaEventDestroy(r.end);
     }
-    DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->amap, &c->depth, &c->dmap, &c->vmap, &c->fprec, &c->phg, &c->gabor, &c->gbank, &c->rlist, &c->pts, &c->nbr, &c->samp, &c->ab, &c->qtab,
-                      &c->vthr, &c->hyps, &c->rot, &c->outs, &c->evald, &c->errw, &c->work, &c->best, &c->feat, &c->prop, &c->lmisc};
+    DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->amap, &c->depth, &c->dmap, &c->vmap, &c->fprec, &c->phg, &c->gabor, &c->gbank, &c->rlist, &c->pts, &c->nbr, &c->samp, &c->vmask,
+                      &c->vthr, &c->hyps, &c->rot, &c->outs, &c->evald, &c->errw, &c->work, &c->feat, &c->prop, &c->lmisc};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->errw_host) cudaFreeHost(c->errw_host);

@@ -22,18 +22,19 @@
 namespace {
 
 // stage slots of the item counters
-enum { ST_PROJECT, ST_FEATURES, ST_SHORT, ST_SELECT, ST_ARGMIN, ST_MAIN, ST_MLP, ST_COUNT };
-const char* const kStageName[ST_COUNT] = {"k_project_batch", "k_features_batch", "k_refine_short_batch",
-                                          "k_start_select_batch", "k_argmin_batch", "k_refine_batch", "k_mlp"};
+enum { ST_PROJECT, ST_FEATURES, ST_LEARN, ST_MAIN, ST_MLP, ST_COUNT };
+const char* const kStageName[ST_COUNT] = {"k_project_batch", "k_features_batch", "k_learn_batch", "k_fuse_batch",
+                                          "k_mlp"};
 static_assert(ST_COUNT <= 8, "eight item counters");
 
 // device control block (bytes); [0, kZeroEnd) is cleared by k_prep_batch at the start of a run
 constexpr size_t kNextOff = 0;                                   // u32 [ST_COUNT] (padded to 8)
-constexpr size_t kDoneOff = 32;                                  // u32 [2][HF_MAX_BATCH]: short, main
+constexpr size_t kDoneOff = 32;                                  // u32 [2][HF_MAX_BATCH]: learn, main
 constexpr size_t kCountOff = kDoneOff + 2 * HF_MAX_BATCH * 4;    // i32 [HF_MAX_BATCH]: fallback list lengths
-constexpr size_t kAccOff = kCountOff + HF_MAX_BATCH * 4;         // i32 [HF_MAX_BATCH]: accepted list lengths
-constexpr size_t kWorkOff = kAccOff + HF_MAX_BATCH * 4;          // u64 [HF_MAX_BATCH]: (point, view) pairs
-constexpr size_t kStampOff = kWorkOff + HF_MAX_BATCH * 8;        // u64 [2][HF_MAX_BATCH]: completion times
+constexpr size_t kWorkOff = kCountOff + HF_MAX_BATCH * 4;        // u64 [HF_MAX_BATCH]: (point, view) pairs
+constexpr size_t kFbWorkOff = kWorkOff + HF_MAX_BATCH * 8;       // u64 [HF_MAX_BATCH]: those of fallback points
+constexpr size_t kAccWorkOff = kFbWorkOff + HF_MAX_BATCH * 8;    // u64 [HF_MAX_BATCH]: of accepted proposals
+constexpr size_t kStampOff = kAccWorkOff + HF_MAX_BATCH * 8;     // u64 [2][HF_MAX_BATCH]: completion times
 constexpr size_t kZeroEnd = kStampOff + 2 * HF_MAX_BATCH * 8;
 constexpr size_t kT0Off = kZeroEnd;                              // u64 batch start
 constexpr size_t kBoxOff = kT0Off + 8;                           // u32 [HF_MAX_BATCH][6]
@@ -57,9 +58,8 @@ struct ArgBlock {
     PrepArgs prep[HF_MAX_BATCH];
     ProjectArgs proj[HF_MAX_BATCH];
     FeatArgs feat[HF_MAX_BATCH];
-    FuseArgs shrt[HF_MAX_BATCH];
-    StartSelectArgs ssel[HF_MAX_BATCH];
-    FuseArgs main[HF_MAX_BATCH];
+    LearnArgs learn[HF_MAX_BATCH];
+    CostArgs main[HF_MAX_BATCH];
 };
 
 }  // namespace
@@ -72,7 +72,8 @@ struct hf_batch {
     cudaStream_t user = nullptr;    // caller's stream (ordering only)
     cudaStream_t stream = nullptr;  // the batch's own non-blocking stream (captured)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, t_beg = nullptr, t_end = nullptr;
-    int kp = 9, hc = 32, nt_a = 128, nt_r = 128, order = 1;   // order: 1 heaviest first, 2 as given, 3 lightest first
+    int kp = 9, nt = 128, order = 1;   // nt: threads per CTA of the cost kernels; order: 1 heaviest first, 2 as given, 3 lightest first
+    int hpad_max = 2;
     bool tuned = false, configured = false;
     long long total = 0;
     char* ctl = nullptr;
@@ -82,7 +83,6 @@ struct hf_batch {
     float* prop = nullptr;
     uint16_t* h1 = nullptr;
     int32_t* list = nullptr;       // fallback points, per scene from its row offset
-    int32_t* acc_list = nullptr;   // accepted proposals, likewise
     cudaGraphExec_t gexec = nullptr;
     long long launches = 0;   // kernels enqueued (graph replays counted by their kernels)
     std::string err;
@@ -109,7 +109,7 @@ void drop_graph(hf_batch* b) {
     b->gexec = nullptr;
 }
 
-// Fill and upload the argument arrays for the current tuning choice (hc, order).
+// Fill and upload the argument arrays for the current scene order.
 int configure(hf_batch* b) {
     const int ns = (int)b->sc.size();
     b->pos.resize(ns);
@@ -123,8 +123,9 @@ int configure(hf_batch* b) {
     const bool learned = b->mlp != nullptr;
     unsigned* box = reinterpret_cast<unsigned*>(b->ctl + kBoxOff);
     int* count = reinterpret_cast<int*>(b->ctl + kCountOff);
-    int* acc = reinterpret_cast<int*>(b->ctl + kAccOff);
     unsigned long long* work = reinterpret_cast<unsigned long long*>(b->ctl + kWorkOff);
+    unsigned long long* fb_work = reinterpret_cast<unsigned long long*>(b->ctl + kFbWorkOff);
+    unsigned long long* acc_work = reinterpret_cast<unsigned long long*>(b->ctl + kAccWorkOff);
     float2* rot_s = reinterpret_cast<float2*>(b->ctl + kRotOff);
     uint32_t* errw = reinterpret_cast<uint32_t*>(b->ctl + kErrOff);
     ArgBlock& A = *b->args_h;
@@ -133,34 +134,27 @@ int configure(hf_batch* b) {
         const BatchScene& s = b->sc[b->pos[p]];
         hf_ctx* c = s.c;
         const int N = c->N, V = c->V, H = c->cfg.H, T = c->cfg.T;
-        const int Hpad = (H + b->hc - 1) / b->hc * b->hc;
-        int32_t* bi = (int32_t*)c->best.p;
-        A.prep[p] = PrepArgs{(const float*)c->cams.p, V, nullptr, H, Hpad, T, (float*)c->hyps.p, (float4*)c->qtab.p,
+        A.prep[p] = PrepArgs{(const float*)c->cams.p, V, nullptr, H, hf_hpad(H), T, (float*)c->hyps.p,
                              (float*)c->vthr.p, (float2*)c->rot.p, errw};
         A.proj[p] = ProjectArgs{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh,
                                 (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0,
-                                c->cfg.top_k_views, (float2*)c->samp.p, (float2*)c->ab.p, work + p,
+                                c->cfg.top_k_views, (float2*)c->samp.p, (unsigned long long*)c->vmask.p, work + p,
                                 learned ? box + 6 * p : nullptr, (const float2*)c->amap.p};
         A.feat[p] = FeatArgs{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh,
                              (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, nullptr,
                              b->x + (size_t)s.off * 64, box + 6 * p, (const float2*)c->amap.p};
-        FuseArgs m{(const float*)c->pts.p, N, (const int32_t*)c->nbr.p, c->k, (const float*)c->cams.p, V,
-                   (const float2*)c->samp.p, (const float2*)c->ab.p, (const float4*)c->qtab.p, (const float*)c->vthr.p,
-                   (const float*)c->hyps.p, H, Hpad, (const float2*)c->rot.p, T, s.dir, s.cost, s.idx, s.status,
-                   bi, (float*)(bi + N), bi + 2 * (size_t)N, hf_fuse_vblock_q(V, b->hc), hf_fuse_vblock_c(V)};
+        CostArgs m = hf_cost_args(c);
+        m.dir_out = s.dir;
+        m.cost_out = s.cost;
+        m.idx_out = s.idx;
+        m.status_out = s.status;
         if (learned) {
-            // the proposal's cost sorts the points into the fallback and the accepted list
-            FuseArgs sel = m;
-            sel.start_dir = b->prop + (size_t)s.off * 3;
-            sel.list = b->list + s.off;
-            sel.list_count = count + p;
-            A.ssel[p] = StartSelectArgs{sel, b->cfg.tau, b->acc_list + s.off, acc + p};
-            FuseArgs f = sel;
-            f.rot = rot_s;
-            f.T = b->cfg.T_short;
-            f.list = b->acc_list + s.off;
-            f.list_count = acc + p;
-            A.shrt[p] = f;
+            // the proposal's cost sorts the points into the fallback list and the short refinement
+            LearnArgs la{m, b->prop + (size_t)s.off * 3, b->cfg.tau, b->list + s.off, count + p, fb_work + p,
+                         acc_work + p};
+            la.f.rot = rot_s;
+            la.f.T = b->cfg.T_short;
+            A.learn[p] = la;
             m.list = b->list + s.off;
             m.list_count = count + p;
             m.fell_back = 1;
@@ -209,15 +203,13 @@ cudaError_t launch_stage(hf_batch* b, int stage) {
         case ST_FEATURES: return hf_launch_features_batch(A->feat, ctl_for(b, ST_FEATURES, -1), s);
         case ST_MLP:
             return hf_mlp_infer_rows(b->mlp, b->x, b->total, b->h1, b->prop, reinterpret_cast<uint32_t*>(b->ctl + kErrOff), s);
-        case ST_SHORT: return hf_launch_refine_batch(A->shrt, ctl_for(b, ST_SHORT, 0), b->kp, b->nt_r, s);
-        case ST_SELECT: return hf_launch_start_select_batch(A->ssel, ctl_for(b, ST_SELECT, -1), b->kp, s);
-        case ST_ARGMIN: return hf_launch_argmin_batch(A->main, ctl_for(b, ST_ARGMIN, -1), b->kp, b->hc, b->nt_a, s);
-        default: return hf_launch_refine_batch(A->main, ctl_for(b, ST_MAIN, 1), b->kp, b->nt_r, s);
+        case ST_LEARN: return hf_launch_learn_batch(A->learn, ctl_for(b, ST_LEARN, 0), b->kp, b->nt, s);
+        default: return hf_launch_fuse_batch(A->main, ctl_for(b, ST_MAIN, 1), b->kp, b->nt, b->hpad_max, s);
     }
 }
 
 // kernels of one run (the network's two GEMMs included)
-int kernels_per_run(const hf_batch* b) { return b->mlp ? 9 : 4; }
+int kernels_per_run(const hf_batch* b) { return b->mlp ? 7 : 3; }
 
 // the whole run: constants (and counter reset), then every stage in order; with ev (profiling,
 // eager only) an event is recorded after the constants and after every stage
@@ -227,10 +219,10 @@ cudaError_t enqueue(hf_batch* b, cudaEvent_t* ev = nullptr, int* stages_out = nu
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], b->stream);
     const bool learned = b->mlp != nullptr;
-    const int plain_stages[] = {ST_PROJECT, ST_ARGMIN, ST_MAIN};
-    const int learned_stages[] = {ST_PROJECT, ST_FEATURES, ST_MLP, ST_SELECT, ST_SHORT, ST_ARGMIN, ST_MAIN};
+    const int plain_stages[] = {ST_PROJECT, ST_MAIN};
+    const int learned_stages[] = {ST_PROJECT, ST_FEATURES, ST_MLP, ST_LEARN, ST_MAIN};
     const int* st = learned ? learned_stages : plain_stages;
-    const int n = learned ? 7 : 3;
+    const int n = learned ? 5 : 2;
     for (int q = 0; q < n && e == cudaSuccess; ++q) {
         e = launch_stage(b, st[q]);
         if (ev) cudaEventRecord(ev[2 + q], b->stream);
@@ -247,8 +239,9 @@ int time_stage(hf_batch* b, int stage, int reps, float* ms) {
     float best = INFINITY;
     for (int r = 0; r < reps; ++r) {
         cudaError_t e = cudaMemsetAsync(reinterpret_cast<unsigned*>(b->ctl + kNextOff) + stage, 0, 4, b->stream);
-        // the selection appends to the fallback and accepted lists: they start empty
-        if (e == cudaSuccess && stage == ST_SELECT) e = cudaMemsetAsync(b->ctl + kCountOff, 0, 2 * HF_MAX_BATCH * 4, b->stream);
+        // the learned stage appends to the fallback lists and adds to the work counts: they start empty
+        if (e == cudaSuccess && stage == ST_LEARN) e = cudaMemsetAsync(b->ctl + kCountOff, 0, HF_MAX_BATCH * 4, b->stream);
+        if (e == cudaSuccess && stage == ST_LEARN) e = cudaMemsetAsync(b->ctl + kFbWorkOff, 0, 2 * HF_MAX_BATCH * 8, b->stream);
         if (e == cudaSuccess) e = cudaEventRecord(b->t_beg, b->stream);
         if (e == cudaSuccess) e = launch_stage(b, stage);
         if (e == cudaSuccess) e = cudaEventRecord(b->t_end, b->stream);
@@ -269,53 +262,30 @@ int run_eager(hf_batch* b) {
     return HF_OK;
 }
 
-// Autotuner: candidate tile shapes timed on the batch itself.  The stages are re-run in pipeline
-// order, so every buffer a timed stage reads holds what the full run left there.
+// Autotuner: candidate launch shapes timed on the batch itself.  The stages are re-run in pipeline
+// order, so every buffer a timed stage reads holds what the full run left there.  The lanes per
+// point follow from each scene's view count (they fix the order of the sums, so they are not tuned:
+// a batched result stays bit-identical to the scene run alone).
 int autotune(hf_batch* b) {
     int rc;
-    const int hcs[] = {8, 16, 32};
     const int nts[] = {64, 128, 256};
     const bool learned = b->mlp != nullptr;
     if ((rc = configure(b)) || (rc = run_eager(b))) return rc;
-    // refinement: points per CTA (both refinement stages)
+    // threads per CTA of the cost kernels (the learned stage, then the fusion of the fallback points)
     float best = INFINITY;
-    int best_nt = b->nt_r;
+    int best_nt = b->nt;
     for (int nt : nts) {
-        if (b->cfg.points_per_cta && nt != b->cfg.points_per_cta) continue;
-        b->nt_r = nt;
+        if (b->cfg.cta_threads && nt != b->cfg.cta_threads) continue;
+        b->nt = nt;
         float t = 0.0f, t2 = 0.0f;
-        if (learned && (rc = time_stage(b, ST_SHORT, 2, &t2))) return rc;
-        if ((rc = time_stage(b, ST_ARGMIN, 1, &t))) return rc;
+        if (learned && (rc = time_stage(b, ST_LEARN, 2, &t2))) return rc;
         if ((rc = time_stage(b, ST_MAIN, 2, &t))) return rc;
         if (t + t2 < best) {
             best = t + t2;
             best_nt = nt;
         }
     }
-    b->nt_r = best_nt;
-    // argmin: hypothesis chunk x points per CTA (the constants are rebuilt for each chunk)
-    best = INFINITY;
-    int best_hc = b->hc, best_nta = b->nt_a;
-    for (int hc : hcs) {
-        if (b->cfg.hchunk && hc != b->cfg.hchunk) continue;
-        b->hc = hc;
-        if ((rc = configure(b))) return rc;
-        cudaError_t e = launch_prep(b, false);
-        if (e != cudaSuccess) return b_cuda(b, e, "autotune constants");
-        for (int nt : nts) {
-            if (b->cfg.points_per_cta && nt != b->cfg.points_per_cta) continue;
-            b->nt_a = nt;
-            float t = 0.0f;
-            if ((rc = time_stage(b, ST_ARGMIN, 2, &t))) return rc;
-            if (t < best) {
-                best = t;
-                best_hc = hc;
-                best_nta = nt;
-            }
-        }
-    }
-    b->hc = best_hc;
-    b->nt_a = best_nta;
+    b->nt = best_nt;
     // scene order: heaviest first (best balance at the end of a stage) against lightest first (small
     // scenes complete early); lightest first unless it costs more than 1 % of throughput
     if (!b->cfg.order) {
@@ -369,9 +339,8 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
     if (cfg) c = *cfg;
     if (mlp && (c.T_short < 1 || c.T_short > HF_MAX_T || !(c.alpha_short > 0.0f) || !(c.tau == c.tau)))
         return fail(HF_ERR_INVALID_ARG, "learned batch: T_short in [1, 24], alpha_short > 0 and a non-NaN tau required");
-    if (c.hchunk && c.hchunk != 8 && c.hchunk != 16 && c.hchunk != 32) return fail(HF_ERR_INVALID_ARG, "hchunk: 0, 8, 16 or 32");
-    if (c.points_per_cta && c.points_per_cta != 64 && c.points_per_cta != 128 && c.points_per_cta != 256)
-        return fail(HF_ERR_INVALID_ARG, "points_per_cta: 0, 64, 128 or 256");
+    if (c.cta_threads && c.cta_threads != 64 && c.cta_threads != 128 && c.cta_threads != 256)
+        return fail(HF_ERR_INVALID_ARG, "cta_threads: 0, 64, 128 or 256");
     if (c.order < 0 || c.order > 3) return fail(HF_ERR_INVALID_ARG, "order: 0, 1, 2 or 3");
     long long total = 0;
     int max_k = 0, maxH = 1;
@@ -392,8 +361,8 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
     b->user = (cudaStream_t)cuda_stream;
     b->total = total;
     b->kp = hf_batch_kp_for(max_k);
-    b->hc = c.hchunk ? c.hchunk : hf_fuse_chunk_for(maxH);
-    b->nt_a = b->nt_r = c.points_per_cta ? c.points_per_cta : 128;
+    b->hpad_max = hf_hpad(maxH);
+    b->nt = c.cta_threads ? c.cta_threads : 128;
     b->order = c.order ? c.order : 1;
     b->sc.resize(n_scenes);
     int rc = HF_OK;
@@ -411,7 +380,6 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
         if (e == cudaSuccess) e = cudaMalloc(&b->prop, (size_t)total * 3 * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&b->h1, (size_t)total * 256 * sizeof(uint16_t));
         if (e == cudaSuccess) e = cudaMalloc(&b->list, (size_t)total * sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMalloc(&b->acc_list, (size_t)total * sizeof(int32_t));
     }
     if (e != cudaSuccess) {
         hair_fuse_batch_destroy(b);
@@ -427,15 +395,12 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
         // per-(point, view) work: hypotheses, refinement candidates, patch members
         bs.work = (double)x->V * (x->cfg.H + 6.0 * x->cfg.T) * (x->k + 1);
         const int N = x->N, V = x->V, T = x->cfg.T;
-        const int Hpad = (x->cfg.H + 31) / 32 * 32;   // room for every hypothesis chunk
-        const size_t vn = (size_t)V * N;
-        if (!rc) rc = hf_ensure(x, x->samp, vn * sizeof(float2));
-        if (!rc) rc = hf_ensure(x, x->ab, vn * sizeof(float2));
-        if (!rc) rc = hf_ensure(x, x->qtab, (size_t)V * Hpad * sizeof(float4));
+        const int Hpad = hf_hpad(x->cfg.H);
+        if (!rc) rc = hf_ensure(x, x->samp, (size_t)N * hf_samp_stride(V) * sizeof(float2));
+        if (!rc) rc = hf_ensure(x, x->vmask, (size_t)N * hf_mask_words(V) * sizeof(unsigned long long));
         if (!rc) rc = hf_ensure(x, x->vthr, (size_t)V * sizeof(float));
         if (!rc) rc = hf_ensure(x, x->hyps, (size_t)Hpad * 3 * sizeof(float));
         if (!rc) rc = hf_ensure(x, x->rot, (size_t)(T > 0 ? T : 1) * sizeof(float2));
-        if (!rc) rc = hf_ensure(x, x->best, (size_t)N * 12);
         if (!rc && cudaStreamSynchronize(x->stream) != cudaSuccess) rc = HF_ERR_CUDA;   // uploads complete
         if (rc) g_batch_create_err = "scene " + std::to_string(s) + ": " + x->err;
     }
@@ -543,12 +508,10 @@ extern "C" int hair_fuse_batch_fallbacks(hf_batch* b, int* n_out) {
     return HF_OK;
 }
 
-extern "C" int hair_fuse_batch_tuning(const hf_batch* b, int* out4) {
-    if (!b || !out4) return HF_ERR_INVALID_ARG;
-    out4[0] = b->hc;
-    out4[1] = b->nt_a;
-    out4[2] = b->nt_r;
-    out4[3] = b->order;
+extern "C" int hair_fuse_batch_tuning(const hf_batch* b, int* out2) {
+    if (!b || !out2) return HF_ERR_INVALID_ARG;
+    out2[0] = b->nt;
+    out2[1] = b->order;
     return HF_OK;
 }
 
@@ -595,27 +558,15 @@ extern "C" int hair_fuse_batch_stats(hf_batch* b, long long* launches, long long
     if (!b) return HF_ERR_INVALID_ARG;
     if (launches) *launches = b->launches;
     if (!point_views && !fallback_point_views) return HF_OK;
-    cudaError_t e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return b_cuda(b, e, "stream synchronize");
     const int ns = (int)b->sc.size();
-    std::vector<unsigned long long> work(HF_MAX_BATCH);
-    std::vector<int> cnt(HF_MAX_BATCH);
-    e = cudaMemcpy(work.data(), b->ctl + kWorkOff, HF_MAX_BATCH * 8, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(cnt.data(), b->ctl + kCountOff, HF_MAX_BATCH * 4, cudaMemcpyDeviceToHost);
+    unsigned long long w[2 * HF_MAX_BATCH];
+    cudaError_t e = cudaMemcpyAsync(w, b->ctl + kWorkOff, sizeof w, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return b_cuda(b, e, "read work counters");
     long long pv = 0, fpv = 0;
     for (int p = 0; p < ns; ++p) {
-        pv += (long long)work[p];
-        if (!b->mlp || !fallback_point_views || cnt[p] <= 0) continue;
-        // view-set sizes of the fallback points (the argmin left them in the scene's view counts)
-        const BatchScene& s = b->sc[b->pos[p]];
-        const int N = s.c->N;
-        std::vector<int32_t> lst(cnt[p]), nvs(N);
-        e = cudaMemcpy(lst.data(), b->list + s.off, (size_t)cnt[p] * 4, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(nvs.data(), (int32_t*)s.c->best.p + 2 * (size_t)N, (size_t)N * 4, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return b_cuda(b, e, "read fallback view counts");
-        for (int q = 0; q < cnt[p]; ++q) fpv += nvs[lst[q]] > 0 ? nvs[lst[q]] : 0;
+        pv += (long long)w[p];
+        if (b->mlp) fpv += (long long)w[HF_MAX_BATCH + p];
     }
     if (point_views) *point_views = pv;
     if (fallback_point_views) *fallback_point_views = fpv;
@@ -633,7 +584,6 @@ extern "C" void hair_fuse_batch_destroy(hf_batch* b) {
     cudaFree(b->prop);
     cudaFree(b->h1);
     cudaFree(b->list);
-    cudaFree(b->acc_list);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->t_beg) cudaEventDestroy(b->t_beg);

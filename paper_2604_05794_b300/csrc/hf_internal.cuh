@@ -41,14 +41,12 @@ struct hf_ctx {
     int N = 0, k = 0;
     DevBuf pts, nbr;
     // scratch of the fusion path
-    DevBuf samp;    // [V][N] float2: C (cos theta, sin theta) at the point's pixel, 0 when not visible
-    DevBuf ab;      // [V][N] float2: projection ratios (X/Z, Y/Z); NaN when v is not in the point's view set
-    DevBuf qtab;    // [V][Hpad] float4: hypothesis pairs of (fx q_x, fx q_z) and (fy q_y, fy q_z), q = R_v h_m
+    DevBuf samp;    // [N][Vs] float2: C (cos theta, sin theta) at the point's pixel, 0 when not visible
+    DevBuf vmask;   // [N][Vw] u64: the point's view set V_i
     DevBuf vthr;    // [V] float: degenerate-offset threshold 1e-20 (fx^2 + fy^2)
     DevBuf hyps;    // [Hpad] x 3 float
     DevBuf rot;     // [T] float2: (cos alpha_t, sin alpha_t)
     DevBuf outs;    // device outputs staged for HF_HOST calls
-    DevBuf best;    // [N] x (int32 index, f32 cost, int32 view count) from argmin to refinement
     DevBuf evald;   // device copy of eval directions for HF_HOST calls
     DevBuf errw;    // uint32 device error word
     DevBuf work;    // uint64 (point, view) pairs of the last projection
@@ -67,6 +65,7 @@ struct hf_ctx {
     bool gbank_ok = false;
     long long views_gen = 0;   // bumped by every view upload
     long long depth_gen = -1;  // views_gen the FPMVO maps were built for
+    bool learned_ran = false;  // a learned fusion has filled the work counters
     uint32_t* errw_host = nullptr;  // pinned read-back slot
     long long launches = 0;
     long long dev_bytes = 0;
@@ -100,12 +99,24 @@ int run_launch(hf_ctx* c, const char* name, F&& f) {
 }
 
 // Kernel-launch helpers (defined in hf_kernels.cu); each returns the launch error -------------
+//
+// Scratch of the fusion path (per context, or the static array of the allocation-free entry):
+//   samp  [N][Vs] float2  C (cos theta, sin theta) at point i's own pixel in view v, 0 when the point
+//                         does not project into view v; Vs = V rounded up to 4 (32-byte rows)
+//   vmask [N][Vw] u64     bit v of word v / 64: v is in the point's view set V_i; Vw = ceil(V / 64)
+//   hyps  [Hpad][3] f32   the hypotheses, padded to an even count with copies of h_0
+//   vthr  [V] f32         degenerate-offset threshold 1e-20 (fx^2 + fy^2) per view
+//   rot   [T] float2      (cos alpha_t, sin alpha_t) of the refinement rounds
+__host__ __device__ inline int hf_samp_stride(int V) { return (V + 3) & ~3; }
+__host__ __device__ inline int hf_mask_words(int V) { return (V + 63) / 64; }
+__host__ __device__ inline int hf_hpad(int H) { return (H + 1) & ~1; }
+
 struct ProjectArgs {
     const float* pts; int N;
     const float* cams; int V; int W; int H;
     const float* angle; const void* conf; int conf_f16;
     int top_k;
-    float2* samp; float2* ab;
+    float2* samp; unsigned long long* vmask;
     unsigned long long* work;   // += number of (point, view) pairs in the view sets
     unsigned* box_keys;         // optional: bounding-box keys lo[3], hi[3] folded in (see hf_launch_bbox_init)
     const float2* amap;         // optional: interleaved (angle, confidence) maps, read instead of angle / conf
@@ -122,44 +133,52 @@ struct PrepArgs {
     const float* hyps_in;  // device H x 3, or nullptr for the Fibonacci set
     int H; int Hpad; int T;
     float* hyps;           // out Hpad x 3
-    float4* qtab;          // out [V][Hpad]
     float* vthr;           // out [V]
     float2* rot;           // out [T]
     uint32_t* errw;
 };
 cudaError_t hf_launch_prep(const PrepArgs& a, cudaStream_t s);
 
-struct FuseArgs {
+// The cost kernels: a point is served by a group of L lanes (L in {4, 8, 16, 32}) over which the
+// views of its view set are dealt; hf_cost_lanes() picks L from the largest view-set size.
+struct CostArgs {
     const float* pts; int N;
     const int32_t* nbr; int k;
     const float* cams; int V;
-    const float2* samp; const float2* ab;
-    const float4* qtab; const float* vthr;
+    const float2* samp; int Vs;
+    const unsigned long long* vmask; int Vw;
+    const float* vthr;
     const float* hyps; int H; int Hpad;
     const float2* rot; int T;
+    int L;                                               // lanes per point
     float* dir_out; float* cost_out; int32_t* idx_out; uint8_t* status_out;
-    int32_t* best_idx; float* best_cost; int32_t* nvs;   // [N] hand-off from argmin to refinement
-    int vblock_q, vblock_c;                              // views staged in shared memory per block
-    const int32_t* list; const int* list_count;          // optional: fuse only these points (device count)
-    const float* start_dir;                              // optional [N x 3]: refine from here, not hyps[best_idx]
+    int32_t* nvs;                                        // optional [N]: |V_i|, -1 for a non-finite point
+    const int32_t* list; const int* list_count;          // optional: only these points (device count)
     int fell_back;                                       // mark outputs HF_STATUS_FELL_BACK
     int out_first;   // outputs of point i go to row i - out_first (0: point-indexed)
 };
-int hf_fuse_chunk_for(int H);
-int hf_fuse_vblock_q(int V, int hchunk);
-int hf_fuse_vblock_c(int V);
-cudaError_t hf_launch_argmin(const FuseArgs& a, int hchunk, cudaStream_t s);   // K2
-cudaError_t hf_launch_refine(const FuseArgs& a, cudaStream_t s);               // K3
-cudaError_t hf_launch_fuse(const FuseArgs& a, int hchunk, cudaStream_t s);     // K2 then K3
+int hf_cost_lanes(int veff, int k);    // lanes per point for view sets of up to veff views
+struct hf_ctx;
+CostArgs hf_cost_args(const hf_ctx* c);   // the uploaded scene's arguments (outputs, list unset)
+cudaError_t hf_launch_fuse(const CostArgs& a, cudaStream_t s);   // argmin + refinement
+
+// Learned path after the network: the cost c_i of the proposal start_dir; points with a view and
+// c_i > tau are appended to fb_list (count *fb_count, from 0; work += |V_i| into fb_work), the
+// others get f.T rounds of the refinement from the proposal with steps f.rot (work into acc_work);
+// non-finite points get their BAD_INPUT outputs.  f.nvs (if set) receives |V_i|.
+struct LearnArgs {
+    CostArgs f;
+    const float* start_dir;
+    float tau;
+    int32_t* fb_list; int* fb_count;
+    unsigned long long* fb_work; unsigned long long* acc_work;
+};
+cudaError_t hf_launch_learn(const LearnArgs& a, cudaStream_t s);
 
 struct EvalArgs {
-    const float* pts; int N;
-    const int32_t* nbr; int k;
-    const float* cams; int V;
-    const float2* samp; const float2* ab;
-    const float* vthr;
+    CostArgs f;
     const float* dirs; int M;
-    float* cost_out;
+    float* cost;     // [N][M]
 };
 cudaError_t hf_launch_eval(const EvalArgs& a, cudaStream_t s);
 
@@ -176,16 +195,6 @@ struct FeatArgs {
     const float2* amap;         // optional: interleaved (angle, confidence) maps, read instead of angle / conf
 };
 cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s);
-// Cost c_i of f.start_dir and the view count -> f.best_cost, f.nvs (-1 for non-finite points, whose
-// BAD_INPUT outputs are written here); points with a view and c_i > tau are appended to f.list
-// (count *f.list_count), the other finite points to acc_list (*acc_count); counts start at 0.
-struct StartSelectArgs {
-    FuseArgs f;
-    float tau;
-    int32_t* acc_list;
-    int* acc_count;
-};
-cudaError_t hf_launch_start_select(const StartSelectArgs& a, cudaStream_t s);
 // (cos, sin) of alpha0 / 2^t for t < T, in double then rounded
 cudaError_t hf_launch_rot(float2* rot, int T, double alpha0, cudaStream_t s);
 cudaError_t hf_launch_check_nbr(const int32_t* nbr, long long n, int N, uint32_t* errw, cudaStream_t s);
@@ -215,11 +224,10 @@ int hf_batch_kp_for(int k);   // patch width instantiated for the batched kernel
 cudaError_t hf_launch_prep_batch(const PrepArgs* pr, int ns, const BatchReset& r, cudaStream_t s);
 cudaError_t hf_launch_project_batch(const ProjectArgs* pa, const BatchCtl& c, cudaStream_t s);
 cudaError_t hf_launch_features_batch(const FeatArgs* fe, const BatchCtl& c, cudaStream_t s);
-cudaError_t hf_launch_start_select_batch(const StartSelectArgs* sa, const BatchCtl& c, int kp, cudaStream_t s);
-// nt: points per CTA (64, 128, 256); hc: hypothesis chunk (8, 16, 32; the scenes' Hpad and
-// vblock_q must be built for it); kp from hf_batch_kp_for(max k)
-cudaError_t hf_launch_argmin_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int hc, int nt, cudaStream_t s);
-cudaError_t hf_launch_refine_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int nt, cudaStream_t s);
+// nt: threads per CTA of the cost kernels (64, 128 or 256); kp from hf_batch_kp_for(max k); hpad_max
+// the largest Hpad of the scenes
+cudaError_t hf_launch_fuse_batch(const CostArgs* fa, const BatchCtl& c, int kp, int nt, int hpad_max, cudaStream_t s);
+cudaError_t hf_launch_learn_batch(const LearnArgs* la, const BatchCtl& c, int kp, int nt, cudaStream_t s);
 
 // ------------------------------------------------------------------ FPMVO (hf_fpmvo.cu)
 #define HF_FPMVO_MAX_K 8

@@ -1,13 +1,15 @@
 // hf_kernels.cu - the fusion path's device code for sm_103a.
 //
-//   k_prep          per-scene constants: hypothesis table q = R_v h_m (folded with fx, fy),
-//                   degenerate thresholds, refinement rotation steps.
+//   k_prep          per-scene constants: hypotheses (padded to an even count), degenerate
+//                   thresholds, refinement rotation steps.
 //   k_project       K1, thread per point: projection of the point into every view with the pixel
 //                   index decided in float-float arithmetic, nearest-pixel gather of the orientation
 //                   and confidence maps, view set (visible or top-K) of the point.
-//   k_argmin<HC,KP> K2, thread per point: cost of all hypotheses (Eqs. proj_r .. patch_min and the
-//                   view mean) and their argmin.
-//   k_refine<KP>    K3, thread per point: T rounds of the six-rotation refinement, final outputs.
+//   k_fuse<KP>      K2 + K3, a group of lanes per point: the cost of every hypothesis (Eqs. proj_r ..
+//                   patch_min and the view mean), their argmin, then the T rounds of the six-rotation
+//                   refinement, from one gather of the point's patch held in registers.
+//   k_learn<KP>     the learned path after the network: cost of the proposal, fallback selection,
+//                   short refinement of the accepted proposals.
 //   k_eval<KP>      cost of caller-given directions (no argmin).
 #include <math.h>
 
@@ -25,12 +27,6 @@ __device__ __forceinline__ float load_conf(const void* conf, int f16, size_t o) 
     return reinterpret_cast<const float*>(conf)[o];
 }
 
-// ------------------------------------------------------------------ K1: project + gather
-// One thread per point, views in order.  For view v it writes
-//   samp[v][i] = C (cos theta, sin theta) at the point's pixel (0 when outside the view),
-//   ab[v][i]   = (X/Z, Y/Z) when v is in the point's view set, NaN otherwise.
-// The view set is every view the point projects into, or with top_k > 0 the top_k of them by the
-// confidence at the point's own pixel, ties to the lower view index.
 // Order-preserving integer encoding of floats (exact, order-independent min / max by atomics).
 __device__ __forceinline__ unsigned fkey(float x) {
     const unsigned u = __float_as_uint(x);
@@ -38,6 +34,12 @@ __device__ __forceinline__ unsigned fkey(float x) {
 }
 __device__ __forceinline__ float fval(unsigned k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k); }
 
+// ------------------------------------------------------------------ K1: project + gather
+// One thread per point, views in groups of four.  For view v it writes
+//   samp[i][v] = C (cos theta, sin theta) at the point's pixel (0 when outside the view),
+// four views (one 32-byte sector of the row) at a time, and the point's view-set mask: every view
+// the point projects into, or with top_k > 0 the top_k of them by the confidence at the point's own
+// pixel, ties to the lower view index.
 constexpr int kProjectThreads = 128;
 
 // With a.box_keys set, the tile also folds its finite coordinates into the point cloud's bounding
@@ -62,19 +64,20 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
     if (i >= a.N) return;
     const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
     const size_t npx = (size_t)a.W * a.H;
-    const float qnan = __int_as_float(0x7fc00000);
+    const int Vs = hf_samp_stride(a.V), Vw = hf_mask_words(a.V);
+    float4* row = reinterpret_cast<float4*>(a.samp + (size_t)i * Vs);
+    unsigned long long* mrow = a.vmask + (size_t)i * Vw;
     float topc[HF_MAX_TOPK];
     int topv[HF_MAX_TOPK];
     int ntop = 0, nset = 0;
+    unsigned long long word = 0ull;
     // views in groups of four: the pixel decisions first, then the four gathers in flight together
     constexpr int G = 4;
     for (int v0 = 0; v0 < a.V; v0 += G) {
         long long off[G];
-        float ra_[G], rb_[G];
 #pragma unroll
         for (int q = 0; q < G; ++q) {
             off[q] = -1;
-            ra_[q] = rb_[q] = qnan;
             const int v = v0 + q;
             if (v >= a.V) continue;
             const float* cam = a.cams + 16 * v;
@@ -83,13 +86,10 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
             const ff X1 = ff_dot3_plus(__ldg(cam + 7), __ldg(cam + 8), __ldg(cam + 9), p0, p1, p2, __ldg(cam + 14));
             const ff X2 = ff_dot3_plus(__ldg(cam + 10), __ldg(cam + 11), __ldg(cam + 12), p0, p1, p2, __ldg(cam + 15));
             if (!(X2.hi > 1e-6f)) continue;
-            const ff ra = ff_div(X0, X2), rb = ff_div(X1, X2);
-            const float fu = ff_floor(ff_affine(fx, ra, cx));
-            const float fv = ff_floor(ff_affine(fy, rb, cy));
+            const float fu = ff_floor(ff_affine(fx, ff_div(X0, X2), cx));
+            const float fv = ff_floor(ff_affine(fy, ff_div(X1, X2), cy));
             if (!(fu >= 0.0f && fu < (float)a.W && fv >= 0.0f && fv < (float)a.H)) continue;
             off[q] = (long long)((size_t)v * npx + (size_t)fv * a.W + (size_t)fu);
-            ra_[q] = ra.hi;
-            rb_[q] = rb.hi;
         }
         float th[G], C[G];
 #pragma unroll
@@ -105,41 +105,46 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
                 C[q] = load_conf(a.conf, a.conf_f16, (size_t)off[q]);
             }
         }
+        float sv[2 * G];
 #pragma unroll
         for (int q = 0; q < G; ++q) {
+            sv[2 * q] = sv[2 * q + 1] = 0.0f;
+            if (off[q] < 0) continue;
+            float sn, cs;
+            sincosf(th[q], &sn, &cs);
+            sv[2 * q] = C[q] * cs;
+            sv[2 * q + 1] = C[q] * sn;
             const int v = v0 + q;
-            if (v >= a.V) break;
-            float2 sv = make_float2(0.0f, 0.0f), r = make_float2(qnan, qnan);
-            if (off[q] >= 0) {
-                float sn, cs;
-                sincosf(th[q], &sn, &cs);
-                sv = make_float2(C[q] * cs, C[q] * sn);
-                r = make_float2(ra_[q], rb_[q]);
-                ++nset;
-                if (TOPK) {
-                    // keep the top_k (conf desc, view asc); later views need a strictly larger conf
-                    const float c = C[q];
-                    if (ntop < a.top_k || c > topc[ntop - 1]) {
-                        int pos = ntop < a.top_k ? ntop++ : ntop - 1;
-                        while (pos > 0 && c > topc[pos - 1]) {
-                            topc[pos] = topc[pos - 1];
-                            topv[pos] = topv[pos - 1];
-                            --pos;
-                        }
-                        topc[pos] = c;
-                        topv[pos] = v;
+            word |= 1ull << (v & 63);
+            if (TOPK) {
+                // keep the top_k (conf desc, view asc); later views need a strictly larger conf
+                const float c = C[q];
+                if (ntop < a.top_k || c > topc[ntop - 1]) {
+                    int pos = ntop < a.top_k ? ntop++ : ntop - 1;
+                    while (pos > 0 && c > topc[pos - 1]) {
+                        topc[pos] = topc[pos - 1];
+                        topv[pos] = topv[pos - 1];
+                        --pos;
                     }
+                    topc[pos] = c;
+                    topv[pos] = v;
                 }
             }
-            a.samp[(size_t)v * a.N + i] = sv;
-            a.ab[(size_t)v * a.N + i] = r;
+        }
+        row[v0 / 2] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+        row[v0 / 2 + 1] = make_float4(sv[4], sv[5], sv[6], sv[7]);
+        if (((v0 + G) & 63) == 0 || v0 + G >= a.V) {   // a mask word is complete
+            if (!TOPK) mrow[v0 >> 6] = word;
+            nset += __popcll(word);
+            word = 0ull;
         }
     }
     if (TOPK) {
-        for (int v = 0; v < a.V; ++v) {
-            bool keep = false;
-            for (int q = 0; q < ntop; ++q) keep |= (topv[q] == v);
-            if (!keep) a.ab[(size_t)v * a.N + i] = make_float2(qnan, qnan);
+        for (int w = 0; w < Vw; ++w) {
+            unsigned long long m = 0ull;
+            for (int q = 0; q < ntop; ++q)
+                if ((topv[q] >> 6) == w) m |= 1ull << (topv[q] & 63);
+            mrow[w] = m;
         }
         nset = ntop;
     }
@@ -201,24 +206,6 @@ __device__ __forceinline__ void prep_body(const PrepArgs& a) {
         }
         for (int q = 0; q < 3; ++q) a.hyps[3 * m + q] = (float)h[q];
     }
-    __syncthreads();
-    // hypothesis pairs (m, m+1) interleaved for packed evaluation, q = R_v h:
-    //   qtab[v][m]   = (fx q_x(m), fx q_x(m+1), fx q_z(m), fx q_z(m+1))
-    //   qtab[v][m+1] = (fy q_y(m), fy q_y(m+1), fy q_z(m), fy q_z(m+1))
-    for (int e = threadIdx.x; e < a.V * (a.Hpad / 2); e += blockDim.x) {
-        const int v = e / (a.Hpad / 2), m = 2 * (e % (a.Hpad / 2));
-        const float* cam = a.cams + 16 * v;
-        double q[2][3];
-        for (int h = 0; h < 2; ++h)
-            for (int r = 0; r < 3; ++r)
-                q[h][r] = (double)cam[4 + 3 * r] * a.hyps[3 * (m + h)] + (double)cam[5 + 3 * r] * a.hyps[3 * (m + h) + 1] +
-                          (double)cam[6 + 3 * r] * a.hyps[3 * (m + h) + 2];
-        const double fx = cam[0], fy = cam[1];
-        a.qtab[(size_t)v * a.Hpad + m] =
-            make_float4((float)(fx * q[0][0]), (float)(fx * q[1][0]), (float)(fx * q[0][2]), (float)(fx * q[1][2]));
-        a.qtab[(size_t)v * a.Hpad + m + 1] =
-            make_float4((float)(fy * q[0][1]), (float)(fy * q[1][1]), (float)(fy * q[0][2]), (float)(fy * q[1][2]));
-    }
     for (int v = threadIdx.x; v < a.V; v += blockDim.x) {
         const double fx = a.cams[16 * v], fy = a.cams[16 * v + 1];
         a.vthr[v] = (float)(1e-20 * (fx * fx + fy * fy));
@@ -231,29 +218,26 @@ __device__ __forceinline__ void prep_body(const PrepArgs& a) {
 
 __global__ void k_prep(PrepArgs a) { prep_body(a); }
 
-// ------------------------------------------------------------------ K2 + K3
-// Patch term of one direction in one view: r = (rx, ry) is Z times the image offset (the scale
-// cancels), s[] the patch samples C (cos theta, sin theta).  Returns max_j |<r, s_j>| / |r|, or 0
-// when |r|^2 is below the degenerate threshold.
-template <int KP>
-__device__ __forceinline__ float view_term(float rx, float ry, const float2 (&s)[KP], float thr) {
-    const float r2 = fmaf(rx, rx, ry * ry);
-    float mx = 0.0f;
-#pragma unroll
-    for (int j = 0; j < KP; ++j) mx = fmaxf(mx, fabsf(fmaf(rx, s[j].x, ry * s[j].y)));
-    return r2 >= thr ? mx * rsqrtf(r2) : 0.0f;
-}
-
-template <int KP>
-__device__ __forceinline__ void load_patch(const float2* __restrict__ samp, size_t base, int i, const int (&nb)[KP],
-                                           float2 (&s)[KP]) {
-    s[0] = samp[base + i];
-#pragma unroll
-    for (int j = 1; j < KP; ++j) s[j] = nb[j] >= 0 ? samp[base + nb[j]] : make_float2(0.0f, 0.0f);
-}
-
-// ---- packed FP32 pairs (sm_100+ fma/mul .f32x2): each lane is rounded exactly like the scalar
-// instruction, so the packed evaluation gives the same bits as view_term() lane by lane.
+// ------------------------------------------------------------------ K2 + K3: the cost kernels
+//
+// A point is served by a group of L lanes (L in {4, 8, 16, 32}; 32 / L points per warp).  The views
+// of the point's view set V_i, in view order, are dealt to the lanes: member n of V_i goes to lane
+// n mod L, slot (n / L) mod SM, chunk n / (L SM).  Per chunk a lane gathers, for each of its slots,
+// the projection Jacobian of its view at the point (single precision, scaled by Z, which cancels),
+// the view's degenerate threshold and the samples C (cos theta, sin theta) of the k + 1 patch
+// members at their own pixels.  With one chunk (|V_i| <= L SM, the usual case) these stay in
+// registers while every direction is evaluated: the H hypotheses, then the T rounds of six
+// rotations.  A direction's patch terms are summed over the lane's slots and then over the group
+// by a butterfly of shuffles, which leaves the bitwise-same sum in every lane of the group; every
+// lane therefore takes the same decisions.  Larger view sets are processed chunk by chunk (the
+// chunk gathered again for every direction).
+//
+// The patch term of a direction d in view v (Eqs. proj_r, sim, patchloss, patch_min):
+//   r = J d (Z times the image offset), L_v = max_j |<r, s_j>| / |r|, 0 when |r|^2 < threshold;
+// the members are evaluated in pairs with packed FP32 instructions (fma.rn.f32x2 / mul.rn.f32x2,
+// each lane rounded exactly like the scalar instruction) and folded into the running maximum with
+// the three-input max.f32 of two absolute values.  The cost is c = 1 - (sum_v L_v) / |V_i| (Eq.
+// final_dout with the view mean); minimising c is maximising the sum, which the kernels compare.
 typedef unsigned long long f32x2;
 __device__ __forceinline__ f32x2 pk(float a, float b) {
     f32x2 r;
@@ -271,310 +255,234 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+// max(m, |a|, |b|)
+__device__ __forceinline__ float max3abs(float m, float a, float b) {
+    float r;
+    asm("{ .reg .f32 t, u; abs.f32 t, %1; abs.f32 u, %2; max.f32 %0, %3, t, u; }" : "=f"(r) : "f"(a), "f"(b), "f"(m));
+    return r;
+}
 
-// Patch terms of two directions in one view: (rx, ry) hold the pair's offsets, SX/SY the patch
-// samples broadcast to both lanes.
+// slots per lane for a patch width: the patch data of a slot is 2 KP + 7 registers
 template <int KP>
-__device__ __forceinline__ void view_term2(f32x2 rx, f32x2 ry, const f32x2 (&SX)[KP], const f32x2 (&SY)[KP],
-                                           float thr0, float thr1, float& L0, float& L1) {
-    const f32x2 r2 = fma2(rx, rx, mul2(ry, ry));
-    float mx0 = 0.0f, mx1 = 0.0f;
-#pragma unroll
-    for (int j = 0; j < KP; ++j) {
-        float u0, u1;
-        upk(fma2(rx, SX[j], mul2(ry, SY[j])), u0, u1);
-        mx0 = fmaxf(mx0, fabsf(u0));
-        mx1 = fmaxf(mx1, fabsf(u1));
-    }
-    float a0, a1;
-    upk(r2, a0, a1);
-    L0 = a0 >= thr0 ? mx0 * rsqrtf(a0) : 0.0f;
-    L1 = a1 >= thr1 ? mx1 * rsqrtf(a1) : 0.0f;
-}
-
-// ---- shared-memory staging
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-constexpr int kFuseThreads = 128;
-constexpr size_t kQStageBytes = 16384;   // hypothesis-table slice staged per view block
-constexpr int kCamStageViews = 256;      // camera rows staged per view block
-
-// Per-thread ring of S views of patch data: item 0 = the point's (a, b), items 1..KP = the patch
-// samples; laid out [stage][item][thread] so a warp reads consecutive 8-byte words.  View v lives
-// in stage v % S and is copied in S - 1 views ahead of its use.
-template <int KP, int S, int NT>
-struct PatchStage {
-    float2 v[S][KP + 1][NT];
+struct SlotsFor {
+    static constexpr int value = KP <= 9 ? 4 : 2;
 };
-constexpr int kArgminStages = 2;
-constexpr int kRefineStages = 2;
 
-// Queue the copies of one view's patch data into stage st (one commit group per call, also when
-// the thread has nothing to copy, so that group counting stays uniform).
-template <int KP, int S, int NT>
-__device__ __forceinline__ void issue_patch(PatchStage<KP, S, NT>& sg, int st, const float2* __restrict__ ab,
-                                            const float2* __restrict__ samp, size_t base, int i, const int (&nb)[KP],
-                                            bool active) {
-    const int t = threadIdx.x;
-    if (active) {
-        cp_async8(&sg.v[st][0][t], ab + base + i);
-        cp_async8(&sg.v[st][1][t], samp + base + i);
-#pragma unroll
-        for (int j = 1; j < KP; ++j)
-            if (nb[j] >= 0) cp_async8(&sg.v[st][1 + j][t], samp + base + nb[j]);
-    }
-    cp_async_commit();
-}
+// One view of the point held by a lane.
+template <int KP>
+struct Slot {
+    static constexpr int NP = KP / 2 > 0 ? KP / 2 : 1;
+    float j0, j1, j2, j3, j4, j5;   // rows of Z x the projection Jacobian: fx (R_0 - a R_2), fy (R_1 - b R_2)
+    float thr;                      // degenerate threshold of the view; +inf for an empty slot
+    f32x2 sx[NP], sy[NP];           // members 2q, 2q+1 (q < KP / 2): (x_2q, x_2q+1), (y_2q, y_2q+1)
+    float ox, oy;                   // member KP - 1 when KP is odd
+};
 
-template <int KP, int S, int NT>
-__device__ __forceinline__ void load_nbrs(const FuseArgs& a, int i, bool active, int (&nb)[KP], PatchStage<KP, S, NT>& sg) {
-    nb[0] = active ? i : -1;
+template <int KP>
+__device__ __forceinline__ float patch_term(const Slot<KP>& s, float d0, float d1, float d2, float thr) {
+    const float rx = fmaf(s.j0, d0, fmaf(s.j1, d1, __fmul_rn(s.j2, d2)));
+    const float ry = fmaf(s.j3, d0, fmaf(s.j4, d1, __fmul_rn(s.j5, d2)));
+    const float r2 = fmaf(rx, rx, __fmul_rn(ry, ry));
+    float m = 0.0f;
+    if (KP & 1) m = fabsf(fmaf(rx, s.ox, __fmul_rn(ry, s.oy)));
+    if (KP >= 2) {
+        const f32x2 RX = pk(rx, rx), RY = pk(ry, ry);
 #pragma unroll
-    for (int j = 1; j < KP; ++j) nb[j] = (active && (j - 1) < a.k) ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
-    // padded / inactive members read as zero samples in every stage, never overwritten
-#pragma unroll
-    for (int j = 1; j < KP; ++j)
-        if (nb[j] < 0)
-#pragma unroll
-            for (int st = 0; st < S; ++st) sg.v[st][1 + j][threadIdx.x] = make_float2(0.0f, 0.0f);
-}
-
-template <int KP, int S, int NT>
-__device__ __forceinline__ void stage_samples(const PatchStage<KP, S, NT>& sg, int st, f32x2 (&SX)[KP], f32x2 (&SY)[KP]) {
-#pragma unroll
-    for (int j = 0; j < KP; ++j) {
-        const float2 sj = sg.v[st][1 + j][threadIdx.x];
-        SX[j] = pk(sj.x, sj.x);
-        SY[j] = pk(sj.y, sj.y);
-    }
-}
-
-// K2: cost of every hypothesis and the argmin (lowest index on ties), thread per point.  The
-// hypothesis table of HC hypotheses x a block of views sits in shared memory; the next view's
-// patch data is copied in (cp.async) while the current view is evaluated, two hypotheses at a time.
-template <int HC, int KP, int NT>
-__device__ __forceinline__ void argmin_tile(const FuseArgs& a, int blk, unsigned char* smem_raw) {
-    constexpr int S = kArgminStages;
-    PatchStage<KP, S, NT>& sg = *reinterpret_cast<PatchStage<KP, S, NT>*>(smem_raw);
-    float4* qs = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP, S, NT>));   // [view in block][HC]
-    const int tid = threadIdx.x;
-    const int cnt = a.list ? *a.list_count : a.N;
-    if (blk * NT >= cnt) return;   // whole block past the list: uniform exit
-    const int t_ = blk * NT + tid;
-    const int i = t_ < cnt ? (a.list ? a.list[t_] : t_) : -1;
-    bool active = i >= 0;
-    if (active) {
-        const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
-        if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) {
-            a.nvs[i] = -1;
-            active = false;
+        for (int q = 0; q < KP / 2; ++q) {
+            float u0, u1;
+            upk(fma2(RX, s.sx[q], mul2(RY, s.sy[q])), u0, u1);
+            m = max3abs(m, u0, u1);
         }
     }
-    int nb[KP];
-    load_nbrs<KP, S, NT>(a, i, active, nb, sg);
-    float best = INFINITY;
-    int bestm = 0, nv = 0;
-    for (int c0 = 0; c0 < a.Hpad; c0 += HC) {
-        float acc[HC];
+    return r2 >= thr ? __fmul_rn(m, rsqrtf(r2)) : 0.0f;
+}
+
+// the n-th (from 0) set bit of a mask word
+__device__ __forceinline__ int nth_bit(unsigned long long x, int n) {
+    const unsigned lo = (unsigned)x, hi = (unsigned)(x >> 32);
+    const int cl = __popc(lo);
+    return n < cl ? (int)__fns(lo, 0, n + 1) : 32 + (int)__fns(hi, 0, n - cl + 1);
+}
+
+// the view of member n of a point's view set, or -1
+__device__ __forceinline__ int nth_view(const CostArgs& a, int i, unsigned long long w0, int n) {
+    if (a.Vw == 1) return n < __popcll(w0) ? nth_bit(w0, n) : -1;
+    const unsigned long long* m = a.vmask + (size_t)i * a.Vw;
+    for (int w = 0; w < a.Vw; ++w) {
+        const unsigned long long x = w ? m[w] : w0;
+        const int c = __popcll(x);
+        if (n < c) return 64 * w + nth_bit(x, n);
+        n -= c;
+    }
+    return -1;
+}
+
+// Per-point state of a lane's group.
+template <int KP>
+struct PointCtx {
+    int i;           // point index (0 for a group without a point)
+    bool in;         // the group has a point
+    bool finite;     // its coordinates are finite
+    int nv;          // |V_i|
+    unsigned long long w0;   // first mask word
+    float p0, p1, p2;
+    int nb[KP];      // patch members: the point, its neighbours, -1 past k
+};
+
+template <int KP>
+__device__ __forceinline__ void point_ctx(const CostArgs& a, int q, int cnt, PointCtx<KP>& pc) {
+    pc.in = q < cnt;
+    pc.i = pc.in ? (a.list ? a.list[q] : q) : 0;
+    const int i = pc.i;
+    pc.p0 = a.pts[3 * i];
+    pc.p1 = a.pts[3 * i + 1];
+    pc.p2 = a.pts[3 * i + 2];
+    pc.finite = pc.in && isfinite(pc.p0) && isfinite(pc.p1) && isfinite(pc.p2);
+    pc.w0 = pc.finite ? a.vmask[(size_t)i * a.Vw] : 0ull;
+    int nv = __popcll(pc.w0);
+    if (pc.finite)
+        for (int w = 1; w < a.Vw; ++w) nv += __popcll(a.vmask[(size_t)i * a.Vw + w]);
+    pc.nv = nv;
+    pc.nb[0] = pc.finite ? i : -1;
 #pragma unroll
-        for (int m = 0; m < HC; ++m) acc[m] = 0.0f;
-        nv = 0;
-        for (int p = 0; p < S - 1; ++p)
-            if (p < a.V) issue_patch<KP, S, NT>(sg, p, a.ab, a.samp, (size_t)p * a.N, i, nb, active);
-            else cp_async_commit();
-        for (int vb = 0; vb < a.V; vb += a.vblock_q) {
-            const int nvb = min(a.vblock_q, a.V - vb);
-            __syncthreads();
-            for (int e = tid; e < nvb * HC; e += NT)
-                qs[e] = a.qtab[(size_t)(vb + e / HC) * a.Hpad + c0 + e % HC];
-            __syncthreads();
-            for (int v = vb; v < vb + nvb; ++v) {
-                const int vn = v + S - 1;
-                if (vn < a.V) issue_patch<KP, S, NT>(sg, vn % S, a.ab, a.samp, (size_t)vn * a.N, i, nb, active);
-                else cp_async_commit();
-                cp_async_wait<S - 1>();
-                if (!active) continue;
-                const int st = v % S;
-                const float2 r = sg.v[st][0][tid];
-                if (r.x != r.x) continue;
-                ++nv;
-                f32x2 SX[KP], SY[KP];
-                stage_samples<KP, S, NT>(sg, st, SX, SY);
-                const f32x2 na = pk(-r.x, -r.x), nb2 = pk(-r.y, -r.y);
-                const float thr = __ldg(a.vthr + v);
-                const float4* q = qs + (v - vb) * HC;
+    for (int j = 1; j < KP; ++j) pc.nb[j] = (pc.finite && (j - 1) < a.k) ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
+}
+
+// Gather chunk `chunk` of the point's view set into the lane's slots (slots >= ns stay empty).
+template <int KP, int SM>
+__device__ __forceinline__ void gather(const CostArgs& a, const PointCtx<KP>& pc, int lg, int chunk, int ns,
+                                       Slot<KP> (&S)[SM]) {
 #pragma unroll
-                for (int m = 0; m < HC; m += 2) {
-                    // hypotheses m, m+1: rx = fx q_x - a fx q_z, ry = fy q_y - b fy q_z
-                    const float4 QA = q[m], QB = q[m + 1];
-                    float L0, L1;
-                    view_term2<KP>(fma2(na, pk(QA.z, QA.w), pk(QA.x, QA.y)), fma2(nb2, pk(QB.z, QB.w), pk(QB.x, QB.y)),
-                                   SX, SY, thr, thr, L0, L1);
-                    acc[m] += L0;
-                    acc[m + 1] += L1;
-                }
+    for (int s = 0; s < SM; ++s) {
+        Slot<KP>& q = S[s];
+        const int n = (chunk * SM + s) * a.L + lg;
+        const int v = (s < ns && n < pc.nv) ? nth_view(a, pc.i, pc.w0, n) : -1;
+        float2 sm[KP];
+        if (v < 0) {
+            q.j0 = q.j1 = q.j2 = q.j3 = q.j4 = q.j5 = 0.0f;
+            q.thr = INFINITY;
+#pragma unroll
+            for (int j = 0; j < KP; ++j) sm[j] = make_float2(0.0f, 0.0f);
+        } else {
+            const float* cam = a.cams + 16 * v;
+            const float fx = __ldg(cam), fy = __ldg(cam + 1);
+            const float r00 = __ldg(cam + 4), r01 = __ldg(cam + 5), r02 = __ldg(cam + 6);
+            const float r10 = __ldg(cam + 7), r11 = __ldg(cam + 8), r12 = __ldg(cam + 9);
+            const float r20 = __ldg(cam + 10), r21 = __ldg(cam + 11), r22 = __ldg(cam + 12);
+            const float X = fmaf(r00, pc.p0, fmaf(r01, pc.p1, fmaf(r02, pc.p2, __ldg(cam + 13))));
+            const float Y = fmaf(r10, pc.p0, fmaf(r11, pc.p1, fmaf(r12, pc.p2, __ldg(cam + 14))));
+            const float Z = fmaf(r20, pc.p0, fmaf(r21, pc.p1, fmaf(r22, pc.p2, __ldg(cam + 15))));
+            const float iz = 1.0f / Z;
+            const float ra = __fmul_rn(X, iz), rb = __fmul_rn(Y, iz);
+            q.j0 = __fmul_rn(fx, fmaf(-ra, r20, r00));
+            q.j1 = __fmul_rn(fx, fmaf(-ra, r21, r01));
+            q.j2 = __fmul_rn(fx, fmaf(-ra, r22, r02));
+            q.j3 = __fmul_rn(fy, fmaf(-rb, r20, r10));
+            q.j4 = __fmul_rn(fy, fmaf(-rb, r21, r11));
+            q.j5 = __fmul_rn(fy, fmaf(-rb, r22, r12));
+            q.thr = __ldg(a.vthr + v);
+#pragma unroll
+            for (int j = 0; j < KP; ++j)
+                sm[j] = pc.nb[j] >= 0 ? __ldg(a.samp + (size_t)pc.nb[j] * a.Vs + v) : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int p = 0; p < KP / 2; ++p) {
+            q.sx[p] = pk(sm[2 * p].x, sm[2 * p + 1].x);
+            q.sy[p] = pk(sm[2 * p].y, sm[2 * p + 1].y);
+        }
+        if (KP & 1) {
+            q.ox = sm[KP - 1].x;
+            q.oy = sm[KP - 1].y;
+        }
+    }
+}
+
+__device__ __forceinline__ float group_sum(float x, int L) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1)
+        if (o < L) x = __fadd_rn(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Group sums of the patch terms of ND directions (all lanes of the warp take part).  With one chunk
+// the slots hold the data (ns of them in use); otherwise each chunk is gathered again here.
+template <int KP, int SM, int ND>
+__device__ __forceinline__ void dir_sums(const CostArgs& a, const PointCtx<KP>& pc, int lg, int nch, int ns,
+                                         Slot<KP> (&S)[SM], const float (&d)[ND][3], float tscale, float (&out)[ND]) {
+#pragma unroll
+    for (int q = 0; q < ND; ++q) out[q] = 0.0f;
+    for (int c = 0; c < nch; ++c) {
+        if (nch > 1) gather<KP, SM>(a, pc, lg, c, SM, S);
+#pragma unroll
+        for (int s = 0; s < SM; ++s) {
+            if (s < ns || nch > 1) {
+#pragma unroll
+                for (int q = 0; q < ND; ++q)
+                    out[q] = __fadd_rn(out[q], patch_term<KP>(S[s], d[q][0], d[q][1], d[q][2], __fmul_rn(S[s].thr, tscale)));
             }
         }
-        cp_async_wait<0>();
+    }
 #pragma unroll
-        for (int m = 0; m < HC; ++m) {
-            const float c = nv ? 1.0f - acc[m] / (float)nv : 1.0f;
-            if (c0 + m < a.H && c < best) {
-                best = c;
-                bestm = c0 + m;
-            }
-        }
-    }
-    if (active) {
-        a.best_idx[i] = bestm;
-        a.best_cost[i] = best;
-        a.nvs[i] = nv;
-    }
+    for (int q = 0; q < ND; ++q) out[q] = group_sum(out[q], a.L);
 }
 
-template <int HC, int KP>
-__global__ void __launch_bounds__(kFuseThreads) k_argmin(FuseArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    argmin_tile<HC, KP, kFuseThreads>(a, blockIdx.x, smem_raw);
+// Group geometry of the calling lane for tile `tile`: returns false when the whole warp is past
+// the end of the work list (a warp-uniform exit).
+struct Lanes {
+    int lane, lg, g, q;   // lane, lane in group, group in warp, work-list position of the group
+};
+__device__ __forceinline__ bool lanes_of(int L, int tile, int cnt, Lanes& ln) {
+    ln.lane = threadIdx.x & 31;
+    ln.lg = ln.lane & (L - 1);
+    ln.g = ln.lane / L;
+    const int ppw = 32 / L;
+    const int w = tile * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    ln.q = w * ppw + ln.g;
+    return w * ppw < cnt;
 }
 
-// K3: T rounds of +-alpha rotations about world x, y, z from the argmin; move to the first strictly
-// lowest cost; halve alpha.  The two candidates of one axis are evaluated as a packed pair.
-template <int KP, int NT>
-__device__ __forceinline__ void refine_tile(const FuseArgs& a, int blk, unsigned char* smem_raw) {
-    constexpr int S = kRefineStages;
-    PatchStage<KP, S, NT>& sg = *reinterpret_cast<PatchStage<KP, S, NT>*>(smem_raw);
-    float4* cs4 = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP, S, NT>));   // [view in block][3]
-    const int tid = threadIdx.x;
-    const int cnt = a.list ? *a.list_count : a.N;
-    if (blk * NT >= cnt) return;   // whole block past the list: uniform exit
-    const int t_ = blk * NT + tid;
-    const int i = t_ < cnt ? (a.list ? a.list[t_] : t_) : -1;
-    const bool inb = i >= 0;
-    // From a given start direction (the learned proposal) the view count and the start cost are
-    // taken in round 0, next to the six candidates; otherwise they come from k_argmin.
-    const bool from_start = a.start_dir != nullptr;
-    int nv = 0;
-    if (inb) {
-        if (from_start && a.T > 0) {
-            const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
-            nv = (isfinite(p0) && isfinite(p1) && isfinite(p2)) ? 0 : -1;
-        } else {   // from k_argmin, or (no rounds) from k_start_select
-            nv = a.nvs[i];
-        }
-    }
-    if (inb && nv < 0) {
-        const int o = i - a.out_first;   // output row
-        a.dir_out[3 * o] = a.dir_out[3 * o + 1] = a.dir_out[3 * o + 2] = 0.0f;
-        if (a.cost_out) a.cost_out[o] = __int_as_float(0x7fc00000);
-        if (a.idx_out) a.idx_out[o] = -1;
-        if (a.status_out) a.status_out[o] = HF_STATUS_BAD_INPUT;
-        if (from_start) a.nvs[i] = -1;
-    }
-    // points with no view keep their start (all costs are 1)
-    const bool active = inb && ((from_start && a.T > 0) ? nv == 0 : nv > 0);
-    int nb[KP];
-    load_nbrs<KP, S, NT>(a, i, active, nb, sg);
-    // start: the argmin hypothesis, or a given direction (the learned proposal; index -1)
-    const int bestm = from_start ? -1 : ((inb && nv >= 0) ? a.best_idx[i] : 0);
-    float best = ((!from_start || a.T == 0) && inb && nv >= 0) ? a.best_cost[i] : 0.0f;
-    float acc_c = 0.0f;   // round 0 from a start: the start direction's patch terms
-    float d0, d1, d2;
-    if (a.start_dir) {
-        d0 = inb ? a.start_dir[3 * i] : 1.0f;
-        d1 = inb ? a.start_dir[3 * i + 1] : 0.0f;
-        d2 = inb ? a.start_dir[3 * i + 2] : 0.0f;
-    } else {
-        d0 = a.hyps[3 * bestm];
-        d1 = a.hyps[3 * bestm + 1];
-        d2 = a.hyps[3 * bestm + 2];
-    }
-    const int nblk = (a.V + a.vblock_c - 1) / a.vblock_c;
+// chunks and slots in use, uniform over the warp
+template <int SM>
+__device__ __forceinline__ void chunking(int nv, int L, int& nch, int& ns) {
+    const int per = L * SM;
+    nch = (int)__reduce_max_sync(0xffffffffu, (unsigned)((nv + per - 1) / per));
+    ns = (int)__reduce_max_sync(0xffffffffu, (unsigned)min(SM, (nv + L - 1) / L));
+    if (nch < 1) nch = 1;
+}
+
+__device__ __forceinline__ void write_bad(const CostArgs& a, int i) {
+    const int o = i - a.out_first;   // output row
+    a.dir_out[3 * o] = a.dir_out[3 * o + 1] = a.dir_out[3 * o + 2] = 0.0f;
+    if (a.cost_out) a.cost_out[o] = __int_as_float(0x7fc00000);
+    if (a.idx_out) a.idx_out[o] = -1;
+    if (a.status_out) a.status_out[o] = HF_STATUS_BAD_INPUT;
+}
+
+// Six rotations of d by +-alpha about world x, y, z (in that order) and their sums; move to the first
+// strictly larger sum (the first strictly lower cost).
+template <int KP, int SM>
+__device__ __forceinline__ void refine_rounds(const CostArgs& a, const PointCtx<KP>& pc, int lg, int nch, int ns,
+                                              Slot<KP> (&S)[SM], float& d0, float& d1, float& d2, float& best) {
     for (int t = 0; t < a.T; ++t) {
         const float2 cr = a.rot[t];
         const float c = cr.x, sn = cr.y;
-        const float cd[6][3] = {{d0, c * d1 - sn * d2, sn * d1 + c * d2}, {d0, c * d1 + sn * d2, -sn * d1 + c * d2},
-                                {c * d0 + sn * d2, d1, -sn * d0 + c * d2}, {c * d0 - sn * d2, d1, sn * d0 + c * d2},
-                                {c * d0 - sn * d1, sn * d0 + c * d1, d2}, {c * d0 + sn * d1, -sn * d0 + c * d1, d2}};
-        f32x2 CX[3], CY[3], CZ[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            CX[q] = pk(cd[2 * q][0], cd[2 * q + 1][0]);
-            CY[q] = pk(cd[2 * q][1], cd[2 * q + 1][1]);
-            CZ[q] = pk(cd[2 * q][2], cd[2 * q + 1][2]);
-        }
-        float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        for (int p = 0; p < S - 1; ++p)
-            if (p < a.V) issue_patch<KP, S, NT>(sg, p, a.ab, a.samp, (size_t)p * a.N, i, nb, active);
-            else cp_async_commit();
-        for (int vb = 0; vb < a.V; vb += a.vblock_c) {
-            const int nvb = min(a.vblock_c, a.V - vb);
-            if (nblk > 1 || t == 0) {
-                __syncthreads();
-                for (int e = tid; e < nvb; e += NT) {
-                    const float* cam = a.cams + 16 * (vb + e);
-                    cs4[3 * e] = make_float4(cam[0], cam[1], cam[4], cam[5]);
-                    cs4[3 * e + 1] = make_float4(cam[6], cam[7], cam[8], cam[9]);
-                    cs4[3 * e + 2] = make_float4(cam[10], cam[11], cam[12], a.vthr[vb + e]);
-                }
-                __syncthreads();
-            }
-            for (int v = vb; v < vb + nvb; ++v) {
-                const int vn = v + S - 1;
-                if (vn < a.V) issue_patch<KP, S, NT>(sg, vn % S, a.ab, a.samp, (size_t)vn * a.N, i, nb, active);
-                else cp_async_commit();
-                cp_async_wait<S - 1>();
-                if (!active) continue;
-                const int st = v % S;
-                const float2 r = sg.v[st][0][tid];
-                if (r.x != r.x) continue;
-                f32x2 SX[KP], SY[KP];
-                stage_samples<KP, S, NT>(sg, st, SX, SY);
-                // staged rows: k0 = (fx, fy, R00, R01), k1 = (R02, R10, R11, R12), k2 = (R20, R21, R22, thr)
-                const bool centre = from_start && t == 0;
-                const float4 k0 = cs4[3 * (v - vb)], k1 = cs4[3 * (v - vb) + 1], k2 = cs4[3 * (v - vb) + 2];
-                // Z times the projection Jacobian: rows fx (R_0 - a R_2), fy (R_1 - b R_2)
-                const float j0 = k0.x * fmaf(-r.x, k2.x, k0.z), j1 = k0.x * fmaf(-r.x, k2.y, k0.w),
-                            j2 = k0.x * fmaf(-r.x, k2.z, k1.x);
-                const float j3 = k0.y * fmaf(-r.y, k2.x, k1.y), j4 = k0.y * fmaf(-r.y, k2.y, k1.z),
-                            j5 = k0.y * fmaf(-r.y, k2.z, k1.w);
-                const f32x2 J0 = pk(j0, j0), J1 = pk(j1, j1), J2 = pk(j2, j2);
-                const f32x2 J3 = pk(j3, j3), J4 = pk(j4, j4), J5 = pk(j5, j5);
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {   // the +alpha / -alpha pair of axis q
-                    float L0, L1;
-                    view_term2<KP>(fma2(J0, CX[q], fma2(J1, CY[q], mul2(J2, CZ[q]))),
-                                   fma2(J3, CX[q], fma2(J4, CY[q], mul2(J5, CZ[q]))), SX, SY, k2.w, k2.w, L0, L1);
-                    acc[2 * q] += L0;
-                    acc[2 * q + 1] += L1;
-                }
-                if (centre) {
-                    const f32x2 D0 = pk(d0, d0), D1 = pk(d1, d1), D2 = pk(d2, d2);
-                    float L0, L1;
-                    view_term2<KP>(fma2(J0, D0, fma2(J1, D1, mul2(J2, D2))), fma2(J3, D0, fma2(J4, D1, mul2(J5, D2))), SX,
-                                   SY, k2.w, k2.w, L0, L1);
-                    acc_c += L0;
-                    ++nv;
-                }
-            }
-        }
-        cp_async_wait<0>();
-        if (from_start && t == 0) best = nv > 0 ? 1.0f - acc_c / (float)nv : 1.0f;
+        // every product rounded once and added with an explicit fused multiply-add, so that all
+        // instances of this code round alike
+        const float cd[6][3] = {{d0, fmaf(c, d1, __fmul_rn(-sn, d2)), fmaf(sn, d1, __fmul_rn(c, d2))},
+                                {d0, fmaf(c, d1, __fmul_rn(sn, d2)), fmaf(-sn, d1, __fmul_rn(c, d2))},
+                                {fmaf(c, d0, __fmul_rn(sn, d2)), d1, fmaf(-sn, d0, __fmul_rn(c, d2))},
+                                {fmaf(c, d0, __fmul_rn(-sn, d2)), d1, fmaf(sn, d0, __fmul_rn(c, d2))},
+                                {fmaf(c, d0, __fmul_rn(-sn, d1)), fmaf(sn, d0, __fmul_rn(c, d1)), d2},
+                                {fmaf(c, d0, __fmul_rn(sn, d1)), fmaf(-sn, d0, __fmul_rn(c, d1)), d2}};
+        float acc[6];
+        dir_sums<KP, SM, 6>(a, pc, lg, nch, ns, S, cd, 1.0f, acc);
         int choice = -1;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const float cq = nv > 0 ? 1.0f - acc[q] / (float)nv : 1.0f;
-            if (cq < best) {
-                best = cq;
+        for (int q = 0; q < 6; ++q)
+            if (acc[q] > best) {
+                best = acc[q];
                 choice = q;
             }
-        }
 #pragma unroll
         for (int q = 0; q < 6; ++q)
             if (q == choice) {
@@ -583,9 +491,12 @@ __device__ __forceinline__ void refine_tile(const FuseArgs& a, int blk, unsigned
                 d2 = cd[q][2];
             }
     }
-    if (!inb || nv < 0) return;
-    if (from_start && a.T > 0) a.nvs[i] = nv;
-    const float n = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+}
+
+// Normalised direction with the canonical sign, the cost, index and status of a point.
+__device__ __forceinline__ void write_out(const CostArgs& a, int i, int nv, float d0, float d1, float d2, float best,
+                                          int idx) {
+    const float n = sqrtf(fmaf(d0, d0, fmaf(d1, d1, __fmul_rn(d2, d2))));
     d0 /= n;
     d1 /= n;
     d2 /= n;
@@ -594,15 +505,147 @@ __device__ __forceinline__ void refine_tile(const FuseArgs& a, int blk, unsigned
     a.dir_out[3 * o] = sgn * d0;
     a.dir_out[3 * o + 1] = sgn * d1;
     a.dir_out[3 * o + 2] = sgn * d2;
-    if (a.cost_out) a.cost_out[o] = best;
-    if (a.idx_out) a.idx_out[o] = bestm;
+    if (a.cost_out) a.cost_out[o] = nv ? 1.0f - best / (float)nv : 1.0f;
+    if (a.idx_out) a.idx_out[o] = idx;
     if (a.status_out) a.status_out[o] = a.fell_back ? HF_STATUS_FELL_BACK : (nv ? HF_STATUS_OK : HF_STATUS_NO_VIEWS);
 }
 
+// The hypotheses of the scene into shared memory (a CTA-wide barrier follows).
+__device__ __forceinline__ void stage_hyps(const CostArgs& a, float* sh) {
+    for (int e = threadIdx.x; e < 3 * a.Hpad; e += blockDim.x) sh[e] = a.hyps[e];
+    __syncthreads();
+}
+
+// K2 + K3 for the points of one tile.
 template <int KP>
-__global__ void __launch_bounds__(kFuseThreads) k_refine(FuseArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    refine_tile<KP, kFuseThreads>(a, blockIdx.x, smem_raw);
+__device__ __forceinline__ void fuse_tile(const CostArgs& a, int tile, float* sh) {
+    constexpr int SM = SlotsFor<KP>::value;
+    stage_hyps(a, sh);
+    const int cnt = a.list ? *a.list_count : a.N;
+    Lanes ln;
+    if (!lanes_of(a.L, tile, cnt, ln)) return;
+    PointCtx<KP> pc;
+    point_ctx<KP>(a, ln.q, cnt, pc);
+    int nch, ns;
+    chunking<SM>(pc.nv, a.L, nch, ns);
+    Slot<KP> S[SM];
+    if (nch == 1) gather<KP, SM>(a, pc, ln.lg, 0, ns, S);
+    // argmin over the hypotheses, two at a time (largest sum, lowest index on ties)
+    float best = -1.0f;
+    int bm = 0;
+    for (int m = 0; m < a.Hpad; m += 2) {
+        const float hd[2][3] = {{sh[3 * m], sh[3 * m + 1], sh[3 * m + 2]}, {sh[3 * m + 3], sh[3 * m + 4], sh[3 * m + 5]}};
+        float l[2];
+        dir_sums<KP, SM, 2>(a, pc, ln.lg, nch, ns, S, hd, 1.0f, l);
+        if (l[0] > best) {
+            best = l[0];
+            bm = m;
+        }
+        if (m + 1 < a.H && l[1] > best) {
+            best = l[1];
+            bm = m + 1;
+        }
+    }
+    float d0 = sh[3 * bm], d1 = sh[3 * bm + 1], d2 = sh[3 * bm + 2];
+    refine_rounds<KP, SM>(a, pc, ln.lg, nch, ns, S, d0, d1, d2, best);
+    if (ln.lg != 0 || !pc.in) return;
+    if (!pc.finite) {
+        write_bad(a, pc.i);
+        if (a.nvs) a.nvs[pc.i] = -1;
+        return;
+    }
+    write_out(a, pc.i, pc.nv, d0, d1, d2, best, bm);
+}
+
+constexpr int kCostThreads = 128;
+
+template <int KP>
+__global__ void __launch_bounds__(kCostThreads) k_fuse(CostArgs a) {
+    extern __shared__ __align__(16) float smem_f[];
+    fuse_tile<KP>(a, blockIdx.x, smem_f);
+}
+
+// The learned path after the network, for the points of one tile.
+template <int KP>
+__device__ __forceinline__ void learn_tile(const LearnArgs& la, int tile) {
+    constexpr int SM = SlotsFor<KP>::value;
+    const CostArgs& a = la.f;
+    const int cnt = a.N;
+    Lanes ln;
+    if (!lanes_of(a.L, tile, cnt, ln)) return;
+    PointCtx<KP> pc;
+    point_ctx<KP>(a, ln.q, cnt, pc);
+    int nch, ns;
+    chunking<SM>(pc.nv, a.L, nch, ns);
+    Slot<KP> S[SM];
+    if (nch == 1) gather<KP, SM>(a, pc, ln.lg, 0, ns, S);
+    float d0 = 1.0f, d1 = 0.0f, d2 = 0.0f;
+    if (pc.finite) {
+        d0 = la.start_dir[3 * pc.i];
+        d1 = la.start_dir[3 * pc.i + 1];
+        d2 = la.start_dir[3 * pc.i + 2];
+    }
+    const float dd[1][3] = {{d0, d1, d2}};
+    float l0[1];
+    dir_sums<KP, SM, 1>(a, pc, ln.lg, nch, ns, S, dd, 1.0f, l0);
+    const float c0 = pc.nv ? 1.0f - l0[0] / (float)pc.nv : 1.0f;
+    const bool lead = ln.lg == 0 && pc.in;
+    const bool fb = lead && pc.finite && pc.nv > 0 && c0 > la.tau;
+    const bool ok = lead && pc.finite && !fb;
+    if (lead && a.nvs) a.nvs[pc.i] = pc.finite ? pc.nv : -1;
+    // warp-aggregated appends to the fallback list and work counts
+    const unsigned mfb = __ballot_sync(0xffffffffu, fb);
+    if (mfb) {
+        const int leader = __ffs(mfb) - 1;
+        int base = 0;
+        if (ln.lane == leader) base = atomicAdd(la.fb_count, __popc(mfb));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (fb) la.fb_list[base + __popc(mfb & ((1u << ln.lane) - 1u))] = pc.i;
+    }
+    const unsigned wfb = __reduce_add_sync(0xffffffffu, fb ? (unsigned)pc.nv : 0u);
+    const unsigned wok = __reduce_add_sync(0xffffffffu, ok ? (unsigned)pc.nv : 0u);
+    if (ln.lane == 0) {
+        if (la.fb_work && wfb) atomicAdd(la.fb_work, (unsigned long long)wfb);
+        if (la.acc_work && wok) atomicAdd(la.acc_work, (unsigned long long)wok);
+    }
+    // short refinement from the proposal (every group takes part in the shuffles; the fallback
+    // points' results are dropped)
+    float best = l0[0];
+    refine_rounds<KP, SM>(a, pc, ln.lg, nch, ns, S, d0, d1, d2, best);
+    if (!lead) return;
+    if (!pc.finite) {
+        write_bad(a, pc.i);
+        return;
+    }
+    if (ok) write_out(a, pc.i, pc.nv, d0, d1, d2, best, -1);
+}
+
+template <int KP>
+__global__ void __launch_bounds__(kCostThreads) k_learn(LearnArgs la) {
+    learn_tile<KP>(la, blockIdx.x);
+}
+
+// ------------------------------------------------------------------ cost of given directions
+template <int KP>
+__global__ void __launch_bounds__(kCostThreads) k_eval(EvalArgs e) {
+    constexpr int SM = SlotsFor<KP>::value;
+    const CostArgs& a = e.f;
+    Lanes ln;
+    if (!lanes_of(a.L, blockIdx.x, a.N, ln)) return;
+    PointCtx<KP> pc;
+    point_ctx<KP>(a, ln.q, a.N, pc);
+    int nch, ns;
+    chunking<SM>(pc.nv, a.L, nch, ns);
+    Slot<KP> S[SM];
+    if (nch == 1) gather<KP, SM>(a, pc, ln.lg, 0, ns, S);
+    for (int m = 0; m < e.M; ++m) {
+        const float* d = e.dirs + ((size_t)pc.i * e.M + m) * 3;
+        const float dd[1][3] = {{d[0], d[1], d[2]}};
+        const float dn2 = fmaf(dd[0][0], dd[0][0], fmaf(dd[0][1], dd[0][1], __fmul_rn(dd[0][2], dd[0][2])));
+        float l[1];
+        dir_sums<KP, SM, 1>(a, pc, ln.lg, nch, ns, S, dd, dn2, l);
+        if (ln.lg == 0 && pc.in) e.cost[(size_t)pc.i * e.M + m] = pc.nv ? 1.0f - l[0] / (float)pc.nv : 1.0f;
+    }
 }
 
 // ------------------------------------------------------------------ learned proposal path
@@ -685,133 +728,11 @@ __device__ __forceinline__ void features_tile(const FeatArgs& a, int blk) {
 
 __global__ void __launch_bounds__(kFeatThreads) k_features(FeatArgs a) { features_tile(a, blockIdx.x); }
 
-// Cost c_i of the proposal (a.start_dir) and the fallback decision: points with a view and
-// c_i > tau go to the fallback list (a.list), the others to the accepted list (s.acc_list), in
-// the order warps append them; non-finite points get their BAD_INPUT outputs here and no list.
-// best_cost / nvs receive c_i and |V_i| (the refinement's zero-round outputs).
-constexpr int kStartThreads = 128;
-
-// One direction per view: the next view's (a, b) and patch samples are loaded while the current
-// view is evaluated (register double buffering; loads of views outside V_i are harmless reads).
-template <int KP>
-__device__ __forceinline__ void start_select_tile(const StartSelectArgs& s, int blk) {
-    const FuseArgs& a = s.f;
-    const int tid = threadIdx.x;
-    const int i = blk * kStartThreads + tid;
-    const bool in = i < a.N;
-    bool bad = false;
-    if (in) {
-        const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
-        bad = !(isfinite(p0) && isfinite(p1) && isfinite(p2));
-    }
-    const bool active = in && !bad;
-    float acc = 0.0f;
-    int nv = 0;
-    if (active) {
-        int nb[KP];
-        nb[0] = i;
-#pragma unroll
-        for (int j = 1; j < KP; ++j) nb[j] = (j - 1) < a.k ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
-        const float d0 = a.start_dir[3 * i], d1 = a.start_dir[3 * i + 1], d2 = a.start_dir[3 * i + 2];
-        float2 rn = a.ab[i];
-        float2 sn[KP];
-        load_patch<KP>(a.samp, 0, i, nb, sn);
-        for (int v = 0; v < a.V; ++v) {
-            const float2 r = rn;
-            float2 sm[KP];
-#pragma unroll
-            for (int j = 0; j < KP; ++j) sm[j] = sn[j];
-            if (v + 1 < a.V) {
-                const size_t nxt = (size_t)(v + 1) * a.N;
-                rn = a.ab[nxt + i];
-                load_patch<KP>(a.samp, nxt, i, nb, sn);
-            }
-            if (r.x != r.x) continue;
-            ++nv;
-            const float* cam = a.cams + 16 * v;
-            // Z times the projection Jacobian, rounded as in the refinement's round 0
-            const float j0 = cam[0] * fmaf(-r.x, cam[10], cam[4]), j1 = cam[0] * fmaf(-r.x, cam[11], cam[5]),
-                        j2 = cam[0] * fmaf(-r.x, cam[12], cam[6]);
-            const float j3 = cam[1] * fmaf(-r.y, cam[10], cam[7]), j4 = cam[1] * fmaf(-r.y, cam[11], cam[8]),
-                        j5 = cam[1] * fmaf(-r.y, cam[12], cam[9]);
-            acc += view_term<KP>(fmaf(j0, d0, fmaf(j1, d1, j2 * d2)), fmaf(j3, d0, fmaf(j4, d1, j5 * d2)), sm,
-                                 a.vthr[v]);
-        }
-    }
-    const float c0 = nv ? 1.0f - acc / (float)nv : 1.0f;
-    if (active) {
-        a.best_cost[i] = c0;
-        a.nvs[i] = nv;
-    } else if (in) {
-        const int o = i - a.out_first;   // output row
-        a.nvs[i] = -1;
-        a.dir_out[3 * o] = a.dir_out[3 * o + 1] = a.dir_out[3 * o + 2] = 0.0f;
-        if (a.cost_out) a.cost_out[o] = __int_as_float(0x7fc00000);
-        if (a.idx_out) a.idx_out[o] = -1;
-        if (a.status_out) a.status_out[o] = HF_STATUS_BAD_INPUT;
-    }
-    const bool fb = active && nv > 0 && c0 > s.tau;
-    const bool ok = active && !fb;
-    const int lane = tid & 31;
-    const unsigned below = (1u << lane) - 1u;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {   // warp-aggregated appends: fallback, then accepted
-        const bool want = q == 0 ? fb : ok;
-        const unsigned m = __ballot_sync(0xffffffffu, want);
-        if (!m) continue;
-        const int leader = __ffs(m) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(q == 0 ? const_cast<int*>(a.list_count) : s.acc_count, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (want) (q == 0 ? const_cast<int32_t*>(a.list) : s.acc_list)[base + __popc(m & below)] = i;
-    }
-}
-
-template <int KP>
-__global__ void __launch_bounds__(kStartThreads) k_start_select(StartSelectArgs s) {
-    start_select_tile<KP>(s, blockIdx.x);
-}
-
-
 __global__ void k_rot(float2* rot, int T, double alpha0) {
     const int t = threadIdx.x;
     if (t < T) {
         const double al = alpha0 / (double)(1u << t);
         rot[t] = make_float2((float)cos(al), (float)sin(al));
-    }
-}
-
-// ------------------------------------------------------------------ cost of given directions
-template <int KP>
-__global__ void __launch_bounds__(128) k_eval(EvalArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.N) return;
-    int nb[KP];
-    nb[0] = i;
-#pragma unroll
-    for (int j = 1; j < KP; ++j) nb[j] = (j - 1) < a.k ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
-    for (int m = 0; m < a.M; ++m) {
-        const float* d = a.dirs + ((size_t)i * a.M + m) * 3;
-        const float d0 = d[0], d1 = d[1], d2 = d[2];
-        const float dn2 = d0 * d0 + d1 * d1 + d2 * d2;
-        float acc = 0.0f;
-        int nv = 0;
-        for (int v = 0; v < a.V; ++v) {
-            const size_t base = (size_t)v * a.N;
-            const float2 r = a.ab[base + i];
-            if (r.x != r.x) continue;
-            ++nv;
-            float2 s[KP];
-            load_patch<KP>(a.samp, base, i, nb, s);
-            const float* cam = a.cams + 16 * v;
-            const float fx = cam[0], fy = cam[1];
-            float q[3];
-            for (int rr = 0; rr < 3; ++rr) q[rr] = fmaf(cam[4 + 3 * rr], d0, fmaf(cam[5 + 3 * rr], d1, cam[6 + 3 * rr] * d2));
-            const float rx = fx * fmaf(-r.x, q[2], q[0]);
-            const float ry = fy * fmaf(-r.y, q[2], q[1]);
-            acc += view_term<KP>(rx, ry, s, a.vthr[v] * dn2);
-        }
-        a.cost_out[(size_t)i * a.M + m] = nv ? 1.0f - acc / (float)nv : 1.0f;
     }
 }
 
@@ -837,14 +758,15 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
-template <int NT, typename Args, typename Count, typename Body>
-__device__ __forceinline__ void batch_tiles(const Args* __restrict__ args, const BatchCtl& c, Count count, Body body) {
+// tiles(args) gives a scene's tile count (evaluated on the device: list lengths are device counts)
+template <typename Args, typename Tiles, typename Body>
+__device__ __forceinline__ void batch_tiles(const Args* __restrict__ args, const BatchCtl& c, Tiles tiles, Body body) {
     __shared__ Args sa;
     __shared__ int pref[HF_MAX_BATCH + 1];
     __shared__ int s_item, s_pos, s_cur;
     if (threadIdx.x == 0) {
         pref[0] = 0;
-        for (int p = 0; p < c.ns; ++p) pref[p + 1] = pref[p] + (count(args[p]) + NT - 1) / NT;
+        for (int p = 0; p < c.ns; ++p) pref[p + 1] = pref[p] + tiles(args[p]);
         s_cur = -1;
     }
     for (;;) {
@@ -874,37 +796,36 @@ __device__ __forceinline__ void batch_tiles(const Args* __restrict__ args, const
     }
 }
 
-__device__ __forceinline__ int fuse_count(const FuseArgs& a) { return a.list ? *a.list_count : a.N; }
-
-template <int HC, int KP, int NT>
-__global__ void __launch_bounds__(NT) k_argmin_batch(const FuseArgs* __restrict__ fa, BatchCtl c) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    batch_tiles<NT>(fa, c, [](const FuseArgs& a) { return fuse_count(a); }, [&](const FuseArgs& a, int blk) { argmin_tile<HC, KP, NT>(a, blk, smem_raw); });
+// points per CTA of the cost kernels: 32 / L points per warp
+__device__ __forceinline__ int cost_tiles(const CostArgs& a, int cnt) {
+    const int ppc = (int)(blockDim.x >> 5) * (32 / a.L);
+    return (cnt + ppc - 1) / ppc;
 }
 
 template <int KP, int NT>
-__global__ void __launch_bounds__(NT) k_refine_batch(const FuseArgs* __restrict__ fa, BatchCtl c) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    batch_tiles<NT>(fa, c, [](const FuseArgs& a) { return fuse_count(a); }, [&](const FuseArgs& a, int blk) { refine_tile<KP, NT>(a, blk, smem_raw); });
+__global__ void __launch_bounds__(NT) k_fuse_batch(const CostArgs* __restrict__ fa, BatchCtl c) {
+    extern __shared__ __align__(16) float smem_f[];
+    batch_tiles(fa, c, [](const CostArgs& a) { return cost_tiles(a, a.list ? *a.list_count : a.N); },
+                [&](const CostArgs& a, int t) { fuse_tile<KP>(a, t, smem_f); });
+}
+
+template <int KP, int NT>
+__global__ void __launch_bounds__(NT) k_learn_batch(const LearnArgs* __restrict__ la, BatchCtl c) {
+    batch_tiles(la, c, [](const LearnArgs& a) { return cost_tiles(a.f, a.f.N); },
+                [](const LearnArgs& a, int t) { learn_tile<KP>(a, t); });
 }
 
 __global__ void __launch_bounds__(kProjectThreads) k_project_batch(const ProjectArgs* __restrict__ pa, BatchCtl c) {
-    batch_tiles<kProjectThreads>(pa, c, [](const ProjectArgs& a) { return a.N; }, [](const ProjectArgs& a, int blk) {
-        if (a.top_k > 0) project_tile<true>(a, blk);
-        else project_tile<false>(a, blk);
-    });
+    batch_tiles(pa, c, [](const ProjectArgs& a) { return (a.N + kProjectThreads - 1) / kProjectThreads; },
+                [](const ProjectArgs& a, int blk) {
+                    if (a.top_k > 0) project_tile<true>(a, blk);
+                    else project_tile<false>(a, blk);
+                });
 }
 
 __global__ void __launch_bounds__(kFeatThreads) k_features_batch(const FeatArgs* __restrict__ fe, BatchCtl c) {
-    batch_tiles<kFeatThreads>(fe, c, [](const FeatArgs& a) { return a.N; },
-                              [](const FeatArgs& a, int blk) { features_tile(a, blk); });
-}
-
-template <int KP>
-__global__ void __launch_bounds__(kStartThreads) k_start_select_batch(const StartSelectArgs* __restrict__ sa,
-                                                                      BatchCtl c) {
-    batch_tiles<kStartThreads>(sa, c, [](const StartSelectArgs& a) { return a.f.N; },
-                               [](const StartSelectArgs& a, int blk) { start_select_tile<KP>(a, blk); });
+    batch_tiles(fe, c, [](const FeatArgs& a) { return (a.N + kFeatThreads - 1) / kFeatThreads; },
+                [](const FeatArgs& a, int blk) { features_tile(a, blk); });
 }
 
 // Per-scene constants of every scene (block = scene), the batch's counters cleared, empty bounding
@@ -922,7 +843,7 @@ __global__ void k_prep_batch(const PrepArgs* __restrict__ pr, BatchReset r) {
     }
 }
 
-// persistent grid: resident CTAs per SM x SMs (cached per kernel and shared-memory size)
+// persistent grid: resident CTAs per SM x SMs
 template <typename K>
 int persistent_grid(K kernel, int threads, size_t smem) {
     static int sms = 0;
@@ -945,55 +866,6 @@ cudaError_t set_smem(K kernel, size_t smem, cudaStream_t s) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <int HC, int KP, int NT>
-cudaError_t launch_argmin_batch(const FuseArgs* fa, const BatchCtl& c, cudaStream_t s) {
-    const size_t sm = sizeof(PatchStage<KP, kArgminStages, NT>) + kQStageBytes;
-    cudaError_t e = set_smem(k_argmin_batch<HC, KP, NT>, sm, s);
-    if (e != cudaSuccess) return e;
-    static int grid = 0;
-    if (!grid) grid = persistent_grid(k_argmin_batch<HC, KP, NT>, NT, sm);
-    k_argmin_batch<HC, KP, NT><<<grid, NT, sm, s>>>(fa, c);
-    return cudaGetLastError();
-}
-
-template <int KP, int NT>
-cudaError_t launch_refine_batch(const FuseArgs* fa, const BatchCtl& c, cudaStream_t s) {
-    const size_t sm = sizeof(PatchStage<KP, kRefineStages, NT>) + (size_t)kCamStageViews * 3 * sizeof(float4);
-    cudaError_t e = set_smem(k_refine_batch<KP, NT>, sm, s);
-    if (e != cudaSuccess) return e;
-    static int grid = 0;
-    if (!grid) grid = persistent_grid(k_refine_batch<KP, NT>, NT, sm);
-    k_refine_batch<KP, NT><<<grid, NT, sm, s>>>(fa, c);
-    return cudaGetLastError();
-}
-
-template <int HC, int KP>
-cudaError_t launch_argmin_batch_nt(const FuseArgs* fa, const BatchCtl& c, int nt, cudaStream_t s) {
-    switch (nt) {
-        case 64: return launch_argmin_batch<HC, KP, 64>(fa, c, s);
-        case 256: return launch_argmin_batch<HC, KP, 256>(fa, c, s);
-        default: return launch_argmin_batch<HC, KP, 128>(fa, c, s);
-    }
-}
-
-template <int HC>
-cudaError_t launch_argmin_batch_kp(const FuseArgs* fa, const BatchCtl& c, int kp, int nt, cudaStream_t s) {
-    switch (kp) {
-        case 4: return launch_argmin_batch_nt<HC, 4>(fa, c, nt, s);
-        case 9: return launch_argmin_batch_nt<HC, 9>(fa, c, nt, s);
-        default: return launch_argmin_batch_nt<HC, 17>(fa, c, nt, s);
-    }
-}
-
-template <int KP>
-cudaError_t launch_refine_batch_nt(const FuseArgs* fa, const BatchCtl& c, int nt, cudaStream_t s) {
-    switch (nt) {
-        case 64: return launch_refine_batch<KP, 64>(fa, c, s);
-        case 256: return launch_refine_batch<KP, 256>(fa, c, s);
-        default: return launch_refine_batch<KP, 128>(fa, c, s);
-    }
-}
-
 // patch width (k + 1) rounded up to an instantiated size
 int kp_for(int k) {
     const int need = k + 1;
@@ -1005,48 +877,86 @@ int kp_for(int k) {
     return 17;
 }
 
-// stage 1: k_argmin, stage 2: k_refine.  Dynamic shared memory above 48 KB needs the function
-// attribute, which is cheap and set on every launch (it is per function and per device).
-template <int HC, int KP>
-cudaError_t launch_fuse_kp(const FuseArgs& a, int stage, cudaStream_t s) {
-    const dim3 grid((a.N + kFuseThreads - 1) / kFuseThreads), block(kFuseThreads);
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(s, &cs);
-    const bool set_attr = cs == cudaStreamCaptureStatusNone;   // set outside capture only
-    if (stage == 1) {
-        const size_t sm = sizeof(PatchStage<KP, kArgminStages, kFuseThreads>) + (size_t)a.vblock_q * HC * sizeof(float4);
-        cudaError_t e = set_attr ? cudaFuncSetAttribute(k_argmin<HC, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                                 : cudaSuccess;
-        if (e != cudaSuccess) return e;
-        k_argmin<HC, KP><<<grid, block, sm, s>>>(a);
-    } else {
-        const size_t sm = sizeof(PatchStage<KP, kRefineStages, kFuseThreads>) + (size_t)a.vblock_c * 3 * sizeof(float4);
-        cudaError_t e = set_attr ? cudaFuncSetAttribute(k_refine<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                                 : cudaSuccess;
-        if (e != cudaSuccess) return e;
-        k_refine<KP><<<grid, block, sm, s>>>(a);
+int slots_for_kp(int kp) {
+    switch (kp) {
+        case 1: return SlotsFor<1>::value;
+        case 4: return SlotsFor<4>::value;
+        case 6: return SlotsFor<6>::value;
+        case 9: return SlotsFor<9>::value;
+        case 12: return SlotsFor<12>::value;
+        default: return SlotsFor<17>::value;
     }
+}
+
+template <int KP, int NT>
+cudaError_t launch_fuse_batch(const CostArgs* fa, const BatchCtl& c, int hpad_max, cudaStream_t s) {
+    const size_t sm = (size_t)3 * hpad_max * sizeof(float);
+    cudaError_t e = set_smem(k_fuse_batch<KP, NT>, sm, s);
+    if (e != cudaSuccess) return e;
+    const int grid = persistent_grid(k_fuse_batch<KP, NT>, NT, sm);
+    k_fuse_batch<KP, NT><<<grid, NT, sm, s>>>(fa, c);
     return cudaGetLastError();
 }
 
-template <int HC>
-cudaError_t launch_fuse_hc(const FuseArgs& a, int stage, cudaStream_t s) {
-    switch (kp_for(a.k)) {
-        case 1: return launch_fuse_kp<HC, 1>(a, stage, s);
-        case 4: return launch_fuse_kp<HC, 4>(a, stage, s);
-        case 6: return launch_fuse_kp<HC, 6>(a, stage, s);
-        case 9: return launch_fuse_kp<HC, 9>(a, stage, s);
-        case 12: return launch_fuse_kp<HC, 12>(a, stage, s);
-        default: return launch_fuse_kp<HC, 17>(a, stage, s);
+template <int KP, int NT>
+cudaError_t launch_learn_batch(const LearnArgs* la, const BatchCtl& c, cudaStream_t s) {
+    static int grid = 0;
+    if (!grid) grid = persistent_grid(k_learn_batch<KP, NT>, NT, 0);
+    k_learn_batch<KP, NT><<<grid, NT, 0, s>>>(la, c);
+    return cudaGetLastError();
+}
+
+template <int KP>
+cudaError_t launch_fuse_batch_nt(const CostArgs* fa, const BatchCtl& c, int nt, int hpad_max, cudaStream_t s) {
+    switch (nt) {
+        case 64: return launch_fuse_batch<KP, 64>(fa, c, hpad_max, s);
+        case 256: return launch_fuse_batch<KP, 256>(fa, c, hpad_max, s);
+        default: return launch_fuse_batch<KP, 128>(fa, c, hpad_max, s);
     }
+}
+
+template <int KP>
+cudaError_t launch_learn_batch_nt(const LearnArgs* la, const BatchCtl& c, int nt, cudaStream_t s) {
+    switch (nt) {
+        case 64: return launch_learn_batch<KP, 64>(la, c, s);
+        case 256: return launch_learn_batch<KP, 256>(la, c, s);
+        default: return launch_learn_batch<KP, 128>(la, c, s);
+    }
+}
+
+template <int KP>
+cudaError_t launch_fuse_kp(const CostArgs& a, cudaStream_t s) {
+    const int cnt_max = a.N;   // with a list, its length is at most N (tiles past the list exit at once)
+    const int ppc = kCostThreads / a.L;
+    const dim3 grid((cnt_max + ppc - 1) / ppc), block(kCostThreads);
+    const size_t sm = (size_t)3 * a.Hpad * sizeof(float);
+    cudaError_t e = set_smem(k_fuse<KP>, sm, s);
+    if (e != cudaSuccess) return e;
+    k_fuse<KP><<<grid, block, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int KP>
+cudaError_t launch_learn_kp(const LearnArgs& a, cudaStream_t s) {
+    const int ppc = kCostThreads / a.f.L;
+    k_learn<KP><<<(a.f.N + ppc - 1) / ppc, kCostThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int KP>
+cudaError_t launch_eval_kp(const EvalArgs& a, cudaStream_t s) {
+    const int ppc = kCostThreads / a.f.L;
+    k_eval<KP><<<(a.f.N + ppc - 1) / ppc, kCostThreads, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-int hf_fuse_chunk_for(int H) {
-    if (H <= 8) return 8;
-    if (H <= 16) return 16;
-    return 32;
+int hf_cost_lanes(int veff, int k) {
+    const int sm = slots_for_kp(kp_for(k));
+    int L = 4;
+    while (L < 32 && L * sm < veff) L *= 2;
+    return L;
 }
 
 cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s) {
@@ -1074,39 +984,37 @@ cudaError_t hf_launch_prep(const PrepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int hf_fuse_vblock_q(int V, int hchunk) {
-    const int vb = (int)(kQStageBytes / ((size_t)hchunk * sizeof(float4)));
-    return vb < 1 ? 1 : (vb < V ? vb : V);
-}
-
-int hf_fuse_vblock_c(int V) { return V < kCamStageViews ? V : kCamStageViews; }
-
-cudaError_t hf_launch_argmin(const FuseArgs& a, int hchunk, cudaStream_t s) {
-    switch (hchunk) {
-        case 8: return launch_fuse_hc<8>(a, 1, s);
-        case 16: return launch_fuse_hc<16>(a, 1, s);
-        default: return launch_fuse_hc<32>(a, 1, s);
+cudaError_t hf_launch_fuse(const CostArgs& a, cudaStream_t s) {
+    switch (kp_for(a.k)) {
+        case 1: return launch_fuse_kp<1>(a, s);
+        case 4: return launch_fuse_kp<4>(a, s);
+        case 6: return launch_fuse_kp<6>(a, s);
+        case 9: return launch_fuse_kp<9>(a, s);
+        case 12: return launch_fuse_kp<12>(a, s);
+        default: return launch_fuse_kp<17>(a, s);
     }
 }
 
-cudaError_t hf_launch_refine(const FuseArgs& a, cudaStream_t s) { return launch_fuse_hc<8>(a, 2, s); }
-
-cudaError_t hf_launch_fuse(const FuseArgs& a, int hchunk, cudaStream_t s) {
-    cudaError_t e = hf_launch_argmin(a, hchunk, s);
-    return e != cudaSuccess ? e : hf_launch_refine(a, s);
+cudaError_t hf_launch_learn(const LearnArgs& a, cudaStream_t s) {
+    switch (kp_for(a.f.k)) {
+        case 1: return launch_learn_kp<1>(a, s);
+        case 4: return launch_learn_kp<4>(a, s);
+        case 6: return launch_learn_kp<6>(a, s);
+        case 9: return launch_learn_kp<9>(a, s);
+        case 12: return launch_learn_kp<12>(a, s);
+        default: return launch_learn_kp<17>(a, s);
+    }
 }
 
 cudaError_t hf_launch_eval(const EvalArgs& a, cudaStream_t s) {
-    const dim3 grid((a.N + 127) / 128), block(128);
-    switch (kp_for(a.k)) {
-        case 1: k_eval<1><<<grid, block, 0, s>>>(a); break;
-        case 4: k_eval<4><<<grid, block, 0, s>>>(a); break;
-        case 6: k_eval<6><<<grid, block, 0, s>>>(a); break;
-        case 9: k_eval<9><<<grid, block, 0, s>>>(a); break;
-        case 12: k_eval<12><<<grid, block, 0, s>>>(a); break;
-        default: k_eval<17><<<grid, block, 0, s>>>(a); break;
+    switch (kp_for(a.f.k)) {
+        case 1: return launch_eval_kp<1>(a, s);
+        case 4: return launch_eval_kp<4>(a, s);
+        case 6: return launch_eval_kp<6>(a, s);
+        case 9: return launch_eval_kp<9>(a, s);
+        case 12: return launch_eval_kp<12>(a, s);
+        default: return launch_eval_kp<17>(a, s);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t hf_launch_fib(int H, float* out, cudaStream_t s) {
@@ -1118,24 +1026,6 @@ cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s) {
     k_features<<<(a.N + kFeatThreads - 1) / kFeatThreads, kFeatThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
-
-template <int KP>
-cudaError_t launch_start_select(const StartSelectArgs& a, cudaStream_t s) {
-    k_start_select<KP><<<(a.f.N + kStartThreads - 1) / kStartThreads, kStartThreads, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t hf_launch_start_select(const StartSelectArgs& a, cudaStream_t s) {
-    switch (kp_for(a.f.k)) {
-        case 1: return launch_start_select<1>(a, s);
-        case 4: return launch_start_select<4>(a, s);
-        case 6: return launch_start_select<6>(a, s);
-        case 9: return launch_start_select<9>(a, s);
-        case 12: return launch_start_select<12>(a, s);
-        default: return launch_start_select<17>(a, s);
-    }
-}
-
 
 cudaError_t hf_launch_rot(float2* rot, int T, double alpha0, cudaStream_t s) {
     if (T <= 0) return cudaSuccess;
@@ -1172,34 +1062,18 @@ cudaError_t hf_launch_features_batch(const FeatArgs* fe, const BatchCtl& c, cuda
     return cudaGetLastError();
 }
 
-template <int KP>
-cudaError_t launch_start_select_batch(const StartSelectArgs* sa, const BatchCtl& c, cudaStream_t s) {
-    static int grid = 0;
-    if (!grid) grid = persistent_grid(k_start_select_batch<KP>, kStartThreads, 0);
-    k_start_select_batch<KP><<<grid, kStartThreads, 0, s>>>(sa, c);
-    return cudaGetLastError();
-}
-
-cudaError_t hf_launch_start_select_batch(const StartSelectArgs* sa, const BatchCtl& c, int kp, cudaStream_t s) {
+cudaError_t hf_launch_fuse_batch(const CostArgs* fa, const BatchCtl& c, int kp, int nt, int hpad_max, cudaStream_t s) {
     switch (kp) {
-        case 4: return launch_start_select_batch<4>(sa, c, s);
-        case 9: return launch_start_select_batch<9>(sa, c, s);
-        default: return launch_start_select_batch<17>(sa, c, s);
+        case 4: return launch_fuse_batch_nt<4>(fa, c, nt, hpad_max, s);
+        case 9: return launch_fuse_batch_nt<9>(fa, c, nt, hpad_max, s);
+        default: return launch_fuse_batch_nt<17>(fa, c, nt, hpad_max, s);
     }
 }
 
-cudaError_t hf_launch_argmin_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int hc, int nt, cudaStream_t s) {
-    switch (hc) {
-        case 8: return launch_argmin_batch_kp<8>(fa, c, kp, nt, s);
-        case 16: return launch_argmin_batch_kp<16>(fa, c, kp, nt, s);
-        default: return launch_argmin_batch_kp<32>(fa, c, kp, nt, s);
-    }
-}
-
-cudaError_t hf_launch_refine_batch(const FuseArgs* fa, const BatchCtl& c, int kp, int nt, cudaStream_t s) {
+cudaError_t hf_launch_learn_batch(const LearnArgs* la, const BatchCtl& c, int kp, int nt, cudaStream_t s) {
     switch (kp) {
-        case 4: return launch_refine_batch_nt<4>(fa, c, nt, s);
-        case 9: return launch_refine_batch_nt<9>(fa, c, nt, s);
-        default: return launch_refine_batch_nt<17>(fa, c, nt, s);
+        case 4: return launch_learn_batch_nt<4>(la, c, nt, s);
+        case 9: return launch_learn_batch_nt<9>(la, c, nt, s);
+        default: return launch_learn_batch_nt<17>(la, c, nt, s);
     }
 }

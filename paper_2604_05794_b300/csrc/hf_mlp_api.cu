@@ -412,7 +412,7 @@ int learned_scratch(hf_ctx* c, long long N) {
     int rc;
     if ((rc = hf_ensure(c, c->feat, (size_t)N * 64 * 2))) return rc;
     if ((rc = hf_ensure(c, c->prop, (size_t)N * 3 * 4))) return rc;
-    if ((rc = hf_ensure(c, c->lmisc, 256 + (size_t)N * 4 + (size_t)N * 4 + 64 * 8))) return rc;
+    if ((rc = hf_ensure(c, c->lmisc, 256 + 64 * 8 + (size_t)N * 4))) return rc;
     return HF_OK;
 }
 }  // namespace
@@ -451,35 +451,31 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     int rc;
     if ((rc = learned_scratch(c, N))) return rc;
     // per-scene constants and the projection / gather (shared with the plain path)
-    const int hc = hf_fuse_chunk_for(H);
-    const int Hpad = (H + hc - 1) / hc * hc;
-    if ((rc = hf_ensure(c, c->qtab, (size_t)V * Hpad * sizeof(float4)))) return rc;
+    const int Hpad = hf_hpad(H);
     if ((rc = hf_ensure(c, c->vthr, (size_t)V * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->hyps, (size_t)Hpad * 3 * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->rot, (size_t)(T > 0 ? T : 1) * sizeof(float2)))) return rc;
-    if ((rc = hf_ensure(c, c->samp, (size_t)V * N * sizeof(float2)))) return rc;
-    if ((rc = hf_ensure(c, c->ab, (size_t)V * N * sizeof(float2)))) return rc;
+    if ((rc = hf_ensure(c, c->samp, (size_t)N * hf_samp_stride(V) * sizeof(float2)))) return rc;
+    if ((rc = hf_ensure(c, c->vmask, (size_t)N * hf_mask_words(V) * sizeof(unsigned long long)))) return rc;
     if ((rc = hf_ensure(c, c->work, sizeof(unsigned long long)))) return rc;
-    if ((rc = hf_ensure(c, c->best, (size_t)N * 12))) return rc;
     if ((rc = hf_ensure(c, c->outs, (size_t)N * 21))) return rc;
     if ((rc = ensure_h1(m, N))) return rc;
     char* lm = (char*)c->lmisc.p;
     float* box = (float*)lm;
-    int* count = (int*)(lm + 64);       // fallback points
-    int* acc_count = (int*)(lm + 68);   // accepted proposals
+    int* count = (int*)(lm + 64);                                        // fallback points
+    unsigned long long* fb_work = (unsigned long long*)(lm + 72);       // their (point, view) pairs
+    unsigned long long* acc_work = (unsigned long long*)(lm + 80);      // those of the accepted proposals
     float2* rot_s = (float2*)(lm + 128);
     int32_t* list = (int32_t*)(lm + 256 + 64 * 8);
-    int32_t* acc_list = list + N;
     char* so = (char*)c->outs.p;
     float* d_dir = mem_kind == HF_HOST ? (float*)so : dir_out;
     float* d_cost = (mem_kind == HF_HOST || !cost_out) ? (float*)(so + (size_t)N * 12) : cost_out;
     int32_t* d_idx = mem_kind == HF_HOST ? (int32_t*)(so + (size_t)N * 16) : idx_out;
     uint8_t* d_status = mem_kind == HF_HOST ? (uint8_t*)(so + (size_t)N * 20) : status_out;
-    int32_t* bi = (int32_t*)c->best.p;
     cudaStream_t s = c->stream;
 
-    PrepArgs pr{(const float*)c->cams.p, V, nullptr, H, Hpad, T, (float*)c->hyps.p, (float4*)c->qtab.p,
-                (float*)c->vthr.p, (float2*)c->rot.p, (uint32_t*)c->errw.p};
+    PrepArgs pr{(const float*)c->cams.p, V, nullptr, H, Hpad, T, (float*)c->hyps.p, (float*)c->vthr.p,
+                (float2*)c->rot.p, (uint32_t*)c->errw.p};
     unsigned* box_keys = reinterpret_cast<unsigned*>(box + 8);
     if ((rc = run_launch(c, "k_prep", [&] {
              cudaError_t e2 = hf_launch_prep(pr, s);
@@ -490,8 +486,8 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     if (e != cudaSuccess) return hf_cuda_err(c, e, "clear work counter");
     // the projection also folds the points into the bounding box the features are normalised by
     ProjectArgs pa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p,
-                   c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, c->cfg.top_k_views, (float2*)c->samp.p, (float2*)c->ab.p,
-                   (unsigned long long*)c->work.p, box_keys, (const float2*)c->amap.p};
+                   c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, c->cfg.top_k_views, (float2*)c->samp.p,
+                   (unsigned long long*)c->vmask.p, (unsigned long long*)c->work.p, box_keys, (const float2*)c->amap.p};
     if ((rc = run_launch(c, "k_project", [&] { return hf_launch_project(pa, s); }))) return rc;
     // proposal: features -> network
     FeatArgs fa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p, c->conf.p,
@@ -502,34 +498,28 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
                                  (uint32_t*)c->errw.p, s);
          })))
         return rc;
-    // cost of the proposal, then the short refinement from it
-    FuseArgs fl{(const float*)c->pts.p, N, (const int32_t*)c->nbr.p, c->k, (const float*)c->cams.p, V,
-                (const float2*)c->samp.p, (const float2*)c->ab.p, (const float4*)c->qtab.p, (const float*)c->vthr.p,
-                (const float*)c->hyps.p, H, Hpad, rot_s, T_short, d_dir, d_cost, d_idx, d_status,
-                bi, (float*)(bi + N), bi + 2 * (size_t)N, hf_fuse_vblock_q(V, hc), hf_fuse_vblock_c(V)};
-    fl.start_dir = (const float*)c->prop.p;
     // the proposal's cost decides: above tau -> the plain fusion (fallback list), else the short
-    // refinement from the proposal (accepted list)
-    fl.list = list;
-    fl.list_count = count;
-    const StartSelectArgs ss{fl, tau, acc_list, acc_count};
-    if ((rc = run_launch(c, "k_start_select", [&] {
-             cudaError_t e2 = cudaMemsetAsync(count, 0, 2 * sizeof(int), s);
+    // refinement from the proposal
+    CostArgs base = hf_cost_args(c);
+    base.dir_out = d_dir;
+    base.cost_out = d_cost;
+    base.idx_out = d_idx;
+    base.status_out = d_status;
+    LearnArgs la{base, (const float*)c->prop.p, tau, list, count, fb_work, acc_work};
+    la.f.rot = rot_s;
+    la.f.T = T_short;
+    if ((rc = run_launch(c, "k_learn", [&] {
+             cudaError_t e2 = cudaMemsetAsync(count, 0, 24, s);   // count, fb_work, acc_work
              if (e2 == cudaSuccess) e2 = hf_launch_rot(rot_s, T_short, (double)alpha_short, s);
-             return e2 != cudaSuccess ? e2 : hf_launch_start_select(ss, s);
+             return e2 != cudaSuccess ? e2 : hf_launch_learn(la, s);
          })))
         return rc;
-    FuseArgs fs = fl;
-    fs.list = acc_list;
-    fs.list_count = acc_count;
-    if ((rc = run_launch(c, "k_refine_short", [&] { return hf_launch_refine(fs, s); }))) return rc;
-    FuseArgs fb = fl;
-    fb.start_dir = nullptr;
-    fb.rot = (const float2*)c->rot.p;
-    fb.T = T;
+    CostArgs fb = base;
+    fb.list = list;
+    fb.list_count = count;
     fb.fell_back = 1;
-    if ((rc = run_launch(c, "k_argmin_fallback", [&] { return hf_launch_argmin(fb, hc, s); }))) return rc;
-    if ((rc = run_launch(c, "k_refine_fallback", [&] { return hf_launch_refine(fb, s); }))) return rc;
+    if ((rc = run_launch(c, "k_fuse_fallback", [&] { return hf_launch_fuse(fb, s); }))) return rc;
+    c->learned_ran = true;
     if (mem_kind == HF_HOST) {
         e = cudaMemcpyAsync(dir_out, d_dir, (size_t)N * 12, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && cost_out) e = cudaMemcpyAsync(cost_out, d_cost, (size_t)N * 4, cudaMemcpyDeviceToHost, s);
@@ -556,25 +546,12 @@ cudaStream_t hf_mlp_stream(hf_mlp* m) { return m->stream; }
 
 extern "C" int hair_fuse_learned_work(hf_ctx* c, long long* fallback_point_views, long long* accepted_point_views) {
     if (!c) return HF_ERR_INVALID_ARG;
-    if (c->N <= 0 || !c->lmisc.p || !c->best.p) return hf_set_err(c, HF_ERR_NOT_UPLOADED, "no learned fusion has run");
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return hf_cuda_err(c, e, "stream synchronize");
-    const int N = c->N;
-    const char* lm = (const char*)c->lmisc.p;
-    int cnt[2] = {0, 0};
-    e = cudaMemcpy(cnt, lm + 64, sizeof cnt, cudaMemcpyDeviceToHost);
-    std::vector<int32_t> nvs(N), lst((size_t)cnt[0] + cnt[1]);
-    if (e == cudaSuccess) e = cudaMemcpy(nvs.data(), (const int32_t*)c->best.p + 2 * (size_t)N, (size_t)N * 4, cudaMemcpyDeviceToHost);
-    const int32_t* list = (const int32_t*)(lm + 256 + 64 * 8);
-    if (e == cudaSuccess && cnt[0] > 0) e = cudaMemcpy(lst.data(), list, (size_t)cnt[0] * 4, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && cnt[1] > 0) e = cudaMemcpy(lst.data() + cnt[0], list + N, (size_t)cnt[1] * 4, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return hf_cuda_err(c, e, "read view counts");
-    long long fb = 0, ac = 0;
-    for (int q = 0; q < cnt[0] + cnt[1]; ++q) {
-        const int32_t v = nvs[lst[q]];
-        (q < cnt[0] ? fb : ac) += v > 0 ? v : 0;
-    }
-    if (fallback_point_views) *fallback_point_views = fb;
-    if (accepted_point_views) *accepted_point_views = ac;
+    if (c->N <= 0 || !c->lmisc.p || !c->learned_ran) return hf_set_err(c, HF_ERR_NOT_UPLOADED, "no learned fusion has run");
+    unsigned long long w[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(w, (const char*)c->lmisc.p + 72, sizeof w, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return hf_cuda_err(c, e, "read work counters");
+    if (fallback_point_views) *fallback_point_views = (long long)w[0];
+    if (accepted_point_views) *accepted_point_views = (long long)w[1];
     return HF_OK;
 }

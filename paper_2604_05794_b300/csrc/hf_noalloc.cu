@@ -4,7 +4,7 @@
 // processes whose device memory is owned by a framework's caching allocator, or real-time code
 // with a fixed memory budget.  hair_fuse_fuse_directions_noalloc() serves them: the caller passes
 // every input and output as device memory, and the scratch the fusion needs between its kernels
-// (per point-view samples and projection ratios, the hypothesis table, a few per-scene constants)
+// (per point-view samples, the points' view-set masks, a few per-scene constants)
 // lives in one file-scope __device__ array of fixed size.  Every GPU that loads this library
 // holds that array until the process exits.
 //
@@ -21,22 +21,22 @@ namespace {
 constexpr long long kMaxPointViews = 1LL << 20;   // N * V
 constexpr long long kMaxPoints = 1LL << 18;       // N
 constexpr int kMaxViews = 1024;                   // V
-constexpr long long kMaxTable = 1LL << 16;        // V * Hpad (hypothesis table entries)
 
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
-constexpr size_t kSampBytes = align256(kMaxPointViews * sizeof(float2));
-constexpr size_t kAbBytes = align256(kMaxPointViews * sizeof(float2));
-constexpr size_t kQtabBytes = align256(kMaxTable * sizeof(float4));
+// samples: N rows of V rounded up to 4 views, at most N V + 3 N entries
+constexpr size_t kSampBytes = align256((size_t)(kMaxPointViews + 3 * kMaxPoints) * sizeof(float2));
+// view-set masks: N rows of ceil(V / 64) words, at most N words when V <= 64 and fewer beyond
+constexpr size_t kMaskBytes = align256((size_t)kMaxPoints * sizeof(unsigned long long));
 constexpr size_t kVthrBytes = align256(kMaxViews * sizeof(float));
 constexpr size_t kHypsBytes = align256(HF_MAX_H * 3 * sizeof(float));
 constexpr size_t kRotBytes = align256(HF_MAX_T * sizeof(float2));
 constexpr size_t kWorkBytes = 256;
 constexpr size_t kErrBytes = 256;
-constexpr size_t kBestBytes = align256(kMaxPoints * 12);   // argmin -> refinement hand-off
-constexpr size_t kScratchBytes =
-    kSampBytes + kAbBytes + kQtabBytes + kVthrBytes + kHypsBytes + kRotBytes + kWorkBytes + kErrBytes + kBestBytes;
+constexpr size_t kScratchBytes = kSampBytes + kMaskBytes + kVthrBytes + kHypsBytes + kRotBytes + kWorkBytes + kErrBytes;
+// the size the header states
+static_assert(kScratchBytes == 16794368, "static scratch size differs from the documented 16,794,368 bytes");
 
-// The shared scratch: 20.2 MB, reused (and overwritten) by every call on this device.
+// The shared scratch: 16,794,368 bytes (16.0 MiB), reused (and overwritten) by every call on this device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -82,26 +82,24 @@ extern "C" int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, in
     if (!cams || !angle || !conf || !xyz || (k > 0 && !nbr) || !dir_out)
         return fail(HF_ERR_INVALID_ARG, "null input or dir_out pointer");
     if (conf_dtype != HF_F32 && conf_dtype != HF_F16) return fail(HF_ERR_INVALID_ARG, "conf_dtype must be HF_F32 or HF_F16");
-    const int hc = hf_fuse_chunk_for(H);
-    const int Hpad = (H + hc - 1) / hc * hc;
     if ((long long)N * V > kMaxPointViews) return fail(HF_ERR_SHAPE, "N * V exceeds the static scratch limit of 1048576 point-views");
     if (N > kMaxPoints) return fail(HF_ERR_SHAPE, "N exceeds the static scratch limit of 262144 points");
     if (V > kMaxViews) return fail(HF_ERR_SHAPE, "V exceeds the static scratch limit of 1024 views");
-    if ((long long)V * Hpad > kMaxTable) return fail(HF_ERR_SHAPE, "V * H (H rounded up to the hypothesis chunk) exceeds 65536");
     if ((long long)width * height > (1LL << 31)) return fail(HF_ERR_SHAPE, "map larger than 2^31 pixels");
+    const int Vs = hf_samp_stride(V), Vw = hf_mask_words(V), Hpad = hf_hpad(H);
+    if ((size_t)N * Vs * sizeof(float2) > kSampBytes || (size_t)N * Vw * sizeof(unsigned long long) > kMaskBytes)
+        return fail(HF_ERR_SHAPE, "the samples or view-set masks exceed the static scratch");
 
     unsigned char* base = nullptr;
     int rc = scratch_for_current_device(&base);
     if (rc) return rc;
     float2* samp = (float2*)base;
-    float2* ab = (float2*)(base + kSampBytes);
-    float4* qtab = (float4*)(base + kSampBytes + kAbBytes);
-    float* vthr = (float*)(base + kSampBytes + kAbBytes + kQtabBytes);
-    float* hy = (float*)(base + kSampBytes + kAbBytes + kQtabBytes + kVthrBytes);
-    float2* rot = (float2*)(base + kSampBytes + kAbBytes + kQtabBytes + kVthrBytes + kHypsBytes);
-    unsigned long long* work = (unsigned long long*)(base + kSampBytes + kAbBytes + kQtabBytes + kVthrBytes + kHypsBytes + kRotBytes);
+    unsigned long long* vmask = (unsigned long long*)(base + kSampBytes);
+    float* vthr = (float*)(base + kSampBytes + kMaskBytes);
+    float* hy = (float*)(base + kSampBytes + kMaskBytes + kVthrBytes);
+    float2* rot = (float2*)(base + kSampBytes + kMaskBytes + kVthrBytes + kHypsBytes);
+    unsigned long long* work = (unsigned long long*)(base + kSampBytes + kMaskBytes + kVthrBytes + kHypsBytes + kRotBytes);
     uint32_t* errw = (uint32_t*)((unsigned char*)work + kWorkBytes);
-    int32_t* best = (int32_t*)((unsigned char*)errw + kErrBytes);
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
     // the counter and the error word keep the previous call's values: clear them
@@ -113,13 +111,33 @@ extern "C" int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, in
     if (e != cudaSuccess) return fail(HF_ERR_CUDA, cudaGetErrorString(e));
     if (host_err & HF_DEV_ERR_BAD_NBR) return fail(HF_ERR_INVALID_ARG, "a neighbour index is outside [0, N)");
 
-    PrepArgs pr{cams, V, hyps, H, Hpad, T, hy, qtab, vthr, rot, errw};
+    PrepArgs pr{cams, V, hyps, H, Hpad, T, hy, vthr, rot, errw};
     e = hf_launch_prep(pr, s);
-    ProjectArgs pa{xyz, N, cams, V, width, height, angle, conf, conf_dtype == HF_F16 ? 1 : 0, top_k, samp, ab, work};
+    ProjectArgs pa{xyz, N, cams, V, width, height, angle, conf, conf_dtype == HF_F16 ? 1 : 0, top_k, samp, vmask, work};
     if (e == cudaSuccess) e = hf_launch_project(pa, s);
-    FuseArgs fa{xyz, N, nbr, k, cams, V, samp, ab, qtab, vthr, hy, H, Hpad, rot, T, dir_out, cost_out, idx_out, status_out,
-                best, (float*)(best + N), best + 2 * (size_t)N, hf_fuse_vblock_q(V, hc), hf_fuse_vblock_c(V)};
-    if (e == cudaSuccess) e = hf_launch_fuse(fa, hc, s);
+    CostArgs fa{};
+    fa.pts = xyz;
+    fa.N = N;
+    fa.nbr = nbr;
+    fa.k = k;
+    fa.cams = cams;
+    fa.V = V;
+    fa.samp = samp;
+    fa.Vs = Vs;
+    fa.vmask = vmask;
+    fa.Vw = Vw;
+    fa.vthr = vthr;
+    fa.hyps = hy;
+    fa.H = H;
+    fa.Hpad = Hpad;
+    fa.rot = rot;
+    fa.T = T;
+    fa.L = hf_cost_lanes(top_k > 0 && top_k < V ? top_k : V, k);
+    fa.dir_out = dir_out;
+    fa.cost_out = cost_out;
+    fa.idx_out = idx_out;
+    fa.status_out = status_out;
+    if (e == cudaSuccess) e = hf_launch_fuse(fa, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&host_err, errw, sizeof host_err, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(HF_ERR_CUDA, cudaGetErrorString(e));

@@ -62,10 +62,10 @@ def _equal(a, b):
         assert x.dtype == y.dtype and np.array_equal(x.view(np.uint8), y.view(np.uint8))
 
 
-@pytest.mark.parametrize("shape", [dict(autotune=True), dict(autotune=False, hchunk=8, points_per_cta=64, order=2),
-                                   dict(autotune=False, hchunk=16, points_per_cta=256, order=3),
-                                   dict(autotune=False, hchunk=8, points_per_cta=128, order=1),
-                                   dict(autotune=False, hchunk=32, points_per_cta=128, order=0)])
+@pytest.mark.parametrize("shape", [dict(autotune=True), dict(autotune=False, cta_threads=64, order=2),
+                                   dict(autotune=False, cta_threads=256, order=3),
+                                   dict(autotune=False, cta_threads=128, order=1),
+                                   dict(autotune=False, cta_threads=128, order=0)])
 def test_plain_batch_equals_alone(scenes, shape):
     import torch
 
@@ -88,9 +88,9 @@ def test_plain_batch_equals_alone(scenes, shape):
         assert np.all(lat > 0) and np.all(np.isfinite(lat))
         assert np.all(b.fallbacks() == 0)
         t = b.tuning()
-        assert t["hchunk"] in (8, 16, 32) and t["points_per_cta_argmin"] in (64, 128, 256)
+        assert t["cta_threads"] in (64, 128, 256)
         if not shape["autotune"]:
-            assert t["hchunk"] == shape["hchunk"] and t["points_per_cta_refine"] == shape["points_per_cta"]
+            assert t["cta_threads"] == shape["cta_threads"]
     torch.cuda.synchronize()
     for f in ctxs:
         f.close()
