@@ -7,9 +7,9 @@ Default workload (serving16): the learned + batched form against the plain form 
 of 16 synthetic scenes (50k-1M points, 16-64 views, 512x512 to 1920x1080 maps, H = 64, k = 8,
 T = 8).  One step = one fusion of every point of every scene: for the learned + batched form, one
 replay of the batch's CUDA graph (per-stage persistent launches over all scenes: constants,
-projection + gather, features, proposal network, short refinement, fallback selection, argmin and
-refinement of the fallback points); for the plain form, the plain fusion of the scenes one after
-another.  The proposal network is trained on the GPU first (library kernels, four scenes shaped like
+projection + gather, features, proposal network, proposal cost with fallback selection and short
+refinement, argmin and refinement of the fallback points); for the plain form, the plain fusion of
+the scenes one after another.  The proposal network is trained on the GPU first (library kernels, four scenes shaped like
 the full workload) and its fallback threshold calibrated on a training scene.
 
 --workload full|mid|tiny: the plain fusion of one resident scene (full: 1,000,000 points, 64 views
@@ -64,6 +64,71 @@ FPMVO_CFG = dict(K=5, S=5, P=5, lambda_px=4.0, delta=0.0046, eps_vis=0.02)
 PHG_CFG = dict(voxel=0.02, step=0.01, max_steps=64, root_steps=4, cos_turn=0.5, occ_cap=4, batch=32768, link_dist=0.03,
                link_cos=0.7)
 SM_COUNT, FP32_LANES_PER_SM = 148, 128
+
+
+def s8d_ops(k):
+    """FP32 operations per (direction, view) as the survey's measurement section counts them: 3 per
+    patch member (multiply, multiply-add, maximum) + 12 per (hypothesis, view), + 9 more per
+    refinement candidate (its rotation into the view)."""
+    per_hyp = 3 * (k + 1) + 12
+    return per_hyp, per_hyp + 9
+
+
+def issued_per_dir_view(k):
+    """Instructions the cost kernels issue per (direction, view), counted from their source: 6 for
+    r = J d, 2 for |r|^2, 2 to broadcast r, 3 per member pair (packed multiply, packed multiply-add,
+    three-input max of |x|), 3 for an odd last member, 4 for the threshold test, reciprocal square
+    root, scale and sum."""
+    kp = k + 1
+    for cand in (1, 4, 6, 9, 12, 17):   # the compiled patch widths
+        if kp <= cand:
+            kp = cand
+            break
+    return 14 + 3 * (kp // 2) + 3 * (kp & 1)
+
+
+_ALU_PEAK = None
+
+
+def alu_peak(reps=5):
+    """Measured FP32 peak for the cost kernels (hair_fuse_issue_rate, CUDA events, full-occupancy grid):
+    the best rate of the patch term's inner step (packed multiply / multiply-add and the three-input
+    max of absolute values), in operations/s at 3 operations per evaluation as the survey counts
+    them; scalar fma, packed fma and the three-input max are measured beside it.  Cached per run."""
+    global _ALU_PEAK
+    if _ALU_PEAK is None:
+        import paper_2604_05794_b300 as hf
+        rates = {}
+        for kind in ("ffma", "ffma2", "fmax3_abs", "patch", "patch3"):
+            rates[kind] = max(hf.issue_rate(kind, iters=4096)["ops_per_s"] for _ in range(reps))
+        _ALU_PEAK = {"peak": rates["patch3"], "rates_ops_per_s": rates,
+                     "source": "measured: hair_fuse_issue_rate HF_ISSUE_PATCH3 (2 mul.f32x2 + 2 fma.f32x2 + 2 "
+                               "three-input max of |x| per 4 patch-term evaluations, 3 ops each), best of "
+                               f"{reps} launches"}
+    return _ALU_PEAK
+
+
+# DRAM bytes (read + write) per work unit of a kernel from one ncu capture, valid only for the kernel
+# source it was taken on: the first 12 hex digits of the SHA-256 of csrc/hf_kernels.cu.  A kernel
+# whose source changed reports traffic null until it is captured again.
+TRAFFIC = {}
+
+
+def kernels_source_sha():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2604_05794_b300", "csrc", "hf_kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
+def kernel_traffic(name, units):
+    """(traffic bytes of a launch, source note) from TRAFFIC, or (None, why)."""
+    t = TRAFFIC.get(name)
+    if t is None:
+        return None, "no ncu capture of this kernel"
+    bpu, unit, sha, how = t
+    if sha != kernels_source_sha():
+        return None, f"stale: captured on kernel source {sha}, now {kernels_source_sha()}"
+    return bpu * units, f"{bpu:.2f} DRAM bytes per {unit} ({how}) x {units} units of this launch"
 
 
 def _hbm_peak():
@@ -418,29 +483,42 @@ def run_ours(args):
     if args.partition:
         point_views = point_views * R // N   # the range's share of the projection's work count
 
-    # rooflines: the cost kernels are FP32-issue bound, the projection/gather kernel HBM bound
-    peak_alu = SM_COUNT * FP32_LANES_PER_SM * 2032.0e6
-    per_member = 3 * (k + 1) + 6     # FP32 ops per (direction, view): 3 per patch member + 6
+    # rooflines: the cost kernel is FP32-issue bound, the projection/gather kernel HBM bound
+    ap = alu_peak()
+    ca, cr = s8d_ops(k)
     conf_b = sc["conf"].itemsize
-    work = {"k_argmin": (Hh * per_member, "alu"), "k_refine": (6 * T * per_member, "alu"),
-            "k_project": (4 + conf_b + 16, "hbm")}
     rooflines = {}
-    for name, (per_pv, bound) in work.items():
+    for name, per_pv, ndir in (("k_argmin", Hh * ca, Hh), ("k_refine", 6 * T * cr, 6 * T + 1)):
         if name not in kt:
             continue
         n_, t_ = kt[name]
         sec = t_ / n_ / 1e3
-        if bound == "alu":
-            ach, pk_, unit = per_pv * point_views / sec / 1e12, peak_alu / 1e12, "TFLOP/s"
-            src = "derived: 148 SMs x 128 FP32 lanes x 2032 MHz max SM clock (1 op per lane per clock)"
-            wk = f"{per_pv} FP32 ops per (point, view) in V_i x {point_views} point-views per launch"
-        else:
-            byt = per_pv * N * V + 12 * N
-            ach, pk_, unit = byt / sec / 1e9, HBM_GBS, "GB/s"
-            src = "of measured: MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"
-            wk = f"{per_pv} B per (point, view) x {N * V} point-views + 12 B per point"
-        rooflines[name] = {"bound": bound, "achieved": ach, "peak": pk_, "unit": unit, "frac": ach / pk_,
-                           "traffic": None, "kernel": name, "peak_source": src, "work": wk, "share": t_ / ms}
+        ach = per_pv * point_views / sec
+        issued = ndir * issued_per_dir_view(k) * point_views / sec
+        traffic, tsrc = kernel_traffic(name, point_views)
+        rooflines[name] = {
+            "bound": "alu", "achieved": ach / 1e12, "peak": ap["peak"] / 1e12, "unit": "TFLOP/s",
+            "frac": ach / ap["peak"], "traffic": traffic, "traffic_source": tsrc, "kernel": name,
+            "peak_source": ap["source"], "peak_rates_ops_per_s": ap["rates_ops_per_s"],
+            "work": (f"{Hh} x {ca} FP32 ops per (point, view) in V_i" if name == "k_argmin" else
+                     f"{6 * T} x {cr} FP32 ops per (point, view) in V_i") +
+                    f" (survey count) x {point_views} point-views per launch",
+            "builder_count": {"instr_per_dir_view": issued_per_dir_view(k), "directions": ndir,
+                              "achieved_instr_per_s": issued,
+                              "frac_of_ffma_issue": issued / ap["rates_ops_per_s"]["ffma"]},
+            "units": point_views, "ms": t_ / n_, "share": t_ / ms}
+    if "k_project" in kt:
+        n_, t_ = kt["k_project"]
+        sec = t_ / n_ / 1e3
+        alg = (12 + 4 * k + V * (4 + conf_b) + 20) * N
+        moved = (4 + conf_b) * N * V + 12 * N + 8 * N * V + 8 * N * ((V + 63) // 64)
+        traffic, tsrc = kernel_traffic("k_project", N * V)
+        rooflines["k_project"] = {
+            "bound": "hbm", "achieved": alg / sec / 1e9, "peak": HBM_GBS, "unit": "GB/s",
+            "frac": alg / sec / 1e9 / HBM_GBS, "traffic": traffic, "traffic_source": tsrc, "kernel": "k_project",
+            "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+            "work": f"12 + 4k + V (4 + conf bytes) + 20 B per point (the path's algorithmic bytes) x {N} points",
+            "moved_by_design_GBs": moved / sec / 1e9, "ms": t_ / n_, "share": t_ / ms}
     dom = max(rooflines, key=lambda x: rooflines[x]["share"])
     roofline = dict(rooflines[dom])
     kernels = {name: {"launches": n_, "ms_per_launch": t_ / max(1, n_), "share": t_ / ms} for name, (n_, t_) in kt.items()}
@@ -610,20 +688,11 @@ def serving_cpu_baseline(scenes, budget_s=15.0):
                       f"counts, evenly spaced in each; FP64 C + OpenMP, plain fusion, {dt:.1f} s"}
 
 
-# DRAM bytes (read + write) per work unit of the batched cost kernels, from one ncu --set full capture
-# of the 4-scene serving batch (profiles/k_refine_batch_k_argmin_batch_serving4_ncu.md); a full launch's
-# traffic is scaled from it by the units the launch processes.  Re-take it whenever these kernels change.
-DRAM_BYTES_PER_UNIT = {"k_refine_batch": (1022.566 + 12.861) * 1e6 / 14635443,      # per fallback point-view
-                       "k_argmin_batch": (600.096 + 15.433) * 1e6 / 14635443,       # per fallback point-view
-                       "k_refine_short_batch": (401.193 + 8.197) * 1e6 / 5276307,   # per accepted point-view
-                       "k_start_select_batch": (439.860 + 9.251) * 1e6 / 19911750,  # per point-view
-                       "k_project_batch": (176.747 + 283.276) * 1e6 / 19911750}     # per point-view
-
-
 def stage_rooflines(kt, ms_step, scenes, st, T_short):
     """Per-stage rooflines of the learned + batched run from one profiled eager run (stage times) and
-    the work counters of the library (point-views of all points and of the fallback points)."""
-    peak_alu = SM_COUNT * FP32_LANES_PER_SM * 2032.0e6
+    the work counters of the library (point-views of all points, of the fallback points and of the
+    accepted proposals)."""
+    ap = alu_peak()
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             pk = json.load(f)
@@ -632,45 +701,48 @@ def stage_rooflines(kt, ms_step, scenes, st, T_short):
     except (OSError, KeyError, ValueError, TypeError):
         bf16, bf16_src = 1400.0, "of fallback: 1.4 PFLOP/s sustained bf16"
     k, H, T = 8, 64, 8
-    per_member = 3 * (k + 1) + 6
+    ca, cr = s8d_ops(k)
     Ntot = sum(sc["N"] for sc in scenes)
-    proj_bytes = sum((4 + sc["conf"].itemsize + 16) * sc["N"] * sc["V"] + 12 * sc["N"] for sc in scenes)
+    proj_bytes = sum((12 + 4 * k + sc["V"] * (4 + sc["conf"].itemsize) + 20) * sc["N"] for sc in scenes)
     feat_bytes = sum((16 * (4 + sc["conf"].itemsize) + 12 + 128) * sc["N"] for sc in scenes)
-    pv, fpv = st["point_views"], st["fallback_point_views"]
-    apv = pv - fpv   # point-views of the accepted proposals
-    units = {"k_refine_batch": fpv, "k_argmin_batch": fpv, "k_refine_short_batch": apv, "k_start_select_batch": pv}
-    traffic_units = dict(units, k_project_batch=pv)
+    pv, fpv, apv = st["point_views"], st["fallback_point_views"], st["accepted_point_views"]
+    units = {"k_argmin_batch": fpv, "k_refine_batch": fpv, "k_refine_short_batch": apv, "k_select_batch": pv,
+             "k_project_batch": pv}
+    ip = issued_per_dir_view(k)
     work = {
-        "k_project_batch": ("hbm", proj_bytes, "(4 + conf bytes + 16) B per (point, view) + 12 B per point"),
-        "k_features_batch": ("hbm", feat_bytes, "16 x (4 + conf bytes) B gathered + 12 B in + 128 B out per point"),
-        "k_mlp": ("tensor", MLP_FLOP_PER_POINT * Ntot, f"{MLP_FLOP_PER_POINT} FLOP per point (51-256-256-3)"),
-        "k_start_select_batch": ("alu", per_member * pv, f"1 direction x {per_member} FP32 ops per (point, view), "
-                                 f"{pv} point-views"),
-        "k_refine_short_batch": ("alu", (6 * T_short + 1) * per_member * apv,
-                                 f"{6 * T_short + 1} directions x {per_member} FP32 ops per accepted (point, view), "
-                                 f"{apv} point-views"),
-        "k_argmin_batch": ("alu", H * per_member * fpv, f"{H} x {per_member} ops per fallback (point, view), {fpv}"),
-        "k_refine_batch": ("alu", 6 * T * per_member * fpv, f"{6 * T} x {per_member} ops per fallback (point, view)"),
+        "k_project_batch": ("hbm", proj_bytes, "12 + 4k + V (4 + conf bytes) + 20 B per point (the path's "
+                            "algorithmic bytes)", None),
+        "k_features_batch": ("hbm", feat_bytes, "16 x (4 + conf bytes) B gathered + 12 B in + 128 B out per point", None),
+        "k_mlp": ("tensor", MLP_FLOP_PER_POINT * Ntot, f"{MLP_FLOP_PER_POINT} FLOP per point (51-256-256-3)", None),
+        "k_select_batch": ("alu", ca * pv, f"{ca} FP32 ops per (point, view) for the proposal's cost ({pv} point-views)",
+                           pv * ip),
+        "k_refine_short_batch": ("alu", 6 * T_short * cr * apv,
+                                 f"{6 * T_short} x {cr} FP32 ops per accepted (point, view) ({apv})",
+                                 (6 * T_short + 1) * apv * ip),
+        "k_argmin_batch": ("alu", H * ca * fpv, f"{H} x {ca} FP32 ops per fallback (point, view), {fpv} point-views",
+                           H * fpv * ip),
+        "k_refine_batch": ("alu", 6 * T * cr * fpv, f"{6 * T} x {cr} FP32 ops per fallback (point, view), {fpv}",
+                           (6 * T + 1) * fpv * ip),
     }
     out = {}
-    for name, (bound, amount, how) in work.items():
+    for name, (bound, amount, how, issued) in work.items():
         if name not in kt:
             continue
         sec = kt[name][1] / 1e3
         if bound == "alu":
-            ach, peak, unit, src = amount / sec / 1e12, peak_alu / 1e12, "TFLOP/s", \
-                "derived: 148 SMs x 128 FP32 lanes x 2032 MHz (1 op per lane per clock)"
+            ach, peak, unit, src = amount / sec / 1e12, ap["peak"] / 1e12, "TFLOP/s", ap["source"]
         elif bound == "tensor":
             ach, peak, unit, src = amount / sec / 1e12, bf16, "TFLOP/s", bf16_src
         else:
             ach, peak, unit, src = amount / sec / 1e9, HBM_GBS, "GB/s", "of measured: MEASURED_PEAKS.json hbm_gbs"
-        traffic = DRAM_BYTES_PER_UNIT[name] * traffic_units[name] if name in DRAM_BYTES_PER_UNIT else None
+        traffic, tsrc = kernel_traffic(name, units.get(name, Ntot))
         out[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                     "traffic": traffic, "kernel": name, "peak_source": src, "work": how,
+                     "traffic": traffic, "traffic_source": tsrc, "kernel": name, "peak_source": src, "work": how,
                      "units": units.get(name, Ntot), "ms": kt[name][1], "share": kt[name][1] / ms_step}
-        if traffic is not None:
-            out[name]["traffic_source"] = ("DRAM read+write bytes per unit from the ncu capture of the 4-scene batch, "
-                                           "x units of this launch")
+        if bound == "alu":
+            out[name]["peak_rates_ops_per_s"] = ap["rates_ops_per_s"]
+            out[name]["builder_count"] = {"instr_per_dir_view": ip, "achieved_instr_per_s": issued / sec,
+                                          "frac_of_ffma_issue": issued / sec / ap["rates_ops_per_s"]["ffma"]}
     return out
 
 
@@ -970,9 +1042,10 @@ def run_learned(args):
     value, plain_value = Nall * K / (ms_l / 1e3), Nall * K / (ms_p / 1e3)
     ms_prof = sum(v[1] for v in kt.values())
     # per-stage rooflines from the exact work of this scene (the same units as the batched line)
-    st = {"point_views": point_views, "fallback_point_views": lw["fallback_point_views"]}
+    st = {"point_views": point_views, "fallback_point_views": lw["fallback_point_views"],
+          "accepted_point_views": lw["accepted_point_views"]}
     names = {"k_project": "k_project_batch", "k_features": "k_features_batch", "k_mlp": "k_mlp",
-             "k_start_select": "k_start_select_batch", "k_refine_short": "k_refine_short_batch",
+             "k_select": "k_select_batch", "k_refine_short": "k_refine_short_batch",
              "k_argmin_fallback": "k_argmin_batch", "k_refine_fallback": "k_refine_batch"}
     kt_b = {names[n_]: v for n_, v in kt.items() if n_ in names}
     rb = stage_rooflines(kt_b, ms_prof, [sc], st, SERVING_T_SHORT)
@@ -980,9 +1053,7 @@ def run_learned(args):
     rooflines = {}
     for n_b, r in rb.items():
         r = dict(r, kernel=back[n_b])
-        if n_b in DRAM_BYTES_PER_UNIT:   # per-unit traffic was taken on the batched kernels
-            r["traffic"] = None
-            r.pop("traffic_source", None)
+        r["traffic"], r["traffic_source"] = kernel_traffic(back[n_b], r["units"])
         rooflines[back[n_b]] = r
     kernels = {n_: {"launches": v[0], "ms": v[1], "share": v[1] / ms_prof} for n_, v in kt.items()}
     dom = max(rooflines, key=lambda x: rooflines[x]["share"])

@@ -285,10 +285,10 @@ int hair_fuse_eval_costs(hf_ctx* ctx, int M, const float* dirs, float* cost_out,
  *  - All pointers are device memory of the current device: cams, angle, conf, xyz, nbr and hyps
  *    (NULL = built-in set) as in those calls; dir_out (required), cost_out, idx_out, status_out
  *    (each may be NULL) as in hair_fuse_fuse_directions.  cfg gives H, k, T and top_k_views.
- *  - The scratch between the kernels is one static device array of 16,794,368 bytes (16.0 MiB)
+ *  - The scratch between the kernels is one static device array of 20,988,672 bytes (20.0 MiB)
  *    inside this library, which every GPU that loads the library holds until the process exits.
- *    Limits: N * V <= 1,048,576, N <= 262,144, V <= 1024; larger inputs are rejected with
- *    HF_ERR_SHAPE before any work is queued.
+ *    Limits: N * V <= 1,048,576, N <= 262,144, V <= 1024, V * Hq <= 65,536 (Hq = H rounded up to
+ *    a multiple of 32); larger inputs are rejected with HF_ERR_SHAPE before any work is queued.
  *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress, with
  *    that device current); make that first call before any stream capture.
  *  - Every call on a device shares the one array and leaves its contents behind; the call clears
@@ -430,8 +430,10 @@ int hair_fuse_batch_tuning(const hf_batch* b, int* out2);
 int hair_fuse_batch_profile_run(hf_batch* b, hf_kernel_time* out, int max_entries);
 /* Kernel launches issued so far (graph replays counted by their kernels), and from the last run the
  * (point, view) pairs in the points' view sets of all scenes and, for the learned path, of the
- * fallback points (any pointer may be NULL; the work counts synchronise). */
-int hair_fuse_batch_stats(hf_batch* b, long long* launches, long long* point_views, long long* fallback_point_views);
+ * fallback points and of the accepted proposals (any pointer may be NULL; the work counts
+ * synchronise). */
+int hair_fuse_batch_stats(hf_batch* b, long long* launches, long long* point_views, long long* fallback_point_views,
+                          long long* accepted_point_views);
 void hair_fuse_batch_destroy(hf_batch* b);
 const char* hair_fuse_batch_last_error(const hf_batch* b);
 

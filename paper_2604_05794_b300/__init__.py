@@ -116,7 +116,8 @@ _SIGS = {
     "hair_fuse_batch_fallbacks": ([_vp, _vp], _i),
     "hair_fuse_batch_tuning": ([_vp, _vp], _i),
     "hair_fuse_batch_profile_run": ([_vp, ctypes.POINTER(hf_kernel_time), _i], _i),
-    "hair_fuse_batch_stats": ([_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll), ctypes.POINTER(_ll)], _i),
+    "hair_fuse_batch_stats": ([_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll), ctypes.POINTER(_ll),
+                               ctypes.POINTER(_ll)], _i),
     "hair_fuse_batch_destroy": ([_vp], None),
     "hair_fuse_batch_last_error": ([_vp], ctypes.c_char_p),
     "hair_fuse_issue_rate": ([_i, _i, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -644,7 +645,9 @@ class Batch:
         return {recs[q].name.decode(): (recs[q].launches, recs[q].total_ms) for q in range(min(n, 16))}
 
     def stats(self):
-        """launches so far; (point, view) pairs of all points and of the fallback points (last run)."""
-        l, pv, fpv = _ll(0), _ll(0), _ll(0)
-        self._c(hair_fuse_batch_stats(self.h, ctypes.byref(l), ctypes.byref(pv), ctypes.byref(fpv)))
-        return dict(launches=l.value, point_views=pv.value, fallback_point_views=fpv.value)
+        """launches so far; (point, view) pairs of all points, of the fallback points and of the
+        accepted proposals (last run)."""
+        l, pv, fpv, apv = _ll(0), _ll(0), _ll(0), _ll(0)
+        self._c(hair_fuse_batch_stats(self.h, ctypes.byref(l), ctypes.byref(pv), ctypes.byref(fpv), ctypes.byref(apv)))
+        return dict(launches=l.value, point_views=pv.value, fallback_point_views=fpv.value,
+                    accepted_point_views=apv.value)

@@ -54,16 +54,17 @@ int ready(hf_ctx* c) {
 
 // K1 over the uploaded scene into the context's scratch
 int run_project(hf_ctx* c) {
-    const int Vs = hf_samp_stride(c->V), Vw = hf_mask_words(c->V);
+    const int Vw = hf_mask_words(c->V);
     int rc;
-    if ((rc = hf_ensure(c, c->samp, (size_t)c->N * Vs * sizeof(float2)))) return rc;
+    if ((rc = hf_ensure(c, c->samp, (size_t)c->N * c->V * sizeof(float2)))) return rc;
+    if ((rc = hf_ensure(c, c->ab, (size_t)c->N * c->V * sizeof(float2)))) return rc;
     if ((rc = hf_ensure(c, c->vmask, (size_t)c->N * Vw * sizeof(unsigned long long)))) return rc;
     if ((rc = hf_ensure(c, c->work, sizeof(unsigned long long)))) return rc;
     cudaError_t e = cudaMemsetAsync(c->work.p, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return hf_cuda_err(c, e, "clear work counter");
     ProjectArgs pa{(const float*)c->pts.p, c->N, (const float*)c->cams.p, c->V, c->W, c->Hh,
                    (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, c->cfg.top_k_views,
-                   (float2*)c->samp.p, (unsigned long long*)c->vmask.p, (unsigned long long*)c->work.p, nullptr,
+                   (float2*)c->samp.p, (float2*)c->ab.p, (unsigned long long*)c->vmask.p, (unsigned long long*)c->work.p, nullptr,
                    (const float2*)c->amap.p};
     return run_launch(c, "k_project", [&] { return hf_launch_project(pa, c->stream); });
 }
@@ -114,7 +115,7 @@ CostArgs hf_cost_args(const hf_ctx* c) {
     a.cams = (const float*)c->cams.p;
     a.V = c->V;
     a.samp = (const float2*)c->samp.p;
-    a.Vs = hf_samp_stride(c->V);
+    a.ab = (const float2*)c->ab.p;
     a.vmask = (const unsigned long long*)c->vmask.p;
     a.Vw = hf_mask_words(c->V);
     a.vthr = (const float*)c->vthr.p;
@@ -125,6 +126,9 @@ CostArgs hf_cost_args(const hf_ctx* c) {
     a.T = c->cfg.T;
     const int tk = c->cfg.top_k_views;
     a.L = hf_cost_lanes(tk > 0 && tk < c->V ? tk : c->V, c->k);
+    a.qtab = (const float4*)c->qtab.p;
+    a.Hq = hf_hq(c->cfg.H);
+    a.best_idx = (int32_t*)c->best.p;
     return a;
 }
 
@@ -266,8 +270,10 @@ int fuse_impl(hf_ctx* c, const float* hyps, bool ranged, int first, int count, f
     if ((rc = hf_ensure(c, c->vthr, (size_t)V * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->hyps, (size_t)Hpad * 3 * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->rot, (size_t)(T > 0 ? T : 1) * sizeof(float2)))) return rc;
+    if ((rc = hf_ensure(c, c->qtab, (size_t)V * hf_hq(H) * sizeof(float4)))) return rc;
+    if ((rc = hf_ensure(c, c->best, (size_t)c->N * sizeof(int32_t)))) return rc;
     PrepArgs pr{(const float*)c->cams.p, V, hyps_dev, H, Hpad, T, (float*)c->hyps.p, (float*)c->vthr.p,
-                (float2*)c->rot.p, (uint32_t*)c->errw.p};
+                (float2*)c->rot.p, (uint32_t*)c->errw.p, (float4*)c->qtab.p, hf_hq(H)};
     if ((rc = run_launch(c, "k_prep", [&] { return hf_launch_prep(pr, c->stream); }))) return rc;
     if ((rc = run_project(c))) return rc;
 
@@ -297,7 +303,8 @@ int fuse_impl(hf_ctx* c, const float* hyps, bool ranged, int first, int count, f
         fa.list_count = cnt;
         fa.out_first = first;
     }
-    if ((rc = run_launch(c, "k_fuse", [&] { return hf_launch_fuse(fa, c->stream); }))) return rc;
+    if ((rc = run_launch(c, "k_argmin", [&] { return hf_launch_argmin(fa, c->stream); }))) return rc;
+    if ((rc = run_launch(c, "k_refine", [&] { return hf_launch_refine(fa, c->stream); }))) return rc;
     if (mem_kind == HF_HOST) {
         cudaError_t e = cudaMemcpyAsync(dir_out, d_dir, (size_t)R * 12, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess && cost_out) e = cudaMemcpyAsync(cost_out, d_cost, (size_t)R * 4, cudaMemcpyDeviceToHost, c->stream);
@@ -333,7 +340,7 @@ int hair_fuse_eval_costs(hf_ctx* c, int M, const float* dirs, float* cost_out, i
     if ((rc = hf_ensure(c, c->hyps, (size_t)Hpad * 3 * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->rot, (size_t)(c->cfg.T > 0 ? c->cfg.T : 1) * sizeof(float2)))) return rc;
     PrepArgs pr{(const float*)c->cams.p, V, nullptr, c->cfg.H, Hpad, c->cfg.T, (float*)c->hyps.p, (float*)c->vthr.p,
-                (float2*)c->rot.p, (uint32_t*)c->errw.p};
+                (float2*)c->rot.p, (uint32_t*)c->errw.p, nullptr, 0};
     if ((rc = run_launch(c, "k_prep", [&] { return hf_launch_prep(pr, c->stream); }))) return rc;
     if ((rc = run_project(c))) return rc;
     const float* d_dirs = dirs;
@@ -439,8 +446,8 @@ void hair_fuse_destroy(hf_ctx* c) {
         cudaEventDestroy(r.beg);
         cudaEventDestroy(r.end);
     }
-    DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->amap, &c->depth, &c->dmap, &c->vmap, &c->fprec, &c->phg, &c->gabor, &c->gbank, &c->rlist, &c->pts, &c->nbr, &c->samp, &c->vmask,
-                      &c->vthr, &c->hyps, &c->rot, &c->outs, &c->evald, &c->errw, &c->work, &c->feat, &c->prop, &c->lmisc};
+    DevBuf* bufs[] = {&c->cams, &c->angle, &c->conf, &c->amap, &c->depth, &c->dmap, &c->vmap, &c->fprec, &c->phg, &c->gabor, &c->gbank, &c->rlist, &c->pts, &c->nbr, &c->samp, &c->ab, &c->vmask,
+                      &c->vthr, &c->qtab, &c->best, &c->hyps, &c->rot, &c->outs, &c->evald, &c->errw, &c->work, &c->feat, &c->prop, &c->lmisc};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->errw_host) cudaFreeHost(c->errw_host);

@@ -21,17 +21,33 @@
 
 namespace {
 
-// stage slots of the item counters
-enum { ST_PROJECT, ST_FEATURES, ST_LEARN, ST_MAIN, ST_MLP, ST_COUNT };
-const char* const kStageName[ST_COUNT] = {"k_project_batch", "k_features_batch", "k_learn_batch", "k_fuse_batch",
-                                          "k_mlp"};
-static_assert(ST_COUNT <= 8, "eight item counters");
+// stages of a run; the refinement stages run one launch per lane class (a point per thread, or 4, 8,
+// 16, 32 lanes per point), each with its own item counter
+enum { ST_PROJECT, ST_FEATURES, ST_SELECT, ST_SHORT, ST_ARGMIN, ST_MAIN, ST_MLP, ST_COUNT };
+const char* const kStageName[ST_COUNT] = {"k_project_batch", "k_features_batch", "k_select_batch", "k_refine_short_batch",
+                                          "k_argmin_batch", "k_refine_batch", "k_mlp"};
+constexpr int kClasses = 5;   // a point per thread (L = 0), then 4, 8, 16, 32 lanes per point
+int class_of(int L) { return L == 0 ? 0 : L <= 4 ? 1 : L <= 8 ? 2 : L <= 16 ? 3 : 4; }
+// item counter of a stage (and lane class)
+int counter_of(int stage, int cls) {
+    switch (stage) {
+        case ST_PROJECT: return 0;
+        case ST_FEATURES: return 1;
+        case ST_SELECT: return 2;
+        case ST_ARGMIN: return 3;
+        case ST_SHORT: return 4 + cls;
+        default: return 4 + kClasses + cls;
+    }
+}
+constexpr int kCounters = 4 + 2 * kClasses;
+static_assert(kCounters <= 16, "sixteen item counters");
 
 // device control block (bytes); [0, kZeroEnd) is cleared by k_prep_batch at the start of a run
-constexpr size_t kNextOff = 0;                                   // u32 [ST_COUNT] (padded to 8)
-constexpr size_t kDoneOff = 32;                                  // u32 [2][HF_MAX_BATCH]: learn, main
+constexpr size_t kNextOff = 0;                                   // u32 [16] item counters
+constexpr size_t kDoneOff = 64;                                  // u32 [2][HF_MAX_BATCH]: short, main
 constexpr size_t kCountOff = kDoneOff + 2 * HF_MAX_BATCH * 4;    // i32 [HF_MAX_BATCH]: fallback list lengths
-constexpr size_t kWorkOff = kCountOff + HF_MAX_BATCH * 4;        // u64 [HF_MAX_BATCH]: (point, view) pairs
+constexpr size_t kAccOff = kCountOff + HF_MAX_BATCH * 4;         // i32 [HF_MAX_BATCH]: accepted list lengths
+constexpr size_t kWorkOff = kAccOff + HF_MAX_BATCH * 4;          // u64 [HF_MAX_BATCH]: (point, view) pairs
 constexpr size_t kFbWorkOff = kWorkOff + HF_MAX_BATCH * 8;       // u64 [HF_MAX_BATCH]: those of fallback points
 constexpr size_t kAccWorkOff = kFbWorkOff + HF_MAX_BATCH * 8;    // u64 [HF_MAX_BATCH]: of accepted proposals
 constexpr size_t kStampOff = kAccWorkOff + HF_MAX_BATCH * 8;     // u64 [2][HF_MAX_BATCH]: completion times
@@ -58,7 +74,8 @@ struct ArgBlock {
     PrepArgs prep[HF_MAX_BATCH];
     ProjectArgs proj[HF_MAX_BATCH];
     FeatArgs feat[HF_MAX_BATCH];
-    LearnArgs learn[HF_MAX_BATCH];
+    LearnArgs sel[HF_MAX_BATCH];
+    CostArgs shrt[HF_MAX_BATCH];
     CostArgs main[HF_MAX_BATCH];
 };
 
@@ -73,7 +90,10 @@ struct hf_batch {
     cudaStream_t stream = nullptr;  // the batch's own non-blocking stream (captured)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, t_beg = nullptr, t_end = nullptr;
     int kp = 9, nt = 128, order = 1;   // nt: threads per CTA of the cost kernels; order: 1 heaviest first, 2 as given, 3 lightest first
-    int hpad_max = 2;
+    struct Class {
+        int L, first, count, hmax;   // lanes per point, positions [first, first + count), largest H
+    };
+    std::vector<Class> cls;          // the lane classes present, positions grouped by class
     bool tuned = false, configured = false;
     long long total = 0;
     char* ctl = nullptr;
@@ -83,6 +103,7 @@ struct hf_batch {
     float* prop = nullptr;
     uint16_t* h1 = nullptr;
     int32_t* list = nullptr;       // fallback points, per scene from its row offset
+    int32_t* acc_list = nullptr;   // accepted proposals, likewise
     cudaGraphExec_t gexec = nullptr;
     long long launches = 0;   // kernels enqueued (graph replays counted by their kernels)
     std::string err;
@@ -120,9 +141,20 @@ int configure(hf_batch* b) {
         std::stable_sort(b->pos.begin(), b->pos.end(), [&](int u, int v) { return load(u) > load(v); });
     else if (b->order == 3)
         std::stable_sort(b->pos.begin(), b->pos.end(), [&](int u, int v) { return load(u) < load(v); });
+    // positions grouped by lane class (one launch per class), the order kept inside a class
+    auto lanes = [&](int u) { return hf_cost_args(b->sc[u].c).L; };
+    std::stable_sort(b->pos.begin(), b->pos.end(), [&](int u, int v) { return lanes(u) < lanes(v); });
+    b->cls.clear();
+    for (int p = 0; p < ns; ++p) {
+        const int L = lanes(b->pos[p]), H = b->sc[b->pos[p]].c->cfg.H;
+        if (b->cls.empty() || b->cls.back().L != L) b->cls.push_back({L, p, 0, 0});
+        b->cls.back().count++;
+        b->cls.back().hmax = std::max(b->cls.back().hmax, H);
+    }
     const bool learned = b->mlp != nullptr;
     unsigned* box = reinterpret_cast<unsigned*>(b->ctl + kBoxOff);
     int* count = reinterpret_cast<int*>(b->ctl + kCountOff);
+    int* acc = reinterpret_cast<int*>(b->ctl + kAccOff);
     unsigned long long* work = reinterpret_cast<unsigned long long*>(b->ctl + kWorkOff);
     unsigned long long* fb_work = reinterpret_cast<unsigned long long*>(b->ctl + kFbWorkOff);
     unsigned long long* acc_work = reinterpret_cast<unsigned long long*>(b->ctl + kAccWorkOff);
@@ -135,10 +167,10 @@ int configure(hf_batch* b) {
         hf_ctx* c = s.c;
         const int N = c->N, V = c->V, H = c->cfg.H, T = c->cfg.T;
         A.prep[p] = PrepArgs{(const float*)c->cams.p, V, nullptr, H, hf_hpad(H), T, (float*)c->hyps.p,
-                             (float*)c->vthr.p, (float2*)c->rot.p, errw};
+                             (float*)c->vthr.p, (float2*)c->rot.p, errw, (float4*)c->qtab.p, hf_hq(H)};
         A.proj[p] = ProjectArgs{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh,
                                 (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0,
-                                c->cfg.top_k_views, (float2*)c->samp.p, (unsigned long long*)c->vmask.p, work + p,
+                                c->cfg.top_k_views, (float2*)c->samp.p, (float2*)c->ab.p, (unsigned long long*)c->vmask.p, work + p,
                                 learned ? box + 6 * p : nullptr, (const float2*)c->amap.p};
         A.feat[p] = FeatArgs{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh,
                              (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, nullptr,
@@ -149,13 +181,17 @@ int configure(hf_batch* b) {
         m.idx_out = s.idx;
         m.status_out = s.status;
         if (learned) {
-            // the proposal's cost sorts the points into the fallback list and the short refinement
-            LearnArgs la{m, b->prop + (size_t)s.off * 3, b->cfg.tau, b->list + s.off, count + p, fb_work + p,
-                         acc_work + p};
-            la.f.rot = rot_s;
-            la.f.T = b->cfg.T_short;
-            A.learn[p] = la;
-            m.list = b->list + s.off;
+            // the proposal's cost sorts the points into the fallback and the accepted list
+            A.sel[p] = LearnArgs{m, b->prop + (size_t)s.off * 3, b->cfg.tau, b->list + s.off, count + p, fb_work + p,
+                                 acc_work + p, b->acc_list + s.off, acc + p};
+            CostArgs f = m;   // accepted: T_short rounds from the proposal
+            f.list = b->acc_list + s.off;
+            f.list_count = acc + p;
+            f.start_dir = b->prop + (size_t)s.off * 3;
+            f.rot = rot_s;
+            f.T = b->cfg.T_short;
+            A.shrt[p] = f;
+            m.list = b->list + s.off;   // fallback: the plain fusion
             m.list_count = count + p;
             m.fell_back = 1;
         }
@@ -168,13 +204,14 @@ int configure(hf_batch* b) {
     return HF_OK;
 }
 
-BatchCtl ctl_for(hf_batch* b, int stage, int stamp_slot) {
+// work distribution of a stage over positions [first, first + count) (all positions when count < 0)
+BatchCtl ctl_for(hf_batch* b, int stage, int stamp_slot, int cls = 0, int first = 0, int count = -1) {
     BatchCtl c{};
-    c.next = reinterpret_cast<unsigned*>(b->ctl + kNextOff) + stage;
-    c.ns = (int)b->sc.size();
+    c.next = reinterpret_cast<unsigned*>(b->ctl + kNextOff) + counter_of(stage, cls);
+    c.ns = count < 0 ? (int)b->sc.size() : count;
     if (stamp_slot >= 0) {
-        c.done = reinterpret_cast<unsigned*>(b->ctl + kDoneOff) + stamp_slot * HF_MAX_BATCH;
-        c.stamp = reinterpret_cast<unsigned long long*>(b->ctl + kStampOff) + stamp_slot * HF_MAX_BATCH;
+        c.done = reinterpret_cast<unsigned*>(b->ctl + kDoneOff) + stamp_slot * HF_MAX_BATCH + first;
+        c.stamp = reinterpret_cast<unsigned long long*>(b->ctl + kStampOff) + stamp_slot * HF_MAX_BATCH + first;
     }
     return c;
 }
@@ -203,13 +240,32 @@ cudaError_t launch_stage(hf_batch* b, int stage) {
         case ST_FEATURES: return hf_launch_features_batch(A->feat, ctl_for(b, ST_FEATURES, -1), s);
         case ST_MLP:
             return hf_mlp_infer_rows(b->mlp, b->x, b->total, b->h1, b->prop, reinterpret_cast<uint32_t*>(b->ctl + kErrOff), s);
-        case ST_LEARN: return hf_launch_learn_batch(A->learn, ctl_for(b, ST_LEARN, 0), b->kp, b->nt, s);
-        default: return hf_launch_fuse_batch(A->main, ctl_for(b, ST_MAIN, 1), b->kp, b->nt, b->hpad_max, s);
+        case ST_SELECT: return hf_launch_select_batch(A->sel, ctl_for(b, ST_SELECT, -1), b->kp, s);
+        case ST_ARGMIN: return hf_launch_argmin_batch(A->main, ctl_for(b, ST_ARGMIN, -1), b->kp, b->nt, s);
+        case ST_SHORT:
+        case ST_MAIN: {
+            for (const auto& k : b->cls) {
+                const BatchCtl c = ctl_for(b, stage, stage == ST_SHORT ? 0 : 1, class_of(k.L), k.first, k.count);
+                const cudaError_t e = hf_launch_refine_batch((stage == ST_SHORT ? A->shrt : A->main) + k.first, c, b->kp,
+                                                             k.L, b->nt, s);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        }
+        default: return cudaErrorInvalidValue;
     }
 }
 
+// launches of a stage
+int stage_launches(const hf_batch* b, int stage) {
+    return stage == ST_MLP ? 2 : (stage == ST_SHORT || stage == ST_MAIN) ? (int)b->cls.size() : 1;
+}
+
 // kernels of one run (the network's two GEMMs included)
-int kernels_per_run(const hf_batch* b) { return b->mlp ? 7 : 3; }
+int kernels_per_run(const hf_batch* b) {
+    const int nc = (int)b->cls.size();
+    return b->mlp ? 7 + 2 * nc : 3 + nc;
+}
 
 // the whole run: constants (and counter reset), then every stage in order; with ev (profiling,
 // eager only) an event is recorded after the constants and after every stage
@@ -219,10 +275,10 @@ cudaError_t enqueue(hf_batch* b, cudaEvent_t* ev = nullptr, int* stages_out = nu
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], b->stream);
     const bool learned = b->mlp != nullptr;
-    const int plain_stages[] = {ST_PROJECT, ST_MAIN};
-    const int learned_stages[] = {ST_PROJECT, ST_FEATURES, ST_MLP, ST_LEARN, ST_MAIN};
+    const int plain_stages[] = {ST_PROJECT, ST_ARGMIN, ST_MAIN};
+    const int learned_stages[] = {ST_PROJECT, ST_FEATURES, ST_MLP, ST_SELECT, ST_SHORT, ST_ARGMIN, ST_MAIN};
     const int* st = learned ? learned_stages : plain_stages;
-    const int n = learned ? 5 : 2;
+    const int n = learned ? 7 : 3;
     for (int q = 0; q < n && e == cudaSuccess; ++q) {
         e = launch_stage(b, st[q]);
         if (ev) cudaEventRecord(ev[2 + q], b->stream);
@@ -238,10 +294,12 @@ cudaError_t enqueue(hf_batch* b, cudaEvent_t* ev = nullptr, int* stages_out = nu
 int time_stage(hf_batch* b, int stage, int reps, float* ms) {
     float best = INFINITY;
     for (int r = 0; r < reps; ++r) {
-        cudaError_t e = cudaMemsetAsync(reinterpret_cast<unsigned*>(b->ctl + kNextOff) + stage, 0, 4, b->stream);
-        // the learned stage appends to the fallback lists and adds to the work counts: they start empty
-        if (e == cudaSuccess && stage == ST_LEARN) e = cudaMemsetAsync(b->ctl + kCountOff, 0, HF_MAX_BATCH * 4, b->stream);
-        if (e == cudaSuccess && stage == ST_LEARN) e = cudaMemsetAsync(b->ctl + kFbWorkOff, 0, 2 * HF_MAX_BATCH * 8, b->stream);
+        cudaError_t e = cudaSuccess;
+        for (int q = 0; q < kClasses && e == cudaSuccess; ++q)
+            e = cudaMemsetAsync(reinterpret_cast<unsigned*>(b->ctl + kNextOff) + counter_of(stage, q), 0, 4, b->stream);
+        // the selection appends to the lists and adds to the work counts: they start empty
+        if (e == cudaSuccess && stage == ST_SELECT) e = cudaMemsetAsync(b->ctl + kCountOff, 0, 2 * HF_MAX_BATCH * 4, b->stream);
+        if (e == cudaSuccess && stage == ST_SELECT) e = cudaMemsetAsync(b->ctl + kFbWorkOff, 0, 2 * HF_MAX_BATCH * 8, b->stream);
         if (e == cudaSuccess) e = cudaEventRecord(b->t_beg, b->stream);
         if (e == cudaSuccess) e = launch_stage(b, stage);
         if (e == cudaSuccess) e = cudaEventRecord(b->t_end, b->stream);
@@ -271,17 +329,18 @@ int autotune(hf_batch* b) {
     const int nts[] = {64, 128, 256};
     const bool learned = b->mlp != nullptr;
     if ((rc = configure(b)) || (rc = run_eager(b))) return rc;
-    // threads per CTA of the cost kernels (the learned stage, then the fusion of the fallback points)
+    // threads per CTA of the cost kernels (the short refinement, the argmin and the refinement)
     float best = INFINITY;
     int best_nt = b->nt;
     for (int nt : nts) {
         if (b->cfg.cta_threads && nt != b->cfg.cta_threads) continue;
         b->nt = nt;
-        float t = 0.0f, t2 = 0.0f;
-        if (learned && (rc = time_stage(b, ST_LEARN, 2, &t2))) return rc;
+        float t = 0.0f, t2 = 0.0f, t3 = 0.0f;
+        if (learned && (rc = time_stage(b, ST_SHORT, 2, &t2))) return rc;
+        if ((rc = time_stage(b, ST_ARGMIN, 2, &t3))) return rc;
         if ((rc = time_stage(b, ST_MAIN, 2, &t))) return rc;
-        if (t + t2 < best) {
-            best = t + t2;
+        if (t + t2 + t3 < best) {
+            best = t + t2 + t3;
             best_nt = nt;
         }
     }
@@ -343,7 +402,7 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
         return fail(HF_ERR_INVALID_ARG, "cta_threads: 0, 64, 128 or 256");
     if (c.order < 0 || c.order > 3) return fail(HF_ERR_INVALID_ARG, "order: 0, 1, 2 or 3");
     long long total = 0;
-    int max_k = 0, maxH = 1;
+    int max_k = 0;
     for (int s = 0; s < n_scenes; ++s) {
         hf_ctx* x = scenes[s];
         if (!x) return fail(HF_ERR_INVALID_ARG, "a scene is null");
@@ -352,7 +411,6 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
             if (scenes[t] == x) return fail(HF_ERR_INVALID_ARG, "a scene appears twice");
         total += x->N;
         max_k = std::max(max_k, x->k);
-        maxH = std::max(maxH, x->cfg.H);
     }
     if (total > (1LL << 30)) return fail(HF_ERR_SHAPE, "more than 2^30 points in a batch");
     hf_batch* b = new hf_batch();
@@ -361,7 +419,6 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
     b->user = (cudaStream_t)cuda_stream;
     b->total = total;
     b->kp = hf_batch_kp_for(max_k);
-    b->hpad_max = hf_hpad(maxH);
     b->nt = c.cta_threads ? c.cta_threads : 128;
     b->order = c.order ? c.order : 1;
     b->sc.resize(n_scenes);
@@ -380,6 +437,7 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
         if (e == cudaSuccess) e = cudaMalloc(&b->prop, (size_t)total * 3 * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&b->h1, (size_t)total * 256 * sizeof(uint16_t));
         if (e == cudaSuccess) e = cudaMalloc(&b->list, (size_t)total * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&b->acc_list, (size_t)total * sizeof(int32_t));
     }
     if (e != cudaSuccess) {
         hair_fuse_batch_destroy(b);
@@ -396,11 +454,14 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
         bs.work = (double)x->V * (x->cfg.H + 6.0 * x->cfg.T) * (x->k + 1);
         const int N = x->N, V = x->V, T = x->cfg.T;
         const int Hpad = hf_hpad(x->cfg.H);
-        if (!rc) rc = hf_ensure(x, x->samp, (size_t)N * hf_samp_stride(V) * sizeof(float2));
+        if (!rc) rc = hf_ensure(x, x->samp, (size_t)N * V * sizeof(float2));
+        if (!rc) rc = hf_ensure(x, x->ab, (size_t)N * V * sizeof(float2));
         if (!rc) rc = hf_ensure(x, x->vmask, (size_t)N * hf_mask_words(V) * sizeof(unsigned long long));
         if (!rc) rc = hf_ensure(x, x->vthr, (size_t)V * sizeof(float));
         if (!rc) rc = hf_ensure(x, x->hyps, (size_t)Hpad * 3 * sizeof(float));
         if (!rc) rc = hf_ensure(x, x->rot, (size_t)(T > 0 ? T : 1) * sizeof(float2));
+        if (!rc) rc = hf_ensure(x, x->qtab, (size_t)V * hf_hq(x->cfg.H) * sizeof(float4));
+        if (!rc) rc = hf_ensure(x, x->best, (size_t)N * sizeof(int32_t));
         if (!rc && cudaStreamSynchronize(x->stream) != cudaSuccess) rc = HF_ERR_CUDA;   // uploads complete
         if (rc) g_batch_create_err = "scene " + std::to_string(s) + ": " + x->err;
     }
@@ -543,7 +604,7 @@ extern "C" int hair_fuse_batch_profile_run(hf_batch* b, hf_kernel_time* out, int
             cudaEventElapsedTime(&t, ev[1 + q], ev[2 + q]);
             if (k < max_entries) {
                 std::snprintf(out[k].name, sizeof out[k].name, "%s", kStageName[st[q]]);
-                out[k].launches = st[q] == ST_MLP ? 2 : 1;
+                out[k].launches = stage_launches(b, st[q]);
                 out[k].total_ms = t;
             }
         }
@@ -554,22 +615,26 @@ extern "C" int hair_fuse_batch_profile_run(hf_batch* b, hf_kernel_time* out, int
 }
 
 extern "C" int hair_fuse_batch_stats(hf_batch* b, long long* launches, long long* point_views,
-                                     long long* fallback_point_views) {
+                                     long long* fallback_point_views, long long* accepted_point_views) {
     if (!b) return HF_ERR_INVALID_ARG;
     if (launches) *launches = b->launches;
-    if (!point_views && !fallback_point_views) return HF_OK;
+    if (!point_views && !fallback_point_views && !accepted_point_views) return HF_OK;
     const int ns = (int)b->sc.size();
-    unsigned long long w[2 * HF_MAX_BATCH];
+    unsigned long long w[3 * HF_MAX_BATCH];
     cudaError_t e = cudaMemcpyAsync(w, b->ctl + kWorkOff, sizeof w, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return b_cuda(b, e, "read work counters");
-    long long pv = 0, fpv = 0;
+    long long pv = 0, fpv = 0, apv = 0;
     for (int p = 0; p < ns; ++p) {
         pv += (long long)w[p];
-        if (b->mlp) fpv += (long long)w[HF_MAX_BATCH + p];
+        if (b->mlp) {
+            fpv += (long long)w[HF_MAX_BATCH + p];
+            apv += (long long)w[2 * HF_MAX_BATCH + p];
+        }
     }
     if (point_views) *point_views = pv;
     if (fallback_point_views) *fallback_point_views = fpv;
+    if (accepted_point_views) *accepted_point_views = apv;
     return HF_OK;
 }
 
@@ -584,6 +649,7 @@ extern "C" void hair_fuse_batch_destroy(hf_batch* b) {
     cudaFree(b->prop);
     cudaFree(b->h1);
     cudaFree(b->list);
+    cudaFree(b->acc_list);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->t_beg) cudaEventDestroy(b->t_beg);

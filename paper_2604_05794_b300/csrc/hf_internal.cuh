@@ -41,9 +41,12 @@ struct hf_ctx {
     int N = 0, k = 0;
     DevBuf pts, nbr;
     // scratch of the fusion path
-    DevBuf samp;    // [N][Vs] float2: C (cos theta, sin theta) at the point's pixel, 0 when not visible
+    DevBuf samp;    // [V][N] float2: C (cos theta, sin theta) at the point's pixel, 0 when not visible
+    DevBuf ab;      // [V][N] float2: projection ratios (X/Z, Y/Z); NaN when v is not in the point's view set
     DevBuf vmask;   // [N][Vw] u64: the point's view set V_i
     DevBuf vthr;    // [V] float: degenerate-offset threshold 1e-20 (fx^2 + fy^2)
+    DevBuf qtab;    // [V][Hq] float4: the argmin's hypothesis-pair table
+    DevBuf best;    // [N] int32: the argmin's hypothesis index
     DevBuf hyps;    // [Hpad] x 3 float
     DevBuf rot;     // [T] float2: (cos alpha_t, sin alpha_t)
     DevBuf outs;    // device outputs staged for HF_HOST calls
@@ -101,13 +104,15 @@ int run_launch(hf_ctx* c, const char* name, F&& f) {
 // Kernel-launch helpers (defined in hf_kernels.cu); each returns the launch error -------------
 //
 // Scratch of the fusion path (per context, or the static array of the allocation-free entry):
-//   samp  [N][Vs] float2  C (cos theta, sin theta) at point i's own pixel in view v, 0 when the point
-//                         does not project into view v; Vs = V rounded up to 4 (32-byte rows)
-//   vmask [N][Vw] u64     bit v of word v / 64: v is in the point's view set V_i; Vw = ceil(V / 64)
+//   samp  [V][N] float2  C (cos theta, sin theta) at point i's own pixel in view v, 0 when the point
+//                        does not project into view v
+//   ab    [V][N] float2  projection ratios (X/Z, Y/Z) of point i in view v; NaN when v is not in V_i
+//   vmask [N][Vw] u64    bit v of word v / 64: v is in the point's view set V_i; Vw = ceil(V / 64)
 //   hyps  [Hpad][3] f32   the hypotheses, padded to an even count with copies of h_0
+//   qtab  [V][Hq] float4  hypothesis pairs q = R_v h folded with fx, fy (the argmin's table)
+//   best  [N] i32         the argmin's hypothesis index, read by the refinement
 //   vthr  [V] f32         degenerate-offset threshold 1e-20 (fx^2 + fy^2) per view
 //   rot   [T] float2      (cos alpha_t, sin alpha_t) of the refinement rounds
-__host__ __device__ inline int hf_samp_stride(int V) { return (V + 3) & ~3; }
 __host__ __device__ inline int hf_mask_words(int V) { return (V + 63) / 64; }
 __host__ __device__ inline int hf_hpad(int H) { return (H + 1) & ~1; }
 
@@ -116,7 +121,7 @@ struct ProjectArgs {
     const float* cams; int V; int W; int H;
     const float* angle; const void* conf; int conf_f16;
     int top_k;
-    float2* samp; unsigned long long* vmask;
+    float2* samp; float2* ab; unsigned long long* vmask;
     unsigned long long* work;   // += number of (point, view) pairs in the view sets
     unsigned* box_keys;         // optional: bounding-box keys lo[3], hi[3] folded in (see hf_launch_bbox_init)
     const float2* amap;         // optional: interleaved (angle, confidence) maps, read instead of angle / conf
@@ -136,44 +141,54 @@ struct PrepArgs {
     float* vthr;           // out [V]
     float2* rot;           // out [T]
     uint32_t* errw;
+    float4* qtab; int Hq;  // out [V][Hq]: the argmin's hypothesis-pair table (Hq = hf_hq(H)); may be null
 };
+// hypotheses of the argmin's table: H rounded up to its chunk of 32
+__host__ __device__ inline int hf_hq(int H) { return (H + 31) & ~31; }
 cudaError_t hf_launch_prep(const PrepArgs& a, cudaStream_t s);
 
-// The cost kernels: a point is served by a group of L lanes (L in {4, 8, 16, 32}) over which the
-// views of its view set are dealt; hf_cost_lanes() picks L from the largest view-set size.
+// The cost kernels: the argmin runs a point per thread; the refinement either also runs a point per
+// thread (L = 0) or serves a point by a group of L lanes (L in {4, 8, 16, 32}) over which the views
+// of its view set are dealt (hf_cost_lanes() picks from the largest view-set size).
 struct CostArgs {
     const float* pts; int N;
     const int32_t* nbr; int k;
     const float* cams; int V;
-    const float2* samp; int Vs;
+    const float2* samp; const float2* ab;
     const unsigned long long* vmask; int Vw;
     const float* vthr;
     const float* hyps; int H; int Hpad;
     const float2* rot; int T;
-    int L;                                               // lanes per point
+    int L;                                               // refinement: lanes per point, 0 = a point per thread
     float* dir_out; float* cost_out; int32_t* idx_out; uint8_t* status_out;
     int32_t* nvs;                                        // optional [N]: |V_i|, -1 for a non-finite point
     const int32_t* list; const int* list_count;          // optional: only these points (device count)
     int fell_back;                                       // mark outputs HF_STATUS_FELL_BACK
     int out_first;   // outputs of point i go to row i - out_first (0: point-indexed)
+    const float4* qtab; int Hq;                          // argmin: hypothesis-pair table
+    int32_t* best_idx;                                   // argmin output, refinement start (hyps[best_idx[i]])
+    const float* start_dir;                              // refinement start instead (learned proposals)
 };
 int hf_cost_lanes(int veff, int k);    // lanes per point for view sets of up to veff views
 struct hf_ctx;
 CostArgs hf_cost_args(const hf_ctx* c);   // the uploaded scene's arguments (outputs, list unset)
-cudaError_t hf_launch_fuse(const CostArgs& a, cudaStream_t s);   // argmin + refinement
+cudaError_t hf_launch_argmin(const CostArgs& a, cudaStream_t s);   // K2: -> best_idx
+cudaError_t hf_launch_refine(const CostArgs& a, cudaStream_t s);   // K3: from best_idx or start_dir -> outputs
+cudaError_t hf_launch_fuse(const CostArgs& a, cudaStream_t s);     // K2 then K3
 
 // Learned path after the network: the cost c_i of the proposal start_dir; points with a view and
 // c_i > tau are appended to fb_list (count *fb_count, from 0; work += |V_i| into fb_work), the
-// others get f.T rounds of the refinement from the proposal with steps f.rot (work into acc_work);
-// non-finite points get their BAD_INPUT outputs.  f.nvs (if set) receives |V_i|.
+// other finite points to acc_list (count *acc_count; work into acc_work); non-finite points get
+// their BAD_INPUT outputs.
 struct LearnArgs {
     CostArgs f;
     const float* start_dir;
     float tau;
     int32_t* fb_list; int* fb_count;
     unsigned long long* fb_work; unsigned long long* acc_work;
+    int32_t* acc_list; int* acc_count;
 };
-cudaError_t hf_launch_learn(const LearnArgs& a, cudaStream_t s);
+cudaError_t hf_launch_select(const LearnArgs& a, cudaStream_t s);
 
 struct EvalArgs {
     CostArgs f;
@@ -224,10 +239,12 @@ int hf_batch_kp_for(int k);   // patch width instantiated for the batched kernel
 cudaError_t hf_launch_prep_batch(const PrepArgs* pr, int ns, const BatchReset& r, cudaStream_t s);
 cudaError_t hf_launch_project_batch(const ProjectArgs* pa, const BatchCtl& c, cudaStream_t s);
 cudaError_t hf_launch_features_batch(const FeatArgs* fe, const BatchCtl& c, cudaStream_t s);
-// nt: threads per CTA of the cost kernels (64, 128 or 256); kp from hf_batch_kp_for(max k); hpad_max
-// the largest Hpad of the scenes
-cudaError_t hf_launch_fuse_batch(const CostArgs* fa, const BatchCtl& c, int kp, int nt, int hpad_max, cudaStream_t s);
-cudaError_t hf_launch_learn_batch(const LearnArgs* la, const BatchCtl& c, int kp, int nt, cudaStream_t s);
+// The batched cost kernels (hf_batch_kernels.cu) over the c.ns scenes at fa / la; kp from
+// hf_batch_kp_for(max k); nt threads per CTA (64, 128 or 256).  The refinement takes the scenes
+// that share the lane count L.
+cudaError_t hf_launch_argmin_batch(const CostArgs* fa, const BatchCtl& c, int kp, int nt, cudaStream_t s);
+cudaError_t hf_launch_refine_batch(const CostArgs* fa, const BatchCtl& c, int kp, int L, int nt, cudaStream_t s);
+cudaError_t hf_launch_select_batch(const LearnArgs* la, const BatchCtl& c, int kp, cudaStream_t s);
 
 // ------------------------------------------------------------------ FPMVO (hf_fpmvo.cu)
 #define HF_FPMVO_MAX_K 8

@@ -5,16 +5,19 @@
 //   k_project       K1, thread per point: projection of the point into every view with the pixel
 //                   index decided in float-float arithmetic, nearest-pixel gather of the orientation
 //                   and confidence maps, view set (visible or top-K) of the point.
-//   k_fuse<KP>      K2 + K3, a group of lanes per point: the cost of every hypothesis (Eqs. proj_r ..
-//                   patch_min and the view mean), their argmin, then the T rounds of the six-rotation
-//                   refinement, from one gather of the point's patch held in registers.
-//   k_learn<KP>     the learned path after the network: cost of the proposal, fallback selection,
-//                   short refinement of the accepted proposals.
-//   k_eval<KP>      cost of caller-given directions (no argmin).
+//   k_argmin<KP>    K2, thread per point: the cost of every hypothesis (Eqs. proj_r .. patch_min and
+//                   the view mean) and their argmin, hypotheses in packed pairs.
+//   k_refine<KP,L>  K3, a group of L lanes per point: T rounds of the six-rotation refinement from
+//                   the argmin hypothesis (or a given start), the point's patch gathered once and held
+//                   in registers across the rounds.
+//   k_select<KP>    the learned path after the network: cost of the proposal and fallback selection.
+//   k_eval<KP,L>    cost of caller-given directions (no argmin).
 #include <math.h>
 
 #include <cuda_bf16.h>
 
+#include "hf_batchtiles.cuh"
+#include "hf_cost.cuh"
 #include "hf_ff.cuh"
 #include "hf_internal.cuh"
 
@@ -35,10 +38,11 @@ __device__ __forceinline__ unsigned fkey(float x) {
 __device__ __forceinline__ float fval(unsigned k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k); }
 
 // ------------------------------------------------------------------ K1: project + gather
-// One thread per point, views in groups of four.  For view v it writes
-//   samp[i][v] = C (cos theta, sin theta) at the point's pixel (0 when outside the view),
-// four views (one 32-byte sector of the row) at a time, and the point's view-set mask: every view
-// the point projects into, or with top_k > 0 the top_k of them by the confidence at the point's own
+// One thread per point, views in order.  For view v it writes
+//   samp[v][i] = C (cos theta, sin theta) at the point's pixel (0 when outside the view),
+//   ab[v][i]   = (X/Z, Y/Z) when v is in the point's view set, NaN otherwise,
+// and the point's view-set mask vmask[i][v / 64] (bit v % 64).  The view set is every view the
+// point projects into, or with top_k > 0 the top_k of them by the confidence at the point's own
 // pixel, ties to the lower view index.
 constexpr int kProjectThreads = 128;
 
@@ -64,9 +68,9 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
     if (i >= a.N) return;
     const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
     const size_t npx = (size_t)a.W * a.H;
-    const int Vs = hf_samp_stride(a.V), Vw = hf_mask_words(a.V);
-    float4* row = reinterpret_cast<float4*>(a.samp + (size_t)i * Vs);
+    const int Vw = hf_mask_words(a.V);
     unsigned long long* mrow = a.vmask + (size_t)i * Vw;
+    const float qnan = __int_as_float(0x7fc00000);
     float topc[HF_MAX_TOPK];
     int topv[HF_MAX_TOPK];
     int ntop = 0, nset = 0;
@@ -75,9 +79,11 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
     constexpr int G = 4;
     for (int v0 = 0; v0 < a.V; v0 += G) {
         long long off[G];
+        float ra_[G], rb_[G];
 #pragma unroll
         for (int q = 0; q < G; ++q) {
             off[q] = -1;
+            ra_[q] = rb_[q] = qnan;
             const int v = v0 + q;
             if (v >= a.V) continue;
             const float* cam = a.cams + 16 * v;
@@ -86,10 +92,13 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
             const ff X1 = ff_dot3_plus(__ldg(cam + 7), __ldg(cam + 8), __ldg(cam + 9), p0, p1, p2, __ldg(cam + 14));
             const ff X2 = ff_dot3_plus(__ldg(cam + 10), __ldg(cam + 11), __ldg(cam + 12), p0, p1, p2, __ldg(cam + 15));
             if (!(X2.hi > 1e-6f)) continue;
-            const float fu = ff_floor(ff_affine(fx, ff_div(X0, X2), cx));
-            const float fv = ff_floor(ff_affine(fy, ff_div(X1, X2), cy));
+            const ff ra = ff_div(X0, X2), rb = ff_div(X1, X2);
+            const float fu = ff_floor(ff_affine(fx, ra, cx));
+            const float fv = ff_floor(ff_affine(fy, rb, cy));
             if (!(fu >= 0.0f && fu < (float)a.W && fv >= 0.0f && fv < (float)a.H)) continue;
             off[q] = (long long)((size_t)v * npx + (size_t)fv * a.W + (size_t)fu);
+            ra_[q] = ra.hi;
+            rb_[q] = rb.hi;
         }
         float th[G], C[G];
 #pragma unroll
@@ -105,34 +114,35 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
                 C[q] = load_conf(a.conf, a.conf_f16, (size_t)off[q]);
             }
         }
-        float sv[2 * G];
 #pragma unroll
         for (int q = 0; q < G; ++q) {
-            sv[2 * q] = sv[2 * q + 1] = 0.0f;
-            if (off[q] < 0) continue;
-            float sn, cs;
-            sincosf(th[q], &sn, &cs);
-            sv[2 * q] = C[q] * cs;
-            sv[2 * q + 1] = C[q] * sn;
             const int v = v0 + q;
-            word |= 1ull << (v & 63);
-            if (TOPK) {
-                // keep the top_k (conf desc, view asc); later views need a strictly larger conf
-                const float c = C[q];
-                if (ntop < a.top_k || c > topc[ntop - 1]) {
-                    int pos = ntop < a.top_k ? ntop++ : ntop - 1;
-                    while (pos > 0 && c > topc[pos - 1]) {
-                        topc[pos] = topc[pos - 1];
-                        topv[pos] = topv[pos - 1];
-                        --pos;
+            if (v >= a.V) break;
+            float2 sv = make_float2(0.0f, 0.0f), r = make_float2(qnan, qnan);
+            if (off[q] >= 0) {
+                float sn, cs;
+                sincosf(th[q], &sn, &cs);
+                sv = make_float2(C[q] * cs, C[q] * sn);
+                r = make_float2(ra_[q], rb_[q]);
+                word |= 1ull << (v & 63);
+                if (TOPK) {
+                    // keep the top_k (conf desc, view asc); later views need a strictly larger conf
+                    const float c = C[q];
+                    if (ntop < a.top_k || c > topc[ntop - 1]) {
+                        int pos = ntop < a.top_k ? ntop++ : ntop - 1;
+                        while (pos > 0 && c > topc[pos - 1]) {
+                            topc[pos] = topc[pos - 1];
+                            topv[pos] = topv[pos - 1];
+                            --pos;
+                        }
+                        topc[pos] = c;
+                        topv[pos] = v;
                     }
-                    topc[pos] = c;
-                    topv[pos] = v;
                 }
             }
+            a.samp[(size_t)v * a.N + i] = sv;
+            a.ab[(size_t)v * a.N + i] = r;
         }
-        row[v0 / 2] = make_float4(sv[0], sv[1], sv[2], sv[3]);
-        row[v0 / 2 + 1] = make_float4(sv[4], sv[5], sv[6], sv[7]);
         if (((v0 + G) & 63) == 0 || v0 + G >= a.V) {   // a mask word is complete
             if (!TOPK) mrow[v0 >> 6] = word;
             nset += __popcll(word);
@@ -145,6 +155,11 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
             for (int q = 0; q < ntop; ++q)
                 if ((topv[q] >> 6) == w) m |= 1ull << (topv[q] & 63);
             mrow[w] = m;
+        }
+        for (int v = 0; v < a.V; ++v) {
+            bool keep = false;
+            for (int q = 0; q < ntop; ++q) keep |= (topv[q] == v);
+            if (!keep) a.ab[(size_t)v * a.N + i] = make_float2(qnan, qnan);
         }
         nset = ntop;
     }
@@ -210,6 +225,26 @@ __device__ __forceinline__ void prep_body(const PrepArgs& a) {
         const double fx = a.cams[16 * v], fy = a.cams[16 * v + 1];
         a.vthr[v] = (float)(1e-20 * (fx * fx + fy * fy));
     }
+    if (a.qtab) {
+        __syncthreads();   // the hypotheses are written
+        // hypothesis pairs (m, m+1), q = R_v h in double, folded with fx / fy (past Hpad: h_0)
+        for (int e = threadIdx.x; e < a.V * (a.Hq / 2); e += blockDim.x) {
+            const int v = e / (a.Hq / 2), m = 2 * (e % (a.Hq / 2));
+            const float* cam = a.cams + 16 * v;
+            double q[2][3];
+            for (int h = 0; h < 2; ++h) {
+                const int src = m + h < a.Hpad ? m + h : 0;
+                for (int r = 0; r < 3; ++r)
+                    q[h][r] = (double)cam[4 + 3 * r] * a.hyps[3 * src] + (double)cam[5 + 3 * r] * a.hyps[3 * src + 1] +
+                              (double)cam[6 + 3 * r] * a.hyps[3 * src + 2];
+            }
+            const double fx = cam[0], fy = cam[1];
+            a.qtab[(size_t)v * a.Hq + m] =
+                make_float4((float)(fx * q[0][0]), (float)(fx * q[1][0]), (float)(fx * q[0][2]), (float)(fx * q[1][2]));
+            a.qtab[(size_t)v * a.Hq + m + 1] =
+                make_float4((float)(fy * q[0][1]), (float)(fy * q[1][1]), (float)(fy * q[0][2]), (float)(fy * q[1][2]));
+        }
+    }
     for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
         const double al = 0.5 * sqrt(2.0 * kPi / a.H) / (double)(1u << t);
         a.rot[t] = make_float2((float)cos(al), (float)sin(al));
@@ -218,434 +253,41 @@ __device__ __forceinline__ void prep_body(const PrepArgs& a) {
 
 __global__ void k_prep(PrepArgs a) { prep_body(a); }
 
-// ------------------------------------------------------------------ K2 + K3: the cost kernels
-//
-// A point is served by a group of L lanes (L in {4, 8, 16, 32}; 32 / L points per warp).  The views
-// of the point's view set V_i, in view order, are dealt to the lanes: member n of V_i goes to lane
-// n mod L, slot (n / L) mod SM, chunk n / (L SM).  Per chunk a lane gathers, for each of its slots,
-// the projection Jacobian of its view at the point (single precision, scaled by Z, which cancels),
-// the view's degenerate threshold and the samples C (cos theta, sin theta) of the k + 1 patch
-// members at their own pixels.  With one chunk (|V_i| <= L SM, the usual case) these stay in
-// registers while every direction is evaluated: the H hypotheses, then the T rounds of six
-// rotations.  A direction's patch terms are summed over the lane's slots and then over the group
-// by a butterfly of shuffles, which leaves the bitwise-same sum in every lane of the group; every
-// lane therefore takes the same decisions.  Larger view sets are processed chunk by chunk (the
-// chunk gathered again for every direction).
-//
-// The patch term of a direction d in view v (Eqs. proj_r, sim, patchloss, patch_min):
-//   r = J d (Z times the image offset), L_v = max_j |<r, s_j>| / |r|, 0 when |r|^2 < threshold;
-// the members are evaluated in pairs with packed FP32 instructions (fma.rn.f32x2 / mul.rn.f32x2,
-// each lane rounded exactly like the scalar instruction) and folded into the running maximum with
-// the three-input max.f32 of two absolute values.  The cost is c = 1 - (sum_v L_v) / |V_i| (Eq.
-// final_dout with the view mean); minimising c is maximising the sum, which the kernels compare.
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pk(float a, float b) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk(f32x2 r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-// max(m, |a|, |b|)
-__device__ __forceinline__ float max3abs(float m, float a, float b) {
-    float r;
-    asm("{ .reg .f32 t, u; abs.f32 t, %1; abs.f32 u, %2; max.f32 %0, %3, t, u; }" : "=f"(r) : "f"(a), "f"(b), "f"(m));
-    return r;
-}
-
-// slots per lane for a patch width: the patch data of a slot is 2 KP + 7 registers
-template <int KP>
-struct SlotsFor {
-    static constexpr int value = KP <= 9 ? 4 : 2;
-};
-
-// One view of the point held by a lane.
-template <int KP>
-struct Slot {
-    static constexpr int NP = KP / 2 > 0 ? KP / 2 : 1;
-    float j0, j1, j2, j3, j4, j5;   // rows of Z x the projection Jacobian: fx (R_0 - a R_2), fy (R_1 - b R_2)
-    float thr;                      // degenerate threshold of the view; +inf for an empty slot
-    f32x2 sx[NP], sy[NP];           // members 2q, 2q+1 (q < KP / 2): (x_2q, x_2q+1), (y_2q, y_2q+1)
-    float ox, oy;                   // member KP - 1 when KP is odd
-};
-
-template <int KP>
-__device__ __forceinline__ float patch_term(const Slot<KP>& s, float d0, float d1, float d2, float thr) {
-    const float rx = fmaf(s.j0, d0, fmaf(s.j1, d1, __fmul_rn(s.j2, d2)));
-    const float ry = fmaf(s.j3, d0, fmaf(s.j4, d1, __fmul_rn(s.j5, d2)));
-    const float r2 = fmaf(rx, rx, __fmul_rn(ry, ry));
-    float m = 0.0f;
-    if (KP & 1) m = fabsf(fmaf(rx, s.ox, __fmul_rn(ry, s.oy)));
-    if (KP >= 2) {
-        const f32x2 RX = pk(rx, rx), RY = pk(ry, ry);
-#pragma unroll
-        for (int q = 0; q < KP / 2; ++q) {
-            float u0, u1;
-            upk(fma2(RX, s.sx[q], mul2(RY, s.sy[q])), u0, u1);
-            m = max3abs(m, u0, u1);
-        }
-    }
-    return r2 >= thr ? __fmul_rn(m, rsqrtf(r2)) : 0.0f;
-}
-
-// the n-th (from 0) set bit of a mask word
-__device__ __forceinline__ int nth_bit(unsigned long long x, int n) {
-    const unsigned lo = (unsigned)x, hi = (unsigned)(x >> 32);
-    const int cl = __popc(lo);
-    return n < cl ? (int)__fns(lo, 0, n + 1) : 32 + (int)__fns(hi, 0, n - cl + 1);
-}
-
-// the view of member n of a point's view set, or -1
-__device__ __forceinline__ int nth_view(const CostArgs& a, int i, unsigned long long w0, int n) {
-    if (a.Vw == 1) return n < __popcll(w0) ? nth_bit(w0, n) : -1;
-    const unsigned long long* m = a.vmask + (size_t)i * a.Vw;
-    for (int w = 0; w < a.Vw; ++w) {
-        const unsigned long long x = w ? m[w] : w0;
-        const int c = __popcll(x);
-        if (n < c) return 64 * w + nth_bit(x, n);
-        n -= c;
-    }
-    return -1;
-}
-
-// Per-point state of a lane's group.
-template <int KP>
-struct PointCtx {
-    int i;           // point index (0 for a group without a point)
-    bool in;         // the group has a point
-    bool finite;     // its coordinates are finite
-    int nv;          // |V_i|
-    unsigned long long w0;   // first mask word
-    float p0, p1, p2;
-    int nb[KP];      // patch members: the point, its neighbours, -1 past k
-};
-
-template <int KP>
-__device__ __forceinline__ void point_ctx(const CostArgs& a, int q, int cnt, PointCtx<KP>& pc) {
-    pc.in = q < cnt;
-    pc.i = pc.in ? (a.list ? a.list[q] : q) : 0;
-    const int i = pc.i;
-    pc.p0 = a.pts[3 * i];
-    pc.p1 = a.pts[3 * i + 1];
-    pc.p2 = a.pts[3 * i + 2];
-    pc.finite = pc.in && isfinite(pc.p0) && isfinite(pc.p1) && isfinite(pc.p2);
-    pc.w0 = pc.finite ? a.vmask[(size_t)i * a.Vw] : 0ull;
-    int nv = __popcll(pc.w0);
-    if (pc.finite)
-        for (int w = 1; w < a.Vw; ++w) nv += __popcll(a.vmask[(size_t)i * a.Vw + w]);
-    pc.nv = nv;
-    pc.nb[0] = pc.finite ? i : -1;
-#pragma unroll
-    for (int j = 1; j < KP; ++j) pc.nb[j] = (pc.finite && (j - 1) < a.k) ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
-}
-
-// Gather chunk `chunk` of the point's view set into the lane's slots (slots >= ns stay empty).
-template <int KP, int SM>
-__device__ __forceinline__ void gather(const CostArgs& a, const PointCtx<KP>& pc, int lg, int chunk, int ns,
-                                       Slot<KP> (&S)[SM]) {
-#pragma unroll
-    for (int s = 0; s < SM; ++s) {
-        Slot<KP>& q = S[s];
-        const int n = (chunk * SM + s) * a.L + lg;
-        const int v = (s < ns && n < pc.nv) ? nth_view(a, pc.i, pc.w0, n) : -1;
-        float2 sm[KP];
-        if (v < 0) {
-            q.j0 = q.j1 = q.j2 = q.j3 = q.j4 = q.j5 = 0.0f;
-            q.thr = INFINITY;
-#pragma unroll
-            for (int j = 0; j < KP; ++j) sm[j] = make_float2(0.0f, 0.0f);
-        } else {
-            const float* cam = a.cams + 16 * v;
-            const float fx = __ldg(cam), fy = __ldg(cam + 1);
-            const float r00 = __ldg(cam + 4), r01 = __ldg(cam + 5), r02 = __ldg(cam + 6);
-            const float r10 = __ldg(cam + 7), r11 = __ldg(cam + 8), r12 = __ldg(cam + 9);
-            const float r20 = __ldg(cam + 10), r21 = __ldg(cam + 11), r22 = __ldg(cam + 12);
-            const float X = fmaf(r00, pc.p0, fmaf(r01, pc.p1, fmaf(r02, pc.p2, __ldg(cam + 13))));
-            const float Y = fmaf(r10, pc.p0, fmaf(r11, pc.p1, fmaf(r12, pc.p2, __ldg(cam + 14))));
-            const float Z = fmaf(r20, pc.p0, fmaf(r21, pc.p1, fmaf(r22, pc.p2, __ldg(cam + 15))));
-            const float iz = 1.0f / Z;
-            const float ra = __fmul_rn(X, iz), rb = __fmul_rn(Y, iz);
-            q.j0 = __fmul_rn(fx, fmaf(-ra, r20, r00));
-            q.j1 = __fmul_rn(fx, fmaf(-ra, r21, r01));
-            q.j2 = __fmul_rn(fx, fmaf(-ra, r22, r02));
-            q.j3 = __fmul_rn(fy, fmaf(-rb, r20, r10));
-            q.j4 = __fmul_rn(fy, fmaf(-rb, r21, r11));
-            q.j5 = __fmul_rn(fy, fmaf(-rb, r22, r12));
-            q.thr = __ldg(a.vthr + v);
-#pragma unroll
-            for (int j = 0; j < KP; ++j)
-                sm[j] = pc.nb[j] >= 0 ? __ldg(a.samp + (size_t)pc.nb[j] * a.Vs + v) : make_float2(0.0f, 0.0f);
-        }
-#pragma unroll
-        for (int p = 0; p < KP / 2; ++p) {
-            q.sx[p] = pk(sm[2 * p].x, sm[2 * p + 1].x);
-            q.sy[p] = pk(sm[2 * p].y, sm[2 * p + 1].y);
-        }
-        if (KP & 1) {
-            q.ox = sm[KP - 1].x;
-            q.oy = sm[KP - 1].y;
-        }
-    }
-}
-
-__device__ __forceinline__ float group_sum(float x, int L) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1)
-        if (o < L) x = __fadd_rn(x, __shfl_xor_sync(0xffffffffu, x, o));
-    return x;
-}
-
-// Group sums of the patch terms of ND directions (all lanes of the warp take part).  With one chunk
-// the slots hold the data (ns of them in use); otherwise each chunk is gathered again here.
-template <int KP, int SM, int ND>
-__device__ __forceinline__ void dir_sums(const CostArgs& a, const PointCtx<KP>& pc, int lg, int nch, int ns,
-                                         Slot<KP> (&S)[SM], const float (&d)[ND][3], float tscale, float (&out)[ND]) {
-#pragma unroll
-    for (int q = 0; q < ND; ++q) out[q] = 0.0f;
-    for (int c = 0; c < nch; ++c) {
-        if (nch > 1) gather<KP, SM>(a, pc, lg, c, SM, S);
-#pragma unroll
-        for (int s = 0; s < SM; ++s) {
-            if (s < ns || nch > 1) {
-#pragma unroll
-                for (int q = 0; q < ND; ++q)
-                    out[q] = __fadd_rn(out[q], patch_term<KP>(S[s], d[q][0], d[q][1], d[q][2], __fmul_rn(S[s].thr, tscale)));
-            }
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < ND; ++q) out[q] = group_sum(out[q], a.L);
-}
-
-// Group geometry of the calling lane for tile `tile`: returns false when the whole warp is past
-// the end of the work list (a warp-uniform exit).
-struct Lanes {
-    int lane, lg, g, q;   // lane, lane in group, group in warp, work-list position of the group
-};
-__device__ __forceinline__ bool lanes_of(int L, int tile, int cnt, Lanes& ln) {
-    ln.lane = threadIdx.x & 31;
-    ln.lg = ln.lane & (L - 1);
-    ln.g = ln.lane / L;
-    const int ppw = 32 / L;
-    const int w = tile * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    ln.q = w * ppw + ln.g;
-    return w * ppw < cnt;
-}
-
-// chunks and slots in use, uniform over the warp
-template <int SM>
-__device__ __forceinline__ void chunking(int nv, int L, int& nch, int& ns) {
-    const int per = L * SM;
-    nch = (int)__reduce_max_sync(0xffffffffu, (unsigned)((nv + per - 1) / per));
-    ns = (int)__reduce_max_sync(0xffffffffu, (unsigned)min(SM, (nv + L - 1) / L));
-    if (nch < 1) nch = 1;
-}
-
-__device__ __forceinline__ void write_bad(const CostArgs& a, int i) {
-    const int o = i - a.out_first;   // output row
-    a.dir_out[3 * o] = a.dir_out[3 * o + 1] = a.dir_out[3 * o + 2] = 0.0f;
-    if (a.cost_out) a.cost_out[o] = __int_as_float(0x7fc00000);
-    if (a.idx_out) a.idx_out[o] = -1;
-    if (a.status_out) a.status_out[o] = HF_STATUS_BAD_INPUT;
-}
-
-// Six rotations of d by +-alpha about world x, y, z (in that order) and their sums; move to the first
-// strictly larger sum (the first strictly lower cost).
-template <int KP, int SM>
-__device__ __forceinline__ void refine_rounds(const CostArgs& a, const PointCtx<KP>& pc, int lg, int nch, int ns,
-                                              Slot<KP> (&S)[SM], float& d0, float& d1, float& d2, float& best) {
-    for (int t = 0; t < a.T; ++t) {
-        const float2 cr = a.rot[t];
-        const float c = cr.x, sn = cr.y;
-        // every product rounded once and added with an explicit fused multiply-add, so that all
-        // instances of this code round alike
-        const float cd[6][3] = {{d0, fmaf(c, d1, __fmul_rn(-sn, d2)), fmaf(sn, d1, __fmul_rn(c, d2))},
-                                {d0, fmaf(c, d1, __fmul_rn(sn, d2)), fmaf(-sn, d1, __fmul_rn(c, d2))},
-                                {fmaf(c, d0, __fmul_rn(sn, d2)), d1, fmaf(-sn, d0, __fmul_rn(c, d2))},
-                                {fmaf(c, d0, __fmul_rn(-sn, d2)), d1, fmaf(sn, d0, __fmul_rn(c, d2))},
-                                {fmaf(c, d0, __fmul_rn(-sn, d1)), fmaf(sn, d0, __fmul_rn(c, d1)), d2},
-                                {fmaf(c, d0, __fmul_rn(sn, d1)), fmaf(-sn, d0, __fmul_rn(c, d1)), d2}};
-        float acc[6];
-        dir_sums<KP, SM, 6>(a, pc, lg, nch, ns, S, cd, 1.0f, acc);
-        int choice = -1;
-#pragma unroll
-        for (int q = 0; q < 6; ++q)
-            if (acc[q] > best) {
-                best = acc[q];
-                choice = q;
-            }
-#pragma unroll
-        for (int q = 0; q < 6; ++q)
-            if (q == choice) {
-                d0 = cd[q][0];
-                d1 = cd[q][1];
-                d2 = cd[q][2];
-            }
-    }
-}
-
-// Normalised direction with the canonical sign, the cost, index and status of a point.
-__device__ __forceinline__ void write_out(const CostArgs& a, int i, int nv, float d0, float d1, float d2, float best,
-                                          int idx) {
-    const float n = sqrtf(fmaf(d0, d0, fmaf(d1, d1, __fmul_rn(d2, d2))));
-    d0 /= n;
-    d1 /= n;
-    d2 /= n;
-    const float sgn = fabsf(d2) > 1e-12f ? copysignf(1.0f, d2) : fabsf(d1) > 1e-12f ? copysignf(1.0f, d1) : copysignf(1.0f, d0);
-    const int o = i - a.out_first;   // output row
-    a.dir_out[3 * o] = sgn * d0;
-    a.dir_out[3 * o + 1] = sgn * d1;
-    a.dir_out[3 * o + 2] = sgn * d2;
-    if (a.cost_out) a.cost_out[o] = nv ? 1.0f - best / (float)nv : 1.0f;
-    if (a.idx_out) a.idx_out[o] = idx;
-    if (a.status_out) a.status_out[o] = a.fell_back ? HF_STATUS_FELL_BACK : (nv ? HF_STATUS_OK : HF_STATUS_NO_VIEWS);
-}
-
-// The hypotheses of the scene into shared memory (a CTA-wide barrier follows).
-__device__ __forceinline__ void stage_hyps(const CostArgs& a, float* sh) {
-    for (int e = threadIdx.x; e < 3 * a.Hpad; e += blockDim.x) sh[e] = a.hyps[e];
-    __syncthreads();
-}
-
-// K2 + K3 for the points of one tile.
-template <int KP>
-__device__ __forceinline__ void fuse_tile(const CostArgs& a, int tile, float* sh) {
-    constexpr int SM = SlotsFor<KP>::value;
-    stage_hyps(a, sh);
-    const int cnt = a.list ? *a.list_count : a.N;
-    Lanes ln;
-    if (!lanes_of(a.L, tile, cnt, ln)) return;
-    PointCtx<KP> pc;
-    point_ctx<KP>(a, ln.q, cnt, pc);
-    int nch, ns;
-    chunking<SM>(pc.nv, a.L, nch, ns);
-    Slot<KP> S[SM];
-    if (nch == 1) gather<KP, SM>(a, pc, ln.lg, 0, ns, S);
-    // argmin over the hypotheses, two at a time (largest sum, lowest index on ties)
-    float best = -1.0f;
-    int bm = 0;
-    for (int m = 0; m < a.Hpad; m += 2) {
-        const float hd[2][3] = {{sh[3 * m], sh[3 * m + 1], sh[3 * m + 2]}, {sh[3 * m + 3], sh[3 * m + 4], sh[3 * m + 5]}};
-        float l[2];
-        dir_sums<KP, SM, 2>(a, pc, ln.lg, nch, ns, S, hd, 1.0f, l);
-        if (l[0] > best) {
-            best = l[0];
-            bm = m;
-        }
-        if (m + 1 < a.H && l[1] > best) {
-            best = l[1];
-            bm = m + 1;
-        }
-    }
-    float d0 = sh[3 * bm], d1 = sh[3 * bm + 1], d2 = sh[3 * bm + 2];
-    refine_rounds<KP, SM>(a, pc, ln.lg, nch, ns, S, d0, d1, d2, best);
-    if (ln.lg != 0 || !pc.in) return;
-    if (!pc.finite) {
-        write_bad(a, pc.i);
-        if (a.nvs) a.nvs[pc.i] = -1;
-        return;
-    }
-    write_out(a, pc.i, pc.nv, d0, d1, d2, best, bm);
-}
+// ------------------------------------------------------------------ K2 + K3 (device code in hf_cost.cuh)
+using namespace hf_cost;
 
 constexpr int kCostThreads = 128;
+// resident CTAs per SM the register budget is sized for: 16 warps per SM (12 for the widest patch)
+template <int KP>
+struct MinCtas {
+    static constexpr int value = KP <= 9 ? 4 : 3;
+};
 
 template <int KP>
-__global__ void __launch_bounds__(kCostThreads) k_fuse(CostArgs a) {
-    extern __shared__ __align__(16) float smem_f[];
-    fuse_tile<KP>(a, blockIdx.x, smem_f);
+__global__ void __launch_bounds__(kCostThreads, 4) k_argmin(CostArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    argmin_tile<KP>(a, blockIdx.x, smem_raw);
 }
 
-// The learned path after the network, for the points of one tile.
-template <int KP>
-__device__ __forceinline__ void learn_tile(const LearnArgs& la, int tile) {
-    constexpr int SM = SlotsFor<KP>::value;
-    const CostArgs& a = la.f;
-    const int cnt = a.N;
-    Lanes ln;
-    if (!lanes_of(a.L, tile, cnt, ln)) return;
-    PointCtx<KP> pc;
-    point_ctx<KP>(a, ln.q, cnt, pc);
-    int nch, ns;
-    chunking<SM>(pc.nv, a.L, nch, ns);
-    Slot<KP> S[SM];
-    if (nch == 1) gather<KP, SM>(a, pc, ln.lg, 0, ns, S);
-    float d0 = 1.0f, d1 = 0.0f, d2 = 0.0f;
-    if (pc.finite) {
-        d0 = la.start_dir[3 * pc.i];
-        d1 = la.start_dir[3 * pc.i + 1];
-        d2 = la.start_dir[3 * pc.i + 2];
-    }
-    const float dd[1][3] = {{d0, d1, d2}};
-    float l0[1];
-    dir_sums<KP, SM, 1>(a, pc, ln.lg, nch, ns, S, dd, 1.0f, l0);
-    const float c0 = pc.nv ? 1.0f - l0[0] / (float)pc.nv : 1.0f;
-    const bool lead = ln.lg == 0 && pc.in;
-    const bool fb = lead && pc.finite && pc.nv > 0 && c0 > la.tau;
-    const bool ok = lead && pc.finite && !fb;
-    if (lead && a.nvs) a.nvs[pc.i] = pc.finite ? pc.nv : -1;
-    // warp-aggregated appends to the fallback list and work counts
-    const unsigned mfb = __ballot_sync(0xffffffffu, fb);
-    if (mfb) {
-        const int leader = __ffs(mfb) - 1;
-        int base = 0;
-        if (ln.lane == leader) base = atomicAdd(la.fb_count, __popc(mfb));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (fb) la.fb_list[base + __popc(mfb & ((1u << ln.lane) - 1u))] = pc.i;
-    }
-    const unsigned wfb = __reduce_add_sync(0xffffffffu, fb ? (unsigned)pc.nv : 0u);
-    const unsigned wok = __reduce_add_sync(0xffffffffu, ok ? (unsigned)pc.nv : 0u);
-    if (ln.lane == 0) {
-        if (la.fb_work && wfb) atomicAdd(la.fb_work, (unsigned long long)wfb);
-        if (la.acc_work && wok) atomicAdd(la.acc_work, (unsigned long long)wok);
-    }
-    // short refinement from the proposal (every group takes part in the shuffles; the fallback
-    // points' results are dropped)
-    float best = l0[0];
-    refine_rounds<KP, SM>(a, pc, ln.lg, nch, ns, S, d0, d1, d2, best);
-    if (!lead) return;
-    if (!pc.finite) {
-        write_bad(a, pc.i);
-        return;
-    }
-    if (ok) write_out(a, pc.i, pc.nv, d0, d1, d2, best, -1);
+template <int KP, int L>
+__global__ void __launch_bounds__(kCostThreads, MinCtas<KP>::value) k_refine(CostArgs a) {
+    refine_tile_l<KP, L, PairsFor<KP>::value>(a, blockIdx.x);
 }
 
 template <int KP>
-__global__ void __launch_bounds__(kCostThreads) k_learn(LearnArgs la) {
-    learn_tile<KP>(la, blockIdx.x);
+__global__ void __launch_bounds__(kCostThreads) k_refine_t(CostArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    refine_stage_tile<KP, kCostThreads>(a, blockIdx.x, smem_raw);
 }
 
-// ------------------------------------------------------------------ cost of given directions
 template <int KP>
+__global__ void __launch_bounds__(kCostThreads) k_select(LearnArgs la) {
+    select_tile<KP>(la, blockIdx.x);
+}
+
+template <int KP, int L>
 __global__ void __launch_bounds__(kCostThreads) k_eval(EvalArgs e) {
-    constexpr int SM = SlotsFor<KP>::value;
-    const CostArgs& a = e.f;
-    Lanes ln;
-    if (!lanes_of(a.L, blockIdx.x, a.N, ln)) return;
-    PointCtx<KP> pc;
-    point_ctx<KP>(a, ln.q, a.N, pc);
-    int nch, ns;
-    chunking<SM>(pc.nv, a.L, nch, ns);
-    Slot<KP> S[SM];
-    if (nch == 1) gather<KP, SM>(a, pc, ln.lg, 0, ns, S);
-    for (int m = 0; m < e.M; ++m) {
-        const float* d = e.dirs + ((size_t)pc.i * e.M + m) * 3;
-        const float dd[1][3] = {{d[0], d[1], d[2]}};
-        const float dn2 = fmaf(dd[0][0], dd[0][0], fmaf(dd[0][1], dd[0][1], __fmul_rn(dd[0][2], dd[0][2])));
-        float l[1];
-        dir_sums<KP, SM, 1>(a, pc, ln.lg, nch, ns, S, dd, dn2, l);
-        if (ln.lg == 0 && pc.in) e.cost[(size_t)pc.i * e.M + m] = pc.nv ? 1.0f - l[0] / (float)pc.nv : 1.0f;
-    }
+    eval_tile_l<KP, L, PairsFor<KP>::value>(e, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ learned proposal path
@@ -746,74 +388,8 @@ __global__ void k_check_nbr(const int32_t* __restrict__ nbr, long long n, int N,
     }
 }
 
-// ------------------------------------------------------------------ batched scenes
-// One persistent grid per stage walks the (scene, tile) items of every scene of a batch, scenes in
-// the order of the argument array: a CTA takes the next item from a global counter, copies that
-// scene's arguments to shared memory when the scene changes, and runs the single-scene tile body,
-// so a batched result is bit-identical to the scene run alone.  With c.done set, the CTA that
-// finishes a scene's last tile stamps the global timer (per-scene completion time).
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// tiles(args) gives a scene's tile count (evaluated on the device: list lengths are device counts)
-template <typename Args, typename Tiles, typename Body>
-__device__ __forceinline__ void batch_tiles(const Args* __restrict__ args, const BatchCtl& c, Tiles tiles, Body body) {
-    __shared__ Args sa;
-    __shared__ int pref[HF_MAX_BATCH + 1];
-    __shared__ int s_item, s_pos, s_cur;
-    if (threadIdx.x == 0) {
-        pref[0] = 0;
-        for (int p = 0; p < c.ns; ++p) pref[p + 1] = pref[p] + tiles(args[p]);
-        s_cur = -1;
-    }
-    for (;;) {
-        __syncthreads();   // the previous item is done with shared memory
-        if (threadIdx.x == 0) {
-            const int t = (int)atomicAdd(c.next, 1u);
-            int p = 0;
-            while (p < c.ns - 1 && t >= pref[p + 1]) ++p;
-            s_item = t;
-            s_pos = p;
-            if (t < pref[c.ns] && p != s_cur) {
-                sa = args[p];
-                s_cur = p;
-            }
-        }
-        __syncthreads();
-        const int t = s_item, p = s_pos;
-        if (t >= pref[c.ns]) break;
-        body(sa, t - pref[p]);
-        if (c.done) {
-            __syncthreads();   // every thread's outputs of the tile are written
-            if (threadIdx.x == 0) {
-                __threadfence();
-                if ((int)atomicAdd(c.done + p, 1u) + 1 == pref[p + 1] - pref[p]) c.stamp[p] = gtimer();
-            }
-        }
-    }
-}
-
-// points per CTA of the cost kernels: 32 / L points per warp
-__device__ __forceinline__ int cost_tiles(const CostArgs& a, int cnt) {
-    const int ppc = (int)(blockDim.x >> 5) * (32 / a.L);
-    return (cnt + ppc - 1) / ppc;
-}
-
-template <int KP, int NT>
-__global__ void __launch_bounds__(NT) k_fuse_batch(const CostArgs* __restrict__ fa, BatchCtl c) {
-    extern __shared__ __align__(16) float smem_f[];
-    batch_tiles(fa, c, [](const CostArgs& a) { return cost_tiles(a, a.list ? *a.list_count : a.N); },
-                [&](const CostArgs& a, int t) { fuse_tile<KP>(a, t, smem_f); });
-}
-
-template <int KP, int NT>
-__global__ void __launch_bounds__(NT) k_learn_batch(const LearnArgs* __restrict__ la, BatchCtl c) {
-    batch_tiles(la, c, [](const LearnArgs& a) { return cost_tiles(a.f, a.f.N); },
-                [](const LearnArgs& a, int t) { learn_tile<KP>(a, t); });
-}
+// ------------------------------------------------------------------ batched scenes (work loop in hf_batchtiles.cuh)
+using namespace hf_bt;
 
 __global__ void __launch_bounds__(kProjectThreads) k_project_batch(const ProjectArgs* __restrict__ pa, BatchCtl c) {
     batch_tiles(pa, c, [](const ProjectArgs& a) { return (a.N + kProjectThreads - 1) / kProjectThreads; },
@@ -843,29 +419,6 @@ __global__ void k_prep_batch(const PrepArgs* __restrict__ pr, BatchReset r) {
     }
 }
 
-// persistent grid: resident CTAs per SM x SMs
-template <typename K>
-int persistent_grid(K kernel, int threads, size_t smem) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) per = 1;
-    return per * sms;
-}
-
-template <typename K>
-cudaError_t set_smem(K kernel, size_t smem, cudaStream_t s) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(s, &cs);
-    if (cs != cudaStreamCaptureStatusNone) return cudaSuccess;   // set by the eager launch before capture
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
 // patch width (k + 1) rounded up to an instantiated size
 int kp_for(int k) {
     const int need = k + 1;
@@ -877,86 +430,85 @@ int kp_for(int k) {
     return 17;
 }
 
+// views a lane holds at once for a patch width: two per view pair
 int slots_for_kp(int kp) {
     switch (kp) {
-        case 1: return SlotsFor<1>::value;
-        case 4: return SlotsFor<4>::value;
-        case 6: return SlotsFor<6>::value;
-        case 9: return SlotsFor<9>::value;
-        case 12: return SlotsFor<12>::value;
-        default: return SlotsFor<17>::value;
+        case 1: return 2 * PairsFor<1>::value;
+        case 4: return 2 * PairsFor<4>::value;
+        case 6: return 2 * PairsFor<6>::value;
+        case 9: return 2 * PairsFor<9>::value;
+        case 12: return 2 * PairsFor<12>::value;
+        default: return 2 * PairsFor<17>::value;
     }
 }
 
-template <int KP, int NT>
-cudaError_t launch_fuse_batch(const CostArgs* fa, const BatchCtl& c, int hpad_max, cudaStream_t s) {
-    const size_t sm = (size_t)3 * hpad_max * sizeof(float);
-    cudaError_t e = set_smem(k_fuse_batch<KP, NT>, sm, s);
+template <int KP>
+cudaError_t launch_argmin_kp(const CostArgs& a, cudaStream_t s) {
+    const int cnt_max = a.N;   // with a list, its length is at most N (blocks past the list exit at once)
+    const size_t sm = argmin_smem_bytes();
+    cudaError_t e = set_smem(k_argmin<KP>, sm, s);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_grid(k_fuse_batch<KP, NT>, NT, sm);
-    k_fuse_batch<KP, NT><<<grid, NT, sm, s>>>(fa, c);
+    k_argmin<KP><<<(cnt_max + kCostThreads - 1) / kCostThreads, kCostThreads, sm, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int KP, int NT>
-cudaError_t launch_learn_batch(const LearnArgs* la, const BatchCtl& c, cudaStream_t s) {
-    static int grid = 0;
-    if (!grid) grid = persistent_grid(k_learn_batch<KP, NT>, NT, 0);
-    k_learn_batch<KP, NT><<<grid, NT, 0, s>>>(la, c);
+template <int KP, int L>
+cudaError_t launch_refine_l(const CostArgs& a, cudaStream_t s) {
+    constexpr int ppc = kCostThreads / L;
+    k_refine<KP, L><<<(a.N + ppc - 1) / ppc, kCostThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int KP, int L>
+cudaError_t launch_eval_l(const EvalArgs& a, cudaStream_t s) {
+    constexpr int ppc = kCostThreads / L;
+    k_eval<KP, L><<<(a.f.N + ppc - 1) / ppc, kCostThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int KP>
-cudaError_t launch_fuse_batch_nt(const CostArgs* fa, const BatchCtl& c, int nt, int hpad_max, cudaStream_t s) {
-    switch (nt) {
-        case 64: return launch_fuse_batch<KP, 64>(fa, c, hpad_max, s);
-        case 256: return launch_fuse_batch<KP, 256>(fa, c, hpad_max, s);
-        default: return launch_fuse_batch<KP, 128>(fa, c, hpad_max, s);
+cudaError_t launch_refine_kp(const CostArgs& a, cudaStream_t s) {
+    if (a.L == 0) {   // a point per thread
+        const size_t sm = refine_smem_bytes<KP, kCostThreads>();
+        cudaError_t e = set_smem(k_refine_t<KP>, sm, s);
+        if (e != cudaSuccess) return e;
+        k_refine_t<KP><<<(a.N + kCostThreads - 1) / kCostThreads, kCostThreads, sm, s>>>(a);
+        return cudaGetLastError();
     }
-}
-
-template <int KP>
-cudaError_t launch_learn_batch_nt(const LearnArgs* la, const BatchCtl& c, int nt, cudaStream_t s) {
-    switch (nt) {
-        case 64: return launch_learn_batch<KP, 64>(la, c, s);
-        case 256: return launch_learn_batch<KP, 256>(la, c, s);
-        default: return launch_learn_batch<KP, 128>(la, c, s);
+    switch (a.L) {
+        case 4: return launch_refine_l<KP, 4>(a, s);
+        case 8: return launch_refine_l<KP, 8>(a, s);
+        case 16: return launch_refine_l<KP, 16>(a, s);
+        default: return launch_refine_l<KP, 32>(a, s);
     }
-}
-
-template <int KP>
-cudaError_t launch_fuse_kp(const CostArgs& a, cudaStream_t s) {
-    const int cnt_max = a.N;   // with a list, its length is at most N (tiles past the list exit at once)
-    const int ppc = kCostThreads / a.L;
-    const dim3 grid((cnt_max + ppc - 1) / ppc), block(kCostThreads);
-    const size_t sm = (size_t)3 * a.Hpad * sizeof(float);
-    cudaError_t e = set_smem(k_fuse<KP>, sm, s);
-    if (e != cudaSuccess) return e;
-    k_fuse<KP><<<grid, block, sm, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <int KP>
-cudaError_t launch_learn_kp(const LearnArgs& a, cudaStream_t s) {
-    const int ppc = kCostThreads / a.f.L;
-    k_learn<KP><<<(a.f.N + ppc - 1) / ppc, kCostThreads, 0, s>>>(a);
-    return cudaGetLastError();
 }
 
 template <int KP>
 cudaError_t launch_eval_kp(const EvalArgs& a, cudaStream_t s) {
-    const int ppc = kCostThreads / a.f.L;
-    k_eval<KP><<<(a.f.N + ppc - 1) / ppc, kCostThreads, 0, s>>>(a);
+    switch (a.f.L) {
+        case 4: return launch_eval_l<KP, 4>(a, s);
+        case 8: return launch_eval_l<KP, 8>(a, s);
+        case 16: return launch_eval_l<KP, 16>(a, s);
+        default: return launch_eval_l<KP, 32>(a, s);
+    }
+}
+
+template <int KP>
+cudaError_t launch_select_kp(const LearnArgs& a, cudaStream_t s) {
+    k_select<KP><<<(a.f.N + kCostThreads - 1) / kCostThreads, kCostThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+// The refinement's layout for view sets of up to veff views: lanes over views when the view set
+// fills at least 7/8 of a group's view slots (the patch then stays in registers for all rounds at
+// little idle-lane cost), else a point per thread (no idle lanes, the patch copied per round).
 int hf_cost_lanes(int veff, int k) {
     const int sm = slots_for_kp(kp_for(k));
     int L = 4;
     while (L < 32 && L * sm < veff) L *= 2;
-    return L;
+    return 8 * veff >= 7 * L * sm ? L : 0;
 }
 
 cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s) {
@@ -984,25 +536,41 @@ cudaError_t hf_launch_prep(const PrepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t hf_launch_fuse(const CostArgs& a, cudaStream_t s) {
+cudaError_t hf_launch_argmin(const CostArgs& a, cudaStream_t s) {
     switch (kp_for(a.k)) {
-        case 1: return launch_fuse_kp<1>(a, s);
-        case 4: return launch_fuse_kp<4>(a, s);
-        case 6: return launch_fuse_kp<6>(a, s);
-        case 9: return launch_fuse_kp<9>(a, s);
-        case 12: return launch_fuse_kp<12>(a, s);
-        default: return launch_fuse_kp<17>(a, s);
+        case 1: return launch_argmin_kp<1>(a, s);
+        case 4: return launch_argmin_kp<4>(a, s);
+        case 6: return launch_argmin_kp<6>(a, s);
+        case 9: return launch_argmin_kp<9>(a, s);
+        case 12: return launch_argmin_kp<12>(a, s);
+        default: return launch_argmin_kp<17>(a, s);
     }
 }
 
-cudaError_t hf_launch_learn(const LearnArgs& a, cudaStream_t s) {
+cudaError_t hf_launch_refine(const CostArgs& a, cudaStream_t s) {
+    switch (kp_for(a.k)) {
+        case 1: return launch_refine_kp<1>(a, s);
+        case 4: return launch_refine_kp<4>(a, s);
+        case 6: return launch_refine_kp<6>(a, s);
+        case 9: return launch_refine_kp<9>(a, s);
+        case 12: return launch_refine_kp<12>(a, s);
+        default: return launch_refine_kp<17>(a, s);
+    }
+}
+
+cudaError_t hf_launch_fuse(const CostArgs& a, cudaStream_t s) {
+    cudaError_t e = hf_launch_argmin(a, s);
+    return e != cudaSuccess ? e : hf_launch_refine(a, s);
+}
+
+cudaError_t hf_launch_select(const LearnArgs& a, cudaStream_t s) {
     switch (kp_for(a.f.k)) {
-        case 1: return launch_learn_kp<1>(a, s);
-        case 4: return launch_learn_kp<4>(a, s);
-        case 6: return launch_learn_kp<6>(a, s);
-        case 9: return launch_learn_kp<9>(a, s);
-        case 12: return launch_learn_kp<12>(a, s);
-        default: return launch_learn_kp<17>(a, s);
+        case 1: return launch_select_kp<1>(a, s);
+        case 4: return launch_select_kp<4>(a, s);
+        case 6: return launch_select_kp<6>(a, s);
+        case 9: return launch_select_kp<9>(a, s);
+        case 12: return launch_select_kp<12>(a, s);
+        default: return launch_select_kp<17>(a, s);
     }
 }
 
@@ -1060,20 +628,4 @@ cudaError_t hf_launch_features_batch(const FeatArgs* fe, const BatchCtl& c, cuda
     if (!grid) grid = persistent_grid(k_features_batch, kFeatThreads, 0);
     k_features_batch<<<grid, kFeatThreads, 0, s>>>(fe, c);
     return cudaGetLastError();
-}
-
-cudaError_t hf_launch_fuse_batch(const CostArgs* fa, const BatchCtl& c, int kp, int nt, int hpad_max, cudaStream_t s) {
-    switch (kp) {
-        case 4: return launch_fuse_batch_nt<4>(fa, c, nt, hpad_max, s);
-        case 9: return launch_fuse_batch_nt<9>(fa, c, nt, hpad_max, s);
-        default: return launch_fuse_batch_nt<17>(fa, c, nt, hpad_max, s);
-    }
-}
-
-cudaError_t hf_launch_learn_batch(const LearnArgs* la, const BatchCtl& c, int kp, int nt, cudaStream_t s) {
-    switch (kp) {
-        case 4: return launch_learn_batch_nt<4>(la, c, nt, s);
-        case 9: return launch_learn_batch_nt<9>(la, c, nt, s);
-        default: return launch_learn_batch_nt<17>(la, c, nt, s);
-    }
 }

@@ -412,7 +412,7 @@ int learned_scratch(hf_ctx* c, long long N) {
     int rc;
     if ((rc = hf_ensure(c, c->feat, (size_t)N * 64 * 2))) return rc;
     if ((rc = hf_ensure(c, c->prop, (size_t)N * 3 * 4))) return rc;
-    if ((rc = hf_ensure(c, c->lmisc, 256 + 64 * 8 + (size_t)N * 4))) return rc;
+    if ((rc = hf_ensure(c, c->lmisc, 256 + 64 * 8 + (size_t)N * 8))) return rc;
     return HF_OK;
 }
 }  // namespace
@@ -455,7 +455,10 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     if ((rc = hf_ensure(c, c->vthr, (size_t)V * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->hyps, (size_t)Hpad * 3 * sizeof(float)))) return rc;
     if ((rc = hf_ensure(c, c->rot, (size_t)(T > 0 ? T : 1) * sizeof(float2)))) return rc;
-    if ((rc = hf_ensure(c, c->samp, (size_t)N * hf_samp_stride(V) * sizeof(float2)))) return rc;
+    if ((rc = hf_ensure(c, c->qtab, (size_t)V * hf_hq(H) * sizeof(float4)))) return rc;
+    if ((rc = hf_ensure(c, c->best, (size_t)N * sizeof(int32_t)))) return rc;
+    if ((rc = hf_ensure(c, c->samp, (size_t)N * V * sizeof(float2)))) return rc;
+    if ((rc = hf_ensure(c, c->ab, (size_t)N * V * sizeof(float2)))) return rc;
     if ((rc = hf_ensure(c, c->vmask, (size_t)N * hf_mask_words(V) * sizeof(unsigned long long)))) return rc;
     if ((rc = hf_ensure(c, c->work, sizeof(unsigned long long)))) return rc;
     if ((rc = hf_ensure(c, c->outs, (size_t)N * 21))) return rc;
@@ -463,10 +466,12 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     char* lm = (char*)c->lmisc.p;
     float* box = (float*)lm;
     int* count = (int*)(lm + 64);                                        // fallback points
+    int* acc_count = (int*)(lm + 68);                                    // accepted proposals
     unsigned long long* fb_work = (unsigned long long*)(lm + 72);       // their (point, view) pairs
     unsigned long long* acc_work = (unsigned long long*)(lm + 80);      // those of the accepted proposals
     float2* rot_s = (float2*)(lm + 128);
     int32_t* list = (int32_t*)(lm + 256 + 64 * 8);
+    int32_t* acc_list = list + N;
     char* so = (char*)c->outs.p;
     float* d_dir = mem_kind == HF_HOST ? (float*)so : dir_out;
     float* d_cost = (mem_kind == HF_HOST || !cost_out) ? (float*)(so + (size_t)N * 12) : cost_out;
@@ -475,7 +480,7 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     cudaStream_t s = c->stream;
 
     PrepArgs pr{(const float*)c->cams.p, V, nullptr, H, Hpad, T, (float*)c->hyps.p, (float*)c->vthr.p,
-                (float2*)c->rot.p, (uint32_t*)c->errw.p};
+                (float2*)c->rot.p, (uint32_t*)c->errw.p, (float4*)c->qtab.p, hf_hq(H)};
     unsigned* box_keys = reinterpret_cast<unsigned*>(box + 8);
     if ((rc = run_launch(c, "k_prep", [&] {
              cudaError_t e2 = hf_launch_prep(pr, s);
@@ -487,7 +492,7 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     // the projection also folds the points into the bounding box the features are normalised by
     ProjectArgs pa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p,
                    c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, c->cfg.top_k_views, (float2*)c->samp.p,
-                   (unsigned long long*)c->vmask.p, (unsigned long long*)c->work.p, box_keys, (const float2*)c->amap.p};
+                   (float2*)c->ab.p, (unsigned long long*)c->vmask.p, (unsigned long long*)c->work.p, box_keys, (const float2*)c->amap.p};
     if ((rc = run_launch(c, "k_project", [&] { return hf_launch_project(pa, s); }))) return rc;
     // proposal: features -> network
     FeatArgs fa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p, c->conf.p,
@@ -505,20 +510,26 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     base.cost_out = d_cost;
     base.idx_out = d_idx;
     base.status_out = d_status;
-    LearnArgs la{base, (const float*)c->prop.p, tau, list, count, fb_work, acc_work};
-    la.f.rot = rot_s;
-    la.f.T = T_short;
-    if ((rc = run_launch(c, "k_learn", [&] {
-             cudaError_t e2 = cudaMemsetAsync(count, 0, 24, s);   // count, fb_work, acc_work
+    LearnArgs la{base, (const float*)c->prop.p, tau, list, count, fb_work, acc_work, acc_list, acc_count};
+    if ((rc = run_launch(c, "k_select", [&] {
+             cudaError_t e2 = cudaMemsetAsync(count, 0, 24, s);   // counts, fb_work, acc_work
              if (e2 == cudaSuccess) e2 = hf_launch_rot(rot_s, T_short, (double)alpha_short, s);
-             return e2 != cudaSuccess ? e2 : hf_launch_learn(la, s);
+             return e2 != cudaSuccess ? e2 : hf_launch_select(la, s);
          })))
         return rc;
-    CostArgs fb = base;
+    CostArgs fs = base;   // the accepted proposals: T_short rounds from the proposal
+    fs.list = acc_list;
+    fs.list_count = acc_count;
+    fs.start_dir = (const float*)c->prop.p;
+    fs.rot = rot_s;
+    fs.T = T_short;
+    if ((rc = run_launch(c, "k_refine_short", [&] { return hf_launch_refine(fs, s); }))) return rc;
+    CostArgs fb = base;   // the fallback points: the plain fusion
     fb.list = list;
     fb.list_count = count;
     fb.fell_back = 1;
-    if ((rc = run_launch(c, "k_fuse_fallback", [&] { return hf_launch_fuse(fb, s); }))) return rc;
+    if ((rc = run_launch(c, "k_argmin_fallback", [&] { return hf_launch_argmin(fb, s); }))) return rc;
+    if ((rc = run_launch(c, "k_refine_fallback", [&] { return hf_launch_refine(fb, s); }))) return rc;
     c->learned_ran = true;
     if (mem_kind == HF_HOST) {
         e = cudaMemcpyAsync(dir_out, d_dir, (size_t)N * 12, cudaMemcpyDeviceToHost, s);

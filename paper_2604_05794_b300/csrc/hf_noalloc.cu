@@ -4,7 +4,8 @@
 // processes whose device memory is owned by a framework's caching allocator, or real-time code
 // with a fixed memory budget.  hair_fuse_fuse_directions_noalloc() serves them: the caller passes
 // every input and output as device memory, and the scratch the fusion needs between its kernels
-// (per point-view samples, the points' view-set masks, a few per-scene constants)
+// (per point-view samples, the points' view-set masks, the hypothesis table, the argmin's
+// hand-off to the refinement, a few per-scene constants)
 // lives in one file-scope __device__ array of fixed size.  Every GPU that loads this library
 // holds that array until the process exits.
 //
@@ -21,22 +22,27 @@ namespace {
 constexpr long long kMaxPointViews = 1LL << 20;   // N * V
 constexpr long long kMaxPoints = 1LL << 18;       // N
 constexpr int kMaxViews = 1024;                   // V
+constexpr long long kMaxTable = 1LL << 16;        // V * Hq (the argmin's hypothesis-pair table)
 
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
-// samples: N rows of V rounded up to 4 views, at most N V + 3 N entries
-constexpr size_t kSampBytes = align256((size_t)(kMaxPointViews + 3 * kMaxPoints) * sizeof(float2));
+// samples and projection ratios: N V entries each
+constexpr size_t kSampBytes = align256((size_t)kMaxPointViews * sizeof(float2));
+constexpr size_t kAbBytes = align256((size_t)kMaxPointViews * sizeof(float2));
 // view-set masks: N rows of ceil(V / 64) words, at most N words when V <= 64 and fewer beyond
 constexpr size_t kMaskBytes = align256((size_t)kMaxPoints * sizeof(unsigned long long));
+constexpr size_t kQtabBytes = align256((size_t)kMaxTable * sizeof(float4));
+constexpr size_t kBestBytes = align256((size_t)kMaxPoints * sizeof(int32_t));   // argmin -> refinement
 constexpr size_t kVthrBytes = align256(kMaxViews * sizeof(float));
 constexpr size_t kHypsBytes = align256(HF_MAX_H * 3 * sizeof(float));
 constexpr size_t kRotBytes = align256(HF_MAX_T * sizeof(float2));
 constexpr size_t kWorkBytes = 256;
 constexpr size_t kErrBytes = 256;
-constexpr size_t kScratchBytes = kSampBytes + kMaskBytes + kVthrBytes + kHypsBytes + kRotBytes + kWorkBytes + kErrBytes;
+constexpr size_t kScratchBytes = kSampBytes + kAbBytes + kMaskBytes + kQtabBytes + kBestBytes + kVthrBytes + kHypsBytes +
+                                 kRotBytes + kWorkBytes + kErrBytes;
 // the size the header states
-static_assert(kScratchBytes == 16794368, "static scratch size differs from the documented 16,794,368 bytes");
+static_assert(kScratchBytes == 20988672, "static scratch size differs from the documented 20,988,672 bytes");
 
-// The shared scratch: 16,794,368 bytes (16.0 MiB), reused (and overwritten) by every call on this device.
+// The shared scratch: 20,988,672 bytes (20.0 MiB), reused (and overwritten) by every call on this device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -85,20 +91,32 @@ extern "C" int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, in
     if ((long long)N * V > kMaxPointViews) return fail(HF_ERR_SHAPE, "N * V exceeds the static scratch limit of 1048576 point-views");
     if (N > kMaxPoints) return fail(HF_ERR_SHAPE, "N exceeds the static scratch limit of 262144 points");
     if (V > kMaxViews) return fail(HF_ERR_SHAPE, "V exceeds the static scratch limit of 1024 views");
+    if ((long long)V * hf_hq(H) > kMaxTable)
+        return fail(HF_ERR_SHAPE, "V * H (H rounded up to a multiple of 32) exceeds the static scratch limit of 65536");
     if ((long long)width * height > (1LL << 31)) return fail(HF_ERR_SHAPE, "map larger than 2^31 pixels");
-    const int Vs = hf_samp_stride(V), Vw = hf_mask_words(V), Hpad = hf_hpad(H);
-    if ((size_t)N * Vs * sizeof(float2) > kSampBytes || (size_t)N * Vw * sizeof(unsigned long long) > kMaskBytes)
-        return fail(HF_ERR_SHAPE, "the samples or view-set masks exceed the static scratch");
+    const int Vw = hf_mask_words(V), Hpad = hf_hpad(H);
+    if ((size_t)N * Vw * sizeof(unsigned long long) > kMaskBytes)
+        return fail(HF_ERR_SHAPE, "the view-set masks exceed the static scratch");
 
     unsigned char* base = nullptr;
     int rc = scratch_for_current_device(&base);
     if (rc) return rc;
     float2* samp = (float2*)base;
-    unsigned long long* vmask = (unsigned long long*)(base + kSampBytes);
-    float* vthr = (float*)(base + kSampBytes + kMaskBytes);
-    float* hy = (float*)(base + kSampBytes + kMaskBytes + kVthrBytes);
-    float2* rot = (float2*)(base + kSampBytes + kMaskBytes + kVthrBytes + kHypsBytes);
-    unsigned long long* work = (unsigned long long*)(base + kSampBytes + kMaskBytes + kVthrBytes + kHypsBytes + kRotBytes);
+    float2* ab = (float2*)(base + kSampBytes);
+    unsigned char* at = base + kSampBytes + kAbBytes;
+    unsigned long long* vmask = (unsigned long long*)at;
+    at += kMaskBytes;
+    float4* qtab = (float4*)at;
+    at += kQtabBytes;
+    int32_t* best = (int32_t*)at;
+    at += kBestBytes;
+    float* vthr = (float*)at;
+    at += kVthrBytes;
+    float* hy = (float*)at;
+    at += kHypsBytes;
+    float2* rot = (float2*)at;
+    at += kRotBytes;
+    unsigned long long* work = (unsigned long long*)at;
     uint32_t* errw = (uint32_t*)((unsigned char*)work + kWorkBytes);
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
@@ -111,9 +129,9 @@ extern "C" int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, in
     if (e != cudaSuccess) return fail(HF_ERR_CUDA, cudaGetErrorString(e));
     if (host_err & HF_DEV_ERR_BAD_NBR) return fail(HF_ERR_INVALID_ARG, "a neighbour index is outside [0, N)");
 
-    PrepArgs pr{cams, V, hyps, H, Hpad, T, hy, vthr, rot, errw};
+    PrepArgs pr{cams, V, hyps, H, Hpad, T, hy, vthr, rot, errw, qtab, hf_hq(H)};
     e = hf_launch_prep(pr, s);
-    ProjectArgs pa{xyz, N, cams, V, width, height, angle, conf, conf_dtype == HF_F16 ? 1 : 0, top_k, samp, vmask, work};
+    ProjectArgs pa{xyz, N, cams, V, width, height, angle, conf, conf_dtype == HF_F16 ? 1 : 0, top_k, samp, ab, vmask, work};
     if (e == cudaSuccess) e = hf_launch_project(pa, s);
     CostArgs fa{};
     fa.pts = xyz;
@@ -123,7 +141,7 @@ extern "C" int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, in
     fa.cams = cams;
     fa.V = V;
     fa.samp = samp;
-    fa.Vs = Vs;
+    fa.ab = ab;
     fa.vmask = vmask;
     fa.Vw = Vw;
     fa.vthr = vthr;
@@ -133,6 +151,9 @@ extern "C" int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, in
     fa.rot = rot;
     fa.T = T;
     fa.L = hf_cost_lanes(top_k > 0 && top_k < V ? top_k : V, k);
+    fa.qtab = qtab;
+    fa.Hq = hf_hq(H);
+    fa.best_idx = best;
     fa.dir_out = dir_out;
     fa.cost_out = cost_out;
     fa.idx_out = idx_out;
