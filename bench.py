@@ -584,7 +584,8 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------- serving workload
-SERVING_T_SHORT, SERVING_ALPHA = 2, 0.16   # short refinement from the proposal
+SERVING_T_SHORT, SERVING_ALPHA = 2, 0.24   # short refinement from the proposal
+CALIB_SEED, CALIB_SCENES = 300, 6          # held-out serving-shaped scenes for the fallback threshold
 TRAIN_SEEDS, TRAIN_SAMPLES, TRAIN_STEPS, TRAIN_BATCH, TRAIN_LR = (100, 101, 102, 103), 500_000, 20000, 8192, 1e-3
 MLP_FLOP_PER_POINT = 2 * (51 * 256 + 256 * 256 + 256 * 3)   # forward, unpadded inputs
 
@@ -599,7 +600,7 @@ def serving_scenes(first_seed, pick="16"):
     return [scenegen.make_scene(**c) for c in cfgs]
 
 
-def train_proposal(dev, seed_offset):
+def train_proposal(dev, seed_offset, calib="serving"):
     """Proposal network trained on the GPU by the library (targets: the plain GPU fusion of four
     full-like scenes), fallback threshold calibrated on the first of them."""
     import torch
@@ -616,15 +617,34 @@ def train_proposal(dev, seed_offset):
     t2 = time.perf_counter()
     n_samples = int(X.shape[0])
     del X, Tg
-    cal = scenegen.make_scene("full", seed=seeds[0])
-    tau, info = L.calibrate_tau(cal, net, 64, 8, SERVING_T_SHORT, SERVING_ALPHA, dev, median_deg=1.8, p95_deg=7.5)
-    return net, tau, {"samples": n_samples, "scenes": seeds, "steps": TRAIN_STEPS, "batch": TRAIN_BATCH,
-                      "lr": TRAIN_LR, "loss_first50": float(np.mean(losses[:50])),
-                      "loss_last200": float(np.mean(losses[-200:])), "data_s": round(t1 - t0, 2),
-                      "train_s": round(t2 - t1, 2), "tau": tau, "T_short": SERVING_T_SHORT,
-                      "alpha_short": SERVING_ALPHA, "calibration": "largest tau keeping median <= 1.8 deg and "
-                      "p95 <= 7.5 deg against the plain fusion on training scene %d" % seeds[0],
-                      "calibration_fallback_frac": float(np.mean(info["cost"] > tau))}
+    tau, info = calibrate(net, dev, seed_offset, calib)
+    t3 = time.perf_counter()
+    return net, tau, dict(info, samples=n_samples, scenes=seeds, steps=TRAIN_STEPS, batch=TRAIN_BATCH, lr=TRAIN_LR,
+                          loss_first50=float(np.mean(losses[:50])), loss_last200=float(np.mean(losses[-200:])),
+                          data_s=round(t1 - t0, 2), train_s=round(t2 - t1, 2), calib_s=round(t3 - t2, 2))
+
+
+def calibrate(net, dev, seed_offset, kind="serving"):
+    """Fallback threshold from held-out scenes (seeds disjoint from the benchmark's and the training
+    scenes) shaped like the workload: serving-batch scenes, or for the single full scene two
+    full-preset scenes; the largest tau keeping, pooled over their points, median <= 1.8 deg and
+    p95 <= 7.5 deg against the plain fusion (margins under 2 / 8 deg)."""
+    import scenegen
+    from paper_2604_05794_b300 import learned as L
+    if kind == "serving":
+        first = CALIB_SEED + seed_offset
+        scenes = [scenegen.make_scene(**c) for c in scenegen.serving_batch(first, CALIB_SCENES)]
+        what = f"{CALIB_SCENES} held-out serving-shaped scenes (seeds {first}..{first + CALIB_SCENES - 1})"
+    else:
+        first = 105 + seed_offset
+        scenes = [scenegen.make_scene("full", seed=first + q) for q in range(2)]
+        what = f"2 held-out full-preset scenes (seeds {first}, {first + 1})"
+    tau, info = L.calibrate_tau_batch(scenes, net, 64, 8, SERVING_T_SHORT, SERVING_ALPHA, dev, median_deg=1.8,
+                                      p95_deg=7.5)
+    return tau, {"tau": tau, "T_short": SERVING_T_SHORT, "alpha_short": SERVING_ALPHA,
+                 "calibration": f"largest tau keeping median <= 1.8 deg and p95 <= 7.5 deg against the plain fusion, "
+                                f"pooled over {what}",
+                 "calibration_fallback_frac": info["fallback_frac"]}
 
 
 def serving_accuracy(scenes, outs_learned, outs_plain, n_total):
@@ -766,12 +786,8 @@ def run_serving(args):
         if args.tau is not None:
             tau, train_info = args.tau, {"loaded": args.net, "tau": args.tau}
         else:
-            import scenegen
-            from paper_2604_05794_b300 import learned as L
-            tau, _ = L.calibrate_tau(scenegen.make_scene("full", seed=TRAIN_SEEDS[0] + rank_first_seed(rank) - 200),
-                                     net, 64, 8,
-                                     SERVING_T_SHORT, SERVING_ALPHA, dev, median_deg=1.8, p95_deg=7.5)
-            train_info = {"loaded": args.net, "tau": tau}
+            tau, train_info = calibrate(net, dev, rank_first_seed(rank) - 200)
+            train_info["loaded"] = args.net
     else:
         net, tau, train_info = train_proposal(dev, rank_first_seed(rank) - 200)
     if args.save_net:
@@ -993,7 +1009,7 @@ def run_learned(args):
         pg = dist
     stream = torch.cuda.current_stream(dev)
     off = rank_first_seed(rank) - 200
-    net, tau, train_info = train_proposal(dev, off)
+    net, tau, train_info = train_proposal(dev, off, calib="full")
     sc = scenegen.make_scene("full", seed=104 + off)
     N, V, k = sc["N"], sc["V"], sc["k"]
     H, T = sc["cfg"]["H"], sc["cfg"]["T"]

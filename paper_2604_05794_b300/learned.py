@@ -2,7 +2,7 @@
 
 The network is trained on directions the plain fusion itself produces: for each training scene the
 plain GPU fusion gives the targets and the library computes the features; a seeded subset of the
-points forms the training set.  The fallback threshold tau is calibrated on a training scene so that
+points forms the training set.  The fallback threshold tau is calibrated on held-out scenes so that
 the points it accepts (proposal cost at most tau, then refined) stay close to the plain result.
 """
 import numpy as np
@@ -90,6 +90,29 @@ def proposal_costs(sc, net, H, T, dev):
         f.eval_costs(prop.view(N, 1, 3).contiguous(), c0)
         f.sync()
     return prop, c0[:, 0]
+
+
+def calibrate_tau_batch(scenes, net, H, T, T_short, alpha_short, dev, median_deg=1.8, p95_deg=7.5):
+    """Largest tau on the proposal cost for which, pooled over the points of all `scenes`, the
+    accepted points refined from their proposals (fallback points counted as exact) keep the angular
+    error against the plain fusion within median_deg and p95_deg.  Returns (tau, info) with the
+    fallback fraction at that tau."""
+    errs, costs = [], []
+    for sc in scenes:
+        plain, _, _ = plain_and_features(sc, H, T, dev)
+        d, _ = learned_no_fallback(sc, net, H, T, T_short, alpha_short, dev)
+        _, c0 = proposal_costs(sc, net, H, T, dev)
+        errs.append(angle_deg(d.cpu().numpy(), plain.cpu().numpy()))
+        costs.append(c0.cpu().numpy())
+    err, cost = np.concatenate(errs), np.concatenate(costs)
+    best = float(np.min(cost)) - 1e-6
+    for q in np.linspace(1.0, 0.0, 801):
+        tau = float(np.quantile(cost, q))
+        e = np.where(cost <= tau, err, 0.0)
+        if np.median(e) <= median_deg and np.percentile(e, 95) <= p95_deg:
+            best = tau
+            break
+    return best, dict(err=err, cost=cost, fallback_frac=float(np.mean(cost > best)))
 
 
 def calibrate_tau(sc, net, H, T, T_short, alpha_short, dev, median_deg=1.0, p95_deg=5.0):
