@@ -184,7 +184,8 @@ int configure(hf_batch* b) {
             // the proposal's cost sorts the points into the fallback and the accepted list
             A.sel[p] = LearnArgs{m, b->prop + (size_t)s.off * 3, b->cfg.tau, b->list + s.off, count + p, fb_work + p,
                                  acc_work + p, b->acc_list + s.off, acc + p};
-            CostArgs f = m;   // accepted: T_short rounds from the proposal
+            CostArgs f = m;   // accepted: T_short rounds from the proposal, a point per thread
+            f.L = 0;
             f.list = b->acc_list + s.off;
             f.list_count = acc + p;
             f.start_dir = b->prop + (size_t)s.off * 3;
@@ -242,12 +243,11 @@ cudaError_t launch_stage(hf_batch* b, int stage) {
             return hf_mlp_infer_rows(b->mlp, b->x, b->total, b->h1, b->prop, reinterpret_cast<uint32_t*>(b->ctl + kErrOff), s);
         case ST_SELECT: return hf_launch_select_batch(A->sel, ctl_for(b, ST_SELECT, -1), b->kp, s);
         case ST_ARGMIN: return hf_launch_argmin_batch(A->main, ctl_for(b, ST_ARGMIN, -1), b->kp, b->nt, s);
-        case ST_SHORT:
+        case ST_SHORT: return hf_launch_refine_batch(A->shrt, ctl_for(b, ST_SHORT, 0), b->kp, 0, b->nt, s);
         case ST_MAIN: {
             for (const auto& k : b->cls) {
-                const BatchCtl c = ctl_for(b, stage, stage == ST_SHORT ? 0 : 1, class_of(k.L), k.first, k.count);
-                const cudaError_t e = hf_launch_refine_batch((stage == ST_SHORT ? A->shrt : A->main) + k.first, c, b->kp,
-                                                             k.L, b->nt, s);
+                const BatchCtl c = ctl_for(b, stage, 1, class_of(k.L), k.first, k.count);
+                const cudaError_t e = hf_launch_refine_batch(A->main + k.first, c, b->kp, k.L, b->nt, s);
                 if (e != cudaSuccess) return e;
             }
             return cudaSuccess;
@@ -258,13 +258,13 @@ cudaError_t launch_stage(hf_batch* b, int stage) {
 
 // launches of a stage
 int stage_launches(const hf_batch* b, int stage) {
-    return stage == ST_MLP ? 2 : (stage == ST_SHORT || stage == ST_MAIN) ? (int)b->cls.size() : 1;
+    return stage == ST_MLP ? 2 : stage == ST_MAIN ? (int)b->cls.size() : 1;
 }
 
 // kernels of one run (the network's two GEMMs included)
 int kernels_per_run(const hf_batch* b) {
     const int nc = (int)b->cls.size();
-    return b->mlp ? 7 + 2 * nc : 3 + nc;
+    return b->mlp ? 8 + nc : 3 + nc;
 }
 
 // the whole run: constants (and counter reset), then every stage in order; with ev (profiling,

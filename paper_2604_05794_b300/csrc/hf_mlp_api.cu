@@ -517,7 +517,8 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
              return e2 != cudaSuccess ? e2 : hf_launch_select(la, s);
          })))
         return rc;
-    CostArgs fs = base;   // the accepted proposals: T_short rounds from the proposal
+    CostArgs fs = base;   // the accepted proposals: T_short rounds from the proposal, a point per thread
+    fs.L = 0;
     fs.list = acc_list;
     fs.list_count = acc_count;
     fs.start_dir = (const float*)c->prop.p;
