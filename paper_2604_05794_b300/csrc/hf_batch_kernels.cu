@@ -29,7 +29,7 @@ template <int KP, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) k_argmin_batch(const CostArgs* __restrict__ fa, BatchCtl c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     batch_tiles(fa, c, [](const CostArgs& a) { return thread_tiles(a.list ? *a.list_count : a.N); },
-                [&](const CostArgs& a, int t) { argmin_tile<KP>(a, t, smem_raw); });
+                [&](const CostArgs& a, int t) { argmin_tile<KP, NT>(a, t, smem_raw); });
 }
 
 template <int KP, int L, int NT>
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(128) k_select_batch(const LearnArgs* __restric
 
 template <int KP, int NT>
 cudaError_t launch_argmin(const CostArgs* fa, const BatchCtl& c, cudaStream_t s) {
-    const size_t sm = argmin_smem_bytes();
+    const size_t sm = argmin_smem_bytes<KP, NT>();
     cudaError_t e = set_smem(k_argmin_batch<KP, NT>, sm, s);
     if (e != cudaSuccess) return e;
     static int grid = 0;

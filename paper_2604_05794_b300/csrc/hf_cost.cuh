@@ -472,95 +472,7 @@ struct PairsFor {
     static constexpr int value = 1;
 };
 
-// ------------------------------------------------------------------ K2: thread per point
-// The cost of every hypothesis and the argmin (largest sum, lowest index on ties), a point per
-// thread.  Hypotheses are evaluated in pairs: the packed instructions carry hypotheses m and m + 1
-// of one view, with the view's patch samples broadcast to both halves.  The hypothesis table of a
-// chunk of HC hypotheses x a block of views and the views' camera rows sit in shared memory
-// (read by all threads at the same address); per view a thread forms its projection ratios
-// (a, b) = (X / Z, Y / Z) in single precision and reads its k + 1 samples from the point-major
-// sample rows.
-//   qtab[v][2p]     = (fx q_x(2p), fx q_x(2p+1), fx q_z(2p), fx q_z(2p+1)),  q = R_v h
-//   qtab[v][2p + 1] = (fy q_y(2p), fy q_y(2p+1), fy q_z(2p), fy q_z(2p+1))
-//   r = (fx q_x - a fx q_z, fy q_y - b fy q_z) = Z times the image offset of h
-constexpr int kArgminHC = 32;   // hypotheses per chunk
-constexpr int kArgminVB = 32;   // views per staged block
-__host__ __device__ constexpr size_t argmin_smem_bytes() {
-    return (size_t)kArgminVB * kArgminHC * sizeof(float4) + (size_t)kArgminVB * sizeof(float);
-}
-
-template <int KP>
-__device__ __forceinline__ void argmin_tile(const CostArgs& a, int blk, unsigned char* smem) {
-    constexpr int HC = kArgminHC, VB = kArgminVB;
-    float4* qs = reinterpret_cast<float4*>(smem);                                     // [VB][HC]
-    float* ts = reinterpret_cast<float*>(smem + (size_t)VB * HC * sizeof(float4));   // [VB] thresholds
-    const int cnt = a.list ? *a.list_count : a.N;
-    if (blk * (int)blockDim.x >= cnt) return;   // whole block past the list: uniform exit
-    const int q = blk * blockDim.x + threadIdx.x;
-    const bool in = q < cnt;
-    const int i = in ? (a.list ? a.list[q] : q) : 0;
-    const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
-    const bool active = in && isfinite(p0) && isfinite(p1) && isfinite(p2);
-    int nb[KP];
-    nb[0] = active ? i : -1;
-#pragma unroll
-    for (int j = 1; j < KP; ++j) nb[j] = (active && (j - 1) < a.k) ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
-    float best = -1.0f;
-    int bm = 0;
-    for (int c0 = 0; c0 < a.Hq; c0 += HC) {
-        float acc[HC];
-#pragma unroll
-        for (int m = 0; m < HC; ++m) acc[m] = 0.0f;
-        for (int vb = 0; vb < a.V; vb += VB) {
-            const int nvb = min(VB, a.V - vb);
-            __syncthreads();
-            for (int e = threadIdx.x; e < nvb * HC; e += blockDim.x)
-                qs[e] = a.qtab[(size_t)(vb + e / HC) * a.Hq + c0 + e % HC];
-            for (int e = threadIdx.x; e < nvb; e += blockDim.x) ts[e] = a.vthr[vb + e];
-            __syncthreads();
-            for (int v = vb; v < vb + nvb; ++v) {
-                const size_t base = (size_t)v * a.N;
-                const float2 r = active ? __ldg(a.ab + base + i) : make_float2(__int_as_float(0x7fc00000), 0.0f);
-                if (r.x != r.x) continue;   // v is not in the point's view set
-                const float thr = ts[v - vb];
-                float2 sm[KP];
-#pragma unroll
-                for (int j = 0; j < KP; ++j) sm[j] = nb[j] >= 0 ? __ldg(a.samp + base + nb[j]) : make_float2(0.0f, 0.0f);
-                f32x2 SX[KP], SY[KP];
-#pragma unroll
-                for (int j = 0; j < KP; ++j) {
-                    SX[j] = pk(sm[j].x, sm[j].x);
-                    SY[j] = pk(sm[j].y, sm[j].y);
-                }
-                const f32x2 NA = pk(-r.x, -r.x), NB = pk(-r.y, -r.y);
-                const f32x2* qv = reinterpret_cast<const f32x2*>(qs + (v - vb) * HC);
-#pragma unroll
-                for (int m = 0; m < HC; m += 2) {
-                    const f32x2 RX = fma2(NA, qv[2 * m + 1], qv[2 * m]);
-                    const f32x2 RY = fma2(NB, qv[2 * m + 3], qv[2 * m + 2]);
-                    const f32x2 R2 = fma2(RX, RX, mul2(RY, RY));
-                    float u0[KP], u1[KP];
-#pragma unroll
-                    for (int j = 0; j < KP; ++j) upk(fma2(RX, SX[j], mul2(RY, SY[j])), u0[j], u1[j]);
-                    const float m0 = patch_max<KP>(u0), m1 = patch_max<KP>(u1);
-                    float r0, r1;
-                    upk(R2, r0, r1);
-                    acc[m] = __fadd_rn(acc[m], r0 >= thr ? __fmul_rn(m0, rsqrt_ftz(r0)) : 0.0f);
-                    acc[m + 1] = __fadd_rn(acc[m + 1], r1 >= thr ? __fmul_rn(m1, rsqrt_ftz(r1)) : 0.0f);
-                }
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < HC; ++m)
-            if (c0 + m < a.H && acc[m] > best) {
-                best = acc[m];
-                bm = c0 + m;
-            }
-    }
-    if (in) a.best_idx[i] = bm;
-}
-
-// ---- shared-memory staging for the point-per-thread refinement
+// ---- shared-memory staging for the point-per-thread kernels (argmin, refinement)
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
@@ -598,6 +510,108 @@ __device__ __forceinline__ void issue_patch(PatchStage<KP, NT>& sg, int st, cons
             if (nb[j] >= 0) cp_async8(&sg.v[st][1 + j][t], samp + base + nb[j]);
     }
     cp_async_commit();
+}
+
+// ------------------------------------------------------------------ K2: thread per point
+// The cost of every hypothesis and the argmin (largest sum, lowest index on ties), a point per
+// thread.  Hypotheses are evaluated in pairs: the packed instructions carry hypotheses m and m + 1
+// of one view, with the view's patch samples broadcast to both halves.  The hypothesis table of a
+// chunk of HC hypotheses x a block of views and the views' camera rows sit in shared memory
+// (read by all threads at the same address); the next view's ratios (a, b) and k + 1 samples are
+// copied into shared memory (cp.async) while the current view is evaluated.
+//   qtab[v][2p]     = (fx q_x(2p), fx q_x(2p+1), fx q_z(2p), fx q_z(2p+1)),  q = R_v h
+//   qtab[v][2p + 1] = (fy q_y(2p), fy q_y(2p+1), fy q_z(2p), fy q_z(2p+1))
+//   r = (fx q_x - a fx q_z, fy q_y - b fy q_z) = Z times the image offset of h
+constexpr int kArgminHC = 32;   // hypotheses per chunk
+constexpr int kArgminVB = 32;   // views per staged block
+template <int KP, int NT>
+__host__ __device__ constexpr size_t argmin_smem_bytes() {
+    return sizeof(PatchStage<KP, NT>) + (size_t)kArgminVB * kArgminHC * sizeof(float4) + (size_t)kArgminVB * sizeof(float);
+}
+
+template <int KP, int NT>
+__device__ __forceinline__ void argmin_tile(const CostArgs& a, int blk, unsigned char* smem) {
+    constexpr int HC = kArgminHC, VB = kArgminVB, S = kRefineStages;
+    PatchStage<KP, NT>& sg = *reinterpret_cast<PatchStage<KP, NT>*>(smem);
+    float4* qs = reinterpret_cast<float4*>(smem + sizeof(PatchStage<KP, NT>));                        // [VB][HC]
+    float* ts = reinterpret_cast<float*>(smem + sizeof(PatchStage<KP, NT>) + (size_t)VB * HC * sizeof(float4));   // [VB]
+    const int tid = threadIdx.x;
+    const int cnt = a.list ? *a.list_count : a.N;
+    if (blk * NT >= cnt) return;   // whole block past the list: uniform exit
+    const int q = blk * NT + tid;
+    const bool in = q < cnt;
+    const int i = in ? (a.list ? a.list[q] : q) : 0;
+    const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
+    const bool active = in && isfinite(p0) && isfinite(p1) && isfinite(p2);
+    int nb[KP];
+    nb[0] = active ? i : -1;
+#pragma unroll
+    for (int j = 1; j < KP; ++j) nb[j] = (active && (j - 1) < a.k) ? a.nbr[(size_t)i * a.k + (j - 1)] : -1;
+    // padded / inactive members read as zero samples in every stage, never overwritten
+#pragma unroll
+    for (int j = 1; j < KP; ++j)
+        if (nb[j] < 0)
+#pragma unroll
+            for (int st = 0; st < S; ++st) sg.v[st][1 + j][tid] = make_float2(0.0f, 0.0f);
+    float best = -1.0f;
+    int bm = 0;
+    for (int c0 = 0; c0 < a.Hq; c0 += HC) {
+        float acc[HC];
+#pragma unroll
+        for (int m = 0; m < HC; ++m) acc[m] = 0.0f;
+        for (int p = 0; p < S - 1; ++p)
+            if (p < a.V) issue_patch<KP, NT>(sg, p, a.ab, a.samp, (size_t)p * a.N, i, nb, active);
+            else cp_async_commit();
+        for (int vb = 0; vb < a.V; vb += VB) {
+            const int nvb = min(VB, a.V - vb);
+            __syncthreads();
+            for (int e = tid; e < nvb * HC; e += NT) qs[e] = a.qtab[(size_t)(vb + e / HC) * a.Hq + c0 + e % HC];
+            for (int e = tid; e < nvb; e += NT) ts[e] = a.vthr[vb + e];
+            __syncthreads();
+            for (int v = vb; v < vb + nvb; ++v) {
+                const int vn = v + S - 1;
+                if (vn < a.V) issue_patch<KP, NT>(sg, vn % S, a.ab, a.samp, (size_t)vn * a.N, i, nb, active);
+                else cp_async_commit();
+                cp_async_wait<S - 1>();
+                if (!active) continue;
+                const int st = v % S;
+                const float2 r = sg.v[st][0][tid];
+                if (r.x != r.x) continue;   // v is not in the point's view set
+                const float thr = ts[v - vb];
+                f32x2 SX[KP], SY[KP];
+#pragma unroll
+                for (int j = 0; j < KP; ++j) {
+                    const float2 sj = sg.v[st][1 + j][tid];
+                    SX[j] = pk(sj.x, sj.x);
+                    SY[j] = pk(sj.y, sj.y);
+                }
+                const f32x2 NA = pk(-r.x, -r.x), NB = pk(-r.y, -r.y);
+                const f32x2* qv = reinterpret_cast<const f32x2*>(qs + (v - vb) * HC);
+#pragma unroll
+                for (int m = 0; m < HC; m += 2) {
+                    const f32x2 RX = fma2(NA, qv[2 * m + 1], qv[2 * m]);
+                    const f32x2 RY = fma2(NB, qv[2 * m + 3], qv[2 * m + 2]);
+                    const f32x2 R2 = fma2(RX, RX, mul2(RY, RY));
+                    float u0[KP], u1[KP];
+#pragma unroll
+                    for (int j = 0; j < KP; ++j) upk(fma2(RX, SX[j], mul2(RY, SY[j])), u0[j], u1[j]);
+                    const float m0 = patch_max<KP>(u0), m1 = patch_max<KP>(u1);
+                    float r0, r1;
+                    upk(R2, r0, r1);
+                    acc[m] = __fadd_rn(acc[m], r0 >= thr ? __fmul_rn(m0, rsqrt_ftz(r0)) : 0.0f);
+                    acc[m + 1] = __fadd_rn(acc[m + 1], r1 >= thr ? __fmul_rn(m1, rsqrt_ftz(r1)) : 0.0f);
+                }
+            }
+        }
+        cp_async_wait<0>();
+#pragma unroll
+        for (int m = 0; m < HC; ++m)
+            if (c0 + m < a.H && acc[m] > best) {
+                best = acc[m];
+                bm = c0 + m;
+            }
+    }
+    if (in) a.best_idx[i] = bm;
 }
 
 // Patch terms of two directions (the packed halves of rx, ry) in one view, samples broadcast.

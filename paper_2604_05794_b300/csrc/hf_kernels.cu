@@ -266,7 +266,7 @@ struct MinCtas {
 template <int KP>
 __global__ void __launch_bounds__(kCostThreads, 4) k_argmin(CostArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    argmin_tile<KP>(a, blockIdx.x, smem_raw);
+    argmin_tile<KP, kCostThreads>(a, blockIdx.x, smem_raw);
 }
 
 template <int KP, int L>
@@ -445,7 +445,7 @@ int slots_for_kp(int kp) {
 template <int KP>
 cudaError_t launch_argmin_kp(const CostArgs& a, cudaStream_t s) {
     const int cnt_max = a.N;   // with a list, its length is at most N (blocks past the list exit at once)
-    const size_t sm = argmin_smem_bytes();
+    const size_t sm = argmin_smem_bytes<KP, kCostThreads>();
     cudaError_t e = set_smem(k_argmin<KP>, sm, s);
     if (e != cudaSuccess) return e;
     k_argmin<KP><<<(cnt_max + kCostThreads - 1) / kCostThreads, kCostThreads, sm, s>>>(a);
