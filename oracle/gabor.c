@@ -14,8 +14,14 @@
  *         both rounded to bfloat16 (round to nearest even), the precision the GPU multiplies in;
  *  input  the image rounded to bfloat16, zero outside;
  *  F_k    sqrt(e_k^2 + o_k^2), e_k / o_k the window correlations (sums in double);
- *  theta  theta_k* with k* the largest F_k, the first on ties; a pixel whose two largest F lie
- *         within 1e-4 is flagged (its index is not unique in single-precision sums);
+ *  theta  theta_k* with k* the largest F_k, the first on ties;
+ *  flag   set where the index is not determined at single precision: the two largest F lie within
+ *         m = 2 (2r+1) 2^-22 max_k (S_e,k + S_o,k) + 2^-16 F_k*, where S_e,k, S_o,k are the sums of
+ *         the absolute products of the two correlations.  The first term bounds twice the error of
+ *         F_k when each correlation is accumulated in FP32 one window row at a time (the row's exact
+ *         bf16 products added to the running sum with a relative error of at most 2^-22 of the
+ *         absolute sum so far: 2r+1 such steps); the second covers F^2 formed in FP32 and compared
+ *         at a 16-bit relative resolution;
  *  C      1 - mean_k F_k / F_k* (0 where every F is 0).
  */
 #include <math.h>
@@ -65,10 +71,10 @@ void or_gabor_pixels(const float* img, int H, int W, int n_theta, int r, const f
     for (long long q = 0; q < n_idx; q++) {
         const long long pix = idx[q];
         const int y = (int)(pix / W), x = (int)(pix % W);
-        double best = -1.0, second = -1.0, sum = 0.0;
+        double best = -1.0, second = -1.0, sum = 0.0, smax = 0.0;
         int kb = 0;
         for (int k = 0; k < n_theta; k++) {
-            double e = 0.0, o = 0.0;
+            double e = 0.0, o = 0.0, abs_sum = 0.0;
             for (int v = -r; v <= r; v++) {
                 const int yy = y + v;
                 if (yy < 0 || yy >= H) continue;
@@ -79,9 +85,11 @@ void or_gabor_pixels(const float* img, int H, int W, int n_theta, int r, const f
                     const int t = (v + r) * w + (u + r);
                     e += bank[(size_t)(2 * k) * n + t] * iv;
                     o += bank[(size_t)(2 * k + 1) * n + t] * iv;
+                    abs_sum += fabs(bank[(size_t)(2 * k) * n + t] * iv) + fabs(bank[(size_t)(2 * k + 1) * n + t] * iv);
                 }
             }
             F[k] = sqrt(e * e + o * o);
+            if (abs_sum > smax) smax = abs_sum;
             sum += F[k];
             if (F[k] > best) {
                 second = best;
@@ -94,7 +102,8 @@ void or_gabor_pixels(const float* img, int H, int W, int n_theta, int r, const f
         kbest[q] = kb;
         theta[q] = (float)(3.14159265358979323846 * kb / n_theta);
         conf[q] = best > 0.0 ? (float)(1.0 - sum / n_theta / best) : 0.0f;
-        flag[q] = (uint8_t)(second >= 0.0 && best - second < 1e-4);
+        const double margin = 2.0 * ldexp((double)w, -22) * smax + ldexp(best, -16);
+        flag[q] = (uint8_t)(second >= 0.0 && best - second <= margin);
     }
     free(F);
 }

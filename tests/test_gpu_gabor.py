@@ -1,6 +1,8 @@
 """GPU parity of the Gabor orientation / confidence maps (hair_fuse_gabor, tensor cores) against the
 CPU oracle on the same seeded images: the orientation index wherever the oracle's two largest
-responses are not tied within 1e-4, the confidence within the FP32-accumulation tolerance."""
+responses are further apart than the spread an FP32 evaluation can give them (the oracle's flag; at
+least 95 % of the pixels of images without blank regions), the confidence within the
+FP32-accumulation tolerance."""
 import numpy as np
 import pytest
 
@@ -24,7 +26,7 @@ def run(images, device=True):
         return f.gabor(np.ascontiguousarray(images))
 
 
-def compare(images, th, cf, v, idx, min_unique=0.7):
+def compare(images, th, cf, v, idx, min_unique=0.95):
     o = oracle.gabor_pixels(images[v], idx)
     k = np.rint(th[v].ravel()[idx] * 64 / np.pi).astype(int) % 64
     ok = o["flag"] == 0
@@ -53,8 +55,8 @@ def test_ragged_sizes_and_random_images():
         im = RNG.random((V, H, W)).astype(np.float32)
         im[0, :, : W // 2] = 0.0
         th, cf = run(im)
-        for v in range(V):   # the zeroed half and a one-column image tie everywhere
-            compare(im, th, cf, v, np.arange(H * W), min_unique=0.0 if W == 1 else 0.3)
+        for v in range(V):   # the zeroed half of image 0 ties everywhere
+            compare(im, th, cf, v, np.arange(H * W), min_unique=0.45 if v == 0 and W > 1 else 0.95)
 
 
 
@@ -67,7 +69,8 @@ def test_unit_boundaries_and_short_units():
         th, cf = run(im)
         for v in sorted({0, V // 2, V - 1}):
             idx = np.arange(H * W) if not sample else np.linspace(0, H * W - 1, sample).astype(np.int64)
-            compare(im, th, cf, v, idx, min_unique=0.3)
+            compare(im, th, cf, v, idx)
+
 
 def test_full_view_sampled_and_host_path():
     sc = scenegen.make_scene("full", seed=2, knn=False)

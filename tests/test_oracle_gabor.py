@@ -88,13 +88,19 @@ def test_correlations_against_scipy():
     img = oracle.bf16(RNG.random((H, W)).astype(np.float32)).astype(np.float64)
     b = oracle.gabor_bank().astype(np.float64)
     F = np.empty((64, H, W))
+    S = np.empty((64, H, W))   # sums of the absolute products of both correlations
+    cor = lambda a, k: correlate2d(a, k, mode="same", boundary="fill", fillvalue=0.0)
     for k in range(64):
-        e = correlate2d(img, b[k, 0], mode="same", boundary="fill", fillvalue=0.0)
-        o = correlate2d(img, b[k, 1], mode="same", boundary="fill", fillvalue=0.0)
+        e, o = cor(img, b[k, 0]), cor(img, b[k, 1])
         F[k] = np.sqrt(e * e + o * o)
+        S[k] = cor(np.abs(img), np.abs(b[k, 0])) + cor(np.abs(img), np.abs(b[k, 1]))
     r = oracle.gabor_pixels(img.astype(np.float32), np.arange(H * W))
     Fs = np.sort(F, axis=0)
-    unique = (Fs[-1] - Fs[-2]).ravel() >= 1e-4
+    # the index is unique unless the two largest responses lie within the spread an FP32 evaluation
+    # can give them: 15 window-row steps of relative error 2^-22 on each correlation, F^2 compared
+    # at 2^-16
+    margin = 2 * 15 * 2.0 ** -22 * S.max(axis=0) + 2.0 ** -16 * Fs[-1]
+    unique = (Fs[-1] - Fs[-2] > margin).ravel()
     assert np.array_equal(r["flag"] == 0, unique)
     kb = np.argmax(F, axis=0).ravel()
     assert unique.mean() > 0.9 and np.array_equal(r["k"][unique], kb[unique])
