@@ -311,6 +311,14 @@ int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, int V, int wi
  * Runs on cuda_stream and waits for it. */
 int hair_fuse_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, void* cuda_stream);
 
+/* The same GEMM with the limit of its pipeline's bounded waits set to wait_ns nanoseconds (0: the
+ * default 2 s), for exercising the timeout path (the paper has no counterpart).  When a wait runs
+ * out the CTA records the expiry, waits (up to 2 s) for the copies and tensor-core operations it has
+ * already issued, which complete by themselves, releases its tensor memory and writes no output;
+ * the call then returns HF_ERR_TIMEOUT (C is left unspecified) and the next call starts clean. */
+int hair_fuse_gemm_bf16_bounded(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K,
+                                unsigned long long wait_ns, void* cuda_stream);
+
 /* ------------------------------------------------------------------------------------------------
  * Learned proposal network.  The paper has no counterpart: a small MLP maps per-point multi-view
  * orientation features to an initial direction that a short refinement finishes, replacing most of
@@ -350,6 +358,9 @@ int hair_fuse_mlp_grads(hf_mlp* mlp, const uint16_t* X, const float* T, long lon
                         float* grads_out, float* loss_out, uint16_t* xb_out, float* tb_out);
 /* Proposals dir_out (n x 3, unit) for features X (n x 64 bf16), both of kind mem_kind. */
 int hair_fuse_mlp_forward(hf_mlp* mlp, const uint16_t* X, int n, float* dir_out, int mem_kind);
+/* The same forward pass, writing the head's raw outputs y = W3 h2 + b3 (n x 3, before the
+ * normalisation) to y_out. */
+int hair_fuse_mlp_forward_raw(hf_mlp* mlp, const uint16_t* X, int n, float* y_out, int mem_kind);
 /* Parameters, Adam state and step counter to / from a binary file (magic "HFMLP001"). */
 int hair_fuse_mlp_save(hf_mlp* mlp, const char* path);
 int hair_fuse_mlp_load(hf_mlp* mlp, const char* path);
@@ -478,6 +489,13 @@ int hair_fuse_fibonacci_hemisphere(int H, float* out);
 #define HF_ISSUE_PATCH3 7
 #define HF_ISSUE_PATCH3S 8
 int hair_fuse_issue_rate(int kind, int iters, void* cuda_stream, double* instr_out, double* ops_out, float* ms_out);
+
+/* Allocation-failure hook for testing the error paths (the paper has no counterpart): after
+ * hair_fuse_fail_alloc_after(n) with n >= 0, the (n + 1)-th device allocation that a context makes
+ * for its buffers from then on fails as if the device were out of memory (once; the call that needed
+ * it returns HF_ERR_OOM with nothing else changed); n < 0 disables the hook.  Process-wide; meant
+ * for single-threaded tests. */
+int hair_fuse_fail_alloc_after(int n);
 
 /* Wait for the context's stream and return any error latched on the device. */
 int hair_fuse_sync(hf_ctx* ctx);

@@ -85,6 +85,8 @@ _SIGS = {
                        _i], _i),
     "hair_fuse_fibonacci_hemisphere": ([_i, _vp], _i),
     "hair_fuse_gemm_bf16": ([_vp, _vp, _vp, _i, _i, _i, _vp], _i),
+    "hair_fuse_gemm_bf16_bounded": ([_vp, _vp, _vp, _i, _i, _i, ctypes.c_ulonglong, _vp], _i),
+    "hair_fuse_fail_alloc_after": ([_i], _i),
     "hair_fuse_sync": ([_vp], _i),
     "hair_fuse_profile": ([_vp, _i], _i),
     "hair_fuse_profile_read": ([_vp, ctypes.POINTER(hf_kernel_time), _i], _i),
@@ -101,6 +103,7 @@ _SIGS = {
     "hair_fuse_mlp_train": ([_vp, _vp, _vp, _ll, _i, _i, ctypes.c_float, ctypes.c_uint64, _i, _vp], _i),
     "hair_fuse_mlp_grads": ([_vp, _vp, _vp, _ll, _i, ctypes.c_uint64, _vp, _vp, _vp, _vp], _i),
     "hair_fuse_mlp_forward": ([_vp, _vp, _i, _vp, _i], _i),
+    "hair_fuse_mlp_forward_raw": ([_vp, _vp, _i, _vp, _i], _i),
     "hair_fuse_mlp_save": ([_vp, ctypes.c_char_p], _i),
     "hair_fuse_mlp_load": ([_vp, ctypes.c_char_p], _i),
     "hair_fuse_mlp_last_error": ([_vp], ctypes.c_char_p),
@@ -155,6 +158,8 @@ def gabor_bank(**kw):
     return out
 hair_fuse_fibonacci_hemisphere = _lib.hair_fuse_fibonacci_hemisphere
 hair_fuse_gemm_bf16 = _lib.hair_fuse_gemm_bf16
+hair_fuse_gemm_bf16_bounded = _lib.hair_fuse_gemm_bf16_bounded
+hair_fuse_fail_alloc_after = _lib.hair_fuse_fail_alloc_after
 hair_fuse_sync = _lib.hair_fuse_sync
 hair_fuse_profile = _lib.hair_fuse_profile
 hair_fuse_profile_read = _lib.hair_fuse_profile_read
@@ -171,6 +176,7 @@ hair_fuse_mlp_get_params = _lib.hair_fuse_mlp_get_params
 hair_fuse_mlp_train = _lib.hair_fuse_mlp_train
 hair_fuse_mlp_grads = _lib.hair_fuse_mlp_grads
 hair_fuse_mlp_forward = _lib.hair_fuse_mlp_forward
+hair_fuse_mlp_forward_raw = _lib.hair_fuse_mlp_forward_raw
 hair_fuse_mlp_save = _lib.hair_fuse_mlp_save
 hair_fuse_mlp_load = _lib.hair_fuse_mlp_load
 hair_fuse_mlp_last_error = _lib.hair_fuse_mlp_last_error
@@ -516,16 +522,18 @@ class ProposalNet:
                                     loss.ctypes.data, xb.ctypes.data, tb.ctypes.data))
         return g, float(loss[0]), xb, tb
 
-    def forward(self, X, out=None):
-        """Proposals (n, 3) for features X (n, 64) bf16 (CUDA tensor or uint16 numpy array)."""
+    def forward(self, X, out=None, raw=False):
+        """Proposals (n, 3) for features X (n, 64) bf16 (CUDA tensor or uint16 numpy array); with
+        raw=True the head's outputs before the normalisation."""
+        fn = hair_fuse_mlp_forward_raw if raw else hair_fuse_mlp_forward
         n = X.shape[0]
         if isinstance(X, np.ndarray):
             out = np.empty((n, 3), np.float32) if out is None else out
-            self._c(hair_fuse_mlp_forward(self.h, np.ascontiguousarray(X).ctypes.data, n, out.ctypes.data, HF_HOST))
+            self._c(fn(self.h, np.ascontiguousarray(X).ctypes.data, n, out.ctypes.data, HF_HOST))
             return out
         import torch
         out = torch.empty((n, 3), device=X.device) if out is None else out
-        self._c(hair_fuse_mlp_forward(self.h, X.data_ptr(), n, out.data_ptr(), HF_DEVICE))
+        self._c(fn(self.h, X.data_ptr(), n, out.data_ptr(), HF_DEVICE))
         return out
 
     def save(self, path):

@@ -1,5 +1,6 @@
 // hf_api.cu - the C ABI: argument checks, device memory owned by the context, launches on the
 // context's stream, error latching and per-kernel event timing.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -85,6 +86,10 @@ int hf_cuda_err(hf_ctx* c, cudaError_t e, const char* what) {
     return hf_set_err(c, e == cudaErrorMemoryAllocation ? HF_ERR_OOM : HF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Allocation-failure hook: with g_fail_after = n >= 0 the (n + 1)-th device allocation of a context
+// from then on reports out-of-memory (once); -1 disables it.
+static std::atomic<int> g_fail_after{-1};
+
 int hf_ensure(hf_ctx* c, DevBuf& b, size_t bytes) {
     if (bytes <= b.cap) return HF_OK;
     if (b.p) {
@@ -94,6 +99,12 @@ int hf_ensure(hf_ctx* c, DevBuf& b, size_t bytes) {
         c->dev_bytes -= (long long)b.cap;
         b.p = nullptr;
         b.cap = 0;
+    }
+    for (int n = g_fail_after.load(); n >= 0;) {   // the hook: count this allocation down
+        if (g_fail_after.compare_exchange_weak(n, n - 1)) {
+            if (n == 0) return hf_set_err(c, HF_ERR_OOM, "cudaMalloc of %zu bytes failed: injected out-of-memory", bytes);
+            break;
+        }
     }
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
@@ -375,6 +386,11 @@ int hair_fuse_fibonacci_hemisphere(int H, float* out) {
         cudaGetLastError();
         return hf_set_err(nullptr, HF_ERR_CUDA, "fibonacci hemisphere: %s", cudaGetErrorString(e));
     }
+    return HF_OK;
+}
+
+int hair_fuse_fail_alloc_after(int n) {
+    g_fail_after.store(n < 0 ? -1 : n);
     return HF_OK;
 }
 

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
     const uint32_t tmem = *tslot;
 
     __shared__ int s_ok;
+    const uint64_t wait_ns = g.wait_ns ? g.wait_ns : kWaitTimeoutNs;
     if (threadIdx.x == 0) {
         bool ok = true;
         int issued = 0;   // chunks whose loads were issued
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
         for (; c < nk; ++c) {
             const int s = c % kStages;
             const uint32_t ph = (c / kStages) & 1;
-            if (!mbar_wait(full + s, ph, kWaitTimeoutNs)) {
+            if (!mbar_wait(full + s, ph, wait_ns)) {
                 ok = false;
                 break;
             }
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
             mma_commit(empty + s);
             if (issued < nk) {
                 // the stage is reused: wait until the MMAs that read it are done
-                if (!mbar_wait(empty + s, ph, kWaitTimeoutNs)) {
+                if (!mbar_wait(empty + s, ph, wait_ns)) {
                     ok = false;
                     ++c;
                     break;
@@ -211,9 +212,12 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
     }
     __syncthreads();
     bool ok = s_ok != 0;
-    if (!mbar_wait(done, 0, kWaitTimeoutNs)) {
+    if (!mbar_wait(done, 0, wait_ns)) {
         ok = false;
         if (lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
+        // the committed MMAs complete by themselves: wait for them (bounded) before the tensor
+        // memory they write is released
+        mbar_wait(done, 0, kWaitTimeoutNs);
     }
     fence_after();
 
@@ -294,7 +298,11 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
             y2 += part[3 * lrow + 2] + consts[BN + 770];
             const float nn = sqrtf(y0 * y0 + y1 * y1 + y2 * y2);
             float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
-            if (nn > 0.0f) {
+            if (g.head_raw) {
+                d0 = y0;
+                d1 = y1;
+                d2 = y2;
+            } else if (nn > 0.0f) {
                 d0 = y0 / nn;
                 d1 = y1 / nn;
                 d2 = y2 / nn;
@@ -528,7 +536,11 @@ __global__ void __launch_bounds__(kPThreads, 1) k_gemm_persist(const __grid_cons
                     if (wr) {
                         const float nn = sqrtf(y0 * y0 + y1 * y1 + y2 * y2);
                         float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
-                        if (nn > 0.0f) {
+                        if (g.head_raw) {
+                            d0 = y0;
+                            d1 = y1;
+                            d2 = y2;
+                        } else if (nn > 0.0f) {
                             d0 = y0 / nn;
                             d1 = y1 / nn;
                             d2 = y2 / nn;
@@ -660,7 +672,8 @@ cudaError_t hf_gemm_persist(int epi, const CUtensorMap& ta, const CUtensorMap& t
     return epi == EPI_HEAD ? launch_persist<EPI_HEAD>(ta, tb, g, s) : launch_persist<EPI_GELU>(ta, tb, g, s);
 }
 
-extern "C" int hair_fuse_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, void* stream) {
+namespace {
+int gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, unsigned long long wait_ns, void* stream) {
     if (!A || !B || !C || M < 1 || N < 16 || K < 64 || K % 64 || N % 16)
         return hf_set_err(nullptr, HF_ERR_INVALID_ARG, "need M >= 1, N a multiple of 16, K a multiple of 64");
     const int bn = N % 256 == 0 ? 256 : N % 128 == 0 ? 128 : N % 64 == 0 ? 64 : 16;
@@ -679,6 +692,7 @@ extern "C" int hair_fuse_gemm_bf16(const uint16_t* A, const uint16_t* B, float* 
     g.C = C;
     g.ldc = N;
     g.errw = errw;
+    g.wait_ns = wait_ns;
     if (e == cudaSuccess) e = hf_gemm_tn(EPI_STORE, bn, ta, tb, g, 1, (cudaStream_t)stream);
     uint32_t host_err = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&host_err, errw, sizeof host_err, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
@@ -687,4 +701,14 @@ extern "C" int hair_fuse_gemm_bf16(const uint16_t* A, const uint16_t* B, float* 
     if (e != cudaSuccess) return hf_set_err(nullptr, HF_ERR_CUDA, "gemm: %s", cudaGetErrorString(e));
     if (host_err) return hf_set_err(nullptr, HF_ERR_TIMEOUT, "gemm: a bounded device wait expired");
     return HF_OK;
+}
+}  // namespace
+
+extern "C" int hair_fuse_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, void* stream) {
+    return gemm_bf16(A, B, C, M, N, K, 0, stream);
+}
+
+extern "C" int hair_fuse_gemm_bf16_bounded(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K,
+                                           unsigned long long wait_ns, void* stream) {
+    return gemm_bf16(A, B, C, M, N, K, wait_ns, stream);
 }

@@ -11,7 +11,7 @@ enum {
     EPI_ATOMIC = 1,       // C[row][n] += acc (+ bias[n] from split 0): split-K partial sums (f32)
     EPI_GELU_TRAIN = 2,   // Z = acc + bias (f32), H = bf16(gelu(Z)), HT = H transposed (bf16)
     EPI_GELU = 3,         // H = bf16(gelu(acc + bias))
-    EPI_HEAD = 4,         // h = bf16(gelu(acc + bias)), y = w3 . h + b3 (3 outputs), dir = y / |y|; BN = N = 256
+    EPI_HEAD = 4,         // h = bf16(gelu(acc + bias)), y = w3 . h + b3 (3 outputs), dir = y / |y| (or y); BN = N = 256
     EPI_PARTIAL = 5,      // C[split z][row][n] = acc: split-K partial tiles, summed afterwards in a fixed order
 };
 
@@ -30,9 +30,12 @@ struct GemmArgs {
     const float* w3;          // EPI_HEAD: 3 x 256 f32 (values of the bf16 layer-3 weights)
     const float* b3;          // EPI_HEAD: 3
     float* dir_out;           // EPI_HEAD: M x 3
+    int head_raw;             // EPI_HEAD: write y itself instead of y / |y|
     uint32_t* errw;           // device error word (HF_DEV_ERR_TIMEOUT)
     long long split_stride;   // EPI_PARTIAL: elements between the partial tiles of consecutive splits
     int stages;               // set by hf_gemm_tn: operand ring depth
+    unsigned long long wait_ns;   // limit of the pipeline's waits (0: kWaitTimeoutNs); the drain after an
+                                  // expiry always waits up to kWaitTimeoutNs for work that completes by itself
 };
 
 // 2D bf16 tensor map of a row-major [rows x cols] matrix (cols a multiple of 64, base 16-byte

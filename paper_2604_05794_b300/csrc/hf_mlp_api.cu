@@ -327,7 +327,8 @@ int hair_fuse_mlp_grads(hf_mlp* m, const uint16_t* X, const float* T, long long 
     return mlp_sync_check(m);
 }
 
-int hair_fuse_mlp_forward(hf_mlp* m, const uint16_t* X, int n, float* dir_out, int mem_kind) {
+namespace {
+int mlp_forward(hf_mlp* m, const uint16_t* X, int n, float* dir_out, int mem_kind, bool raw) {
     if (!m || !X || !dir_out || n < 1) return mlp_err(m, HF_ERR_INVALID_ARG, "%s", "bad forward arguments");
     int rc;
     if ((rc = ensure_h1(m, n))) return rc;
@@ -341,7 +342,7 @@ int hair_fuse_mlp_forward(hf_mlp* m, const uint16_t* X, int n, float* dir_out, i
         xd = (const uint16_t*)tmp;
         od = (float*)((char*)tmp + (size_t)n * 128);
     }
-    if (e == cudaSuccess) e = hf_mlp_infer(m->d, m->P, xd, n, m->h1, od, m->errw, m->stream);
+    if (e == cudaSuccess) e = hf_mlp_infer(m->d, m->P, xd, n, m->h1, od, m->errw, m->stream, raw);
     if (e == cudaSuccess && mem_kind == HF_HOST) e = cudaMemcpyAsync(dir_out, od, (size_t)n * 12, cudaMemcpyDeviceToHost, m->stream);
     if (mem_kind == HF_HOST) {
         cudaError_t e2 = cudaStreamSynchronize(m->stream);
@@ -350,6 +351,15 @@ int hair_fuse_mlp_forward(hf_mlp* m, const uint16_t* X, int n, float* dir_out, i
     }
     if (e != cudaSuccess) return mlp_cuda(m, e, "forward");
     return mem_kind == HF_HOST ? mlp_sync_check(m) : HF_OK;
+}
+}  // namespace
+
+int hair_fuse_mlp_forward(hf_mlp* m, const uint16_t* X, int n, float* dir_out, int mem_kind) {
+    return mlp_forward(m, X, n, dir_out, mem_kind, false);
+}
+
+int hair_fuse_mlp_forward_raw(hf_mlp* m, const uint16_t* X, int n, float* y_out, int mem_kind) {
+    return mlp_forward(m, X, n, y_out, mem_kind, true);
 }
 
 int hair_fuse_mlp_save(hf_mlp* m, const char* path) {
