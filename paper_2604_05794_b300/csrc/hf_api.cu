@@ -236,6 +236,8 @@ int hair_fuse_upload_points(hf_ctx* c, int N, const float* xyz, const int32_t* n
     if (k > 0) {
         rc = run_launch(c, "k_check_nbr", [&] { return hf_launch_check_nbr((const int32_t*)c->nbr.p, (long long)N * k, N, (uint32_t*)c->errw.p, c->stream); });
         if (rc) return rc;
+        rc = run_launch(c, "k_order_nbr", [&] { return hf_launch_order_nbr((int32_t*)c->nbr.p, N, k, c->stream); });
+        if (rc) return rc;
     }
     if ((rc = sync_and_check(c))) return rc;
     c->N = N;

@@ -787,9 +787,13 @@ __device__ __forceinline__ void refine_stage_tile(const CostArgs& a, int blk, un
 // The learned path's selection, a point per thread: the cost c_i of the proposal; points with a view
 // and c_i > tau are appended to the fallback list, the other finite points to the accepted list
 // (warp-aggregated appends, in the order warps reach them), |V_i| to the matching work count;
-// non-finite points get their BAD_INPUT outputs here and no list.
+// non-finite points get their BAD_INPUT outputs here and no list.  The views' camera rows are staged
+// in shared memory per block of views; the next view's ratios and patch samples are loaded into
+// registers while the current view is evaluated.
+constexpr int kSelectViews = 128;   // camera rows staged per view block
 template <int KP>
 __device__ __forceinline__ void select_tile(const LearnArgs& la, int blk) {
+    __shared__ float4 cs4[kSelectViews * 3];
     const CostArgs& a = la.f;
     const int i = blk * blockDim.x + threadIdx.x;
     const bool in = i < a.N;
@@ -808,28 +812,46 @@ __device__ __forceinline__ void select_tile(const LearnArgs& la, int blk) {
     }
     float acc = 0.0f;
     int nv = 0;
-    if (active) {
-        for (int v = 0; v < a.V; ++v) {
-            const size_t base = (size_t)v * a.N;
-            const float2 r = __ldg(a.ab + base + ic);
+    for (int vb = 0; vb < a.V; vb += kSelectViews) {
+        const int nvb = min(kSelectViews, a.V - vb);
+        __syncthreads();   // the previous block's rows are no longer read
+        for (int e = threadIdx.x; e < nvb; e += blockDim.x) {
+            const float* cam = a.cams + 16 * (vb + e);
+            cs4[3 * e] = make_float4(cam[0], cam[1], cam[4], cam[5]);
+            cs4[3 * e + 1] = make_float4(cam[6], cam[7], cam[8], cam[9]);
+            cs4[3 * e + 2] = make_float4(cam[10], cam[11], cam[12], a.vthr[vb + e]);
+        }
+        __syncthreads();
+        if (!active) continue;
+        float2 rn = __ldg(a.ab + (size_t)vb * a.N + ic), sn[KP];
+#pragma unroll
+        for (int j = 0; j < KP; ++j) sn[j] = nb[j] >= 0 ? __ldg(a.samp + (size_t)vb * a.N + nb[j]) : make_float2(0.0f, 0.0f);
+        for (int v = vb; v < vb + nvb; ++v) {
+            const float2 r = rn;
+            float2 sv[KP];
+#pragma unroll
+            for (int j = 0; j < KP; ++j) sv[j] = sn[j];
+            if (v + 1 < vb + nvb) {   // the next view's data while this one is evaluated
+                const size_t base = (size_t)(v + 1) * a.N;
+                rn = __ldg(a.ab + base + ic);
+#pragma unroll
+                for (int j = 0; j < KP; ++j) sn[j] = nb[j] >= 0 ? __ldg(a.samp + base + nb[j]) : make_float2(0.0f, 0.0f);
+            }
             if (r.x != r.x) continue;
             ++nv;
-            const float* cam = a.cams + 16 * v;
-            const float fx = __ldg(cam), fy = __ldg(cam + 1);
+            // staged rows: k0 = (fx, fy, R00, R01), k1 = (R02, R10, R11, R12), k2 = (R20, R21, R22, thr)
+            const float4 k0 = cs4[3 * (v - vb)], k1 = cs4[3 * (v - vb) + 1], k2 = cs4[3 * (v - vb) + 2];
             // q = R d, then Z times the image offset (fx (q_x - a q_z), fy (q_y - b q_z))
-            const float qx = fmaf(__ldg(cam + 4), d0, fmaf(__ldg(cam + 5), d1, __fmul_rn(__ldg(cam + 6), d2)));
-            const float qy = fmaf(__ldg(cam + 7), d0, fmaf(__ldg(cam + 8), d1, __fmul_rn(__ldg(cam + 9), d2)));
-            const float qz = fmaf(__ldg(cam + 10), d0, fmaf(__ldg(cam + 11), d1, __fmul_rn(__ldg(cam + 12), d2)));
-            const float rx = __fmul_rn(fx, fmaf(-r.x, qz, qx)), ry = __fmul_rn(fy, fmaf(-r.y, qz, qy));
+            const float qx = fmaf(k0.z, d0, fmaf(k0.w, d1, __fmul_rn(k1.x, d2)));
+            const float qy = fmaf(k1.y, d0, fmaf(k1.z, d1, __fmul_rn(k1.w, d2)));
+            const float qz = fmaf(k2.x, d0, fmaf(k2.y, d1, __fmul_rn(k2.z, d2)));
+            const float rx = __fmul_rn(k0.x, fmaf(-r.x, qz, qx)), ry = __fmul_rn(k0.y, fmaf(-r.y, qz, qy));
             const float r2 = fmaf(rx, rx, __fmul_rn(ry, ry));
             float u[KP];
 #pragma unroll
-            for (int j = 0; j < KP; ++j) {
-                const float2 sj = nb[j] >= 0 ? __ldg(a.samp + base + nb[j]) : make_float2(0.0f, 0.0f);
-                u[j] = fmaf(rx, sj.x, __fmul_rn(ry, sj.y));
-            }
+            for (int j = 0; j < KP; ++j) u[j] = fmaf(rx, sv[j].x, __fmul_rn(ry, sv[j].y));
             const float mx = patch_max<KP>(u);
-            acc = __fadd_rn(acc, r2 >= __ldg(a.vthr + v) ? __fmul_rn(mx, rsqrt_ftz(r2)) : 0.0f);
+            acc = __fadd_rn(acc, r2 >= k2.w ? __fmul_rn(mx, rsqrt_ftz(r2)) : 0.0f);
         }
     }
     const float c0 = nv ? 1.0f - acc / (float)nv : 1.0f;

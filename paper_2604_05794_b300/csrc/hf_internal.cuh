@@ -213,6 +213,8 @@ cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s);
 // (cos, sin) of alpha0 / 2^t for t < T, in double then rounded
 cudaError_t hf_launch_rot(float2* rot, int T, double alpha0, cudaStream_t s);
 cudaError_t hf_launch_check_nbr(const int32_t* nbr, long long n, int N, uint32_t* errw, cudaStream_t s);
+// reorder each point's k neighbours by index distance (the cost kernels' gather order)
+cudaError_t hf_launch_order_nbr(int32_t* nbr, int N, int k, cudaStream_t s);
 
 // ------------------------------------------------------------------ batched scenes (hf_batch.cu)
 #define HF_MAX_BATCH HF_MAX_BATCH_SCENES

@@ -388,6 +388,36 @@ __global__ void k_check_nbr(const int32_t* __restrict__ nbr, long long n, int N,
     }
 }
 
+// Each point's neighbour list reordered by index distance |j - i|, the later of two equally distant
+// indices first (a point per thread, once per upload).  The patch maximum (Eq. patch_min) does not
+// depend on the order of the members, so the costs do not change; with this order member slot j of
+// consecutive points tends to address nearby samples (points along a strand are consecutive), and
+// the cost kernels' gathers of one slot across a warp touch fewer cache lines.
+__global__ void k_order_nbr(int32_t* __restrict__ nbr, int N, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N || k < 2 || k > HF_MAX_K) return;
+    int32_t* row = nbr + (size_t)i * k;
+    int v[HF_MAX_K];
+    unsigned long long key[HF_MAX_K];
+    for (int q = 0; q < k; ++q) {
+        v[q] = row[q];
+        const long long d = (long long)v[q] - i;
+        key[q] = (unsigned long long)(d < 0 ? -d : d) * 2u + (d < 0 ? 1u : 0u);
+    }
+    for (int q = 1; q < k; ++q) {   // insertion sort, stable
+        const int vq = v[q];
+        const unsigned long long kq = key[q];
+        int p = q - 1;
+        for (; p >= 0 && key[p] > kq; --p) {
+            key[p + 1] = key[p];
+            v[p + 1] = v[p];
+        }
+        key[p + 1] = kq;
+        v[p + 1] = vq;
+    }
+    for (int q = 0; q < k; ++q) row[q] = v[q];
+}
+
 // ------------------------------------------------------------------ batched scenes (work loop in hf_batchtiles.cuh)
 using namespace hf_bt;
 
@@ -598,6 +628,11 @@ cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s) {
 cudaError_t hf_launch_rot(float2* rot, int T, double alpha0, cudaStream_t s) {
     if (T <= 0) return cudaSuccess;
     k_rot<<<1, 32, 0, s>>>(rot, T, alpha0);
+    return cudaGetLastError();
+}
+
+cudaError_t hf_launch_order_nbr(int32_t* nbr, int N, int k, cudaStream_t s) {
+    k_order_nbr<<<(N + 255) / 256, 256, 0, s>>>(nbr, N, k);
     return cudaGetLastError();
 }
 

@@ -79,6 +79,20 @@ def test_deterministic(tiny):
         assert np.array_equal(a[key], b[key]), key
 
 
+def test_neighbour_order_does_not_matter(tiny):
+    """The patch maximum is over a set (Eq. patch_min): permuting each point's neighbour list (the
+    library reorders it for its gathers) gives the same outputs bit for bit, k = 8 and k = 16."""
+    rng = np.random.default_rng(11)
+    for k in (8, 16):
+        sc = dict(tiny)
+        sc["nbr"] = scenegen.knn_of(tiny["points"], k)
+        a = run_library(sc, 32, 4)
+        sc["nbr"] = np.ascontiguousarray(rng.permuted(sc["nbr"], axis=1))
+        b = run_library(sc, 32, 4)
+        for key in a:
+            assert np.array_equal(a[key], b[key]), (k, key)
+
+
 @pytest.mark.parametrize("n", [1, 2, 7, 127, 128, 129, 300])
 def test_ragged_sizes(tiny, n):
     sub = scenegen.subset_scene(tiny, np.arange(0, tiny["N"], tiny["N"] // n)[:n])   # k = min(5, n - 1)
