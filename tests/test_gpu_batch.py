@@ -13,7 +13,9 @@ pytestmark = pytest.mark.gpu
 
 
 def _scenes():
-    """Four small scenes that differ in point count, views, map size and dtype, k, H, T, top-K."""
+    """Five small scenes that differ in point count, views, map size and dtype, k, H, T, top-K; the
+    last has 150 views, more than one group of 32 lanes holds, so its refinement gathers the patch
+    in several chunks."""
     return [
         (scenegen.make_scene("tiny"), dict(H=32, T=4, top_k=0)),
         (scenegen.make_scene("mid", seed=11, n_strands=150, width=512, height=512, f=600.0), dict(H=64, T=8, top_k=0)),
@@ -21,6 +23,8 @@ def _scenes():
          dict(H=48, T=6, top_k=5)),
         (scenegen.make_scene("mid", seed=13, n_strands=40, V=24, width=512, height=512, f=600.0),
          dict(H=64, T=8, top_k=0)),
+        (scenegen.make_scene("mid", seed=14, n_strands=12, V=150, width=256, height=256, f=300.0),
+         dict(H=32, T=4, top_k=0)),
     ]
 
 
@@ -96,11 +100,12 @@ def test_plain_batch_equals_alone(scenes, shape):
         f.close()
 
 
-def test_learned_batch_equals_alone(scenes):
+@pytest.mark.parametrize("Ts", [2, 4])
+def test_learned_batch_equals_alone(scenes, Ts):
     import paper_2604_05794_b300 as hf
     net = hf.ProposalNet(1024)
     net.set_params(om.init(5).astype(np.float32))
-    Ts, al, tau = 2, 0.05, 0.3
+    al, tau = 0.05, 0.3
     ctxs = [_ctx(sc, o) for sc, o in scenes]
     want, nf_want = [], []
     for f, (sc, _) in zip(ctxs, scenes):
