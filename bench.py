@@ -109,15 +109,19 @@ def alu_peak(reps=5):
 
 
 # DRAM bytes (read + write) per work unit of a kernel from one ncu capture, valid only for the kernel
-# source it was taken on: the first 12 hex digits of the SHA-256 of csrc/hf_kernels.cu.  A kernel
-# whose source changed reports traffic null until it is captured again.
+# sources it was taken on: the first 12 hex digits of the SHA-256 of every csrc/*.cu and *.cuh file
+# (in name order).  After any source change every kernel reports traffic null until captured again.
 TRAFFIC = {}
 
 
 def kernels_source_sha():
+    import glob
     import hashlib
-    with open(os.path.join(ROOT, "paper_2604_05794_b300", "csrc", "hf_kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:12]
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2604_05794_b300", "csrc", "*.cu*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def kernel_traffic(name, units):

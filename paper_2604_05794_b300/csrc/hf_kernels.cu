@@ -48,6 +48,62 @@ constexpr int kProjectThreads = 128;
 
 // With a.box_keys set, the tile also folds its finite coordinates into the point cloud's bounding
 // box (keys lo[3] from 0xffffffff, hi[3] from 0, per coordinate).
+// The pixel of point p in the camera record cam (fx, fy, cx, cy, R row-major, t) and its projection
+// ratios (X/Z, Y/Z); false when the depth is not above 1e-6 or the pixel is outside W x H.  FP32
+// first, with a bound on its error: X = R p + t by nested FMAs is within 3 u S of exact (u = 2^-24,
+// S the sum of the absolute terms; 8 u S is used), the ratio's error is then at most
+// (e_X + |ra| e_Z) / (Z - e_Z) + u |ra| (a correctly rounded division), and the pixel coordinate
+// f ra + c adds one FMA rounding.  When the interval coordinate +- bound (rounded outward) holds no
+// integer, floor() of the coordinate is the exact pixel; otherwise, and when the depth test is that
+// close to its threshold, the float-float evaluation decides as before.
+__device__ __forceinline__ bool pixel_of(const float* __restrict__ cam, float p0, float p1, float p2, int W, int H,
+                                         float& fu, float& fv, float& ra_out, float& rb_out) {
+    const float fx = __ldg(cam), fy = __ldg(cam + 1), cx = __ldg(cam + 2), cy = __ldg(cam + 3);
+    const float r00 = __ldg(cam + 4), r01 = __ldg(cam + 5), r02 = __ldg(cam + 6);
+    const float r10 = __ldg(cam + 7), r11 = __ldg(cam + 8), r12 = __ldg(cam + 9);
+    const float r20 = __ldg(cam + 10), r21 = __ldg(cam + 11), r22 = __ldg(cam + 12);
+    const float t0 = __ldg(cam + 13), t1 = __ldg(cam + 14), t2 = __ldg(cam + 15);
+    const float x0 = fmaf(r00, p0, fmaf(r01, p1, fmaf(r02, p2, t0)));
+    const float x1 = fmaf(r10, p0, fmaf(r11, p1, fmaf(r12, p2, t1)));
+    const float x2 = fmaf(r20, p0, fmaf(r21, p1, fmaf(r22, p2, t2)));
+    const float e0 = 0x1p-21f * (fabsf(r00 * p0) + fabsf(r01 * p1) + fabsf(r02 * p2) + fabsf(t0));
+    const float e1 = 0x1p-21f * (fabsf(r10 * p0) + fabsf(r11 * p1) + fabsf(r12 * p2) + fabsf(t1));
+    const float e2 = 0x1p-21f * (fabsf(r20 * p0) + fabsf(r21 * p1) + fabsf(r22 * p2) + fabsf(t2));
+    const float zlo = __fsub_rd(x2, e2);
+    bool decided = false;
+    if (zlo > 2e-6f) {
+        const float ra = __fdiv_rn(x0, x2), rb = __fdiv_rn(x1, x2);
+        const float dra = 1.01f * ((e0 + fabsf(ra) * e2) / zlo + 0x1p-23f * fabsf(ra));
+        const float drb = 1.01f * ((e1 + fabsf(rb) * e2) / zlo + 0x1p-23f * fabsf(rb));
+        const float u = fmaf(fx, ra, cx), v = fmaf(fy, rb, cy);
+        const float eu = 1.01f * (fabsf(fx) * dra + 0x1p-23f * fabsf(u)) + 1e-30f;
+        const float ev = 1.01f * (fabsf(fy) * drb + 0x1p-23f * fabsf(v)) + 1e-30f;
+        const float ulo = floorf(__fsub_rd(u, eu)), uhi = floorf(__fadd_ru(u, eu));
+        const float vlo = floorf(__fsub_rd(v, ev)), vhi = floorf(__fadd_ru(v, ev));
+        if (ulo == uhi && vlo == vhi && isfinite(u) && isfinite(v)) {
+            fu = ulo;
+            fv = vlo;
+            ra_out = ra;
+            rb_out = rb;
+            decided = true;
+        }
+    } else if (__fadd_ru(x2, e2) < 0.5e-6f) {
+        return false;   // behind (or at) the camera
+    }
+    if (!decided) {
+        const ff X0 = ff_dot3_plus(r00, r01, r02, p0, p1, p2, t0);
+        const ff X1 = ff_dot3_plus(r10, r11, r12, p0, p1, p2, t1);
+        const ff X2 = ff_dot3_plus(r20, r21, r22, p0, p1, p2, t2);
+        if (!(X2.hi > 1e-6f)) return false;
+        const ff ra = ff_div(X0, X2), rb = ff_div(X1, X2);
+        fu = ff_floor(ff_affine(fx, ra, cx));
+        fv = ff_floor(ff_affine(fy, rb, cy));
+        ra_out = ra.hi;
+        rb_out = rb.hi;
+    }
+    return fu >= 0.0f && fu < (float)W && fv >= 0.0f && fv < (float)H;
+}
+
 template <bool TOPK>
 __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
     const int i = blk * kProjectThreads + threadIdx.x;
@@ -86,19 +142,11 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
             ra_[q] = rb_[q] = qnan;
             const int v = v0 + q;
             if (v >= a.V) continue;
-            const float* cam = a.cams + 16 * v;
-            const float fx = __ldg(cam), fy = __ldg(cam + 1), cx = __ldg(cam + 2), cy = __ldg(cam + 3);
-            const ff X0 = ff_dot3_plus(__ldg(cam + 4), __ldg(cam + 5), __ldg(cam + 6), p0, p1, p2, __ldg(cam + 13));
-            const ff X1 = ff_dot3_plus(__ldg(cam + 7), __ldg(cam + 8), __ldg(cam + 9), p0, p1, p2, __ldg(cam + 14));
-            const ff X2 = ff_dot3_plus(__ldg(cam + 10), __ldg(cam + 11), __ldg(cam + 12), p0, p1, p2, __ldg(cam + 15));
-            if (!(X2.hi > 1e-6f)) continue;
-            const ff ra = ff_div(X0, X2), rb = ff_div(X1, X2);
-            const float fu = ff_floor(ff_affine(fx, ra, cx));
-            const float fv = ff_floor(ff_affine(fy, rb, cy));
-            if (!(fu >= 0.0f && fu < (float)a.W && fv >= 0.0f && fv < (float)a.H)) continue;
+            float fu, fv, ra, rb;
+            if (!pixel_of(a.cams + 16 * v, p0, p1, p2, a.W, a.H, fu, fv, ra, rb)) continue;
             off[q] = (long long)((size_t)v * npx + (size_t)fv * a.W + (size_t)fu);
-            ra_[q] = ra.hi;
-            rb_[q] = rb.hi;
+            ra_[q] = ra;
+            rb_[q] = rb;
         }
         float th[G], C[G];
 #pragma unroll
@@ -120,9 +168,9 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
             if (v >= a.V) break;
             float2 sv = make_float2(0.0f, 0.0f), r = make_float2(qnan, qnan);
             if (off[q] >= 0) {
-                float sn, cs;
-                sincosf(th[q], &sn, &cs);
-                sv = make_float2(C[q] * cs, C[q] * sn);
+                float sn, cn;
+                __sincosf(th[q], &sn, &cn);   // theta in [0, pi): absolute error below 1e-6
+                sv = make_float2(C[q] * cn, C[q] * sn);
                 r = make_float2(ra_[q], rb_[q]);
                 word |= 1ull << (v & 63);
                 if (TOPK) {
@@ -309,15 +357,9 @@ __device__ __forceinline__ void features_tile(const FeatArgs& a, int blk) {
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
         const int v = (m * a.V) / 16;
-        const float* cam = a.cams + 16 * v;
         off[m] = -1;
-        const ff X0 = ff_dot3_plus(cam[4], cam[5], cam[6], p0, p1, p2, cam[13]);
-        const ff X1 = ff_dot3_plus(cam[7], cam[8], cam[9], p0, p1, p2, cam[14]);
-        const ff X2 = ff_dot3_plus(cam[10], cam[11], cam[12], p0, p1, p2, cam[15]);
-        if (!(X2.hi > 1e-6f)) continue;
-        const float fu = ff_floor(ff_affine(cam[0], ff_div(X0, X2), cam[2]));
-        const float fv = ff_floor(ff_affine(cam[1], ff_div(X1, X2), cam[3]));
-        if (!(fu >= 0.0f && fu < (float)a.W && fv >= 0.0f && fv < (float)a.H)) continue;
+        float fu, fv, ra, rb;
+        if (!pixel_of(a.cams + 16 * v, p0, p1, p2, a.W, a.H, fu, fv, ra, rb)) continue;
         off[m] = (long long)((size_t)v * npx + (size_t)fv * a.W + (size_t)fu);
     }
     float th[16], C[16];
