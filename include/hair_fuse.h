@@ -435,6 +435,11 @@ int hair_fuse_batch_fallbacks(hf_batch* b, int* n_out);
 /* The launch shape in use: out2 = {threads per CTA of the cost kernels, scene order (1 heaviest first,
  * 2 as given, 3 lightest first)}. */
 int hair_fuse_batch_tuning(const hf_batch* b, int* out2);
+/* 1 when the batch took its launch shape from an earlier batch of the same shape class in this
+ * process (autotune results are cached per class: learned or plain, patch width, scene count, total
+ * points and total views each within a factor of two, the fixed cta_threads / order), 0 when it was
+ * timed on this batch or not tuned, or a negative error code. */
+int hair_fuse_batch_tuned_from_cache(const hf_batch* b);
 /* One eager run with CUDA events between the stages (synchronous): per-stage records as in
  * hair_fuse_profile_read (the network's stage counts its two GEMM launches).  Returns the number of
  * stages (records beyond max_entries are dropped) or a negative error code. */

@@ -118,6 +118,7 @@ _SIGS = {
     "hair_fuse_batch_latency": ([_vp, _vp], _i),
     "hair_fuse_batch_fallbacks": ([_vp, _vp], _i),
     "hair_fuse_batch_tuning": ([_vp, _vp], _i),
+    "hair_fuse_batch_tuned_from_cache": ([_vp], _i),
     "hair_fuse_batch_profile_run": ([_vp, ctypes.POINTER(hf_kernel_time), _i], _i),
     "hair_fuse_batch_stats": ([_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll), ctypes.POINTER(_ll),
                                ctypes.POINTER(_ll)], _i),
@@ -190,6 +191,7 @@ hair_fuse_batch_sync = _lib.hair_fuse_batch_sync
 hair_fuse_batch_latency = _lib.hair_fuse_batch_latency
 hair_fuse_batch_fallbacks = _lib.hair_fuse_batch_fallbacks
 hair_fuse_batch_tuning = _lib.hair_fuse_batch_tuning
+hair_fuse_batch_tuned_from_cache = _lib.hair_fuse_batch_tuned_from_cache
 hair_fuse_batch_profile_run = _lib.hair_fuse_batch_profile_run
 hair_fuse_batch_stats = _lib.hair_fuse_batch_stats
 hair_fuse_batch_destroy = _lib.hair_fuse_batch_destroy
@@ -641,8 +643,12 @@ class Batch:
     def tuning(self):
         out = np.zeros(2, np.int32)
         self._c(hair_fuse_batch_tuning(self.h, out.ctypes.data))
+        cached = hair_fuse_batch_tuned_from_cache(self.h)
+        if cached < 0:
+            self._c(cached)
         return dict(cta_threads=int(out[0]),
-                    order={1: "heaviest first", 2: "as given", 3: "lightest first"}.get(int(out[1]), "?"))
+                    order={1: "heaviest first", 2: "as given", 3: "lightest first"}.get(int(out[1]), "?"),
+                    cached=bool(cached))
 
     def profile_run(self):
         """One eager run with events between the stages: {stage: (launches, ms)}."""

@@ -13,7 +13,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "hf_internal.cuh"
@@ -95,6 +98,7 @@ struct hf_batch {
     };
     std::vector<Class> cls;          // the lane classes present, positions grouped by class
     bool tuned = false, configured = false;
+    bool tuned_from_cache = false;   // the launch shape came from an earlier batch of the same class
     long long total = 0;
     char* ctl = nullptr;
     ArgBlock* args = nullptr;   // device
@@ -324,10 +328,44 @@ int run_eager(hf_batch* b) {
 // order, so every buffer a timed stage reads holds what the full run left there.  The lanes per
 // point follow from each scene's view count (they fix the order of the sums, so they are not tuned:
 // a batched result stays bit-identical to the scene run alone).
+// Tuned shapes are kept per process for batches of one shape class: learned or plain, patch width,
+// scene count, total points and total views each within a factor of two, and the caller's fixed
+// choices; a later batch of the class takes them without timing.
+using TuneKey = std::tuple<int, int, int, int, int, int, int>;
+std::map<TuneKey, std::pair<int, int>>& tune_cache() {
+    static std::map<TuneKey, std::pair<int, int>> m;
+    return m;
+}
+std::mutex& tune_mutex() {
+    static std::mutex m;
+    return m;
+}
+TuneKey tune_key(const hf_batch* b) {
+    long long pts = 0, views = 0;
+    for (const auto& s : b->sc) {
+        pts += s.c->N;
+        views += s.c->V;
+    }
+    auto lg = [](long long x) { int e = 0; while (x > 1) { x >>= 1; ++e; } return e; };
+    return TuneKey{b->mlp ? 1 : 0, b->kp, (int)b->sc.size(), lg(pts), lg(views), b->cfg.cta_threads, b->cfg.order};
+}
+
 int autotune(hf_batch* b) {
     int rc;
     const int nts[] = {64, 128, 256};
     const bool learned = b->mlp != nullptr;
+    const TuneKey key = tune_key(b);
+    {
+        std::lock_guard<std::mutex> lock(tune_mutex());
+        const auto it = tune_cache().find(key);
+        if (it != tune_cache().end()) {
+            b->nt = it->second.first;
+            b->order = it->second.second;
+            if ((rc = configure(b))) return rc;
+            b->tuned = b->tuned_from_cache = true;
+            return HF_OK;
+        }
+    }
     if ((rc = configure(b)) || (rc = run_eager(b))) return rc;
     // threads per CTA of the cost kernels (the short refinement, the argmin and the refinement)
     float best = INFINITY;
@@ -364,6 +402,8 @@ int autotune(hf_batch* b) {
     }
     if ((rc = configure(b)) || (rc = run_eager(b))) return rc;
     b->tuned = true;
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    tune_cache()[key] = {b->nt, b->order};
     return HF_OK;
 }
 
@@ -574,6 +614,11 @@ extern "C" int hair_fuse_batch_tuning(const hf_batch* b, int* out2) {
     out2[0] = b->nt;
     out2[1] = b->order;
     return HF_OK;
+}
+
+extern "C" int hair_fuse_batch_tuned_from_cache(const hf_batch* b) {
+    if (!b) return HF_ERR_INVALID_ARG;
+    return b->tuned_from_cache ? 1 : 0;
 }
 
 extern "C" int hair_fuse_batch_profile_run(hf_batch* b, hf_kernel_time* out, int max_entries) {

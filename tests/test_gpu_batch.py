@@ -100,6 +100,32 @@ def test_plain_batch_equals_alone(scenes, shape):
         f.close()
 
 
+def test_autotune_result_cached_per_shape_class(scenes):
+    """A second batch of the same shape class takes the first one's tuned launch shape without
+    timing, and its results are still those of each scene fused alone."""
+    import torch
+
+    import paper_2604_05794_b300 as hf
+    ctxs = [_ctx(sc, o) for sc, o in scenes]
+    want = _alone_plain(ctxs, scenes)
+    shapes = []
+    for rep in range(2):
+        outs = [_outs(sc["N"]) for sc, _ in scenes]
+        with hf.Batch(ctxs, autotune=True) as b:
+            for s, o in enumerate(outs):
+                b.set_outputs(s, *o)
+            b.run(use_graph=True)
+            b.sync()
+            for s in range(len(scenes)):
+                _equal(_host(outs[s]), want[s])
+            shapes.append(b.tuning())
+    assert shapes[1]["cached"]
+    assert (shapes[0]["cta_threads"], shapes[0]["order"]) == (shapes[1]["cta_threads"], shapes[1]["order"])
+    torch.cuda.synchronize()
+    for f in ctxs:
+        f.close()
+
+
 @pytest.mark.parametrize("Ts", [2, 4])
 def test_learned_batch_equals_alone(scenes, Ts):
     import paper_2604_05794_b300 as hf
