@@ -287,8 +287,9 @@ int hair_fuse_eval_costs(hf_ctx* ctx, int M, const float* dirs, float* cost_out,
  *    (each may be NULL) as in hair_fuse_fuse_directions.  cfg gives H, k, T and top_k_views.
  *  - The scratch between the kernels is one static device array of 20,988,672 bytes (20.0 MiB)
  *    inside this library, which every GPU that loads the library holds until the process exits.
- *    Limits: N * V <= 1,048,576, N <= 262,144, V <= 1024, V * Hq <= 65,536 (Hq = H rounded up to
- *    a multiple of 32); larger inputs are rejected with HF_ERR_SHAPE before any work is queued.
+ *    Limits: N * V' <= 1,048,576 (V' = V rounded up to even), N <= 262,144, V <= 1024,
+ *    V * Hq <= 65,536 (Hq = H rounded up to a multiple of 32); larger inputs are rejected with
+ *    HF_ERR_SHAPE before any work is queued.
  *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress, with
  *    that device current); make that first call before any stream capture.
  *  - Every call on a device shares the one array and leaves its contents behind; the call clears

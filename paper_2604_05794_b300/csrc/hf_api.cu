@@ -57,8 +57,8 @@ int ready(hf_ctx* c) {
 int run_project(hf_ctx* c) {
     const int Vw = hf_mask_words(c->V);
     int rc;
-    if ((rc = hf_ensure(c, c->samp, (size_t)c->N * c->V * sizeof(float2)))) return rc;
-    if ((rc = hf_ensure(c, c->ab, (size_t)c->N * c->V * sizeof(float2)))) return rc;
+    if ((rc = hf_ensure(c, c->samp, (size_t)c->N * hf_view_pairs(c->V) * sizeof(float4)))) return rc;
+    if ((rc = hf_ensure(c, c->ab, (size_t)c->N * hf_view_pairs(c->V) * sizeof(float4)))) return rc;
     if ((rc = hf_ensure(c, c->vmask, (size_t)c->N * Vw * sizeof(unsigned long long)))) return rc;
     if ((rc = hf_ensure(c, c->work, sizeof(unsigned long long)))) return rc;
     cudaError_t e = cudaMemsetAsync(c->work.p, 0, sizeof(unsigned long long), c->stream);

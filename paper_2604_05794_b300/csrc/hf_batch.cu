@@ -494,8 +494,8 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
         bs.work = (double)x->V * (x->cfg.H + 6.0 * x->cfg.T) * (x->k + 1);
         const int N = x->N, V = x->V, T = x->cfg.T;
         const int Hpad = hf_hpad(x->cfg.H);
-        if (!rc) rc = hf_ensure(x, x->samp, (size_t)N * V * sizeof(float2));
-        if (!rc) rc = hf_ensure(x, x->ab, (size_t)N * V * sizeof(float2));
+        if (!rc) rc = hf_ensure(x, x->samp, (size_t)N * hf_view_pairs(V) * sizeof(float4));
+        if (!rc) rc = hf_ensure(x, x->ab, (size_t)N * hf_view_pairs(V) * sizeof(float4));
         if (!rc) rc = hf_ensure(x, x->vmask, (size_t)N * hf_mask_words(V) * sizeof(unsigned long long));
         if (!rc) rc = hf_ensure(x, x->vthr, (size_t)V * sizeof(float));
         if (!rc) rc = hf_ensure(x, x->hyps, (size_t)Hpad * 3 * sizeof(float));

@@ -189,7 +189,7 @@ __device__ __forceinline__ void view_data(const CostArgs& a, const PointCtx<KP>&
     const float r00 = __ldg(cam + 4), r01 = __ldg(cam + 5), r02 = __ldg(cam + 6);
     const float r10 = __ldg(cam + 7), r11 = __ldg(cam + 8), r12 = __ldg(cam + 9);
     const float r20 = __ldg(cam + 10), r21 = __ldg(cam + 11), r22 = __ldg(cam + 12);
-    const float2 r = __ldg(a.ab + (size_t)v * a.N + pc.i);
+    const float2 r = __ldg(a.ab + hf_pv(v, pc.i, a.N));
     const float ra = r.x, rb = r.y;
     j[0] = __fmul_rn(fx, fmaf(-ra, r20, r00));
     j[1] = __fmul_rn(fx, fmaf(-ra, r21, r01));
@@ -200,7 +200,7 @@ __device__ __forceinline__ void view_data(const CostArgs& a, const PointCtx<KP>&
     thr = __ldg(a.vthr + v);
 #pragma unroll
     for (int m = 0; m < KP; ++m)
-        sm[m] = pc.nb[m] >= 0 ? __ldg(a.samp + (size_t)v * a.N + pc.nb[m]) : make_float2(0.0f, 0.0f);
+        sm[m] = pc.nb[m] >= 0 ? __ldg(a.samp + hf_pv(v, pc.nb[m], a.N)) : make_float2(0.0f, 0.0f);
 }
 
 // Gather chunk `chunk` of the point's view set into the lane's NP view pairs (pairs >= np stay
@@ -490,24 +490,52 @@ template <int KP, int NT>
 struct PatchStage {
     float2 v[kRefineStages][KP + 1][NT];
 };
+// The refinement's ring holds view pairs: one 16-byte element per item for views 2q and 2q + 1.
+template <int KP, int NT>
+struct PairStage {
+    float4 v[kRefineStages][KP + 1][NT];
+};
 template <int KP, int NT>
 __host__ __device__ constexpr size_t refine_smem_bytes() {
-    return sizeof(PatchStage<KP, NT>) + (size_t)kCamStageViews * 3 * sizeof(float4);
+    return sizeof(PairStage<KP, NT>) + (size_t)kCamStageViews * 3 * sizeof(float4);
+}
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+
+// Queue the copies of view pair q's patch data into stage st (16 bytes an item, L2 only; one commit
+// group per call, also when the thread has nothing to copy).
+template <int KP, int NT>
+__device__ __forceinline__ void issue_pair(PairStage<KP, NT>& sg, int st, const float2* __restrict__ ab,
+                                           const float2* __restrict__ samp, int q, int N, int i, const int (&nb)[KP],
+                                           bool active) {
+    const int t = threadIdx.x;
+    if (active) {
+        const float4* ab4 = reinterpret_cast<const float4*>(ab) + (size_t)q * N;
+        const float4* sp4 = reinterpret_cast<const float4*>(samp) + (size_t)q * N;
+        cp_async16(&sg.v[st][0][t], ab4 + i);
+        cp_async16(&sg.v[st][1][t], sp4 + i);
+#pragma unroll
+        for (int j = 1; j < KP; ++j)
+            if (nb[j] >= 0) cp_async16(&sg.v[st][1 + j][t], sp4 + nb[j]);
+    }
+    cp_async_commit();
 }
 
 // Queue the copies of one view's patch data into stage st (one commit group per call, also when
 // the thread has nothing to copy, so that group counting stays uniform).
 template <int KP, int NT>
 __device__ __forceinline__ void issue_patch(PatchStage<KP, NT>& sg, int st, const float2* __restrict__ ab,
-                                            const float2* __restrict__ samp, size_t base, int i, const int (&nb)[KP],
+                                            const float2* __restrict__ samp, int v, int N, int i, const int (&nb)[KP],
                                             bool active) {
     const int t = threadIdx.x;
     if (active) {
-        cp_async8(&sg.v[st][0][t], ab + base + i);
-        cp_async8(&sg.v[st][1][t], samp + base + i);
+        cp_async8(&sg.v[st][0][t], ab + hf_pv(v, i, N));
+        cp_async8(&sg.v[st][1][t], samp + hf_pv(v, i, N));
 #pragma unroll
         for (int j = 1; j < KP; ++j)
-            if (nb[j] >= 0) cp_async8(&sg.v[st][1 + j][t], samp + base + nb[j]);
+            if (nb[j] >= 0) cp_async8(&sg.v[st][1 + j][t], samp + hf_pv(v, nb[j], N));
     }
     cp_async_commit();
 }
@@ -560,7 +588,7 @@ __device__ __forceinline__ void argmin_tile(const CostArgs& a, int blk, unsigned
 #pragma unroll
         for (int m = 0; m < HC; ++m) acc[m] = 0.0f;
         for (int p = 0; p < S - 1; ++p)
-            if (p < a.V) issue_patch<KP, NT>(sg, p, a.ab, a.samp, (size_t)p * a.N, i, nb, active);
+            if (p < a.V) issue_patch<KP, NT>(sg, p, a.ab, a.samp, p, a.N, i, nb, active);
             else cp_async_commit();
         for (int vb = 0; vb < a.V; vb += VB) {
             const int nvb = min(VB, a.V - vb);
@@ -570,7 +598,7 @@ __device__ __forceinline__ void argmin_tile(const CostArgs& a, int blk, unsigned
             __syncthreads();
             for (int v = vb; v < vb + nvb; ++v) {
                 const int vn = v + S - 1;
-                if (vn < a.V) issue_patch<KP, NT>(sg, vn % S, a.ab, a.samp, (size_t)vn * a.N, i, nb, active);
+                if (vn < a.V) issue_patch<KP, NT>(sg, vn % S, a.ab, a.samp, vn, a.N, i, nb, active);
                 else cp_async_commit();
                 cp_async_wait<S - 1>();
                 if (!active) continue;
@@ -630,17 +658,17 @@ __device__ __forceinline__ void view_term2(f32x2 rx, f32x2 ry, const f32x2 (&SX)
 }
 
 // K3, a point per thread: T rounds of the refinement from hyps[best_idx[i]] (index output) or
-// start_dir[i] (index -1).  Per round every view of the point's set is visited once: the next
-// view's patch data is copied into shared memory (cp.async) while the current view is evaluated;
-// the Jacobian rows come from the staged camera rows and the point's ratios (a, b); the two
-// candidates of one axis (+alpha, -alpha) are evaluated as a packed pair with the samples
-// broadcast to both halves.  Round 0 also evaluates the start (paired with itself), so that every
-// compared sum is taken in the same order.
+// start_dir[i] (index -1).  Per round every view of the point's set is visited once, in view order:
+// the patch data of the next view pair is copied into shared memory (cp.async, 16 bytes an item
+// for the two views) while the current pair's two views are evaluated; the Jacobian rows come from
+// the staged camera rows and the point's ratios (a, b); the two candidates of one axis (+alpha,
+// -alpha) are evaluated as a packed pair with the samples broadcast to both halves.  Round 0 also
+// evaluates the start (paired with itself), so that every compared sum is taken in the same order.
 template <int KP, int NT>
 __device__ __forceinline__ void refine_stage_tile(const CostArgs& a, int blk, unsigned char* smem_raw) {
     constexpr int S = kRefineStages;
-    PatchStage<KP, NT>& sg = *reinterpret_cast<PatchStage<KP, NT>*>(smem_raw);
-    float4* cs4 = reinterpret_cast<float4*>(smem_raw + sizeof(PatchStage<KP, NT>));   // [view in block][3]
+    PairStage<KP, NT>& sg = *reinterpret_cast<PairStage<KP, NT>*>(smem_raw);
+    float4* cs4 = reinterpret_cast<float4*>(smem_raw + sizeof(PairStage<KP, NT>));   // [view in block][3]
     const int tid = threadIdx.x;
     const int cnt = a.list ? *a.list_count : a.N;
     if (blk * NT >= cnt) return;   // whole block past the list: uniform exit
@@ -658,7 +686,7 @@ __device__ __forceinline__ void refine_stage_tile(const CostArgs& a, int blk, un
     for (int j = 1; j < KP; ++j)
         if (nb[j] < 0)
 #pragma unroll
-            for (int st = 0; st < S; ++st) sg.v[st][1 + j][tid] = make_float2(0.0f, 0.0f);
+            for (int st = 0; st < S; ++st) sg.v[st][1 + j][tid] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     int idx = -1;
     float d0 = 1.0f, d1 = 0.0f, d2 = 0.0f;
     if (a.start_dir) {
@@ -676,6 +704,7 @@ __device__ __forceinline__ void refine_stage_tile(const CostArgs& a, int blk, un
     float best = 0.0f;
     int nv = 0;
     const int nblk = (a.V + kCamStageViews - 1) / kCamStageViews;
+    const int npair = hf_view_pairs(a.V);
     const int rounds = a.T > 0 ? a.T : 1;   // with T = 0 round 0 takes the start's sum and stops
     for (int t = 0; t < rounds; ++t) {
         const float2 cr = t < a.T ? a.rot[t] : make_float2(1.0f, 0.0f);
@@ -699,7 +728,7 @@ __device__ __forceinline__ void refine_stage_tile(const CostArgs& a, int blk, un
         float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, acc_c = 0.0f;
         int n = 0;
         for (int p = 0; p < S - 1; ++p)
-            if (p < a.V) issue_patch<KP, NT>(sg, p, a.ab, a.samp, (size_t)p * a.N, i, nb, active);
+            if (p < npair) issue_pair<KP, NT>(sg, p, a.ab, a.samp, p, a.N, i, nb, active);
             else cp_async_commit();
         for (int vb = 0; vb < a.V; vb += kCamStageViews) {
             const int nvb = min(kCamStageViews, a.V - vb);
@@ -713,45 +742,51 @@ __device__ __forceinline__ void refine_stage_tile(const CostArgs& a, int blk, un
                 }
                 __syncthreads();
             }
-            for (int v = vb; v < vb + nvb; ++v) {
-                const int vn = v + S - 1;
-                if (vn < a.V) issue_patch<KP, NT>(sg, vn % S, a.ab, a.samp, (size_t)vn * a.N, i, nb, active);
+            // the pairs of this block (kCamStageViews is even, so a pair never straddles two blocks)
+            for (int q = vb >> 1; q < (vb + nvb + 1) >> 1; ++q) {
+                const int qn = q + S - 1;
+                if (qn < npair) issue_pair<KP, NT>(sg, qn % S, a.ab, a.samp, qn, a.N, i, nb, active);
                 else cp_async_commit();
                 cp_async_wait<S - 1>();
                 if (!active) continue;
-                const int st = v % S;
-                const float2 r = sg.v[st][0][tid];
-                if (r.x != r.x) continue;   // v is not in the point's view set
-                ++n;
-                f32x2 SX[KP], SY[KP];
+                const int st = q % S;
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {   // view h of the pair: the h-th 8-byte half of each item
+                    const int v = 2 * q + h;
+                    if (v >= vb + nvb) break;   // the missing second view of an odd V
+                    const float2 r = reinterpret_cast<const float2*>(&sg.v[st][0][tid])[h];
+                    if (r.x != r.x) continue;   // v is not in the point's view set
+                    ++n;
+                    f32x2 SX[KP], SY[KP];
 #pragma unroll
-                for (int j = 0; j < KP; ++j) {
-                    const float2 sj = sg.v[st][1 + j][tid];
-                    SX[j] = pk(sj.x, sj.x);
-                    SY[j] = pk(sj.y, sj.y);
-                }
-                // staged rows: k0 = (fx, fy, R00, R01), k1 = (R02, R10, R11, R12), k2 = (R20, R21, R22, thr)
-                const float4 k0 = cs4[3 * (v - vb)], k1 = cs4[3 * (v - vb) + 1], k2 = cs4[3 * (v - vb) + 2];
-                // Z times the projection Jacobian: rows fx (R_0 - a R_2), fy (R_1 - b R_2)
-                const float j0 = __fmul_rn(k0.x, fmaf(-r.x, k2.x, k0.z)), j1 = __fmul_rn(k0.x, fmaf(-r.x, k2.y, k0.w)),
-                            j2 = __fmul_rn(k0.x, fmaf(-r.x, k2.z, k1.x));
-                const float j3 = __fmul_rn(k0.y, fmaf(-r.y, k2.x, k1.y)), j4 = __fmul_rn(k0.y, fmaf(-r.y, k2.y, k1.z)),
-                            j5 = __fmul_rn(k0.y, fmaf(-r.y, k2.z, k1.w));
-                const f32x2 J0 = pk(j0, j0), J1 = pk(j1, j1), J2 = pk(j2, j2);
-                const f32x2 J3 = pk(j3, j3), J4 = pk(j4, j4), J5 = pk(j5, j5);
+                    for (int j = 0; j < KP; ++j) {
+                        const float2 sj = reinterpret_cast<const float2*>(&sg.v[st][1 + j][tid])[h];
+                        SX[j] = pk(sj.x, sj.x);
+                        SY[j] = pk(sj.y, sj.y);
+                    }
+                    // staged rows: k0 = (fx, fy, R00, R01), k1 = (R02, R10, R11, R12), k2 = (R20, R21, R22, thr)
+                    const float4 k0 = cs4[3 * (v - vb)], k1 = cs4[3 * (v - vb) + 1], k2 = cs4[3 * (v - vb) + 2];
+                    // Z times the projection Jacobian: rows fx (R_0 - a R_2), fy (R_1 - b R_2)
+                    const float j0 = __fmul_rn(k0.x, fmaf(-r.x, k2.x, k0.z)), j1 = __fmul_rn(k0.x, fmaf(-r.x, k2.y, k0.w)),
+                                j2 = __fmul_rn(k0.x, fmaf(-r.x, k2.z, k1.x));
+                    const float j3 = __fmul_rn(k0.y, fmaf(-r.y, k2.x, k1.y)), j4 = __fmul_rn(k0.y, fmaf(-r.y, k2.y, k1.z)),
+                                j5 = __fmul_rn(k0.y, fmaf(-r.y, k2.z, k1.w));
+                    const f32x2 J0 = pk(j0, j0), J1 = pk(j1, j1), J2 = pk(j2, j2);
+                    const f32x2 J3 = pk(j3, j3), J4 = pk(j4, j4), J5 = pk(j5, j5);
 #pragma unroll
-                for (int p = 0; p < 3; ++p) {   // the +alpha / -alpha pair of axis p
-                    float L0, L1;
-                    view_term2<KP>(fma2(J0, CX[p], fma2(J1, CY[p], mul2(J2, CZ[p]))),
-                                   fma2(J3, CX[p], fma2(J4, CY[p], mul2(J5, CZ[p]))), SX, SY, k2.w, L0, L1);
-                    acc[2 * p] = __fadd_rn(acc[2 * p], L0);
-                    acc[2 * p + 1] = __fadd_rn(acc[2 * p + 1], L1);
-                }
-                if (centre) {
-                    float L0, L1;
-                    view_term2<KP>(fma2(J0, D0, fma2(J1, D1, mul2(J2, D2))), fma2(J3, D0, fma2(J4, D1, mul2(J5, D2))),
-                                   SX, SY, k2.w, L0, L1);
-                    acc_c = __fadd_rn(acc_c, L0);
+                    for (int p = 0; p < 3; ++p) {   // the +alpha / -alpha pair of axis p
+                        float L0, L1;
+                        view_term2<KP>(fma2(J0, CX[p], fma2(J1, CY[p], mul2(J2, CZ[p]))),
+                                       fma2(J3, CX[p], fma2(J4, CY[p], mul2(J5, CZ[p]))), SX, SY, k2.w, L0, L1);
+                        acc[2 * p] = __fadd_rn(acc[2 * p], L0);
+                        acc[2 * p + 1] = __fadd_rn(acc[2 * p + 1], L1);
+                    }
+                    if (centre) {
+                        float L0, L1;
+                        view_term2<KP>(fma2(J0, D0, fma2(J1, D1, mul2(J2, D2))), fma2(J3, D0, fma2(J4, D1, mul2(J5, D2))),
+                                       SX, SY, k2.w, L0, L1);
+                        acc_c = __fadd_rn(acc_c, L0);
+                    }
                 }
             }
         }
@@ -823,19 +858,18 @@ __device__ __forceinline__ void select_tile(const LearnArgs& la, int blk) {
         }
         __syncthreads();
         if (!active) continue;
-        float2 rn = __ldg(a.ab + (size_t)vb * a.N + ic), sn[KP];
+        float2 rn = __ldg(a.ab + hf_pv(vb, ic, a.N)), sn[KP];
 #pragma unroll
-        for (int j = 0; j < KP; ++j) sn[j] = nb[j] >= 0 ? __ldg(a.samp + (size_t)vb * a.N + nb[j]) : make_float2(0.0f, 0.0f);
+        for (int j = 0; j < KP; ++j) sn[j] = nb[j] >= 0 ? __ldg(a.samp + hf_pv(vb, nb[j], a.N)) : make_float2(0.0f, 0.0f);
         for (int v = vb; v < vb + nvb; ++v) {
             const float2 r = rn;
             float2 sv[KP];
 #pragma unroll
             for (int j = 0; j < KP; ++j) sv[j] = sn[j];
             if (v + 1 < vb + nvb) {   // the next view's data while this one is evaluated
-                const size_t base = (size_t)(v + 1) * a.N;
-                rn = __ldg(a.ab + base + ic);
+                rn = __ldg(a.ab + hf_pv(v + 1, ic, a.N));
 #pragma unroll
-                for (int j = 0; j < KP; ++j) sn[j] = nb[j] >= 0 ? __ldg(a.samp + base + nb[j]) : make_float2(0.0f, 0.0f);
+                for (int j = 0; j < KP; ++j) sn[j] = nb[j] >= 0 ? __ldg(a.samp + hf_pv(v + 1, nb[j], a.N)) : make_float2(0.0f, 0.0f);
             }
             if (r.x != r.x) continue;
             ++nv;

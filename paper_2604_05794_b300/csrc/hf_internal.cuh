@@ -104,9 +104,11 @@ int run_launch(hf_ctx* c, const char* name, F&& f) {
 // Kernel-launch helpers (defined in hf_kernels.cu); each returns the launch error -------------
 //
 // Scratch of the fusion path (per context, or the static array of the allocation-free entry):
-//   samp  [V][N] float2  C (cos theta, sin theta) at point i's own pixel in view v, 0 when the point
-//                        does not project into view v
-//   ab    [V][N] float2  projection ratios (X/Z, Y/Z) of point i in view v; NaN when v is not in V_i
+//   samp  [V/2][N] float4  C (cos theta, sin theta) at point i's own pixel in views 2p and 2p + 1 (one
+//                        16-byte element per view pair; 0 when the point does not project into the view)
+//   ab    [V/2][N] float4  projection ratios (X/Z, Y/Z) of point i in views 2p and 2p + 1; NaN when the
+//                        view is not in V_i (and for the missing second view of an odd V)
+//                        (V/2 rounded up; element (v, i) is float2 number hf_pv(v, i, N))
 //   vmask [N][Vw] u64    bit v of word v / 64: v is in the point's view set V_i; Vw = ceil(V / 64)
 //   hyps  [Hpad][3] f32   the hypotheses, padded to an even count with copies of h_0
 //   qtab  [V][Hq] float4  hypothesis pairs q = R_v h folded with fx, fy (the argmin's table)
@@ -114,6 +116,9 @@ int run_launch(hf_ctx* c, const char* name, F&& f) {
 //   vthr  [V] f32         degenerate-offset threshold 1e-20 (fx^2 + fy^2) per view
 //   rot   [T] float2      (cos alpha_t, sin alpha_t) of the refinement rounds
 __host__ __device__ inline int hf_mask_words(int V) { return (V + 63) / 64; }
+// view pairs of the samp / ab planes, and the float2 index of (view v, point i)
+__host__ __device__ inline int hf_view_pairs(int V) { return (V + 1) >> 1; }
+__host__ __device__ inline size_t hf_pv(int v, int i, int N) { return (((size_t)(v >> 1) * N + i) << 1) + (v & 1); }
 __host__ __device__ inline int hf_hpad(int H) { return (H + 1) & ~1; }
 
 struct ProjectArgs {

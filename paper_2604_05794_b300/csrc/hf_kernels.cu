@@ -162,12 +162,12 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
                 C[q] = load_conf(a.conf, a.conf_f16, (size_t)off[q]);
             }
         }
+        float2 svq[G], rq[G];   // this group's samples and ratios (a view past V: 0 and NaN)
 #pragma unroll
         for (int q = 0; q < G; ++q) {
             const int v = v0 + q;
-            if (v >= a.V) break;
             float2 sv = make_float2(0.0f, 0.0f), r = make_float2(qnan, qnan);
-            if (off[q] >= 0) {
+            if (v < a.V && off[q] >= 0) {
                 float sn, cn;
                 __sincosf(th[q], &sn, &cn);   // theta in [0, pi): absolute error below 1e-6
                 sv = make_float2(C[q] * cn, C[q] * sn);
@@ -188,9 +188,17 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
                     }
                 }
             }
-            a.samp[(size_t)v * a.N + i] = sv;
-            a.ab[(size_t)v * a.N + i] = r;
+            svq[q] = sv;
+            rq[q] = r;
         }
+        // one 16-byte store per view pair (G is even and v0 a multiple of G: pairs never straddle)
+#pragma unroll
+        for (int q = 0; q < G; q += 2)
+            if (v0 + q < a.V) {
+                const size_t e = hf_pv(v0 + q, i, a.N) >> 1;   // float4 element of the pair
+                reinterpret_cast<float4*>(a.samp)[e] = make_float4(svq[q].x, svq[q].y, svq[q + 1].x, svq[q + 1].y);
+                reinterpret_cast<float4*>(a.ab)[e] = make_float4(rq[q].x, rq[q].y, rq[q + 1].x, rq[q + 1].y);
+            }
         if (((v0 + G) & 63) == 0 || v0 + G >= a.V) {   // a mask word is complete
             if (!TOPK) mrow[v0 >> 6] = word;
             nset += __popcll(word);
@@ -207,7 +215,7 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
         for (int v = 0; v < a.V; ++v) {
             bool keep = false;
             for (int q = 0; q < ntop; ++q) keep |= (topv[q] == v);
-            if (!keep) a.ab[(size_t)v * a.N + i] = make_float2(qnan, qnan);
+            if (!keep) a.ab[hf_pv(v, i, a.N)] = make_float2(qnan, qnan);
         }
         nset = ntop;
     }

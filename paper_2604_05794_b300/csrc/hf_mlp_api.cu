@@ -467,8 +467,8 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     if ((rc = hf_ensure(c, c->rot, (size_t)(T > 0 ? T : 1) * sizeof(float2)))) return rc;
     if ((rc = hf_ensure(c, c->qtab, (size_t)V * hf_hq(H) * sizeof(float4)))) return rc;
     if ((rc = hf_ensure(c, c->best, (size_t)N * sizeof(int32_t)))) return rc;
-    if ((rc = hf_ensure(c, c->samp, (size_t)N * V * sizeof(float2)))) return rc;
-    if ((rc = hf_ensure(c, c->ab, (size_t)N * V * sizeof(float2)))) return rc;
+    if ((rc = hf_ensure(c, c->samp, (size_t)N * hf_view_pairs(V) * sizeof(float4)))) return rc;
+    if ((rc = hf_ensure(c, c->ab, (size_t)N * hf_view_pairs(V) * sizeof(float4)))) return rc;
     if ((rc = hf_ensure(c, c->vmask, (size_t)N * hf_mask_words(V) * sizeof(unsigned long long)))) return rc;
     if ((rc = hf_ensure(c, c->work, sizeof(unsigned long long)))) return rc;
     if ((rc = hf_ensure(c, c->outs, (size_t)N * 21))) return rc;

@@ -19,7 +19,7 @@
 namespace {
 
 // Limits of the static scratch (see the header for the caller-facing statement).
-constexpr long long kMaxPointViews = 1LL << 20;   // N * V
+constexpr long long kMaxPointViews = 1LL << 20;   // N * V, V rounded up to even (views stored in pairs)
 constexpr long long kMaxPoints = 1LL << 18;       // N
 constexpr int kMaxViews = 1024;                   // V
 constexpr long long kMaxTable = 1LL << 16;        // V * Hq (the argmin's hypothesis-pair table)
@@ -88,7 +88,8 @@ extern "C" int hair_fuse_fuse_directions_noalloc(const hf_config* cfg, int N, in
     if (!cams || !angle || !conf || !xyz || (k > 0 && !nbr) || !dir_out)
         return fail(HF_ERR_INVALID_ARG, "null input or dir_out pointer");
     if (conf_dtype != HF_F32 && conf_dtype != HF_F16) return fail(HF_ERR_INVALID_ARG, "conf_dtype must be HF_F32 or HF_F16");
-    if ((long long)N * V > kMaxPointViews) return fail(HF_ERR_SHAPE, "N * V exceeds the static scratch limit of 1048576 point-views");
+    if ((long long)N * 2 * hf_view_pairs(V) > kMaxPointViews)
+        return fail(HF_ERR_SHAPE, "N * V (V rounded up to even) exceeds the static scratch limit of 1048576 point-views");
     if (N > kMaxPoints) return fail(HF_ERR_SHAPE, "N exceeds the static scratch limit of 262144 points");
     if (V > kMaxViews) return fail(HF_ERR_SHAPE, "V exceeds the static scratch limit of 1024 views");
     if ((long long)V * hf_hq(H) > kMaxTable)
