@@ -112,14 +112,14 @@ def alu_peak(reps=5):
 # sources it was taken on: the first 12 hex digits of the SHA-256 of every csrc/*.cu and *.cuh file
 # (in name order).  After any source change every kernel reports traffic null until captured again.
 TRAFFIC = {
-    "k_project_batch": (22.71, "point-view (N V)", "bdbf4221e192", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_select_batch": (40.38, "point-view (N V)", "bdbf4221e192", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_refine_short_batch": (108.93, "accepted point-view", "bdbf4221e192", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_argmin_batch": (115.66, "fallback point-view", "bdbf4221e192", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_refine_batch": (252.96, "fallback point-view", "bdbf4221e192", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_project": (36.28, "point-view (N V)", "bdbf4221e192", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
-    "k_argmin": (19.97, "point-view in V_i", "bdbf4221e192", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
-    "k_refine": (21.74, "point-view in V_i", "bdbf4221e192", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_project_batch": (22.74, "point-view (N V)", "e183212cc004", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_select_batch": (32.64, "point-view (N V)", "e183212cc004", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_refine_short_batch": (68.18, "accepted point-view", "e183212cc004", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_argmin_batch": (76.36, "fallback point-view", "e183212cc004", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_refine_batch": (115.03, "fallback point-view", "e183212cc004", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_project": (35.20, "point-view (N V)", "e183212cc004", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_argmin": (19.54, "point-view in V_i", "e183212cc004", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_refine": (20.62, "point-view in V_i", "e183212cc004", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
 }
 
 
