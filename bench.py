@@ -67,9 +67,9 @@ SM_COUNT, FP32_LANES_PER_SM = 148, 128
 
 
 def s8d_ops(k):
-    """FP32 operations per (direction, view) as the survey's measurement section counts them: 3 per
-    patch member (multiply, multiply-add, maximum) + 12 per (hypothesis, view), + 9 more per
-    refinement candidate (its rotation into the view)."""
+    """FP32 operations per (direction, view) of the cost's reference count: 3 per patch member
+    (multiply, multiply-add, maximum) + 12 per (hypothesis, view), + 9 more per refinement candidate
+    (its rotation into the view)."""
     per_hyp = 3 * (k + 1) + 12
     return per_hyp, per_hyp + 9
 
@@ -93,8 +93,9 @@ _ALU_PEAK = None
 def alu_peak(reps=5):
     """Measured FP32 peak for the cost kernels (hair_fuse_issue_rate, CUDA events, full-occupancy grid):
     the best rate of the patch term's inner step (packed multiply / multiply-add and the three-input
-    max of absolute values), in operations/s at 3 operations per evaluation as the survey counts
-    them; scalar fma, packed fma and the three-input max are measured beside it.  Cached per run."""
+    max of absolute values), in operations/s at 3 operations per evaluation (the reference count of a
+    patch member); scalar fma, packed fma and the three-input max are measured beside it.  Cached per
+    run."""
     global _ALU_PEAK
     if _ALU_PEAK is None:
         import paper_2604_05794_b300 as hf
@@ -515,7 +516,7 @@ def run_ours(args):
             "peak_source": ap["source"], "peak_rates_ops_per_s": ap["rates_ops_per_s"],
             "work": (f"{Hh} x {ca} FP32 ops per (point, view) in V_i" if name == "k_argmin" else
                      f"{6 * T} x {cr} FP32 ops per (point, view) in V_i") +
-                    f" (survey count) x {point_views} point-views per launch",
+                    f" (reference op count) x {point_views} point-views per launch",
             "builder_count": {"instr_per_dir_view": issued_per_dir_view(k), "directions": ndir,
                               "achieved_instr_per_s": issued,
                               "frac_of_ffma_issue": issued / ap["rates_ops_per_s"]["ffma"]},
