@@ -93,6 +93,19 @@ def test_neighbour_order_does_not_matter(tiny):
             assert np.array_equal(a[key], b[key]), (k, key)
 
 
+@pytest.mark.parametrize("V", [1, 7, 21])
+def test_odd_view_counts(V):
+    """Samples and ratios are stored in view pairs: with an odd V the last pair's second half is
+    padding that no kernel may read as a view (one view, and the point-per-thread and lanes layouts)."""
+    sc = scenegen.make_scene("mid", seed=30 + V, n_strands=40, V=V, width=384, height=384, f=450.0)
+    H, T = 32, 4
+    hyps = lib_hyps(H)
+    gpu = run_library(sc, H, T)
+    osc = oracle.Scene.from_dict(sc)
+    orc = oracle.fuse(osc, hyps, T)
+    compare(gpu, orc, np.arange(sc["N"]), osc, hyps, H, strict_frac=0.9)
+
+
 @pytest.mark.parametrize("n", [1, 2, 7, 127, 128, 129, 300])
 def test_ragged_sizes(tiny, n):
     sub = scenegen.subset_scene(tiny, np.arange(0, tiny["N"], tiny["N"] // n)[:n])   # k = min(5, n - 1)

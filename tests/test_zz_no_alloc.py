@@ -52,6 +52,8 @@ def _scene(kind):
         return scenegen.make_scene("tiny")
     if kind == "tiny_f16":
         return scenegen.make_scene("tiny", conf_f16=True, seed=11)
+    if kind == "odd":   # an odd view count: the last view pair's second half is padding
+        return scenegen.make_scene("mid", seed=13, n_strands=30, V=13, width=384, height=384, f=450.0)
     # more points and views than the tiny scene, to reuse the shared array with another shape
     return scenegen.make_scene("mid", seed=12, n_strands=60, V=20, width=512, height=512, f=600.0)
 
@@ -68,7 +70,8 @@ def _reference(hf, sc, H, T, top_k, d, hyps, mk):
 
 # (scene, H, T, top-K, caller hypotheses, outputs other than dir given)
 CASES = [("tiny", 32, 4, 0, False, True), ("tiny_f16", 32, 4, 0, False, True), ("tiny", 64, 4, 0, True, True),
-         ("tiny", 32, 4, 3, False, True), ("tiny", 32, 4, 0, False, False), ("larger", 48, 6, 0, False, True)]
+         ("tiny", 32, 4, 3, False, True), ("tiny", 32, 4, 0, False, False), ("larger", 48, 6, 0, False, True),
+         ("odd", 32, 4, 0, False, True)]
 
 
 @pytest.mark.gpu
