@@ -485,7 +485,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // samples; laid out [stage][item][thread] so a warp reads consecutive 8-byte words.  View v lives
 // in stage v % S and is copied in S - 1 views ahead of its use.
 constexpr int kRefineStages = 2;
-constexpr int kCamStageViews = 256;   // camera rows staged per view block
+constexpr int kCamStageViews = 64;    // camera rows staged per view block (a multiple of 2)
 template <int KP, int NT>
 struct PatchStage {
     float2 v[kRefineStages][KP + 1][NT];
@@ -823,8 +823,8 @@ __device__ __forceinline__ void refine_stage_tile(const CostArgs& a, int blk, un
 // and c_i > tau are appended to the fallback list, the other finite points to the accepted list
 // (warp-aggregated appends, in the order warps reach them), |V_i| to the matching work count;
 // non-finite points get their BAD_INPUT outputs here and no list.  The views' camera rows are staged
-// in shared memory per block of views; the next view's ratios and patch samples are loaded into
-// registers while the current view is evaluated.
+// in shared memory per block of views; the next view pair's ratios and patch samples (one 16-byte
+// element an item) are loaded into registers while the current pair's two views are evaluated.
 constexpr int kSelectViews = 128;   // camera rows staged per view block
 template <int KP>
 __device__ __forceinline__ void select_tile(const LearnArgs& la, int blk) {
@@ -858,34 +858,49 @@ __device__ __forceinline__ void select_tile(const LearnArgs& la, int blk) {
         }
         __syncthreads();
         if (!active) continue;
-        float2 rn = __ldg(a.ab + hf_pv(vb, ic, a.N)), sn[KP];
+        // view pairs: one 16-byte load per item brings both views; the next pair is loaded while
+        // the current pair's two views are evaluated
+        const float4* ab4 = reinterpret_cast<const float4*>(a.ab);
+        const float4* sp4 = reinterpret_cast<const float4*>(a.samp);
+        const int q0 = vb >> 1, q1 = (vb + nvb + 1) >> 1;   // kSelectViews is even: pairs stay in the block
+        float4 rn = __ldg(ab4 + (size_t)q0 * a.N + ic), sn[KP];
 #pragma unroll
-        for (int j = 0; j < KP; ++j) sn[j] = nb[j] >= 0 ? __ldg(a.samp + hf_pv(vb, nb[j], a.N)) : make_float2(0.0f, 0.0f);
-        for (int v = vb; v < vb + nvb; ++v) {
-            const float2 r = rn;
-            float2 sv[KP];
+        for (int j = 0; j < KP; ++j) sn[j] = nb[j] >= 0 ? __ldg(sp4 + (size_t)q0 * a.N + nb[j]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int q = q0; q < q1; ++q) {
+            const float4 r4 = rn;
+            float4 s4[KP];
 #pragma unroll
-            for (int j = 0; j < KP; ++j) sv[j] = sn[j];
-            if (v + 1 < vb + nvb) {   // the next view's data while this one is evaluated
-                rn = __ldg(a.ab + hf_pv(v + 1, ic, a.N));
+            for (int j = 0; j < KP; ++j) s4[j] = sn[j];
+            if (q + 1 < q1) {
+                rn = __ldg(ab4 + (size_t)(q + 1) * a.N + ic);
 #pragma unroll
-                for (int j = 0; j < KP; ++j) sn[j] = nb[j] >= 0 ? __ldg(a.samp + hf_pv(v + 1, nb[j], a.N)) : make_float2(0.0f, 0.0f);
+                for (int j = 0; j < KP; ++j)
+                    sn[j] = nb[j] >= 0 ? __ldg(sp4 + (size_t)(q + 1) * a.N + nb[j]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
-            if (r.x != r.x) continue;
-            ++nv;
-            // staged rows: k0 = (fx, fy, R00, R01), k1 = (R02, R10, R11, R12), k2 = (R20, R21, R22, thr)
-            const float4 k0 = cs4[3 * (v - vb)], k1 = cs4[3 * (v - vb) + 1], k2 = cs4[3 * (v - vb) + 2];
-            // q = R d, then Z times the image offset (fx (q_x - a q_z), fy (q_y - b q_z))
-            const float qx = fmaf(k0.z, d0, fmaf(k0.w, d1, __fmul_rn(k1.x, d2)));
-            const float qy = fmaf(k1.y, d0, fmaf(k1.z, d1, __fmul_rn(k1.w, d2)));
-            const float qz = fmaf(k2.x, d0, fmaf(k2.y, d1, __fmul_rn(k2.z, d2)));
-            const float rx = __fmul_rn(k0.x, fmaf(-r.x, qz, qx)), ry = __fmul_rn(k0.y, fmaf(-r.y, qz, qy));
-            const float r2 = fmaf(rx, rx, __fmul_rn(ry, ry));
-            float u[KP];
 #pragma unroll
-            for (int j = 0; j < KP; ++j) u[j] = fmaf(rx, sv[j].x, __fmul_rn(ry, sv[j].y));
-            const float mx = patch_max<KP>(u);
-            acc = __fadd_rn(acc, r2 >= k2.w ? __fmul_rn(mx, rsqrt_ftz(r2)) : 0.0f);
+            for (int h = 0; h < 2; ++h) {
+                const int v = 2 * q + h;
+                if (v >= vb + nvb) break;   // the missing second view of an odd V
+                const float2 r = h ? make_float2(r4.z, r4.w) : make_float2(r4.x, r4.y);
+                if (r.x != r.x) continue;
+                ++nv;
+                // staged rows: k0 = (fx, fy, R00, R01), k1 = (R02, R10, R11, R12), k2 = (R20, R21, R22, thr)
+                const float4 k0 = cs4[3 * (v - vb)], k1 = cs4[3 * (v - vb) + 1], k2 = cs4[3 * (v - vb) + 2];
+                // q = R d, then Z times the image offset (fx (q_x - a q_z), fy (q_y - b q_z))
+                const float qx = fmaf(k0.z, d0, fmaf(k0.w, d1, __fmul_rn(k1.x, d2)));
+                const float qy = fmaf(k1.y, d0, fmaf(k1.z, d1, __fmul_rn(k1.w, d2)));
+                const float qz = fmaf(k2.x, d0, fmaf(k2.y, d1, __fmul_rn(k2.z, d2)));
+                const float rx = __fmul_rn(k0.x, fmaf(-r.x, qz, qx)), ry = __fmul_rn(k0.y, fmaf(-r.y, qz, qy));
+                const float r2 = fmaf(rx, rx, __fmul_rn(ry, ry));
+                float u[KP];
+#pragma unroll
+                for (int j = 0; j < KP; ++j) {
+                    const float sx = h ? s4[j].z : s4[j].x, sy = h ? s4[j].w : s4[j].y;
+                    u[j] = fmaf(rx, sx, __fmul_rn(ry, sy));
+                }
+                const float mx = patch_max<KP>(u);
+                acc = __fadd_rn(acc, r2 >= k2.w ? __fmul_rn(mx, rsqrt_ftz(r2)) : 0.0f);
+            }
         }
     }
     const float c0 = nv ? 1.0f - acc / (float)nv : 1.0f;

@@ -58,11 +58,24 @@ constexpr int kProjectThreads = 128;
 // close to its threshold, the float-float evaluation decides as before.
 __device__ __forceinline__ bool pixel_of(const float* __restrict__ cam, float p0, float p1, float p2, int W, int H,
                                          float& fu, float& fv, float& ra_out, float& rb_out) {
-    const float fx = __ldg(cam), fy = __ldg(cam + 1), cx = __ldg(cam + 2), cy = __ldg(cam + 3);
-    const float r00 = __ldg(cam + 4), r01 = __ldg(cam + 5), r02 = __ldg(cam + 6);
-    const float r10 = __ldg(cam + 7), r11 = __ldg(cam + 8), r12 = __ldg(cam + 9);
-    const float r20 = __ldg(cam + 10), r21 = __ldg(cam + 11), r22 = __ldg(cam + 12);
-    const float t0 = __ldg(cam + 13), t1 = __ldg(cam + 14), t2 = __ldg(cam + 15);
+    float4 c0, c1, c2, c3;   // the record: four 16-byte loads when aligned, else sixteen scalar ones
+    if ((reinterpret_cast<uintptr_t>(cam) & 15) == 0) {
+        const float4* c4 = reinterpret_cast<const float4*>(cam);
+        c0 = __ldg(c4);
+        c1 = __ldg(c4 + 1);
+        c2 = __ldg(c4 + 2);
+        c3 = __ldg(c4 + 3);
+    } else {
+        c0 = make_float4(__ldg(cam), __ldg(cam + 1), __ldg(cam + 2), __ldg(cam + 3));
+        c1 = make_float4(__ldg(cam + 4), __ldg(cam + 5), __ldg(cam + 6), __ldg(cam + 7));
+        c2 = make_float4(__ldg(cam + 8), __ldg(cam + 9), __ldg(cam + 10), __ldg(cam + 11));
+        c3 = make_float4(__ldg(cam + 12), __ldg(cam + 13), __ldg(cam + 14), __ldg(cam + 15));
+    }
+    const float fx = c0.x, fy = c0.y, cx = c0.z, cy = c0.w;
+    const float r00 = c1.x, r01 = c1.y, r02 = c1.z;
+    const float r10 = c1.w, r11 = c2.x, r12 = c2.y;
+    const float r20 = c2.z, r21 = c2.w, r22 = c3.x;
+    const float t0 = c3.y, t1 = c3.z, t2 = c3.w;
     const float x0 = fmaf(r00, p0, fmaf(r01, p1, fmaf(r02, p2, t0)));
     const float x1 = fmaf(r10, p0, fmaf(r11, p1, fmaf(r12, p2, t1)));
     const float x2 = fmaf(r20, p0, fmaf(r21, p1, fmaf(r22, p2, t2)));
