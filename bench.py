@@ -113,14 +113,14 @@ def alu_peak(reps=5):
 # sources it was taken on: the first 12 hex digits of the SHA-256 of every csrc/*.cu and *.cuh file
 # (in name order).  After any source change every kernel reports traffic null until captured again.
 TRAFFIC = {
-    "k_project_batch": (22.74, "point-view (N V)", "e183212cc004", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_select_batch": (32.64, "point-view (N V)", "e183212cc004", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_refine_short_batch": (68.18, "accepted point-view", "e183212cc004", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_argmin_batch": (76.36, "fallback point-view", "e183212cc004", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_refine_batch": (115.03, "fallback point-view", "e183212cc004", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_project": (35.20, "point-view (N V)", "e183212cc004", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
-    "k_argmin": (19.54, "point-view in V_i", "e183212cc004", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
-    "k_refine": (20.62, "point-view in V_i", "e183212cc004", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_project_batch": (22.70, "point-view (N V)", "f2f60ee143e1", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_select_batch": (32.77, "point-view (N V)", "f2f60ee143e1", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_refine_short_batch": (74.39, "accepted point-view", "f2f60ee143e1", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_argmin_batch": (76.27, "fallback point-view", "f2f60ee143e1", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_refine_batch": (148.83, "fallback point-view", "f2f60ee143e1", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_project": (35.53, "point-view (N V)", "f2f60ee143e1", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_argmin": (19.54, "point-view in V_i", "f2f60ee143e1", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_refine": (20.66, "point-view in V_i", "f2f60ee143e1", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
 }
 
 
