@@ -7,10 +7,11 @@ Default workload (serving16): the learned + batched form against the plain form 
 of 16 synthetic scenes (50k-1M points, 16-64 views, 512x512 to 1920x1080 maps, H = 64, k = 8,
 T = 8).  One step = one fusion of every point of every scene: for the learned + batched form, one
 replay of the batch's CUDA graph (per-stage persistent launches over all scenes: constants,
-projection + gather, features, proposal network, proposal cost with fallback selection and short
-refinement, argmin and refinement of the fallback points); for the plain form, the plain fusion of
-the scenes one after another.  The proposal network is trained on the GPU first (library kernels, four scenes shaped like
-the full workload) and its fallback threshold calibrated on a training scene.
+projection + gather (which also writes the features' view part), the features' position part,
+proposal network, proposal cost with fallback selection and short refinement, argmin and
+refinement of the fallback points); for the plain form, the plain fusion of the scenes one after
+another.  The proposal network is trained on the GPU first (library kernels, four scenes shaped like
+the full workload) and its fallback threshold calibrated on eight held-out serving-shaped scenes.
 
 --workload full|mid|tiny: the plain fusion of one resident scene (full: 1,000,000 points, 64 views
 of 1920x1080).
@@ -738,16 +739,17 @@ def stage_rooflines(kt, ms_step, scenes, st, T_short):
     k, H, T = 8, 64, 8
     ca, cr = s8d_ops(k)
     Ntot = sum(sc["N"] for sc in scenes)
-    proj_bytes = sum((12 + 4 * k + sc["V"] * (4 + sc["conf"].itemsize) + 20) * sc["N"] for sc in scenes)
-    feat_bytes = sum((16 * (4 + sc["conf"].itemsize) + 12 + 128) * sc["N"] for sc in scenes)
+    # the learned path's projection also writes the features' view part (96 B per point)
+    proj_bytes = sum((12 + 4 * k + sc["V"] * (4 + sc["conf"].itemsize) + 20 + 96) * sc["N"] for sc in scenes)
+    feat_bytes = sum((12 + 32) * sc["N"] for sc in scenes)
     pv, fpv, apv = st["point_views"], st["fallback_point_views"], st["accepted_point_views"]
     units = {"k_argmin_batch": fpv, "k_refine_batch": fpv, "k_refine_short_batch": apv, "k_select_batch": pv,
              "k_project_batch": pv}
     ip = issued_per_dir_view(k)
     work = {
         "k_project_batch": ("hbm", proj_bytes, "12 + 4k + V (4 + conf bytes) + 20 B per point (the path's "
-                            "algorithmic bytes)", None),
-        "k_features_batch": ("hbm", feat_bytes, "16 x (4 + conf bytes) B gathered + 12 B in + 128 B out per point", None),
+                            "algorithmic bytes) + 96 B of features (their view part) per point", None),
+        "k_featpos_batch": ("hbm", feat_bytes, "12 B in + 32 B out per point (the features' position part)", None),
         "k_mlp": ("tensor", MLP_FLOP_PER_POINT * Ntot, f"{MLP_FLOP_PER_POINT} FLOP per point (51-256-256-3)", None),
         "k_select_batch": ("alu", ca * pv, f"{ca} FP32 ops per (point, view) for the proposal's cost ({pv} point-views)",
                            pv * ip),
@@ -1075,7 +1077,7 @@ def run_learned(args):
     # per-stage rooflines from the exact work of this scene (the same units as the batched line)
     st = {"point_views": point_views, "fallback_point_views": lw["fallback_point_views"],
           "accepted_point_views": lw["accepted_point_views"]}
-    names = {"k_project": "k_project_batch", "k_features": "k_features_batch", "k_mlp": "k_mlp",
+    names = {"k_project": "k_project_batch", "k_featpos": "k_featpos_batch", "k_mlp": "k_mlp",
              "k_select": "k_select_batch", "k_refine_short": "k_refine_short_batch",
              "k_argmin_fallback": "k_argmin_batch", "k_refine_fallback": "k_refine_batch"}
     kt_b = {names[n_]: v for n_, v in kt.items() if n_ in names}

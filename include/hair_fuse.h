@@ -320,6 +320,13 @@ int hair_fuse_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, i
 int hair_fuse_gemm_bf16_bounded(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K,
                                 unsigned long long wait_ns, void* cuda_stream);
 
+/* The GELU that the network's inference epilogues apply, y[i] = gelu(x[i]) for n FP32 values
+ * (device pointers, n >= 0; x and y may be the same array), asynchronous on cuda_stream; for
+ * testing.  gelu(x) = x Phi(x) from a polynomial on x clamped to [-5, 5]; |gelu(x) - x Phi(x)| <=
+ * 4.1e-7 |x| for finite x (NaN propagates).  The paper has no counterpart (the network is not in
+ * it).  Returns HF_ERR_INVALID_ARG for n < 0 or a NULL pointer with n > 0. */
+int hair_fuse_gelu_eval(const float* x, float* y, long long n, void* cuda_stream);
+
 /* ------------------------------------------------------------------------------------------------
  * Learned proposal network.  The paper has no counterpart: a small MLP maps per-point multi-view
  * orientation features to an initial direction that a short refinement finishes, replacing most of
@@ -328,7 +335,8 @@ int hair_fuse_gemm_bf16_bounded(const uint16_t* A, const uint16_t* B, float* C, 
  *  features x (51, zero-padded to 64, bf16): for the 16 views v_m = floor(m V / 16),
  *    (sin 2 theta, cos 2 theta, C) at the point's pixel (zeros outside the view), then
  *    (p - centre) / half_extent of the points' bounding box (half_extent = largest half side);
- *  network: 64 -> 256 -> 256 -> 3, GELU (erf form) on both hidden layers, BF16 operands, FP32
+ *  network: 64 -> 256 -> 256 -> 3, GELU x Phi(x) on both hidden layers (training: erff;
+ *    inference: the polynomial of hair_fuse_gelu_eval), BF16 operands, FP32
  *    accumulation and FP32 master weights; proposal = y / |y|;
  *  loss per sample 1 - (y_hat . t)^2 (sign-invariant), mean over the batch; Adam (0.9, 0.999, 1e-8).
  *  Parameter vector (f32, hair_fuse_mlp_param_count() entries): W1 [256 x 64] (columns 51..63 zero),

@@ -86,6 +86,7 @@ _SIGS = {
     "hair_fuse_fibonacci_hemisphere": ([_i, _vp], _i),
     "hair_fuse_gemm_bf16": ([_vp, _vp, _vp, _i, _i, _i, _vp], _i),
     "hair_fuse_gemm_bf16_bounded": ([_vp, _vp, _vp, _i, _i, _i, ctypes.c_ulonglong, _vp], _i),
+    "hair_fuse_gelu_eval": ([_vp, _vp, _ll, _vp], _i),
     "hair_fuse_fail_alloc_after": ([_i], _i),
     "hair_fuse_sync": ([_vp], _i),
     "hair_fuse_profile": ([_vp, _i], _i),
@@ -160,6 +161,7 @@ def gabor_bank(**kw):
 hair_fuse_fibonacci_hemisphere = _lib.hair_fuse_fibonacci_hemisphere
 hair_fuse_gemm_bf16 = _lib.hair_fuse_gemm_bf16
 hair_fuse_gemm_bf16_bounded = _lib.hair_fuse_gemm_bf16_bounded
+hair_fuse_gelu_eval = _lib.hair_fuse_gelu_eval
 hair_fuse_fail_alloc_after = _lib.hair_fuse_fail_alloc_after
 hair_fuse_sync = _lib.hair_fuse_sync
 hair_fuse_profile = _lib.hair_fuse_profile
@@ -278,6 +280,17 @@ def gemm_bf16(a, b, out=None, stream=None):
     if out is None:
         out = torch.empty((M, N), dtype=torch.float32, device=a.device)
     _check(hair_fuse_gemm_bf16(a.data_ptr(), b.data_ptr(), out.data_ptr(), M, N, K,
+                               current_stream_handle() if stream is None else stream))
+    return out
+
+
+def gelu_eval(x, out=None, stream=None):
+    """The network's inference GELU on a CUDA float32 tensor (asynchronous on the stream)."""
+    import torch
+    assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+    if out is None:
+        out = torch.empty_like(x)
+    _check(hair_fuse_gelu_eval(x.data_ptr(), out.data_ptr(), x.numel(),
                                current_stream_handle() if stream is None else stream))
     return out
 

@@ -27,7 +27,7 @@ namespace {
 // stages of a run; the refinement stages run one launch per lane class (a point per thread, or 4, 8,
 // 16, 32 lanes per point), each with its own item counter
 enum { ST_PROJECT, ST_FEATURES, ST_SELECT, ST_SHORT, ST_ARGMIN, ST_MAIN, ST_MLP, ST_COUNT };
-const char* const kStageName[ST_COUNT] = {"k_project_batch", "k_features_batch", "k_select_batch", "k_refine_short_batch",
+const char* const kStageName[ST_COUNT] = {"k_project_batch", "k_featpos_batch", "k_select_batch", "k_refine_short_batch",
                                           "k_argmin_batch", "k_refine_batch", "k_mlp"};
 constexpr int kClasses = 5;   // a point per thread (L = 0), then 4, 8, 16, 32 lanes per point
 int class_of(int L) { return L == 0 ? 0 : L <= 4 ? 1 : L <= 8 ? 2 : L <= 16 ? 3 : 4; }
@@ -175,10 +175,9 @@ int configure(hf_batch* b) {
         A.proj[p] = ProjectArgs{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh,
                                 (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0,
                                 c->cfg.top_k_views, (float2*)c->samp.p, (float2*)c->ab.p, (unsigned long long*)c->vmask.p, work + p,
-                                learned ? box + 6 * p : nullptr, (const float2*)c->amap.p};
-        A.feat[p] = FeatArgs{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh,
-                             (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, nullptr,
-                             b->x + (size_t)s.off * 64, box + 6 * p, (const float2*)c->amap.p};
+                                learned ? box + 6 * p : nullptr, (const float2*)c->amap.p,
+                                learned ? b->x + (size_t)s.off * 64 : nullptr};
+        A.feat[p] = FeatArgs{(const float*)c->pts.p, N, nullptr, b->x + (size_t)s.off * 64, box + 6 * p};
         CostArgs m = hf_cost_args(c);
         m.dir_out = s.dir;
         m.cost_out = s.cost;
@@ -241,8 +240,8 @@ cudaError_t launch_stage(hf_batch* b, int stage) {
     cudaStream_t s = b->stream;
     ArgBlock* A = b->args;
     switch (stage) {
-        case ST_PROJECT: return hf_launch_project_batch(A->proj, ctl_for(b, ST_PROJECT, -1), s);
-        case ST_FEATURES: return hf_launch_features_batch(A->feat, ctl_for(b, ST_FEATURES, -1), s);
+        case ST_PROJECT: return hf_launch_project_batch(A->proj, ctl_for(b, ST_PROJECT, -1), b->mlp != nullptr, s);
+        case ST_FEATURES: return hf_launch_featpos_batch(A->feat, ctl_for(b, ST_FEATURES, -1), s);
         case ST_MLP:
             return hf_mlp_infer_rows(b->mlp, b->x, b->total, b->h1, b->prop, reinterpret_cast<uint32_t*>(b->ctl + kErrOff), s);
         case ST_SELECT: return hf_launch_select_batch(A->sel, ctl_for(b, ST_SELECT, -1), b->kp, s);

@@ -17,6 +17,8 @@
 
 #include "hf_gemm.cuh"
 #include "hf_internal.cuh"
+#include <algorithm>
+
 #include "hf_tc.cuh"
 
 using namespace hf_tc;
@@ -28,26 +30,7 @@ constexpr uint32_t kATileBytes = 128 * 128;   // 128 rows x 64 bf16
 
 __device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
-// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26: for z >= 0,
-// erf z = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-z^2), t = 1 / (1 + p z), with
-// |error| <= 1.5e-7; odd in z.  Hardware reciprocal and exponential (about 1e-6 more).  Used by
-// the inference epilogues, where the result is rounded to bf16 (relative spacing 3.9e-3).
-__device__ __forceinline__ float erf_as(float x) {
-    const float z = fabsf(x);
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
-    float p = fmaf(1.061405429f, t, -1.453152027f);
-    p = fmaf(p, t, 1.421413741f);
-    p = fmaf(p, t, -0.284496736f);
-    p = fmaf(p, t, 0.254829592f);
-    const float r = fmaf(-p * t, __expf(-z * z), 1.0f);
-    return copysignf(r, x);
-}
-
-__device__ __forceinline__ float gelu_as(float x) { return 0.5f * x * (1.0f + erf_as(x * 0.70710678118654752f)); }
-
-// The same GELU for two values at once: the scalings, the polynomial and the products as packed
-// FP32 pairs (each lane rounded like the scalar instruction), the reciprocal, the exponential and
-// the sign per value.  The polynomial is evaluated with negated coefficients, so q = -p exactly.
+// FP32 pairs: packed fma / mul / add (each lane rounded like the scalar instruction).
 typedef unsigned long long g2_t;
 __device__ __forceinline__ g2_t g2(float a, float b) {
     g2_t r;
@@ -70,25 +53,45 @@ __device__ __forceinline__ g2_t g2add(g2_t a, g2_t b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
-__device__ __forceinline__ void gelu_as2(float xa, float xb, float& ga, float& gb) {
-    const g2_t X = g2(xa, xb);
-    float s0, s1;
-    g2u(g2mul(X, g2(0.70710678118654752f, 0.70710678118654752f)), s0, s1);
-    const float z0 = fabsf(s0), z1 = fabsf(s1);
-    const g2_t Z = g2(z0, z1);
-    float u0, u1;
-    g2u(g2fma(g2(0.3275911f, 0.3275911f), Z, g2(1.0f, 1.0f)), u0, u1);
-    const g2_t T = g2(__fdividef(1.0f, u0), __fdividef(1.0f, u1));
-    g2_t Q = g2fma(g2(-1.061405429f, -1.061405429f), T, g2(1.453152027f, 1.453152027f));
-    Q = g2fma(Q, T, g2(-1.421413741f, -1.421413741f));
-    Q = g2fma(Q, T, g2(0.284496736f, 0.284496736f));
-    Q = g2fma(Q, T, g2(-0.254829592f, -0.254829592f));
-    float e0, e1;
-    g2u(g2mul(g2(-z0, -z1), Z), e0, e1);
-    float r0, r1;
-    g2u(g2fma(g2mul(Q, T), g2(__expf(e0), __expf(e1)), g2(1.0f, 1.0f)), r0, r1);
-    const g2_t ERF = g2(copysignf(r0, s0), copysignf(r1, s1));
-    g2u(g2mul(g2mul(g2(0.5f, 0.5f), X), g2add(g2(1.0f, 1.0f), ERF)), ga, gb);
+__device__ __forceinline__ g2_t g2s(float a) { return g2(a, a); }
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {   // clamped to [0, 1]
+    float d;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// GELU of the inference epilogues: x Phi(x), Phi the standard normal CDF, from a polynomial on the
+// clamped input.  t = sat(x / 10 + 1/2) clamps x to [-5, 5] (1 - Phi(5) = 2.9e-7), w8 = 8 t - 4
+// (= 4 x / 5 there), q = w8^2 - 8 in [-8, 8], Phi = 1/2 + w8 R(q) with R of degree 12, fitted by
+// gen_gelu_poly.py (Lawson's reweighted least squares, coefficients rounded to FP32).  For every
+// FP32 x, |gelu_poly(x) - x Phi(x)| <= 4.1e-7 |x| (the generator's FP32 emulation of this exact
+// sequence over a dense sweep, against FP64 erf): far below the bf16 rounding that follows (relative spacing
+// 3.9e-3).  Fused multiply-adds only, no special-function unit; two values per packed instruction.
+__device__ constexpr float kGeluC[13] = {
+    1.767047942e-01f,  -1.098382473e-02f, 1.006262843e-03f,  -9.872522060e-05f, 9.593048162e-06f,
+    -8.886037790e-07f, 7.842153593e-08f,  -6.620918480e-09f, 4.703698542e-10f,  -2.552603615e-11f,
+    2.115369728e-12f,  -2.318493704e-13f, 1.046213846e-14f};
+__device__ __forceinline__ g2_t gelu_poly2(g2_t X) {
+    float xa, xb;
+    g2u(X, xa, xb);
+    const g2_t T = g2(fma_sat(xa, 0.1f, 0.5f), fma_sat(xb, 0.1f, 0.5f));
+    const g2_t W = g2fma(T, g2s(8.0f), g2s(-4.0f));
+    const g2_t Q = g2fma(W, W, g2s(-8.0f));
+    g2_t R = g2fma(g2s(kGeluC[12]), Q, g2s(kGeluC[11]));
+#pragma unroll
+    for (int j = 10; j >= 0; --j) R = g2fma(R, Q, g2s(kGeluC[j]));
+    return g2mul(X, g2fma(W, R, g2s(0.5f)));
+}
+__device__ __forceinline__ float gelu_poly(float x) {
+    float a, b;
+    g2u(gelu_poly2(g2(x, x)), a, b);
+    return a;
+}
+// two FP32 values rounded to bf16 (RNE) and packed, the first in the low half
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -115,6 +118,20 @@ __device__ __forceinline__ void st_bf16x16(uint16_t* dst, const uint16_t* h, boo
     } else {
 #pragma unroll
         for (int q = 0; q < 16; ++q) dst[q] = h[q];
+    }
+}
+
+__device__ __forceinline__ void st_bf16x16w(uint16_t* dst, const uint32_t* w, bool vec) {
+    if (vec) {
+        uint4* d4 = reinterpret_cast<uint4*>(dst);
+        d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            dst[2 * q] = (uint16_t)(w[q] & 0xffffu);
+            dst[2 * q + 1] = (uint16_t)(w[q] >> 16);
+        }
     }
 }
 
@@ -270,12 +287,12 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
             } else if constexpr (EPI == EPI_GELU) {
                 uint16_t h[16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) h[q] = bf16_bits(gelu_as(v[q] + consts[c0 + q]));
+                for (int q = 0; q < 16; ++q) h[q] = bf16_bits(gelu_poly(v[q] + consts[c0 + q]));
                 st_bf16x16(g.H + (size_t)row * g.ldh + n, h, vec);
             } else {   // EPI_HEAD: h2 = bf16(gelu(z2)), y = W3 h2 (FP32, in column order within each half)
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const float h = bf16_round(gelu_as(v[q] + consts[c0 + q]));
+                    const float h = bf16_round(gelu_poly(v[q] + consts[c0 + q]));
                     y0 = fmaf(consts[BN + n + q], h, y0);
                     y1 = fmaf(consts[BN + 256 + n + q], h, y1);
                     y2 = fmaf(consts[BN + 512 + n + q], h, y2);
@@ -469,7 +486,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_gemm_persist(const __grid_cons
             const int row = t * 128 + lrow;
             const bool wr = row < g.M;
             const int cbase = half * 128;
-            float y0 = 0.0f, y1 = 0.0f, y2 = 0.0f;
+            g2_t Y0 = g2s(0.0f), Y1 = g2s(0.0f), Y2 = g2s(0.0f);
             // the next 16 columns are in flight from tensor memory while these are processed
             uint32_t nxt[16];
             tmem_ld16_issue(tl, nxt);
@@ -482,27 +499,30 @@ __global__ void __launch_bounds__(kPThreads, 1) k_gemm_persist(const __grid_cons
                 if (c0 + 16 < 128) tmem_ld16_issue(tl + c0 + 16, nxt);
                 const int n = cbase + c0;
                 if constexpr (EPI == EPI_GELU) {
-                    uint16_t h[16];
+                    uint32_t w[8];
 #pragma unroll
                     for (int q = 0; q < 16; q += 2) {
+                        const float2 b = *reinterpret_cast<const float2*>(consts + n + q);
                         float ga, gb;
-                        gelu_as2(v[q] + consts[n + q], v[q + 1] + consts[n + q + 1], ga, gb);
-                        h[q] = bf16_bits(ga);
-                        h[q + 1] = bf16_bits(gb);
+                        g2u(gelu_poly2(g2add(g2(v[q], v[q + 1]), g2(b.x, b.y))), ga, gb);
+                        w[q >> 1] = bf16x2_bits(ga, gb);
                     }
-                    if (wr) st_bf16x16(g.H + (size_t)row * g.ldh + n, h, vec);
+                    if (wr) st_bf16x16w(g.H + (size_t)row * g.ldh + n, w, vec);
                 } else {
+                    // packed partial sums over the even and the odd columns
 #pragma unroll
                     for (int q = 0; q < 16; q += 2) {
+                        const float2 b = *reinterpret_cast<const float2*>(consts + n + q);
                         float ga, gb;
-                        gelu_as2(v[q] + consts[n + q], v[q + 1] + consts[n + q + 1], ga, gb);
-                        const float h0 = bf16_round(ga), h1 = bf16_round(gb);
-                        y0 = fmaf(consts[256 + n + q], h0, y0);
-                        y1 = fmaf(consts[512 + n + q], h0, y1);
-                        y2 = fmaf(consts[768 + n + q], h0, y2);
-                        y0 = fmaf(consts[256 + n + q + 1], h1, y0);
-                        y1 = fmaf(consts[512 + n + q + 1], h1, y1);
-                        y2 = fmaf(consts[768 + n + q + 1], h1, y2);
+                        g2u(gelu_poly2(g2add(g2(v[q], v[q + 1]), g2(b.x, b.y))), ga, gb);
+                        const uint32_t hb = bf16x2_bits(ga, gb);
+                        const g2_t H = g2(__uint_as_float(hb << 16), __uint_as_float(hb & 0xffff0000u));
+                        const float2 w0 = *reinterpret_cast<const float2*>(consts + 256 + n + q);
+                        const float2 w1 = *reinterpret_cast<const float2*>(consts + 512 + n + q);
+                        const float2 w2 = *reinterpret_cast<const float2*>(consts + 768 + n + q);
+                        Y0 = g2fma(g2(w0.x, w0.y), H, Y0);
+                        Y1 = g2fma(g2(w1.x, w1.y), H, Y1);
+                        Y2 = g2fma(g2(w2.x, w2.y), H, Y2);
                     }
                 }
                 if (c0 + 16 < 128) tmem_ld_wait(nxt);
@@ -512,6 +532,13 @@ __global__ void __launch_bounds__(kPThreads, 1) k_gemm_persist(const __grid_cons
             __syncwarp();
             if (lane == 0) mbar_arrive(acce + grp);
             if constexpr (EPI == EPI_HEAD) {
+                float y0, y1, y2, o0, o1, o2;
+                g2u(Y0, y0, o0);
+                g2u(Y1, y1, o1);
+                g2u(Y2, y2, o2);
+                y0 += o0;
+                y1 += o1;
+                y2 += o2;
                 if (half == 1) {
                     // hand the partial sums over (once the first half has read the previous ones)
                     if (!mbar_wait(hfree + grp, (uint32_t)((k & 1) ^ 1), kWaitTimeoutNs)) {
@@ -702,7 +729,21 @@ int gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int 
     if (host_err) return hf_set_err(nullptr, HF_ERR_TIMEOUT, "gemm: a bounded device wait expired");
     return HF_OK;
 }
+__global__ void k_gelu_eval(const float* __restrict__ x, float* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = gelu_poly(x[i]);
+}
 }  // namespace
+
+extern "C" int hair_fuse_gelu_eval(const float* x, float* y, long long n, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !y))) return hf_set_err(nullptr, HF_ERR_INVALID_ARG, "need n >= 0 and device x, y");
+    if (n == 0) return HF_OK;
+    const long long blocks = std::min<long long>((n + 255) / 256, 148LL * 16);
+    k_gelu_eval<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, y, n);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return hf_set_err(nullptr, HF_ERR_CUDA, "gelu_eval: %s", cudaGetErrorString(e));
+    return HF_OK;
+}
 
 extern "C" int hair_fuse_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, void* stream) {
     return gemm_bf16(A, B, C, M, N, K, 0, stream);

@@ -130,6 +130,8 @@ struct ProjectArgs {
     unsigned long long* work;   // += number of (point, view) pairs in the view sets
     unsigned* box_keys;         // optional: bounding-box keys lo[3], hi[3] folded in (see hf_launch_bbox_init)
     const float2* amap;         // optional: interleaved (angle, confidence) maps, read instead of angle / conf
+    uint16_t* featx;            // optional: [N x 64] bf16 network features; the projection writes columns
+                                // 0..47, the view part (hf_launch_featpos writes the rest)
 };
 cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s);
 // list[q] = first + q for q < n, *count = n
@@ -205,16 +207,16 @@ cudaError_t hf_launch_eval(const EvalArgs& a, cudaStream_t s);
 cudaError_t hf_launch_fib(int H, float* out, cudaStream_t s);
 
 // learned proposal path
+// The position part of the network features: columns 48..63 of each row of x, (p - centre) /
+// half_extent of the points' bounding box and zero padding.  The view part (columns 0..47) is
+// written by the projection (ProjectArgs::featx) from the samples it gathers anyway.
 struct FeatArgs {
     const float* pts; int N;
-    const float* cams; int V; int W; int H;
-    const float* angle; const void* conf; int conf_f16;
-    const float* box;       // bounding box lo[3], hi[3] (used when box_keys is null)
-    uint16_t* x;            // [N x 64] bf16 features
+    const float* box;           // bounding box lo[3], hi[3] (used when box_keys is null)
+    uint16_t* x;                // [N x 64] bf16 features
     const unsigned* box_keys;   // bounding box as order-preserving keys lo[3], hi[3], or null
-    const float2* amap;         // optional: interleaved (angle, confidence) maps, read instead of angle / conf
 };
-cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s);
+cudaError_t hf_launch_featpos(const FeatArgs& a, cudaStream_t s);
 // (cos, sin) of alpha0 / 2^t for t < T, in double then rounded
 cudaError_t hf_launch_rot(float2* rot, int T, double alpha0, cudaStream_t s);
 cudaError_t hf_launch_check_nbr(const int32_t* nbr, long long n, int N, uint32_t* errw, cudaStream_t s);
@@ -244,8 +246,9 @@ struct BatchReset {
 
 int hf_batch_kp_for(int k);   // patch width instantiated for the batched kernels (4, 9 or 17)
 cudaError_t hf_launch_prep_batch(const PrepArgs* pr, int ns, const BatchReset& r, cudaStream_t s);
-cudaError_t hf_launch_project_batch(const ProjectArgs* pa, const BatchCtl& c, cudaStream_t s);
-cudaError_t hf_launch_features_batch(const FeatArgs* fe, const BatchCtl& c, cudaStream_t s);
+// feat: the scenes' ProjectArgs carry featx (the learned path)
+cudaError_t hf_launch_project_batch(const ProjectArgs* pa, const BatchCtl& c, bool feat, cudaStream_t s);
+cudaError_t hf_launch_featpos_batch(const FeatArgs* fe, const BatchCtl& c, cudaStream_t s);
 // The batched cost kernels (hf_batch_kernels.cu) over the c.ns scenes at fa / la; kp from
 // hf_batch_kp_for(max k); nt threads per CTA (64, 128 or 256).  The refinement takes the scenes
 // that share the lane count L.

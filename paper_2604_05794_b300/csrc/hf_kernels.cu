@@ -117,7 +117,7 @@ __device__ __forceinline__ bool pixel_of(const float* __restrict__ cam, float p0
     return fu >= 0.0f && fu < (float)W && fv >= 0.0f && fv < (float)H;
 }
 
-template <bool TOPK>
+template <bool TOPK, bool FEAT>
 __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
     const int i = blk * kProjectThreads + threadIdx.x;
     if (a.box_keys) {
@@ -144,6 +144,12 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
     int topv[HF_MAX_TOPK];
     int ntop = 0, nset = 0;
     unsigned long long word = 0ull;
+    // the network's view features: slot m (< 16) samples view floor(m V / 16); fm is the next slot
+    // and fvw its view (warp-uniform).  Four slots (12 bf16, 24 bytes) are collected in a 192-bit
+    // shift register fa : fb : fc and written as three 8-byte stores.
+    int fm = 0, fvw = 0;
+    uint16_t* frow = FEAT && a.featx ? a.featx + (size_t)i * 64 : nullptr;
+    unsigned long long fa = 0ull, fb = 0ull, fc = 0ull;
     // views in groups of four: the pixel decisions first, then the four gathers in flight together
     constexpr int G = 4;
     for (int v0 = 0; v0 < a.V; v0 += G) {
@@ -173,6 +179,36 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
             } else {
                 th[q] = __ldg(a.angle + off[q]);
                 C[q] = load_conf(a.conf, a.conf_f16, (size_t)off[q]);
+            }
+        }
+        if (FEAT && frow) {
+            // (sin 2 theta, cos 2 theta, C) of each feature slot whose view is in this group, zeros
+            // when the point projects outside it
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                while (fm < 16 && fvw == v0 + q) {
+                    uint16_t h0 = 0, h1 = 0, h2 = 0;
+                    if (off[q] >= 0) {
+                        float s2, c2;
+                        sincosf(2.0f * th[q], &s2, &c2);
+                        h0 = __bfloat16_as_ushort(__float2bfloat16_rn(s2));
+                        h1 = __bfloat16_as_ushort(__float2bfloat16_rn(c2));
+                        h2 = __bfloat16_as_ushort(__float2bfloat16_rn(C[q]));
+                    }
+                    const unsigned long long t = (unsigned long long)h0 | ((unsigned long long)h1 << 16) |
+                                                 ((unsigned long long)h2 << 32);
+                    fa = (fa >> 48) | (fb << 16);
+                    fb = (fb >> 48) | (fc << 16);
+                    fc = (fc >> 48) | (t << 16);
+                    if ((fm & 3) == 3) {   // slots fm - 3 .. fm: columns 3 (fm - 3) .. 3 fm + 2
+                        unsigned long long* dst = reinterpret_cast<unsigned long long*>(frow + 3 * (fm - 3));
+                        dst[0] = fa;
+                        dst[1] = fb;
+                        dst[2] = fc;
+                    }
+                    ++fm;
+                    fvw = (fm * a.V) >> 4;
+                }
             }
         }
         float2 svq[G], rq[G];   // this group's samples and ratios (a view past V: 0 and NaN)
@@ -238,9 +274,9 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
     if ((threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(a.work, (unsigned long long)tot);
 }
 
-template <bool TOPK>
+template <bool TOPK, bool FEAT>
 __global__ void __launch_bounds__(kProjectThreads) k_project(ProjectArgs a) {
-    project_tile<TOPK>(a, blockIdx.x);
+    project_tile<TOPK, FEAT>(a, blockIdx.x);
 }
 
 __global__ void k_iota(int32_t* list, int* count, int first, int n) {
@@ -363,75 +399,33 @@ __global__ void __launch_bounds__(kCostThreads) k_eval(EvalArgs e) {
 // Features of one point for the proposal network: for the 16 views v_m = floor(m V / 16),
 // (sin 2 theta, cos 2 theta, C) at the point's pixel (zeros when it projects outside), then the
 // position (p - centre) / half_extent of the point cloud's bounding box; bf16, zero-padded to 64.
+// The view part comes from the projection (project_tile with featx set), which has the samples in
+// registers; the position part needs the complete bounding box, which the projection folds, so it
+// is written here, one 32-byte row tail per point.
 constexpr int kFeatThreads = 128;
 
-__device__ __forceinline__ void features_tile(const FeatArgs& a, int blk) {
+__device__ __forceinline__ void featpos_tile(const FeatArgs& a, int blk) {
     const int i = blk * kFeatThreads + threadIdx.x;
     if (i >= a.N) return;
-    const float p0 = a.pts[3 * i], p1 = a.pts[3 * i + 1], p2 = a.pts[3 * i + 2];
-    const size_t npx = (size_t)a.W * a.H;
-    uint16_t f[64];
-#pragma unroll
-    for (int q = 0; q < 64; ++q) f[q] = 0;
-    // all 16 pixel decisions first, then the 16 gathers in flight together, then the features
-    long long off[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        const int v = (m * a.V) / 16;
-        off[m] = -1;
-        float fu, fv, ra, rb;
-        if (!pixel_of(a.cams + 16 * v, p0, p1, p2, a.W, a.H, fu, fv, ra, rb)) continue;
-        off[m] = (long long)((size_t)v * npx + (size_t)fv * a.W + (size_t)fu);
-    }
-    float th[16], C[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        th[m] = 0.0f;
-        C[m] = 0.0f;
-        if (off[m] < 0) continue;
-        if (a.amap) {
-            const float2 t = __ldg(a.amap + off[m]);
-            th[m] = t.x;
-            C[m] = t.y;
-        } else {
-            th[m] = a.angle[off[m]];
-            C[m] = load_conf(a.conf, a.conf_f16, (size_t)off[m]);
-        }
-    }
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        if (off[m] < 0) continue;
-        float s2, c2;
-        sincosf(2.0f * th[m], &s2, &c2);
-        f[3 * m] = __bfloat16_as_ushort(__float2bfloat16_rn(s2));
-        f[3 * m + 1] = __bfloat16_as_ushort(__float2bfloat16_rn(c2));
-        f[3 * m + 2] = __bfloat16_as_ushort(__float2bfloat16_rn(C[m]));
-    }
+    const float pc[3] = {a.pts[3 * i], a.pts[3 * i + 1], a.pts[3 * i + 2]};
     float b[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) b[q] = a.box_keys ? fval(a.box_keys[q]) : a.box[q];
     float half = 0.5f * fmaxf(fmaxf(b[3] - b[0], b[4] - b[1]), b[5] - b[2]);
     if (!(half > 0.0f)) half = 1.0f;
-    const float pc[3] = {p0, p1, p2};
+    uint32_t f[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const float c = 0.5f * (b[q] + b[3 + q]);
         const float x = isfinite(pc[q]) ? (pc[q] - c) / half : 0.0f;
-        f[48 + q] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+        f[q] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
     }
-    uint4* dst = reinterpret_cast<uint4*>(a.x + (size_t)i * 64);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        uint4 w;
-        w.x = f[8 * q] | ((uint32_t)f[8 * q + 1] << 16);
-        w.y = f[8 * q + 2] | ((uint32_t)f[8 * q + 3] << 16);
-        w.z = f[8 * q + 4] | ((uint32_t)f[8 * q + 5] << 16);
-        w.w = f[8 * q + 6] | ((uint32_t)f[8 * q + 7] << 16);
-        dst[q] = w;
-    }
+    uint4* dst = reinterpret_cast<uint4*>(a.x + (size_t)i * 64 + 48);
+    dst[0] = make_uint4(f[0] | (f[1] << 16), f[2], 0u, 0u);
+    dst[1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-__global__ void __launch_bounds__(kFeatThreads) k_features(FeatArgs a) { features_tile(a, blockIdx.x); }
+__global__ void __launch_bounds__(kFeatThreads) k_featpos(FeatArgs a) { featpos_tile(a, blockIdx.x); }
 
 __global__ void k_rot(float2* rot, int T, double alpha0) {
     const int t = threadIdx.x;
@@ -484,17 +478,18 @@ __global__ void k_order_nbr(int32_t* __restrict__ nbr, int N, int k) {
 // ------------------------------------------------------------------ batched scenes (work loop in hf_batchtiles.cuh)
 using namespace hf_bt;
 
-__global__ void __launch_bounds__(kProjectThreads) k_project_batch(const ProjectArgs* __restrict__ pa, BatchCtl c) {
+template <bool FEAT>
+__global__ void __launch_bounds__(kProjectThreads, 7) k_project_batch(const ProjectArgs* __restrict__ pa, BatchCtl c) {
     batch_tiles(pa, c, [](const ProjectArgs& a) { return (a.N + kProjectThreads - 1) / kProjectThreads; },
                 [](const ProjectArgs& a, int blk) {
-                    if (a.top_k > 0) project_tile<true>(a, blk);
-                    else project_tile<false>(a, blk);
+                    if (a.top_k > 0) project_tile<true, FEAT>(a, blk);
+                    else project_tile<false, FEAT>(a, blk);
                 });
 }
 
-__global__ void __launch_bounds__(kFeatThreads) k_features_batch(const FeatArgs* __restrict__ fe, BatchCtl c) {
+__global__ void __launch_bounds__(kFeatThreads) k_featpos_batch(const FeatArgs* __restrict__ fe, BatchCtl c) {
     batch_tiles(fe, c, [](const FeatArgs& a) { return (a.N + kFeatThreads - 1) / kFeatThreads; },
-                [](const FeatArgs& a, int blk) { features_tile(a, blk); });
+                [](const FeatArgs& a, int blk) { featpos_tile(a, blk); });
 }
 
 // Per-scene constants of every scene (block = scene), the batch's counters cleared, empty bounding
@@ -606,8 +601,14 @@ int hf_cost_lanes(int veff, int k) {
 
 cudaError_t hf_launch_project(const ProjectArgs& a, cudaStream_t s) {
     const dim3 grid((a.N + kProjectThreads - 1) / kProjectThreads), block(kProjectThreads);
-    if (a.top_k > 0) k_project<true><<<grid, block, 0, s>>>(a);
-    else k_project<false><<<grid, block, 0, s>>>(a);
+    // the plain path's instance has no feature code (its registers stay at the plain count)
+    if (a.featx) {
+        if (a.top_k > 0) k_project<true, true><<<grid, block, 0, s>>>(a);
+        else k_project<false, true><<<grid, block, 0, s>>>(a);
+    } else {
+        if (a.top_k > 0) k_project<true, false><<<grid, block, 0, s>>>(a);
+        else k_project<false, false><<<grid, block, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -683,8 +684,8 @@ cudaError_t hf_launch_fib(int H, float* out, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t hf_launch_features(const FeatArgs& a, cudaStream_t s) {
-    k_features<<<(a.N + kFeatThreads - 1) / kFeatThreads, kFeatThreads, 0, s>>>(a);
+cudaError_t hf_launch_featpos(const FeatArgs& a, cudaStream_t s) {
+    k_featpos<<<(a.N + kFeatThreads - 1) / kFeatThreads, kFeatThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -714,16 +715,17 @@ cudaError_t hf_launch_prep_batch(const PrepArgs* pr, int ns, const BatchReset& r
     return cudaGetLastError();
 }
 
-cudaError_t hf_launch_project_batch(const ProjectArgs* pa, const BatchCtl& c, cudaStream_t s) {
-    static int grid = 0;
-    if (!grid) grid = persistent_grid(k_project_batch, kProjectThreads, 0);
-    k_project_batch<<<grid, kProjectThreads, 0, s>>>(pa, c);
+cudaError_t hf_launch_project_batch(const ProjectArgs* pa, const BatchCtl& c, bool feat, cudaStream_t s) {
+    static int grid[2] = {0, 0};
+    if (!grid[feat]) grid[feat] = persistent_grid(feat ? k_project_batch<true> : k_project_batch<false>, kProjectThreads, 0);
+    if (feat) k_project_batch<true><<<grid[1], kProjectThreads, 0, s>>>(pa, c);
+    else k_project_batch<false><<<grid[0], kProjectThreads, 0, s>>>(pa, c);
     return cudaGetLastError();
 }
 
-cudaError_t hf_launch_features_batch(const FeatArgs* fe, const BatchCtl& c, cudaStream_t s) {
+cudaError_t hf_launch_featpos_batch(const FeatArgs* fe, const BatchCtl& c, cudaStream_t s) {
     static int grid = 0;
-    if (!grid) grid = persistent_grid(k_features_batch, kFeatThreads, 0);
-    k_features_batch<<<grid, kFeatThreads, 0, s>>>(fe, c);
+    if (!grid) grid = persistent_grid(k_featpos_batch, kFeatThreads, 0);
+    k_featpos_batch<<<grid, kFeatThreads, 0, s>>>(fe, c);
     return cudaGetLastError();
 }

@@ -425,22 +425,52 @@ int learned_scratch(hf_ctx* c, long long N) {
     if ((rc = hf_ensure(c, c->lmisc, 256 + 64 * 8 + (size_t)N * 8))) return rc;
     return HF_OK;
 }
+
+// The projection's outputs (samples, ratios, view-set masks, work counter) for the current scene.
+int projection_buffers(hf_ctx* c) {
+    const int N = c->N, V = c->V;
+    int rc;
+    if ((rc = hf_ensure(c, c->samp, (size_t)N * hf_view_pairs(V) * sizeof(float4)))) return rc;
+    if ((rc = hf_ensure(c, c->ab, (size_t)N * hf_view_pairs(V) * sizeof(float4)))) return rc;
+    if ((rc = hf_ensure(c, c->vmask, (size_t)N * hf_mask_words(V) * sizeof(unsigned long long)))) return rc;
+    if ((rc = hf_ensure(c, c->work, sizeof(unsigned long long)))) return rc;
+    return HF_OK;
+}
+
+// The projection of the uploaded points with the view part of the features written to x, folding
+// the points into the bounding box at box_keys (which the caller resets); work counts its (point,
+// view) pairs.
+ProjectArgs feature_projection(hf_ctx* c, uint16_t* x, unsigned* box_keys, unsigned long long* work) {
+    return ProjectArgs{(const float*)c->pts.p, c->N, (const float*)c->cams.p, c->V, c->W, c->Hh,
+                       (const float*)c->angle.p, c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, c->cfg.top_k_views,
+                       (float2*)c->samp.p, (float2*)c->ab.p, (unsigned long long*)c->vmask.p, work, box_keys,
+                       (const float2*)c->amap.p, x};
+}
 }  // namespace
 
 extern "C" int hair_fuse_features(hf_ctx* c, uint16_t* x_out, int mem_kind) {
     if (!c || !x_out) return HF_ERR_INVALID_ARG;
     if (c->V <= 0 || c->N <= 0) return hf_set_err(c, HF_ERR_NOT_UPLOADED, "views or points not uploaded");
+    if (mem_kind != HF_HOST && mem_kind != HF_DEVICE) return hf_set_err(c, HF_ERR_INVALID_ARG, "bad mem_kind");
     int rc;
     if ((rc = learned_scratch(c, c->N))) return rc;
-    float* box = (float*)c->lmisc.p;
-    uint16_t* x = mem_kind == HF_HOST ? (uint16_t*)c->feat.p : x_out;
-    cudaError_t e = hf_launch_bbox((const float*)c->pts.p, c->N, box, c->stream);
-    FeatArgs fa{(const float*)c->pts.p, c->N, (const float*)c->cams.p, c->V, c->W, c->Hh, (const float*)c->angle.p,
-                c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, box, x, nullptr, (const float2*)c->amap.p};
-    if (e == cudaSuccess) e = hf_launch_features(fa, c->stream);
-    c->launches += 2;
-    if (e == cudaSuccess && mem_kind == HF_HOST)
-        e = cudaMemcpyAsync(x_out, x, (size_t)c->N * 128, cudaMemcpyDeviceToHost, c->stream);
+    if ((rc = projection_buffers(c))) return rc;
+    // the same kernels as the learned path: the projection (view part, bounding box), then the
+    // position part; its own work counter, so the last fusion's count stays readable
+    char* lm = (char*)c->lmisc.p;
+    unsigned* box_keys = reinterpret_cast<unsigned*>(lm + 32);
+    unsigned long long* work = reinterpret_cast<unsigned long long*>(lm + 88);
+    // the kernels store 8 and 16 bytes at a time: an unaligned device destination gets a copy
+    const bool direct = mem_kind == HF_DEVICE && (reinterpret_cast<uintptr_t>(x_out) & 15) == 0;
+    uint16_t* x = direct ? x_out : (uint16_t*)c->feat.p;
+    cudaError_t e = hf_launch_bbox_init(box_keys, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, 8, c->stream);
+    if (e == cudaSuccess) e = hf_launch_project(feature_projection(c, x, box_keys, work), c->stream);
+    if (e == cudaSuccess) e = hf_launch_featpos(FeatArgs{(const float*)c->pts.p, c->N, nullptr, x, box_keys}, c->stream);
+    c->launches += 3;
+    if (e == cudaSuccess && !direct)
+        e = cudaMemcpyAsync(x_out, x, (size_t)c->N * 128, mem_kind == HF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                            c->stream);
     if (e != cudaSuccess) return hf_cuda_err(c, e, "features");
     if (mem_kind == HF_HOST) {
         e = cudaStreamSynchronize(c->stream);
@@ -467,10 +497,7 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     if ((rc = hf_ensure(c, c->rot, (size_t)(T > 0 ? T : 1) * sizeof(float2)))) return rc;
     if ((rc = hf_ensure(c, c->qtab, (size_t)V * hf_hq(H) * sizeof(float4)))) return rc;
     if ((rc = hf_ensure(c, c->best, (size_t)N * sizeof(int32_t)))) return rc;
-    if ((rc = hf_ensure(c, c->samp, (size_t)N * hf_view_pairs(V) * sizeof(float4)))) return rc;
-    if ((rc = hf_ensure(c, c->ab, (size_t)N * hf_view_pairs(V) * sizeof(float4)))) return rc;
-    if ((rc = hf_ensure(c, c->vmask, (size_t)N * hf_mask_words(V) * sizeof(unsigned long long)))) return rc;
-    if ((rc = hf_ensure(c, c->work, sizeof(unsigned long long)))) return rc;
+    if ((rc = projection_buffers(c))) return rc;
     if ((rc = hf_ensure(c, c->outs, (size_t)N * 21))) return rc;
     if ((rc = ensure_h1(m, N))) return rc;
     char* lm = (char*)c->lmisc.p;
@@ -499,15 +526,13 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
         return rc;
     cudaError_t e = cudaMemsetAsync(c->work.p, 0, 8, s);
     if (e != cudaSuccess) return hf_cuda_err(c, e, "clear work counter");
-    // the projection also folds the points into the bounding box the features are normalised by
-    ProjectArgs pa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p,
-                   c->conf.p, c->conf_dtype == HF_F16 ? 1 : 0, c->cfg.top_k_views, (float2*)c->samp.p,
-                   (float2*)c->ab.p, (unsigned long long*)c->vmask.p, (unsigned long long*)c->work.p, box_keys, (const float2*)c->amap.p};
+    // the projection also writes the view part of the features and folds the points into the
+    // bounding box their position part is normalised by
+    const ProjectArgs pa = feature_projection(c, (uint16_t*)c->feat.p, box_keys, (unsigned long long*)c->work.p);
     if ((rc = run_launch(c, "k_project", [&] { return hf_launch_project(pa, s); }))) return rc;
-    // proposal: features -> network
-    FeatArgs fa{(const float*)c->pts.p, N, (const float*)c->cams.p, V, c->W, c->Hh, (const float*)c->angle.p, c->conf.p,
-                c->conf_dtype == HF_F16 ? 1 : 0, nullptr, (uint16_t*)c->feat.p, box_keys, (const float2*)c->amap.p};
-    if ((rc = run_launch(c, "k_features", [&] { return hf_launch_features(fa, s); }))) return rc;
+    // proposal: the features' position part -> network
+    const FeatArgs fa{(const float*)c->pts.p, N, nullptr, (uint16_t*)c->feat.p, box_keys};
+    if ((rc = run_launch(c, "k_featpos", [&] { return hf_launch_featpos(fa, s); }))) return rc;
     if ((rc = run_launch(c, "k_mlp", [&] {
              return hf_mlp_infer(m->d, m->P, (const uint16_t*)c->feat.p, N, m->h1, (float*)c->prop.p,
                                  (uint32_t*)c->errw.p, s);
