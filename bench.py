@@ -114,14 +114,16 @@ def alu_peak(reps=5):
 # sources it was taken on: the first 12 hex digits of the SHA-256 of every csrc/*.cu and *.cuh file
 # (in name order).  After any source change every kernel reports traffic null until captured again.
 TRAFFIC = {
-    "k_project_batch": (22.70, "point-view (N V)", "f2f60ee143e1", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_select_batch": (32.77, "point-view (N V)", "f2f60ee143e1", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_refine_short_batch": (74.39, "accepted point-view", "f2f60ee143e1", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_argmin_batch": (76.27, "fallback point-view", "f2f60ee143e1", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_refine_batch": (148.83, "fallback point-view", "f2f60ee143e1", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_project": (35.53, "point-view (N V)", "f2f60ee143e1", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
-    "k_argmin": (19.54, "point-view in V_i", "f2f60ee143e1", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
-    "k_refine": (20.66, "point-view in V_i", "f2f60ee143e1", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_project_batch": (28.68, "point-view (N V)", "1b1cf28ec881", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_featpos_batch": (37.94, "point", "1b1cf28ec881", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_mlp": (137.60, "point (feature row)", "1b1cf28ec881", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_select_batch": (32.80, "point-view (N V)", "1b1cf28ec881", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_refine_short_batch": (74.39, "accepted point-view", "1b1cf28ec881", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_argmin_batch": (76.16, "fallback point-view", "1b1cf28ec881", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_refine_batch": (147.83, "fallback point-view", "1b1cf28ec881", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_project": (35.70, "point-view (N V)", "1b1cf28ec881", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_argmin": (19.53, "point-view in V_i", "1b1cf28ec881", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_refine": (20.67, "point-view in V_i", "1b1cf28ec881", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
 }
 
 
@@ -604,6 +606,10 @@ CALIB_SEED, CALIB_SCENES = 300, 8          # held-out serving-shaped scenes for 
 CALIB_MEDIAN, CALIB_P95 = 1.8, 7.0         # their accuracy bounds against the plain fusion (targets 2 / 8 deg)
 TRAIN_SEEDS, TRAIN_SAMPLES, TRAIN_STEPS, TRAIN_BATCH, TRAIN_LR = (100, 101, 102, 103), 500_000, 20000, 8192, 1e-3
 MLP_FLOP_PER_POINT = 2 * (51 * 256 + 256 * 256 + 256 * 3)   # forward, unpadded inputs
+# FP32 operations of the network's epilogue per row (CUDA cores, not tensor cores): per hidden unit
+# the bias add, the clamped scaling, w8 = 8 t - 4, q = w8^2 - 8, 12 polynomial steps, Phi and the
+# product x Phi (18), in both hidden layers, plus the head's 3 fused multiply-adds in layer 2
+MLP_EPILOGUE_OPS_PER_POINT = 256 * (18 + 18 + 3)
 
 
 def serving_scenes(first_seed, pick="16"):
@@ -780,6 +786,13 @@ def stage_rooflines(kt, ms_step, scenes, st, T_short):
             out[name]["peak_rates_ops_per_s"] = ap["rates_ops_per_s"]
             out[name]["builder_count"] = {"instr_per_dir_view": ip, "achieved_instr_per_s": issued / sec,
                                           "frac_of_ffma_issue": issued / sec / ap["rates_ops_per_s"]["ffma"]}
+        if name == "k_mlp":
+            # what binds the network: its GELU / head epilogue on the FP32 pipe
+            ops = MLP_EPILOGUE_OPS_PER_POINT * Ntot / sec
+            out[name]["epilogue_fp32"] = {"ops_per_point": MLP_EPILOGUE_OPS_PER_POINT, "achieved_ops_per_s": ops,
+                                          "peak_ops_per_s": ap["rates_ops_per_s"]["ffma"],
+                                          "frac_of_ffma": ops / ap["rates_ops_per_s"]["ffma"],
+                                          "peak_source": "measured: hair_fuse_issue_rate HF_ISSUE_FFMA"}
     return out
 
 

@@ -105,7 +105,6 @@ struct hf_batch {
     ArgBlock* args_h = nullptr; // pinned host copy
     uint16_t* x = nullptr;
     float* prop = nullptr;
-    uint16_t* h1 = nullptr;
     int32_t* list = nullptr;       // fallback points, per scene from its row offset
     int32_t* acc_list = nullptr;   // accepted proposals, likewise
     cudaGraphExec_t gexec = nullptr;
@@ -243,7 +242,7 @@ cudaError_t launch_stage(hf_batch* b, int stage) {
         case ST_PROJECT: return hf_launch_project_batch(A->proj, ctl_for(b, ST_PROJECT, -1), b->mlp != nullptr, s);
         case ST_FEATURES: return hf_launch_featpos_batch(A->feat, ctl_for(b, ST_FEATURES, -1), s);
         case ST_MLP:
-            return hf_mlp_infer_rows(b->mlp, b->x, b->total, b->h1, b->prop, reinterpret_cast<uint32_t*>(b->ctl + kErrOff), s);
+            return hf_mlp_infer_rows(b->mlp, b->x, b->total, b->prop, reinterpret_cast<uint32_t*>(b->ctl + kErrOff), s);
         case ST_SELECT: return hf_launch_select_batch(A->sel, ctl_for(b, ST_SELECT, -1), b->kp, s);
         case ST_ARGMIN: return hf_launch_argmin_batch(A->main, ctl_for(b, ST_ARGMIN, -1), b->kp, b->nt, s);
         case ST_SHORT: return hf_launch_refine_batch(A->shrt, ctl_for(b, ST_SHORT, 0), b->kp, 0, b->nt, s);
@@ -474,7 +473,6 @@ extern "C" int hair_fuse_batch_create(hf_batch** out, hf_ctx* const* scenes, int
     if (e == cudaSuccess && mlp) {
         e = cudaMalloc(&b->x, (size_t)total * 64 * sizeof(uint16_t));
         if (e == cudaSuccess) e = cudaMalloc(&b->prop, (size_t)total * 3 * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc(&b->h1, (size_t)total * 256 * sizeof(uint16_t));
         if (e == cudaSuccess) e = cudaMalloc(&b->list, (size_t)total * sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMalloc(&b->acc_list, (size_t)total * sizeof(int32_t));
     }
@@ -691,7 +689,6 @@ extern "C" void hair_fuse_batch_destroy(hf_batch* b) {
     if (b->args_h) cudaFreeHost(b->args_h);
     cudaFree(b->x);
     cudaFree(b->prop);
-    cudaFree(b->h1);
     cudaFree(b->list);
     cudaFree(b->acc_list);
     if (b->ev_in) cudaEventDestroy(b->ev_in);

@@ -94,7 +94,6 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
     return d;
 }
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
-__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 __device__ __forceinline__ void st_f32x16(float* dst, const float* v, bool vec) {
     if (vec) {
@@ -118,20 +117,6 @@ __device__ __forceinline__ void st_bf16x16(uint16_t* dst, const uint16_t* h, boo
     } else {
 #pragma unroll
         for (int q = 0; q < 16; ++q) dst[q] = h[q];
-    }
-}
-
-__device__ __forceinline__ void st_bf16x16w(uint16_t* dst, const uint32_t* w, bool vec) {
-    if (vec) {
-        uint4* d4 = reinterpret_cast<uint4*>(dst);
-        d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
-    } else {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            dst[2 * q] = (uint16_t)(w[q] & 0xffffu);
-            dst[2 * q + 1] = (uint16_t)(w[q] >> 16);
-        }
     }
 }
 
@@ -174,8 +159,6 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
     }
     if (g.bias)
         for (int q = threadIdx.x; q < BN; q += blockDim.x) consts[q] = g.bias[n0 + q];
-    if constexpr (EPI == EPI_HEAD)
-        for (int q = threadIdx.x; q < 3 * 256 + 3; q += blockDim.x) consts[BN + q] = q < 768 ? g.w3[q] : g.b3[q - 768];
     fence_before();
     __syncthreads();
     fence_after();
@@ -250,12 +233,9 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
     bool vec = false;   // 16-byte row stores when the destination allows them
     if constexpr (EPI == EPI_STORE || EPI == EPI_PARTIAL)
         vec = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0) && (g.ldc & 3) == 0 && (g.split_stride & 3) == 0;
-    if constexpr (EPI == EPI_GELU)
-        vec = ((reinterpret_cast<uintptr_t>(g.H) & 15) == 0) && (g.ldh & 7) == 0;
     if constexpr (EPI == EPI_GELU_TRAIN)
         vec = ((reinterpret_cast<uintptr_t>(g.H) & 15) == 0) && (g.ldh & 7) == 0 &&
               ((reinterpret_cast<uintptr_t>(g.Z) & 15) == 0) && (g.ldz & 3) == 0;
-    float y0 = 0.0f, y1 = 0.0f, y2 = 0.0f;   // EPI_HEAD accumulators
     if (active) {
 #pragma unroll 1
         for (int c0 = cbeg; c0 < cbeg + kCols; c0 += 16) {
@@ -284,49 +264,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
                 }
                 st_f32x16(g.Z + (size_t)row * g.ldz + n, v, vec);
                 st_bf16x16(g.H + (size_t)row * g.ldh + n, h, vec);
-            } else if constexpr (EPI == EPI_GELU) {
-                uint16_t h[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) h[q] = bf16_bits(gelu_poly(v[q] + consts[c0 + q]));
-                st_bf16x16(g.H + (size_t)row * g.ldh + n, h, vec);
-            } else {   // EPI_HEAD: h2 = bf16(gelu(z2)), y = W3 h2 (FP32, in column order within each half)
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float h = bf16_round(gelu_poly(v[q] + consts[c0 + q]));
-                    y0 = fmaf(consts[BN + n + q], h, y0);
-                    y1 = fmaf(consts[BN + 256 + n + q], h, y1);
-                    y2 = fmaf(consts[BN + 512 + n + q], h, y2);
-                }
             }
-        }
-    }
-    if constexpr (EPI == EPI_HEAD) {
-        // the second column half hands its partial sums to the first through shared memory
-        float* part = consts + BN + 3 * 256 + 4;
-        if (half == 1) {
-            part[3 * lrow] = y0;
-            part[3 * lrow + 1] = y1;
-            part[3 * lrow + 2] = y2;
-        }
-        __syncthreads();
-        if (half == 0 && wr) {
-            y0 += part[3 * lrow] + consts[BN + 768];
-            y1 += part[3 * lrow + 1] + consts[BN + 769];
-            y2 += part[3 * lrow + 2] + consts[BN + 770];
-            const float nn = sqrtf(y0 * y0 + y1 * y1 + y2 * y2);
-            float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
-            if (g.head_raw) {
-                d0 = y0;
-                d1 = y1;
-                d2 = y2;
-            } else if (nn > 0.0f) {
-                d0 = y0 / nn;
-                d1 = y1 / nn;
-                d2 = y2 / nn;
-            }
-            g.dir_out[3 * (size_t)row] = d0;
-            g.dir_out[3 * (size_t)row + 1] = d1;
-            g.dir_out[3 * (size_t)row + 2] = d2;
         }
     }
     fence_before();
@@ -334,55 +272,69 @@ __global__ void __launch_bounds__(256) k_gemm_tn(const __grid_constant__ CUtenso
     if (warp == 0) tmem_dealloc(tmem, tmem_cols<BN>());
 }
 
-// ---------------------------------------------------------------- persistent inference GEMM
-// C = A . B^T with N = 256 and K <= 256 for the proposal network's inference (EPI_GELU, EPI_HEAD):
-// one CTA per SM walks the 128-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...  B (the layer's
-// weights, K/64 chunks of 256 x 64) stays in shared memory; A streams through a three-stage TMA
-// ring; the accumulator is double-buffered in tensor memory (2 x 256 columns), so the MMAs of the
-// next tile run while the epilogue drains the previous one.  Warp 16 (one thread) issues the TMA
-// loads and the MMAs; warps 0-7 drain the even tiles (buffer 0), warps 8-15 the odd ones (buffer
-// 1): warp w reads TMEM lane quarter w % 4 (rows) and column half (w / 4) % 2.  For the head, the
-// second column half hands its partial 256->3 sums to the first through shared memory (two
-// mbarriers per group).  All waits are bounded; on expiry the CTA records HF_DEV_ERR_TIMEOUT and
-// winds down.
-constexpr int kPStages = 3;
-constexpr int kPThreads = 17 * 32;
-constexpr uint32_t kPBChunk = 256 * 128;   // 256 rows x 64 bf16
+// ---------------------------------------------------------------- fused inference network
+// The whole forward pass of the proposal network per 128-row tile in one persistent kernel: the
+// hidden layer never leaves the SM.  Each layer runs as two N = 128 halves ("steps"), each into one
+// of two 128-column tensor-memory accumulator regions (step s uses region s mod 2); the epilogue
+// writes the bf16 layer-1 activations of tile t into activation region t mod 2 (columns 256..383
+// or 384..511), from where layer 2 reads its A operand (tcgen05.mma with A in tensor memory).
+// Steps are software-pipelined by one tile: layer 1 of tile t + 1, then layer 2 of tile t, so
+// that while the epilogue drains step s the tensor cores already compute step s + 1 and no step
+// waits on the activations it depends on.  Warp 16 loads (TMA: the weights once, the feature
+// tiles through a two-stage ring) and issues the MMAs; warps 0-15 drain each step, warp w covering
+// TMEM lanes 32 (w % 4) .. + 31 (rows) and the 32 columns 32 (w / 4) .. + 31 of the region.  The
+// head (256 -> 3) sums in packed FP32 per warp; column groups 1..3 hand their partial sums to
+// group 0 through shared memory.  All waits are bounded; on expiry the CTA records
+// HF_DEV_ERR_TIMEOUT and winds down.
+constexpr int kFXStages = 2;
+constexpr int kFThreads = 17 * 32;
+constexpr uint32_t kFW1Bytes = 256 * 128;        // 256 rows x 64 bf16
+constexpr uint32_t kFW2Bytes = 4 * 256 * 128;    // 4 K chunks of 256 rows x 64 bf16
+constexpr uint32_t kFHCol = 256;                 // tensor-memory columns of the activation regions
+constexpr size_t kFSmemBytes = 1024 + kFW1Bytes + kFW2Bytes + kFXStages * kATileBytes + 256 +
+                               (512 + 3 * 256 + 4) * 4 + 3 * 128 * 3 * 4;
 
-template <int EPI>
-__global__ void __launch_bounds__(kPThreads, 1) k_gemm_persist(const __grid_constant__ CUtensorMap ta,
-                                                               const __grid_constant__ CUtensorMap tb, GemmArgs g) {
+__global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constant__ CUtensorMap tx,
+                                                            const __grid_constant__ CUtensorMap tw1,
+                                                            const __grid_constant__ CUtensorMap tw2, GemmArgs g,
+                                                            const float* __restrict__ b2) {
     extern __shared__ unsigned char smem_raw[];
-    const int nk = g.K / 64;
     unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
-    unsigned char* sB = base;                                  // nk x 32 KB
-    unsigned char* sA = sB + nk * kPBChunk;                     // kPStages x 16 KB
-    uint64_t* afull = reinterpret_cast<uint64_t*>(sA + kPStages * kATileBytes);
-    uint64_t* aempty = afull + kPStages;
-    uint64_t* bfull = aempty + kPStages;
-    uint64_t* accf = bfull + 1;    // [2] MMA -> epilogue group
-    uint64_t* acce = accf + 2;     // [2] epilogue group (8 warps) -> MMA
-    uint64_t* hbar = acce + 2;     // [2] head: second column half wrote its partial sums (4 warps)
-    uint64_t* hfree = hbar + 2;    // [2] head: first column half read them (4 warps)
-    uint64_t* done = hfree + 2;
+    unsigned char* sW1 = base;
+    unsigned char* sW2 = sW1 + kFW1Bytes;
+    unsigned char* sX = sW2 + kFW2Bytes;
+    uint64_t* xfull = reinterpret_cast<uint64_t*>(sX + kFXStages * kATileBytes);
+    uint64_t* xempty = xfull + kFXStages;
+    uint64_t* wfull = xempty + kFXStages;
+    uint64_t* accf = wfull + 1;    // [2] MMA step done -> epilogue
+    uint64_t* acce = accf + 2;     // [2] region read (16 warps) -> MMA
+    uint64_t* hfull = acce + 2;    // [2] a tile's layer-1 activations written (16 warps) -> MMA
+    uint64_t* hbar = hfull + 2;    // head partial sums written (12 warps)
+    uint64_t* hfree = hbar + 1;    // head partial sums read (4 warps)
+    uint64_t* done = hfree + 1;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
-    float* consts = reinterpret_cast<float*>(tslot + 4);   // bias [256] (and W3 [3][256], b3 [3] for the head)
-    float* part = consts + 256 + 3 * 256 + 4;              // head: [2 groups][128 rows][3]
+    float* consts = reinterpret_cast<float*>(base + kFW1Bytes + kFW2Bytes + kFXStages * kATileBytes + 256);
+    float* cb1 = consts;              // [256]
+    float* cb2 = consts + 256;        // [256]
+    float* cw3 = consts + 512;        // [3][256], then b3 [3]
+    float* part = consts + 512 + 3 * 256 + 4;   // [3 column groups][128 rows][3]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles = (g.M + 127) / 128;
+    const int my_tiles = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kPStages; ++s) {
-            mbar_init(afull + s, 1);
-            mbar_init(aempty + s, 1);
+        for (int q = 0; q < kFXStages; ++q) {
+            mbar_init(xfull + q, 1);
+            mbar_init(xempty + q, 1);
         }
-        mbar_init(bfull, 1);
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(accf + b, 1);
-            mbar_init(acce + b, 8);
-            mbar_init(hbar + b, 4);
-            mbar_init(hfree + b, 4);
+        mbar_init(wfull, 1);
+        for (int r = 0; r < 2; ++r) {
+            mbar_init(accf + r, 1);
+            mbar_init(acce + r, 16);
+            mbar_init(hfull + r, 16);
         }
+        mbar_init(hbar, 12);
+        mbar_init(hfree, 4);
         mbar_init(done, 1);
         fence_mbar_init();
     }
@@ -390,222 +342,236 @@ __global__ void __launch_bounds__(kPThreads, 1) k_gemm_persist(const __grid_cons
         tmem_alloc(tslot, 512);
         tmem_relinquish();
     }
-    for (int q = threadIdx.x; q < 256; q += blockDim.x) consts[q] = g.bias ? g.bias[q] : 0.0f;
-    if constexpr (EPI == EPI_HEAD)
-        for (int q = threadIdx.x; q < 3 * 256 + 3; q += blockDim.x) consts[256 + q] = q < 768 ? g.w3[q] : g.b3[q - 768];
+    for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+        cb1[q] = g.bias[q];
+        cb2[q] = b2[q];
+    }
+    for (int q = threadIdx.x; q < 3 * 256 + 3; q += blockDim.x) cw3[q] = q < 768 ? g.w3[q] : g.b3[q - 768];
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
 
     if (warp == 16) {
-        // The whole warp runs the producer / MMA loop (its values stay warp-uniform); the elected
-        // lane issues the copies and the MMAs, and lane 0's verdict on each wait holds for all.  A
-        // loop run by one lane alone issues several times slower while the epilogue warps compute.
+        // the whole warp runs the loop (warp-uniform state); the elected lane issues
         auto agree = [](bool x) { return __shfl_sync(0xffffffffu, x ? 1 : 0, 0) != 0; };
-        bool ok = true;
-        const uint32_t idesc = idesc_bf16_f32(128, 256);
-        const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-        const long long total = (long long)my_tiles * nk;
-        long long g_load = 0, g_use = 0;
-        // the weights, once
+        const uint32_t idesc = idesc_bf16_f32(128, 128);
+        int loaded = 0, used = 0;   // feature tiles whose loads were issued / that were consumed
+        int step = 0;
         if (elect_one()) {
-            mbar_expect_tx(bfull, nk * kPBChunk);
-            for (int c = 0; c < nk; ++c) tma_load_2d(sB + c * kPBChunk, &tb, bfull, c * 64, 0);
+            mbar_expect_tx(wfull, kFW1Bytes + kFW2Bytes);
+            tma_load_2d(sW1, &tw1, wfull, 0, 0);
+            for (int c = 0; c < 4; ++c) tma_load_2d(sW2 + c * kFW1Bytes, &tw2, wfull, c * 64, 0);
         }
         __syncwarp();
-        auto top_up = [&]() -> bool {   // keep up to kPStages A chunks in flight
-            while (g_load < total && g_load < g_use + kPStages) {
-                const int s = (int)(g_load % kPStages);
-                if (!agree(mbar_wait(aempty + s, (uint32_t)(((g_load / kPStages) & 1) ^ 1), kWaitTimeoutNs))) return false;
-                const int t = blockIdx.x + (int)(g_load / nk) * gridDim.x, c = (int)(g_load % nk);
+        auto top_up = [&]() -> bool {
+            while (loaded < my_tiles && loaded < used + kFXStages) {
+                const int q = loaded % kFXStages;
+                if (!agree(mbar_wait(xempty + q, (uint32_t)(((loaded / kFXStages) & 1) ^ 1), kWaitTimeoutNs))) return false;
                 if (elect_one()) {
-                    mbar_expect_tx(afull + s, kATileBytes);
-                    tma_load_2d(sA + s * kATileBytes, &ta, afull + s, c * 64, t * 128);
+                    mbar_expect_tx(xfull + q, kATileBytes);
+                    tma_load_2d(sX + q * kATileBytes, &tx, xfull + q, 0, ((int)blockIdx.x + loaded * (int)gridDim.x) * 128);
                 }
                 __syncwarp();
-                ++g_load;
+                ++loaded;
             }
             return true;
         };
-        ok = top_up() && agree(mbar_wait(bfull, 0, kWaitTimeoutNs));
-        int lt = 0;
-        for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x, ++lt) {
-            const int b = lt & 1;
-            if (!agree(mbar_wait(acce + b, (uint32_t)(((lt >> 1) & 1) ^ 1), kWaitTimeoutNs))) {
-                ok = false;
-                break;
-            }
+        // wait until accumulator region step % 2 is free (the step two before it drained)
+        auto region = [&]() -> bool {
+            if (!agree(mbar_wait(acce + (step & 1), (uint32_t)(((step >> 1) & 1) ^ 1), kWaitTimeoutNs))) return false;
             fence_after();
-            for (int c = 0; c < nk; ++c) {
-                if (!top_up()) {
-                    ok = false;
-                    break;
-                }
-                const int s = (int)(g_use % kPStages);
-                if (!agree(mbar_wait(afull + s, (uint32_t)((g_use / kPStages) & 1), kWaitTimeoutNs))) {
-                    ok = false;
-                    break;
-                }
-                fence_after();
-                const uint32_t a0 = saddr(sA + s * kATileBytes), b0 = saddr(sB + c * kPBChunk);
+            return true;
+        };
+        // layer 1 of the next feature tile: two steps from the feature ring
+        auto layer1 = [&]() -> bool {
+            const int q = used % kFXStages;
+            if (!agree(mbar_wait(xfull + q, (uint32_t)((used / kFXStages) & 1), kWaitTimeoutNs))) return false;
+            fence_after();
+            const uint32_t a0 = saddr(sX + q * kATileBytes);
+            for (int j = 0; j < 2; ++j, ++step) {
+                if (!region()) return false;
                 if (elect_one()) {
+                    const uint32_t d = tmem + (uint32_t)(step & 1) * 128, b0 = saddr(sW1) + (uint32_t)j * 16384;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
-                        mma_bf16(tmem + b * 256, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
-                                 (c > 0 || kk > 0) ? 1u : 0u);
-                    mma_commit(aempty + s);
+                        mma_bf16(d, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, kk > 0 ? 1u : 0u);
+                    if (j == 1) mma_commit(xempty + q);
+                    mma_commit(accf + (step & 1));
                 }
                 __syncwarp();
-                ++g_use;
             }
-            if (!ok) break;
-            if (elect_one()) mma_commit(accf + b);
-            __syncwarp();
+            ++used;
+            return top_up();
+        };
+        // layer 2 of local tile lt: two steps from its activations in tensor memory
+        auto layer2 = [&](int lt) -> bool {
+            if (!agree(mbar_wait(hfull + (lt & 1), (uint32_t)((lt >> 1) & 1), kWaitTimeoutNs))) return false;
+            fence_after();
+            const uint32_t a = tmem + kFHCol + (uint32_t)(lt & 1) * 128;
+            for (int j = 0; j < 2; ++j, ++step) {
+                if (!region()) return false;
+                if (elect_one()) {
+                    const uint32_t d = tmem + (uint32_t)(step & 1) * 128;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint32_t b0 = saddr(sW2) + (uint32_t)c * kFW1Bytes + (uint32_t)j * 16384;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_bf16_ts(d, a + (uint32_t)(c * 4 + kk) * 8, sdesc_sw128(b0 + kk * 32), idesc,
+                                        (c > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(accf + (step & 1));
+                }
+                __syncwarp();
+            }
+            return true;
+        };
+        bool ok = top_up() && agree(mbar_wait(wfull, 0, kWaitTimeoutNs));
+        if (ok && my_tiles > 0) ok = layer1();
+        for (int lt = 0; ok && lt < my_tiles; ++lt) {
+            if (lt + 1 < my_tiles) ok = layer1();
+            if (ok) ok = layer2(lt);
         }
         // wind down: every issued MMA complete, every issued copy landed (bounded)
         if (elect_one()) mma_commit(done);
         __syncwarp();
         mbar_wait(done, 0, kWaitTimeoutNs);
-        for (long long q = g_use; q < g_load; ++q)
-            mbar_wait(afull + (int)(q % kPStages), (uint32_t)((q / kPStages) & 1), kWaitTimeoutNs);
+        for (int u = used; u < loaded; ++u)
+            mbar_wait(xfull + u % kFXStages, (uint32_t)((u / kFXStages) & 1), kWaitTimeoutNs);
         if (!ok && lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
     } else {
-        const int grp = warp >> 3, quarter = warp & 3, half = (warp >> 2) & 1;
+        const int quarter = warp & 3, grp = warp >> 2;
         const int lrow = quarter * 32 + lane;
-        const uint32_t tl = tmem + (uint32_t)grp * 256 + ((uint32_t)(quarter * 32) << 16) + (uint32_t)half * 128;
-        const bool vec = ((reinterpret_cast<uintptr_t>(g.H) & 15) == 0) && (g.ldh & 7) == 0;
-        float* pg = part + grp * 128 * 3;
-        int k = 0;   // this group's tile count
-        for (int t = blockIdx.x + grp * gridDim.x; t < tiles; t += 2 * gridDim.x, ++k) {
-            if (!mbar_wait(accf + grp, (uint32_t)(k & 1), kWaitTimeoutNs)) {
-                if (lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
-                break;
-            }
+        const uint32_t lanes = tmem + ((uint32_t)(quarter * 32) << 16);
+        int step = 0;
+        // this warp's 32 columns of the next step's accumulator; the region is released at once
+        auto drain = [&](uint32_t (&va)[16], uint32_t (&vb)[16]) -> bool {
+            const int r = step & 1;
+            if (!mbar_wait(accf + r, (uint32_t)((step >> 1) & 1), kWaitTimeoutNs)) return false;
             fence_after();
-            const int row = t * 128 + lrow;
-            const bool wr = row < g.M;
-            const int cbase = half * 128;
-            g2_t Y0 = g2s(0.0f), Y1 = g2s(0.0f), Y2 = g2s(0.0f);
-            // the next 16 columns are in flight from tensor memory while these are processed
-            uint32_t nxt[16];
-            tmem_ld16_issue(tl, nxt);
-            tmem_ld_wait(nxt);
-#pragma unroll 2
-            for (int c0 = 0; c0 < 128; c0 += 16) {
-                float v[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(nxt[q]);
-                if (c0 + 16 < 128) tmem_ld16_issue(tl + c0 + 16, nxt);
-                const int n = cbase + c0;
-                if constexpr (EPI == EPI_GELU) {
-                    uint32_t w[8];
-#pragma unroll
-                    for (int q = 0; q < 16; q += 2) {
-                        const float2 b = *reinterpret_cast<const float2*>(consts + n + q);
-                        float ga, gb;
-                        g2u(gelu_poly2(g2add(g2(v[q], v[q + 1]), g2(b.x, b.y))), ga, gb);
-                        w[q >> 1] = bf16x2_bits(ga, gb);
-                    }
-                    if (wr) st_bf16x16w(g.H + (size_t)row * g.ldh + n, w, vec);
-                } else {
-                    // packed partial sums over the even and the odd columns
-#pragma unroll
-                    for (int q = 0; q < 16; q += 2) {
-                        const float2 b = *reinterpret_cast<const float2*>(consts + n + q);
-                        float ga, gb;
-                        g2u(gelu_poly2(g2add(g2(v[q], v[q + 1]), g2(b.x, b.y))), ga, gb);
-                        const uint32_t hb = bf16x2_bits(ga, gb);
-                        const g2_t H = g2(__uint_as_float(hb << 16), __uint_as_float(hb & 0xffff0000u));
-                        const float2 w0 = *reinterpret_cast<const float2*>(consts + 256 + n + q);
-                        const float2 w1 = *reinterpret_cast<const float2*>(consts + 512 + n + q);
-                        const float2 w2 = *reinterpret_cast<const float2*>(consts + 768 + n + q);
-                        Y0 = g2fma(g2(w0.x, w0.y), H, Y0);
-                        Y1 = g2fma(g2(w1.x, w1.y), H, Y1);
-                        Y2 = g2fma(g2(w2.x, w2.y), H, Y2);
-                    }
-                }
-                if (c0 + 16 < 128) tmem_ld_wait(nxt);
-            }
-            // the buffer is drained: the MMAs of a later tile may overwrite it
+            const uint32_t ta = lanes + (uint32_t)r * 128 + (uint32_t)grp * 32;
+            tmem_ld16_issue(ta, va);
+            tmem_ld16_issue(ta + 16, vb);
+            tmem_ld_wait(va);
+            tmem_ld_wait(vb);
             fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acce + grp);
-            if constexpr (EPI == EPI_HEAD) {
-                float y0, y1, y2, o0, o1, o2;
-                g2u(Y0, y0, o0);
-                g2u(Y1, y1, o1);
-                g2u(Y2, y2, o2);
-                y0 += o0;
-                y1 += o1;
-                y2 += o2;
-                if (half == 1) {
-                    // hand the partial sums over (once the first half has read the previous ones)
-                    if (!mbar_wait(hfree + grp, (uint32_t)((k & 1) ^ 1), kWaitTimeoutNs)) {
-                        if (lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
-                        break;
-                    }
-                    pg[3 * lrow] = y0;
-                    pg[3 * lrow + 1] = y1;
-                    pg[3 * lrow + 2] = y2;
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(hbar + grp);
-                } else {
-                    if (!mbar_wait(hbar + grp, (uint32_t)(k & 1), kWaitTimeoutNs)) {
-                        if (lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
-                        break;
-                    }
-                    y0 += pg[3 * lrow] + consts[1024];
-                    y1 += pg[3 * lrow + 1] + consts[1025];
-                    y2 += pg[3 * lrow + 2] + consts[1026];
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(hfree + grp);
-                    if (wr) {
-                        const float nn = sqrtf(y0 * y0 + y1 * y1 + y2 * y2);
-                        float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
-                        if (g.head_raw) {
-                            d0 = y0;
-                            d1 = y1;
-                            d2 = y2;
-                        } else if (nn > 0.0f) {
-                            d0 = y0 / nn;
-                            d1 = y1 / nn;
-                            d2 = y2 / nn;
-                        }
-                        g.dir_out[3 * (size_t)row] = d0;
-                        g.dir_out[3 * (size_t)row + 1] = d1;
-                        g.dir_out[3 * (size_t)row + 2] = d2;
-                    }
+            if (lane == 0) mbar_arrive(acce + r);
+            ++step;
+            return true;
+        };
+        // bf16 pairs of GELU(accumulator + bias) for the 32 columns (bias at the first one)
+        auto act = [&](const uint32_t (&va)[16], const uint32_t (&vb)[16], const float* bias, uint32_t (&w)[16]) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t xa = i < 8 ? va[2 * i] : vb[2 * i - 16];
+                const uint32_t xb = i < 8 ? va[2 * i + 1] : vb[2 * i - 15];
+                const float2 b = *reinterpret_cast<const float2*>(bias + 2 * i);
+                float ga, gb;
+                g2u(gelu_poly2(g2add(g2(__uint_as_float(xa), __uint_as_float(xb)), g2(b.x, b.y))), ga, gb);
+                w[i] = bf16x2_bits(ga, gb);
+            }
+        };
+        // layer 1 of local tile lt: its activations into activation region lt % 2
+        auto e1 = [&](int lt) -> bool {
+            for (int j = 0; j < 2; ++j) {
+                uint32_t va[16], vb[16], w[16];
+                if (!drain(va, vb)) return false;
+                const int n0 = j * 128 + grp * 32;
+                act(va, vb, cb1 + n0, w);
+                const uint32_t hc = lanes + kFHCol + (uint32_t)(lt & 1) * 128 + (uint32_t)(n0 >> 1);
+                const uint32_t lo[8] = {w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7]};
+                const uint32_t hi[8] = {w[8], w[9], w[10], w[11], w[12], w[13], w[14], w[15]};
+                tmem_st8(hc, lo);
+                tmem_st8(hc + 8, hi);
+                tmem_st_wait();
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(hfull + (lt & 1));
+            return true;
+        };
+        // layer 2 and the head of local tile lt
+        auto e2 = [&](int lt) -> bool {
+            g2_t Y0 = g2s(0.0f), Y1 = g2s(0.0f), Y2 = g2s(0.0f);   // head sums over even / odd units
+            for (int j = 0; j < 2; ++j) {
+                uint32_t va[16], vb[16], w[16];
+                if (!drain(va, vb)) return false;
+                const int n0 = j * 128 + grp * 32;
+                act(va, vb, cb2 + n0, w);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const g2_t H = g2(__uint_as_float(w[i] << 16), __uint_as_float(w[i] & 0xffff0000u));
+                    const float2 w0 = *reinterpret_cast<const float2*>(cw3 + n0 + 2 * i);
+                    const float2 w1 = *reinterpret_cast<const float2*>(cw3 + 256 + n0 + 2 * i);
+                    const float2 w2 = *reinterpret_cast<const float2*>(cw3 + 512 + n0 + 2 * i);
+                    Y0 = g2fma(g2(w0.x, w0.y), H, Y0);
+                    Y1 = g2fma(g2(w1.x, w1.y), H, Y1);
+                    Y2 = g2fma(g2(w2.x, w2.y), H, Y2);
                 }
             }
+            float y0, y1, y2, o0, o1, o2;
+            g2u(Y0, y0, o0);
+            g2u(Y1, y1, o1);
+            g2u(Y2, y2, o2);
+            y0 += o0;
+            y1 += o1;
+            y2 += o2;
+            if (grp != 0) {
+                // hand the partial sums over (once group 0 has read the previous tile's)
+                if (!mbar_wait(hfree, (uint32_t)((lt & 1) ^ 1), kWaitTimeoutNs)) return false;
+                float* pp = part + ((grp - 1) * 128 + lrow) * 3;
+                pp[0] = y0;
+                pp[1] = y1;
+                pp[2] = y2;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(hbar);
+                return true;
+            }
+            if (!mbar_wait(hbar, (uint32_t)(lt & 1), kWaitTimeoutNs)) return false;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float* pp = part + (q * 128 + lrow) * 3;
+                y0 += pp[0];
+                y1 += pp[1];
+                y2 += pp[2];
+            }
+            y0 += cw3[768];
+            y1 += cw3[769];
+            y2 += cw3[770];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(hfree);
+            const int row = ((int)blockIdx.x + lt * (int)gridDim.x) * 128 + lrow;
+            if (row < g.M) {
+                const float nn = sqrtf(y0 * y0 + y1 * y1 + y2 * y2);
+                float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
+                if (g.head_raw) {
+                    d0 = y0;
+                    d1 = y1;
+                    d2 = y2;
+                } else if (nn > 0.0f) {
+                    d0 = y0 / nn;
+                    d1 = y1 / nn;
+                    d2 = y2 / nn;
+                }
+                g.dir_out[3 * (size_t)row] = d0;
+                g.dir_out[3 * (size_t)row + 1] = d1;
+                g.dir_out[3 * (size_t)row + 2] = d2;
+            }
+            return true;
+        };
+        bool ok = true;
+        if (my_tiles > 0) ok = e1(0);
+        for (int lt = 0; ok && lt < my_tiles; ++lt) {
+            if (lt + 1 < my_tiles) ok = e1(lt + 1);
+            if (ok) ok = e2(lt);
         }
+        if (!ok && lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
     }
     fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 512);
-}
-
-template <int EPI>
-cudaError_t launch_persist(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t s) {
-    // at least 120 KB, so that one CTA holds an SM (it allocates all 512 tensor-memory columns)
-    size_t smem = 1024 + (size_t)(g.K / 64) * kPBChunk + kPStages * kATileBytes + 256 +
-                  (256 + 3 * 256 + 4 + 2 * 128 * 3) * 4;
-    if (smem < 120 * 1024) smem = 120 * 1024;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaError_t e = cudaStreamIsCapturing(s, &cs);
-    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone)
-        e = cudaFuncSetAttribute(k_gemm_persist<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    const int tiles = (g.M + 127) / 128;
-    k_gemm_persist<EPI><<<tiles < sms ? tiles : sms, kPThreads, smem, s>>>(ta, tb, g);
-    return cudaGetLastError();
 }
 
 template <int BN, int EPI>
@@ -688,15 +654,28 @@ cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap
         case EPI_STORE: return launch_epi<EPI_STORE>(bn, ta, tb, ga, splits, s);
         case EPI_ATOMIC: return launch_epi<EPI_ATOMIC>(bn, ta, tb, ga, splits, s);
         case EPI_GELU_TRAIN: return launch_epi<EPI_GELU_TRAIN>(bn, ta, tb, ga, splits, s);
-        case EPI_GELU: return launch_epi<EPI_GELU>(bn, ta, tb, ga, splits, s);
-        case EPI_PARTIAL: return launch_epi<EPI_PARTIAL>(bn, ta, tb, ga, splits, s);
-        default: return launch_epi<EPI_HEAD>(bn, ta, tb, ga, splits, s);
+        default: return launch_epi<EPI_PARTIAL>(bn, ta, tb, ga, splits, s);
     }
 }
 
-cudaError_t hf_gemm_persist(int epi, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t s) {
-    if (g.N != 256 || g.K % 64 || g.K < 64 || g.K > 256 || g.M < 1) return cudaErrorInvalidValue;
-    return epi == EPI_HEAD ? launch_persist<EPI_HEAD>(ta, tb, g, s) : launch_persist<EPI_GELU>(ta, tb, g, s);
+cudaError_t hf_mlp_fused(const CUtensorMap& tx, const CUtensorMap& tw1, const CUtensorMap& tw2, const GemmArgs& g,
+                         const float* b2, cudaStream_t s) {
+    if (g.M <= 0) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+        e = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmemBytes);
+    if (e != cudaSuccess) return e;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const int tiles = (g.M + 127) / 128;
+    k_mlp_fused<<<tiles < sms ? tiles : sms, kFThreads, kFSmemBytes, s>>>(tx, tw1, tw2, g, b2);
+    return cudaGetLastError();
 }
 
 namespace {

@@ -10,8 +10,6 @@ enum {
     EPI_STORE = 0,        // C[row][n] = acc + bias[n] (f32)
     EPI_ATOMIC = 1,       // C[row][n] += acc (+ bias[n] from split 0): split-K partial sums (f32)
     EPI_GELU_TRAIN = 2,   // Z = acc + bias (f32), H = bf16(gelu(Z)), HT = H transposed (bf16)
-    EPI_GELU = 3,         // H = bf16(gelu(acc + bias))
-    EPI_HEAD = 4,         // h = bf16(gelu(acc + bias)), y = w3 . h + b3 (3 outputs), dir = y / |y| (or y); BN = N = 256
     EPI_PARTIAL = 5,      // C[split z][row][n] = acc: split-K partial tiles, summed afterwards in a fixed order
 };
 
@@ -27,10 +25,10 @@ struct GemmArgs {
     int ldh;
     uint16_t* HT;
     int ldht;
-    const float* w3;          // EPI_HEAD: 3 x 256 f32 (values of the bf16 layer-3 weights)
-    const float* b3;          // EPI_HEAD: 3
-    float* dir_out;           // EPI_HEAD: M x 3
-    int head_raw;             // EPI_HEAD: write y itself instead of y / |y|
+    const float* w3;          // inference head: 3 x 256 f32 (values of the bf16 layer-3 weights)
+    const float* b3;          // inference head: 3
+    float* dir_out;           // inference: M x 3
+    int head_raw;             // inference: write y itself instead of y / |y|
     uint32_t* errw;           // device error word (HF_DEV_ERR_TIMEOUT)
     long long split_stride;   // EPI_PARTIAL: elements between the partial tiles of consecutive splits
     int stages;               // set by hf_gemm_tn: operand ring depth
@@ -50,7 +48,9 @@ cudaError_t hf_make_tmap_bf16_rows32(CUtensorMap* map, const void* base, long lo
 cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits,
                        cudaStream_t s);
 
-// The proposal network's inference layers (EPI_GELU or EPI_HEAD only, N = 256, K = 64..256): a
-// persistent kernel (one CTA per SM, weights resident in shared memory, double-buffered tensor
-// memory accumulator); ta: A map (box 128 rows), tb: B map (box 256 rows).
-cudaError_t hf_gemm_persist(int epi, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t s);
+// The proposal network's whole inference in one persistent kernel (the hidden layer stays in
+// tensor memory): tx the features [M x 64] (box 128 rows), tw1 W1 [256 x 64] and tw2 W2
+// [256 x 256] (box 256 rows); g.bias = b1, b2 the layer-2 bias, g.w3 / g.b3 the head, g.dir_out
+// (M x 3), g.head_raw, g.errw.
+cudaError_t hf_mlp_fused(const CUtensorMap& tx, const CUtensorMap& tw1, const CUtensorMap& tw2, const GemmArgs& g,
+                         const float* b2, cudaStream_t s);

@@ -318,20 +318,16 @@ cudaError_t hf_train_step(const MlpTrain& t, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Inference: x [n x 64] bf16 -> directions [n x 3] (two GEMMs; the second fuses GELU and the head).
-cudaError_t hf_mlp_infer(const MlpDev& d, const float* P, const uint16_t* x, int n, uint16_t* h1, float* dir_out,
-                         uint32_t* errw, cudaStream_t s, bool raw) {
-    CUtensorMap tx, tw1, th1, tw2;
+// Inference: x [n x 64] bf16 -> directions [n x 3], the whole network in one kernel.
+cudaError_t hf_mlp_infer(const MlpDev& d, const float* P, const uint16_t* x, int n, float* dir_out, uint32_t* errw,
+                         cudaStream_t s, bool raw) {
+    CUtensorMap tx, tw1, tw2;
     cudaError_t e = hf_make_tmap_bf16(&tx, x, n, kIn, 128);
     if (e == cudaSuccess) e = hf_make_tmap_bf16(&tw1, d.W1b, kHid, kIn, 256);
-    if (e == cudaSuccess) e = hf_make_tmap_bf16(&th1, h1, n, kHid, 128);
     if (e == cudaSuccess) e = hf_make_tmap_bf16(&tw2, d.W2b, kHid, kHid, 256);
     if (e != cudaSuccess) return e;
     GemmArgs g{};
-    g.errw = errw; g.M = n; g.N = kHid; g.K = kIn; g.kchunks_per_split = 1; g.bias = P + kB1; g.H = h1; g.ldh = kHid;
-    if ((e = hf_gemm_persist(EPI_GELU, tx, tw1, g, s))) return e;
-    GemmArgs g2{};
-    g2.errw = errw; g2.M = n; g2.N = kHid; g2.K = kHid; g2.kchunks_per_split = kHid / 64; g2.bias = P + kB2;
-    g2.w3 = d.w3f; g2.b3 = P + kB3; g2.dir_out = dir_out; g2.head_raw = raw ? 1 : 0;
-    return hf_gemm_persist(EPI_HEAD, th1, tw2, g2, s);
+    g.errw = errw; g.M = n; g.N = kHid; g.K = kIn; g.bias = P + kB1;
+    g.w3 = d.w3f; g.b3 = P + kB3; g.dir_out = dir_out; g.head_raw = raw ? 1 : 0;
+    return hf_mlp_fused(tx, tw1, tw2, g, P + kB2, s);
 }

@@ -50,12 +50,11 @@ cudaError_t hf_launch_bbox(const float* pts, int N, float* box, cudaStream_t s);
 cudaError_t hf_launch_bbox_init(unsigned* keys, cudaStream_t s);
 cudaError_t hf_train_step(const MlpTrain& t, cudaStream_t s);
 // raw: the head's raw 3-vectors y instead of the directions y / |y|
-cudaError_t hf_mlp_infer(const MlpDev& d, const float* P, const uint16_t* x, int n, uint16_t* h1, float* dir_out,
-                         uint32_t* errw, cudaStream_t s, bool raw = false);
+cudaError_t hf_mlp_infer(const MlpDev& d, const float* P, const uint16_t* x, int n, float* dir_out, uint32_t* errw,
+                         cudaStream_t s, bool raw = false);
 
-// the network behind the C-ABI handle (hf_mlp_api.cu): inference on n rows of features (the
-// caller provides the [n x 256] bf16 hidden scratch), and the stream the handle was created with
+// the network behind the C-ABI handle (hf_mlp_api.cu): inference on n rows of features, and the
+// stream the handle was created with
 typedef struct hf_mlp hf_mlp;
-cudaError_t hf_mlp_infer_rows(hf_mlp* m, const uint16_t* x, long long n, uint16_t* h1, float* dir_out, uint32_t* errw,
-                              cudaStream_t s);
+cudaError_t hf_mlp_infer_rows(hf_mlp* m, const uint16_t* x, long long n, float* dir_out, uint32_t* errw, cudaStream_t s);
 cudaStream_t hf_mlp_stream(hf_mlp* m);

@@ -23,8 +23,6 @@ struct hf_mlp {
     uint32_t* errw_host = nullptr;
     int tm_batch = 0;                       // batch size the tensor maps were encoded for
     CUtensorMap tm[TM_COUNT];
-    uint16_t* h1 = nullptr;                 // inference scratch [rows x 256] bf16
-    long long h1_rows = 0;
     cudaStream_t cap_stream = nullptr;      // non-blocking stream the training step is captured on
     cudaGraphExec_t graph = nullptr;        // captured training step and what it was captured for
     const void* g_X = nullptr;
@@ -108,19 +106,6 @@ int check_batch(hf_mlp* m, int B) {
     return HF_OK;
 }
 
-int ensure_h1(hf_mlp* m, long long rows) {
-    if (rows <= m->h1_rows) return HF_OK;
-    if (m->h1) {
-        cudaStreamSynchronize(m->stream);
-        cudaFree(m->h1);
-        m->h1 = nullptr;
-        m->h1_rows = 0;
-    }
-    cudaError_t e = cudaMalloc(&m->h1, (size_t)rows * 256 * sizeof(uint16_t));
-    if (e != cudaSuccess) return mlp_cuda(m, e, "inference scratch");
-    m->h1_rows = rows;
-    return HF_OK;
-}
 
 // loss history covers steps [0, loss_cap); grow (keeping values) when a run goes further
 int ensure_loss(hf_mlp* m, long long upto) {
@@ -218,7 +203,6 @@ void hair_fuse_mlp_destroy(hf_mlp* m) {
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     if (m->block) cudaFree(m->block);
     if (m->loss_hist) cudaFree(m->loss_hist);
-    if (m->h1) cudaFree(m->h1);
     if (m->errw_host) cudaFreeHost(m->errw_host);
     delete m;
 }
@@ -331,7 +315,6 @@ namespace {
 int mlp_forward(hf_mlp* m, const uint16_t* X, int n, float* dir_out, int mem_kind, bool raw) {
     if (!m || !X || !dir_out || n < 1) return mlp_err(m, HF_ERR_INVALID_ARG, "%s", "bad forward arguments");
     int rc;
-    if ((rc = ensure_h1(m, n))) return rc;
     const uint16_t* xd = X;
     float* od = dir_out;
     void* tmp = nullptr;
@@ -342,7 +325,7 @@ int mlp_forward(hf_mlp* m, const uint16_t* X, int n, float* dir_out, int mem_kin
         xd = (const uint16_t*)tmp;
         od = (float*)((char*)tmp + (size_t)n * 128);
     }
-    if (e == cudaSuccess) e = hf_mlp_infer(m->d, m->P, xd, n, m->h1, od, m->errw, m->stream, raw);
+    if (e == cudaSuccess) e = hf_mlp_infer(m->d, m->P, xd, n, od, m->errw, m->stream, raw);
     if (e == cudaSuccess && mem_kind == HF_HOST) e = cudaMemcpyAsync(dir_out, od, (size_t)n * 12, cudaMemcpyDeviceToHost, m->stream);
     if (mem_kind == HF_HOST) {
         cudaError_t e2 = cudaStreamSynchronize(m->stream);
@@ -499,7 +482,6 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     if ((rc = hf_ensure(c, c->best, (size_t)N * sizeof(int32_t)))) return rc;
     if ((rc = projection_buffers(c))) return rc;
     if ((rc = hf_ensure(c, c->outs, (size_t)N * 21))) return rc;
-    if ((rc = ensure_h1(m, N))) return rc;
     char* lm = (char*)c->lmisc.p;
     float* box = (float*)lm;
     int* count = (int*)(lm + 64);                                        // fallback points
@@ -534,7 +516,7 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     const FeatArgs fa{(const float*)c->pts.p, N, nullptr, (uint16_t*)c->feat.p, box_keys};
     if ((rc = run_launch(c, "k_featpos", [&] { return hf_launch_featpos(fa, s); }))) return rc;
     if ((rc = run_launch(c, "k_mlp", [&] {
-             return hf_mlp_infer(m->d, m->P, (const uint16_t*)c->feat.p, N, m->h1, (float*)c->prop.p,
+             return hf_mlp_infer(m->d, m->P, (const uint16_t*)c->feat.p, N, (float*)c->prop.p,
                                  (uint32_t*)c->errw.p, s);
          })))
         return rc;
@@ -583,10 +565,9 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     return HF_OK;
 }
 
-cudaError_t hf_mlp_infer_rows(hf_mlp* m, const uint16_t* x, long long n, uint16_t* h1, float* dir_out, uint32_t* errw,
-                              cudaStream_t s) {
+cudaError_t hf_mlp_infer_rows(hf_mlp* m, const uint16_t* x, long long n, float* dir_out, uint32_t* errw, cudaStream_t s) {
     if (n <= 0 || n > 0x7fffffffLL) return cudaErrorInvalidValue;
-    return hf_mlp_infer(m->d, m->P, x, (int)n, h1, dir_out, errw, s);
+    return hf_mlp_infer(m->d, m->P, x, (int)n, dir_out, errw, s);
 }
 
 cudaStream_t hf_mlp_stream(hf_mlp* m) { return m->stream; }

@@ -140,6 +140,20 @@ def test_forward_matches_oracle(tiny):
     assert np.min(np.sum(got * want, axis=1)) > 0.999
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000])
+def test_forward_rows_are_independent(tiny, n):
+    """Each row's proposal depends on that row alone: the first n rows of a larger call, the tile
+    boundaries (128 rows) and a single row give the same bits."""
+    net = _net()
+    net.set_params(om.init(9).astype(np.float32))
+    X, _ = _dataset(tiny)
+    full = net.forward(X, raw=True)
+    part = net.forward(np.ascontiguousarray(X[:n]), raw=True)
+    assert np.array_equal(part, full[:n])
+    rev = net.forward(np.ascontiguousarray(X[:n][::-1]), raw=True)
+    assert np.array_equal(rev[::-1], full[:n])
+
+
 @pytest.mark.parametrize("B", [256, 1024])
 def test_gradients_match_oracle(tiny, B):
     import torch
