@@ -374,6 +374,16 @@ int hair_fuse_mlp_forward_raw(hf_mlp* mlp, const uint16_t* X, int n, float* y_ou
 int hair_fuse_mlp_save(hf_mlp* mlp, const char* path);
 int hair_fuse_mlp_load(hf_mlp* mlp, const char* path);
 const char* hair_fuse_mlp_last_error(const hf_mlp* mlp);
+/* Test hook (no counterpart in the paper) for the inference kernel's expiry path.  wait_ns > 0
+ * limits every wait of its pipeline (mbarrier waits on copies, tensor-core steps and the other
+ * warps) to wait_ns nanoseconds instead of the default 2 s, and makes the producer, once it has
+ * issued the first tile's layer-1 steps, wait on a barrier that nothing completes, so the limit
+ * always expires there.  On expiry every warp stops; the kernel waits, up to the default limit,
+ * for the copies and tensor-core work it already issued (they complete by themselves), releases
+ * its tensor memory and writes no further output; the call returns HF_ERR_TIMEOUT.  wait_ns = 0
+ * restores normal operation.  Applies to hair_fuse_mlp_forward(_raw), the learned fusion and the
+ * batches that use this network. */
+int hair_fuse_mlp_set_wait_limit(hf_mlp* mlp, unsigned long long wait_ns);
 
 /* Features (N x 64 bf16, kind mem_kind) of the uploaded scene's points. */
 int hair_fuse_features(hf_ctx* ctx, uint16_t* x_out, int mem_kind);

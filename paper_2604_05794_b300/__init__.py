@@ -87,6 +87,7 @@ _SIGS = {
     "hair_fuse_gemm_bf16": ([_vp, _vp, _vp, _i, _i, _i, _vp], _i),
     "hair_fuse_gemm_bf16_bounded": ([_vp, _vp, _vp, _i, _i, _i, ctypes.c_ulonglong, _vp], _i),
     "hair_fuse_gelu_eval": ([_vp, _vp, _ll, _vp], _i),
+    "hair_fuse_mlp_set_wait_limit": ([_vp, ctypes.c_ulonglong], _i),
     "hair_fuse_fail_alloc_after": ([_i], _i),
     "hair_fuse_sync": ([_vp], _i),
     "hair_fuse_profile": ([_vp, _i], _i),
@@ -162,6 +163,7 @@ hair_fuse_fibonacci_hemisphere = _lib.hair_fuse_fibonacci_hemisphere
 hair_fuse_gemm_bf16 = _lib.hair_fuse_gemm_bf16
 hair_fuse_gemm_bf16_bounded = _lib.hair_fuse_gemm_bf16_bounded
 hair_fuse_gelu_eval = _lib.hair_fuse_gelu_eval
+hair_fuse_mlp_set_wait_limit = _lib.hair_fuse_mlp_set_wait_limit
 hair_fuse_fail_alloc_after = _lib.hair_fuse_fail_alloc_after
 hair_fuse_sync = _lib.hair_fuse_sync
 hair_fuse_profile = _lib.hair_fuse_profile

@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constan
     uint64_t* hbar = hfull + 2;    // head partial sums written (12 warps)
     uint64_t* hfree = hbar + 1;    // head partial sums read (4 warps)
     uint64_t* done = hfree + 1;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* never = done + 1;    // test mode: a barrier nothing completes
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(never + 1);
     float* consts = reinterpret_cast<float*>(base + kFW1Bytes + kFW2Bytes + kFXStages * kATileBytes + 256);
     float* cb1 = consts;              // [256]
     float* cb2 = consts + 256;        // [256]
@@ -336,6 +337,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constan
         mbar_init(hbar, 12);
         mbar_init(hfree, 4);
         mbar_init(done, 1);
+        mbar_init(never, 1);
         fence_mbar_init();
     }
     if (warp == 0) {
@@ -351,6 +353,12 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constan
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
+    // the pipeline's waits: the default limit, or the caller's (hinted, so that a short one expires
+    // deterministically); the wind-down after an expiry always allows kWaitTimeoutNs
+    const uint64_t wait_ns = g.wait_ns ? g.wait_ns : kWaitTimeoutNs;
+    auto pwait = [&](uint64_t* b, uint32_t parity) -> bool {
+        return g.wait_ns ? mbar_wait_hinted(b, parity, wait_ns) : mbar_wait(b, parity, kWaitTimeoutNs);
+    };
 
     if (warp == 16) {
         // the whole warp runs the loop (warp-uniform state); the elected lane issues
@@ -367,7 +375,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constan
         auto top_up = [&]() -> bool {
             while (loaded < my_tiles && loaded < used + kFXStages) {
                 const int q = loaded % kFXStages;
-                if (!agree(mbar_wait(xempty + q, (uint32_t)(((loaded / kFXStages) & 1) ^ 1), kWaitTimeoutNs))) return false;
+                if (!agree(pwait(xempty + q, (uint32_t)(((loaded / kFXStages) & 1) ^ 1)))) return false;
                 if (elect_one()) {
                     mbar_expect_tx(xfull + q, kATileBytes);
                     tma_load_2d(sX + q * kATileBytes, &tx, xfull + q, 0, ((int)blockIdx.x + loaded * (int)gridDim.x) * 128);
@@ -379,14 +387,14 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constan
         };
         // wait until accumulator region step % 2 is free (the step two before it drained)
         auto region = [&]() -> bool {
-            if (!agree(mbar_wait(acce + (step & 1), (uint32_t)(((step >> 1) & 1) ^ 1), kWaitTimeoutNs))) return false;
+            if (!agree(pwait(acce + (step & 1), (uint32_t)(((step >> 1) & 1) ^ 1)))) return false;
             fence_after();
             return true;
         };
         // layer 1 of the next feature tile: two steps from the feature ring
         auto layer1 = [&]() -> bool {
             const int q = used % kFXStages;
-            if (!agree(mbar_wait(xfull + q, (uint32_t)((used / kFXStages) & 1), kWaitTimeoutNs))) return false;
+            if (!agree(pwait(xfull + q, (uint32_t)((used / kFXStages) & 1)))) return false;
             fence_after();
             const uint32_t a0 = saddr(sX + q * kATileBytes);
             for (int j = 0; j < 2; ++j, ++step) {
@@ -406,7 +414,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constan
         };
         // layer 2 of local tile lt: two steps from its activations in tensor memory
         auto layer2 = [&](int lt) -> bool {
-            if (!agree(mbar_wait(hfull + (lt & 1), (uint32_t)((lt >> 1) & 1), kWaitTimeoutNs))) return false;
+            if (!agree(pwait(hfull + (lt & 1), (uint32_t)((lt >> 1) & 1)))) return false;
             fence_after();
             const uint32_t a = tmem + kFHCol + (uint32_t)(lt & 1) * 128;
             for (int j = 0; j < 2; ++j, ++step) {
@@ -427,8 +435,11 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constan
             }
             return true;
         };
-        bool ok = top_up() && agree(mbar_wait(wfull, 0, kWaitTimeoutNs));
+        bool ok = top_up() && agree(pwait(wfull, 0));
         if (ok && my_tiles > 0) ok = layer1();
+        // test mode: with the first tile's layer-1 steps in flight, wait for what never comes, so
+        // that the limit expires with tensor-core work, copies and epilogue waits outstanding
+        if (ok && g.wait_ns && !agree(pwait(never, 0))) ok = false;
         for (int lt = 0; ok && lt < my_tiles; ++lt) {
             if (lt + 1 < my_tiles) ok = layer1();
             if (ok) ok = layer2(lt);
@@ -437,6 +448,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constan
         if (elect_one()) mma_commit(done);
         __syncwarp();
         mbar_wait(done, 0, kWaitTimeoutNs);
+        mbar_wait(wfull, 0, kWaitTimeoutNs);   // the weight copies, if their wait gave up
         for (int u = used; u < loaded; ++u)
             mbar_wait(xfull + u % kFXStages, (uint32_t)((u / kFXStages) & 1), kWaitTimeoutNs);
         if (!ok && lane == 0) atomicOr(g.errw, HF_DEV_ERR_TIMEOUT);
@@ -448,7 +460,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constan
         // this warp's 32 columns of the next step's accumulator; the region is released at once
         auto drain = [&](uint32_t (&va)[16], uint32_t (&vb)[16]) -> bool {
             const int r = step & 1;
-            if (!mbar_wait(accf + r, (uint32_t)((step >> 1) & 1), kWaitTimeoutNs)) return false;
+            if (!pwait(accf + r, (uint32_t)((step >> 1) & 1))) return false;
             fence_after();
             const uint32_t ta = lanes + (uint32_t)r * 128 + (uint32_t)grp * 32;
             tmem_ld16_issue(ta, va);
@@ -520,7 +532,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constan
             y2 += o2;
             if (grp != 0) {
                 // hand the partial sums over (once group 0 has read the previous tile's)
-                if (!mbar_wait(hfree, (uint32_t)((lt & 1) ^ 1), kWaitTimeoutNs)) return false;
+                if (!pwait(hfree, (uint32_t)((lt & 1) ^ 1))) return false;
                 float* pp = part + ((grp - 1) * 128 + lrow) * 3;
                 pp[0] = y0;
                 pp[1] = y1;
@@ -529,7 +541,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(const __grid_constan
                 if (lane == 0) mbar_arrive(hbar);
                 return true;
             }
-            if (!mbar_wait(hbar, (uint32_t)(lt & 1), kWaitTimeoutNs)) return false;
+            if (!pwait(hbar, (uint32_t)(lt & 1))) return false;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const float* pp = part + (q * 128 + lrow) * 3;

@@ -51,6 +51,6 @@ cudaError_t hf_gemm_tn(int epi, int bn, const CUtensorMap& ta, const CUtensorMap
 // The proposal network's whole inference in one persistent kernel (the hidden layer stays in
 // tensor memory): tx the features [M x 64] (box 128 rows), tw1 W1 [256 x 64] and tw2 W2
 // [256 x 256] (box 256 rows); g.bias = b1, b2 the layer-2 bias, g.w3 / g.b3 the head, g.dir_out
-// (M x 3), g.head_raw, g.errw.
+// (M x 3), g.head_raw, g.errw, g.wait_ns (0: the default limit).
 cudaError_t hf_mlp_fused(const CUtensorMap& tx, const CUtensorMap& tw1, const CUtensorMap& tw2, const GemmArgs& g,
                          const float* b2, cudaStream_t s);

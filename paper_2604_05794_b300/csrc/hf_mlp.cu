@@ -320,7 +320,7 @@ cudaError_t hf_train_step(const MlpTrain& t, cudaStream_t s) {
 
 // Inference: x [n x 64] bf16 -> directions [n x 3], the whole network in one kernel.
 cudaError_t hf_mlp_infer(const MlpDev& d, const float* P, const uint16_t* x, int n, float* dir_out, uint32_t* errw,
-                         cudaStream_t s, bool raw) {
+                         cudaStream_t s, bool raw, unsigned long long wait_ns) {
     CUtensorMap tx, tw1, tw2;
     cudaError_t e = hf_make_tmap_bf16(&tx, x, n, kIn, 128);
     if (e == cudaSuccess) e = hf_make_tmap_bf16(&tw1, d.W1b, kHid, kIn, 256);
@@ -328,6 +328,6 @@ cudaError_t hf_mlp_infer(const MlpDev& d, const float* P, const uint16_t* x, int
     if (e != cudaSuccess) return e;
     GemmArgs g{};
     g.errw = errw; g.M = n; g.N = kHid; g.K = kIn; g.bias = P + kB1;
-    g.w3 = d.w3f; g.b3 = P + kB3; g.dir_out = dir_out; g.head_raw = raw ? 1 : 0;
+    g.w3 = d.w3f; g.b3 = P + kB3; g.dir_out = dir_out; g.head_raw = raw ? 1 : 0; g.wait_ns = wait_ns;
     return hf_mlp_fused(tx, tw1, tw2, g, P + kB2, s);
 }

@@ -50,8 +50,9 @@ cudaError_t hf_launch_bbox(const float* pts, int N, float* box, cudaStream_t s);
 cudaError_t hf_launch_bbox_init(unsigned* keys, cudaStream_t s);
 cudaError_t hf_train_step(const MlpTrain& t, cudaStream_t s);
 // raw: the head's raw 3-vectors y instead of the directions y / |y|
+// wait_ns: limit of the kernel's pipeline waits (0: the default)
 cudaError_t hf_mlp_infer(const MlpDev& d, const float* P, const uint16_t* x, int n, float* dir_out, uint32_t* errw,
-                         cudaStream_t s, bool raw = false);
+                         cudaStream_t s, bool raw = false, unsigned long long wait_ns = 0);
 
 // the network behind the C-ABI handle (hf_mlp_api.cu): inference on n rows of features, and the
 // stream the handle was created with

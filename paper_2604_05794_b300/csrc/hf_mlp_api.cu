@@ -22,6 +22,7 @@ struct hf_mlp {
     uint32_t* errw = nullptr;
     uint32_t* errw_host = nullptr;
     int tm_batch = 0;                       // batch size the tensor maps were encoded for
+    unsigned long long wait_ns = 0;         // limit of the inference kernel's waits (0: the default)
     CUtensorMap tm[TM_COUNT];
     cudaStream_t cap_stream = nullptr;      // non-blocking stream the training step is captured on
     cudaGraphExec_t graph = nullptr;        // captured training step and what it was captured for
@@ -314,7 +315,6 @@ int hair_fuse_mlp_grads(hf_mlp* m, const uint16_t* X, const float* T, long long 
 namespace {
 int mlp_forward(hf_mlp* m, const uint16_t* X, int n, float* dir_out, int mem_kind, bool raw) {
     if (!m || !X || !dir_out || n < 1) return mlp_err(m, HF_ERR_INVALID_ARG, "%s", "bad forward arguments");
-    int rc;
     const uint16_t* xd = X;
     float* od = dir_out;
     void* tmp = nullptr;
@@ -325,7 +325,7 @@ int mlp_forward(hf_mlp* m, const uint16_t* X, int n, float* dir_out, int mem_kin
         xd = (const uint16_t*)tmp;
         od = (float*)((char*)tmp + (size_t)n * 128);
     }
-    if (e == cudaSuccess) e = hf_mlp_infer(m->d, m->P, xd, n, od, m->errw, m->stream, raw);
+    if (e == cudaSuccess) e = hf_mlp_infer(m->d, m->P, xd, n, od, m->errw, m->stream, raw, m->wait_ns);
     if (e == cudaSuccess && mem_kind == HF_HOST) e = cudaMemcpyAsync(dir_out, od, (size_t)n * 12, cudaMemcpyDeviceToHost, m->stream);
     if (mem_kind == HF_HOST) {
         cudaError_t e2 = cudaStreamSynchronize(m->stream);
@@ -396,6 +396,12 @@ int hair_fuse_mlp_load(hf_mlp* m, const char* path) {
 }
 
 const char* hair_fuse_mlp_last_error(const hf_mlp* m) { return m ? m->err.c_str() : hair_fuse_last_error(nullptr); }
+
+int hair_fuse_mlp_set_wait_limit(hf_mlp* m, unsigned long long wait_ns) {
+    if (!m) return HF_ERR_INVALID_ARG;
+    m->wait_ns = wait_ns;
+    return HF_OK;
+}
 
 }  // extern "C"
 
@@ -517,7 +523,7 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
     if ((rc = run_launch(c, "k_featpos", [&] { return hf_launch_featpos(fa, s); }))) return rc;
     if ((rc = run_launch(c, "k_mlp", [&] {
              return hf_mlp_infer(m->d, m->P, (const uint16_t*)c->feat.p, N, (float*)c->prop.p,
-                                 (uint32_t*)c->errw.p, s);
+                                 (uint32_t*)c->errw.p, s, false, m->wait_ns);
          })))
         return rc;
     // the proposal's cost decides: above tau -> the plain fusion (fallback list), else the short
@@ -567,7 +573,7 @@ extern "C" int hair_fuse_fuse_learned(hf_ctx* c, hf_mlp* m, int T_short, float a
 
 cudaError_t hf_mlp_infer_rows(hf_mlp* m, const uint16_t* x, long long n, float* dir_out, uint32_t* errw, cudaStream_t s) {
     if (n <= 0 || n > 0x7fffffffLL) return cudaErrorInvalidValue;
-    return hf_mlp_infer(m->d, m->P, x, (int)n, dir_out, errw, s);
+    return hf_mlp_infer(m->d, m->P, x, (int)n, dir_out, errw, s, false, m->wait_ns);
 }
 
 cudaStream_t hf_mlp_stream(hf_mlp* m) { return m->stream; }

@@ -50,6 +50,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t
     return true;
 }
 
+// The same wait with a suspend-time hint: each try_wait gives up after about hint_ns (at most 1 ms)
+// instead of the system-dependent limit, so even a limit of a few nanoseconds expires on a phase
+// that is not already complete.  Used when a caller sets a short limit to test the expiry path.
+__device__ __forceinline__ bool mbar_try_hint(uint64_t* b, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_hinted(uint64_t* b, uint32_t parity, uint64_t timeout_ns) {
+    const uint32_t hint = timeout_ns < 1000000ull ? (uint32_t)timeout_ns : 1000000u;
+    if (mbar_try_hint(b, parity, hint)) return true;
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_hint(b, parity, hint))
+        if (globaltimer() - t0 > timeout_ns) return false;
+    return true;
+}
+
 // The same wait for threads that have nothing else to do: between tests the thread sleeps, so a
 // warp that waits long does not take issue slots from the warps that work.
 __device__ __forceinline__ bool mbar_wait_idle(uint64_t* b, uint32_t parity, uint64_t timeout_ns) {

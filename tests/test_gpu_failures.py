@@ -1,7 +1,7 @@
 """Failure paths that can be exercised without faulting the GPU.
 
-A bounded device wait is made to expire by giving the GEMM's pipeline a limit of 1 ns: the call must
-report HF_ERR_TIMEOUT (the CTAs drain their own copies and tensor-core work, which complete by
+A bounded device wait is made to expire by giving the GEMM's (or the network kernel's) pipeline a
+limit of 1 ns: the call must report HF_ERR_TIMEOUT (the CTAs drain their own copies and tensor-core work, which complete by
 themselves, before they release shared and tensor memory) and the next call must run normally.
 An out-of-memory condition is injected on the host at every device allocation a fusion makes in
 turn: the call that needed it must return HF_ERR_OOM, and destroying the context must give all
@@ -34,6 +34,30 @@ def test_forced_wait_expiry_then_clean_call():
         assert rc == hf.HF_OK, hf.hair_fuse_last_error(None)
         torch.cuda.synchronize()
         assert (c - ref).abs().max().item() <= 2e-5 * ref.abs().max().item() + 1e-3
+
+
+def test_network_forced_wait_expiry_then_clean_call():
+    """The fused inference kernel in its test mode (a 1 ns limit on every pipeline wait, and a wait on
+    a barrier nothing completes once the first tile's layer-1 steps are in flight): HF_ERR_TIMEOUT,
+    with the warps draining their own copies and tensor-core steps before the CTA releases its
+    memory; then, back in normal operation, the same proposals as before, bit for bit."""
+    import paper_2604_05794_b300 as hf
+    net = hf.ProposalNet(1024)
+    net.init(3)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1.0, 1.0, size=(3000, 64)).astype(np.float32)
+    x[:, 51:] = 0.0
+    X = (x.view(np.uint32) >> 16).astype(np.uint16)   # bf16 codes (truncated)
+    ref = net.forward(X)
+    for _ in range(2):
+        assert hf.hair_fuse_mlp_set_wait_limit(net.h, 1) == hf.HF_OK
+        with pytest.raises(hf.HairFuseError) as e:
+            net.forward(X)
+        assert e.value.code == hf.HF_ERR_TIMEOUT
+        assert b"bounded device wait expired" in hf.hair_fuse_mlp_last_error(net.h)
+        assert hf.hair_fuse_mlp_set_wait_limit(net.h, 0) == hf.HF_OK
+        assert np.array_equal(net.forward(X), ref)
+    net.close()
 
 
 def _fuse_once(hf, sc, H, T):
