@@ -100,7 +100,8 @@ int hair_fuse_set_stream(hf_ctx* ctx, void* cuda_stream);
  *  angle: V x height x width f32, orientation angle theta in [0, pi) in pixel axes (+u right,
  *         +v down), row-major (row = v, column = u).
  *  conf:  V x height x width, f32 or IEEE half (conf_dtype HF_F32 / HF_F16), values in [0, 1].
- * Errors: V < 1, width/height < 1, null pointers, bad dtype -> HF_ERR_INVALID_ARG. */
+ * Errors: V < 1, width/height < 1, null pointers, bad dtype -> HF_ERR_INVALID_ARG; a map of more
+ * than 2^31 pixels or a side above 2^22 pixels -> HF_ERR_SHAPE. */
 int hair_fuse_upload_views(hf_ctx* ctx, int V, int width, int height, const float* cams, const float* angle,
                            const void* conf, int conf_dtype, int mem_kind);
 

@@ -194,6 +194,7 @@ int hair_fuse_upload_views(hf_ctx* c, int V, int width, int height, const float*
     if (!cams || !angle || !conf) return hf_set_err(c, HF_ERR_INVALID_ARG, "null view pointer");
     if (conf_dtype != HF_F32 && conf_dtype != HF_F16) return hf_set_err(c, HF_ERR_INVALID_ARG, "conf_dtype must be HF_F32 or HF_F16");
     if ((long long)width * height > (1LL << 31)) return hf_set_err(c, HF_ERR_SHAPE, "map larger than 2^31 pixels");
+    if (width > (1 << 22) || height > (1 << 22)) return hf_set_err(c, HF_ERR_SHAPE, "map side above 2^22 pixels");
     const size_t npx = (size_t)V * width * height;
     const size_t cb = conf_dtype == HF_F16 ? 2 : 4;
     if ((rc = hf_ensure(c, c->cams, (size_t)V * 16 * sizeof(float)))) return rc;

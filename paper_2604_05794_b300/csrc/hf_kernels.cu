@@ -86,8 +86,10 @@ __device__ __forceinline__ bool pixel_of(const float* __restrict__ cam, float p0
     bool decided = false;
     if (zlo > 2e-6f) {
         const float ra = __fdiv_rn(x0, x2), rb = __fdiv_rn(x1, x2);
-        const float dra = 1.01f * ((e0 + fabsf(ra) * e2) / zlo + 0x1p-23f * fabsf(ra));
-        const float drb = 1.01f * ((e1 + fabsf(rb) * e2) / zlo + 0x1p-23f * fabsf(rb));
+        // 1 / zlo rounded up: the bounds take a product instead of two divisions
+        const float rz = __frcp_ru(zlo);
+        const float dra = 1.01f * ((e0 + fabsf(ra) * e2) * rz + 0x1p-23f * fabsf(ra));
+        const float drb = 1.01f * ((e1 + fabsf(rb) * e2) * rz + 0x1p-23f * fabsf(rb));
         const float u = fmaf(fx, ra, cx), v = fmaf(fy, rb, cy);
         const float eu = 1.01f * (fabsf(fx) * dra + 0x1p-23f * fabsf(u)) + 1e-30f;
         const float ev = 1.01f * (fabsf(fy) * drb + 0x1p-23f * fabsf(v)) + 1e-30f;
@@ -163,7 +165,11 @@ __device__ __forceinline__ void project_tile(const ProjectArgs& a, int blk) {
             if (v >= a.V) continue;
             float fu, fv, ra, rb;
             if (!pixel_of(a.cams + 16 * v, p0, p1, p2, a.W, a.H, fu, fv, ra, rb)) continue;
-            off[q] = (long long)((size_t)v * npx + (size_t)fv * a.W + (size_t)fu);
+            // fu, fv are whole numbers below 2^22: the integer is the low mantissa bits of
+            // f + 1.5 * 2^23 (exact; no conversion instruction, none on the FP64 pipe)
+            const int iu = __float_as_int(fu + 12582912.0f) - 0x4B400000;
+            const int iv = __float_as_int(fv + 12582912.0f) - 0x4B400000;
+            off[q] = (long long)v * (long long)npx + (long long)(iv * a.W + iu);
             ra_[q] = ra;
             rb_[q] = rb;
         }
