@@ -48,7 +48,10 @@ def test_features_match_oracle(tiny):
         f.upload_points(tiny["points"], tiny["nbr"])
         got = f.features(np.empty((tiny["N"], 64), np.uint16))
         dev = f.features(torch.empty((tiny["N"], 64), dtype=torch.int16, device="cuda")).cpu().numpy().view(np.uint16)
-    assert np.array_equal(got, dev)
+        # a destination that is not 16-byte aligned gets the same rows (through a copy)
+        buf = torch.empty(tiny["N"] * 64 + 1, dtype=torch.int16, device="cuda")
+        odd = f.features(buf[1:].view(tiny["N"], 64)).cpu().numpy().view(np.uint16)
+    assert np.array_equal(got, dev) and np.array_equal(got, odd)
     diff = got.astype(np.int32) - want.astype(np.int32)
     # bf16 codes agree except, rarely, one unit in the last place (FP32 vs FP64 before rounding)
     assert np.max(np.abs(diff)) <= 1 and np.mean(diff != 0) < 1e-3

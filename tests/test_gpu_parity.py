@@ -203,6 +203,11 @@ def test_invalid_arguments(tiny):
     with pytest.raises(hf.HairFuseError):
         f.sync()
     f.sync()   # cleared
+    # a map side above 2^22 pixels is refused before anything is copied
+    wide = np.zeros((1, 1, (1 << 22) + 1), np.float32)
+    with pytest.raises(hf.HairFuseError) as e:
+        f.upload_views(tiny["cams"][:1], wide, wide)
+    assert e.value.code == hf.HF_ERR_SHAPE
     f.close()
 
 
