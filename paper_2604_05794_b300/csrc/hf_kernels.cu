@@ -596,12 +596,17 @@ cudaError_t launch_select_kp(const LearnArgs& a, cudaStream_t s) {
 }  // namespace
 
 // The refinement's layout for view sets of up to veff views: lanes over views when the view set
-// fills at least 7/8 of a group's view slots (the patch then stays in registers for all rounds at
-// little idle-lane cost), else a point per thread (no idle lanes, the patch copied per round).
+// fills at least 7/8 of a group's view slots and, for patches of up to 9 members, a group is at
+// most 16 lanes (the patch then stays in registers for all rounds at little idle-lane cost), else
+// a point per thread (no idle lanes, the patch staged per round).  Measured at k = 8: 32 lanes lose
+// to a point per thread (64 views, 1M points: 6.23 against 5.69 ms), 16 lanes tie (32 views:
+// 0.59 ms both), and 4 lanes win on a few thousand points, where a thread per point leaves the
+// GPU idle.  Larger patches keep 32 lanes (a point per thread stages 18 members per view there).
 int hf_cost_lanes(int veff, int k) {
-    const int sm = slots_for_kp(kp_for(k));
+    const int kp = kp_for(k), sm = slots_for_kp(kp);
     int L = 4;
     while (L < 32 && L * sm < veff) L *= 2;
+    if (L >= 32 && kp <= 9) return 0;
     return 8 * veff >= 7 * L * sm ? L : 0;
 }
 
