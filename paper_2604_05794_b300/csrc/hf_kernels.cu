@@ -602,9 +602,6 @@ cudaError_t launch_select_kp(const LearnArgs& a, cudaStream_t s) {
 // to a point per thread (64 views, 1M points: 6.23 against 5.69 ms), 16 lanes tie (32 views:
 // 0.59 ms both), and 4 lanes win on a few thousand points, where a thread per point leaves the
 // GPU idle.  Larger patches keep 32 lanes (a point per thread stages 18 members per view there).
-// A single scene's fallback list (a fifth of 1M points, 64 views) would take 1.54 ms with 32 lanes
-// against 1.71 ms, but batch and single-scene runs must take the same layout to agree bit for bit,
-// and the serving batch gains more from a point per thread.
 int hf_cost_lanes(int veff, int k) {
     const int kp = kp_for(k), sm = slots_for_kp(kp);
     int L = 4;
