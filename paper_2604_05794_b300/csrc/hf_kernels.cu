@@ -487,7 +487,10 @@ using namespace hf_bt;
 template <bool FEAT>
 __global__ void __launch_bounds__(kProjectThreads, 7) k_project_batch(const ProjectArgs* __restrict__ pa, BatchCtl c) {
     batch_tiles(pa, c, [](const ProjectArgs& a) { return (a.N + kProjectThreads - 1) / kProjectThreads; },
-                [](const ProjectArgs& a, int blk) {
+                [](const ProjectArgs& sa, int blk) {
+                    // a register copy: the tile's stores could alias the shared-memory arguments,
+                    // which would make every field access a reload from shared memory
+                    const ProjectArgs a = sa;
                     if (a.top_k > 0) project_tile<true, FEAT>(a, blk);
                     else project_tile<false, FEAT>(a, blk);
                 });
