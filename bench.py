@@ -114,16 +114,16 @@ def alu_peak(reps=5):
 # sources it was taken on: the first 12 hex digits of the SHA-256 of every csrc/*.cu and *.cuh file
 # (in name order).  After any source change every kernel reports traffic null until captured again.
 TRAFFIC = {
-    "k_project_batch": (27.17, "point-view (N V)", "ce6d1ef798ac", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_featpos_batch": (37.81, "point", "ce6d1ef798ac", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_mlp": (137.66, "point (feature row)", "ce6d1ef798ac", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_select_batch": (32.91, "point-view (N V)", "ce6d1ef798ac", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_refine_short_batch": (74.20, "accepted point-view", "ce6d1ef798ac", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_argmin_batch": (76.49, "fallback point-view", "ce6d1ef798ac", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_refine_batch": (305.65, "fallback point-view", "ce6d1ef798ac", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
-    "k_project": (35.57, "point-view (N V)", "ce6d1ef798ac", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
-    "k_argmin": (19.48, "point-view in V_i", "ce6d1ef798ac", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
-    "k_refine": (20.73, "point-view in V_i", "ce6d1ef798ac", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_project_batch": (27.82, "point-view (N V)", "b73f0f2b1272", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_featpos_batch": (37.50, "point", "b73f0f2b1272", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_mlp": (137.58, "point (feature row)", "b73f0f2b1272", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_select_batch": (32.91, "point-view (N V)", "b73f0f2b1272", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_refine_short_batch": (74.16, "accepted point-view", "b73f0f2b1272", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_argmin_batch": (76.47, "fallback point-view", "b73f0f2b1272", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_refine_batch": (305.76, "fallback point-view", "b73f0f2b1272", "ncu --set full, 4-scene serving batch (seeds 200-203, 1,979,650 points), scaled by units"),
+    "k_project": (34.87, "point-view (N V)", "b73f0f2b1272", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_argmin": (19.50, "point-view in V_i", "b73f0f2b1272", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
+    "k_refine": (20.70, "point-view in V_i", "b73f0f2b1272", "ncu --set full, mid workload (200,000 points, 32 views 1024x1024), scaled by units"),
 }
 
 
