@@ -386,7 +386,11 @@ const char* hair_fuse_mlp_last_error(const hf_mlp* mlp);
  * batches that use this network. */
 int hair_fuse_mlp_set_wait_limit(hf_mlp* mlp, unsigned long long wait_ns);
 
-/* Features (N x 64 bf16, kind mem_kind) of the uploaded scene's points. */
+/* Features (N x 64 bf16, kind mem_kind) of the uploaded scene's points, as the learned fusion
+ * computes them: the projection writes the view part (it also refreshes the context's per-view
+ * samples, which the next fusion recomputes anyway), then the position part.  A device x_out that
+ * is not 16-byte aligned is filled through a copy.  Errors: NULL arguments or a bad mem_kind ->
+ * HF_ERR_INVALID_ARG; no views or points uploaded -> HF_ERR_NOT_UPLOADED; HF_ERR_OOM, HF_ERR_CUDA. */
 int hair_fuse_features(hf_ctx* ctx, uint16_t* x_out, int mem_kind);
 
 /* Learned fusion of all uploaded points: proposal from the network and its cost c_i; points whose
