@@ -57,6 +57,23 @@ def test_features_match_oracle(tiny):
     assert np.max(np.abs(diff)) <= 1 and np.mean(diff != 0) < 1e-3
 
 
+@pytest.mark.parametrize("V,top_k", [(1, 0), (7, 0), (21, 0), (21, 4)])
+def test_features_other_view_counts(V, top_k):
+    """The projection writes the view features for the 16 slots v_m = floor(m V / 16): with V < 16
+    several slots share a view, with V > 16 most views have no slot, an odd V ends on a half pair, and
+    top-K view sets do not change them."""
+    import paper_2604_05794_b300 as hf
+    sc = scenegen.make_scene("mid", seed=60 + V, n_strands=40, V=V, width=384, height=384, f=450.0)
+    want = om.bf16_bits(oracle.features(oracle.Scene.from_dict(sc)))
+    with hf.HairFuse(32, sc["k"], 4, top_k_views=top_k) as f:
+        f.upload_views(sc["cams"], sc["angle"], sc["conf"])
+        f.upload_points(sc["points"], sc["nbr"])
+        got = f.features(np.empty((sc["N"], 64), np.uint16))
+    diff = got.astype(np.int32) - want.astype(np.int32)
+    assert np.max(np.abs(diff)) <= 1 and np.mean(diff != 0) < 1e-3
+    assert np.all(got[:, 51:] == 0)
+
+
 def test_inference_gelu_error_bound():
     """The inference epilogues' GELU (a clamped polynomial, no erf) against x Phi(x) in FP64: every
     256th FP32 bit pattern with 2^-20 <= |x| < 2^7, every FP32 value within 2^-10 of the clamp points
